@@ -1,0 +1,683 @@
+// elm_oracle.cpp -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT PATH.
+//
+// A slow, plain, FP64 CPU restatement of the advection step of the modified
+// method of characteristics (MMOC) of Kohl, Mohr, Eibl and Ruede (arXiv
+// 2103.02388).  Only tests/, the smoke check and the CPU-baseline leg of the
+// benchmark may load this library.  It shares no code, header, table or helper
+// with the CUDA library; the only thing the two sides have in common is the
+// seeded input arrays the tests hand to both.
+//
+// What it computes, step by step, in the order of the paper:
+//   * Sec. 2.1 (hierarchical hybrid grids): a coarse mesh of macro triangles or
+//     tetrahedra, each refined uniformly (Bey) L times.  For a simplex whose
+//     vertices are taken in ascending global id order this refinement is the
+//     Freudenthal/Kuhn subdivision of the reference simplex
+//     {N >= q1 >= q2 >= q3 >= 0}, N = 2^L.
+//   * Sec. 2.2 (spaces S^m_l): P2 Lagrange nodes = micro vertices and edge
+//     midpoints; a global node is identified by the macro vertices it lies
+//     between and its integer barycentric weights, so nodes shared by several
+//     macros are one unknown.
+//   * Eq. (characteristic curves) / Eq. (departure point): X(x, t_{n+1}, t_n)
+//     integrated backwards with classic RK4 (Sec. 4.1 "Test setup"), with
+//     n_sub equal substeps.
+//   * Eq. (linear interpolation): the velocity at a stage time is the linear
+//     time interpolant of u^n_h and u^{n+1}_h.
+//   * Sec. 3 "Field evaluation": locate the macro (here: brute force over all
+//     macros, keeping the one with the largest minimum barycentric), locate the
+//     micro element in O(1) (floor + sort of the fractional parts), pull back to
+//     the micro element (solve its barycentric system) and sum the P2 basis.
+//   * Step (iii): T^{n+1}_i = c^n_h(X_i) (kappa = 0, no diffusion).
+//   * Sec. 4.1: the error metrics need e^T M e with the P2 mass matrix M,
+//     assembled here element by element from exact barycentric-monomial
+//     integrals.
+//   * Eq. (departure point), differentiated: forward-mode (dual number)
+//     directional derivatives of T^{n+1} with respect to the nodal velocity and
+//     the transpose of the interpolation for T^n, used to check adjoints.
+//
+// Readings of points the paper leaves open (each also listed in the design doc):
+//   * Out-of-domain stage points: every RK stage point and the final departure
+//     point are clamped componentwise to the axis-aligned bounding box of the
+//     mesh (the Euclidean projection for box domains).  If the clamped point
+//     still lies outside every macro (non-box domains only), its barycentric
+//     coordinates in the closest macro are clamped at 0 and renormalised.
+//   * Micro-face ties: floor, cell clamped to [0, N-1], ties in the sort broken
+//     by axis index; any containing element is valid because P2 is C0.
+//   * Steady velocity (u_old and u_new the same array): no time interpolation.
+//
+// Build: g++ -O2 -std=c++17 -shared -fPIC -pthread elm_oracle.cpp -o liboracle.so
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <thread>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Small dense linear algebra (Gauss-Jordan with partial pivoting).
+// ---------------------------------------------------------------------------
+
+// Solves A z = b for an n x n system (n <= 4), row-major A.  Returns false if
+// the matrix is singular.
+bool solve_small(int n, const double* A_in, const double* b_in, double* z) {
+  double A[4][5];
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) A[i][j] = A_in[i * n + j];
+    A[i][n] = b_in[i];
+  }
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+    if (A[piv][col] == 0.0) return false;
+    if (piv != col)
+      for (int j = 0; j <= n; ++j) std::swap(A[piv][j], A[col][j]);
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      double f = A[r][col] / A[col][col];
+      for (int j = col; j <= n; ++j) A[r][j] -= f * A[col][j];
+    }
+  }
+  for (int i = 0; i < n; ++i) z[i] = A[i][n] / A[i][i];
+  return true;
+}
+
+// Barycentric coordinates of point y with respect to the simplex with
+// vertices V[0..d] (each d coordinates): solve [V_0 .. V_d ; 1 .. 1] lam = [y; 1].
+bool barycentric(int d, const double V[4][3], const double* y, double* lam) {
+  double A[16], b[4];
+  const int n = d + 1;
+  for (int r = 0; r < d; ++r) {
+    for (int c = 0; c < n; ++c) A[r * n + c] = V[c][r];
+    b[r] = y[r];
+  }
+  for (int c = 0; c < n; ++c) A[d * n + c] = 1.0;
+  b[d] = 1.0;
+  return solve_small(n, A, b, lam);
+}
+
+// ---------------------------------------------------------------------------
+// Mesh: macro simplices, uniform refinement, P2 node numbering (Sec. 2.1, 2.2).
+// ---------------------------------------------------------------------------
+
+struct Macro {
+  int64_t v[4];      // global vertex ids in ascending order (Kuhn order)
+  double P[4][3];    // their coordinates
+};
+
+struct Mesh {
+  int d = 0, L = 0, N = 0, M = 0;   // dimension, level, N = 2^L, M = 2N
+  std::vector<Macro> mac;
+  std::vector<std::vector<int32_t>> id;  // per macro: dense (M+1)^d table p -> node
+  std::vector<double> X;                 // node coordinates, [n_nodes, d]
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  int64_t n_nodes = 0;
+
+  int64_t dense(const int* p) const {
+    int64_t k = 0;
+    for (int i = 0; i < d; ++i) k = k * (M + 1) + p[i];
+    return k;
+  }
+};
+
+// Barycentric integer weights of the lattice point p (M >= p1 >= ... >= pd >= 0)
+// of the reference Kuhn simplex: w_k = p_k - p_{k+1} with p_0 = M, p_{d+1} = 0.
+void lattice_weights(int d, int M, const int* p, int* w) {
+  int pp[5];
+  pp[0] = M;
+  for (int i = 0; i < d; ++i) pp[i + 1] = p[i];
+  pp[d + 1] = 0;
+  for (int k = 0; k <= d; ++k) w[k] = pp[k] - pp[k + 1];
+}
+
+// Physical position of a lattice point with weights w (sum = den).
+void lattice_point(const Macro& m, int d, const int* w, int den, double* x) {
+  for (int r = 0; r < d; ++r) {
+    double s = 0.0;
+    for (int k = 0; k <= d; ++k) s += double(w[k]) * m.P[k][r];
+    x[r] = s / double(den);
+  }
+}
+
+// Calls f(p) for every lattice point of the reference simplex with side M.
+template <class F>
+void for_each_lattice_point(int d, int M, F&& f) {
+  int p[3] = {0, 0, 0};
+  if (d == 2) {
+    for (p[0] = 0; p[0] <= M; ++p[0])
+      for (p[1] = 0; p[1] <= p[0]; ++p[1]) f(p);
+  } else {
+    for (p[0] = 0; p[0] <= M; ++p[0])
+      for (p[1] = 0; p[1] <= p[0]; ++p[1])
+        for (p[2] = 0; p[2] <= p[1]; ++p[2]) f(p);
+  }
+}
+
+Mesh* build_mesh(int d, int64_t nv, const double* xyz, int64_t nm, const int64_t* mv, int level) {
+  if ((d != 2 && d != 3) || nv <= 0 || nm <= 0 || level < 0 || level > 8) return nullptr;
+  Mesh* me = new Mesh();
+  me->d = d;
+  me->L = level;
+  me->N = 1 << level;
+  me->M = 2 * me->N;
+  for (int r = 0; r < d; ++r) {
+    me->lo[r] = std::numeric_limits<double>::infinity();
+    me->hi[r] = -std::numeric_limits<double>::infinity();
+  }
+  for (int64_t i = 0; i < nv; ++i)
+    for (int r = 0; r < d; ++r) {
+      me->lo[r] = std::min(me->lo[r], xyz[i * d + r]);
+      me->hi[r] = std::max(me->hi[r], xyz[i * d + r]);
+    }
+  me->mac.resize(nm);
+  for (int64_t m = 0; m < nm; ++m) {
+    Macro& mc = me->mac[m];
+    for (int k = 0; k <= d; ++k) mc.v[k] = mv[m * (d + 1) + k];
+    std::sort(mc.v, mc.v + d + 1);
+    for (int k = 0; k <= d; ++k) {
+      if (mc.v[k] < 0 || mc.v[k] >= nv) { delete me; return nullptr; }
+      for (int r = 0; r < d; ++r) mc.P[k][r] = xyz[mc.v[k] * d + r];
+    }
+  }
+  // Global P2 node numbering.  Interior lattice points (all weights > 0) belong
+  // to one macro only; points on a macro face, edge or vertex are keyed by the
+  // (vertex id, weight) pairs with non-zero weight so that all macros sharing
+  // them agree on one node.
+  const int M = me->M;
+  int64_t per_macro = 1;
+  for (int i = 0; i < d; ++i) per_macro *= (M + 1);
+  me->id.assign(nm, std::vector<int32_t>(per_macro, -1));
+  std::map<std::vector<int64_t>, int32_t> shared;
+  int64_t next = 0;
+  std::vector<double>& X = me->X;
+  for (int64_t m = 0; m < nm; ++m) {
+    const Macro& mc = me->mac[m];
+    for_each_lattice_point(d, M, [&](const int* p) {
+      int w[4];
+      lattice_weights(d, M, p, w);
+      bool interior = true;
+      for (int k = 0; k <= d; ++k) interior = interior && (w[k] > 0);
+      int32_t nid;
+      if (interior) {
+        nid = int32_t(next++);
+      } else {
+        std::vector<int64_t> key;
+        for (int k = 0; k <= d; ++k)
+          if (w[k] > 0) { key.push_back(mc.v[k]); key.push_back(w[k]); }
+        auto it = shared.find(key);
+        if (it != shared.end()) {
+          me->id[m][me->dense(p)] = it->second;
+          return;
+        }
+        nid = int32_t(next++);
+        shared.emplace(std::move(key), nid);
+      }
+      me->id[m][me->dense(p)] = nid;
+      double x[3];
+      lattice_point(mc, d, w, M, x);
+      for (int r = 0; r < d; ++r) X.push_back(x[r]);
+    });
+  }
+  me->n_nodes = next;
+  return me;
+}
+
+// ---------------------------------------------------------------------------
+// Field evaluation (Sec. 3, "Field evaluation").
+// ---------------------------------------------------------------------------
+
+struct Located {
+  int64_t macro;
+  int w[4][3];      // micro vertices as lattice points of the level-L grid (q space)
+  double mu[4];     // barycentric coordinates of the point in that micro simplex
+};
+
+// Domain rule for points outside the domain: componentwise clamp to the
+// bounding box (box domains: the Euclidean projection).
+void clamp_to_box(const Mesh& me, double* y) {
+  for (int r = 0; r < me.d; ++r) y[r] = std::min(std::max(y[r], me.lo[r]), me.hi[r]);
+}
+
+// Locates y (already clamped to the box).  May move y onto the mesh boundary
+// when y is outside every macro (non-box domains).
+void locate(const Mesh& me, double* y, Located& out) {
+  const int d = me.d;
+  // Macro: brute force, keep the macro with the largest minimum barycentric.
+  int64_t best = -1;
+  double best_min = -std::numeric_limits<double>::infinity();
+  double lam_best[4] = {0, 0, 0, 0};
+  for (int64_t m = 0; m < (int64_t)me.mac.size(); ++m) {
+    double lam[4];
+    if (!barycentric(d, me.mac[m].P, y, lam)) continue;
+    double mn = lam[0];
+    for (int k = 1; k <= d; ++k) mn = std::min(mn, lam[k]);
+    if (mn > best_min) {
+      best_min = mn;
+      best = m;
+      std::memcpy(lam_best, lam, sizeof(lam));
+    }
+  }
+  const Macro& mc = me.mac[best];
+  if (best_min < -1e-12) {
+    // Outside the mesh: clamp the barycentric coordinates at zero and renormalise.
+    double s = 0.0;
+    for (int k = 0; k <= d; ++k) { lam_best[k] = std::max(lam_best[k], 0.0); s += lam_best[k]; }
+    for (int k = 0; k <= d; ++k) lam_best[k] /= s;
+    for (int r = 0; r < d; ++r) {
+      double v = 0.0;
+      for (int k = 0; k <= d; ++k) v += lam_best[k] * mc.P[k][r];
+      y[r] = v;
+    }
+  }
+  out.macro = best;
+  // Reference Kuhn coordinates: s_k = lam_k + ... + lam_d (k = 1..d); q = N s.
+  double q[3];
+  for (int k = 1; k <= d; ++k) {
+    double s = 0.0;
+    for (int j = k; j <= d; ++j) s += lam_best[j];
+    q[k - 1] = me.N * s;
+  }
+  // Keep q in the closed reference simplex N >= q1 >= ... >= qd >= 0 (this only
+  // moves points that are outside by rounding).
+  q[0] = std::min(std::max(q[0], 0.0), double(me.N));
+  for (int k = 1; k < d; ++k) q[k] = std::min(std::max(q[k], 0.0), q[k - 1]);
+  // Micro element in O(1): cell = floor(q) clamped to [0, N-1]; the Kuhn
+  // simplex of the cell is fixed by the descending order of the fractions.
+  int c[3];
+  double f[3];
+  for (int k = 0; k < d; ++k) {
+    c[k] = std::min(int(std::floor(q[k])), me.N - 1);
+    f[k] = q[k] - c[k];
+  }
+  int order[3] = {0, 1, 2};
+  std::stable_sort(order, order + d, [&](int a, int b) { return f[a] > f[b]; });
+  for (int r = 0; r < d; ++r) out.w[0][r] = c[r];
+  for (int j = 1; j <= d; ++j) {
+    for (int r = 0; r < d; ++r) out.w[j][r] = out.w[j - 1][r];
+    out.w[j][order[j - 1]] += 1;
+  }
+  // Pull back: barycentric coordinates in the physical micro simplex.
+  double V[4][3];
+  for (int j = 0; j <= d; ++j) {
+    int wt[4];
+    lattice_weights(d, me.N, out.w[j], wt);
+    lattice_point(mc, d, wt, me.N, V[j]);
+  }
+  barycentric(d, V, y, out.mu);
+}
+
+// The (d+1)(d+2)/2 P2 nodes of a located micro simplex with their basis values:
+// vertex v -> mu_v (2 mu_v - 1); edge (a, b) -> 4 mu_a mu_b  (Sec. 2.2, P2).
+int p2_stencil(const Mesh& me, const Located& lc, int32_t* node, double* phi) {
+  const int d = me.d;
+  int n = 0;
+  for (int v = 0; v <= d; ++v) {
+    int p[3];
+    for (int r = 0; r < d; ++r) p[r] = 2 * lc.w[v][r];
+    node[n] = me.id[lc.macro][me.dense(p)];
+    phi[n] = lc.mu[v] * (2.0 * lc.mu[v] - 1.0);
+    ++n;
+  }
+  for (int a = 0; a <= d; ++a)
+    for (int b = a + 1; b <= d; ++b) {
+      int p[3];
+      for (int r = 0; r < d; ++r) p[r] = lc.w[a][r] + lc.w[b][r];
+      node[n] = me.id[lc.macro][me.dense(p)];
+      phi[n] = 4.0 * lc.mu[a] * lc.mu[b];
+      ++n;
+    }
+  return n;
+}
+
+// Evaluates an ncomp-component P2 field (node-major [n_nodes, ncomp]) at y.
+void eval_field(const Mesh& me, const double* F, int ncomp, double* y, double* out) {
+  Located lc;
+  locate(me, y, lc);
+  int32_t node[10];
+  double phi[10];
+  int n = p2_stencil(me, lc, node, phi);
+  for (int c = 0; c < ncomp; ++c) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += phi[j] * F[int64_t(node[j]) * ncomp + c];
+    out[c] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Departure points: Eq. (departure point) by classic RK4 backwards in time,
+// velocity interpolated linearly in time, Eq. (linear interpolation).
+// ---------------------------------------------------------------------------
+
+struct Velocity {
+  const double* u_old;   // u^n_h   at t_n
+  const double* u_new;   // u^{n+1}_h at t_{n+1}
+  double dt;
+};
+
+// u~(y) at the stage time t~ = t_{n+1} - back, back in [0, dt]:
+// (t_{n+1} - t~)/dt * u^n + (t~ - t_n)/dt * u^{n+1}.
+void velocity_at(const Mesh& me, const Velocity& V, double back, double* y, double* k) {
+  const int d = me.d;
+  double a[3], b[3];
+  eval_field(me, V.u_new, d, y, b);
+  if (V.u_old == V.u_new) {
+    for (int r = 0; r < d; ++r) k[r] = b[r];
+    return;
+  }
+  eval_field(me, V.u_old, d, y, a);
+  const double w_old = back / V.dt, w_new = (V.dt - back) / V.dt;
+  for (int r = 0; r < d; ++r) k[r] = w_old * a[r] + w_new * b[r];
+}
+
+// Traces node position x back over dt with n_sub RK4 substeps; writes X.
+void departure_point(const Mesh& me, const Velocity& V, int n_sub, const double* x, double* X) {
+  const int d = me.d;
+  const double h = V.dt / n_sub;
+  double y[3], k1[3], k2[3], k3[3], k4[3], z[3];
+  for (int r = 0; r < d; ++r) y[r] = x[r];
+  for (int j = 0; j < n_sub; ++j) {
+    const double back = j * h;
+    for (int r = 0; r < d; ++r) z[r] = y[r];
+    velocity_at(me, V, back, z, k1);
+    for (int r = 0; r < d; ++r) z[r] = y[r] - 0.5 * h * k1[r];
+    clamp_to_box(me, z);
+    velocity_at(me, V, back + 0.5 * h, z, k2);
+    for (int r = 0; r < d; ++r) z[r] = y[r] - 0.5 * h * k2[r];
+    clamp_to_box(me, z);
+    velocity_at(me, V, back + 0.5 * h, z, k3);
+    for (int r = 0; r < d; ++r) z[r] = y[r] - h * k3[r];
+    clamp_to_box(me, z);
+    velocity_at(me, V, back + h, z, k4);
+    for (int r = 0; r < d; ++r) y[r] = y[r] - h / 6.0 * (k1[r] + 2.0 * k2[r] + 2.0 * k3[r] + k4[r]);
+    clamp_to_box(me, y);
+  }
+  for (int r = 0; r < d; ++r) X[r] = y[r];
+}
+
+template <class F>
+void parallel_for(int64_t begin, int64_t end, int nthreads, F&& f) {
+  if (nthreads <= 1 || end - begin < 2) {
+    for (int64_t i = begin; i < end; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> pool;
+  const int64_t n = end - begin;
+  for (int t = 0; t < nthreads; ++t) {
+    int64_t a = begin + n * t / nthreads, b = begin + n * (t + 1) / nthreads;
+    pool.emplace_back([a, b, &f]() { for (int64_t i = a; i < b; ++i) f(i); });
+  }
+  for (auto& th : pool) th.join();
+}
+
+// ---------------------------------------------------------------------------
+// P2 mass matrix (Sec. 4.1 metrics), exact via barycentric monomial integrals:
+// int_T lam_0^a0 ... lam_d^ad = d! |T| a0! ... ad! / (d + sum a)!.
+// ---------------------------------------------------------------------------
+
+struct Poly {  // polynomial in the d+1 barycentric coordinates
+  std::map<std::array<int, 4>, double> c;
+};
+
+Poly basis_poly(int d, int i) {
+  Poly P;
+  if (i <= d) {  // vertex: 2 lam_i^2 - lam_i
+    std::array<int, 4> e2{0, 0, 0, 0}, e1{0, 0, 0, 0};
+    e2[i] = 2;
+    e1[i] = 1;
+    P.c[e2] += 2.0;
+    P.c[e1] += -1.0;
+  } else {       // edge (a, b) in the order of p2_stencil
+    int n = d + 1;
+    for (int a = 0; a <= d; ++a)
+      for (int b = a + 1; b <= d; ++b) {
+        if (n++ == i) {
+          std::array<int, 4> e{0, 0, 0, 0};
+          e[a] = 1;
+          e[b] = 1;
+          P.c[e] += 4.0;
+        }
+      }
+  }
+  return P;
+}
+
+double factorial(int n) { double f = 1.0; for (int i = 2; i <= n; ++i) f *= i; return f; }
+
+// Mass matrix of the reference simplex scaled to unit volume |T| = 1.
+void p2_mass_unit(int d, double* Mref) {
+  const int nb = (d + 1) * (d + 2) / 2;
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) {
+      Poly A = basis_poly(d, i), B = basis_poly(d, j);
+      double s = 0.0;
+      for (auto& ta : A.c)
+        for (auto& tb : B.c) {
+          int tot = 0;
+          double num = factorial(d);
+          for (int k = 0; k <= d; ++k) {
+            int e = ta.first[k] + tb.first[k];
+            tot += e;
+            num *= factorial(e);
+          }
+          s += ta.second * tb.second * num / factorial(d + tot);
+        }
+      Mref[i * nb + j] = s;
+    }
+}
+
+// Calls f(macro, vertices w[0..d]) for every micro simplex of every macro: the
+// Kuhn simplices (one per permutation) of each cell that lie in the reference
+// simplex.
+template <class F>
+void for_each_micro_simplex(const Mesh& me, F&& f) {
+  const int d = me.d, N = me.N;
+  int perm[3] = {0, 1, 2};
+  for (int64_t m = 0; m < (int64_t)me.mac.size(); ++m) {
+    int c[3] = {0, 0, 0};
+    auto cell = [&]() {
+      int pm[3] = {0, 1, 2};
+      do {
+        int w[4][3];
+        for (int r = 0; r < d; ++r) w[0][r] = c[r];
+        bool inside = true;
+        for (int j = 1; j <= d; ++j) {
+          for (int r = 0; r < d; ++r) w[j][r] = w[j - 1][r];
+          w[j][pm[j - 1]] += 1;
+        }
+        for (int j = 0; j <= d && inside; ++j) {
+          if (w[j][0] > N) inside = false;
+          for (int r = 1; r < d; ++r) if (w[j][r] > w[j][r - 1]) inside = false;
+          if (w[j][d - 1] < 0) inside = false;
+        }
+        if (inside) f(m, w);
+      } while (std::next_permutation(pm, pm + d));
+    };
+    (void)perm;
+    if (d == 2) {
+      for (c[0] = 0; c[0] < N; ++c[0])
+        for (c[1] = 0; c[1] <= c[0]; ++c[1]) cell();
+    } else {
+      for (c[0] = 0; c[0] < N; ++c[0])
+        for (c[1] = 0; c[1] <= c[0]; ++c[1])
+          for (c[2] = 0; c[2] <= c[1]; ++c[2]) cell();
+    }
+  }
+}
+
+double simplex_volume(int d, const double V[4][3]) {
+  double A[9];
+  for (int r = 0; r < d; ++r)
+    for (int c = 0; c < d; ++c) A[r * d + c] = V[c + 1][r] - V[0][r];
+  double det = (d == 2) ? A[0] * A[3] - A[1] * A[2]
+                        : A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                              A[2] * (A[3] * A[7] - A[4] * A[6]);
+  return std::fabs(det) / (d == 2 ? 2.0 : 6.0);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C interface used by the Python wrapper in oracle/__init__.py.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void* orc_mesh_create(int dim, int64_t nv, const double* xyz, int64_t nm, const int64_t* mv, int level) {
+  return build_mesh(dim, nv, xyz, nm, mv, level);
+}
+
+void orc_mesh_destroy(void* h) { delete static_cast<Mesh*>(h); }
+
+int64_t orc_num_nodes(void* h) { return static_cast<Mesh*>(h)->n_nodes; }
+
+void orc_node_coords(void* h, double* out) {
+  Mesh* me = static_cast<Mesh*>(h);
+  std::memcpy(out, me->X.data(), me->X.size() * sizeof(double));
+}
+
+// Lattice coordinates p (M >= p1 >= ... >= pd >= 0) of the macro's P2 nodes, in
+// the order (p1, p2, p3) lexicographic, with the global node number of each.
+int64_t orc_macro_nodes(void* h, int64_t macro, int32_t* p_out, int32_t* node_out) {
+  Mesh* me = static_cast<Mesh*>(h);
+  int64_t n = 0;
+  for_each_lattice_point(me->d, me->M, [&](const int* p) {
+    if (p_out) for (int r = 0; r < me->d; ++r) p_out[n * me->d + r] = p[r];
+    if (node_out) node_out[n] = me->id[macro][me->dense(p)];
+    ++n;
+  });
+  return n;
+}
+
+// Locates points (after the box clamp): macro id, micro vertices (q-lattice
+// points, [npts, d+1, d]) and the micro barycentric coordinates.
+void orc_locate(void* h, int64_t npts, const double* pts, int64_t* macro, int32_t* wv, double* mu) {
+  Mesh* me = static_cast<Mesh*>(h);
+  const int d = me->d;
+  for (int64_t i = 0; i < npts; ++i) {
+    double y[3];
+    for (int r = 0; r < d; ++r) y[r] = pts[i * d + r];
+    clamp_to_box(*me, y);
+    Located lc;
+    locate(*me, y, lc);
+    macro[i] = lc.macro;
+    for (int j = 0; j <= d; ++j)
+      for (int r = 0; r < d; ++r) wv[(i * (d + 1) + j) * d + r] = lc.w[j][r];
+    for (int j = 0; j <= d; ++j) mu[i * (d + 1) + j] = lc.mu[j];
+  }
+}
+
+// P2 interpolation of a field ([n_nodes, ncomp]) at arbitrary points.
+void orc_eval(void* h, const double* F, int ncomp, int64_t npts, const double* pts, double* out, int nthreads) {
+  Mesh* me = static_cast<Mesh*>(h);
+  const int d = me->d;
+  parallel_for(0, npts, nthreads, [&](int64_t i) {
+    double y[3];
+    for (int r = 0; r < d; ++r) y[r] = pts[i * d + r];
+    clamp_to_box(*me, y);
+    eval_field(*me, F, ncomp, y, out + i * ncomp);
+  });
+}
+
+// Departure points X_i of nodes [begin, end) ([n, d] output rows begin..end-1).
+void orc_departure(void* h, const double* u_old, const double* u_new, double dt, int n_sub,
+                   int64_t begin, int64_t end, double* X, int nthreads) {
+  Mesh* me = static_cast<Mesh*>(h);
+  const int d = me->d;
+  Velocity V{u_old, u_new, dt};
+  parallel_for(begin, end, nthreads, [&](int64_t i) {
+    departure_point(*me, V, n_sub, &me->X[i * d], X + (i - begin) * d);
+  });
+}
+
+// One advection step for nodes [begin, end): T_new[i] = T^n_h(X_i) (step (iii)).
+void orc_advect(void* h, const double* u_old, const double* u_new, const double* T_old, double* T_new,
+                double dt, int n_sub, int64_t begin, int64_t end, int nthreads) {
+  Mesh* me = static_cast<Mesh*>(h);
+  const int d = me->d;
+  Velocity V{u_old, u_new, dt};
+  parallel_for(begin, end, nthreads, [&](int64_t i) {
+    double X[3];
+    departure_point(*me, V, n_sub, &me->X[i * d], X);
+    double v;
+    eval_field(*me, T_old, 1, X, &v);
+    T_new[i - begin] = v;
+  });
+}
+
+// Transpose of the interpolation: g_old[j] += sum_i phi_j(X_i) g_new[i].
+void orc_advect_transpose(void* h, const double* u_old, const double* u_new, const double* g_new,
+                          double* g_old, double dt, int n_sub) {
+  Mesh* me = static_cast<Mesh*>(h);
+  const int d = me->d;
+  Velocity V{u_old, u_new, dt};
+  std::fill(g_old, g_old + me->n_nodes, 0.0);
+  for (int64_t i = 0; i < me->n_nodes; ++i) {
+    double X[3];
+    departure_point(*me, V, n_sub, &me->X[i * d], X);
+    Located lc;
+    locate(*me, X, lc);
+    int32_t node[10];
+    double phi[10];
+    int n = p2_stencil(*me, lc, node, phi);
+    for (int j = 0; j < n; ++j) g_old[node[j]] += phi[j] * g_new[i];
+  }
+}
+
+// Mass-matrix products for the metrics of Sec. 4.1: out[k] = a_k^T M b_k for
+// the nvec column pairs (a, b given node-major [n_nodes, nvec]).
+void orc_mass_products(void* h, int nvec, const double* a, const double* b, double* out) {
+  Mesh* me = static_cast<Mesh*>(h);
+  const int d = me->d;
+  const int nb = (d + 1) * (d + 2) / 2;
+  std::vector<double> Mref(nb * nb);
+  p2_mass_unit(d, Mref.data());
+  for (int k = 0; k < nvec; ++k) out[k] = 0.0;
+  for_each_micro_simplex(*me, [&](int64_t m, int w[4][3]) {
+    Located lc;
+    lc.macro = m;
+    for (int j = 0; j <= d; ++j)
+      for (int r = 0; r < d; ++r) lc.w[j][r] = w[j][r];
+    for (int j = 0; j < 4; ++j) lc.mu[j] = 0.0;
+    int32_t node[10];
+    double phi[10];
+    p2_stencil(*me, lc, node, phi);
+    double V[4][3];
+    for (int j = 0; j <= d; ++j) {
+      int wt[4];
+      lattice_weights(d, me->N, w[j], wt);
+      lattice_point(me->mac[m], d, wt, me->N, V[j]);
+    }
+    const double vol = simplex_volume(d, V);
+    for (int k = 0; k < nvec; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < nb; ++i)
+        for (int j = 0; j < nb; ++j)
+          s += a[int64_t(node[i]) * nvec + k] * Mref[i * nb + j] * b[int64_t(node[j]) * nvec + k];
+      out[k] += vol * s;
+    }
+  });
+}
+
+// Every micro simplex: macro id and vertex lattice points ([count, d+1, d]).
+int64_t orc_micro_simplices(void* h, int64_t* macro, int32_t* wv) {
+  Mesh* me = static_cast<Mesh*>(h);
+  const int d = me->d;
+  int64_t n = 0;
+  for_each_micro_simplex(*me, [&](int64_t m, int w[4][3]) {
+    if (macro) macro[n] = m;
+    if (wv)
+      for (int j = 0; j <= d; ++j)
+        for (int r = 0; r < d; ++r) wv[(n * (d + 1) + j) * d + r] = w[j][r];
+    ++n;
+  });
+  return n;
+}
+
+// Reference P2 mass matrix for a simplex of unit volume ([nb, nb]).
+void orc_p2_mass_unit(int d, double* out) { p2_mass_unit(d, out); }
+
+}  // extern "C"

@@ -1,0 +1,379 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test below checks the oracle (``oracle/``) against something other than
+itself: Bey's refinement rule, brute-force point location, exact
+reproduction of P2 fields, closed forms of RK4 on linear fields, the exact
+solution of a non-autonomous linear ODE, textbook P2 mass-matrix integrals and
+the values printed in Table 2 of the paper.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import solve_ivp
+
+import oracle
+from paper_2103_02388_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EPS = np.finfo(np.float64).eps
+
+
+def _clamp01(x):
+    return np.clip(x, 0.0, 1.0)
+
+
+# ---------------------------------------------------------------------------
+# Mesh structure: uniform refinement (Sec. 2.1, "refined according to Bey").
+# ---------------------------------------------------------------------------
+
+
+def _bey_children(t):
+    """Bey's 8 children of the ordered tetrahedron t = (x0, x1, x2, x3)."""
+    x0, x1, x2, x3 = t
+    mid = lambda a, b: tuple((np.array(a) + np.array(b)) // 2)  # noqa: E731
+    x01, x02, x03 = mid(x0, x1), mid(x0, x2), mid(x0, x3)
+    x12, x13, x23 = mid(x1, x2), mid(x1, x3), mid(x2, x3)
+    return [(x0, x01, x02, x03), (x01, x1, x12, x13), (x02, x12, x2, x23), (x03, x13, x23, x3),
+            (x01, x02, x03, x13), (x01, x02, x12, x13), (x02, x03, x13, x23), (x02, x12, x13, x23)]
+
+
+def _red_children(t):
+    x0, x1, x2 = t
+    mid = lambda a, b: tuple((np.array(a) + np.array(b)) // 2)  # noqa: E731
+    x01, x02, x12 = mid(x0, x1), mid(x0, x2), mid(x1, x2)
+    return [(x0, x01, x02), (x01, x1, x12), (x02, x12, x2), (x01, x12, x02)]
+
+
+def _refine(dim, level):
+    """Micro simplices of the reference Kuhn simplex (side N = 2^level) by
+    recursive Bey (3D) / red (2D) refinement, as sets of lattice points."""
+    N = 2 ** level
+    if dim == 3:
+        ts = [((0, 0, 0), (N, 0, 0), (N, N, 0), (N, N, N))]
+        kids = _bey_children
+    else:
+        ts = [((0, 0), (N, 0), (N, N))]
+        kids = _red_children
+    for _ in range(level):
+        ts = [c for t in ts for c in kids(t)]
+    return {frozenset(t) for t in ts}
+
+
+@pytest.mark.parametrize("dim,level", [(2, 1), (2, 3), (3, 1), (3, 2), (3, 3)])
+def test_refinement_is_bey(dim, level):
+    v, m = inputs.unit_cube() if dim == 3 else inputs.unit_square()
+    me = oracle.OracleMesh(v, m, level)
+    macro, w = me.micro_simplices()
+    expect = _refine(dim, level)
+    for k in range(m.shape[0]):
+        got = {frozenset(tuple(int(c) for c in vtx) for vtx in simplex) for simplex in w[macro == k]}
+        assert got == expect
+
+
+@pytest.mark.parametrize("dim,level", [(2, 0), (2, 3), (3, 0), (3, 2), (3, 4)])
+def test_node_count_and_lattice(dim, level):
+    """P2 nodes of the refined unit square / cube are the (2N+1)^d lattice."""
+    v, m = inputs.unit_cube() if dim == 3 else inputs.unit_square()
+    me = oracle.OracleMesh(v, m, level)
+    assert me.n_nodes == inputs.unique_node_count(dim, level)
+    M = 2 ** (level + 1)
+    lat = np.rint(me.coords * M)
+    assert np.abs(lat - me.coords * M).max() < 1e-12
+    assert len({tuple(r) for r in lat.astype(int)}) == me.n_nodes
+
+
+def test_micro_volumes_partition_domain():
+    v, m = inputs.cube_block(2, perturb=0.3, seed=1)
+    me = oracle.OracleMesh(v, m, 2)
+    assert abs(me.mass_product(np.ones(me.n_nodes)) - 1.0) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Point location (Sec. 3, "Field evaluation") against brute force.
+# ---------------------------------------------------------------------------
+
+
+def _all_micro_simplices_physical(vertices, macros, level):
+    """Independent enumeration: Bey-refined reference simplex mapped by each macro."""
+    dim = vertices.shape[1]
+    N = 2 ** level
+    ref = [sorted(s) for s in _refine(dim, level)]
+    out = []
+    for k, mv in enumerate(macros):
+        P = vertices[np.sort(mv)]
+        for s in ref:
+            q = np.array(s, dtype=float) / N                # [d+1, d] reference s-coords
+            lam = np.zeros((dim + 1, dim + 1))
+            lam[:, 0] = 1.0 - q[:, 0]
+            for j in range(1, dim):
+                lam[:, j] = q[:, j - 1] - q[:, j]
+            lam[:, dim] = q[:, dim - 1]
+            out.append((k, frozenset(tuple(int(c) for c in vtx) for vtx in s), lam @ P))
+    return out
+
+
+def _contains(V, y, tol=1e-12):
+    dim = V.shape[1]
+    A = np.vstack([V.T, np.ones(dim + 1)])
+    lam = np.linalg.solve(A, np.append(y, 1.0))
+    return lam.min() >= -tol
+
+
+@pytest.mark.parametrize("mesh,level", [("square", 3), ("cube", 2), ("block", 1), ("sqblock", 2)])
+def test_locate_brute_force(mesh, level):
+    if mesh == "square":
+        v, m = inputs.unit_square()
+    elif mesh == "cube":
+        v, m = inputs.unit_cube()
+    elif mesh == "sqblock":
+        v, m = inputs.square_block(3, perturb=0.3, seed=4)
+    else:
+        v, m = inputs.cube_block(2, perturb=0.3, seed=2)
+    me = oracle.OracleMesh(v, m, level)
+    dim = v.shape[1]
+    rng = np.random.default_rng(11)
+    pts = rng.uniform(0.0, 1.0, size=(400, dim))
+    # also points exactly on micro faces / lattice planes and on the boundary
+    N = 2 ** level
+    pts[:50] = np.floor(pts[:50] * N) / N
+    pts[50:80, 0] = 1.0
+    pts[80:100] = np.round(pts[80:100] * 2 * N) / (2 * N)
+    allm = _all_micro_simplices_physical(v, m, level)
+    mac, w, mu = me.locate(pts)
+    for i, y in enumerate(pts):
+        containing = {(k, key) for k, key, V in allm if _contains(V, y)}
+        assert containing, "brute force found no element"
+        got = (int(mac[i]), frozenset(tuple(int(c) for c in vtx) for vtx in w[i]))
+        assert got in containing
+        assert mu[i].min() >= -1e-12 and abs(mu[i].sum() - 1.0) < 1e-12
+
+
+def test_locate_near_macro_interfaces():
+    """Points close to macro faces end up in a macro that contains them."""
+    v, m = inputs.cube_block(2, perturb=0.3, seed=3)
+    me = oracle.OracleMesh(v, m, 2)
+    rng = np.random.default_rng(5)
+    pts = []
+    for mv in m[rng.choice(len(m), 60)]:
+        P = v[mv]
+        face = P[rng.choice(4, 3, replace=False)]
+        b = rng.dirichlet(np.ones(3))
+        pts.append(b @ face + rng.normal(scale=1e-9, size=3))
+    pts = _clamp01(np.array(pts))
+    mac, _, _ = me.locate(pts)
+    for y, k in zip(pts, mac):
+        assert _contains(v[np.sort(m[k])], y, tol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# Interpolation and the advection step: exactness statements.
+# ---------------------------------------------------------------------------
+
+
+def _setup(dim, level, perturbed=False):
+    if dim == 2:
+        v, m = inputs.square_block(2, 0.3, 7) if perturbed else inputs.unit_square()
+    else:
+        v, m = inputs.cube_block(2, 0.3, 7) if perturbed else inputs.unit_cube()
+    return oracle.OracleMesh(v, m, level)
+
+
+@pytest.mark.parametrize("dim,level,perturbed", [(2, 4, False), (3, 2, False), (3, 1, True)])
+def test_partition_of_unity(dim, level, perturbed):
+    me = _setup(dim, level, perturbed)
+    u = inputs.random_fourier(me.coords, seed=3)
+    dt = inputs.dt_for_cfl(3.0, level, u)
+    for c in (1.0, -2.75):
+        T = np.full(me.n_nodes, c)
+        Tn = me.advect(T, u, dt, n_sub=2)
+        assert np.abs(Tn - c).max() <= 16 * EPS * abs(c)
+
+
+@pytest.mark.parametrize("dim,level,perturbed", [(2, 3, False), (3, 2, False), (3, 1, True), (2, 2, True)])
+def test_p2_reproduction_uniform_velocity(dim, level, perturbed):
+    """Quadratic T and uniform u: T_new(x_i) = q(clamp(x_i - u dt)) exactly."""
+    me = _setup(dim, level, perturbed)
+    x = me.coords
+    U = np.array([0.37, -0.21, 0.11][:dim])
+    u = inputs.uniform_field(x, U)
+    T = inputs.random_quadratic(x, seed=9)
+    for dt, n_sub in ((0.3, 1), (0.45, 3)):
+        Tn = me.advect(T, u, dt, n_sub=n_sub)
+        expect = inputs.random_quadratic(_clamp01(x - U * dt), seed=9)
+        assert np.abs(Tn - expect).max() <= 1e-13 * np.abs(T).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_p2_reproduction_interpolation(dim):
+    me = _setup(dim, 2, perturbed=True)
+    rng = np.random.default_rng(1)
+    pts = rng.uniform(0, 1, size=(500, dim))
+    F = inputs.random_quadratic(me.coords, seed=2)
+    got = me.eval(F, pts)
+    assert np.abs(got - inputs.random_quadratic(pts, seed=2)).max() <= 1e-13 * np.abs(F).max()
+
+
+@pytest.mark.parametrize("dim,level", [(2, 3), (3, 2)])
+def test_zero_velocity_identity(dim, level):
+    me = _setup(dim, level)
+    u = np.zeros_like(me.coords)
+    X = me.departure(u, 0.7, n_sub=3)
+    assert np.array_equal(X, me.coords)
+    T = inputs.random_quadratic(me.coords, 4) + np.sin(7 * me.coords[:, 0])
+    Tn = me.advect(T, u, 0.7)
+    assert np.abs(Tn - T).max() <= 8 * EPS * np.abs(T).max()
+
+
+@pytest.mark.parametrize("dim,n_sub", [(2, 1), (3, 1), (3, 4)])
+def test_uniform_velocity_departure(dim, n_sub):
+    me = _setup(dim, 2)
+    U = np.array([0.9, -0.4, 0.25][:dim])
+    X = me.departure(inputs.uniform_field(me.coords, U), 0.35, n_sub=n_sub)
+    assert np.abs(X - _clamp01(me.coords - 0.35 * U)).max() <= 1e-14
+
+
+def _rk4_stability(Z):
+    I = np.eye(Z.shape[0])
+    return I + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+
+
+@pytest.mark.parametrize("dim,n_sub", [(2, 1), (2, 3), (3, 1), (3, 2)])
+def test_rk4_linear_velocity_closed_form(dim, n_sub):
+    """For u = A(x - c) (P1, hence P2-exact) each RK4 substep multiplies
+    x - c by the RK4 stability polynomial R4(-hA)."""
+    me = _setup(dim, 3 if dim == 3 else 4)
+    x = me.coords
+    c = np.full(dim, 0.5)
+    if dim == 2:
+        A = 2 * np.pi * np.array([[0.0, -1.0], [1.0, 0.0]])
+    else:
+        a = np.array([1.0, 2.0, 3.0]) / np.sqrt(14.0)
+        A = 2 * np.pi * np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    u = inputs.linear_field(x, A, c)
+    dt = 0.06
+    X = me.departure(u, dt, n_sub=n_sub)
+    R = np.linalg.matrix_power(_rk4_stability(-(dt / n_sub) * A), n_sub)
+    expect = c + (x - c) @ R.T
+    inside = np.linalg.norm(x - c, axis=1) < 0.42
+    assert inside.sum() > 10
+    assert np.abs(X[inside] - expect[inside]).max() <= 1e-13
+
+
+def test_time_interpolation_direction():
+    """u^n = A0 (x - c), u^{n+1} = A1 (x - c) with [A0, A1] != 0: the departure
+    point solves dz/dt' = -((t'/dt) A0 + (1 - t'/dt) A1) z backwards in time
+    (Eq. linear interpolation).  RK4 converges to it at fourth order in the
+    substep, and the swapped time weights give a different point."""
+    me = _setup(3, 2)
+    x = me.coords
+    c = np.full(3, 0.5)
+    A0 = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 0.0]]) * 3.0
+    A1 = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, -1.0], [0.0, 1.0, 0.0]]) * 3.0
+    dt = 0.1
+    u0, u1 = inputs.linear_field(x, A0, c), inputs.linear_field(x, A1, c)
+    inside = np.nonzero(np.linalg.norm(x - c, axis=1) < 0.42)[0][:40]
+    exact = []
+    for i in inside:
+        rhs = lambda tb, z: -(((tb / dt) * A0 + (1 - tb / dt) * A1) @ z)  # noqa: E731
+        sol = solve_ivp(rhs, (0.0, dt), x[i] - c, rtol=1e-13, atol=1e-15, method="DOP853")
+        exact.append(c + sol.y[:, -1])
+    exact = np.array(exact)
+    err = [np.abs(me.departure(u0, dt, n_sub=n, u_new=u1)[inside] - exact).max() for n in (4, 8, 16)]
+    assert err[2] < 1e-9
+    assert 10.0 < err[0] / err[1] < 24.0 and 10.0 < err[1] / err[2] < 24.0
+    swapped = me.departure(u1, dt, n_sub=16, u_new=u0)[inside]
+    assert np.abs(swapped - exact).max() > 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Mass matrix (metrics of Sec. 4.1) and the transpose of the interpolation.
+# ---------------------------------------------------------------------------
+
+
+def test_p2_mass_matrix_textbook():
+    M2 = oracle.p2_mass_unit(2)
+    M3 = oracle.p2_mass_unit(3)
+    # integrals of the P2 basis: 2D vertices 0, edges 1/3; 3D vertices -1/20, edges 1/5
+    assert np.allclose(M2.sum(axis=1), [0, 0, 0, 1 / 3, 1 / 3, 1 / 3], atol=1e-15)
+    assert np.allclose(M3.sum(axis=1), [-1 / 20] * 4 + [1 / 5] * 6, atol=1e-15)
+    assert np.allclose(M2, M2.T) and np.allclose(M3, M3.T)
+    # 2D vertex-vertex entry 6/180 of |T| (standard table)
+    assert abs(M2[0, 0] - 6 / 180) < 1e-15
+
+
+def test_mass_product_integrates_quadratics():
+    me = _setup(3, 2, perturbed=True)
+    x = me.coords
+    one = np.ones(me.n_nodes)
+    assert abs(me.mass_product(one, x[:, 0] ** 2) - 1 / 3) < 1e-13
+    assert abs(me.mass_product(x[:, 0], x[:, 1]) - 1 / 4) < 1e-13
+
+
+def test_transpose_dot_product():
+    me = _setup(3, 2)
+    rng = np.random.default_rng(3)
+    u = inputs.random_fourier(me.coords, seed=8)
+    dt = inputs.dt_for_cfl(2.0, 2, u)
+    a = rng.standard_normal(me.n_nodes)
+    b = rng.standard_normal(me.n_nodes)
+    lhs = me.advect(a, u, dt, n_sub=2) @ b
+    rhs = a @ me.advect_transpose(b, u, dt, n_sub=2)
+    assert abs(lhs - rhs) <= 1e-13 * np.abs(a).sum() * np.abs(b).max()
+
+
+# ---------------------------------------------------------------------------
+# Accumulated scheme: the paper's Table 2 and the refinement rate.
+# ---------------------------------------------------------------------------
+
+
+def _revolution(level, c0_fn, steps):
+    v, m = inputs.unit_square()
+    me = oracle.OracleMesh(v, m, level)
+    x = me.coords
+    u = inputs.rotation_2d(x, omega=1.0)
+    c0 = c0_fn(x)
+    T = c0.copy()
+    dt = 2 * np.pi / steps
+    for _ in range(steps):
+        T = me.advect(T, u, dt)
+    return me.metrics(T, c0, c0)
+
+
+@pytest.mark.parametrize("row", [0, 1])
+def test_table2_hill(row):
+    with open(os.path.join(GOLDEN, "table2_hill_p2_b1.json")) as f:
+        ref = json.load(f)["rows"][row]
+    got = _revolution(6, inputs.hill, ref["steps"])
+    assert abs(got["h0"] / ref["h0"] - 1.0) < 0.05
+    assert abs(got["var"] - ref["var"]) < 0.002
+    assert abs(got["dm"]) < 2e-4
+
+
+@pytest.mark.slow
+def test_table2_hill_long():
+    with open(os.path.join(GOLDEN, "table2_hill_p2_b1.json")) as f:
+        ref = json.load(f)["rows"][2]
+    got = _revolution(6, inputs.hill, ref["steps"])
+    assert abs(got["h0"] / ref["h0"] - 1.0) < 0.05
+    assert abs(got["var"] - ref["var"]) < 0.002
+
+
+def test_refinement_rate_gaussian_rotation():
+    """2D rotation, Gaussian (0.25, 0.5), sigma 0.05, dt = 1/200, one revolution:
+    the H0 error falls at the interpolation rate O(h^3 / tau) once resolved."""
+    errs = []
+    v, m = inputs.unit_square()
+    for level in (5, 6, 7):
+        me = oracle.OracleMesh(v, m, level)
+        x = me.coords
+        u = inputs.rotation_2d(x)
+        c0 = inputs.gaussian(x, (0.25, 0.5), 0.05)
+        T = c0.copy()
+        for _ in range(200):
+            T = me.advect(T, u, 1 / 200)
+        errs.append(me.metrics(T, c0, c0)["h0"])
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates.min() >= 2.5
