@@ -1,0 +1,352 @@
+"""Benchmark of the MMOC advection step on GB300.
+
+One step = one call of elm_advect over the whole mesh: every P2 node is
+traced back with RK4 and T^n is interpolated at its departure point
+(Algorithm 1 lines 3-4 of arXiv 2103.02388).  Prints ONE JSON line.
+
+Default workload (the throughput target's configuration): unit cube, 6 Kuhn
+macro tetrahedra, level 7 (257^3 = 16,974,593 P2 nodes), FP32, seeded
+random-Fourier velocity (max |u| = 1), Gaussian cone, CFL 4, one RK4 substep.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c3-l7-fp32|c2-l6-fp64|c3-l6-fp32]
+
+N > 1 (under torchrun): every rank advects its own independent instance of the
+workload (weak scaling, no data-path collective); the time is the maximum over
+ranks and `value` counts the nodes of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (dim, level, precision, velocity, scalar, cfl, n_sub)
+    "c3-l7-fp32": (3, 7, "fp32", "fourier", "gauss", 4.0, 1),
+    "c3-l6-fp32": (3, 6, "fp32", "fourier", "gauss", 4.0, 1),
+    "c2-l6-fp64": (3, 6, "fp64", "cellular", "slotted", 4.0, 1),
+}
+METRIC = "traced node updates/s per advection step (1 GPU), % of HBM roofline, err vs FP64 oracle"
+KERNEL_SRC = os.path.join(ROOT, "paper_2103_02388_gb300", "csrc", "advect.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "advect_traffic.json")
+
+
+def _fields(spec, coords):
+    from paper_2103_02388_gb300 import inputs
+    dim, level, precision, vel, scal, cfl, n_sub = spec
+    if vel == "fourier":
+        u = inputs.random_fourier(coords, seed=3)
+    else:
+        u = inputs.cellular_flow(coords)
+    if scal == "gauss":
+        T = inputs.gaussian(coords, (0.35, 0.5, 0.5), 0.1)
+    else:
+        T = inputs.slotted_sphere(coords)
+    if precision == "fp32":
+        u = u.astype(np.float32).astype(np.float64)
+        T = T.astype(np.float32).astype(np.float64)
+    dt = inputs.dt_for_cfl(cfl, level, u)
+    return u, T, dt
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic(workload):
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        if t.get("kernel_sha") == _kernel_hash() and workload in t.get("per_launch_bytes", {}):
+            return float(t["per_launch_bytes"][workload])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(names, r[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _cpu_baseline(spec, seconds: float = 12.0):
+    """The CPU oracle timed on a bounded sample of the same workload."""
+    import oracle
+    from paper_2103_02388_gb300 import inputs
+    dim, level = spec[0], spec[1]
+    v, m = inputs.unit_cube() if dim == 3 else inputs.unit_square()
+    om = oracle.OracleMesh(v, m, level)
+    u, T, dt = _fields(spec, om.coords)
+    threads = oracle.default_threads()
+    rng = np.random.default_rng(1)
+    n = 20000
+    while True:
+        idx = np.sort(rng.choice(om.n_nodes, min(n, om.n_nodes), replace=False))
+        t0 = time.perf_counter()
+        om.advect_nodes(T, u, dt, idx, n_sub=spec[6], threads=threads)
+        el = time.perf_counter() - t0
+        if el >= seconds / 4 or len(idx) == om.n_nodes:
+            break
+        n = int(n * min(8.0, max(2.0, seconds / 2 / max(el, 1e-3))))
+    return {"value": len(idx) / el, "unit": "node updates/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(idx)} random nodes of the same workload, one step, FP64, {threads} threads",
+            "seconds": el}
+
+
+def run_reference(args, spec):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    import oracle
+    from paper_2103_02388_gb300 import inputs
+    dim, level = spec[0], spec[1]
+    v, m = inputs.unit_cube() if dim == 3 else inputs.unit_square()
+    om = oracle.OracleMesh(v, m, level)
+    u, T, dt = _fields(spec, om.coords)
+    threads = oracle.default_threads()
+    n = min(om.n_nodes, 60000)
+    rng = np.random.default_rng(2)
+    idx = np.sort(rng.choice(om.n_nodes, n, replace=False))
+    for _ in range(warm):
+        om.advect_nodes(T, u, dt, idx[: n // 10], n_sub=spec[6], threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        om.advect_nodes(T, u, dt, idx, n_sub=spec[6], threads=threads)
+    el = time.perf_counter() - t0
+    val = n * steps / el
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "node updates/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_nodes": n},
+        "cpu_baseline": {"kind": "oracle", "cores": threads, "value": val, "unit": "node updates/s",
+                         "sample": f"{n} random nodes per step of the {args.workload} workload"},
+        "e2e": {"value": val, "unit": "node updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args, spec):
+    import torch
+    from paper_2103_02388_gb300 import elm, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dim, level, precision, vel, scal, cfl, n_sub = spec
+    v, m = inputs.unit_cube() if dim == 3 else inputs.unit_square()
+    mesh = elm.Mesh(v, m, level, precision)
+    ucoords = mesh.unique_coords()
+    u, T0, dt = _fields(spec, ucoords)
+    dtype = mesh.dtype
+    u_s = mesh.to_storage(torch.tensor(u, dtype=dtype, device=dev))
+    T_a = mesh.to_storage(torch.tensor(T0, dtype=dtype, device=dev))
+    T_b = torch.empty_like(T_a)
+    mesh.set_velocity(u_s)
+    stream = torch.cuda.current_stream()
+    n_storage, n_unique = mesh.n_nodes, mesh.n_unique
+    esz = 8 if precision == "fp64" else 4
+    alg_bytes = n_storage * (dim * esz + 2 * esz)     # read u + read T_old + write T_new
+    working_set = alg_bytes
+    l2_bytes = 129 * 2**20
+    flush = working_set < 2 * l2_bytes
+    scratch = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev) if flush else None
+
+    def step(src, dst):
+        mesh.advect(src, dt, n_sub, out=dst)
+
+    for _ in range(args.warmup):
+        step(T_a, T_b)
+        T_a, T_b = T_b, T_a
+    torch.cuda.synchronize()
+    mesh.status()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for i in range(args.steps):
+            if flush:
+                scratch.fill_(float(i))
+            starts[i].record(stream)
+            step(T_a, T_b)
+            ends[i].record(stream)
+            T_a, T_b = T_b, T_a
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    mesh.status()
+    times = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(times))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n_unique * args.steps / (total_ms * 1e-3)
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # inputs (u and T_old) from pinned memory, the step, D2H of T_new
+    u_h = u_s.cpu().pin_memory()
+    T_h = T_a.cpu().pin_memory()
+    out_h = torch.empty_like(T_h).pin_memory()
+    u_d = torch.empty_like(u_s)
+    T_d = torch.empty_like(T_a)
+    T_o = torch.empty_like(T_a)
+    e2e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        u_d.copy_(u_h, non_blocking=True)
+        T_d.copy_(T_h, non_blocking=True)
+        mesh.set_velocity(u_d)
+        mesh.advect(T_d, dt, n_sub, out=T_o)
+        out_h.copy_(T_o, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    mesh.status()
+    e2e = {"value": world * n_unique * e2e_steps / e2e_s, "unit": "node updates/s",
+           "h2d_bytes_per_step": int(u_h.numel() * esz + T_h.numel() * esz),
+           "d2h_bytes_per_step": int(out_h.numel() * esz)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "node updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": args.workload,
+            "mesh": f"unit {'cube, 6 Kuhn macro tetrahedra' if dim == 3 else 'square, 2 macro triangles'}",
+            "level": level, "unique_nodes": n_unique, "storage_nodes": n_storage, "velocity": vel,
+            "scalar": scal, "cfl": cfl, "n_sub": n_sub, "dt": dt,
+            "l2": "flushed between steps (256 MB write)" if flush else "inputs larger than L2 (not flushed)",
+            "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU",
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": _traffic(args.workload), "algorithmic_bytes_per_launch": alg_bytes,
+                     "kernel": "k_advect", "avg_launch_ms": ms_per_step},
+        "gpu_launches": args.steps,
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(spec)
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3-l7-fp32", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    spec = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, spec)
+    else:
+        run_ours(args, spec)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,125 @@
+/* elm.h -- C ABI of libelm.so: the advection step of the modified method of
+ * characteristics (MMOC) on block-structured simplex meshes, for one GB300 GPU.
+ *
+ * Method: Kohl, Mohr, Eibl, Ruede, "A massively parallel Eulerian-Lagrangian
+ * method for advection-dominated transport in viscous fluids" (arXiv
+ * 2103.02388).  The library computes lines 3-4 of Algorithm 1 (departure
+ * points and advection, no diffusion): for every P2 node x_i of a mesh of
+ * macro triangles / tetrahedra refined uniformly L times (Sec. 2.1), the
+ * departure point X(x_i, t_{n+1}, t_n) of Eq. (departure point) by classic
+ * RK4 backwards in time through the P2 velocity, linearly interpolated in
+ * time (Eq. linear interpolation), then T^{n+1}_i = T^n_h(X_i) (Sec. 3,
+ * step (iii)).
+ *
+ * Conventions shared by every call:
+ *  - Node vectors live in STORAGE layout: macro after macro, each macro's
+ *    P2 nodes p = (p1 >= p2 [>= p3] >= 0), p1 <= 2^(L+1), packed row by row
+ *    (index p1(p1+1)(p1+2)/6 + p2(p2+1)/2 + p3 in 3D, p1(p1+1)/2 + p2 in 2D).
+ *    Nodes on macro interfaces appear once per macro that holds them; the
+ *    copy in the lowest-numbered macro is the owner.  elm_mesh_unique_map
+ *    gives storage -> unique ids; elm_to_storage / elm_to_unique convert.
+ *  - Scalars are [n] and velocities [n, dim] row-major, in the mesh's
+ *    precision (double for ELM_FP64, float for ELM_FP32).
+ *  - Device pointers are borrowed, caller-owned, and used in stream order on
+ *    the CUDA stream passed as `stream` (a cudaStream_t; NULL = legacy
+ *    default stream).  No call allocates device memory or synchronises after
+ *    elm_mesh_create, except elm_get_status, which synchronises `stream`.
+ *  - Errors: argument errors are returned synchronously and leave the
+ *    mesh unchanged; device-side conditions (walk limit, non-finite values)
+ *    set flags that elm_get_status reports.  No call traps or exits.
+ *    elm_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef ELM_H
+#define ELM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct elm_mesh_s* elm_mesh;
+
+typedef enum {
+  ELM_OK = 0,
+  ELM_ERR_ARG = 1,        /* invalid argument (null pointer, size, level, dtype) */
+  ELM_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+  ELM_ERR_TOPOLOGY = 3,   /* degenerate macro or a face shared by > 2 macros */
+  ELM_ERR_WALK_LIMIT = 4, /* a point needed more macro hops than the limit */
+  ELM_ERR_NONFINITE = 5,  /* a velocity or result value was NaN / Inf */
+  ELM_ERR_STATE = 6       /* call order violated (e.g. advect before set_velocity) */
+} elm_status;
+
+enum { ELM_FP64 = 0, ELM_FP32 = 1 };
+
+/* Flag OR-ed into `precision` of elm_mesh_create: build the host tables only
+ * (node coordinates, unique map; no device memory, no CUDA call).  Calls that
+ * need the device then return ELM_ERR_STATE.  Lets a host without a GPU
+ * prepare inputs and check a mesh. */
+enum { ELM_HOST_ONLY = 0x100 };
+
+/* Builds the refined mesh (Sec. 2.1: coarse mesh T_0 refined uniformly after
+ * Bey; Sec. 3 "Grid data structure": one DoF owner per interface node).
+ *  dim            2 (triangles) or 3 (tetrahedra).
+ *  vertex_xyz     host, [n_vertices, dim] doubles.
+ *  macro_vertices host, [n_macros, dim+1] vertex ids in [0, n_vertices).  The
+ *                 order within a macro is irrelevant: vertices are sorted by
+ *                 id, which makes the refinement conforming across faces.
+ *  level          0..9 in 2D, 0..7 in 3D.
+ *  precision      ELM_FP64 or ELM_FP32, optionally | ELM_HOST_ONLY.
+ * Copies everything it needs; allocates the mesh's device tables on the
+ * current device.  Returns ELM_ERR_TOPOLOGY for a degenerate macro or a
+ * non-manifold face.  *out is set only on success. */
+elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz,
+                           int64_t n_macros, const int64_t* macro_vertices,
+                           int level, int precision, elm_mesh* out);
+
+/* Frees the mesh and its device tables (after pending work on its streams). */
+elm_status elm_mesh_destroy(elm_mesh mesh);
+
+/* Storage length n of every node vector of this mesh (0 for a null mesh). */
+int64_t elm_mesh_num_nodes(elm_mesh mesh);
+
+/* Number of distinct (unique) P2 nodes. */
+int64_t elm_mesh_num_unique(elm_mesh mesh);
+
+/* Node coordinates in storage order into host_out [n, dim] doubles. */
+elm_status elm_mesh_node_coords(elm_mesh mesh, double* host_out);
+
+/* Storage slot -> unique node id into host_out [n] (unique ids follow the
+ * storage order of the owner slots). */
+elm_status elm_mesh_unique_map(elm_mesh mesh, int64_t* host_out);
+
+/* Device copy between layouts, ncomp values per node, mesh precision:
+ * storage_dev[s] = unique_dev[unique_map[s]]  /  unique_dev[u] = storage_dev[owner(u)]. */
+elm_status elm_to_storage(elm_mesh mesh, const void* unique_dev, void* storage_dev, int ncomp, void* stream);
+elm_status elm_to_unique(elm_mesh mesh, const void* storage_dev, void* unique_dev, int ncomp, void* stream);
+
+/* Registers the P2 velocity at t_n (u_old) and t_{n+1} (u_new), storage
+ * layout [n, dim], mesh precision (Sec. 3 step (ii), Eq. linear
+ * interpolation).  u_new == u_old means a steady velocity (no time
+ * interpolation).  Both buffers are borrowed until the next call or
+ * elm_mesh_destroy; they are read, never copied or written. */
+elm_status elm_set_velocity(elm_mesh mesh, const void* u_old_dev, const void* u_new_dev, void* stream);
+
+/* One advection step (Algorithm 1, lines 3-4; Sec. 3 steps (i)-(iii)):
+ * T_new[i] = T_old_h(X_i), X_i traced back over dt from node i with n_sub
+ * equal RK4 substeps.  T_old and T_new are [n] in storage layout and must
+ * not overlap.  Stage and departure points outside the domain are clamped
+ * to the mesh's bounding box.  1 <= n_sub <= 64; dt finite and >= 0. */
+elm_status elm_advect(elm_mesh mesh, const void* T_old_dev, void* T_new_dev, double dt, int n_sub,
+                      void* stream);
+
+/* Synchronises `stream`, returns the first device-side condition raised by
+ * work on this mesh since the previous call (ELM_ERR_WALK_LIMIT or
+ * ELM_ERR_NONFINITE), else ELM_OK, and clears the flags. */
+elm_status elm_get_status(elm_mesh mesh, void* stream);
+
+/* Thread-local description of the last error returned on this thread. */
+const char* elm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELM_H */

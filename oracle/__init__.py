@@ -56,6 +56,7 @@ def _load():
         lib.orc_eval.argtypes = [P, P, I32, I64, P, P, I32]
         lib.orc_departure.argtypes = [P, P, P, D, I32, I64, I64, P, I32]
         lib.orc_advect.argtypes = [P, P, P, P, P, D, I32, I64, I64, I32]
+        lib.orc_advect_nodes.argtypes = [P, P, P, P, D, I32, I64, P, P, I32]
         lib.orc_advect_transpose.argtypes = [P, P, P, P, P, D, I32]
         lib.orc_mass_products.argtypes = [P, I32, P, P, P]
         lib.orc_micro_simplices.restype = I64
@@ -164,6 +165,17 @@ class OracleMesh:
         out = np.empty(end - begin)
         _load().orc_advect(self._h, _ptr(u_old), _ptr(u_new), _ptr(T_old), _ptr(out),
                            float(dt), int(n_sub), begin, end, threads or default_threads())
+        return out
+
+    def advect_nodes(self, T_old, u_old, dt, idx, n_sub=1, u_new=None, threads=None):
+        """One advection step evaluated only at the node ids ``idx``."""
+        T_old = _f64(T_old)
+        u_old = _f64(u_old)
+        u_new = u_old if u_new is None else _f64(u_new)
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        out = np.empty(idx.shape[0])
+        _load().orc_advect_nodes(self._h, _ptr(u_old), _ptr(u_new), _ptr(T_old), float(dt), int(n_sub),
+                                 idx.shape[0], _ptr(idx), _ptr(out), threads or default_threads())
         return out
 
     def advect_transpose(self, g_new, u_old, dt, n_sub=1, u_new=None):

@@ -608,6 +608,19 @@ void orc_advect(void* h, const double* u_old, const double* u_new, const double*
   });
 }
 
+// One advection step for the listed nodes only: out[k] = T^n_h(X_{idx[k]}).
+void orc_advect_nodes(void* h, const double* u_old, const double* u_new, const double* T_old, double dt,
+                      int n_sub, int64_t n_idx, const int64_t* idx, double* out, int nthreads) {
+  Mesh* me = static_cast<Mesh*>(h);
+  const int d = me->d;
+  Velocity V{u_old, u_new, dt};
+  parallel_for(0, n_idx, nthreads, [&](int64_t k) {
+    double X[3];
+    departure_point(*me, V, n_sub, &me->X[idx[k] * d], X);
+    eval_field(*me, T_old, 1, X, out + k);
+  });
+}
+
 // Transpose of the interpolation: g_old[j] += sum_i phi_j(X_i) g_new[i].
 void orc_advect_transpose(void* h, const double* u_old, const double* u_new, const double* g_new,
                           double* g_old, double dt, int n_sub) {

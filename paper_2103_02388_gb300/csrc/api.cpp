@@ -1,0 +1,232 @@
+// api.cpp -- the C ABI of libelm.so (declared in include/elm.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "elm_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+elm_status fail(elm_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+elm_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(ELM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Makes the mesh's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+size_t elem_size(const elm_mesh_s* me) { return me->precision == ELM_FP64 ? 8 : 4; }
+
+void free_tables(elm_mesh_s* me) {
+  cudaFree(me->d_geo);
+  cudaFree(me->d_geo32);
+  cudaFree(me->d_unique_map);
+  cudaFree(me->d_owner);
+  cudaFree(me->d_status);
+  me->d_geo = nullptr;
+  me->d_geo32 = nullptr;
+  me->d_unique_map = me->d_owner = nullptr;
+  me->d_status = nullptr;
+}
+
+bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + bytes && pb < pa + bytes;
+}
+
+}  // namespace
+
+extern "C" {
+
+elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz, int64_t n_macros,
+                           const int64_t* macro_vertices, int level, int precision, elm_mesh* out) {
+  if (!out) return fail(ELM_ERR_ARG, "elm_mesh_create: out is null");
+  if (dim != 2 && dim != 3) return fail(ELM_ERR_ARG, "elm_mesh_create: dim must be 2 or 3");
+  if (n_vertices <= 0 || !vertex_xyz) return fail(ELM_ERR_ARG, "elm_mesh_create: no vertices");
+  if (n_macros <= 0 || !macro_vertices) return fail(ELM_ERR_ARG, "elm_mesh_create: no macros");
+  if (n_macros > (int64_t(1) << 30)) return fail(ELM_ERR_ARG, "elm_mesh_create: too many macros");
+  const int max_level = dim == 2 ? 9 : 7;
+  if (level < 0 || level > max_level)
+    return fail(ELM_ERR_ARG, "elm_mesh_create: level out of range (0.." + std::to_string(max_level) + ")");
+  const bool host_only = (precision & ELM_HOST_ONLY) != 0;
+  precision &= ~ELM_HOST_ONLY;
+  if (precision != ELM_FP64 && precision != ELM_FP32)
+    return fail(ELM_ERR_ARG, "elm_mesh_create: precision must be ELM_FP64 or ELM_FP32");
+  elm_mesh_s* me = new (std::nothrow) elm_mesh_s();
+  if (!me) return fail(ELM_ERR_ARG, "elm_mesh_create: out of host memory");
+  me->host_only = host_only;
+  if (!host_only) {
+    cudaError_t e = cudaGetDevice(&me->device);
+    if (e != cudaSuccess) {
+      delete me;
+      return cuda_fail(e, "elm_mesh_create");
+    }
+  }
+  std::string err;
+  elm_status s;
+  try {
+    s = elm::build_mesh(dim, n_vertices, vertex_xyz, n_macros, macro_vertices, level, precision, me, &err);
+  } catch (const std::bad_alloc&) {
+    s = ELM_ERR_ARG;
+    err = "out of host memory";
+  }
+  if (s != ELM_OK) {
+    if (!host_only) free_tables(me);
+    delete me;
+    return fail(s, "elm_mesh_create: " + err);
+  }
+  *out = me;
+  return ELM_OK;
+}
+
+elm_status elm_mesh_destroy(elm_mesh me) {
+  if (!me) return ELM_OK;
+  if (!me->host_only) {
+    DeviceGuard g(me->device);
+    free_tables(me);
+  }
+  delete me;
+  return ELM_OK;
+}
+
+int64_t elm_mesh_num_nodes(elm_mesh me) { return me ? me->n_storage : 0; }
+
+int64_t elm_mesh_num_unique(elm_mesh me) { return me ? me->n_unique : 0; }
+
+elm_status elm_mesh_node_coords(elm_mesh me, double* host_out) {
+  if (!me || !host_out) return fail(ELM_ERR_ARG, "elm_mesh_node_coords: null argument");
+  const int d = me->dim;
+  const double invM = 1.0 / me->M;
+  for (int64_t m = 0; m < me->n_macros; ++m) {
+    const elm::MacroGeo& g = me->geo[m];
+    int64_t slot = m * me->npm;
+    int p[3] = {0, 0, 0};
+    auto emit = [&]() {
+      for (int r = 0; r < d; ++r) {
+        double x = g.v0[r];
+        for (int c = 0; c < d; ++c) x += g.J[r * 3 + c] * (p[c] * invM);
+        host_out[slot * d + r] = x;
+      }
+      ++slot;
+    };
+    if (d == 2) {
+      for (p[0] = 0; p[0] <= me->M; ++p[0])
+        for (p[1] = 0; p[1] <= p[0]; ++p[1]) emit();
+    } else {
+      for (p[0] = 0; p[0] <= me->M; ++p[0])
+        for (p[1] = 0; p[1] <= p[0]; ++p[1])
+          for (p[2] = 0; p[2] <= p[1]; ++p[2]) emit();
+    }
+  }
+  return ELM_OK;
+}
+
+elm_status elm_mesh_unique_map(elm_mesh me, int64_t* host_out) {
+  if (!me || !host_out) return fail(ELM_ERR_ARG, "elm_mesh_unique_map: null argument");
+  std::memcpy(host_out, me->unique_map.data(), sizeof(int64_t) * me->n_storage);
+  return ELM_OK;
+}
+
+elm_status elm_to_storage(elm_mesh me, const void* unique_dev, void* storage_dev, int ncomp, void* stream) {
+  if (!me || !unique_dev || !storage_dev || ncomp < 1 || ncomp > 16)
+    return fail(ELM_ERR_ARG, "elm_to_storage: invalid argument");
+  if (me->host_only) return fail(ELM_ERR_STATE, "elm_to_storage: host-only mesh");
+  DeviceGuard g(me->device);
+  cudaError_t e = elm::launch_gather(me->precision, unique_dev, storage_dev, me->d_unique_map, me->n_storage,
+                                     ncomp, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? ELM_OK : cuda_fail(e, "elm_to_storage");
+}
+
+elm_status elm_to_unique(elm_mesh me, const void* storage_dev, void* unique_dev, int ncomp, void* stream) {
+  if (!me || !unique_dev || !storage_dev || ncomp < 1 || ncomp > 16)
+    return fail(ELM_ERR_ARG, "elm_to_unique: invalid argument");
+  if (me->host_only) return fail(ELM_ERR_STATE, "elm_to_unique: host-only mesh");
+  DeviceGuard g(me->device);
+  cudaError_t e = elm::launch_gather(me->precision, storage_dev, unique_dev, me->d_owner, me->n_unique, ncomp,
+                                     static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? ELM_OK : cuda_fail(e, "elm_to_unique");
+}
+
+elm_status elm_set_velocity(elm_mesh me, const void* u_old_dev, const void* u_new_dev, void* stream) {
+  (void)stream;
+  if (!me) return fail(ELM_ERR_ARG, "elm_set_velocity: null mesh");
+  if (!u_old_dev || !u_new_dev) return fail(ELM_ERR_ARG, "elm_set_velocity: null velocity");
+  if (me->host_only) return fail(ELM_ERR_STATE, "elm_set_velocity: host-only mesh");
+  me->u_old = u_old_dev;
+  me->u_new = u_new_dev;
+  return ELM_OK;
+}
+
+elm_status elm_advect(elm_mesh me, const void* T_old_dev, void* T_new_dev, double dt, int n_sub, void* stream) {
+  if (!me) return fail(ELM_ERR_ARG, "elm_advect: null mesh");
+  if (!T_old_dev || !T_new_dev) return fail(ELM_ERR_ARG, "elm_advect: null temperature buffer");
+  if (!std::isfinite(dt) || dt < 0.0) return fail(ELM_ERR_ARG, "elm_advect: dt must be finite and >= 0");
+  if (n_sub < 1 || n_sub > 64) return fail(ELM_ERR_ARG, "elm_advect: n_sub must be in 1..64");
+  if (me->host_only) return fail(ELM_ERR_STATE, "elm_advect: host-only mesh");
+  if (!me->u_old || !me->u_new) return fail(ELM_ERR_STATE, "elm_advect: elm_set_velocity has not been called");
+  if (ranges_overlap(T_old_dev, T_new_dev, elem_size(me) * size_t(me->n_storage)))
+    return fail(ELM_ERR_ARG, "elm_advect: T_old and T_new overlap");
+  DeviceGuard g(me->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  elm::AdvectArgs a{};
+  a.geo = me->d_geo;
+  a.geo32 = me->d_geo32;
+  a.n_macros = int32_t(me->n_macros);
+  a.N = me->N;
+  a.npm = me->npm;
+  a.n_storage = me->n_storage;
+  for (int r = 0; r < 3; ++r) {
+    a.lo[r] = me->lo[r];
+    a.hi[r] = me->hi[r];
+  }
+  a.u_old = me->u_old;
+  a.u_new = me->u_new;
+  a.steady = me->u_old == me->u_new;
+  a.T_old = T_old_dev;
+  a.T_new = T_new_dev;
+  a.dt = dt;
+  a.n_sub = n_sub;
+  a.status = me->d_status;
+  a.unique_map = me->d_unique_map;
+  a.owner = me->d_owner;
+  cudaError_t e = elm::launch_advect(me->dim, me->precision, a, s);
+  if (e != cudaSuccess) return cuda_fail(e, "elm_advect");
+  return ELM_OK;
+}
+
+elm_status elm_get_status(elm_mesh me, void* stream) {
+  if (!me) return fail(ELM_ERR_ARG, "elm_get_status: null mesh");
+  if (me->host_only) return fail(ELM_ERR_STATE, "elm_get_status: host-only mesh");
+  DeviceGuard g(me->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned flags = 0;
+  cudaError_t e = cudaMemcpyAsync(&flags, me->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(me->d_status, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return cuda_fail(e, "elm_get_status");
+  if (flags & elm::kFlagWalkLimit)
+    return fail(ELM_ERR_WALK_LIMIT, "a point needed more than the macro-walk limit of hops");
+  if (flags & elm::kFlagNonFinite) return fail(ELM_ERR_NONFINITE, "a velocity or result value was not finite");
+  return ELM_OK;
+}
+
+const char* elm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// elm_internal.h -- internal types shared by the host mesh builder, the C ABI
+// and the CUDA kernels of libelm.so.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "elm.h"
+
+namespace elm {
+
+constexpr int kMaxHops = 32;           // macro walk limit per location
+constexpr unsigned kFlagWalkLimit = 1u;
+constexpr unsigned kFlagNonFinite = 2u;
+
+// Affine data of one macro simplex (Sec. 2.1).  The vertices P_0..P_d are
+// taken in ascending global id; the reference Kuhn simplex
+// {1 >= s_1 >= .. >= s_d >= 0} is mapped by x = P_0 + J s with
+// J = [P_1 - P_0 | P_2 - P_1 | P_3 - P_2], and the level-L lattice coordinate
+// is q = N s = NJinv (x - P_0), N = 2^L.
+struct MacroGeo {
+  double v0[3];
+  double J[9];       // row-major d x d (leading d x d block used in 2D)
+  double NJinv[9];   // row-major, N * J^{-1}
+  int32_t nb[4];     // macro across the face opposite local vertex k; -1 = boundary
+};
+
+// FP32 copy of the macro data, used by the FP32 kernel's common path.
+struct MacroGeo32 {
+  float NJinv[9];
+  float J[9];
+  float v0[3];
+  int32_t nb[4];
+};
+
+// Everything a kernel launch needs, passed by value.
+struct AdvectArgs {
+  const MacroGeo* geo;     // [n_macros]
+  const MacroGeo32* geo32; // [n_macros]
+  int32_t n_macros;
+  int32_t N;               // 2^L
+  int64_t npm;             // storage nodes per macro
+  int64_t n_storage;
+  double lo[3], hi[3];     // bounding box (domain clamp)
+  const void* u_old;
+  const void* u_new;
+  int steady;              // u_old == u_new
+  const void* T_old;
+  void* T_new;
+  double dt;
+  int n_sub;
+  unsigned* status;
+  const int64_t* unique_map;  // storage slot -> unique id
+  const int64_t* owner;       // unique id -> owner storage slot
+};
+
+}  // namespace elm
+
+struct elm_mesh_s {
+  int dim = 0, level = 0, N = 0, M = 0, precision = ELM_FP64;
+  bool host_only = false;
+  int64_t n_macros = 0, npm = 0, n_storage = 0, n_unique = 0, n_ghost = 0;
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  std::vector<elm::MacroGeo> geo;
+  std::vector<int64_t> unique_map;   // storage slot -> unique id
+  std::vector<int64_t> owner;        // unique id -> owner storage slot
+  int device = 0;
+  // device tables
+  elm::MacroGeo* d_geo = nullptr;
+  elm::MacroGeo32* d_geo32 = nullptr;
+  int64_t* d_unique_map = nullptr;
+  int64_t* d_owner = nullptr;
+  unsigned* d_status = nullptr;
+  // borrowed velocity
+  const void* u_old = nullptr;
+  const void* u_new = nullptr;
+};
+
+namespace elm {
+
+// Host mesh construction (mesh.cpp).
+elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const int64_t* mv,
+                      int level, int precision, elm_mesh_s* me, std::string* err);
+
+// Packed P2 node index of lattice point p inside a macro (storage layout).
+inline int64_t packed_index_host(int dim, const int* p) {
+  if (dim == 3)
+    return int64_t(p[0]) * (p[0] + 1) * (p[0] + 2) / 6 + int64_t(p[1]) * (p[1] + 1) / 2 + p[2];
+  return int64_t(p[0]) * (p[0] + 1) / 2 + p[1];
+}
+
+inline int64_t nodes_per_macro(int dim, int M) {
+  return dim == 3 ? int64_t(M + 1) * (M + 2) * (M + 3) / 6 : int64_t(M + 1) * (M + 2) / 2;
+}
+
+// Kernel launchers (advect.cu).  Return a CUDA error code.
+cudaError_t launch_advect(int dim, int precision, const AdvectArgs& a, cudaStream_t s);
+cudaError_t launch_gather(int precision, const void* in, void* out, const int64_t* idx, int64_t n,
+                          int ncomp, cudaStream_t s);
+
+}  // namespace elm

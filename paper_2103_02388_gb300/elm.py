@@ -1,0 +1,146 @@
+"""Python face of libelm.so: torch tensors in, C-ABI calls out.
+
+Every step of the advection path runs in the library's CUDA kernels; this
+module only marshals pointers, sizes and the current CUDA stream.  There is no
+CPU fallback: if libelm.so is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import ELM_FP32, ELM_FP64, ELM_HOST_ONLY, check
+
+_DTYPES = {"fp64": (ELM_FP64, torch.float64, np.float64), "fp32": (ELM_FP32, torch.float32, np.float32)}
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Mesh:
+    """A coarse macro mesh refined uniformly to ``level`` (Sec. 2.1).
+
+    ``vertices``: [n_vertices, dim] coordinates; ``macros``: [n_macros, dim+1]
+    vertex ids; ``precision``: "fp64" or "fp32".  ``host_only=True`` builds only
+    the host tables (coordinates and the unique map), without a GPU.
+    """
+
+    def __init__(self, vertices, macros, level: int, precision: str = "fp64", host_only: bool = False):
+        lib = _lib.load()
+        self.vertices = np.ascontiguousarray(vertices, dtype=np.float64)
+        self.macros = np.ascontiguousarray(macros, dtype=np.int64)
+        self.dim = int(self.vertices.shape[1])
+        self.level = int(level)
+        self.precision = precision
+        code, self.dtype, self.np_dtype = _DTYPES[precision]
+        self.host_only = host_only
+        if not host_only:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        check(lib.elm_mesh_create(self.dim, self.vertices.shape[0],
+                                  self.vertices.ctypes.data_as(ctypes.c_void_p),
+                                  self.macros.shape[0], self.macros.ctypes.data_as(ctypes.c_void_p),
+                                  self.level, code | (ELM_HOST_ONLY if host_only else 0), ctypes.byref(h)))
+        self._h = h
+        self.n_nodes = int(lib.elm_mesh_num_nodes(h))
+        self.n_unique = int(lib.elm_mesh_num_unique(h))
+        self._u = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.load().elm_mesh_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    # -- host tables ------------------------------------------------------
+    def node_coords(self) -> np.ndarray:
+        """Coordinates of the storage slots, [n_nodes, dim]."""
+        out = np.empty((self.n_nodes, self.dim))
+        check(_lib.load().elm_mesh_node_coords(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def unique_map(self) -> np.ndarray:
+        """Storage slot -> unique node id, [n_nodes] int64."""
+        out = np.empty(self.n_nodes, np.int64)
+        check(_lib.load().elm_mesh_unique_map(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def unique_coords(self) -> np.ndarray:
+        """Coordinates of the unique nodes, [n_unique, dim] (owner slots)."""
+        umap = self.unique_map()
+        coords = self.node_coords()
+        out = np.empty((self.n_unique, self.dim))
+        first = np.full(self.n_unique, -1, np.int64)
+        slots = np.arange(self.n_nodes)
+        first[umap[::-1]] = slots[::-1]
+        out[:] = coords[first]
+        return out
+
+    # -- layout conversion (device) ---------------------------------------
+    def _ncomp(self, t: torch.Tensor, n: int) -> int:
+        if t.shape[0] != n:
+            raise ValueError(f"expected {n} rows, got {t.shape[0]}")
+        return 1 if t.dim() == 1 else int(np.prod(t.shape[1:]))
+
+    def _check_tensor(self, t: torch.Tensor, name: str):
+        if not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.dtype} CUDA tensor")
+
+    def to_storage(self, t_unique: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        self._check_tensor(t_unique, "t_unique")
+        nc = self._ncomp(t_unique, self.n_unique)
+        if out is None:
+            out = torch.empty((self.n_nodes,) + tuple(t_unique.shape[1:]), dtype=self.dtype, device=t_unique.device)
+        check(_lib.load().elm_to_storage(self._h, ctypes.c_void_p(t_unique.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), nc, _stream_ptr()))
+        return out
+
+    def to_unique(self, t_storage: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        self._check_tensor(t_storage, "t_storage")
+        nc = self._ncomp(t_storage, self.n_nodes)
+        if out is None:
+            out = torch.empty((self.n_unique,) + tuple(t_storage.shape[1:]), dtype=self.dtype,
+                              device=t_storage.device)
+        check(_lib.load().elm_to_unique(self._h, ctypes.c_void_p(t_storage.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), nc, _stream_ptr()))
+        return out
+
+    # -- the advection step -------------------------------------------------
+    def set_velocity(self, u_old: torch.Tensor, u_new: torch.Tensor | None = None) -> None:
+        """Borrow the P2 velocity at t_n and t_{n+1} (storage layout, [n, dim])."""
+        u_new = u_old if u_new is None else u_new
+        for name, u in (("u_old", u_old), ("u_new", u_new)):
+            self._check_tensor(u, name)
+            if tuple(u.shape) != (self.n_nodes, self.dim):
+                raise ValueError(f"{name} must have shape ({self.n_nodes}, {self.dim})")
+        check(_lib.load().elm_set_velocity(self._h, ctypes.c_void_p(u_old.data_ptr()),
+                                           ctypes.c_void_p(u_new.data_ptr()), _stream_ptr()))
+        self._u = (u_old, u_new)  # keep the borrowed buffers alive
+
+    def advect(self, T_old: torch.Tensor, dt: float, n_sub: int = 1, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+        """One MMOC advection step: T_new[i] = T_old_h(X_i) (storage layout)."""
+        self._check_tensor(T_old, "T_old")
+        if T_old.shape != (self.n_nodes,):
+            raise ValueError(f"T_old must have shape ({self.n_nodes},)")
+        if out is None:
+            out = torch.empty_like(T_old)
+        else:
+            self._check_tensor(out, "out")
+        check(_lib.load().elm_advect(self._h, ctypes.c_void_p(T_old.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     float(dt), int(n_sub), _stream_ptr(stream)))
+        return out
+
+    def status(self, stream=None) -> int:
+        """Synchronises the stream and raises on a device-side condition."""
+        check(_lib.load().elm_get_status(self._h, _stream_ptr(stream)))
+        return _lib.ELM_OK

@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA advection step (through the C ABI) against the CPU
+oracle, element by element on the same seeded inputs.
+
+FP64: max |T_gpu - T_oracle| <= 1e-12 * max |T_old| per step.
+FP32: max |T_gpu - T_oracle| <= 1e-5 * max |T_old| per step, where the
+oracle (FP64) receives the FP32-rounded inputs the GPU computes on.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from _helpers import match_nodes, mesh_for, scalar_for, velocity_for
+from paper_2103_02388_gb300 import _lib, elm, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+class Pair:
+    """The same mesh on both sides, with the node permutation between them."""
+
+    def __init__(self, mesh, level, precision="fp64"):
+        v, m = mesh_for(mesh) if isinstance(mesh, str) else mesh
+        self.om = oracle.OracleMesh(v, m, level)
+        self.gm = elm.Mesh(v, m, level, precision)
+        self.perm = match_nodes(self.om.coords, self.gm.unique_coords())
+        self.precision = precision
+        self.level = level
+        self.x = self.om.coords
+
+    def rounded(self, a):
+        return a.astype(np.float32).astype(np.float64) if self.precision == "fp32" else a
+
+    def to_gpu(self, a):
+        g = np.empty_like(a)
+        g[self.perm] = a
+        t = torch.tensor(g, dtype=self.gm.dtype, device="cuda")
+        return self.gm.to_storage(t)
+
+    def from_gpu(self, t):
+        return self.gm.to_unique(t).double().cpu().numpy()[self.perm]
+
+    def step(self, T, u, dt, n_sub=1, u_new=None, check_copies=True):
+        """One step on both sides; returns (gpu, oracle) in oracle node order."""
+        T, u = self.rounded(T), self.rounded(u)
+        u_new = None if u_new is None else self.rounded(u_new)
+        us = self.to_gpu(u)
+        un = us if u_new is None else self.to_gpu(u_new)
+        self.gm.set_velocity(us, un)
+        out = self.gm.advect(self.to_gpu(T), dt, n_sub)
+        self.gm.status()
+        if check_copies:
+            umap = torch.tensor(self.gm.unique_map(), device="cuda")
+            uniq = self.gm.to_unique(out)
+            assert torch.equal(uniq[umap], out), "storage copies of a node disagree"
+        ref = self.om.advect(T, u, dt, n_sub, u_new=u_new)
+        return self.from_gpu(out), ref
+
+
+def _err(got, ref, T):
+    return np.abs(got - ref).max() / max(np.abs(T).max(), 1e-300)
+
+
+@pytest.mark.parametrize("mesh,level,vel,scal,cfl,n_sub", [
+    ("square", 5, "rotation", "gauss", None, 1),      # circular advection, dt = 1/200
+    ("square", 3, "rotation", "quadratic", 3.0, 3),
+    ("square_block", 3, "fourier", "gauss", 6.0, 2),
+    ("cube", 3, "cellular", "slotted", 1.0, 1),
+    ("cube", 3, "cellular", "slotted", 4.0, 2),
+    ("cube", 3, "cellular", "slotted", 8.0, 4),
+    ("cube", 4, "fourier", "gauss", 4.0, 1),
+    ("cube", 2, "rotation", "gauss", 5.0, 2),           # leaves the cube: clamping
+    ("cube_block", 2, "fourier", "gauss", 8.0, 2),      # 48 perturbed macros: walk
+    ("cube_block", 1, "rotation", "slotted", 3.0, 1),
+])
+def test_fp64_parity(mesh, level, vel, scal, cfl, n_sub):
+    P = Pair(mesh, level, "fp64")
+    u = velocity_for(vel, P.x)
+    T = scalar_for(scal, P.x)
+    dt = 1 / 200 if cfl is None else inputs.dt_for_cfl(cfl, level, u)
+    got, ref = P.step(T, u, dt, n_sub)
+    assert _err(got, ref, T) <= TOL["fp64"]
+
+
+@pytest.mark.parametrize("mesh,level,vel,scal,cfl,n_sub", [
+    ("square", 5, "rotation", "gauss", None, 1),
+    ("square", 6, "fourier", "gauss", 4.0, 2),
+    ("cube", 4, "fourier", "gauss", 4.0, 1),
+    ("cube", 4, "cellular", "slotted", 8.0, 2),
+    ("cube_block", 2, "fourier", "gauss", 8.0, 1),
+])
+def test_fp32_parity(mesh, level, vel, scal, cfl, n_sub):
+    P = Pair(mesh, level, "fp32")
+    u = velocity_for(vel, P.x)
+    T = scalar_for(scal, P.x)
+    dt = 1 / 200 if cfl is None else inputs.dt_for_cfl(cfl, level, u)
+    got, ref = P.step(T, u, dt, n_sub)
+    assert _err(got, ref, T) <= TOL["fp32"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_time_dependent_velocity(precision):
+    P = Pair("cube", 3, precision)
+    u0 = inputs.cellular_flow(P.x)
+    u1 = inputs.random_fourier(P.x, seed=4)
+    T = scalar_for("gauss", P.x)
+    dt = inputs.dt_for_cfl(3.0, 3, u1)
+    got, ref = P.step(T, u0, dt, 3, u_new=u1)
+    assert _err(got, ref, T) <= TOL[precision]
+
+
+@pytest.mark.parametrize("mesh,level", [("square", 0), ("square", 1), ("cube", 0), ("cube", 1)])
+def test_smallest_levels(mesh, level):
+    P = Pair(mesh, level, "fp64")
+    u = velocity_for("fourier", P.x)
+    T = scalar_for("quadratic", P.x)
+    got, ref = P.step(T, u, 0.3, 2)
+    assert _err(got, ref, T) <= TOL["fp64"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_zero_dt_and_zero_velocity_are_identity(precision):
+    P = Pair("cube", 2, precision)
+    T = P.rounded(scalar_for("quadratic", P.x))
+    u = velocity_for("fourier", P.x)
+    got, _ = P.step(T, u, 0.0, 1)
+    tol = 8 * np.finfo(np.float64 if precision == "fp64" else np.float32).eps
+    assert np.abs(got - T).max() <= tol * np.abs(T).max()
+    got, _ = P.step(T, np.zeros_like(P.x), 0.5, 2)
+    assert np.abs(got - T).max() <= tol * np.abs(T).max()
+
+
+def test_accumulated_revolution_fp64():
+    """Config of the circular-advection benchmark: 2D level 5, 200 steps of
+    dt = 1/200 (one revolution), both sides run independently."""
+    P = Pair("square", 5, "fp64")
+    u = inputs.rotation_2d(P.x)
+    T0 = inputs.gaussian(P.x, (0.25, 0.5), 0.05)
+    us = P.to_gpu(u)
+    P.gm.set_velocity(us)
+    Tg = P.to_gpu(T0)
+    To = T0.copy()
+    worst = 0.0
+    for _ in range(200):
+        Tg = P.gm.advect(Tg, 1 / 200)
+        To = P.om.advect(To, u, 1 / 200)
+        worst = max(worst, np.abs(P.from_gpu(Tg) - To).max())
+    P.gm.status()
+    assert worst <= 1e-11
+    # and the scheme itself: H0 error after one revolution is small
+    assert P.om.metrics(To, T0, T0)["h0"] < 0.03
+
+
+@pytest.mark.parametrize("precision,level,n_sub,cfl", [("fp64", 6, 2, 4.0), ("fp32", 7, 1, 4.0)])
+def test_full_size_sampled(precision, level, n_sub, cfl):
+    """The benchmark sizes (3D level 6 FP64, level 7 FP32), checked on 3000
+    sampled nodes the oracle evaluates one by one."""
+    P = Pair("cube", level, precision)
+    if precision == "fp64":
+        u = inputs.cellular_flow(P.x)
+        T = inputs.slotted_sphere(P.x)
+    else:
+        u = inputs.random_fourier(P.x, seed=3)
+        T = inputs.gaussian(P.x, (0.35, 0.5, 0.5), 0.1)
+    u, T = P.rounded(u), P.rounded(T)
+    dt = inputs.dt_for_cfl(cfl, level, u)
+    us = P.to_gpu(u)
+    P.gm.set_velocity(us)
+    out = P.gm.advect(P.to_gpu(T), dt, n_sub)
+    P.gm.status()
+    got = P.from_gpu(out)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(P.om.n_nodes, 3000, replace=False)
+    ref = P.om.advect_nodes(T, u, dt, idx, n_sub)
+    assert np.abs(got[idx] - ref).max() <= TOL[precision] * np.abs(T).max()
+
+
+# ---------------------------------------------------------------------------
+# Error behaviour (no GPU fault is provoked: conditions are flags and codes).
+# ---------------------------------------------------------------------------
+
+
+def test_nonfinite_velocity_is_reported():
+    v, m = inputs.unit_cube()
+    gm = elm.Mesh(v, m, 2, "fp64")
+    u = torch.zeros((gm.n_nodes, 3), dtype=torch.float64, device="cuda")
+    u[17, 1] = float("nan")
+    gm.set_velocity(u)
+    T = torch.ones(gm.n_nodes, dtype=torch.float64, device="cuda")
+    gm.advect(T, 0.1, 1)
+    with pytest.raises(_lib.ElmError) as e:
+        gm.status()
+    assert e.value.status == _lib.ELM_ERR_NONFINITE
+    gm.status()  # flags were cleared
+
+
+def test_walk_limit_is_reported_not_hung():
+    """A step that crosses more macros than the walk limit allows returns a
+    flag instead of looping."""
+    v, m = inputs.square_block(48)
+    gm = elm.Mesh(v, m, 0, "fp64")
+    u = torch.zeros((gm.n_nodes, 2), dtype=torch.float64, device="cuda")
+    u[:, 0] = 1.0
+    u[:, 1] = 0.3
+    gm.set_velocity(u)
+    T = torch.ones(gm.n_nodes, dtype=torch.float64, device="cuda")
+    gm.advect(T, 0.9, 1)
+    with pytest.raises(_lib.ElmError) as e:
+        gm.status()
+    assert e.value.status == _lib.ELM_ERR_WALK_LIMIT
+
+
+def test_argument_errors():
+    v, m = inputs.unit_square()
+    gm = elm.Mesh(v, m, 2, "fp64")
+    T = torch.ones(gm.n_nodes, dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.ElmError) as e:
+        gm.advect(T, 0.1)
+    assert e.value.status == _lib.ELM_ERR_STATE          # no velocity yet
+    gm.set_velocity(torch.zeros((gm.n_nodes, 2), dtype=torch.float64, device="cuda"))
+    with pytest.raises(_lib.ElmError) as e:
+        gm.advect(T, 0.1, out=T)
+    assert e.value.status == _lib.ELM_ERR_ARG            # aliasing
+    with pytest.raises(_lib.ElmError):
+        gm.advect(T, 0.1, n_sub=0)
+    with pytest.raises(_lib.ElmError):
+        gm.advect(T, float("nan"))
+    with pytest.raises(_lib.ElmError):
+        gm.advect(T, -1.0)
