@@ -14,10 +14,13 @@
 //
 // Point representation.  A point is kept as an offset d from its start node
 // x_i, and its level-L lattice coordinate in the current macro m as
-// q = b + r0 + NJinv_m d with an integer part b and a small fraction r0 of
-// the start node.  The integer part carries the node's absolute position
-// exactly, so FP32 keeps full precision in the fractional coordinates that
-// decide the micro element, independent of the macro's size.
+// q = b + r0 + NJinv_m d with an integer-valued part b and a small fraction
+// r0 of the start node.  b carries the node's absolute position exactly, so
+// FP32 keeps full precision in the fractional coordinates that decide the
+// micro element, independent of the macro's size.  When the walk enters
+// another macro, (b, r0) of the start node are recomputed in that macro's
+// frame: in FP64 for the FP64 kernel, in double-float arithmetic on the FP32
+// pipe for the FP32 kernel.
 //
 // Field evaluation (Sec. 3 "Field evaluation"):
 //   macro   -- barycentrics l = (N - q1, q1 - q2, q2 - q3, q3) in lattice
@@ -27,8 +30,17 @@
 //              the cell is given by the descending order of f (O(1));
 //   P2 sum  -- micro barycentrics L = (1 - f_s0, f_s0 - f_s1, f_s1 - f_s2,
 //              f_s2); vertex basis L(2L - 1), edge basis 4 L_a L_b.
-// In FP32, a macro decision whose barycentric lies within kBand32 of 0 is
-// re-taken in FP64 from the exact start node.
+// In FP32, a hop decision across an interior macro face whose barycentric
+// lies within kBand32 of 0 is re-taken in FP64 from the exact start node.
+//
+// GB300 notes.  FP64 runs at a small fraction of the FP32 rate on this part,
+// so the FP32 kernel keeps every FP64 (and double-float) instruction in
+// non-inlined rare-path functions, and lattice integers are kept as
+// integer-valued floats, converted with exact bit tricks on the ALU/FMA
+// pipes (|values| < 2^22).  The packed index of a lattice point is separable,
+// idx(p) = T3(p1) + T2(p2) + p3, so the 10 P2 nodes of a micro simplex are
+// sums of three per-axis table entries; the tables are sorted together with
+// the fractions, which leaves 2 integer adds per node.
 #include <cstdint>
 
 #include "elm_internal.h"
@@ -39,6 +51,74 @@ namespace {
 constexpr double kTol64 = 1e-9;     // "inside" tolerance, lattice units (FP64)
 constexpr float kBand32 = 3e-5f;    // FP32 tie band re-decided in FP64, lattice units
 
+// ---------------------------------------------------------------------------
+// Exact conversions for integer values |v| < 2^22 without conversion
+// instructions (1.5 * 2^23 places the integer in the low mantissa bits).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int f2i_exact(float x) { return __float_as_int(x + 12582912.0f) - 0x4B400000; }
+__device__ __forceinline__ float i2f_exact(int i) { return __int_as_float(i + 0x4B400000) - 12582912.0f; }
+__device__ __forceinline__ int f2i_exact(double x) {
+  return int(__double_as_longlong(x + 6755399441055744.0) - 0x4338000000000000LL);
+}
+__device__ __forceinline__ double i2f_exact_d(int i) {
+  return __longlong_as_double(0x4338000000000000LL + i) - 6755399441055744.0;
+}
+template <class R>
+__device__ __forceinline__ R to_real(int i);
+template <>
+__device__ __forceinline__ float to_real<float>(int i) { return i2f_exact(i); }
+template <>
+__device__ __forceinline__ double to_real<double>(int i) { return i2f_exact_d(i); }
+
+// floor for |x| < 2^22 on the FMA pipe: adding 1.5 * 2^23 rounds x to the
+// nearest integer, which is then corrected down if it lies above x.
+__device__ __forceinline__ float floor_small(float x) {
+  const float r = (x + 12582912.0f) - 12582912.0f;
+  return r > x ? r - 1.0f : r;
+}
+
+// Precision-exact math: the float overloads never promote to FP64.
+__device__ __forceinline__ float r_floor(float x) { return floor_small(x); }
+__device__ __forceinline__ double r_floor(double x) { return ::floor(x); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ float r_clamp(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+__device__ __forceinline__ double r_clamp(double x, double lo, double hi) { return ::fmin(::fmax(x, lo), hi); }
+
+// ---------------------------------------------------------------------------
+// Double-float helpers (error-free transformations; no FP64 instructions).
+// ---------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_renorm(float s, float e) {
+  const float hi = s + e;
+  return {hi, e - (hi - s)};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
+  return df_renorm(s, e);
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p) + fmaf(a.hi, b.lo, a.lo * b.hi);
+  return df_renorm(p, e);
+}
+
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  const float p = a.hi * b;
+  const float e = fmaf(a.hi, b, -p) + a.lo * b;
+  return df_renorm(p, e);
+}
+
+// ---------------------------------------------------------------------------
+// Macro tables in the working precision.
+// ---------------------------------------------------------------------------
 template <class R>
 struct Tables;
 
@@ -63,53 +143,187 @@ struct Tables<float> {
 __device__ __forceinline__ int tri2(int k) { return k * (k + 1) / 2; }
 __device__ __forceinline__ int tri3(int k) { return k * (k + 1) * (k + 2) / 6; }
 
-// Storage slot within a macro -> lattice point p (packed order p1, p2[, p3]).
+// Slot within a macro -> lattice point p (packed order p1, p2[, p3]).  The
+// row and slab are estimated with the MUFU log2/exp2/rsqrt approximations
+// (cbrt(6 r), (sqrt(8 r + 1) - 1) / 2) and made exact by integer fix-up
+// loops; libm's cbrtf/sqrtf would add FP64 or long FP32 sequences.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <int D>
+__device__ __forceinline__ int tri_root2(int r) {
+  const float x = 8.0f * i2f_exact(r) + 1.0f;
+  int k = f2i_exact(floor_small((x * rsqrtf(x) - 1.0f) * 0.5f));
+  k = max(k, 0);
+  while (k > 0 && tri2(k) > r) --k;
+  while (tri2(k + 1) <= r) ++k;
+  return k;
+}
+
 template <int D>
 __device__ __forceinline__ void unpack(int r, int* p) {
   if (D == 3) {
-    int p1 = __float2int_rd(cbrtf(6.0f * float(r)));
+    int p1 = f2i_exact(floor_small(ex2_approx(__log2f(6.0f * i2f_exact(r) + 1.0f) * (1.0f / 3.0f))));
+    p1 = max(p1 - 1, 0);
     while (p1 > 0 && tri3(p1) > r) --p1;
     while (tri3(p1 + 1) <= r) ++p1;
     r -= tri3(p1);
-    int p2 = __float2int_rd((sqrtf(8.0f * float(r) + 1.0f) - 1.0f) * 0.5f);
-    while (p2 > 0 && tri2(p2) > r) --p2;
-    while (tri2(p2 + 1) <= r) ++p2;
+    const int p2 = tri_root2<D>(r);
     p[0] = p1;
     p[1] = p2;
     p[2] = r - tri2(p2);
   } else {
-    int p1 = __float2int_rd((sqrtf(8.0f * float(r) + 1.0f) - 1.0f) * 0.5f);
-    while (p1 > 0 && tri2(p1) > r) --p1;
-    while (tri2(p1 + 1) <= r) ++p1;
+    const int p1 = tri_root2<D>(r);
     p[0] = p1;
     p[1] = r - tri2(p1);
   }
 }
 
+// ---------------------------------------------------------------------------
+// Rare paths: entering a foreign macro and the FP64 tie-break.  They are free,
+// non-inlined functions taking scalars and returning small structs: the
+// start-node position they need is loop-invariant, and once inlined the
+// compiler hoists that FP64 / double-float work out of the rare branch into
+// every thread (costly on this GPU's narrow FP64 pipe), while a non-inlined
+// member function would force the tracer state onto the stack.
+// ---------------------------------------------------------------------------
+struct Frame {
+  float bq0, bq1, bq2, r00, r01, r02;
+};
+struct FrameD {
+  double bq0, bq1, bq2, r00, r01, r02;
+};
+struct Min64 {
+  double lmin;
+  int kmin;
+};
+
+// Start node x_i = v0_m0 + J_m0 (p / M) in FP64.
 template <int D>
-__device__ __forceinline__ int packed(const int* p) {
-  return D == 3 ? tri3(p[0]) + tri2(p[1]) + p[2] : tri2(p[0]) + p[1];
+__device__ __forceinline__ void node_position64(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N,
+                                                double* x) {
+  const MacroGeo& g0 = geo[m0];
+  const double invM = 1.0 / double(2 * N);
+  const double s[3] = {double(p0) * invM, double(p1) * invM, double(p2) * invM};
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    double v = g0.v0[r];
+#pragma unroll
+    for (int c = 0; c < D; ++c) v = ::fma(g0.J[r * 3 + c], s[c], v);
+    x[r] = v;
+  }
+}
+
+// Lattice coordinate of the start node in macro mm, FP64.
+template <int D>
+__device__ __forceinline__ void node_lattice64(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N, int mm,
+                                               double* q) {
+  double x[D];
+  node_position64<D>(geo, m0, p0, p1, p2, N, x);
+  const MacroGeo& g = geo[mm];
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    double v = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) v = ::fma(g.NJinv[r * 3 + c], x[c] - g.v0[c], v);
+    q[r] = v;
+  }
+}
+
+template <int D>
+__device__ __noinline__ FrameD frame64(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N, int mm) {
+  double q[3] = {0.0, 0.0, 0.0};
+  node_lattice64<D>(geo, m0, p0, p1, p2, N, mm, q);
+  FrameD f;
+  f.bq0 = ::floor(q[0]);
+  f.bq1 = ::floor(q[1]);
+  f.bq2 = ::floor(q[2]);
+  f.r00 = q[0] - f.bq0;
+  f.r01 = q[1] - f.bq1;
+  f.r02 = q[2] - f.bq2;
+  return f;
+}
+
+// double-float on the FP32 pipe: x_i = v0_m0 + J_m0 (p / M); q = NJinv_mm (x_i - v0_mm)
+template <int D>
+__device__ __noinline__ Frame frame_df(const MacroGeo32* tg, int m0, int p0, int p1, int p2, float invM, int mm) {
+  const MacroGeo32& g0 = tg[m0];
+  const MacroGeo32& g = tg[mm];
+  const int pp[3] = {p0, p1, p2};
+  df y[D];
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    df acc = {g0.v0[r], g0.v0_lo[r]};
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      acc = df_add(acc, df_mul_f(df{g0.J[r * 3 + c], g0.J_lo[r * 3 + c]}, i2f_exact(pp[c]) * invM));
+    y[r] = df_add(acc, df{-g.v0[r], -g.v0_lo[r]});
+  }
+  float bq[3] = {0.0f, 0.0f, 0.0f}, r0[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    df q = {0.0f, 0.0f};
+#pragma unroll
+    for (int c = 0; c < D; ++c) q = df_add(q, df_mul(df{g.NJinv[r * 3 + c], g.NJinv_lo[r * 3 + c]}, y[c]));
+    float fl = floor_small(q.hi);
+    if (fl == q.hi && q.lo < 0.0f) fl -= 1.0f;
+    bq[r] = fl;
+    r0[r] = (q.hi - fl) + q.lo;
+  }
+  return Frame{bq[0], bq[1], bq[2], r0[0], r0[1], r0[2]};
+}
+
+// FP64 minimum barycentric (lattice units) of x_i + d in macro m, and its face.
+template <int D>
+__device__ __noinline__ Min64 bary64_min(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N, int m,
+                                         float d0, float d1, float d2) {
+  double q[3] = {0.0, 0.0, 0.0};
+  node_lattice64<D>(geo, m0, p0, p1, p2, N, m, q);
+  const MacroGeo& g = geo[m];
+  const double d[3] = {double(d0), double(d1), double(d2)};
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) q[r] = ::fma(g.NJinv[r * 3 + c], d[c], q[r]);
+  double l[D + 1];
+  l[0] = double(N) - q[0];
+#pragma unroll
+  for (int k = 1; k < D; ++k) l[k] = q[k - 1] - q[k];
+  l[D] = q[D - 1];
+  Min64 out{l[0], 0};
+#pragma unroll
+  for (int k = 1; k <= D; ++k)
+    if (l[k] < out.lmin) {
+      out.lmin = l[k];
+      out.kmin = k;
+    }
+  return out;
 }
 
 // Per-thread tracing state.
-template <int D, class R>
+template <int D, class R, bool STEADY>
 struct Tracer {
+  static constexpr int NB = (D + 1) * (D + 2) / 2;  // P2 nodes of a simplex
   // launch constants (copied, so no kernel parameter is addressed)
-  const MacroGeo* geo;   // FP64 macro table (start-node frames, tie-breaks)
+  const MacroGeo* geo;   // FP64 macro table (tie-breaks)
   Tables<R> tab;         // macro table in the working precision
   int N;
-  int64_t npm;
+  int npm;
   const R* un;
   const R* uo;
   const R* T;
-  int steady;
   R dt;
+  R Nf;
+  R invM;          // 1 / 2^(L+1), exact
   unsigned* status;
   int m0;          // home macro
   int p[D];        // home lattice point
-  // current frame: q = b + r0 + nj * d
+  // current frame: q = bq + r0 + nj * d
   int m;
-  int b[D];
+  R bq[D];
   R r0[D];
   R nj[D * D];
   R dlo[D], dhi[D];  // box limits as offsets from x_i
@@ -125,94 +339,62 @@ struct Tracer {
     m = m0;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      b[k] = p[k] >> 1;
+      bq[k] = to_real<R>(p[k] >> 1);
       r0[k] = (p[k] & 1) ? R(0.5) : R(0);
     }
     load_nj(m0);
   }
 
-  // Exact (FP64) start node position.
-  __device__ void node_position64(double* x) const {
-    const MacroGeo& g = geo[m0];
-    const double invM = 1.0 / double(2 * N);
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-      double s = g.v0[r];
-#pragma unroll
-      for (int c = 0; c < D; ++c) s = fma(g.J[r * 3 + c], double(p[c]) * invM, s);
-      x[r] = s;
-    }
-  }
-
-  // Lattice coordinate of the start node in macro mm, FP64.
-  __device__ void node_lattice64(int mm, double* q) const {
-    double x[D];
-    node_position64(x);
-    const MacroGeo& g = geo[mm];
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-      double s = 0.0;
-#pragma unroll
-      for (int c = 0; c < D; ++c) s = fma(g.NJinv[r * 3 + c], x[c] - g.v0[c], s);
-      q[r] = s;
-    }
-  }
-
+  // Enters macro mm: (bq, r0) of the start node in mm's frame.
   __device__ void foreign_frame(int mm) {
     if (mm == m0) {
       home_frame();
       return;
     }
-    double q[D];
-    node_lattice64(mm, q);
     m = mm;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const double fl = floor(q[k]);
-      b[k] = int(fl);
-      r0[k] = R(q[k] - fl);
+    if constexpr (sizeof(R) == 8) {
+      const FrameD f = frame64<D>(geo, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, N, mm);
+      bq[0] = f.bq0;
+      bq[1] = f.bq1;
+      r0[0] = f.r00;
+      r0[1] = f.r01;
+      if (D == 3) {
+        bq[D - 1] = f.bq2;
+        r0[D - 1] = f.r02;
+      }
+    } else {
+      const Frame f = frame_df<D>(tab.g, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, float(invM), mm);
+      bq[0] = R(f.bq0);
+      bq[1] = R(f.bq1);
+      r0[0] = R(f.r00);
+      r0[1] = R(f.r01);
+      if (D == 3) {
+        bq[D - 1] = R(f.bq2);
+        r0[D - 1] = R(f.r02);
+      }
     }
     load_nj(mm);
   }
 
-  // Macro barycentrics in lattice units from the split coordinate (c, f).
-  __device__ static void bary(int N, const int* c, const R* f, R* l) {
-    l[0] = R(N - c[0]) - f[0];
-#pragma unroll
-    for (int k = 1; k < D; ++k) l[k] = R(c[k - 1] - c[k]) + (f[k - 1] - f[k]);
-    l[D] = R(c[D - 1]) + f[D - 1];
-  }
-
-  // FP64 barycentrics of the point x_i + d in the current macro.
-  __device__ void bary64(const R* d, double* l) const {
-    double q[D];
-    node_lattice64(m, q);
-    const MacroGeo& g = geo[m];
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = 0; c < D; ++c) q[r] = fma(g.NJinv[r * 3 + c], double(d[c]), q[r]);
-    l[0] = double(N) - q[0];
-#pragma unroll
-    for (int k = 1; k < D; ++k) l[k] = q[k - 1] - q[k];
-    l[D] = q[D - 1];
-  }
-
   // Locates x_i + d: walks macros from the current frame, returns the micro
-  // cell c and fractions f (retracted into the macro's reference simplex).
-  __device__ void locate(const R* d, int* c, R* f) {
+  // cell c (integer-valued reals) and fractions f, retracted into the
+  // macro's reference simplex N >= q1 >= q2 (>= q3) >= 0.
+  __device__ void locate(const R* d, R* c, R* f) {
     for (int hop = 0;; ++hop) {
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         R r = r0[k];
 #pragma unroll
-        for (int j = 0; j < D; ++j) r = fma(nj[k * D + j], d[j], r);
-        const R fl = floor(r);
-        c[k] = b[k] + int(fl);
+        for (int j = 0; j < D; ++j) r = r_fma(nj[k * D + j], d[j], r);
+        const R fl = r_floor(r);
+        c[k] = bq[k] + fl;
         f[k] = r - fl;
       }
       R l[D + 1];
-      bary(N, c, f, l);
+      l[0] = (Nf - c[0]) - f[0];
+#pragma unroll
+      for (int k = 1; k < D; ++k) l[k] = (c[k - 1] - c[k]) + (f[k - 1] - f[k]);
+      l[D] = c[D - 1] + f[D - 1];
       int kmin = 0;
       R lmin = l[0];
 #pragma unroll
@@ -222,125 +404,156 @@ struct Tracer {
           kmin = k;
         }
       bool outside;
-      if (sizeof(R) == 4) {
+      int nb;
+      if constexpr (sizeof(R) == 4) {
         outside = lmin < R(-kBand32);
-        if (!outside && lmin < R(kBand32)) {
-          // tie band: decide in FP64 from the exact start node
-          double l64[D + 1];
-          bary64(d, l64);
-          double m64 = l64[0];
-          int k64 = 0;
-#pragma unroll
-          for (int k = 1; k <= D; ++k)
-            if (l64[k] < m64) {
-              m64 = l64[k];
-              k64 = k;
-            }
-          outside = m64 < -kTol64;
-          kmin = k64;
+        nb = tab.nb(m, kmin);
+        if (!outside && lmin < R(kBand32) && nb >= 0) {
+          // tie band at an interior face: decide in FP64 from the exact start node
+          const Min64 r64 = bary64_min<D>(geo, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, N, m, float(d[0]),
+                                          float(d[1]), D == 3 ? float(d[D - 1]) : 0.0f);
+          outside = r64.lmin < -kTol64;
+          kmin = r64.kmin;
+          nb = tab.nb(m, kmin);
         }
       } else {
         outside = lmin < R(-kTol64);
+        nb = outside ? tab.nb(m, kmin) : -1;
       }
-      if (!outside) break;
-      const int nb = tab.nb(m, kmin);
-      if (nb < 0) break;  // outside the mesh: the retraction below clamps
+      if (!outside || nb < 0) break;  // inside, or outside the mesh (retraction clamps)
       if (hop >= kMaxHops) {
         atomicOr(status, kFlagWalkLimit);
         break;
       }
       foreign_frame(nb);
     }
-    // Retraction into N >= q1 >= q2 (>= q3) >= 0 on the split coordinate.
-    if (c[0] < 0) { c[0] = 0; f[0] = R(0); }
-    if (c[0] > N - 1) { c[0] = N - 1; f[0] = R(1); }
+    if (c[0] < R(0)) { c[0] = R(0); f[0] = R(0); }
+    if (c[0] > Nf - R(1)) { c[0] = Nf - R(1); f[0] = R(1); }
 #pragma unroll
     for (int k = 1; k < D; ++k) {
       if (c[k] > c[k - 1] || (c[k] == c[k - 1] && f[k] > f[k - 1])) { c[k] = c[k - 1]; f[k] = f[k - 1]; }
-      if (c[k] < 0) { c[k] = 0; f[k] = R(0); }
+      if (c[k] < R(0)) { c[k] = R(0); f[k] = R(0); }
     }
   }
 
-  // P2 stencil of the micro simplex holding (c, f): storage slots and basis.
-  __device__ void stencil(const int* c, const R* f, int64_t* slot, R* phi) const {
-    // descending order of f, ties by axis (stable)
-    int s[D];
+  // P2 stencil of the micro simplex holding (c, f): slots within macro m and
+  // basis values.  Per axis a the packed index contributes A_a[o] for the
+  // lattice offset o in {0, 1, 2} of the node from 2c; sorting the axes by
+  // descending fraction (ties by axis) orders the Kuhn path c -> c + 1, and
+  // each node's offsets along the sorted axes are fixed (alpha >= beta >= gamma).
+  __device__ void stencil(const R* c, const R* f, int* slot, R* phi) const {
+    int A[D][3];
     R fs[D];
+    {
+      const int c0 = 2 * f2i_exact(c[0]);
+      if (D == 3) {
+        const int c1 = 2 * f2i_exact(c[1]);
+        const int c2 = 2 * f2i_exact(c[D - 1]);
+        A[0][0] = tri3(c0);
+        A[0][1] = A[0][0] + tri2(c0 + 1);
+        A[0][2] = A[0][1] + tri2(c0 + 2);
+        A[1][0] = tri2(c1);
+        A[1][1] = A[1][0] + c1 + 1;
+        A[1][2] = A[1][1] + c1 + 2;
+        A[D - 1][0] = c2;
+        A[D - 1][1] = c2 + 1;
+        A[D - 1][2] = c2 + 2;
+      } else {
+        const int c1 = 2 * f2i_exact(c[D - 1]);
+        A[0][0] = tri2(c0);
+        A[0][1] = A[0][0] + c0 + 1;
+        A[0][2] = A[0][1] + c0 + 2;
+        A[D - 1][0] = c1;
+        A[D - 1][1] = c1 + 1;
+        A[D - 1][2] = c1 + 2;
+      }
 #pragma unroll
-    for (int k = 0; k < D; ++k) { s[k] = k; fs[k] = f[k]; }
+      for (int k = 0; k < D; ++k) fs[k] = f[k];
+    }
     auto cswap = [&](int i, int j) {
       if (fs[j] > fs[i]) {
         R t = fs[i]; fs[i] = fs[j]; fs[j] = t;
-        int u = s[i]; s[i] = s[j]; s[j] = u;
+#pragma unroll
+        for (int o = 0; o < 3; ++o) { int u = A[i][o]; A[i][o] = A[j][o]; A[j][o] = u; }
       }
     };
-    if (D == 3) { cswap(0, 1); cswap(1, 2); cswap(0, 1); } else { cswap(0, 1); }
-    // micro vertices w_v = c + e_s0 + .. + e_s(v-1); barycentrics L
-    int w[D + 1][D];
     R L[D + 1];
-#pragma unroll
-    for (int k = 0; k < D; ++k) w[0][k] = c[k];
-#pragma unroll
-    for (int v = 1; v <= D; ++v) {
-#pragma unroll
-      for (int k = 0; k < D; ++k) w[v][k] = w[v - 1][k] + (s[v - 1] == k ? 1 : 0);
+    if (D == 3) {
+      cswap(0, 1); cswap(1, 2); cswap(0, 1);
+      L[0] = R(1) - fs[0];
+      L[1] = fs[0] - fs[1];
+      L[2] = fs[1] - fs[D - 1];
+      L[D] = fs[D - 1];
+      // vertices v0..v3, edges 01 02 03 12 13 23
+      slot[0] = A[0][0] + A[1][0] + A[D - 1][0];
+      slot[1] = A[0][2] + A[1][0] + A[D - 1][0];
+      slot[2] = A[0][2] + A[1][2] + A[D - 1][0];
+      slot[3] = A[0][2] + A[1][2] + A[D - 1][2];
+      slot[4] = A[0][1] + A[1][0] + A[D - 1][0];
+      slot[5] = A[0][1] + A[1][1] + A[D - 1][0];
+      slot[6] = A[0][1] + A[1][1] + A[D - 1][1];
+      slot[7] = A[0][2] + A[1][1] + A[D - 1][0];
+      slot[8] = A[0][2] + A[1][1] + A[D - 1][1];
+      slot[9 % NB] = A[0][2] + A[1][2] + A[D - 1][1];
+      phi[0] = L[0] * (R(2) * L[0] - R(1));
+      phi[1] = L[1] * (R(2) * L[1] - R(1));
+      phi[2] = L[2] * (R(2) * L[2] - R(1));
+      phi[3] = L[D] * (R(2) * L[D] - R(1));
+      phi[4] = R(4) * L[0] * L[1];
+      phi[5] = R(4) * L[0] * L[2];
+      phi[6] = R(4) * L[0] * L[D];
+      phi[7] = R(4) * L[1] * L[2];
+      phi[8] = R(4) * L[1] * L[D];
+      phi[9 % NB] = R(4) * L[2] * L[D];
+    } else {
+      cswap(0, 1);
+      L[0] = R(1) - fs[0];
+      L[1] = fs[0] - fs[D - 1];
+      L[D] = fs[D - 1];
+      // vertices v0..v2, edges 01 02 12
+      slot[0] = A[0][0] + A[D - 1][0];
+      slot[1] = A[0][2] + A[D - 1][0];
+      slot[2] = A[0][2] + A[D - 1][2];
+      slot[3] = A[0][1] + A[D - 1][0];
+      slot[4] = A[0][1] + A[D - 1][1];
+      slot[5] = A[0][2] + A[D - 1][1];
+      phi[0] = L[0] * (R(2) * L[0] - R(1));
+      phi[1] = L[1] * (R(2) * L[1] - R(1));
+      phi[2] = L[D] * (R(2) * L[D] - R(1));
+      phi[3] = R(4) * L[0] * L[1];
+      phi[4] = R(4) * L[0] * L[D];
+      phi[5] = R(4) * L[1] * L[D];
     }
-    L[0] = R(1) - fs[0];
-#pragma unroll
-    for (int v = 1; v < D; ++v) L[v] = fs[v - 1] - fs[v];
-    L[D] = fs[D - 1];
-    const int64_t base = int64_t(m) * npm;
-    int n = 0;
-#pragma unroll
-    for (int v = 0; v <= D; ++v) {
-      int q[D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) q[k] = 2 * w[v][k];
-      slot[n] = base + packed<D>(q);
-      phi[n] = L[v] * (R(2) * L[v] - R(1));
-      ++n;
-    }
-#pragma unroll
-    for (int i = 0; i <= D; ++i)
-#pragma unroll
-      for (int j = i + 1; j <= D; ++j) {
-        int q[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) q[k] = w[i][k] + w[j][k];
-        slot[n] = base + packed<D>(q);
-        phi[n] = R(4) * L[i] * L[j];
-        ++n;
-      }
   }
 
   __device__ void clamp_box(R* d) const {
 #pragma unroll
-    for (int k = 0; k < D; ++k) d[k] = fmin(fmax(d[k], dlo[k]), dhi[k]);
+    for (int k = 0; k < D; ++k) d[k] = r_clamp(d[k], dlo[k], dhi[k]);
   }
 
   // Velocity u~ at x_i + d at backward time `back` (Eq. linear interpolation).
   __device__ void velocity(const R* d, R back, R* k) {
-    constexpr int NB = (D + 1) * (D + 2) / 2;
-    int c[D];
-    R f[D];
+    R c[D], f[D];
     locate(d, c, f);
-    int64_t slot[NB];
+    int slot[NB];
     R phi[NB];
     stencil(c, f, slot, phi);
+    const R* ub = un + int64_t(m) * npm * D;
 #pragma unroll
     for (int r = 0; r < D; ++r) k[r] = R(0);
 #pragma unroll
     for (int j = 0; j < NB; ++j)
 #pragma unroll
-      for (int r = 0; r < D; ++r) k[r] = fma(phi[j], __ldg(un + slot[j] * D + r), k[r]);
-    if (!steady) {
+      for (int r = 0; r < D; ++r) k[r] = r_fma(phi[j], __ldg(ub + slot[j] * D + r), k[r]);
+    if constexpr (!STEADY) {
+      const R* ob = uo + int64_t(m) * npm * D;
       R ko[D];
 #pragma unroll
       for (int r = 0; r < D; ++r) ko[r] = R(0);
 #pragma unroll
       for (int j = 0; j < NB; ++j)
 #pragma unroll
-        for (int r = 0; r < D; ++r) ko[r] = fma(phi[j], __ldg(uo + slot[j] * D + r), ko[r]);
+        for (int r = 0; r < D; ++r) ko[r] = r_fma(phi[j], __ldg(ob + slot[j] * D + r), ko[r]);
       const R w_old = back / dt, w_new = (dt - back) / dt;
 #pragma unroll
       for (int r = 0; r < D; ++r) k[r] = w_old * ko[r] + w_new * k[r];
@@ -348,98 +561,122 @@ struct Tracer {
   }
 
   __device__ R scalar(const R* d) {
-    constexpr int NB = (D + 1) * (D + 2) / 2;
-    int c[D];
-    R f[D];
+    R c[D], f[D];
     locate(d, c, f);
-    int64_t slot[NB];
+    int slot[NB];
     R phi[NB];
     stencil(c, f, slot, phi);
+    const R* tb = T + int64_t(m) * npm;
     R v = R(0);
 #pragma unroll
-    for (int j = 0; j < NB; ++j) v = fma(phi[j], __ldg(T + slot[j]), v);
+    for (int j = 0; j < NB; ++j) v = r_fma(phi[j], __ldg(tb + slot[j]), v);
     return v;
   }
 };
 
-template <int D, class R>
-__global__ void __launch_bounds__(256) k_advect(AdvectArgs args, Tables<R> tab) {
-  const int64_t slot = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (slot >= args.n_storage) return;
-  Tracer<D, R> t;
+#ifndef ELM_ADVECT_MIN_BLOCKS
+#define ELM_ADVECT_MIN_BLOCKS 1
+#endif
+#ifndef ELM_ADVECT_THREADS
+#define ELM_ADVECT_THREADS 256
+#endif
+
+// grid: x = blocks over one macro's slots, y = macro (offset by macro0)
+template <class R>
+__device__ __forceinline__ const StepConsts<R>& consts(const AdvectArgs& a);
+template <>
+__device__ __forceinline__ const StepConsts<float>& consts<float>(const AdvectArgs& a) { return a.k32; }
+template <>
+__device__ __forceinline__ const StepConsts<double>& consts<double>(const AdvectArgs& a) { return a.k64; }
+
+template <int D, class R, bool STEADY>
+__global__ void __launch_bounds__(ELM_ADVECT_THREADS, ELM_ADVECT_MIN_BLOCKS)
+    k_advect(AdvectArgs args, Tables<R> tab, int macro0) {
+  const StepConsts<R>& K = consts<R>(args);
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int npm = int(args.npm);
+  if (r >= npm) return;
+  Tracer<D, R, STEADY> t;
   t.geo = args.geo;
   t.tab = tab;
   t.N = args.N;
-  t.npm = args.npm;
+  t.npm = npm;
   t.un = static_cast<const R*>(args.u_new);
   t.uo = static_cast<const R*>(args.u_old);
   t.T = static_cast<const R*>(args.T_old);
-  t.steady = args.steady;
-  t.dt = R(args.dt);
+  t.dt = K.dt;
+  t.Nf = K.Nf;
+  t.invM = K.invM;
   t.status = args.status;
   // (i) particle creation at the node (interface copies trace their owner)
-  t.m0 = int(slot / args.npm);
-  unpack<D>(int(slot - int64_t(t.m0) * args.npm), t.p);
+  t.m0 = macro0 + int(blockIdx.y);
+  const int64_t slot = int64_t(t.m0) * npm + r;
+  unpack<D>(r, t.p);
+  int r_own = r;
   {
     const int M = 2 * args.N;
     bool iface = t.p[0] == M || t.p[D - 1] == 0;
 #pragma unroll
     for (int k = 1; k < D; ++k) iface = iface || t.p[k] == t.p[k - 1];
     if (iface) {
-      const int64_t own = args.owner[args.unique_map[slot]];
-      if (own != slot) {
-        t.m0 = int(own / args.npm);
-        unpack<D>(int(own - int64_t(t.m0) * args.npm), t.p);
+      const int64_t own = args.owner_mr[args.unique_map[slot]];
+      const int om = int(own >> 32);
+      const int orr = int(own & 0xffffffffLL);
+      if (om != t.m0 || orr != r) {
+        t.m0 = om;
+        r_own = orr;
+        unpack<D>(orr, t.p);
       }
     }
   }
   {
-    const R invM = R(1) / R(2 * args.N);
 #pragma unroll
-    for (int r = 0; r < D; ++r) {
-      R x = tab.v0(t.m0, r);
+    for (int q = 0; q < D; ++q) {
+      R x = tab.v0(t.m0, q);
 #pragma unroll
-      for (int c = 0; c < D; ++c) x = fma(tab.J(t.m0, r * 3 + c), R(t.p[c]) * invM, x);
-      t.dlo[r] = R(args.lo[r]) - x;
-      t.dhi[r] = R(args.hi[r]) - x;
+      for (int c = 0; c < D; ++c) x = r_fma(tab.J(t.m0, q * 3 + c), to_real<R>(t.p[c]) * K.invM, x);
+      t.dlo[q] = K.lo[q] - x;
+      t.dhi[q] = K.hi[q] - x;
     }
   }
   t.home_frame();
-  // (ii) backward RK4, n_sub substeps of h = dt / n_sub
-  const R h = R(args.dt) / R(args.n_sub);
-  const R* un = t.un;
-  R d[D], k1[D], k[D], acc[D], z[D];
+  const R* u_node = t.un + (int64_t(t.m0) * npm + r_own) * D;
+  // (ii) backward RK4, n_sub substeps of h = dt / n_sub.  All 4 n_sub stage
+  // evaluations run through one loop with a single evaluation site (stage s
+  // of a substep sits at d, d - h/2 k, d - h/2 k, d - h k and has weight
+  // 1, 2, 2, 1), which keeps the kernel's code small.
+  const R h = K.h, h2 = K.h2, h6 = K.h6;
+  R d[D], k[D], acc[D];
 #pragma unroll
-  for (int r = 0; r < D; ++r) d[r] = R(0);
+  for (int q = 0; q < D; ++q) {
+    d[q] = R(0);
+    // the first stage sits on the node: the P2 interpolant is the nodal value
+    // (steady, or at t_{n+1} where only u^{n+1} has weight)
+    k[q] = __ldg(u_node + q);
+    acc[q] = k[q];
+  }
   bool finite = true;
-  for (int j = 0; j < args.n_sub; ++j) {
-    const R back = R(j) * h;
-    if (j == 0) {
-      // the first stage sits on the node: the P2 interpolant is the nodal value
+  const int n_eval = 4 * args.n_sub;
+#pragma unroll 1
+  for (int e = 1; e < n_eval; ++e) {
+    const int s = e & 3;
+    const R off = s == 0 ? R(0) : (s == 3 ? h : h2);
+    R z[D];
 #pragma unroll
-      for (int r = 0; r < D; ++r) k1[r] = __ldg(un + slot * D + r);
-    } else {
-      t.velocity(d, back, k1);
+    for (int q = 0; q < D; ++q) z[q] = d[q] - off * k[q];
+    t.clamp_box(z);
+    t.velocity(z, to_real<R>(e >> 2) * h + off, k);
+    const R w = (s == 1 || s == 2) ? R(2) : R(1);
+#pragma unroll
+    for (int q = 0; q < D; ++q) acc[q] = s == 0 ? k[q] : r_fma(w, k[q], acc[q]);
+    if (s == 3) {
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        finite = finite && isfinite(acc[q]);
+        d[q] = d[q] - h6 * acc[q];
+      }
+      t.clamp_box(d);
     }
-#pragma unroll
-    for (int r = 0; r < D; ++r) { acc[r] = k1[r]; z[r] = d[r] - R(0.5) * h * k1[r]; }
-    t.clamp_box(z);
-    t.velocity(z, back + R(0.5) * h, k);
-#pragma unroll
-    for (int r = 0; r < D; ++r) { acc[r] = fma(R(2), k[r], acc[r]); z[r] = d[r] - R(0.5) * h * k[r]; }
-    t.clamp_box(z);
-    t.velocity(z, back + R(0.5) * h, k);
-#pragma unroll
-    for (int r = 0; r < D; ++r) { acc[r] = fma(R(2), k[r], acc[r]); z[r] = d[r] - h * k[r]; }
-    t.clamp_box(z);
-    t.velocity(z, back + h, k);
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-      acc[r] += k[r];
-      finite = finite && isfinite(acc[r]);
-      d[r] = d[r] - h / R(6) * acc[r];
-    }
-    t.clamp_box(d);
   }
   // (iii) temperature at the departure point
   const R v = t.scalar(d);
@@ -458,22 +695,32 @@ __global__ void k_gather(const R* __restrict__ in, R* __restrict__ out, const in
   out[i] = in[idx[node] * ncomp + c];
 }
 
+template <int D, class R, bool STEADY>
+cudaError_t launch_drs(const AdvectArgs& a, Tables<R> t, cudaStream_t s) {
+  const int threads = ELM_ADVECT_THREADS;
+  const unsigned bx = unsigned((a.npm + threads - 1) / threads);
+  for (int m0 = 0; m0 < a.n_macros; m0 += 65535) {
+    const unsigned by = unsigned(a.n_macros - m0 < 65535 ? a.n_macros - m0 : 65535);
+    k_advect<D, R, STEADY><<<dim3(bx, by), threads, 0, s>>>(a, t, m0);
+  }
+  return cudaGetLastError();
+}
+
+template <int D, class R>
+cudaError_t launch_dr(const AdvectArgs& a, Tables<R> t, cudaStream_t s) {
+  return a.steady ? launch_drs<D, R, true>(a, t, s) : launch_drs<D, R, false>(a, t, s);
+}
+
 }  // namespace
 
 cudaError_t launch_advect(int dim, int precision, const AdvectArgs& a, cudaStream_t s) {
-  const int threads = 256;
-  const int64_t blocks = (a.n_storage + threads - 1) / threads;
-  if (blocks == 0) return cudaSuccess;
+  if (a.n_storage == 0) return cudaSuccess;
   if (precision == ELM_FP64) {
     Tables<double> t{a.geo};
-    if (dim == 3) k_advect<3, double><<<unsigned(blocks), threads, 0, s>>>(a, t);
-    else k_advect<2, double><<<unsigned(blocks), threads, 0, s>>>(a, t);
-  } else {
-    Tables<float> t{a.geo32};
-    if (dim == 3) k_advect<3, float><<<unsigned(blocks), threads, 0, s>>>(a, t);
-    else k_advect<2, float><<<unsigned(blocks), threads, 0, s>>>(a, t);
+    return dim == 3 ? launch_dr<3, double>(a, t, s) : launch_dr<2, double>(a, t, s);
   }
-  return cudaGetLastError();
+  Tables<float> t{a.geo32};
+  return dim == 3 ? launch_dr<3, float>(a, t, s) : launch_dr<2, float>(a, t, s);
 }
 
 cudaError_t launch_gather(int precision, const void* in, void* out, const int64_t* idx, int64_t n, int ncomp,

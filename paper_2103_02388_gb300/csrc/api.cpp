@@ -38,10 +38,11 @@ void free_tables(elm_mesh_s* me) {
   cudaFree(me->d_geo32);
   cudaFree(me->d_unique_map);
   cudaFree(me->d_owner);
+  cudaFree(me->d_owner_mr);
   cudaFree(me->d_status);
   me->d_geo = nullptr;
   me->d_geo32 = nullptr;
-  me->d_unique_map = me->d_owner = nullptr;
+  me->d_unique_map = me->d_owner = me->d_owner_mr = nullptr;
   me->d_status = nullptr;
 }
 
@@ -205,7 +206,19 @@ elm_status elm_advect(elm_mesh me, const void* T_old_dev, void* T_new_dev, doubl
   a.n_sub = n_sub;
   a.status = me->d_status;
   a.unique_map = me->d_unique_map;
-  a.owner = me->d_owner;
+  {
+    const double h = dt / n_sub;
+    a.k64 = {h, 0.5 * h, h / 6.0, dt, 1.0 / me->M, double(me->N), {0, 0, 0}, {0, 0, 0}};
+    a.k32 = {float(h), float(0.5 * h), float(h / 6.0), float(dt), float(1.0 / me->M), float(me->N),
+             {0, 0, 0}, {0, 0, 0}};
+    for (int r = 0; r < 3; ++r) {
+      a.k64.lo[r] = me->lo[r];
+      a.k64.hi[r] = me->hi[r];
+      a.k32.lo[r] = float(me->lo[r]);
+      a.k32.hi[r] = float(me->hi[r]);
+    }
+  }
+  a.owner_mr = me->d_owner_mr;
   cudaError_t e = elm::launch_advect(me->dim, me->precision, a, s);
   if (e != cudaSuccess) return cuda_fail(e, "elm_advect");
   return ELM_OK;

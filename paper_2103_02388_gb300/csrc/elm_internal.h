@@ -28,12 +28,30 @@ struct MacroGeo {
   int32_t nb[4];     // macro across the face opposite local vertex k; -1 = boundary
 };
 
-// FP32 copy of the macro data, used by the FP32 kernel's common path.
+// FP32 copy of the macro data, used by the FP32 kernel.  Each FP64 value x is
+// also kept as a pair (hi, lo) with hi = float(x), lo = float(x - hi), so that
+// the rare start-node frame changes can be computed in double-float
+// arithmetic on the FP32 pipe.
 struct MacroGeo32 {
   float NJinv[9];
   float J[9];
   float v0[3];
   int32_t nb[4];
+  float NJinv_lo[9];
+  float J_lo[9];
+  float v0_lo[3];
+};
+
+// Launch constants in the kernel's working precision, computed once on the
+// host (a per-thread FP64 division or conversion costs dozens of cycles on
+// this GPU's narrow FP64 pipe).
+template <class R>
+struct StepConsts {
+  R h, h2, h6;     // substep, half substep, substep / 6
+  R dt;
+  R invM;          // 1 / 2^(L+1)
+  R Nf;            // 2^L
+  R lo[3], hi[3];  // bounding box
 };
 
 // Everything a kernel launch needs, passed by value.
@@ -54,7 +72,9 @@ struct AdvectArgs {
   int n_sub;
   unsigned* status;
   const int64_t* unique_map;  // storage slot -> unique id
-  const int64_t* owner;       // unique id -> owner storage slot
+  const int64_t* owner_mr;    // unique id -> owner as (macro << 32) | slot in macro
+  StepConsts<float> k32;
+  StepConsts<double> k64;
 };
 
 }  // namespace elm
@@ -73,6 +93,7 @@ struct elm_mesh_s {
   elm::MacroGeo32* d_geo32 = nullptr;
   int64_t* d_unique_map = nullptr;
   int64_t* d_owner = nullptr;
+  int64_t* d_owner_mr = nullptr;     // unique id -> (owner macro << 32) | owner slot in macro
   unsigned* d_status = nullptr;
   // borrowed velocity
   const void* u_old = nullptr;

@@ -209,24 +209,34 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
   if (me->host_only) return ELM_OK;
 
   // Device tables.
+  std::vector<int64_t> owner_mr(me->n_unique);
+  for (int64_t u = 0; u < me->n_unique; ++u) {
+    const int64_t m = me->owner[u] / me->npm;
+    owner_mr[u] = (m << 32) | (me->owner[u] - m * me->npm);
+  }
   auto upload = [&](void** dst, const void* src, size_t bytes) -> bool {
     if (bytes == 0) { *dst = nullptr; return true; }
     if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
     return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
   };
   std::vector<MacroGeo32> g32(nm);
+  auto split = [](double x, float* hi, float* lo) {
+    *hi = float(x);
+    *lo = float(x - double(*hi));
+  };
   for (int64_t m = 0; m < nm; ++m) {
     for (int k = 0; k < 9; ++k) {
-      g32[m].NJinv[k] = float(me->geo[m].NJinv[k]);
-      g32[m].J[k] = float(me->geo[m].J[k]);
+      split(me->geo[m].NJinv[k], &g32[m].NJinv[k], &g32[m].NJinv_lo[k]);
+      split(me->geo[m].J[k], &g32[m].J[k], &g32[m].J_lo[k]);
     }
-    for (int k = 0; k < 3; ++k) g32[m].v0[k] = float(me->geo[m].v0[k]);
+    for (int k = 0; k < 3; ++k) split(me->geo[m].v0[k], &g32[m].v0[k], &g32[m].v0_lo[k]);
     for (int k = 0; k < 4; ++k) g32[m].nb[k] = me->geo[m].nb[k];
   }
   bool ok = upload((void**)&me->d_geo, me->geo.data(), sizeof(MacroGeo) * nm) &&
             upload((void**)&me->d_geo32, g32.data(), sizeof(MacroGeo32) * nm) &&
             upload((void**)&me->d_unique_map, me->unique_map.data(), sizeof(int64_t) * me->n_storage) &&
             upload((void**)&me->d_owner, me->owner.data(), sizeof(int64_t) * me->n_unique) &&
+            upload((void**)&me->d_owner_mr, owner_mr.data(), sizeof(int64_t) * me->n_unique) &&
             cudaMalloc((void**)&me->d_status, sizeof(unsigned)) == cudaSuccess &&
             cudaMemset(me->d_status, 0, sizeof(unsigned)) == cudaSuccess;
   if (!ok) {
