@@ -95,11 +95,13 @@ elm_status elm_mesh_unique_map(elm_mesh mesh, int64_t* host_out);
 elm_status elm_to_storage(elm_mesh mesh, const void* unique_dev, void* storage_dev, int ncomp, void* stream);
 elm_status elm_to_unique(elm_mesh mesh, const void* storage_dev, void* unique_dev, int ncomp, void* stream);
 
-/* Registers the P2 velocity at t_n (u_old) and t_{n+1} (u_new), storage
- * layout [n, dim], mesh precision (Sec. 3 step (ii), Eq. linear
- * interpolation).  u_new == u_old means a steady velocity (no time
- * interpolation).  Both buffers are borrowed until the next call or
- * elm_mesh_destroy; they are read, never copied or written. */
+/* Sets the P2 velocity at t_n (u_old) and t_{n+1} (u_new), storage layout
+ * [n, dim], mesh precision (Sec. 3 step (ii), Eq. linear interpolation).
+ * u_new == u_old means a steady velocity (no time interpolation).  The call
+ * enqueues, on `stream`, a copy of the velocity into the mesh's own
+ * device buffers in a padded 4-component record layout (one vector load per
+ * P2 node in the kernel); the caller's buffers are not used afterwards.
+ * Work on other streams must be ordered after it by the caller. */
 elm_status elm_set_velocity(elm_mesh mesh, const void* u_old_dev, const void* u_new_dev, void* stream);
 
 /* One advection step (Algorithm 1, lines 3-4; Sec. 3 steps (i)-(iii)):

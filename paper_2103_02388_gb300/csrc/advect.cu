@@ -83,6 +83,8 @@ __device__ __forceinline__ double r_floor(double x) { return ::floor(x); }
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return ::fma(a, b, c); }
 __device__ __forceinline__ float r_clamp(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+__device__ __forceinline__ float r_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double r_min(double a, double b) { return ::fmin(a, b); }
 __device__ __forceinline__ double r_clamp(double x, double lo, double hi) { return ::fmin(::fmax(x, lo), hi); }
 
 // ---------------------------------------------------------------------------
@@ -147,11 +149,6 @@ __device__ __forceinline__ int tri3(int k) { return k * (k + 1) * (k + 2) / 6; }
 // row and slab are estimated with the MUFU log2/exp2/rsqrt approximations
 // (cbrt(6 r), (sqrt(8 r + 1) - 1) / 2) and made exact by integer fix-up
 // loops; libm's cbrtf/sqrtf would add FP64 or long FP32 sequences.
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 template <int D>
 __device__ __forceinline__ int tri_root2(int r) {
@@ -161,25 +158,6 @@ __device__ __forceinline__ int tri_root2(int r) {
   while (k > 0 && tri2(k) > r) --k;
   while (tri2(k + 1) <= r) ++k;
   return k;
-}
-
-template <int D>
-__device__ __forceinline__ void unpack(int r, int* p) {
-  if (D == 3) {
-    int p1 = f2i_exact(floor_small(ex2_approx(__log2f(6.0f * i2f_exact(r) + 1.0f) * (1.0f / 3.0f))));
-    p1 = max(p1 - 1, 0);
-    while (p1 > 0 && tri3(p1) > r) --p1;
-    while (tri3(p1 + 1) <= r) ++p1;
-    r -= tri3(p1);
-    const int p2 = tri_root2<D>(r);
-    p[0] = p1;
-    p[1] = p2;
-    p[2] = r - tri2(p2);
-  } else {
-    const int p1 = tri_root2<D>(r);
-    p[0] = p1;
-    p[1] = r - tri2(p1);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -380,6 +358,7 @@ struct Tracer {
   // cell c (integer-valued reals) and fractions f, retracted into the
   // macro's reference simplex N >= q1 >= q2 (>= q3) >= 0.
   __device__ void locate(const R* d, R* c, R* f) {
+    R lmin;
     for (int hop = 0;; ++hop) {
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -395,20 +374,21 @@ struct Tracer {
 #pragma unroll
       for (int k = 1; k < D; ++k) l[k] = (c[k - 1] - c[k]) + (f[k - 1] - f[k]);
       l[D] = c[D - 1] + f[D - 1];
-      int kmin = 0;
-      R lmin = l[0];
+      lmin = l[0];
 #pragma unroll
-      for (int k = 1; k <= D; ++k)
-        if (l[k] < lmin) {
-          lmin = l[k];
-          kmin = k;
-        }
+      for (int k = 1; k <= D; ++k) lmin = r_min(lmin, l[k]);
+      // common case: inside the current macro, clear of its faces
+      if (lmin >= R(sizeof(R) == 4 ? kBand32 : kTol64)) return;
+      int kmin = D;
+#pragma unroll
+      for (int k = D - 1; k >= 0; --k)
+        if (l[k] == lmin) kmin = k;
       bool outside;
       int nb;
       if constexpr (sizeof(R) == 4) {
         outside = lmin < R(-kBand32);
         nb = tab.nb(m, kmin);
-        if (!outside && lmin < R(kBand32) && nb >= 0) {
+        if (!outside && nb >= 0) {
           // tie band at an interior face: decide in FP64 from the exact start node
           const Min64 r64 = bary64_min<D>(geo, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, N, m, float(d[0]),
                                           float(d[1]), D == 3 ? float(d[D - 1]) : 0.0f);
@@ -427,6 +407,7 @@ struct Tracer {
       }
       foreign_frame(nb);
     }
+    if (lmin > R(0)) return;
     if (c[0] < R(0)) { c[0] = R(0); f[0] = R(0); }
     if (c[0] > Nf - R(1)) { c[0] = Nf - R(1); f[0] = R(1); }
 #pragma unroll
@@ -436,8 +417,8 @@ struct Tracer {
     }
   }
 
-  // P2 stencil of the micro simplex holding (c, f): slots within macro m and
-  // basis values.  Per axis a the packed index contributes A_a[o] for the
+  // P2 stencil of the micro simplex holding (c, f): storage slots and basis
+  // values (the macro's base slot is folded into the last axis' table).  Per axis a the packed index contributes A_a[o] for the
   // lattice offset o in {0, 1, 2} of the node from 2c; sorting the axes by
   // descending fraction (ties by axis) orders the Kuhn path c -> c + 1, and
   // each node's offsets along the sorted axes are fixed (alpha >= beta >= gamma).
@@ -445,10 +426,11 @@ struct Tracer {
     int A[D][3];
     R fs[D];
     {
+      const int base = m * npm;  // the macro's first storage slot (storage < 2^31)
       const int c0 = 2 * f2i_exact(c[0]);
       if (D == 3) {
         const int c1 = 2 * f2i_exact(c[1]);
-        const int c2 = 2 * f2i_exact(c[D - 1]);
+        const int c2 = 2 * f2i_exact(c[D - 1]) + base;
         A[0][0] = tri3(c0);
         A[0][1] = A[0][0] + tri2(c0 + 1);
         A[0][2] = A[0][1] + tri2(c0 + 2);
@@ -459,7 +441,7 @@ struct Tracer {
         A[D - 1][1] = c2 + 1;
         A[D - 1][2] = c2 + 2;
       } else {
-        const int c1 = 2 * f2i_exact(c[D - 1]);
+        const int c1 = 2 * f2i_exact(c[D - 1]) + base;
         A[0][0] = tri2(c0);
         A[0][1] = A[0][0] + c0 + 1;
         A[0][2] = A[0][1] + c0 + 2;
@@ -532,31 +514,51 @@ struct Tracer {
   }
 
   // Velocity u~ at x_i + d at backward time `back` (Eq. linear interpolation).
+  // Velocities are packed records (x, y[, z], 0): one vector load per node.
   __device__ void velocity(const R* d, R back, R* k) {
     R c[D], f[D];
     locate(d, c, f);
     int slot[NB];
     R phi[NB];
     stencil(c, f, slot, phi);
-    const R* ub = un + int64_t(m) * npm * D;
 #pragma unroll
     for (int r = 0; r < D; ++r) k[r] = R(0);
 #pragma unroll
-    for (int j = 0; j < NB; ++j)
+    for (int j = 0; j < NB; ++j) {
+      R v[D];
+      load_rec(un, slot[j], v);
 #pragma unroll
-      for (int r = 0; r < D; ++r) k[r] = r_fma(phi[j], __ldg(ub + slot[j] * D + r), k[r]);
+      for (int r = 0; r < D; ++r) k[r] = r_fma(phi[j], v[r], k[r]);
+    }
     if constexpr (!STEADY) {
-      const R* ob = uo + int64_t(m) * npm * D;
       R ko[D];
 #pragma unroll
       for (int r = 0; r < D; ++r) ko[r] = R(0);
 #pragma unroll
-      for (int j = 0; j < NB; ++j)
+      for (int j = 0; j < NB; ++j) {
+        R v[D];
+        load_rec(uo, slot[j], v);
 #pragma unroll
-        for (int r = 0; r < D; ++r) ko[r] = r_fma(phi[j], __ldg(ob + slot[j] * D + r), ko[r]);
+        for (int r = 0; r < D; ++r) ko[r] = r_fma(phi[j], v[r], ko[r]);
+      }
       const R w_old = back / dt, w_new = (dt - back) / dt;
 #pragma unroll
       for (int r = 0; r < D; ++r) k[r] = w_old * ko[r] + w_new * k[r];
+    }
+  }
+
+  // One packed velocity record.
+  __device__ static void load_rec(const R* u, int node, R* v) {
+    if constexpr (sizeof(R) == 4) {
+      const float4 w = __ldg(reinterpret_cast<const float4*>(u) + node);
+      v[0] = w.x;
+      v[1] = w.y;
+      if (D == 3) v[D - 1] = w.z;
+    } else {
+      const double2 w = __ldg(reinterpret_cast<const double2*>(u) + 2 * node);
+      v[0] = w.x;
+      v[1] = w.y;
+      if (D == 3) v[D - 1] = __ldg(u + 4 * int64_t(node) + 2);
     }
   }
 
@@ -566,22 +568,19 @@ struct Tracer {
     int slot[NB];
     R phi[NB];
     stencil(c, f, slot, phi);
-    const R* tb = T + int64_t(m) * npm;
     R v = R(0);
 #pragma unroll
-    for (int j = 0; j < NB; ++j) v = r_fma(phi[j], __ldg(tb + slot[j]), v);
+    for (int j = 0; j < NB; ++j) v = r_fma(phi[j], __ldg(T + slot[j]), v);
     return v;
   }
 };
 
+// 128-thread blocks, 8 resident per SM (64 registers per thread): measured
+// fastest on GB300 for the level-7 FP32 step (occupancy beats the few spills).
 #ifndef ELM_ADVECT_MIN_BLOCKS
-#define ELM_ADVECT_MIN_BLOCKS 1
-#endif
-#ifndef ELM_ADVECT_THREADS
-#define ELM_ADVECT_THREADS 256
+#define ELM_ADVECT_MIN_BLOCKS 8
 #endif
 
-// grid: x = blocks over one macro's slots, y = macro (offset by macro0)
 template <class R>
 __device__ __forceinline__ const StepConsts<R>& consts(const AdvectArgs& a);
 template <>
@@ -589,13 +588,21 @@ __device__ __forceinline__ const StepConsts<float>& consts<float>(const AdvectAr
 template <>
 __device__ __forceinline__ const StepConsts<double>& consts<double>(const AdvectArgs& a) { return a.k64; }
 
+template <int D>
+__device__ __forceinline__ int packed(const int* p) {
+  return D == 3 ? tri3(p[0]) + tri2(p[1]) + p[2] : tri2(p[0]) + p[1];
+}
+
+// One block per work-list chunk: a run of up to blockDim consecutive nodes
+// of one slab p1 of one macro (host-built, so no thread divides or searches
+// for its lattice point beyond one row root).
 template <int D, class R, bool STEADY>
-__global__ void __launch_bounds__(ELM_ADVECT_THREADS, ELM_ADVECT_MIN_BLOCKS)
-    k_advect(AdvectArgs args, Tables<R> tab, int macro0) {
+__global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
+    k_advect(AdvectArgs args, Tables<R> tab, int chunk0) {
   const StepConsts<R>& K = consts<R>(args);
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int4 ck = args.chunks[chunk0 + int(blockIdx.x)];
+  if (int(threadIdx.x) >= ck.w) return;
   const int npm = int(args.npm);
-  if (r >= npm) return;
   Tracer<D, R, STEADY> t;
   t.geo = args.geo;
   t.tab = tab;
@@ -609,24 +616,31 @@ __global__ void __launch_bounds__(ELM_ADVECT_THREADS, ELM_ADVECT_MIN_BLOCKS)
   t.invM = K.invM;
   t.status = args.status;
   // (i) particle creation at the node (interface copies trace their owner)
-  t.m0 = macro0 + int(blockIdx.y);
-  const int64_t slot = int64_t(t.m0) * npm + r;
-  unpack<D>(r, t.p);
-  int r_own = r;
+  t.m0 = ck.x;
+  const int i = ck.z + int(threadIdx.x);  // index within slab p1
+  t.p[0] = ck.y;
+  int in_macro;
+  if (D == 3) {
+    const int p2 = tri_root2<D>(i);
+    t.p[1] = p2;
+    t.p[D - 1] = i - tri2(p2);
+    in_macro = tri3(ck.y) + i;
+  } else {
+    t.p[D - 1] = i;
+    in_macro = tri2(ck.y) + i;
+  }
+  const int64_t slot = int64_t(t.m0) * npm + in_macro;
   {
     const int M = 2 * args.N;
     bool iface = t.p[0] == M || t.p[D - 1] == 0;
 #pragma unroll
     for (int k = 1; k < D; ++k) iface = iface || t.p[k] == t.p[k - 1];
     if (iface) {
-      const int64_t own = args.owner_mr[args.unique_map[slot]];
-      const int om = int(own >> 32);
-      const int orr = int(own & 0xffffffffLL);
-      if (om != t.m0 || orr != r) {
-        t.m0 = om;
-        r_own = orr;
-        unpack<D>(orr, t.p);
-      }
+      const int64_t own = args.owner_mp[args.unique_map[slot]];
+      t.m0 = int(own >> 32);
+      t.p[0] = int(own >> 20) & 1023;
+      t.p[1] = int(own >> 10) & 1023;
+      if (D == 3) t.p[D - 1] = int(own) & 1023;
     }
   }
   {
@@ -640,7 +654,8 @@ __global__ void __launch_bounds__(ELM_ADVECT_THREADS, ELM_ADVECT_MIN_BLOCKS)
     }
   }
   t.home_frame();
-  const R* u_node = t.un + (int64_t(t.m0) * npm + r_own) * D;
+  R u_node[D];
+  Tracer<D, R, STEADY>::load_rec(t.un, t.m0 * npm + packed<D>(t.p), u_node);
   // (ii) backward RK4, n_sub substeps of h = dt / n_sub.  All 4 n_sub stage
   // evaluations run through one loop with a single evaluation site (stage s
   // of a substep sits at d, d - h/2 k, d - h/2 k, d - h k and has weight
@@ -652,7 +667,7 @@ __global__ void __launch_bounds__(ELM_ADVECT_THREADS, ELM_ADVECT_MIN_BLOCKS)
     d[q] = R(0);
     // the first stage sits on the node: the P2 interpolant is the nodal value
     // (steady, or at t_{n+1} where only u^{n+1} has weight)
-    k[q] = __ldg(u_node + q);
+    k[q] = u_node[q];
     acc[q] = k[q];
   }
   bool finite = true;
@@ -685,6 +700,16 @@ __global__ void __launch_bounds__(ELM_ADVECT_THREADS, ELM_ADVECT_MIN_BLOCKS)
   static_cast<R*>(args.T_new)[slot] = v;
 }
 
+// [n, dim] -> packed records [n, 4] (x, y[, z], 0).
+template <class R>
+__global__ void k_pack_velocity(const R* __restrict__ u, R* __restrict__ u4, int64_t n, int dim) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  R w[4] = {R(0), R(0), R(0), R(0)};
+  for (int r = 0; r < dim; ++r) w[r] = u[i * dim + r];
+  for (int r = 0; r < 4; ++r) u4[i * 4 + r] = w[r];
+}
+
 template <class R>
 __global__ void k_gather(const R* __restrict__ in, R* __restrict__ out, const int64_t* __restrict__ idx,
                          int64_t n, int ncomp) {
@@ -697,11 +722,9 @@ __global__ void k_gather(const R* __restrict__ in, R* __restrict__ out, const in
 
 template <int D, class R, bool STEADY>
 cudaError_t launch_drs(const AdvectArgs& a, Tables<R> t, cudaStream_t s) {
-  const int threads = ELM_ADVECT_THREADS;
-  const unsigned bx = unsigned((a.npm + threads - 1) / threads);
-  for (int m0 = 0; m0 < a.n_macros; m0 += 65535) {
-    const unsigned by = unsigned(a.n_macros - m0 < 65535 ? a.n_macros - m0 : 65535);
-    k_advect<D, R, STEADY><<<dim3(bx, by), threads, 0, s>>>(a, t, m0);
+  for (int c0 = 0; c0 < a.n_chunks; c0 += (1 << 30)) {
+    const int nb = a.n_chunks - c0 < (1 << 30) ? a.n_chunks - c0 : (1 << 30);
+    k_advect<D, R, STEADY><<<nb, kAdvectThreads, 0, s>>>(a, t, c0);
   }
   return cudaGetLastError();
 }
@@ -721,6 +744,16 @@ cudaError_t launch_advect(int dim, int precision, const AdvectArgs& a, cudaStrea
   }
   Tables<float> t{a.geo32};
   return dim == 3 ? launch_dr<3, float>(a, t, s) : launch_dr<2, float>(a, t, s);
+}
+
+cudaError_t launch_pack_velocity(int precision, int dim, const void* u, void* u4, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const unsigned blocks = unsigned((n + 255) / 256);
+  if (precision == ELM_FP64)
+    k_pack_velocity<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(u), static_cast<double*>(u4), n, dim);
+  else
+    k_pack_velocity<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(u), static_cast<float*>(u4), n, dim);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gather(int precision, const void* in, void* out, const int64_t* idx, int64_t n, int ncomp,

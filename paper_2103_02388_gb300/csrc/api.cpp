@@ -38,11 +38,16 @@ void free_tables(elm_mesh_s* me) {
   cudaFree(me->d_geo32);
   cudaFree(me->d_unique_map);
   cudaFree(me->d_owner);
-  cudaFree(me->d_owner_mr);
+  cudaFree(me->d_owner_mp);
+  cudaFree(me->d_chunks);
+  cudaFree(me->d_u4[0]);
+  cudaFree(me->d_u4[1]);
   cudaFree(me->d_status);
   me->d_geo = nullptr;
   me->d_geo32 = nullptr;
-  me->d_unique_map = me->d_owner = me->d_owner_mr = nullptr;
+  me->d_unique_map = me->d_owner = me->d_owner_mp = nullptr;
+  me->d_chunks = nullptr;
+  me->d_u4[0] = me->d_u4[1] = nullptr;
   me->d_status = nullptr;
 }
 
@@ -70,6 +75,13 @@ elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz
   precision &= ~ELM_HOST_ONLY;
   if (precision != ELM_FP64 && precision != ELM_FP32)
     return fail(ELM_ERR_ARG, "elm_mesh_create: precision must be ELM_FP64 or ELM_FP32");
+  {
+    // the kernels index storage slots with 32-bit integers (int32 storage)
+    const int64_t M = int64_t(2) << level;
+    const int64_t npm = dim == 3 ? (M + 1) * (M + 2) * (M + 3) / 6 : (M + 1) * (M + 2) / 2;
+    if (n_macros * npm >= (int64_t(1) << 31))
+      return fail(ELM_ERR_ARG, "elm_mesh_create: more than 2^31 - 1 storage nodes");
+  }
   elm_mesh_s* me = new (std::nothrow) elm_mesh_s();
   if (!me) return fail(ELM_ERR_ARG, "elm_mesh_create: out of host memory");
   me->host_only = host_only;
@@ -166,12 +178,18 @@ elm_status elm_to_unique(elm_mesh me, const void* storage_dev, void* unique_dev,
 }
 
 elm_status elm_set_velocity(elm_mesh me, const void* u_old_dev, const void* u_new_dev, void* stream) {
-  (void)stream;
   if (!me) return fail(ELM_ERR_ARG, "elm_set_velocity: null mesh");
   if (!u_old_dev || !u_new_dev) return fail(ELM_ERR_ARG, "elm_set_velocity: null velocity");
   if (me->host_only) return fail(ELM_ERR_STATE, "elm_set_velocity: host-only mesh");
-  me->u_old = u_old_dev;
-  me->u_new = u_new_dev;
+  DeviceGuard g(me->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool steady = u_old_dev == u_new_dev;
+  cudaError_t e = elm::launch_pack_velocity(me->precision, me->dim, u_new_dev, me->d_u4[1], me->n_storage, s);
+  if (e == cudaSuccess && !steady)
+    e = elm::launch_pack_velocity(me->precision, me->dim, u_old_dev, me->d_u4[0], me->n_storage, s);
+  if (e != cudaSuccess) return cuda_fail(e, "elm_set_velocity");
+  me->steady = steady;
+  me->have_velocity = true;
   return ELM_OK;
 }
 
@@ -181,7 +199,7 @@ elm_status elm_advect(elm_mesh me, const void* T_old_dev, void* T_new_dev, doubl
   if (!std::isfinite(dt) || dt < 0.0) return fail(ELM_ERR_ARG, "elm_advect: dt must be finite and >= 0");
   if (n_sub < 1 || n_sub > 64) return fail(ELM_ERR_ARG, "elm_advect: n_sub must be in 1..64");
   if (me->host_only) return fail(ELM_ERR_STATE, "elm_advect: host-only mesh");
-  if (!me->u_old || !me->u_new) return fail(ELM_ERR_STATE, "elm_advect: elm_set_velocity has not been called");
+  if (!me->have_velocity) return fail(ELM_ERR_STATE, "elm_advect: elm_set_velocity has not been called");
   if (ranges_overlap(T_old_dev, T_new_dev, elem_size(me) * size_t(me->n_storage)))
     return fail(ELM_ERR_ARG, "elm_advect: T_old and T_new overlap");
   DeviceGuard g(me->device);
@@ -197,9 +215,9 @@ elm_status elm_advect(elm_mesh me, const void* T_old_dev, void* T_new_dev, doubl
     a.lo[r] = me->lo[r];
     a.hi[r] = me->hi[r];
   }
-  a.u_old = me->u_old;
-  a.u_new = me->u_new;
-  a.steady = me->u_old == me->u_new;
+  a.u_old = me->steady ? me->d_u4[1] : me->d_u4[0];
+  a.u_new = me->d_u4[1];
+  a.steady = me->steady;
   a.T_old = T_old_dev;
   a.T_new = T_new_dev;
   a.dt = dt;
@@ -218,7 +236,9 @@ elm_status elm_advect(elm_mesh me, const void* T_old_dev, void* T_new_dev, doubl
       a.k32.hi[r] = float(me->hi[r]);
     }
   }
-  a.owner_mr = me->d_owner_mr;
+  a.owner_mp = me->d_owner_mp;
+  a.chunks = me->d_chunks;
+  a.n_chunks = int(me->n_chunks);
   cudaError_t e = elm::launch_advect(me->dim, me->precision, a, s);
   if (e != cudaSuccess) return cuda_fail(e, "elm_advect");
   return ELM_OK;

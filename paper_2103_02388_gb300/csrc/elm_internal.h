@@ -63,7 +63,7 @@ struct AdvectArgs {
   int64_t npm;             // storage nodes per macro
   int64_t n_storage;
   double lo[3], hi[3];     // bounding box (domain clamp)
-  const void* u_old;
+  const void* u_old;      // packed velocity records [n, 4] (x, y[, z], 0)
   const void* u_new;
   int steady;              // u_old == u_new
   const void* T_old;
@@ -72,7 +72,9 @@ struct AdvectArgs {
   int n_sub;
   unsigned* status;
   const int64_t* unique_map;  // storage slot -> unique id
-  const int64_t* owner_mr;    // unique id -> owner as (macro << 32) | slot in macro
+  const int64_t* owner_mp;    // unique id -> owner (macro << 32 | p1 << 20 | p2 << 10 | p3)
+  const int4* chunks;         // (macro, p1, first index in slab, count) per thread block
+  int n_chunks;
   StepConsts<float> k32;
   StepConsts<double> k64;
 };
@@ -93,11 +95,13 @@ struct elm_mesh_s {
   elm::MacroGeo32* d_geo32 = nullptr;
   int64_t* d_unique_map = nullptr;
   int64_t* d_owner = nullptr;
-  int64_t* d_owner_mr = nullptr;     // unique id -> (owner macro << 32) | owner slot in macro
+  int64_t* d_owner_mp = nullptr;     // unique id -> owner (macro << 32 | p1 << 20 | p2 << 10 | p3)
+  int4* d_chunks = nullptr;          // work list: one block-sized run of a slab each
+  int64_t n_chunks = 0;
+  void* d_u4[2] = {nullptr, nullptr};  // packed velocity records u_old, u_new
+  bool have_velocity = false;
+  bool steady = true;
   unsigned* d_status = nullptr;
-  // borrowed velocity
-  const void* u_old = nullptr;
-  const void* u_new = nullptr;
 };
 
 namespace elm {
@@ -121,5 +125,9 @@ inline int64_t nodes_per_macro(int dim, int M) {
 cudaError_t launch_advect(int dim, int precision, const AdvectArgs& a, cudaStream_t s);
 cudaError_t launch_gather(int precision, const void* in, void* out, const int64_t* idx, int64_t n,
                           int ncomp, cudaStream_t s);
+cudaError_t launch_pack_velocity(int precision, int dim, const void* u, void* u4, int64_t n, cudaStream_t s);
+
+// Threads per block of the advection kernel, and so the work-list chunk size.
+constexpr int kAdvectThreads = 128;
 
 }  // namespace elm

@@ -209,11 +209,34 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
   if (me->host_only) return ELM_OK;
 
   // Device tables.
-  std::vector<int64_t> owner_mr(me->n_unique);
+  // Owner lattice points, packed (macro << 32 | p1 << 20 | p2 << 10 | p3).
+  std::vector<int64_t> slot_p(me->npm);
+  {
+    int64_t k = 0;
+    if (d == 2) {
+      for (int p1 = 0; p1 <= M; ++p1)
+        for (int p2 = 0; p2 <= p1; ++p2) slot_p[k++] = (int64_t(p1) << 20) | (int64_t(p2) << 10);
+    } else {
+      for (int p1 = 0; p1 <= M; ++p1)
+        for (int p2 = 0; p2 <= p1; ++p2)
+          for (int p3 = 0; p3 <= p2; ++p3) slot_p[k++] = (int64_t(p1) << 20) | (int64_t(p2) << 10) | p3;
+    }
+  }
+  std::vector<int64_t> owner_mp(me->n_unique);
   for (int64_t u = 0; u < me->n_unique; ++u) {
     const int64_t m = me->owner[u] / me->npm;
-    owner_mr[u] = (m << 32) | (me->owner[u] - m * me->npm);
+    owner_mp[u] = (m << 32) | slot_p[me->owner[u] - m * me->npm];
   }
+  // Work list: each slab p1 of each macro split into runs of kAdvectThreads
+  // nodes (slab p1 holds (p1+1)(p1+2)/2 nodes in 3D, p1+1 in 2D).
+  std::vector<int4> chunks;
+  for (int64_t m = 0; m < nm; ++m)
+    for (int p1 = 0; p1 <= M; ++p1) {
+      const int len = d == 3 ? (p1 + 1) * (p1 + 2) / 2 : p1 + 1;
+      for (int i0 = 0; i0 < len; i0 += kAdvectThreads)
+        chunks.push_back(make_int4(int(m), p1, i0, std::min(kAdvectThreads, len - i0)));
+    }
+  me->n_chunks = int64_t(chunks.size());
   auto upload = [&](void** dst, const void* src, size_t bytes) -> bool {
     if (bytes == 0) { *dst = nullptr; return true; }
     if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
@@ -236,7 +259,10 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
             upload((void**)&me->d_geo32, g32.data(), sizeof(MacroGeo32) * nm) &&
             upload((void**)&me->d_unique_map, me->unique_map.data(), sizeof(int64_t) * me->n_storage) &&
             upload((void**)&me->d_owner, me->owner.data(), sizeof(int64_t) * me->n_unique) &&
-            upload((void**)&me->d_owner_mr, owner_mr.data(), sizeof(int64_t) * me->n_unique) &&
+            upload((void**)&me->d_owner_mp, owner_mp.data(), sizeof(int64_t) * me->n_unique) &&
+            upload((void**)&me->d_chunks, chunks.data(), sizeof(int4) * chunks.size()) &&
+            cudaMalloc(&me->d_u4[0], size_t(me->n_storage) * 4 * (precision == ELM_FP64 ? 8 : 4)) == cudaSuccess &&
+            cudaMalloc(&me->d_u4[1], size_t(me->n_storage) * 4 * (precision == ELM_FP64 ? 8 : 4)) == cudaSuccess &&
             cudaMalloc((void**)&me->d_status, sizeof(unsigned)) == cudaSuccess &&
             cudaMemset(me->d_status, 0, sizeof(unsigned)) == cudaSuccess;
   if (!ok) {
