@@ -8,7 +8,7 @@
  * macro triangles / tetrahedra refined uniformly L times (Sec. 2.1), the
  * departure point X(x_i, t_{n+1}, t_n) of Eq. (departure point) by classic
  * RK4 backwards in time through the P2 velocity, linearly interpolated in
- * time (Eq. linear interpolation), then T^{n+1}_i = T^n_h(X_i) (Sec. 3,
+ * time (Eq. linear interpolation), then T^{n+1}_i = T^n_h(X_i) (Sec. 2.3.1,
  * step (iii)).
  *
  * Conventions shared by every call:
@@ -59,7 +59,7 @@ enum { ELM_FP64 = 0, ELM_FP32 = 1 };
 enum { ELM_HOST_ONLY = 0x100 };
 
 /* Builds the refined mesh (Sec. 2.1: coarse mesh T_0 refined uniformly after
- * Bey; Sec. 3 "Grid data structure": one DoF owner per interface node).
+ * Bey; Sec. 2.3.1, grid data structure: one DoF owner per interface node).
  *  dim            2 (triangles) or 3 (tetrahedra).
  *  vertex_xyz     host, [n_vertices, dim] doubles.
  *  macro_vertices host, [n_macros, dim+1] vertex ids in [0, n_vertices).  The
@@ -96,7 +96,7 @@ elm_status elm_to_storage(elm_mesh mesh, const void* unique_dev, void* storage_d
 elm_status elm_to_unique(elm_mesh mesh, const void* storage_dev, void* unique_dev, int ncomp, void* stream);
 
 /* Sets the P2 velocity at t_n (u_old) and t_{n+1} (u_new), storage layout
- * [n, dim], mesh precision (Sec. 3 step (ii), Eq. linear interpolation).
+ * [n, dim], mesh precision (Sec. 2.3.1 step (ii), Eq. linear interpolation).
  * u_new == u_old means a steady velocity (no time interpolation).  The call
  * enqueues, on `stream`, a copy of the velocity into the mesh's own
  * device buffers in a padded 4-component record layout (one vector load per
@@ -104,7 +104,7 @@ elm_status elm_to_unique(elm_mesh mesh, const void* storage_dev, void* unique_de
  * Work on other streams must be ordered after it by the caller. */
 elm_status elm_set_velocity(elm_mesh mesh, const void* u_old_dev, const void* u_new_dev, void* stream);
 
-/* One advection step (Algorithm 1, lines 3-4; Sec. 3 steps (i)-(iii)):
+/* One advection step (Algorithm 1, lines 3-4; Sec. 2.3.1 steps (i)-(iii)):
  * T_new[i] = T_old_h(X_i), X_i traced back over dt from node i with n_sub
  * equal RK4 substeps.  T_old and T_new are [n] in storage layout and must
  * not overlap.  Stage and departure points outside the domain are clamped

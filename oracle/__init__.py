@@ -2,10 +2,10 @@
 
 A plain FP64 C++ restatement (``elm_oracle.cpp``) of the advection step of
 Kohl et al., "A massively parallel Eulerian-Lagrangian method for
-advection-dominated transport in viscous fluids" (arXiv 2103.02388): Sec. 3
+advection-dominated transport in viscous fluids" (arXiv 2103.02388): Sec. 2.3.1
 steps (i)-(iii), Eq. (departure point) integrated by classic RK4, the time
-interpolation of Eq. (linear interpolation), the field evaluation of Sec. 3
-and the mass-matrix metrics of Sec. 4.1.
+interpolation of Eq. (linear interpolation), the field evaluation of Sec. 2.3.2
+and the mass-matrix metrics of Sec. 3.1.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
 legs of ``bench.py`` may import this package.  It shares no code with the CUDA
@@ -188,7 +188,7 @@ class OracleMesh:
                                      float(dt), int(n_sub))
         return out
 
-    # -- metrics (Sec. 4.1) ---------------------------------------------------
+    # -- metrics (Sec. 3.1) ---------------------------------------------------
     def mass_product(self, a, b=None):
         """a^T M b with the P2 mass matrix M."""
         a = _f64(a).reshape(self.n_nodes, 1)
@@ -198,7 +198,7 @@ class OracleMesh:
         return float(out[0])
 
     def metrics(self, c_computed, c_exact, c_initial):
-        """H0 error, var, E_peak and the relative mass difference of Sec. 4.1."""
+        """H0 error, var, E_peak and the relative mass difference of Sec. 3.1."""
         c_computed = _f64(c_computed)
         e = _f64(c_exact) - c_computed
         ones = np.ones(self.n_nodes)

@@ -18,16 +18,16 @@
 //     between and its integer barycentric weights, so nodes shared by several
 //     macros are one unknown.
 //   * Eq. (characteristic curves) / Eq. (departure point): X(x, t_{n+1}, t_n)
-//     integrated backwards with classic RK4 (Sec. 4.1 "Test setup"), with
+//     integrated backwards with classic RK4 (Sec. 3.1 "Test setup"), with
 //     n_sub equal substeps.
 //   * Eq. (linear interpolation): the velocity at a stage time is the linear
 //     time interpolant of u^n_h and u^{n+1}_h.
-//   * Sec. 3 "Field evaluation": locate the macro (here: brute force over all
+//   * Sec. 2.3.2, field evaluation: locate the macro (here: brute force over all
 //     macros, keeping the one with the largest minimum barycentric), locate the
 //     micro element in O(1) (floor + sort of the fractional parts), pull back to
 //     the micro element (solve its barycentric system) and sum the P2 basis.
 //   * Step (iii): T^{n+1}_i = c^n_h(X_i) (kappa = 0, no diffusion).
-//   * Sec. 4.1: the error metrics need e^T M e with the P2 mass matrix M,
+//   * Sec. 3.1: the error metrics need e^T M e with the P2 mass matrix M,
 //     assembled here element by element from exact barycentric-monomial
 //     integrals.
 //   * Eq. (departure point), differentiated: forward-mode (dual number)
@@ -228,7 +228,7 @@ Mesh* build_mesh(int d, int64_t nv, const double* xyz, int64_t nm, const int64_t
 }
 
 // ---------------------------------------------------------------------------
-// Field evaluation (Sec. 3, "Field evaluation").
+// Field evaluation (Sec. 2.3.2, field evaluation).
 // ---------------------------------------------------------------------------
 
 struct Located {
@@ -415,7 +415,7 @@ void parallel_for(int64_t begin, int64_t end, int nthreads, F&& f) {
 }
 
 // ---------------------------------------------------------------------------
-// P2 mass matrix (Sec. 4.1 metrics), exact via barycentric monomial integrals:
+// P2 mass matrix (Sec. 3.1 metrics), exact via barycentric monomial integrals:
 // int_T lam_0^a0 ... lam_d^ad = d! |T| a0! ... ad! / (d + sum a)!.
 // ---------------------------------------------------------------------------
 
@@ -640,7 +640,7 @@ void orc_advect_transpose(void* h, const double* u_old, const double* u_new, con
   }
 }
 
-// Mass-matrix products for the metrics of Sec. 4.1: out[k] = a_k^T M b_k for
+// Mass-matrix products for the metrics of Sec. 3.1: out[k] = a_k^T M b_k for
 // the nvec column pairs (a, b given node-major [n_nodes, nvec]).
 void orc_mass_products(void* h, int nvec, const double* a, const double* b, double* out) {
   Mesh* me = static_cast<Mesh*>(h);

@@ -1,4 +1,4 @@
-// advect.cu -- the MMOC advection step on sm_103a (arXiv 2103.02388, Sec. 3
+// advect.cu -- the MMOC advection step on sm_103a (arXiv 2103.02388, Sec. 2.3.1
 // steps (i)-(iii), Eq. departure point, Eq. linear interpolation,
 // Algorithm 1 lines 3-4).
 //
@@ -10,7 +10,7 @@
 // a macro interface is stored once per macro holding it; the thread of every
 // copy traces the owner copy (same macro frame, same instructions), so all
 // copies receive bitwise the same value and no synchronisation pass is needed
-// (the single-owner rule of Sec. 3 "Grid data structure").
+// (the single-owner rule of Sec. 2.3.1, grid data structure).
 //
 // Point representation.  A point is kept as an offset d from its start node
 // x_i, and its level-L lattice coordinate in the current macro m as
@@ -22,7 +22,7 @@
 // frame: in FP64 for the FP64 kernel, in double-float arithmetic on the FP32
 // pipe for the FP32 kernel.
 //
-// Field evaluation (Sec. 3 "Field evaluation"):
+// Field evaluation (Sec. 2.3.2, field evaluation):
 //   macro   -- barycentrics l = (N - q1, q1 - q2, q2 - q3, q3) in lattice
 //              units; if min l < -tol the walk hops across the face opposite
 //              the most negative one (at most kMaxHops hops);

@@ -1,5 +1,5 @@
 // mesh.cpp -- host construction of the block-structured P2 mesh (Sec. 2.1 and
-// Sec. 3 "Grid data structure" of arXiv 2103.02388): macro affine maps, face
+// Sec. 2.3.1, grid data structure of arXiv 2103.02388): macro affine maps, face
 // neighbours, storage layout and the owner of every interface node.
 #include <algorithm>
 #include <array>

@@ -8,7 +8,7 @@ that both the CUDA library and the CPU oracle can take their inputs from it
 without sharing any of the method.
 
 The workloads follow the paper's benchmarks where they are analytic
-(Sec. 4.2 circular advection, Table 1 and Table 2), and otherwise the
+(Sec. 3.2 circular advection, Table 1 and Table 2), and otherwise the
 synthetic recipes of the GB300 benchmark configurations:
 
 * rotation in the unit square on 2 macro triangles, Gaussian cone;
@@ -135,7 +135,7 @@ def cellular_flow(x):
 
 
 def swirl_3d(x, t: float, period: float = 1.5):
-    """The time-dependent swirling flow of Sec. 4.3 at time t."""
+    """The time-dependent swirling flow of Sec. 3.3 at time t."""
     x = np.asarray(x, dtype=np.float64)
     g = np.cos(np.pi * t / period)
     s = lambda k, a: np.sin(k * np.pi * x[:, a])  # noqa: E731
@@ -200,21 +200,21 @@ def slotted_sphere(x, centre=(0.35, 0.5, 0.5), radius: float = 0.15, slot_half: 
 
 
 def hill(x, centre=(0.25, 0.5), r0: float = 0.15):
-    """The smooth hill of Sec. 4.2: (1 + cos(pi r)) / 4 for r = |x - c| / r0 <= 1."""
+    """The smooth hill of Sec. 3.2: (1 + cos(pi r)) / 4 for r = |x - c| / r0 <= 1."""
     x = np.asarray(x, dtype=np.float64)
     r = np.sqrt(((x - np.asarray(centre)) ** 2).sum(axis=1)) / r0
     return np.where(r <= 1.0, 0.25 * (1.0 + np.cos(np.pi * np.minimum(r, 1.0))), 0.0)
 
 
 def cone(x, centre=(0.5, 0.25), r0: float = 0.15):
-    """The cone of Sec. 4.2: 1 - r for r = |x - c| / r0 <= 1."""
+    """The cone of Sec. 3.2: 1 - r for r = |x - c| / r0 <= 1."""
     x = np.asarray(x, dtype=np.float64)
     r = np.sqrt(((x - np.asarray(centre)) ** 2).sum(axis=1)) / r0
     return np.where(r <= 1.0, 1.0 - r, 0.0)
 
 
 def slotted_cylinder(x, centre=(0.5, 0.75), r0: float = 0.15):
-    """The slotted cylinder of Sec. 4.2 (slot of half width 0.025 below y = 0.85)."""
+    """The slotted cylinder of Sec. 3.2 (slot of half width 0.025 below y = 0.85)."""
     x = np.asarray(x, dtype=np.float64)
     r = np.sqrt(((x - np.asarray(centre)) ** 2).sum(axis=1)) / r0
     keep = (np.abs(x[:, 0] - centre[0]) >= 0.025) | (x[:, 1] >= 0.85)

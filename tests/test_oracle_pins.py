@@ -92,7 +92,7 @@ def test_micro_volumes_partition_domain():
 
 
 # ---------------------------------------------------------------------------
-# Point location (Sec. 3, "Field evaluation") against brute force.
+# Point location (Sec. 2.3.2, field evaluation) against brute force.
 # ---------------------------------------------------------------------------
 
 
@@ -289,7 +289,7 @@ def test_time_interpolation_direction():
 
 
 # ---------------------------------------------------------------------------
-# Mass matrix (metrics of Sec. 4.1) and the transpose of the interpolation.
+# Mass matrix (metrics of Sec. 3.1) and the transpose of the interpolation.
 # ---------------------------------------------------------------------------
 
 
