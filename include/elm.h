@@ -112,6 +112,27 @@ elm_status elm_set_velocity(elm_mesh mesh, const void* u_old_dev, const void* u_
 elm_status elm_advect(elm_mesh mesh, const void* T_old_dev, void* T_new_dev, double dt, int n_sub,
                       void* stream);
 
+/* The advection step of elm_advect for callers that cannot allocate device
+ * memory where they advect (for example an application whose device memory
+ * is handed out by its own pool, or a time-critical loop that cannot take the
+ * implicit device synchronisation of cudaMalloc / cudaFree).  The paper has no
+ * counterpart: this entry point changes only where the working copy of the
+ * velocity lives.  It allocates and frees nothing.
+ *  u_old_dev, u_new_dev  the caller's velocity, [n, dim] row-major in the mesh
+ *                        precision (equal pointers: steady velocity); packed on
+ *                        `stream` into a fixed scratch array inside the library
+ *                        (32 MiB of device memory held by every GPU that loads
+ *                        the library until exit), then read by the step.
+ *  T_old_dev, T_new_dev, dt, n_sub, stream  as for elm_advect.
+ * elm_set_velocity is not needed and the mesh's own velocity is untouched.
+ * Limit: meshes of at most 524288 (2^19) storage nodes; larger meshes return
+ * ELM_ERR_ARG.  The first call on a device looks up the scratch array's device
+ * address (with that device current); make that first call before any stream
+ * capture.  Every call shares the one scratch array, so calls that overlap on
+ * the GPU (other streams, other threads) race; order them. */
+elm_status elm_advect_noalloc(elm_mesh mesh, const void* u_old_dev, const void* u_new_dev, const void* T_old_dev,
+                              void* T_new_dev, double dt, int n_sub, void* stream);
+
 /* Synchronises `stream`, returns the first device-side condition raised by
  * work on this mesh since the previous call (ELM_ERR_WALK_LIMIT or
  * ELM_ERR_NONFINITE), else ELM_OK, and clears the flags. */

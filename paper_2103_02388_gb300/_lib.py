@@ -26,6 +26,7 @@ SIGNATURES = [
     ("elm_to_unique", _I, [_P, _P, _P, _I, _P]),
     ("elm_set_velocity", _I, [_P, _P, _P, _P]),
     ("elm_advect", _I, [_P, _P, _P, _D, _I, _P]),
+    ("elm_advect_noalloc", _I, [_P, _P, _P, _P, _P, _D, _I, _P]),
     ("elm_get_status", _I, [_P, _P]),
     ("elm_last_error", ctypes.c_char_p, []),
 ]

@@ -59,6 +59,10 @@ bool ranges_overlap(const void* a, const void* b, size_t bytes) {
 
 }  // namespace
 
+namespace elm {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace elm
+
 extern "C" {
 
 elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz, int64_t n_macros,

@@ -106,6 +106,9 @@ struct elm_mesh_s {
 
 namespace elm {
 
+// Sets the thread-local message returned by elm_last_error (api.cpp).
+void set_last_error(const std::string& msg);
+
 // Host mesh construction (mesh.cpp).
 elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const int64_t* mv,
                       int level, int precision, elm_mesh_s* me, std::string* err);
