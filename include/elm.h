@@ -39,6 +39,7 @@ extern "C" {
 #endif
 
 typedef struct elm_mesh_s* elm_mesh;
+typedef struct elm_batch_s* elm_batch;
 
 typedef enum {
   ELM_OK = 0,
@@ -137,6 +138,32 @@ elm_status elm_advect_noalloc(elm_mesh mesh, const void* u_old_dev, const void* 
  * work on this mesh since the previous call (ELM_ERR_WALK_LIMIT or
  * ELM_ERR_NONFINITE), else ELM_OK, and clears the flags. */
 elm_status elm_get_status(elm_mesh mesh, void* stream);
+
+/* ---- Batched form: many independent advection instances in one launch ----
+ * Each instance is a mesh with its own level, dimension, velocity
+ * (elm_set_velocity on that mesh), dt and n_sub; every instance performs the
+ * step of elm_advect (Algorithm 1, lines 3-4).  One persistent kernel takes
+ * (instance, chunk) items from a shared work list, so small and large
+ * instances share the GPU in a single launch.  The paper has no batched
+ * form; it traces one field per run.
+ *
+ * elm_batch_create: count in 1..128 meshes, all of one precision and device,
+ * borrowed (they must outlive the batch).  blocks_per_sm sets the persistent
+ * grid (resident blocks per SM; 0 = default 6); the autotuner picks it.
+ * Allocates the batch's small device tables. */
+elm_status elm_batch_create(const elm_mesh* meshes, int count, int blocks_per_sm, elm_batch* out);
+elm_status elm_batch_destroy(elm_batch batch);
+/* Number of (instance, chunk) work items of the batch. */
+int64_t elm_batch_num_items(elm_batch batch);
+/* One step of every instance k: T_new[k] = advect(T_old[k], dt[k], n_sub[k]).
+ * T_old, T_new, dt, n_sub are host arrays of `count` entries (device
+ * pointers in storage layout, mesh precision).  Their values are copied into
+ * the launch's parameters, so the call can be captured in a CUDA graph and
+ * replayed with the same pointers.  Zeroes a device counter and launches
+ * one kernel on `stream`; allocates nothing.  Each instance's device flags
+ * are reported by elm_get_status on its mesh. */
+elm_status elm_batch_advect(elm_batch batch, const void* const* T_old, void* const* T_new, const double* dt,
+                            const int* n_sub, void* stream);
 
 /* Thread-local description of the last error returned on this thread. */
 const char* elm_last_error(void);

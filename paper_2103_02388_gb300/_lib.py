@@ -28,6 +28,10 @@ SIGNATURES = [
     ("elm_advect", _I, [_P, _P, _P, _D, _I, _P]),
     ("elm_advect_noalloc", _I, [_P, _P, _P, _P, _P, _D, _I, _P]),
     ("elm_get_status", _I, [_P, _P]),
+    ("elm_batch_create", _I, [_P, _I, _I, ctypes.POINTER(_P)]),
+    ("elm_batch_destroy", _I, [_P]),
+    ("elm_batch_num_items", _I64, [_P]),
+    ("elm_batch_advect", _I, [_P, _P, _P, _P, _P, _P]),
     ("elm_last_error", ctypes.c_char_p, []),
 ]
 

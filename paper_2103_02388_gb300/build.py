@@ -17,7 +17,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["advect.cu", "noalloc.cu"]
-CPP_SOURCES = ["mesh.cpp", "api.cpp"]
+CPP_SOURCES = ["mesh.cpp", "api.cpp", "batch.cpp"]
 HEADERS = ["elm_internal.h"]
 
 

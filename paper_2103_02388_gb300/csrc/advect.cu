@@ -593,31 +593,44 @@ __device__ __forceinline__ int packed(const int* p) {
   return D == 3 ? tri3(p[0]) + tri2(p[1]) + p[2] : tri2(p[0]) + p[1];
 }
 
-// One block per work-list chunk: a run of up to blockDim consecutive nodes
-// of one slab p1 of one macro (host-built, so no thread divides or searches
-// for its lattice point beyond one row root).
+// Everything one node's step needs (one mesh instance, one call).
+template <class R>
+struct NodeJob {
+  const MacroGeo* geo;
+  const R* un;          // packed velocity records, u^{n+1}
+  const R* uo;          // packed velocity records, u^n
+  const R* T_old;
+  R* T_new;
+  unsigned* status;
+  const int64_t* unique_map;
+  const int64_t* owner_mp;
+  StepConsts<R> K;
+  int N;
+  int npm;
+  int n_sub;
+};
+
+// One node: particle creation (i), backward RK4 (ii), T evaluation (iii).
+// The node is entry `tid` of chunk ck = (macro, slab p1, first index, count).
 template <int D, class R, bool STEADY>
-__global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
-    k_advect(AdvectArgs args, Tables<R> tab, int chunk0) {
-  const StepConsts<R>& K = consts<R>(args);
-  const int4 ck = args.chunks[chunk0 + int(blockIdx.x)];
-  if (int(threadIdx.x) >= ck.w) return;
-  const int npm = int(args.npm);
+__device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab, int4 ck, int tid) {
+  const StepConsts<R>& K = job.K;
+  const int npm = job.npm;
   Tracer<D, R, STEADY> t;
-  t.geo = args.geo;
+  t.geo = job.geo;
   t.tab = tab;
-  t.N = args.N;
+  t.N = job.N;
   t.npm = npm;
-  t.un = static_cast<const R*>(args.u_new);
-  t.uo = static_cast<const R*>(args.u_old);
-  t.T = static_cast<const R*>(args.T_old);
+  t.un = job.un;
+  t.uo = job.uo;
+  t.T = job.T_old;
   t.dt = K.dt;
   t.Nf = K.Nf;
   t.invM = K.invM;
-  t.status = args.status;
+  t.status = job.status;
   // (i) particle creation at the node (interface copies trace their owner)
   t.m0 = ck.x;
-  const int i = ck.z + int(threadIdx.x);  // index within slab p1
+  const int i = ck.z + tid;  // index within slab p1
   t.p[0] = ck.y;
   int in_macro;
   if (D == 3) {
@@ -631,12 +644,12 @@ __global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
   }
   const int64_t slot = int64_t(t.m0) * npm + in_macro;
   {
-    const int M = 2 * args.N;
+    const int M = 2 * job.N;
     bool iface = t.p[0] == M || t.p[D - 1] == 0;
 #pragma unroll
     for (int k = 1; k < D; ++k) iface = iface || t.p[k] == t.p[k - 1];
     if (iface) {
-      const int64_t own = args.owner_mp[args.unique_map[slot]];
+      const int64_t own = job.owner_mp[job.unique_map[slot]];
       t.m0 = int(own >> 32);
       t.p[0] = int(own >> 20) & 1023;
       t.p[1] = int(own >> 10) & 1023;
@@ -671,7 +684,7 @@ __global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
     acc[q] = k[q];
   }
   bool finite = true;
-  const int n_eval = 4 * args.n_sub;
+  const int n_eval = 4 * job.n_sub;
 #pragma unroll 1
   for (int e = 1; e < n_eval; ++e) {
     const int s = e & 3;
@@ -696,8 +709,86 @@ __global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
   // (iii) temperature at the departure point
   const R v = t.scalar(d);
   finite = finite && isfinite(v);
-  if (!finite) atomicOr(args.status, kFlagNonFinite);
-  static_cast<R*>(args.T_new)[slot] = v;
+  if (!finite) atomicOr(job.status, kFlagNonFinite);
+  job.T_new[slot] = v;
+}
+
+
+// One block per work-list chunk: a run of up to blockDim consecutive nodes
+// of one slab p1 of one macro (host-built, so no thread divides or searches
+// for its lattice point beyond one row root).
+template <int D, class R, bool STEADY>
+__global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
+    k_advect(AdvectArgs args, Tables<R> tab, int chunk0) {
+  const int4 ck = args.chunks[chunk0 + int(blockIdx.x)];
+  if (int(threadIdx.x) >= ck.w) return;
+  const NodeJob<R> job{args.geo,
+                       static_cast<const R*>(args.u_new),
+                       static_cast<const R*>(args.u_old),
+                       static_cast<const R*>(args.T_old),
+                       static_cast<R*>(args.T_new),
+                       args.status,
+                       args.unique_map,
+                       args.owner_mp,
+                       consts<R>(args),
+                       args.N,
+                       int(args.npm),
+                       args.n_sub};
+  advect_node<D, R, STEADY>(job, tab, ck, int(threadIdx.x));
+}
+
+// Persistent batched kernel: each block repeatedly takes the next (instance,
+// chunk) item from the work list and advects that chunk's nodes with the
+// instance's tables and this call's constants.  Dimension and steadiness are
+// per instance and uniform within a block.
+template <class R>
+__device__ __forceinline__ Tables<R> tables_of(const BatchStatic& S);
+template <>
+__device__ __forceinline__ Tables<float> tables_of<float>(const BatchStatic& S) { return Tables<float>{S.geo32}; }
+template <>
+__device__ __forceinline__ Tables<double> tables_of<double>(const BatchStatic& S) { return Tables<double>{S.geo}; }
+
+#ifndef ELM_BATCH_MIN_BLOCKS
+#define ELM_BATCH_MIN_BLOCKS 6
+#endif
+
+template <class R>
+__global__ void __launch_bounds__(kAdvectThreads, ELM_BATCH_MIN_BLOCKS)
+    k_advect_batch(const __grid_constant__ BatchParams<R> P) {
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(P.counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= P.n_items) return;
+    const int2 w = P.items[it];
+    const BatchStatic& S = P.inst[w.x];
+    const BatchCall<R>& C = P.call[w.x];
+    const int4 ck = S.chunks[w.y];
+    if (int(threadIdx.x) < ck.w) {
+      const NodeJob<R> job{S.geo,
+                           static_cast<const R*>(C.u_new),
+                           static_cast<const R*>(C.u_old),
+                           static_cast<const R*>(C.T_old),
+                           static_cast<R*>(C.T_new),
+                           S.status,
+                           S.unique_map,
+                           S.owner_mp,
+                           C.K,
+                           S.N,
+                           S.npm,
+                           C.n_sub};
+      const Tables<R> tab = tables_of<R>(S);
+      if (S.dim == 3) {
+        if (C.steady) advect_node<3, R, true>(job, tab, ck, int(threadIdx.x));
+        else advect_node<3, R, false>(job, tab, ck, int(threadIdx.x));
+      } else {
+        if (C.steady) advect_node<2, R, true>(job, tab, ck, int(threadIdx.x));
+        else advect_node<2, R, false>(job, tab, ck, int(threadIdx.x));
+      }
+    }
+  }
 }
 
 // [n, dim] -> packed records [n, 4] (x, y[, z], 0).
@@ -744,6 +835,16 @@ cudaError_t launch_advect(int dim, int precision, const AdvectArgs& a, cudaStrea
   }
   Tables<float> t{a.geo32};
   return dim == 3 ? launch_dr<3, float>(a, t, s) : launch_dr<2, float>(a, t, s);
+}
+
+cudaError_t launch_batch32(const BatchParams<float>& p, int grid, cudaStream_t s) {
+  k_advect_batch<float><<<grid, kAdvectThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch64(const BatchParams<double>& p, int grid, cudaStream_t s) {
+  k_advect_batch<double><<<grid, kAdvectThreads, 0, s>>>(p);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pack_velocity(int precision, int dim, const void* u, void* u4, int64_t n, cudaStream_t s) {

@@ -133,4 +133,49 @@ cudaError_t launch_pack_velocity(int precision, int dim, const void* u, void* u4
 // Threads per block of the advection kernel, and so the work-list chunk size.
 constexpr int kAdvectThreads = 128;
 
+// ---------------------------------------------------------------------------
+// Batched form: many independent meshes in one persistent launch.
+// ---------------------------------------------------------------------------
+constexpr int kMaxBatch = 128;
+
+// Per instance, fixed for the batch's lifetime (device table).
+struct BatchStatic {
+  const MacroGeo* geo;
+  const MacroGeo32* geo32;
+  const int64_t* unique_map;
+  const int64_t* owner_mp;
+  const int4* chunks;
+  unsigned* status;
+  int N;
+  int npm;
+  int dim;
+  int pad;
+};
+
+// Per instance, per call (passed by value in the kernel's parameters, so a
+// captured CUDA graph replays exactly the pointers and constants given).
+template <class R>
+struct BatchCall {
+  const void* u_old;
+  const void* u_new;
+  const void* T_old;
+  void* T_new;
+  int n_sub;
+  int steady;
+  StepConsts<R> K;
+};
+
+template <class R>
+struct BatchParams {
+  const BatchStatic* inst;
+  const int2* items;  // (instance, chunk) work list
+  int n_items;
+  int count;
+  int* counter;       // next work item; zeroed before every launch
+  BatchCall<R> call[kMaxBatch];
+};
+
+cudaError_t launch_batch32(const BatchParams<float>& p, int grid, cudaStream_t s);
+cudaError_t launch_batch64(const BatchParams<double>& p, int grid, cudaStream_t s);
+
 }  // namespace elm

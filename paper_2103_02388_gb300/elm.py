@@ -144,3 +144,52 @@ class Mesh:
         """Synchronises the stream and raises on a device-side condition."""
         check(_lib.load().elm_get_status(self._h, _stream_ptr(stream)))
         return _lib.ELM_OK
+
+
+class Batch:
+    """Many independent advection instances (meshes of one precision, any mix
+    of dimensions and levels) advanced by one persistent kernel launch.
+
+    Each mesh keeps its own velocity (``Mesh.set_velocity``).  ``advect`` takes
+    lists of T_old / T_new tensors and per-instance dt and n_sub; it launches
+    one kernel on the current stream and can be captured in a CUDA graph.
+    """
+
+    def __init__(self, meshes, blocks_per_sm: int = 0):
+        lib = _lib.load()
+        self.meshes = list(meshes)
+        arr = (ctypes.c_void_p * len(self.meshes))(*[m.handle.value for m in self.meshes])
+        h = ctypes.c_void_p()
+        check(lib.elm_batch_create(arr, len(self.meshes), int(blocks_per_sm), ctypes.byref(h)))
+        self._h = h
+        self.blocks_per_sm = int(blocks_per_sm)
+        self.n_items = int(lib.elm_batch_num_items(h))
+        n = len(self.meshes)
+        self._told = (ctypes.c_void_p * n)()
+        self._tnew = (ctypes.c_void_p * n)()
+        self._dt = (ctypes.c_double * n)()
+        self._nsub = (ctypes.c_int * n)()
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.load().elm_batch_destroy(h)
+            self._h = None
+
+    def advect(self, T_old, T_new, dt, n_sub, stream=None) -> None:
+        n = len(self.meshes)
+        if not (len(T_old) == len(T_new) == n):
+            raise ValueError(f"expected {n} T_old / T_new tensors")
+        dts = list(dt) if hasattr(dt, "__len__") else [float(dt)] * n
+        subs = list(n_sub) if hasattr(n_sub, "__len__") else [int(n_sub)] * n
+        for k, (m, a, b) in enumerate(zip(self.meshes, T_old, T_new)):
+            m._check_tensor(a, "T_old")
+            m._check_tensor(b, "T_new")
+            if a.shape != (m.n_nodes,) or b.shape != (m.n_nodes,):
+                raise ValueError(f"instance {k}: T must have shape ({m.n_nodes},)")
+            self._told[k] = a.data_ptr()
+            self._tnew[k] = b.data_ptr()
+            self._dt[k] = float(dts[k])
+            self._nsub[k] = int(subs[k])
+        check(_lib.load().elm_batch_advect(self._h, self._told, self._tnew, self._dt, self._nsub,
+                                           _stream_ptr(stream)))

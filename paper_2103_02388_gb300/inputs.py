@@ -258,3 +258,43 @@ def dt_for_cfl(cfl: float, level: int, u_nodes) -> float:
     u = np.asarray(u_nodes, dtype=np.float64)
     vmax = float(np.sqrt((u * u).sum(axis=1)).max())
     return cfl * (0.5 ** level) / vmax
+
+
+# ---------------------------------------------------------------------------
+# Batched workload recipe
+# ---------------------------------------------------------------------------
+
+
+def batch_recipe(seed: int = 4, count: int = 64, levels2d=(4, 5, 6, 7, 8), levels3d=(4, 5, 6)):
+    """A seeded list of independent advection instances for the batched form:
+    2D unit squares (levels 4-8) and 3D unit cubes (levels 4-6), each with a
+    solid-body rotation or a random Fourier velocity (seed 4 + i), a CFL drawn
+    from U(0.5, 8), and a Gaussian-cone or slotted scalar."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        dim = 2 if rng.random() < 0.5 else 3
+        level = int(rng.choice(levels2d if dim == 2 else levels3d))
+        out.append({
+            "dim": dim,
+            "level": level,
+            "velocity": "rotation" if rng.random() < 0.5 else "fourier",
+            "velocity_seed": seed + i,
+            "cfl": float(rng.uniform(0.5, 8.0)),
+            "scalar": "gauss" if rng.random() < 0.5 else "slotted",
+        })
+    return out
+
+
+def batch_fields(entry, coords):
+    """Velocity and scalar of one batch_recipe entry at the given coordinates."""
+    dim = coords.shape[1]
+    if entry["velocity"] == "rotation":
+        u = rotation_2d(coords) if dim == 2 else rotation_3d(coords)
+    else:
+        u = random_fourier(coords, seed=entry["velocity_seed"])
+    if entry["scalar"] == "gauss":
+        T = gaussian(coords, (0.35, 0.5, 0.5)[:dim] if dim == 3 else (0.25, 0.5), 0.1 if dim == 3 else 0.05)
+    else:
+        T = slotted_sphere(coords) if dim == 3 else slotted_cylinder(coords)
+    return u, T, dt_for_cfl(entry["cfl"], entry["level"], u)
