@@ -58,6 +58,7 @@ def _load():
         lib.orc_advect.argtypes = [P, P, P, P, P, D, I32, I64, I64, I32]
         lib.orc_advect_nodes.argtypes = [P, P, P, P, D, I32, I64, P, P, I32]
         lib.orc_advect_transpose.argtypes = [P, P, P, P, P, D, I32]
+        lib.orc_advect_jvp.argtypes = [P, P, P, P, P, P, D, I32, I64, I64, P, P, I32]
         lib.orc_mass_products.argtypes = [P, I32, P, P, P]
         lib.orc_micro_simplices.restype = I64
         lib.orc_micro_simplices.argtypes = [P, P, P]
@@ -177,6 +178,22 @@ class OracleMesh:
         _load().orc_advect_nodes(self._h, _ptr(u_old), _ptr(u_new), _ptr(T_old), float(dt), int(n_sub),
                                  idx.shape[0], _ptr(idx), _ptr(out), threads or default_threads())
         return out
+
+    def advect_jvp(self, T_old, u_old, du_old, dt, n_sub=1, u_new=None, du_new=None, threads=None):
+        """(T_new, dT_new/d eps) for u -> u + eps du (forward mode, dual numbers).
+        For a steady velocity (u_new None) the direction is du_old."""
+        T_old = _f64(T_old)
+        u_old = _f64(u_old)
+        du_old = _f64(du_old)
+        steady = u_new is None
+        u_new = u_old if steady else _f64(u_new)
+        du_new = du_old if steady else _f64(du_new)
+        out = np.empty(self.n_nodes)
+        jvp = np.empty(self.n_nodes)
+        _load().orc_advect_jvp(self._h, _ptr(u_old), _ptr(u_new), _ptr(du_old), _ptr(du_new), _ptr(T_old),
+                               float(dt), int(n_sub), 0, self.n_nodes, _ptr(out), _ptr(jvp),
+                               threads or default_threads())
+        return out, jvp
 
     def advect_transpose(self, g_new, u_old, dt, n_sub=1, u_new=None):
         """Transpose of the advection step's interpolation matrix applied to g_new."""

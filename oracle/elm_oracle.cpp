@@ -519,6 +519,136 @@ double simplex_volume(int d, const double V[4][3]) {
   return std::fabs(det) / (d == 2 ? 2.0 : 6.0);
 }
 
+// ---------------------------------------------------------------------------
+// Forward-mode directional derivatives (dual numbers) of the advection step
+// with respect to the nodal velocity: each velocity value u_j becomes
+// u_j + eps v_j and every operation of the step above is repeated on pairs
+// (value, derivative).  Discrete decisions (macro choice, micro element,
+// pivots, clamps) are taken on the values; a clamped coordinate has zero
+// derivative.  Used only to check the adjoint kernel.
+// ---------------------------------------------------------------------------
+
+struct Dual {
+  double v = 0.0, d = 0.0;
+};
+Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+Dual operator/(Dual a, Dual b) { return {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)}; }
+Dual operator*(double a, Dual b) { return {a * b.v, a * b.d}; }
+
+// Barycentric coordinates of a dual point with respect to a fixed simplex.
+void barycentric_dual(int d, const double V[4][3], const Dual* y, Dual* lam) {
+  Dual A[4][5];
+  const int n = d + 1;
+  for (int r = 0; r < d; ++r) {
+    for (int c = 0; c < n; ++c) A[r][c] = {V[c][r], 0.0};
+    A[r][n] = y[r];
+  }
+  for (int c = 0; c < n; ++c) A[d][c] = {1.0, 0.0};
+  A[d][n] = {1.0, 0.0};
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[r][col].v) > std::fabs(A[piv][col].v)) piv = r;
+    if (piv != col)
+      for (int j = 0; j <= n; ++j) std::swap(A[piv][j], A[col][j]);
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      Dual f = A[r][col] / A[col][col];
+      for (int j = col; j <= n; ++j) A[r][j] = A[r][j] - f * A[col][j];
+    }
+  }
+  for (int i = 0; i < n; ++i) lam[i] = A[i][n] / A[i][i];
+}
+
+void clamp_to_box_dual(const Mesh& me, Dual* y) {
+  for (int r = 0; r < me.d; ++r) {
+    if (y[r].v < me.lo[r]) y[r] = {me.lo[r], 0.0};
+    if (y[r].v > me.hi[r]) y[r] = {me.hi[r], 0.0};
+  }
+}
+
+// Field evaluation with dual point and dual nodal values (F + eps dF).
+void eval_field_dual(const Mesh& me, const double* F, const double* dF, int ncomp, Dual* y, Dual* out) {
+  const int d = me.d;
+  double yv[3];
+  for (int r = 0; r < d; ++r) yv[r] = y[r].v;
+  Located lc;
+  locate(me, yv, lc);  // decisions on the values (may move yv onto the mesh)
+  for (int r = 0; r < d; ++r)
+    if (yv[r] != y[r].v) y[r] = {yv[r], 0.0};
+  double V[4][3];
+  for (int j = 0; j <= d; ++j) {
+    int wt[4];
+    lattice_weights(d, me.N, lc.w[j], wt);
+    lattice_point(me.mac[lc.macro], d, wt, me.N, V[j]);
+  }
+  Dual mu[4];
+  barycentric_dual(d, V, y, mu);
+  int32_t node[10];
+  double phi_unused[10];
+  const int n = p2_stencil(me, lc, node, phi_unused);
+  Dual phi[10];
+  int k = 0;
+  for (int v = 0; v <= d; ++v) phi[k++] = mu[v] * (2.0 * mu[v] - Dual{1.0, 0.0});
+  for (int a = 0; a <= d; ++a)
+    for (int b = a + 1; b <= d; ++b) phi[k++] = 4.0 * (mu[a] * mu[b]);
+  for (int c = 0; c < ncomp; ++c) {
+    Dual s{0.0, 0.0};
+    for (int j = 0; j < n; ++j) {
+      const int64_t id = int64_t(node[j]) * ncomp + c;
+      s = s + phi[j] * Dual{F[id], dF ? dF[id] : 0.0};
+    }
+    out[c] = s;
+  }
+}
+
+struct VelocityDual {
+  const double* u_old;
+  const double* u_new;
+  const double* du_old;
+  const double* du_new;
+  double dt;
+};
+
+void velocity_at_dual(const Mesh& me, const VelocityDual& V, double back, Dual* y, Dual* k) {
+  const int d = me.d;
+  Dual a[3], b[3];
+  eval_field_dual(me, V.u_new, V.du_new, d, y, b);
+  if (V.u_old == V.u_new) {
+    for (int r = 0; r < d; ++r) k[r] = b[r];
+    return;
+  }
+  eval_field_dual(me, V.u_old, V.du_old, d, y, a);
+  const double w_old = back / V.dt, w_new = (V.dt - back) / V.dt;
+  for (int r = 0; r < d; ++r) k[r] = w_old * a[r] + w_new * b[r];
+}
+
+void departure_point_dual(const Mesh& me, const VelocityDual& V, int n_sub, const double* x, Dual* X) {
+  const int d = me.d;
+  const double h = V.dt / n_sub;
+  Dual y[3], k1[3], k2[3], k3[3], k4[3], z[3];
+  for (int r = 0; r < d; ++r) y[r] = {x[r], 0.0};
+  for (int j = 0; j < n_sub; ++j) {
+    const double back = j * h;
+    for (int r = 0; r < d; ++r) z[r] = y[r];
+    velocity_at_dual(me, V, back, z, k1);
+    for (int r = 0; r < d; ++r) z[r] = y[r] - (0.5 * h) * k1[r];
+    clamp_to_box_dual(me, z);
+    velocity_at_dual(me, V, back + 0.5 * h, z, k2);
+    for (int r = 0; r < d; ++r) z[r] = y[r] - (0.5 * h) * k2[r];
+    clamp_to_box_dual(me, z);
+    velocity_at_dual(me, V, back + 0.5 * h, z, k3);
+    for (int r = 0; r < d; ++r) z[r] = y[r] - h * k3[r];
+    clamp_to_box_dual(me, z);
+    velocity_at_dual(me, V, back + h, z, k4);
+    for (int r = 0; r < d; ++r) y[r] = y[r] - (h / 6.0) * (k1[r] + 2.0 * k2[r] + 2.0 * k3[r] + k4[r]);
+    clamp_to_box_dual(me, y);
+  }
+  for (int r = 0; r < d; ++r) X[r] = y[r];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -618,6 +748,25 @@ void orc_advect_nodes(void* h, const double* u_old, const double* u_new, const d
     double X[3];
     departure_point(*me, V, n_sub, &me->X[idx[k] * d], X);
     eval_field(*me, T_old, 1, X, out + k);
+  });
+}
+
+// Directional derivative of one advection step with respect to the nodal
+// velocity in the direction (du_old, du_new): out[i] = T_new[i],
+// jvp[i] = d/deps T_new[i](u + eps du), nodes [begin, end).
+void orc_advect_jvp(void* h, const double* u_old, const double* u_new, const double* du_old, const double* du_new,
+                    const double* T_old, double dt, int n_sub, int64_t begin, int64_t end, double* out, double* jvp,
+                    int nthreads) {
+  Mesh* me = static_cast<Mesh*>(h);
+  const int d = me->d;
+  VelocityDual V{u_old, u_new, du_old, du_new, dt};
+  parallel_for(begin, end, nthreads, [&](int64_t i) {
+    Dual X[3];
+    departure_point_dual(*me, V, n_sub, &me->X[i * d], X);
+    Dual v;
+    eval_field_dual(*me, T_old, nullptr, 1, X, &v);
+    out[i - begin] = v.v;
+    jvp[i - begin] = v.d;
   });
 }
 

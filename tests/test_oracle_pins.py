@@ -3,8 +3,10 @@
 Each test below checks the oracle (``oracle/``) against something other than
 itself: Bey's refinement rule, brute-force point location, exact
 reproduction of P2 fields, closed forms of RK4 on linear fields, the exact
-solution of a non-autonomous linear ODE, textbook P2 mass-matrix integrals and
-the values printed in Table 2 of the paper.
+solution of a non-autonomous linear ODE, textbook P2 mass-matrix integrals,
+the values printed in Table 2 of the paper, and for the forward-mode
+derivative the uniform-velocity closed form and central differences on
+P2-exact (linear) fields.
 """
 import itertools
 import json
@@ -377,3 +379,62 @@ def test_refinement_rate_gaussian_rotation():
         errs.append(me.metrics(T, c0, c0)["h0"])
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert rates.min() >= 2.5
+
+
+# ---------------------------------------------------------------------------
+# Forward-mode derivative of the step with respect to the nodal velocity
+# (used to check the adjoint kernel).
+# ---------------------------------------------------------------------------
+
+
+def _quadratic_parts(seed, dim):
+    rng = np.random.default_rng(seed)  # same draws as inputs.random_quadratic
+    rng.standard_normal()
+    g = rng.standard_normal(dim)
+    H = rng.standard_normal((dim, dim))
+    return g, 0.5 * (H + H.T)
+
+
+@pytest.mark.parametrize("dim,n_sub", [(2, 1), (3, 1), (3, 3)])
+def test_jvp_uniform_velocity_closed_form(dim, n_sub):
+    """u uniform, direction v uniform: X = x - dt u, so dT/deps = -dt v . grad T(X)."""
+    me = _setup(dim, 2)
+    x = me.coords
+    U = np.array([0.3, -0.2, 0.1][:dim])
+    V = np.array([0.1, 0.2, -0.3][:dim])
+    T = inputs.random_quadratic(x, seed=3)
+    dt = 0.2
+    _, jvp = me.advect_jvp(T, inputs.uniform_field(x, U), inputs.uniform_field(x, V), dt, n_sub)
+    X = x - dt * U
+    inside = np.all((X > 1e-9) & (X < 1 - 1e-9), axis=1)
+    g, H = _quadratic_parts(3, dim)
+    grad = g + 2.0 * X @ H
+    assert np.abs(jvp[inside] - grad[inside] @ (-dt * V)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("dim,n_sub,steady", [(2, 2, True), (3, 1, True), (3, 2, False)])
+def test_jvp_linear_fields_match_finite_differences(dim, n_sub, steady):
+    """Linear u and direction (exact in P2) and quadratic T: the step is smooth
+    away from the box clamp, so forward mode equals central differences."""
+    me = _setup(dim, 3 if dim == 3 else 4)
+    x = me.coords
+    c = np.full(dim, 0.5)
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((dim, dim))
+    B = rng.standard_normal((dim, dim))
+    u0 = inputs.linear_field(x, A, c)
+    du0 = inputs.linear_field(x, B, c)
+    u1 = None if steady else inputs.linear_field(x, A + 0.5 * rng.standard_normal((dim, dim)), c)
+    du1 = None if steady else inputs.linear_field(x, rng.standard_normal((dim, dim)), c)
+    T = inputs.random_quadratic(x, seed=4)
+    dt = 0.05
+    _, jvp = me.advect_jvp(T, u0, du0, dt, n_sub, u_new=u1, du_new=du1)
+    e = 1e-6
+
+    def step(s):
+        return me.advect(T, u0 + s * du0, dt, n_sub, u_new=None if steady else u1 + s * du1)
+
+    fd = (step(e) - step(-e)) / (2 * e)
+    inner = np.linalg.norm(x - c, axis=1) < 0.3
+    assert inner.sum() > 20
+    assert np.abs(fd[inner] - jvp[inner]).max() <= 1e-7 * max(1.0, np.abs(jvp[inner]).max())
