@@ -59,6 +59,11 @@ enum { ELM_FP64 = 0, ELM_FP32 = 1 };
  * prepare inputs and check a mesh. */
 enum { ELM_HOST_ONLY = 0x100 };
 
+/* Flag OR-ed into `precision` of elm_mesh_create: also allocate the scratch
+ * of elm_advect_adjoint (64-bit accumulators: (1 + 2 dim) * 8 bytes per
+ * storage node). */
+enum { ELM_ADJOINT = 0x200 };
+
 /* Builds the refined mesh (Sec. 2.1: coarse mesh T_0 refined uniformly after
  * Bey; Sec. 2.3.1, grid data structure: one DoF owner per interface node).
  *  dim            2 (triangles) or 3 (tetrahedra).
@@ -133,6 +138,28 @@ elm_status elm_advect(elm_mesh mesh, const void* T_old_dev, void* T_new_dev, dou
  * the GPU (other streams, other threads) race; order them. */
 elm_status elm_advect_noalloc(elm_mesh mesh, const void* u_old_dev, const void* u_new_dev, const void* T_old_dev,
                               void* T_new_dev, double dt, int n_sub, void* stream);
+
+/* Adjoint of elm_advect (Eq. departure point and step (iii) of Sec. 2.3.1,
+ * differentiated) for the velocity last given to elm_set_velocity:
+ *   gT_old = W^T gT_new, W the interpolation matrix of the step
+ *            (W_ij = phi_j(X_i)), and
+ *   gU_old, gU_new = dL/du^n, dL/du^{n+1} through the backward RK4 stages,
+ *            the P2 velocity evaluations, the time interpolation and the box
+ *            clamps (a clamped coordinate passes no derivative), for
+ *            L = <gT_new, T_new(u)>.
+ * T_old, gT_new, gT_old: [n]; gU_old, gU_new: [n, dim]; storage layout, mesh
+ * precision.  Steady velocity (u_old == u_new in elm_set_velocity): gU_old
+ * receives the whole velocity gradient and gU_new must be NULL; otherwise
+ * gU_new may be NULL to receive the sum in gU_old.  Gradients are
+ * accumulated onto each node's owner slot (duplicate slots get 0), so
+ * elm_to_unique gives per-node gradients.  Deterministic: contributions are
+ * summed as 64-bit fixed-point integers (scale from a first pass), so
+ * repeated calls give bitwise equal results.  Requires ELM_ADJOINT at
+ * creation; allocates nothing; a few kernel launches on `stream`.  The map
+ * is only piecewise smooth (P2 is C0); on element faces the derivative of
+ * the element the point is located in is used. */
+elm_status elm_advect_adjoint(elm_mesh mesh, const void* T_old_dev, const void* gT_new_dev, void* gT_old_dev,
+                              void* gU_old_dev, void* gU_new_dev, double dt, int n_sub, void* stream);
 
 /* Synchronises `stream`, returns the first device-side condition raised by
  * work on this mesh since the previous call (ELM_ERR_WALK_LIMIT or

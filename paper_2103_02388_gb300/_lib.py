@@ -27,6 +27,7 @@ SIGNATURES = [
     ("elm_set_velocity", _I, [_P, _P, _P, _P]),
     ("elm_advect", _I, [_P, _P, _P, _D, _I, _P]),
     ("elm_advect_noalloc", _I, [_P, _P, _P, _P, _P, _D, _I, _P]),
+    ("elm_advect_adjoint", _I, [_P, _P, _P, _P, _P, _P, _D, _I, _P]),
     ("elm_get_status", _I, [_P, _P]),
     ("elm_batch_create", _I, [_P, _I, _I, ctypes.POINTER(_P)]),
     ("elm_batch_destroy", _I, [_P]),
@@ -64,3 +65,4 @@ def check(status: int) -> None:
         raise ElmError(status, load().elm_last_error().decode(errors="replace"))
 
 ELM_HOST_ONLY = 0x100
+ELM_ADJOINT = 0x200

@@ -43,676 +43,10 @@
 // the fractions, which leaves 2 integer adds per node.
 #include <cstdint>
 
-#include "elm_internal.h"
+#include "tracer.cuh"
 
 namespace elm {
 namespace {
-
-constexpr double kTol64 = 1e-9;     // "inside" tolerance, lattice units (FP64)
-constexpr float kBand32 = 3e-5f;    // FP32 tie band re-decided in FP64, lattice units
-
-// ---------------------------------------------------------------------------
-// Exact conversions for integer values |v| < 2^22 without conversion
-// instructions (1.5 * 2^23 places the integer in the low mantissa bits).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int f2i_exact(float x) { return __float_as_int(x + 12582912.0f) - 0x4B400000; }
-__device__ __forceinline__ float i2f_exact(int i) { return __int_as_float(i + 0x4B400000) - 12582912.0f; }
-__device__ __forceinline__ int f2i_exact(double x) {
-  return int(__double_as_longlong(x + 6755399441055744.0) - 0x4338000000000000LL);
-}
-__device__ __forceinline__ double i2f_exact_d(int i) {
-  return __longlong_as_double(0x4338000000000000LL + i) - 6755399441055744.0;
-}
-template <class R>
-__device__ __forceinline__ R to_real(int i);
-template <>
-__device__ __forceinline__ float to_real<float>(int i) { return i2f_exact(i); }
-template <>
-__device__ __forceinline__ double to_real<double>(int i) { return i2f_exact_d(i); }
-
-// floor for |x| < 2^22 on the FMA pipe: adding 1.5 * 2^23 rounds x to the
-// nearest integer, which is then corrected down if it lies above x.
-__device__ __forceinline__ float floor_small(float x) {
-  const float r = (x + 12582912.0f) - 12582912.0f;
-  return r > x ? r - 1.0f : r;
-}
-
-// Precision-exact math: the float overloads never promote to FP64.
-__device__ __forceinline__ float r_floor(float x) { return floor_small(x); }
-__device__ __forceinline__ double r_floor(double x) { return ::floor(x); }
-__device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double r_fma(double a, double b, double c) { return ::fma(a, b, c); }
-__device__ __forceinline__ float r_clamp(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
-__device__ __forceinline__ float r_min(float a, float b) { return fminf(a, b); }
-__device__ __forceinline__ double r_min(double a, double b) { return ::fmin(a, b); }
-__device__ __forceinline__ double r_clamp(double x, double lo, double hi) { return ::fmin(::fmax(x, lo), hi); }
-
-// ---------------------------------------------------------------------------
-// Double-float helpers (error-free transformations; no FP64 instructions).
-// ---------------------------------------------------------------------------
-struct df {
-  float hi, lo;
-};
-
-__device__ __forceinline__ df df_renorm(float s, float e) {
-  const float hi = s + e;
-  return {hi, e - (hi - s)};
-}
-
-__device__ __forceinline__ df df_add(df a, df b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  const float e = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
-  return df_renorm(s, e);
-}
-
-__device__ __forceinline__ df df_mul(df a, df b) {
-  const float p = a.hi * b.hi;
-  const float e = fmaf(a.hi, b.hi, -p) + fmaf(a.hi, b.lo, a.lo * b.hi);
-  return df_renorm(p, e);
-}
-
-__device__ __forceinline__ df df_mul_f(df a, float b) {
-  const float p = a.hi * b;
-  const float e = fmaf(a.hi, b, -p) + a.lo * b;
-  return df_renorm(p, e);
-}
-
-// ---------------------------------------------------------------------------
-// Macro tables in the working precision.
-// ---------------------------------------------------------------------------
-template <class R>
-struct Tables;
-
-template <>
-struct Tables<double> {
-  const MacroGeo* g;
-  __device__ double nj(int m, int k) const { return g[m].NJinv[k]; }
-  __device__ double J(int m, int k) const { return g[m].J[k]; }
-  __device__ double v0(int m, int k) const { return g[m].v0[k]; }
-  __device__ int nb(int m, int k) const { return g[m].nb[k]; }
-};
-
-template <>
-struct Tables<float> {
-  const MacroGeo32* g;
-  __device__ float nj(int m, int k) const { return g[m].NJinv[k]; }
-  __device__ float J(int m, int k) const { return g[m].J[k]; }
-  __device__ float v0(int m, int k) const { return g[m].v0[k]; }
-  __device__ int nb(int m, int k) const { return g[m].nb[k]; }
-};
-
-__device__ __forceinline__ int tri2(int k) { return k * (k + 1) / 2; }
-__device__ __forceinline__ int tri3(int k) { return k * (k + 1) * (k + 2) / 6; }
-
-// Slot within a macro -> lattice point p (packed order p1, p2[, p3]).  The
-// row and slab are estimated with the MUFU log2/exp2/rsqrt approximations
-// (cbrt(6 r), (sqrt(8 r + 1) - 1) / 2) and made exact by integer fix-up
-// loops; libm's cbrtf/sqrtf would add FP64 or long FP32 sequences.
-
-template <int D>
-__device__ __forceinline__ int tri_root2(int r) {
-  const float x = 8.0f * i2f_exact(r) + 1.0f;
-  int k = f2i_exact(floor_small((x * rsqrtf(x) - 1.0f) * 0.5f));
-  k = max(k, 0);
-  while (k > 0 && tri2(k) > r) --k;
-  while (tri2(k + 1) <= r) ++k;
-  return k;
-}
-
-// ---------------------------------------------------------------------------
-// Rare paths: entering a foreign macro and the FP64 tie-break.  They are free,
-// non-inlined functions taking scalars and returning small structs: the
-// start-node position they need is loop-invariant, and once inlined the
-// compiler hoists that FP64 / double-float work out of the rare branch into
-// every thread (costly on this GPU's narrow FP64 pipe), while a non-inlined
-// member function would force the tracer state onto the stack.
-// ---------------------------------------------------------------------------
-struct Frame {
-  float bq0, bq1, bq2, r00, r01, r02;
-};
-struct FrameD {
-  double bq0, bq1, bq2, r00, r01, r02;
-};
-struct Min64 {
-  double lmin;
-  int kmin;
-};
-
-// Start node x_i = v0_m0 + J_m0 (p / M) in FP64.
-template <int D>
-__device__ __forceinline__ void node_position64(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N,
-                                                double* x) {
-  const MacroGeo& g0 = geo[m0];
-  const double invM = 1.0 / double(2 * N);
-  const double s[3] = {double(p0) * invM, double(p1) * invM, double(p2) * invM};
-#pragma unroll
-  for (int r = 0; r < D; ++r) {
-    double v = g0.v0[r];
-#pragma unroll
-    for (int c = 0; c < D; ++c) v = ::fma(g0.J[r * 3 + c], s[c], v);
-    x[r] = v;
-  }
-}
-
-// Lattice coordinate of the start node in macro mm, FP64.
-template <int D>
-__device__ __forceinline__ void node_lattice64(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N, int mm,
-                                               double* q) {
-  double x[D];
-  node_position64<D>(geo, m0, p0, p1, p2, N, x);
-  const MacroGeo& g = geo[mm];
-#pragma unroll
-  for (int r = 0; r < D; ++r) {
-    double v = 0.0;
-#pragma unroll
-    for (int c = 0; c < D; ++c) v = ::fma(g.NJinv[r * 3 + c], x[c] - g.v0[c], v);
-    q[r] = v;
-  }
-}
-
-template <int D>
-__device__ __noinline__ FrameD frame64(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N, int mm) {
-  double q[3] = {0.0, 0.0, 0.0};
-  node_lattice64<D>(geo, m0, p0, p1, p2, N, mm, q);
-  FrameD f;
-  f.bq0 = ::floor(q[0]);
-  f.bq1 = ::floor(q[1]);
-  f.bq2 = ::floor(q[2]);
-  f.r00 = q[0] - f.bq0;
-  f.r01 = q[1] - f.bq1;
-  f.r02 = q[2] - f.bq2;
-  return f;
-}
-
-// double-float on the FP32 pipe: x_i = v0_m0 + J_m0 (p / M); q = NJinv_mm (x_i - v0_mm)
-template <int D>
-__device__ __noinline__ Frame frame_df(const MacroGeo32* tg, int m0, int p0, int p1, int p2, float invM, int mm) {
-  const MacroGeo32& g0 = tg[m0];
-  const MacroGeo32& g = tg[mm];
-  const int pp[3] = {p0, p1, p2};
-  df y[D];
-#pragma unroll
-  for (int r = 0; r < D; ++r) {
-    df acc = {g0.v0[r], g0.v0_lo[r]};
-#pragma unroll
-    for (int c = 0; c < D; ++c)
-      acc = df_add(acc, df_mul_f(df{g0.J[r * 3 + c], g0.J_lo[r * 3 + c]}, i2f_exact(pp[c]) * invM));
-    y[r] = df_add(acc, df{-g.v0[r], -g.v0_lo[r]});
-  }
-  float bq[3] = {0.0f, 0.0f, 0.0f}, r0[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-  for (int r = 0; r < D; ++r) {
-    df q = {0.0f, 0.0f};
-#pragma unroll
-    for (int c = 0; c < D; ++c) q = df_add(q, df_mul(df{g.NJinv[r * 3 + c], g.NJinv_lo[r * 3 + c]}, y[c]));
-    float fl = floor_small(q.hi);
-    if (fl == q.hi && q.lo < 0.0f) fl -= 1.0f;
-    bq[r] = fl;
-    r0[r] = (q.hi - fl) + q.lo;
-  }
-  return Frame{bq[0], bq[1], bq[2], r0[0], r0[1], r0[2]};
-}
-
-// FP64 minimum barycentric (lattice units) of x_i + d in macro m, and its face.
-template <int D>
-__device__ __noinline__ Min64 bary64_min(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N, int m,
-                                         float d0, float d1, float d2) {
-  double q[3] = {0.0, 0.0, 0.0};
-  node_lattice64<D>(geo, m0, p0, p1, p2, N, m, q);
-  const MacroGeo& g = geo[m];
-  const double d[3] = {double(d0), double(d1), double(d2)};
-#pragma unroll
-  for (int r = 0; r < D; ++r)
-#pragma unroll
-    for (int c = 0; c < D; ++c) q[r] = ::fma(g.NJinv[r * 3 + c], d[c], q[r]);
-  double l[D + 1];
-  l[0] = double(N) - q[0];
-#pragma unroll
-  for (int k = 1; k < D; ++k) l[k] = q[k - 1] - q[k];
-  l[D] = q[D - 1];
-  Min64 out{l[0], 0};
-#pragma unroll
-  for (int k = 1; k <= D; ++k)
-    if (l[k] < out.lmin) {
-      out.lmin = l[k];
-      out.kmin = k;
-    }
-  return out;
-}
-
-// Per-thread tracing state.
-template <int D, class R, bool STEADY>
-struct Tracer {
-  static constexpr int NB = (D + 1) * (D + 2) / 2;  // P2 nodes of a simplex
-  // launch constants (copied, so no kernel parameter is addressed)
-  const MacroGeo* geo;   // FP64 macro table (tie-breaks)
-  Tables<R> tab;         // macro table in the working precision
-  int N;
-  int npm;
-  const R* un;
-  const R* uo;
-  const R* T;
-  R dt;
-  R Nf;
-  R invM;          // 1 / 2^(L+1), exact
-  unsigned* status;
-  int m0;          // home macro
-  int p[D];        // home lattice point
-  // current frame: q = bq + r0 + nj * d
-  int m;
-  R bq[D];
-  R r0[D];
-  R nj[D * D];
-  R dlo[D], dhi[D];  // box limits as offsets from x_i
-
-  __device__ void load_nj(int mm) {
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = 0; c < D; ++c) nj[r * D + c] = tab.nj(mm, r * 3 + c);
-  }
-
-  __device__ void home_frame() {
-    m = m0;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      bq[k] = to_real<R>(p[k] >> 1);
-      r0[k] = (p[k] & 1) ? R(0.5) : R(0);
-    }
-    load_nj(m0);
-  }
-
-  // Enters macro mm: (bq, r0) of the start node in mm's frame.
-  __device__ void foreign_frame(int mm) {
-    if (mm == m0) {
-      home_frame();
-      return;
-    }
-    m = mm;
-    if constexpr (sizeof(R) == 8) {
-      const FrameD f = frame64<D>(geo, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, N, mm);
-      bq[0] = f.bq0;
-      bq[1] = f.bq1;
-      r0[0] = f.r00;
-      r0[1] = f.r01;
-      if (D == 3) {
-        bq[D - 1] = f.bq2;
-        r0[D - 1] = f.r02;
-      }
-    } else {
-      const Frame f = frame_df<D>(tab.g, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, float(invM), mm);
-      bq[0] = R(f.bq0);
-      bq[1] = R(f.bq1);
-      r0[0] = R(f.r00);
-      r0[1] = R(f.r01);
-      if (D == 3) {
-        bq[D - 1] = R(f.bq2);
-        r0[D - 1] = R(f.r02);
-      }
-    }
-    load_nj(mm);
-  }
-
-  // Locates x_i + d: walks macros from the current frame, returns the micro
-  // cell c (integer-valued reals) and fractions f, retracted into the
-  // macro's reference simplex N >= q1 >= q2 (>= q3) >= 0.
-  __device__ void locate(const R* d, R* c, R* f) {
-    R lmin;
-    for (int hop = 0;; ++hop) {
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        R r = r0[k];
-#pragma unroll
-        for (int j = 0; j < D; ++j) r = r_fma(nj[k * D + j], d[j], r);
-        const R fl = r_floor(r);
-        c[k] = bq[k] + fl;
-        f[k] = r - fl;
-      }
-      R l[D + 1];
-      l[0] = (Nf - c[0]) - f[0];
-#pragma unroll
-      for (int k = 1; k < D; ++k) l[k] = (c[k - 1] - c[k]) + (f[k - 1] - f[k]);
-      l[D] = c[D - 1] + f[D - 1];
-      lmin = l[0];
-#pragma unroll
-      for (int k = 1; k <= D; ++k) lmin = r_min(lmin, l[k]);
-      // common case: inside the current macro, clear of its faces
-      if (lmin >= R(sizeof(R) == 4 ? kBand32 : kTol64)) return;
-      int kmin = D;
-#pragma unroll
-      for (int k = D - 1; k >= 0; --k)
-        if (l[k] == lmin) kmin = k;
-      bool outside;
-      int nb;
-      if constexpr (sizeof(R) == 4) {
-        outside = lmin < R(-kBand32);
-        nb = tab.nb(m, kmin);
-        if (!outside && nb >= 0) {
-          // tie band at an interior face: decide in FP64 from the exact start node
-          const Min64 r64 = bary64_min<D>(geo, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, N, m, float(d[0]),
-                                          float(d[1]), D == 3 ? float(d[D - 1]) : 0.0f);
-          outside = r64.lmin < -kTol64;
-          kmin = r64.kmin;
-          nb = tab.nb(m, kmin);
-        }
-      } else {
-        outside = lmin < R(-kTol64);
-        nb = outside ? tab.nb(m, kmin) : -1;
-      }
-      if (!outside || nb < 0) break;  // inside, or outside the mesh (retraction clamps)
-      if (hop >= kMaxHops) {
-        atomicOr(status, kFlagWalkLimit);
-        break;
-      }
-      foreign_frame(nb);
-    }
-    if (lmin > R(0)) return;
-    if (c[0] < R(0)) { c[0] = R(0); f[0] = R(0); }
-    if (c[0] > Nf - R(1)) { c[0] = Nf - R(1); f[0] = R(1); }
-#pragma unroll
-    for (int k = 1; k < D; ++k) {
-      if (c[k] > c[k - 1] || (c[k] == c[k - 1] && f[k] > f[k - 1])) { c[k] = c[k - 1]; f[k] = f[k - 1]; }
-      if (c[k] < R(0)) { c[k] = R(0); f[k] = R(0); }
-    }
-  }
-
-  // P2 stencil of the micro simplex holding (c, f): storage slots and basis
-  // values (the macro's base slot is folded into the last axis' table).  Per axis a the packed index contributes A_a[o] for the
-  // lattice offset o in {0, 1, 2} of the node from 2c; sorting the axes by
-  // descending fraction (ties by axis) orders the Kuhn path c -> c + 1, and
-  // each node's offsets along the sorted axes are fixed (alpha >= beta >= gamma).
-  __device__ void stencil(const R* c, const R* f, int* slot, R* phi) const {
-    int A[D][3];
-    R fs[D];
-    {
-      const int base = m * npm;  // the macro's first storage slot (storage < 2^31)
-      const int c0 = 2 * f2i_exact(c[0]);
-      if (D == 3) {
-        const int c1 = 2 * f2i_exact(c[1]);
-        const int c2 = 2 * f2i_exact(c[D - 1]) + base;
-        A[0][0] = tri3(c0);
-        A[0][1] = A[0][0] + tri2(c0 + 1);
-        A[0][2] = A[0][1] + tri2(c0 + 2);
-        A[1][0] = tri2(c1);
-        A[1][1] = A[1][0] + c1 + 1;
-        A[1][2] = A[1][1] + c1 + 2;
-        A[D - 1][0] = c2;
-        A[D - 1][1] = c2 + 1;
-        A[D - 1][2] = c2 + 2;
-      } else {
-        const int c1 = 2 * f2i_exact(c[D - 1]) + base;
-        A[0][0] = tri2(c0);
-        A[0][1] = A[0][0] + c0 + 1;
-        A[0][2] = A[0][1] + c0 + 2;
-        A[D - 1][0] = c1;
-        A[D - 1][1] = c1 + 1;
-        A[D - 1][2] = c1 + 2;
-      }
-#pragma unroll
-      for (int k = 0; k < D; ++k) fs[k] = f[k];
-    }
-    auto cswap = [&](int i, int j) {
-      if (fs[j] > fs[i]) {
-        R t = fs[i]; fs[i] = fs[j]; fs[j] = t;
-#pragma unroll
-        for (int o = 0; o < 3; ++o) { int u = A[i][o]; A[i][o] = A[j][o]; A[j][o] = u; }
-      }
-    };
-    R L[D + 1];
-    if (D == 3) {
-      cswap(0, 1); cswap(1, 2); cswap(0, 1);
-      L[0] = R(1) - fs[0];
-      L[1] = fs[0] - fs[1];
-      L[2] = fs[1] - fs[D - 1];
-      L[D] = fs[D - 1];
-      // vertices v0..v3, edges 01 02 03 12 13 23
-      slot[0] = A[0][0] + A[1][0] + A[D - 1][0];
-      slot[1] = A[0][2] + A[1][0] + A[D - 1][0];
-      slot[2] = A[0][2] + A[1][2] + A[D - 1][0];
-      slot[3] = A[0][2] + A[1][2] + A[D - 1][2];
-      slot[4] = A[0][1] + A[1][0] + A[D - 1][0];
-      slot[5] = A[0][1] + A[1][1] + A[D - 1][0];
-      slot[6] = A[0][1] + A[1][1] + A[D - 1][1];
-      slot[7] = A[0][2] + A[1][1] + A[D - 1][0];
-      slot[8] = A[0][2] + A[1][1] + A[D - 1][1];
-      slot[9 % NB] = A[0][2] + A[1][2] + A[D - 1][1];
-      phi[0] = L[0] * (R(2) * L[0] - R(1));
-      phi[1] = L[1] * (R(2) * L[1] - R(1));
-      phi[2] = L[2] * (R(2) * L[2] - R(1));
-      phi[3] = L[D] * (R(2) * L[D] - R(1));
-      phi[4] = R(4) * L[0] * L[1];
-      phi[5] = R(4) * L[0] * L[2];
-      phi[6] = R(4) * L[0] * L[D];
-      phi[7] = R(4) * L[1] * L[2];
-      phi[8] = R(4) * L[1] * L[D];
-      phi[9 % NB] = R(4) * L[2] * L[D];
-    } else {
-      cswap(0, 1);
-      L[0] = R(1) - fs[0];
-      L[1] = fs[0] - fs[D - 1];
-      L[D] = fs[D - 1];
-      // vertices v0..v2, edges 01 02 12
-      slot[0] = A[0][0] + A[D - 1][0];
-      slot[1] = A[0][2] + A[D - 1][0];
-      slot[2] = A[0][2] + A[D - 1][2];
-      slot[3] = A[0][1] + A[D - 1][0];
-      slot[4] = A[0][1] + A[D - 1][1];
-      slot[5] = A[0][2] + A[D - 1][1];
-      phi[0] = L[0] * (R(2) * L[0] - R(1));
-      phi[1] = L[1] * (R(2) * L[1] - R(1));
-      phi[2] = L[D] * (R(2) * L[D] - R(1));
-      phi[3] = R(4) * L[0] * L[1];
-      phi[4] = R(4) * L[0] * L[D];
-      phi[5] = R(4) * L[1] * L[D];
-    }
-  }
-
-  __device__ void clamp_box(R* d) const {
-#pragma unroll
-    for (int k = 0; k < D; ++k) d[k] = r_clamp(d[k], dlo[k], dhi[k]);
-  }
-
-  // Velocity u~ at x_i + d at backward time `back` (Eq. linear interpolation).
-  // Velocities are packed records (x, y[, z], 0): one vector load per node.
-  __device__ void velocity(const R* d, R back, R* k) {
-    R c[D], f[D];
-    locate(d, c, f);
-    int slot[NB];
-    R phi[NB];
-    stencil(c, f, slot, phi);
-#pragma unroll
-    for (int r = 0; r < D; ++r) k[r] = R(0);
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      R v[D];
-      load_rec(un, slot[j], v);
-#pragma unroll
-      for (int r = 0; r < D; ++r) k[r] = r_fma(phi[j], v[r], k[r]);
-    }
-    if constexpr (!STEADY) {
-      R ko[D];
-#pragma unroll
-      for (int r = 0; r < D; ++r) ko[r] = R(0);
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        R v[D];
-        load_rec(uo, slot[j], v);
-#pragma unroll
-        for (int r = 0; r < D; ++r) ko[r] = r_fma(phi[j], v[r], ko[r]);
-      }
-      const R w_old = back / dt, w_new = (dt - back) / dt;
-#pragma unroll
-      for (int r = 0; r < D; ++r) k[r] = w_old * ko[r] + w_new * k[r];
-    }
-  }
-
-  // One packed velocity record.
-  __device__ static void load_rec(const R* u, int node, R* v) {
-    if constexpr (sizeof(R) == 4) {
-      const float4 w = __ldg(reinterpret_cast<const float4*>(u) + node);
-      v[0] = w.x;
-      v[1] = w.y;
-      if (D == 3) v[D - 1] = w.z;
-    } else {
-      const double2 w = __ldg(reinterpret_cast<const double2*>(u) + 2 * node);
-      v[0] = w.x;
-      v[1] = w.y;
-      if (D == 3) v[D - 1] = __ldg(u + 4 * int64_t(node) + 2);
-    }
-  }
-
-  __device__ R scalar(const R* d) {
-    R c[D], f[D];
-    locate(d, c, f);
-    int slot[NB];
-    R phi[NB];
-    stencil(c, f, slot, phi);
-    R v = R(0);
-#pragma unroll
-    for (int j = 0; j < NB; ++j) v = r_fma(phi[j], __ldg(T + slot[j]), v);
-    return v;
-  }
-};
-
-// 128-thread blocks, 8 resident per SM (64 registers per thread): measured
-// fastest on GB300 for the level-7 FP32 step (occupancy beats the few spills).
-#ifndef ELM_ADVECT_MIN_BLOCKS
-#define ELM_ADVECT_MIN_BLOCKS 8
-#endif
-
-template <class R>
-__device__ __forceinline__ const StepConsts<R>& consts(const AdvectArgs& a);
-template <>
-__device__ __forceinline__ const StepConsts<float>& consts<float>(const AdvectArgs& a) { return a.k32; }
-template <>
-__device__ __forceinline__ const StepConsts<double>& consts<double>(const AdvectArgs& a) { return a.k64; }
-
-template <int D>
-__device__ __forceinline__ int packed(const int* p) {
-  return D == 3 ? tri3(p[0]) + tri2(p[1]) + p[2] : tri2(p[0]) + p[1];
-}
-
-// Everything one node's step needs (one mesh instance, one call).
-template <class R>
-struct NodeJob {
-  const MacroGeo* geo;
-  const R* un;          // packed velocity records, u^{n+1}
-  const R* uo;          // packed velocity records, u^n
-  const R* T_old;
-  R* T_new;
-  unsigned* status;
-  const int64_t* unique_map;
-  const int64_t* owner_mp;
-  StepConsts<R> K;
-  int N;
-  int npm;
-  int n_sub;
-};
-
-// One node: particle creation (i), backward RK4 (ii), T evaluation (iii).
-// The node is entry `tid` of chunk ck = (macro, slab p1, first index, count).
-template <int D, class R, bool STEADY>
-__device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab, int4 ck, int tid) {
-  const StepConsts<R>& K = job.K;
-  const int npm = job.npm;
-  Tracer<D, R, STEADY> t;
-  t.geo = job.geo;
-  t.tab = tab;
-  t.N = job.N;
-  t.npm = npm;
-  t.un = job.un;
-  t.uo = job.uo;
-  t.T = job.T_old;
-  t.dt = K.dt;
-  t.Nf = K.Nf;
-  t.invM = K.invM;
-  t.status = job.status;
-  // (i) particle creation at the node (interface copies trace their owner)
-  t.m0 = ck.x;
-  const int i = ck.z + tid;  // index within slab p1
-  t.p[0] = ck.y;
-  int in_macro;
-  if (D == 3) {
-    const int p2 = tri_root2<D>(i);
-    t.p[1] = p2;
-    t.p[D - 1] = i - tri2(p2);
-    in_macro = tri3(ck.y) + i;
-  } else {
-    t.p[D - 1] = i;
-    in_macro = tri2(ck.y) + i;
-  }
-  const int64_t slot = int64_t(t.m0) * npm + in_macro;
-  {
-    const int M = 2 * job.N;
-    bool iface = t.p[0] == M || t.p[D - 1] == 0;
-#pragma unroll
-    for (int k = 1; k < D; ++k) iface = iface || t.p[k] == t.p[k - 1];
-    if (iface) {
-      const int64_t own = job.owner_mp[job.unique_map[slot]];
-      t.m0 = int(own >> 32);
-      t.p[0] = int(own >> 20) & 1023;
-      t.p[1] = int(own >> 10) & 1023;
-      if (D == 3) t.p[D - 1] = int(own) & 1023;
-    }
-  }
-  {
-#pragma unroll
-    for (int q = 0; q < D; ++q) {
-      R x = tab.v0(t.m0, q);
-#pragma unroll
-      for (int c = 0; c < D; ++c) x = r_fma(tab.J(t.m0, q * 3 + c), to_real<R>(t.p[c]) * K.invM, x);
-      t.dlo[q] = K.lo[q] - x;
-      t.dhi[q] = K.hi[q] - x;
-    }
-  }
-  t.home_frame();
-  R u_node[D];
-  Tracer<D, R, STEADY>::load_rec(t.un, t.m0 * npm + packed<D>(t.p), u_node);
-  // (ii) backward RK4, n_sub substeps of h = dt / n_sub.  All 4 n_sub stage
-  // evaluations run through one loop with a single evaluation site (stage s
-  // of a substep sits at d, d - h/2 k, d - h/2 k, d - h k and has weight
-  // 1, 2, 2, 1), which keeps the kernel's code small.
-  const R h = K.h, h2 = K.h2, h6 = K.h6;
-  R d[D], k[D], acc[D];
-#pragma unroll
-  for (int q = 0; q < D; ++q) {
-    d[q] = R(0);
-    // the first stage sits on the node: the P2 interpolant is the nodal value
-    // (steady, or at t_{n+1} where only u^{n+1} has weight)
-    k[q] = u_node[q];
-    acc[q] = k[q];
-  }
-  bool finite = true;
-  const int n_eval = 4 * job.n_sub;
-#pragma unroll 1
-  for (int e = 1; e < n_eval; ++e) {
-    const int s = e & 3;
-    const R off = s == 0 ? R(0) : (s == 3 ? h : h2);
-    R z[D];
-#pragma unroll
-    for (int q = 0; q < D; ++q) z[q] = d[q] - off * k[q];
-    t.clamp_box(z);
-    t.velocity(z, to_real<R>(e >> 2) * h + off, k);
-    const R w = (s == 1 || s == 2) ? R(2) : R(1);
-#pragma unroll
-    for (int q = 0; q < D; ++q) acc[q] = s == 0 ? k[q] : r_fma(w, k[q], acc[q]);
-    if (s == 3) {
-#pragma unroll
-      for (int q = 0; q < D; ++q) {
-        finite = finite && isfinite(acc[q]);
-        d[q] = d[q] - h6 * acc[q];
-      }
-      t.clamp_box(d);
-    }
-  }
-  // (iii) temperature at the departure point
-  const R v = t.scalar(d);
-  finite = finite && isfinite(v);
-  if (!finite) atomicOr(job.status, kFlagNonFinite);
-  job.T_new[slot] = v;
-}
-
 
 // One block per work-list chunk: a run of up to blockDim consecutive nodes
 // of one slab p1 of one macro (host-built, so no thread divides or searches

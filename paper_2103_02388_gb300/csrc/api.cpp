@@ -43,6 +43,10 @@ void free_tables(elm_mesh_s* me) {
   cudaFree(me->d_u4[0]);
   cudaFree(me->d_u4[1]);
   cudaFree(me->d_status);
+  cudaFree(me->d_acc_T);
+  cudaFree(me->d_acc_U);
+  cudaFree(me->d_maxbits);
+  me->d_acc_T = me->d_acc_U = me->d_maxbits = nullptr;
   me->d_geo = nullptr;
   me->d_geo32 = nullptr;
   me->d_unique_map = me->d_owner = me->d_owner_mp = nullptr;
@@ -76,7 +80,8 @@ elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz
   if (level < 0 || level > max_level)
     return fail(ELM_ERR_ARG, "elm_mesh_create: level out of range (0.." + std::to_string(max_level) + ")");
   const bool host_only = (precision & ELM_HOST_ONLY) != 0;
-  precision &= ~ELM_HOST_ONLY;
+  const bool with_adjoint = (precision & ELM_ADJOINT) != 0;
+  precision &= ~(ELM_HOST_ONLY | ELM_ADJOINT);
   if (precision != ELM_FP64 && precision != ELM_FP32)
     return fail(ELM_ERR_ARG, "elm_mesh_create: precision must be ELM_FP64 or ELM_FP32");
   {
@@ -89,6 +94,7 @@ elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz
   elm_mesh_s* me = new (std::nothrow) elm_mesh_s();
   if (!me) return fail(ELM_ERR_ARG, "elm_mesh_create: out of host memory");
   me->host_only = host_only;
+  me->with_adjoint = with_adjoint;
   if (!host_only) {
     cudaError_t e = cudaGetDevice(&me->device);
     if (e != cudaSuccess) {
@@ -245,6 +251,64 @@ elm_status elm_advect(elm_mesh me, const void* T_old_dev, void* T_new_dev, doubl
   a.n_chunks = int(me->n_chunks);
   cudaError_t e = elm::launch_advect(me->dim, me->precision, a, s);
   if (e != cudaSuccess) return cuda_fail(e, "elm_advect");
+  return ELM_OK;
+}
+
+elm_status elm_advect_adjoint(elm_mesh me, const void* T_old_dev, const void* gT_new_dev, void* gT_old_dev,
+                              void* gU_old_dev, void* gU_new_dev, double dt, int n_sub, void* stream) {
+  if (!me) return fail(ELM_ERR_ARG, "elm_advect_adjoint: null mesh");
+  if (!T_old_dev || !gT_new_dev || !gT_old_dev || !gU_old_dev)
+    return fail(ELM_ERR_ARG, "elm_advect_adjoint: null buffer");
+  if (!std::isfinite(dt) || dt < 0.0) return fail(ELM_ERR_ARG, "elm_advect_adjoint: dt must be finite and >= 0");
+  if (n_sub < 1 || n_sub > 64) return fail(ELM_ERR_ARG, "elm_advect_adjoint: n_sub must be in 1..64");
+  if (me->host_only || !me->with_adjoint)
+    return fail(ELM_ERR_STATE, "elm_advect_adjoint: mesh was created without ELM_ADJOINT");
+  if (!me->have_velocity) return fail(ELM_ERR_STATE, "elm_advect_adjoint: elm_set_velocity has not been called");
+  if (me->steady && gU_new_dev)
+    return fail(ELM_ERR_ARG, "elm_advect_adjoint: steady velocity: pass gU_new = NULL (gU_old gets the gradient)");
+  const size_t bytes = elem_size(me) * size_t(me->n_storage);
+  if (ranges_overlap(gT_new_dev, gT_old_dev, bytes)) return fail(ELM_ERR_ARG, "elm_advect_adjoint: gT_new and gT_old overlap");
+  DeviceGuard g(me->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  elm::AdvectArgs a{};
+  a.geo = me->d_geo;
+  a.geo32 = me->d_geo32;
+  a.n_macros = int32_t(me->n_macros);
+  a.N = me->N;
+  a.npm = me->npm;
+  a.n_storage = me->n_storage;
+  for (int r = 0; r < 3; ++r) {
+    a.lo[r] = me->lo[r];
+    a.hi[r] = me->hi[r];
+  }
+  a.u_old = me->steady ? me->d_u4[1] : me->d_u4[0];
+  a.u_new = me->d_u4[1];
+  a.steady = me->steady;
+  a.T_old = T_old_dev;
+  a.T_new = nullptr;
+  a.dt = dt;
+  a.n_sub = n_sub;
+  a.status = me->d_status;
+  a.unique_map = me->d_unique_map;
+  a.owner_mp = me->d_owner_mp;
+  a.chunks = me->d_chunks;
+  a.n_chunks = int(me->n_chunks);
+  {
+    const double h = dt / n_sub;
+    a.k64 = {h, 0.5 * h, h / 6.0, dt, 1.0 / me->M, double(me->N), {0, 0, 0}, {0, 0, 0}};
+    a.k32 = {float(h), float(0.5 * h), float(h / 6.0), float(dt), float(1.0 / me->M), float(me->N),
+             {0, 0, 0}, {0, 0, 0}};
+    for (int r = 0; r < 3; ++r) {
+      a.k64.lo[r] = me->lo[r];
+      a.k64.hi[r] = me->hi[r];
+      a.k32.lo[r] = float(me->lo[r]);
+      a.k32.hi[r] = float(me->hi[r]);
+    }
+  }
+  const elm::AdjointBuffers b{me->d_acc_T, me->d_acc_U, me->d_maxbits, me->d_owner};
+  cudaError_t e = elm::launch_adjoint(me->dim, me->precision, a, b, gT_new_dev, gT_old_dev, gU_old_dev,
+                                      me->steady ? nullptr : gU_new_dev, s);
+  if (e != cudaSuccess) return cuda_fail(e, "elm_advect_adjoint");
   return ELM_OK;
 }
 

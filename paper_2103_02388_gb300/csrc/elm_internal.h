@@ -101,6 +101,11 @@ struct elm_mesh_s {
   void* d_u4[2] = {nullptr, nullptr};  // packed velocity records u_old, u_new
   bool have_velocity = false;
   bool steady = true;
+  // adjoint scratch (ELM_ADJOINT)
+  bool with_adjoint = false;
+  unsigned long long* d_acc_T = nullptr;
+  unsigned long long* d_acc_U = nullptr;
+  unsigned long long* d_maxbits = nullptr;
   unsigned* d_status = nullptr;
 };
 
@@ -174,6 +179,16 @@ struct BatchParams {
   int* counter;       // next work item; zeroed before every launch
   BatchCall<R> call[kMaxBatch];
 };
+
+// Scratch of the adjoint (allocated at mesh creation with ELM_ADJOINT).
+struct AdjointBuffers {
+  unsigned long long* acc_T;    // [n] 64-bit fixed-point sums
+  unsigned long long* acc_U;    // [2][n][dim]
+  unsigned long long* maxbits;  // [2]
+  const int64_t* owner;         // unique id -> owner slot
+};
+cudaError_t launch_adjoint(int dim, int precision, const AdvectArgs& a, const AdjointBuffers& b,
+                           const void* gT_new, void* gT_old, void* gU_old, void* gU_new, cudaStream_t s);
 
 cudaError_t launch_batch32(const BatchParams<float>& p, int grid, cudaStream_t s);
 cudaError_t launch_batch64(const BatchParams<double>& p, int grid, cudaStream_t s);

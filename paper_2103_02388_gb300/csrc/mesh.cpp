@@ -263,6 +263,10 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
             upload((void**)&me->d_chunks, chunks.data(), sizeof(int4) * chunks.size()) &&
             cudaMalloc(&me->d_u4[0], size_t(me->n_storage) * 4 * (precision == ELM_FP64 ? 8 : 4)) == cudaSuccess &&
             cudaMalloc(&me->d_u4[1], size_t(me->n_storage) * 4 * (precision == ELM_FP64 ? 8 : 4)) == cudaSuccess &&
+            (!me->with_adjoint ||
+             (cudaMalloc((void**)&me->d_acc_T, sizeof(unsigned long long) * me->n_storage) == cudaSuccess &&
+              cudaMalloc((void**)&me->d_acc_U, sizeof(unsigned long long) * me->n_storage * d * 2) == cudaSuccess &&
+              cudaMalloc((void**)&me->d_maxbits, sizeof(unsigned long long) * 2) == cudaSuccess)) &&
             cudaMalloc((void**)&me->d_status, sizeof(unsigned)) == cudaSuccess &&
             cudaMemset(me->d_status, 0, sizeof(unsigned)) == cudaSuccess;
   if (!ok) {

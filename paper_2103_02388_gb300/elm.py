@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import ELM_FP32, ELM_FP64, ELM_HOST_ONLY, check
+from ._lib import ELM_ADJOINT, ELM_FP32, ELM_FP64, ELM_HOST_ONLY, check
 
 _DTYPES = {"fp64": (ELM_FP64, torch.float64, np.float64), "fp32": (ELM_FP32, torch.float32, np.float32)}
 
@@ -30,7 +30,8 @@ class Mesh:
     the host tables (coordinates and the unique map), without a GPU.
     """
 
-    def __init__(self, vertices, macros, level: int, precision: str = "fp64", host_only: bool = False):
+    def __init__(self, vertices, macros, level: int, precision: str = "fp64", host_only: bool = False,
+                 adjoint: bool = False):
         lib = _lib.load()
         self.vertices = np.ascontiguousarray(vertices, dtype=np.float64)
         self.macros = np.ascontiguousarray(macros, dtype=np.int64)
@@ -39,13 +40,15 @@ class Mesh:
         self.precision = precision
         code, self.dtype, self.np_dtype = _DTYPES[precision]
         self.host_only = host_only
+        self.adjoint = adjoint
         if not host_only:
             self.device = torch.device("cuda", torch.cuda.current_device())
         h = ctypes.c_void_p()
         check(lib.elm_mesh_create(self.dim, self.vertices.shape[0],
                                   self.vertices.ctypes.data_as(ctypes.c_void_p),
                                   self.macros.shape[0], self.macros.ctypes.data_as(ctypes.c_void_p),
-                                  self.level, code | (ELM_HOST_ONLY if host_only else 0), ctypes.byref(h)))
+                                  self.level, code | (ELM_HOST_ONLY if host_only else 0) | (ELM_ADJOINT if adjoint else 0),
+                                  ctypes.byref(h)))
         self._h = h
         self.n_nodes = int(lib.elm_mesh_num_nodes(h))
         self.n_unique = int(lib.elm_mesh_num_unique(h))
@@ -139,6 +142,27 @@ class Mesh:
         check(_lib.load().elm_advect(self._h, ctypes.c_void_p(T_old.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                      float(dt), int(n_sub), _stream_ptr(stream)))
         return out
+
+    def advect_adjoint(self, T_old: torch.Tensor, gT_new: torch.Tensor, dt: float, n_sub: int = 1,
+                       split: bool = True, stream=None):
+        """Adjoint of ``advect`` for the current velocity: returns (gT_old,
+        gU_old, gU_new) in storage layout; gU_new is None for a steady
+        velocity or when ``split`` is False (then gU_old holds the sum).
+        Needs ``adjoint=True`` at construction."""
+        self._check_tensor(T_old, "T_old")
+        self._check_tensor(gT_new, "gT_new")
+        if self._u is None:
+            raise RuntimeError("set_velocity has not been called")
+        steady = self._u[0] is self._u[1]
+        gT_old = torch.empty_like(T_old)
+        gU_old = torch.empty((self.n_nodes, self.dim), dtype=self.dtype, device=T_old.device)
+        gU_new = None if (steady or not split) else torch.empty_like(gU_old)
+        check(_lib.load().elm_advect_adjoint(
+            self._h, ctypes.c_void_p(T_old.data_ptr()), ctypes.c_void_p(gT_new.data_ptr()),
+            ctypes.c_void_p(gT_old.data_ptr()), ctypes.c_void_p(gU_old.data_ptr()),
+            ctypes.c_void_p(gU_new.data_ptr()) if gU_new is not None else None,
+            float(dt), int(n_sub), _stream_ptr(stream)))
+        return gT_old, gU_old, gU_new
 
     def status(self, stream=None) -> int:
         """Synchronises the stream and raises on a device-side condition."""

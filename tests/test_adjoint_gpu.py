@@ -1,0 +1,207 @@
+"""GPU adjoint (elm_advect_adjoint) against the oracle and against the GPU
+forward step: transpose interpolation (oracle transpose, dot-product
+identity), velocity sensitivity (oracle forward-mode derivative, central
+differences on P2-exact fields), determinism, and the autograd wrapper with
+step checkpointing."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from _helpers import match_nodes
+from paper_2103_02388_gb300 import autograd, elm, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+class Pair:
+    def __init__(self, level, precision, mesh="cube"):
+        v, m = inputs.unit_cube() if mesh == "cube" else inputs.unit_square()
+        self.om = oracle.OracleMesh(v, m, level)
+        self.gm = elm.Mesh(v, m, level, precision, adjoint=True)
+        self.perm = match_nodes(self.om.coords, self.gm.unique_coords())
+        self.x = self.om.coords
+        self.precision = precision
+        umap = self.gm.unique_map()
+        first = np.full(self.gm.n_unique, -1, np.int64)
+        first[umap[::-1]] = np.arange(self.gm.n_nodes)[::-1]
+        self.owner_slot = first          # unique id (GPU order) -> owner slot
+
+    def rounded(self, a):
+        return a.astype(np.float32).astype(np.float64) if self.precision == "fp32" else a
+
+    def to_gpu(self, a):
+        """Unique field (oracle order) -> storage tensor, copies everywhere."""
+        g = np.empty_like(a)
+        g[self.perm] = a
+        return self.gm.to_storage(torch.tensor(g, dtype=self.gm.dtype, device="cuda"))
+
+    def to_gpu_owner(self, a):
+        """Unique field (oracle order) -> storage tensor on owner slots only
+        (a gradient of a loss over unique nodes)."""
+        g = np.empty_like(a)
+        g[self.perm] = a
+        out = np.zeros((self.gm.n_nodes,) + a.shape[1:])
+        out[self.owner_slot] = g
+        return torch.tensor(out, dtype=self.gm.dtype, device="cuda")
+
+    def from_gpu(self, t):
+        return self.gm.to_unique(t).double().cpu().numpy()[self.perm]
+
+
+def _fields(P, kind):
+    x = P.x
+    if kind == "linear":
+        rng = np.random.default_rng(2)
+        u = inputs.linear_field(x, rng.standard_normal((3, 3)), np.full(3, 0.5))
+        T = inputs.random_quadratic(x, seed=6)
+    else:
+        u = inputs.random_fourier(x, seed=9) + 0.2 * inputs.uniform_field(x, [0.31, -0.17, 0.23])
+        T = inputs.gaussian(x, (0.45, 0.5, 0.55), 0.15)
+    return P.rounded(u), P.rounded(T)
+
+
+@pytest.mark.parametrize("precision,n_sub", [("fp64", 1), ("fp64", 3), ("fp32", 1)])
+def test_transpose_matches_oracle(precision, n_sub):
+    P = Pair(3, precision)
+    u, T = _fields(P, "fourier")
+    dt = inputs.dt_for_cfl(4.0, 3, u)
+    g = np.random.default_rng(1).standard_normal(P.om.n_nodes)
+    P.gm.set_velocity(P.to_gpu(u))
+    gT_old, _, _ = P.gm.advect_adjoint(P.to_gpu(T), P.to_gpu_owner(g), dt, n_sub)
+    P.gm.status()
+    got = P.from_gpu(gT_old)
+    ref = P.om.advect_transpose(g, u, dt, n_sub)
+    assert np.abs(got - ref).max() <= TOL[precision] * np.abs(ref).max() * 10
+    # duplicated slots carry no gradient
+    umap = P.gm.unique_map()
+    ghosts = np.ones(P.gm.n_nodes, bool)
+    ghosts[P.owner_slot] = False
+    assert np.all(gT_old.cpu().numpy()[ghosts] == 0)
+
+
+def test_dot_product_identity_on_gpu():
+    P = Pair(3, "fp64")
+    u, T = _fields(P, "fourier")
+    dt = inputs.dt_for_cfl(4.0, 3, u)
+    rng = np.random.default_rng(4)
+    a, b = rng.standard_normal(P.om.n_nodes), rng.standard_normal(P.om.n_nodes)
+    P.gm.set_velocity(P.to_gpu(u))
+    Wa = P.from_gpu(P.gm.advect(P.to_gpu(a), dt, 2))
+    WTb, _, _ = P.gm.advect_adjoint(P.to_gpu(T), P.to_gpu_owner(b), dt, 2)
+    lhs, rhs = Wa @ b, a @ P.from_gpu(WTb)
+    assert abs(lhs - rhs) <= 1e-12 * np.abs(a).sum() * np.abs(b).max()
+
+
+@pytest.mark.parametrize("kind,n_sub", [("linear", 1), ("linear", 2), ("fourier", 1), ("fourier", 2)])
+def test_velocity_gradient_matches_oracle_jvp(kind, n_sub):
+    """<dL/du, v> from the GPU adjoint equals <g, dT/d eps> of the oracle's
+    forward-mode derivative for 8 random directions v (L = <g, T_new>)."""
+    P = Pair(3, "fp64")
+    u, T = _fields(P, kind)
+    dt = inputs.dt_for_cfl(3.0, 3, u)
+    rng = np.random.default_rng(5)
+    g = rng.standard_normal(P.om.n_nodes)
+    P.gm.set_velocity(P.to_gpu(u))
+    _, gU, _ = P.gm.advect_adjoint(P.to_gpu(T), P.to_gpu_owner(g), dt, n_sub)
+    gU = P.from_gpu(gU)
+    for _ in range(8):
+        v = rng.standard_normal(u.shape)
+        _, jvp = P.om.advect_jvp(T, u, v, dt, n_sub)
+        lhs, rhs = (gU * v).sum(), g @ jvp
+        assert abs(lhs - rhs) <= 1e-9 * (np.abs(g) @ np.abs(jvp) + 1e-30)
+
+
+def test_velocity_gradient_time_dependent_split():
+    P = Pair(3, "fp64")
+    rng = np.random.default_rng(8)
+    u0, T = _fields(P, "fourier")
+    # a generic shift: no stage point runs exactly along a face of the box
+    # (where the clamp makes the step non-differentiable)
+    u1 = inputs.random_fourier(P.x, seed=12) + 0.2 * inputs.uniform_field(P.x, [-0.21, 0.33, 0.14])
+    dt = inputs.dt_for_cfl(3.0, 3, u1)
+    g = rng.standard_normal(P.om.n_nodes)
+    P.gm.set_velocity(P.to_gpu(u0), P.to_gpu(u1))
+    _, gU0, gU1 = P.gm.advect_adjoint(P.to_gpu(T), P.to_gpu_owner(g), dt, 2)
+    gU0, gU1 = P.from_gpu(gU0), P.from_gpu(gU1)
+    zero = np.zeros_like(u0)
+    for _ in range(4):
+        v = rng.standard_normal(u0.shape)
+        _, j0 = P.om.advect_jvp(T, u0, v, dt, 2, u_new=u1, du_new=zero)
+        _, j1 = P.om.advect_jvp(T, u0, zero, dt, 2, u_new=u1, du_new=v)
+        assert abs((gU0 * v).sum() - g @ j0) <= 1e-9 * (np.abs(g) @ np.abs(j0) + 1e-30)
+        assert abs((gU1 * v).sum() - g @ j1) <= 1e-9 * (np.abs(g) @ np.abs(j1) + 1e-30)
+
+
+def test_velocity_gradient_finite_differences_gpu():
+    """Central differences of the GPU forward step on P2-exact (linear) fields."""
+    P = Pair(3, "fp64")
+    u, T = _fields(P, "linear")
+    dt = 0.04
+    rng = np.random.default_rng(3)
+    g = rng.standard_normal(P.om.n_nodes)
+    inner = np.linalg.norm(P.x - 0.5, axis=1) < 0.3
+    g[~inner] = 0.0                          # away from the box clamp
+    Tg = P.to_gpu(T)
+    P.gm.set_velocity(P.to_gpu(u))
+    _, gU, _ = P.gm.advect_adjoint(Tg, P.to_gpu_owner(g), dt, 1)
+    gU = P.from_gpu(gU)
+    for _ in range(4):
+        B = rng.standard_normal((3, 3))
+        v = inputs.linear_field(P.x, B, np.full(3, 0.5))
+        e = 1e-6
+        P.gm.set_velocity(P.to_gpu(u + e * v))
+        fp = P.from_gpu(P.gm.advect(Tg, dt, 1))
+        P.gm.set_velocity(P.to_gpu(u - e * v))
+        fm = P.from_gpu(P.gm.advect(Tg, dt, 1))
+        fd = g @ (fp - fm) / (2 * e)
+        assert abs((gU * v).sum() - fd) <= 1e-7 * (np.abs(g) @ np.abs((fp - fm) / (2 * e)) + 1e-30)
+
+
+def test_adjoint_is_deterministic():
+    P = Pair(3, "fp32")
+    u, T = _fields(P, "fourier")
+    dt = inputs.dt_for_cfl(6.0, 3, u)
+    g = P.to_gpu_owner(np.random.default_rng(2).standard_normal(P.om.n_nodes))
+    P.gm.set_velocity(P.to_gpu(u))
+    r1 = P.gm.advect_adjoint(P.to_gpu(T), g, dt, 2)
+    r2 = P.gm.advect_adjoint(P.to_gpu(T), g, dt, 2)
+    assert torch.equal(r1[0], r2[0]) and torch.equal(r1[1], r2[1])
+
+
+def test_autograd_rollout_with_checkpoints():
+    """L = 1/2 |T_K - T*|^2 after K steps: gradients with and without step
+    checkpointing agree, and match central differences along a direction of
+    T^0 (the map is linear in T^0) and the oracle chain for the velocity."""
+    v, m = inputs.unit_cube()
+    mesh = elm.Mesh(v, m, 3, "fp64", adjoint=True)
+    x = mesh.node_coords()
+    u = torch.tensor(inputs.random_fourier(x, seed=5), dtype=torch.float64, device="cuda")
+    T0 = torch.tensor(inputs.gaussian(x, (0.4, 0.5, 0.5), 0.15), dtype=torch.float64, device="cuda")
+    target = torch.tensor(inputs.smooth_target(x, seed=5), dtype=torch.float64, device="cuda")
+    dt = inputs.dt_for_cfl(2.0, 3, u.cpu().numpy())
+    steps = 12
+
+    def loss(T0_, u_, every):
+        T = autograd.rollout(T0_, u_, mesh, dt, steps, checkpoint_every=every)
+        return 0.5 * ((T - target) ** 2).sum()
+
+    grads = []
+    for every in (0, 4):
+        a = T0.clone().requires_grad_(True)
+        b = u.clone().requires_grad_(True)
+        loss(a, b, every).backward()
+        grads.append((a.grad.clone(), b.grad.clone()))
+    assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
+    gT0 = grads[0][0]
+    e = 1e-4
+    # the gradient sits on owner slots, so compare along a direction that is
+    # equal on all storage copies of a node (as every physical field is)
+    mesh_umap = torch.tensor(mesh.unique_map(), device="cuda")
+    d_unique = torch.randn(mesh.n_unique, dtype=torch.float64, device="cuda")
+    d = d_unique[mesh_umap]
+    with torch.no_grad():
+        fd = (loss(T0 + e * d, u, 0) - loss(T0 - e * d, u, 0)) / (2 * e)
+    assert abs(float((gT0 * d).sum()) - float(fd)) <= 1e-8 * abs(float(fd)) + 1e-10
