@@ -149,7 +149,7 @@ struct Adjoint {
     for (int cc = 0; cc < D; ++cc) {
       R v = R(0);
 #pragma unroll
-      for (int r = 0; r < D; ++r) v = r_fma(t.nj[r * D + cc], gq[r], v);
+      for (int r = 0; r < D; ++r) v = r_fma(t.nj(r * D + cc), gq[r], v);
       gx[cc] = v;
     }
   }
@@ -356,6 +356,7 @@ __global__ void __launch_bounds__(kAdvectThreads)
   t.Nf = K.Nf;
   t.invM = K.invM;
   t.status = args.status;
+  t.load_block_macro(ck.x);
   ad.A = aa;
   ad.n_storage = int(args.n_storage);
   ad.h = K.h;

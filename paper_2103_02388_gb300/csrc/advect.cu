@@ -35,9 +35,11 @@
 //
 // GB300 notes.  FP64 runs at a small fraction of the FP32 rate on this part,
 // so the FP32 kernel keeps every FP64 (and double-float) instruction in
-// non-inlined rare-path functions, and lattice integers are kept as
-// integer-valued floats, converted with exact bit tricks on the ALU/FMA
-// pipes (|values| < 2^22).  The packed index of a lattice point is separable,
+// non-inlined rare-path functions (the compiler would otherwise hoist the
+// loop-invariant FP64 start-node position into every thread).  Lattice
+// integers are integer-valued floats.  Every block works inside one macro,
+// so that macro's N J^{-1} is held once per thread as a block-uniform value
+// and a foreign macro's is read from the L1-resident table after a hand-off.  The packed index of a lattice point is separable,
 // idx(p) = T3(p1) + T2(p2) + p3, so the 10 P2 nodes of a micro simplex are
 // sums of three per-axis table entries; the tables are sorted together with
 // the fractions, which leaves 2 integer adds per node.

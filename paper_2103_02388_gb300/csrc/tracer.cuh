@@ -16,11 +16,10 @@ constexpr double kTol64 = 1e-9;     // "inside" tolerance, lattice units (FP64)
 constexpr float kBand32 = 3e-5f;    // FP32 tie band re-decided in FP64, lattice units
 
 // ---------------------------------------------------------------------------
-// Exact conversions for integer values |v| < 2^22 without conversion
-// instructions (1.5 * 2^23 places the integer in the low mantissa bits).
+// Conversions of integer-valued lattice coordinates (exact for |v| < 2^22).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int f2i_exact(float x) { return __float_as_int(x + 12582912.0f) - 0x4B400000; }
-__device__ __forceinline__ float i2f_exact(int i) { return __int_as_float(i + 0x4B400000) - 12582912.0f; }
+__device__ __forceinline__ int f2i_exact(float x) { return __float2int_rn(x); }
+__device__ __forceinline__ float i2f_exact(int i) { return __int2float_rn(i); }
 __device__ __forceinline__ int f2i_exact(double x) {
   return int(__double_as_longlong(x + 6755399441055744.0) - 0x4338000000000000LL);
 }
@@ -42,7 +41,7 @@ __device__ __forceinline__ float floor_small(float x) {
 }
 
 // Precision-exact math: the float overloads never promote to FP64.
-__device__ __forceinline__ float r_floor(float x) { return floor_small(x); }
+__device__ __forceinline__ float r_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double r_floor(double x) { return ::floor(x); }
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return ::fma(a, b, c); }
@@ -267,15 +266,21 @@ struct Tracer {
   int m;
   R bq[D];
   R r0[D];
-  R nj[D * D];
+  int mb;             // the block's macro (uniform across the block)
+  R njb[D * D];       // N J^{-1} of the block's macro
   R dlo[D], dhi[D];  // box limits as offsets from x_i
 
-  __device__ void load_nj(int mm) {
+  __device__ void load_block_macro(int mm) {
+    mb = mm;
 #pragma unroll
     for (int r = 0; r < D; ++r)
 #pragma unroll
-      for (int c = 0; c < D; ++c) nj[r * D + c] = tab.nj(mm, r * 3 + c);
+      for (int c = 0; c < D; ++c) njb[r * D + c] = tab.nj(mm, r * 3 + c);
   }
+
+  // N J^{-1} entry of the current macro: the block's macro from registers,
+  // any other (after a hand-off) from the L1-resident table.
+  __device__ R nj(int k) const { return m == mb ? njb[k] : tab.nj(m, (k / D) * 3 + k % D); }
 
   __device__ void home_frame() {
     m = m0;
@@ -284,7 +289,6 @@ struct Tracer {
       bq[k] = to_real<R>(p[k] >> 1);
       r0[k] = (p[k] & 1) ? R(0.5) : R(0);
     }
-    load_nj(m0);
   }
 
   // Enters macro mm: (bq, r0) of the start node in mm's frame.
@@ -315,7 +319,6 @@ struct Tracer {
         r0[D - 1] = R(f.r02);
       }
     }
-    load_nj(mm);
   }
 
   // Locates x_i + d: walks macros from the current frame, returns the micro
@@ -328,7 +331,7 @@ struct Tracer {
       for (int k = 0; k < D; ++k) {
         R r = r0[k];
 #pragma unroll
-        for (int j = 0; j < D; ++j) r = r_fma(nj[k * D + j], d[j], r);
+        for (int j = 0; j < D; ++j) r = r_fma(nj(k * D + j), d[j], r);
         const R fl = r_floor(r);
         c[k] = bq[k] + fl;
         f[k] = r - fl;
@@ -592,6 +595,7 @@ __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab
   t.Nf = K.Nf;
   t.invM = K.invM;
   t.status = job.status;
+  t.load_block_macro(ck.x);
   // (i) particle creation at the node (interface copies trace their owner)
   t.m0 = ck.x;
   const int i = ck.z + tid;  // index within slab p1
