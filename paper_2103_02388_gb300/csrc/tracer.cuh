@@ -244,6 +244,27 @@ __device__ __noinline__ Min64 bary64_min(const MacroGeo* geo, int m0, int p0, in
   return out;
 }
 
+// r = r0 + N J_m^{-1} d in a macro other than the block's (after a hand-off;
+// not inlined so the common path carries no table loads or selects).
+template <class R>
+struct Vec3 {
+  R x, y, z;
+};
+template <int D, class R>
+__device__ __noinline__ Vec3<R> lattice_foreign(Tables<R> tab, int m, R r00, R r01, R r02, R d0, R d1, R d2) {
+  const R r0[3] = {r00, r01, r02};
+  const R d[3] = {d0, d1, d2};
+  R r[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    R v = r0[k];
+#pragma unroll
+    for (int j = 0; j < D; ++j) v = r_fma(tab.nj(m, k * 3 + j), d[j], v);
+    r[k] = v;
+  }
+  return Vec3<R>{r[0], r[1], r[2]};
+}
+
 // Per-thread tracing state.
 template <int D, class R, bool STEADY>
 struct Tracer {
@@ -327,14 +348,27 @@ struct Tracer {
   __device__ void locate(const R* d, R* c, R* f) {
     R lmin;
     for (int hop = 0;; ++hop) {
+      R r[D];
+      if (m == mb) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          R v = r0[k];
+#pragma unroll
+          for (int j = 0; j < D; ++j) v = r_fma(njb[k * D + j], d[j], v);
+          r[k] = v;
+        }
+      } else {
+        const Vec3<R> v = lattice_foreign<D, R>(tab, m, r0[0], r0[1], D == 3 ? r0[D - 1] : R(0), d[0], d[1],
+                                                D == 3 ? d[D - 1] : R(0));
+        r[0] = v.x;
+        r[1] = v.y;
+        if (D == 3) r[D - 1] = v.z;
+      }
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        R r = r0[k];
-#pragma unroll
-        for (int j = 0; j < D; ++j) r = r_fma(nj(k * D + j), d[j], r);
-        const R fl = r_floor(r);
+        const R fl = r_floor(r[k]);
         c[k] = bq[k] + fl;
-        f[k] = r - fl;
+        f[k] = r[k] - fl;
       }
       R l[D + 1];
       l[0] = (Nf - c[0]) - f[0];
