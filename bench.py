@@ -38,7 +38,10 @@ WORKLOADS = {
     "c2-l6-fp64": (3, 6, "fp64", "cellular", "slotted", 4.0, 1),
 }
 METRIC = "traced node updates/s per advection step (1 GPU), % of HBM roofline, err vs FP64 oracle"
-KERNEL_SRC = os.path.join(ROOT, "paper_2103_02388_gb300", "csrc", "advect.cu")
+# sources the advection kernel is compiled from: the DRAM traffic recorded in
+# TRAFFIC_FILE is used only while their hash matches the one stored there
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2103_02388_gb300", "csrc", f)
+               for f in ("advect.cu", "tracer.cuh", "elm_internal.h")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "advect_traffic.json")
 
 
@@ -95,8 +98,11 @@ def alg_ops_per_node(dim: int, n_sub: int, steady: bool) -> int:
 
 
 def _kernel_hash():
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for p in KERNEL_SRCS:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _traffic(workload):
@@ -193,7 +199,8 @@ def _cpu_baseline(spec, seconds: float = 12.0):
             break
         n = int(n * min(8.0, max(2.0, seconds / 2 / max(el, 1e-3))))
     return {"value": len(idx) / el, "unit": "node updates/s", "cores": threads, "kind": "oracle",
-            "sample": f"{len(idx)} random nodes of the same workload, one step, FP64, {threads} threads",
+            "sample": (f"all {len(idx)} nodes of the workload" if len(idx) == om.n_nodes else
+                       f"{len(idx)} random nodes of the same workload") + f", one step, FP64, {threads} threads",
             "seconds": el}
 
 

@@ -110,11 +110,23 @@ elm_status elm_to_unique(elm_mesh mesh, const void* storage_dev, void* unique_de
  * Work on other streams must be ordered after it by the caller. */
 elm_status elm_set_velocity(elm_mesh mesh, const void* u_old_dev, const void* u_new_dev, void* stream);
 
+/* Most RK4 substeps of one forward step (elm_advect, elm_advect_noalloc,
+ * elm_batch_advect); elm_advect_adjoint, whose cost grows with the square of
+ * the substep count, takes at most ELM_MAX_ADJOINT_SUBSTEPS. */
+#define ELM_MAX_SUBSTEPS 65536
+#define ELM_MAX_ADJOINT_SUBSTEPS 64
+
 /* One advection step (Algorithm 1, lines 3-4; Sec. 2.3.1 steps (i)-(iii)):
  * T_new[i] = T_old_h(X_i), X_i traced back over dt from node i with n_sub
  * equal RK4 substeps.  T_old and T_new are [n] in storage layout and must
  * not overlap.  Stage and departure points outside the domain are clamped
- * to the mesh's bounding box.  1 <= n_sub <= 64; dt finite and >= 0. */
+ * to the mesh's bounding box.  1 <= n_sub <= ELM_MAX_SUBSTEPS; dt finite
+ * and >= 0.
+ * Look-back distance b (Sec. 2.3.3) for a steady velocity: tracing back b
+ * steps of tau with s RK4 substeps each and interpolating T^{n+1-b} is
+ * exactly elm_advect(T^{n+1-b}, b*tau, b*s); b = infinity is T^0 with
+ * dt = t_{n+1} (one trace over the whole time, no interpolation error
+ * accumulated between steps). */
 elm_status elm_advect(elm_mesh mesh, const void* T_old_dev, void* T_new_dev, double dt, int n_sub,
                       void* stream);
 
@@ -157,7 +169,9 @@ elm_status elm_advect_noalloc(elm_mesh mesh, const void* u_old_dev, const void* 
  * repeated calls give bitwise equal results.  Requires ELM_ADJOINT at
  * creation; allocates nothing; a few kernel launches on `stream`.  The map
  * is only piecewise smooth (P2 is C0); on element faces the derivative of
- * the element the point is located in is used. */
+ * the element the point is located in is used.
+ * 1 <= n_sub <= ELM_MAX_ADJOINT_SUBSTEPS (the reverse sweep recomputes each
+ * substep's start from the node, O(n_sub^2) work). */
 elm_status elm_advect_adjoint(elm_mesh mesh, const void* T_old_dev, const void* gT_new_dev, void* gT_old_dev,
                               void* gU_old_dev, void* gU_new_dev, double dt, int n_sub, void* stream);
 

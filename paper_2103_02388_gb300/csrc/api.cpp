@@ -207,7 +207,8 @@ elm_status elm_advect(elm_mesh me, const void* T_old_dev, void* T_new_dev, doubl
   if (!me) return fail(ELM_ERR_ARG, "elm_advect: null mesh");
   if (!T_old_dev || !T_new_dev) return fail(ELM_ERR_ARG, "elm_advect: null temperature buffer");
   if (!std::isfinite(dt) || dt < 0.0) return fail(ELM_ERR_ARG, "elm_advect: dt must be finite and >= 0");
-  if (n_sub < 1 || n_sub > 64) return fail(ELM_ERR_ARG, "elm_advect: n_sub must be in 1..64");
+  if (n_sub < 1 || n_sub > elm::kMaxSub)
+    return fail(ELM_ERR_ARG, "elm_advect: n_sub must be in 1.." + std::to_string(elm::kMaxSub));
   if (me->host_only) return fail(ELM_ERR_STATE, "elm_advect: host-only mesh");
   if (!me->have_velocity) return fail(ELM_ERR_STATE, "elm_advect: elm_set_velocity has not been called");
   if (ranges_overlap(T_old_dev, T_new_dev, elem_size(me) * size_t(me->n_storage)))
@@ -260,7 +261,8 @@ elm_status elm_advect_adjoint(elm_mesh me, const void* T_old_dev, const void* gT
   if (!T_old_dev || !gT_new_dev || !gT_old_dev || !gU_old_dev)
     return fail(ELM_ERR_ARG, "elm_advect_adjoint: null buffer");
   if (!std::isfinite(dt) || dt < 0.0) return fail(ELM_ERR_ARG, "elm_advect_adjoint: dt must be finite and >= 0");
-  if (n_sub < 1 || n_sub > 64) return fail(ELM_ERR_ARG, "elm_advect_adjoint: n_sub must be in 1..64");
+  if (n_sub < 1 || n_sub > elm::kMaxAdjointSub)
+    return fail(ELM_ERR_ARG, "elm_advect_adjoint: n_sub must be in 1.." + std::to_string(elm::kMaxAdjointSub));
   if (me->host_only || !me->with_adjoint)
     return fail(ELM_ERR_STATE, "elm_advect_adjoint: mesh was created without ELM_ADJOINT");
   if (!me->have_velocity) return fail(ELM_ERR_STATE, "elm_advect_adjoint: elm_set_velocity has not been called");

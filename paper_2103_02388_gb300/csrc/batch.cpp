@@ -172,7 +172,8 @@ elm_status elm_batch_advect(elm_batch b, const void* const* T_old, void* const* 
     if (!me->have_velocity) return bfail(ELM_ERR_STATE, who + "elm_set_velocity has not been called");
     if (!T_old[k] || !T_new[k]) return bfail(ELM_ERR_ARG, who + "null temperature buffer");
     if (!std::isfinite(dt[k]) || dt[k] < 0.0) return bfail(ELM_ERR_ARG, who + "dt must be finite and >= 0");
-    if (n_sub[k] < 1 || n_sub[k] > 64) return bfail(ELM_ERR_ARG, who + "n_sub must be in 1..64");
+    if (n_sub[k] < 1 || n_sub[k] > elm::kMaxSub)
+      return bfail(ELM_ERR_ARG, who + "n_sub must be in 1.." + std::to_string(elm::kMaxSub));
     const size_t bytes = size_t(me->n_storage) * (me->precision == ELM_FP64 ? 8 : 4);
     const char* a = static_cast<const char*>(T_old[k]);
     const char* c = static_cast<const char*>(T_new[k]);

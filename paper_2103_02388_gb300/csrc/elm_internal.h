@@ -142,6 +142,8 @@ constexpr int kAdvectThreads = 128;
 // Batched form: many independent meshes in one persistent launch.
 // ---------------------------------------------------------------------------
 constexpr int kMaxBatch = 128;
+constexpr int kMaxSub = ELM_MAX_SUBSTEPS;
+constexpr int kMaxAdjointSub = ELM_MAX_ADJOINT_SUBSTEPS;
 
 // Per instance, fixed for the batch's lifetime (device table).
 struct BatchStatic {

@@ -61,7 +61,8 @@ extern "C" elm_status elm_advect_noalloc(elm_mesh me, const void* u_old_dev, con
   if (!u_old_dev || !u_new_dev) return noalloc_fail(ELM_ERR_ARG, "elm_advect_noalloc: null velocity");
   if (!T_old_dev || !T_new_dev) return noalloc_fail(ELM_ERR_ARG, "elm_advect_noalloc: null temperature buffer");
   if (!std::isfinite(dt) || dt < 0.0) return noalloc_fail(ELM_ERR_ARG, "elm_advect_noalloc: dt must be finite and >= 0");
-  if (n_sub < 1 || n_sub > 64) return noalloc_fail(ELM_ERR_ARG, "elm_advect_noalloc: n_sub must be in 1..64");
+  if (n_sub < 1 || n_sub > elm::kMaxSub)
+    return noalloc_fail(ELM_ERR_ARG, "elm_advect_noalloc: n_sub must be in 1.." + std::to_string(elm::kMaxSub));
   if (me->n_storage > kNoAllocMaxNodes)
     return noalloc_fail(ELM_ERR_ARG, "elm_advect_noalloc: mesh has " + std::to_string(me->n_storage) +
                                          " storage nodes, more than the static scratch limit of " +

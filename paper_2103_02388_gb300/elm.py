@@ -143,6 +143,21 @@ class Mesh:
                                      float(dt), int(n_sub), _stream_ptr(stream)))
         return out
 
+    def advect_lookback(self, T_src: torch.Tensor, tau: float, b: int, n_sub: int = 1,
+                        out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Look-back distance b (Sec. 2.3.3) for a steady velocity: trace each
+        node back b steps of ``tau`` (``n_sub`` RK4 substeps per step) and
+        interpolate ``T_src`` = T^{n+1-b} there.  With T_src = T^0 and b = n+1
+        this is the b = infinity scheme.  The trace over b steps is one call
+        of ``advect`` with dt = b tau and b n_sub substeps."""
+        if self._u is None:
+            raise RuntimeError("set_velocity has not been called")
+        if self._u[0] is not self._u[1]:
+            raise ValueError("look-back over several steps needs a steady velocity")
+        if b < 1:
+            raise ValueError("b must be >= 1")
+        return self.advect(T_src, b * tau, b * n_sub, out=out, stream=stream)
+
     def advect_adjoint(self, T_old: torch.Tensor, gT_new: torch.Tensor, dt: float, n_sub: int = 1,
                        split: bool = True, stream=None):
         """Adjoint of ``advect`` for the current velocity: returns (gT_old,

@@ -9,7 +9,7 @@ import torch
 
 import oracle
 from _helpers import match_nodes
-from paper_2103_02388_gb300 import autograd, elm, inputs
+from paper_2103_02388_gb300 import _lib, autograd, elm, inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -158,6 +158,15 @@ def test_velocity_gradient_finite_differences_gpu():
         fm = P.from_gpu(P.gm.advect(Tg, dt, 1))
         fd = g @ (fp - fm) / (2 * e)
         assert abs((gU * v).sum() - fd) <= 1e-7 * (np.abs(g) @ np.abs((fp - fm) / (2 * e)) + 1e-30)
+
+
+def test_adjoint_substep_limit():
+    P = Pair(2, "fp64")
+    u, T = _fields(P, "linear")
+    P.gm.set_velocity(P.to_gpu(u))
+    g = P.to_gpu_owner(np.ones(P.om.n_nodes))
+    with pytest.raises(_lib.ElmError):
+        P.gm.advect_adjoint(P.to_gpu(T), g, 0.01, 65)    # above ELM_MAX_ADJOINT_SUBSTEPS
 
 
 def test_adjoint_is_deterministic():

@@ -438,3 +438,60 @@ def test_jvp_linear_fields_match_finite_differences(dim, n_sub, steady):
     inner = np.linalg.norm(x - c, axis=1) < 0.3
     assert inner.sum() > 20
     assert np.abs(fd[inner] - jvp[inner]).max() <= 1e-7 * max(1.0, np.abs(jvp[inner]).max())
+
+
+# ---------------------------------------------------------------------------
+# Look-back distance (Sec. 2.3.3): b = infinity traces every node back to
+# c0; for a steady velocity that is one backward trace over the whole time
+# with one RK4 substep per time step.
+# ---------------------------------------------------------------------------
+
+
+def _lookback_infinity(c0_fn, steps):
+    v, m = inputs.unit_square()
+    me = oracle.OracleMesh(v, m, 6)
+    x = me.coords
+    c0 = c0_fn(x)
+    T = me.advect(c0, inputs.rotation_2d(x, omega=1.0), 2 * np.pi, n_sub=steps)
+    return me.metrics(T, c0, c0)
+
+
+@pytest.mark.parametrize("row", [0, 1])
+def test_table2_hill_lookback_infinity(row):
+    with open(os.path.join(GOLDEN, "table2_hill_p2_binf.json")) as f:
+        ref = json.load(f)["rows"][row]
+    got = _lookback_infinity(inputs.hill, ref["steps"])
+    assert abs(got["h0"] / ref["h0"] - 1.0) < 0.02
+    assert abs(got["dm"] / ref["dm"] - 1.0) < 0.02
+    assert abs(got["var"] - ref["var"]) < 1e-4
+
+
+@pytest.mark.slow
+def test_table2_hill_lookback_infinity_roundoff():
+    with open(os.path.join(GOLDEN, "table2_hill_p2_binf.json")) as f:
+        ref = json.load(f)["rows"][2]
+    got = _lookback_infinity(inputs.hill, ref["steps"])
+    assert got["h0"] < 3 * ref["h0"] and abs(got["dm"]) < 1e-13
+
+
+def _table1_row(b):
+    with open(os.path.join(GOLDEN, "table1_three_bodies_p2.json")) as f:
+        return [r for r in json.load(f)["rows"] if r["b"] == b][0]
+
+
+@pytest.mark.slow
+def test_table1_three_bodies_lookback_infinity():
+    ref = _table1_row("infinity")
+    got = _lookback_infinity(inputs.three_bodies, ref["steps"])
+    assert abs(got["h0"] / ref["h0"] - 1.0) < 0.1
+    assert abs(got["var"] - ref["var"]) < 1e-4
+    assert abs(got["dm"] / ref["dm"] - 1.0) < 0.2
+
+
+@pytest.mark.slow
+def test_table1_three_bodies_b1():
+    ref = _table1_row(1)
+    got = _revolution(6, inputs.three_bodies, ref["steps"])
+    assert abs(got["h0"] / ref["h0"] - 1.0) < 0.02
+    assert abs(got["var"] - ref["var"]) < 0.01
+    assert abs(got["dm"] / ref["dm"] - 1.0) < 0.02

@@ -153,6 +153,39 @@ def test_accumulated_revolution_fp64():
     assert P.om.metrics(To, T0, T0)["h0"] < 0.03
 
 
+@pytest.mark.parametrize("precision,steps", [("fp64", 62), ("fp64", 628), ("fp32", 628)])
+def test_lookback_infinity(precision, steps):
+    """Look-back b = infinity (Sec. 2.3.3, Table 2): one revolution of the hill
+    traced back to c0 in a single call with one RK4 substep per time step.
+    FP64 within 1e-12 of the oracle.  FP32: each of the 4 * steps stage
+    updates of the offset (|d| <= 0.75) rounds by at most 2^-24 |d|, so the
+    departure point moves by at most 4 * 628 * 0.75 * 2^-24 ~ 1.1e-4 and T by
+    that times max |grad c0| = pi / (4 * 0.15) ~ 5.2: 6e-4 (linear worst
+    case, the oracle getting the FP32-rounded inputs)."""
+    P = Pair("square", 6, precision)
+    u = P.rounded(inputs.rotation_2d(P.x, omega=1.0))
+    c0 = P.rounded(inputs.hill(P.x))
+    P.gm.set_velocity(P.to_gpu(u))
+    out = P.gm.advect_lookback(P.to_gpu(c0), 2 * np.pi / steps, steps)
+    P.gm.status()
+    got = P.from_gpu(out)
+    ref = P.om.advect(c0, u, 2 * np.pi, n_sub=steps)
+    tol = TOL["fp64"] if precision == "fp64" else 6e-4
+    assert _err(got, ref, c0) <= tol
+    if precision == "fp64":
+        # the paper's error after one revolution (Table 2, b = infinity)
+        paper = {62: 9.62e-7, 628: 9.13e-11}[steps]
+        assert abs(P.om.metrics(got, c0, c0)["h0"] / paper - 1.0) < 0.02
+
+
+def test_lookback_needs_steady_velocity():
+    P = Pair("square", 2)
+    u = inputs.rotation_2d(P.x, omega=1.0)
+    P.gm.set_velocity(P.to_gpu(u), P.to_gpu(0.5 * u))
+    with pytest.raises(ValueError):
+        P.gm.advect_lookback(P.to_gpu(inputs.hill(P.x)), 0.1, 4)
+
+
 @pytest.mark.parametrize("precision,level,n_sub,cfl", [("fp64", 6, 2, 4.0), ("fp32", 7, 1, 4.0)])
 def test_full_size_sampled(precision, level, n_sub, cfl):
     """The benchmark sizes (3D level 6 FP64, level 7 FP32), checked on 3000
@@ -229,3 +262,5 @@ def test_argument_errors():
         gm.advect(T, float("nan"))
     with pytest.raises(_lib.ElmError):
         gm.advect(T, -1.0)
+    with pytest.raises(_lib.ElmError):
+        gm.advect(T, 0.1, n_sub=65537)                   # above ELM_MAX_SUBSTEPS
