@@ -5,7 +5,8 @@ Kohl et al., "A massively parallel Eulerian-Lagrangian method for
 advection-dominated transport in viscous fluids" (arXiv 2103.02388): Sec. 2.3.1
 steps (i)-(iii), Eq. (departure point) integrated by classic RK4, the time
 interpolation of Eq. (linear interpolation), the field evaluation of Sec. 2.3.2
-and the mass-matrix metrics of Sec. 3.1.
+with P1 or P2 elements (Sec. 3.1), traces continued over several time steps
+(look-back distance, Sec. 2.3.3) and the mass-matrix metrics of Sec. 3.1.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
 legs of ``bench.py`` may import this package.  It shares no code with the CUDA
@@ -45,7 +46,7 @@ def _load():
         lib = ctypes.CDLL(build())
         P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
         lib.orc_mesh_create.restype = P
-        lib.orc_mesh_create.argtypes = [I32, I64, P, I64, P, I32]
+        lib.orc_mesh_create.argtypes = [I32, I64, P, I64, P, I32, I32]
         lib.orc_mesh_destroy.argtypes = [P]
         lib.orc_num_nodes.restype = I64
         lib.orc_num_nodes.argtypes = [P]
@@ -55,6 +56,7 @@ def _load():
         lib.orc_locate.argtypes = [P, I64, P, P, P, P]
         lib.orc_eval.argtypes = [P, P, I32, I64, P, P, I32]
         lib.orc_departure.argtypes = [P, P, P, D, I32, I64, I64, P, I32]
+        lib.orc_trace.argtypes = [P, P, P, D, I32, I64, P, P, I32]
         lib.orc_advect.argtypes = [P, P, P, P, P, D, I32, I64, I64, I32]
         lib.orc_advect_nodes.argtypes = [P, P, P, P, D, I32, I64, P, P, I32]
         lib.orc_advect_transpose.argtypes = [P, P, P, P, P, D, I32]
@@ -62,7 +64,7 @@ def _load():
         lib.orc_mass_products.argtypes = [P, I32, P, P, P]
         lib.orc_micro_simplices.restype = I64
         lib.orc_micro_simplices.argtypes = [P, P, P]
-        lib.orc_p2_mass_unit.argtypes = [I32, P]
+        lib.orc_mass_unit.argtypes = [I32, I32, P]
         _lib = lib
     return _lib
 
@@ -80,21 +82,23 @@ def default_threads() -> int:
 
 
 class OracleMesh:
-    """Macro mesh refined to ``level`` with its global P2 nodes (Sec. 2.1, 2.2).
+    """Macro mesh refined to ``level`` with its global P2 (``order`` 2) or P1
+    (``order`` 1) nodes (Sec. 2.1, 2.2, 3.1).
 
     ``vertices``: [n_vertices, dim] float64; ``macros``: [n_macros, dim+1]
     vertex ids.  Node numbering is the oracle's own; tests map it onto the CUDA
     library's numbering by coordinates.
     """
 
-    def __init__(self, vertices, macros, level: int):
+    def __init__(self, vertices, macros, level: int, order: int = 2):
         lib = _load()
         self.vertices = _f64(vertices)
         self.macros = np.ascontiguousarray(macros, dtype=np.int64)
         self.dim = int(self.vertices.shape[1])
         self.level = int(level)
+        self.order = int(order)
         self._h = lib.orc_mesh_create(self.dim, self.vertices.shape[0], _ptr(self.vertices),
-                                      self.macros.shape[0], _ptr(self.macros), self.level)
+                                      self.macros.shape[0], _ptr(self.macros), self.level, self.order)
         if not self._h:
             raise ValueError("oracle: invalid mesh")
         self.n_nodes = int(lib.orc_num_nodes(self._h))
@@ -109,7 +113,7 @@ class OracleMesh:
 
     # -- structure ---------------------------------------------------------
     def macro_nodes(self, macro: int):
-        """Lattice coordinates p of the macro's P2 nodes and their node ids."""
+        """Lattice coordinates p of the macro's nodes and their node ids."""
         lib = _load()
         n = lib.orc_macro_nodes(self._h, macro, None, None)
         p = np.empty((n, self.dim), np.int32)
@@ -138,7 +142,7 @@ class OracleMesh:
 
     # -- field evaluation and the advection step ----------------------------
     def eval(self, field, pts, threads: int | None = None):
-        """P2 interpolant of ``field`` ([n_nodes] or [n_nodes, c]) at ``pts``."""
+        """P1 / P2 interpolant of ``field`` ([n_nodes] or [n_nodes, c]) at ``pts``."""
         field = _f64(field)
         ncomp = 1 if field.ndim == 1 else field.shape[1]
         pts = _f64(pts).reshape(-1, self.dim)
@@ -156,6 +160,18 @@ class OracleMesh:
         _load().orc_departure(self._h, _ptr(u_old), _ptr(u_new), float(dt), int(n_sub),
                               begin, end, _ptr(X), threads or default_threads())
         return X
+
+    def trace(self, X, u_old, dt, n_sub=1, u_new=None, threads=None):
+        """Continues backward traces from the points ``X`` ([n, dim]) over one
+        further interval of length dt whose velocity is u_old at its start and
+        u_new at its end (Sec. 2.3.3); returns the new points."""
+        X = _f64(X).reshape(-1, self.dim)
+        u_old = _f64(u_old)
+        u_new = u_old if u_new is None else _f64(u_new)
+        out = np.empty_like(X)
+        _load().orc_trace(self._h, _ptr(u_old), _ptr(u_new), float(dt), int(n_sub), X.shape[0],
+                          _ptr(X), _ptr(out), threads or default_threads())
+        return out
 
     def advect(self, T_old, u_old, dt, n_sub=1, u_new=None, begin=0, end=None, threads=None):
         """One MMOC advection step: T^{n+1}_i = T^n_h(X_i) for nodes [begin, end)."""
@@ -207,7 +223,7 @@ class OracleMesh:
 
     # -- metrics (Sec. 3.1) ---------------------------------------------------
     def mass_product(self, a, b=None):
-        """a^T M b with the P2 mass matrix M."""
+        """a^T M b with the mass matrix M of the mesh's element order."""
         a = _f64(a).reshape(self.n_nodes, 1)
         b = a if b is None else _f64(b).reshape(self.n_nodes, 1)
         out = np.empty(1)
@@ -229,9 +245,15 @@ class OracleMesh:
         }
 
 
+def mass_unit(dim: int, order: int = 2) -> np.ndarray:
+    """P1 / P2 mass matrix of a simplex with unit volume (P2: vertex basis
+    first, then edges)."""
+    nb = dim + 1 if order == 1 else (dim + 1) * (dim + 2) // 2
+    out = np.empty((nb, nb))
+    _load().orc_mass_unit(dim, int(order), _ptr(out))
+    return out
+
+
 def p2_mass_unit(dim: int) -> np.ndarray:
     """P2 mass matrix of a simplex with unit volume (vertex basis first, then edges)."""
-    nb = (dim + 1) * (dim + 2) // 2
-    out = np.empty((nb, nb))
-    _load().orc_p2_mass_unit(dim, _ptr(out))
-    return out
+    return mass_unit(dim, 2)

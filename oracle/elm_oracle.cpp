@@ -13,8 +13,9 @@
 //     vertices are taken in ascending global id order this refinement is the
 //     Freudenthal/Kuhn subdivision of the reference simplex
 //     {N >= q1 >= q2 >= q3 >= 0}, N = 2^L.
-//   * Sec. 2.2 (spaces S^m_l): P2 Lagrange nodes = micro vertices and edge
-//     midpoints; a global node is identified by the macro vertices it lies
+//   * Sec. 2.2 (spaces S^m_l) and Sec. 3.1 (linear or quadratic Lagrange
+//     elements): P2 nodes = micro vertices and edge midpoints, P1 nodes = micro
+//     vertices; a global node is identified by the macro vertices it lies
 //     between and its integer barycentric weights, so nodes shared by several
 //     macros are one unknown.
 //   * Eq. (characteristic curves) / Eq. (departure point): X(x, t_{n+1}, t_n)
@@ -25,11 +26,15 @@
 //   * Sec. 2.3.2, field evaluation: locate the macro (here: brute force over all
 //     macros, keeping the one with the largest minimum barycentric), locate the
 //     micro element in O(1) (floor + sort of the fractional parts), pull back to
-//     the micro element (solve its barycentric system) and sum the P2 basis.
+//     the micro element (solve its barycentric system) and sum the P1 or P2
+//     basis.
 //   * Step (iii): T^{n+1}_i = c^n_h(X_i) (kappa = 0, no diffusion).
-//   * Sec. 3.1: the error metrics need e^T M e with the P2 mass matrix M,
+//   * Sec. 3.1: the error metrics need e^T M e with the P1 / P2 mass matrix M,
 //     assembled here element by element from exact barycentric-monomial
 //     integrals.
+//   * Sec. 2.3.3 (look-back distance): a trace continued from given points
+//     over a further time interval with that interval's velocity pair, so a
+//     trace can span several time steps (b > 1) before T is evaluated.
 //   * Eq. (departure point), differentiated: forward-mode (dual number)
 //     directional derivatives of T^{n+1} with respect to the nodal velocity and
 //     the transpose of the interpolation for T^n, used to check adjoints.
@@ -102,7 +107,8 @@ bool barycentric(int d, const double V[4][3], const double* y, double* lam) {
 }
 
 // ---------------------------------------------------------------------------
-// Mesh: macro simplices, uniform refinement, P2 node numbering (Sec. 2.1, 2.2).
+// Mesh: macro simplices, uniform refinement, P1 / P2 node numbering (Sec. 2.1,
+// 2.2).
 // ---------------------------------------------------------------------------
 
 struct Macro {
@@ -111,7 +117,8 @@ struct Macro {
 };
 
 struct Mesh {
-  int d = 0, L = 0, N = 0, M = 0;   // dimension, level, N = 2^L, M = 2N
+  int d = 0, L = 0, N = 0, M = 0;   // dimension, level, N = 2^L, M = order * N
+  int order = 2;                     // 1: P1 (nodes = micro vertices), 2: P2
   std::vector<Macro> mac;
   std::vector<std::vector<int32_t>> id;  // per macro: dense (M+1)^d table p -> node
   std::vector<double> X;                 // node coordinates, [n_nodes, d]
@@ -158,13 +165,16 @@ void for_each_lattice_point(int d, int M, F&& f) {
   }
 }
 
-Mesh* build_mesh(int d, int64_t nv, const double* xyz, int64_t nm, const int64_t* mv, int level) {
-  if ((d != 2 && d != 3) || nv <= 0 || nm <= 0 || level < 0 || level > 8) return nullptr;
+Mesh* build_mesh(int d, int64_t nv, const double* xyz, int64_t nm, const int64_t* mv, int level, int order) {
+  if ((d != 2 && d != 3) || nv <= 0 || nm <= 0 || level < 0 || (order != 1 && order != 2)) return nullptr;
+  // dense per-macro node tables of (M + 1)^d entries: M <= 1024 (2D), 256 (3D)
+  if (level > 12 || (order << level) > (d == 2 ? 1024 : 256)) return nullptr;
   Mesh* me = new Mesh();
   me->d = d;
   me->L = level;
+  me->order = order;
   me->N = 1 << level;
-  me->M = 2 * me->N;
+  me->M = order * me->N;
   for (int r = 0; r < d; ++r) {
     me->lo[r] = std::numeric_limits<double>::infinity();
     me->hi[r] = -std::numeric_limits<double>::infinity();
@@ -184,7 +194,7 @@ Mesh* build_mesh(int d, int64_t nv, const double* xyz, int64_t nm, const int64_t
       for (int r = 0; r < d; ++r) mc.P[k][r] = xyz[mc.v[k] * d + r];
     }
   }
-  // Global P2 node numbering.  Interior lattice points (all weights > 0) belong
+  // Global node numbering.  Interior lattice points (all weights > 0) belong
   // to one macro only; points on a macro face, edge or vertex are keyed by the
   // (vertex id, weight) pairs with non-zero weight so that all macros sharing
   // them agree on one node.
@@ -314,6 +324,7 @@ void locate(const Mesh& me, double* y, Located& out) {
 // The (d+1)(d+2)/2 P2 nodes of a located micro simplex with their basis values:
 // vertex v -> mu_v (2 mu_v - 1); edge (a, b) -> 4 mu_a mu_b  (Sec. 2.2, P2).
 int p2_stencil(const Mesh& me, const Located& lc, int32_t* node, double* phi) {
+  if (me.order != 2) return 0;
   const int d = me.d;
   int n = 0;
   for (int v = 0; v <= d; ++v) {
@@ -334,13 +345,28 @@ int p2_stencil(const Mesh& me, const Located& lc, int32_t* node, double* phi) {
   return n;
 }
 
-// Evaluates an ncomp-component P2 field (node-major [n_nodes, ncomp]) at y.
+// The d+1 P1 nodes of a located micro simplex (its vertices, lattice = the
+// level-L grid) with their basis values mu_v (Sec. 3.1, linear elements).
+int p1_stencil(const Mesh& me, const Located& lc, int32_t* node, double* phi) {
+  if (me.order != 1) return 0;
+  for (int v = 0; v <= me.d; ++v) {
+    node[v] = me.id[lc.macro][me.dense(lc.w[v])];
+    phi[v] = lc.mu[v];
+  }
+  return me.d + 1;
+}
+
+int stencil(const Mesh& me, const Located& lc, int32_t* node, double* phi) {
+  return me.order == 1 ? p1_stencil(me, lc, node, phi) : p2_stencil(me, lc, node, phi);
+}
+
+// Evaluates an ncomp-component P1 / P2 field (node-major [n_nodes, ncomp]) at y.
 void eval_field(const Mesh& me, const double* F, int ncomp, double* y, double* out) {
   Located lc;
   locate(me, y, lc);
   int32_t node[10];
   double phi[10];
-  int n = p2_stencil(me, lc, node, phi);
+  int n = stencil(me, lc, node, phi);
   for (int c = 0; c < ncomp; ++c) {
     double s = 0.0;
     for (int j = 0; j < n; ++j) s += phi[j] * F[int64_t(node[j]) * ncomp + c];
@@ -374,7 +400,8 @@ void velocity_at(const Mesh& me, const Velocity& V, double back, double* y, doub
   for (int r = 0; r < d; ++r) k[r] = w_old * a[r] + w_new * b[r];
 }
 
-// Traces node position x back over dt with n_sub RK4 substeps; writes X.
+// Traces the point x (a node, or the end of an earlier trace) back over dt
+// with n_sub RK4 substeps; writes X.
 void departure_point(const Mesh& me, const Velocity& V, int n_sub, const double* x, double* X) {
   const int d = me.d;
   const double h = V.dt / n_sub;
@@ -415,7 +442,7 @@ void parallel_for(int64_t begin, int64_t end, int nthreads, F&& f) {
 }
 
 // ---------------------------------------------------------------------------
-// P2 mass matrix (Sec. 3.1 metrics), exact via barycentric monomial integrals:
+// P1 / P2 mass matrix (Sec. 3.1 metrics), exact via barycentric monomial integrals:
 // int_T lam_0^a0 ... lam_d^ad = d! |T| a0! ... ad! / (d + sum a)!.
 // ---------------------------------------------------------------------------
 
@@ -423,9 +450,13 @@ struct Poly {  // polynomial in the d+1 barycentric coordinates
   std::map<std::array<int, 4>, double> c;
 };
 
-Poly basis_poly(int d, int i) {
+Poly basis_poly(int d, int order, int i) {
   Poly P;
-  if (i <= d) {  // vertex: 2 lam_i^2 - lam_i
+  if (order == 1) {  // P1 vertex: lam_i
+    std::array<int, 4> e1{0, 0, 0, 0};
+    e1[i] = 1;
+    P.c[e1] += 1.0;
+  } else if (i <= d) {  // P2 vertex: 2 lam_i^2 - lam_i
     std::array<int, 4> e2{0, 0, 0, 0}, e1{0, 0, 0, 0};
     e2[i] = 2;
     e1[i] = 1;
@@ -448,12 +479,14 @@ Poly basis_poly(int d, int i) {
 
 double factorial(int n) { double f = 1.0; for (int i = 2; i <= n; ++i) f *= i; return f; }
 
+int n_basis(int d, int order) { return order == 1 ? d + 1 : (d + 1) * (d + 2) / 2; }
+
 // Mass matrix of the reference simplex scaled to unit volume |T| = 1.
-void p2_mass_unit(int d, double* Mref) {
-  const int nb = (d + 1) * (d + 2) / 2;
+void mass_unit(int d, int order, double* Mref) {
+  const int nb = n_basis(d, order);
   for (int i = 0; i < nb; ++i)
     for (int j = 0; j < nb; ++j) {
-      Poly A = basis_poly(d, i), B = basis_poly(d, j);
+      Poly A = basis_poly(d, order, i), B = basis_poly(d, order, j);
       double s = 0.0;
       for (auto& ta : A.c)
         for (auto& tb : B.c) {
@@ -588,12 +621,16 @@ void eval_field_dual(const Mesh& me, const double* F, const double* dF, int ncom
   barycentric_dual(d, V, y, mu);
   int32_t node[10];
   double phi_unused[10];
-  const int n = p2_stencil(me, lc, node, phi_unused);
+  const int n = stencil(me, lc, node, phi_unused);
   Dual phi[10];
   int k = 0;
-  for (int v = 0; v <= d; ++v) phi[k++] = mu[v] * (2.0 * mu[v] - Dual{1.0, 0.0});
-  for (int a = 0; a <= d; ++a)
-    for (int b = a + 1; b <= d; ++b) phi[k++] = 4.0 * (mu[a] * mu[b]);
+  if (me.order == 1) {
+    for (int v = 0; v <= d; ++v) phi[k++] = mu[v];
+  } else {
+    for (int v = 0; v <= d; ++v) phi[k++] = mu[v] * (2.0 * mu[v] - Dual{1.0, 0.0});
+    for (int a = 0; a <= d; ++a)
+      for (int b = a + 1; b <= d; ++b) phi[k++] = 4.0 * (mu[a] * mu[b]);
+  }
   for (int c = 0; c < ncomp; ++c) {
     Dual s{0.0, 0.0};
     for (int j = 0; j < n; ++j) {
@@ -656,8 +693,8 @@ void departure_point_dual(const Mesh& me, const VelocityDual& V, int n_sub, cons
 // ---------------------------------------------------------------------------
 extern "C" {
 
-void* orc_mesh_create(int dim, int64_t nv, const double* xyz, int64_t nm, const int64_t* mv, int level) {
-  return build_mesh(dim, nv, xyz, nm, mv, level);
+void* orc_mesh_create(int dim, int64_t nv, const double* xyz, int64_t nm, const int64_t* mv, int level, int order) {
+  return build_mesh(dim, nv, xyz, nm, mv, level, order);
 }
 
 void orc_mesh_destroy(void* h) { delete static_cast<Mesh*>(h); }
@@ -669,7 +706,7 @@ void orc_node_coords(void* h, double* out) {
   std::memcpy(out, me->X.data(), me->X.size() * sizeof(double));
 }
 
-// Lattice coordinates p (M >= p1 >= ... >= pd >= 0) of the macro's P2 nodes, in
+// Lattice coordinates p (M >= p1 >= ... >= pd >= 0) of the macro's nodes, in
 // the order (p1, p2, p3) lexicographic, with the global node number of each.
 int64_t orc_macro_nodes(void* h, int64_t macro, int32_t* p_out, int32_t* node_out) {
   Mesh* me = static_cast<Mesh*>(h);
@@ -700,7 +737,7 @@ void orc_locate(void* h, int64_t npts, const double* pts, int64_t* macro, int32_
   }
 }
 
-// P2 interpolation of a field ([n_nodes, ncomp]) at arbitrary points.
+// P1 / P2 interpolation of a field ([n_nodes, ncomp]) at arbitrary points.
 void orc_eval(void* h, const double* F, int ncomp, int64_t npts, const double* pts, double* out, int nthreads) {
   Mesh* me = static_cast<Mesh*>(h);
   const int d = me->d;
@@ -720,6 +757,22 @@ void orc_departure(void* h, const double* u_old, const double* u_new, double dt,
   Velocity V{u_old, u_new, dt};
   parallel_for(begin, end, nthreads, [&](int64_t i) {
     departure_point(*me, V, n_sub, &me->X[i * d], X + (i - begin) * d);
+  });
+}
+
+// Continues backward traces (Sec. 2.3.3): each point X_in[k] is traced back
+// over dt with the velocity pair (u_old at the start of the interval, u_new
+// at its end) and n_sub RK4 substeps; X_out[k] receives the new point.
+void orc_trace(void* h, const double* u_old, const double* u_new, double dt, int n_sub, int64_t npts,
+               const double* X_in, double* X_out, int nthreads) {
+  Mesh* me = static_cast<Mesh*>(h);
+  const int d = me->d;
+  Velocity V{u_old, u_new, dt};
+  parallel_for(0, npts, nthreads, [&](int64_t i) {
+    double x[3];
+    for (int r = 0; r < d; ++r) x[r] = X_in[i * d + r];
+    clamp_to_box(*me, x);
+    departure_point(*me, V, n_sub, x, X_out + i * d);
   });
 }
 
@@ -784,7 +837,7 @@ void orc_advect_transpose(void* h, const double* u_old, const double* u_new, con
     locate(*me, X, lc);
     int32_t node[10];
     double phi[10];
-    int n = p2_stencil(*me, lc, node, phi);
+    int n = stencil(*me, lc, node, phi);
     for (int j = 0; j < n; ++j) g_old[node[j]] += phi[j] * g_new[i];
   }
 }
@@ -794,9 +847,9 @@ void orc_advect_transpose(void* h, const double* u_old, const double* u_new, con
 void orc_mass_products(void* h, int nvec, const double* a, const double* b, double* out) {
   Mesh* me = static_cast<Mesh*>(h);
   const int d = me->d;
-  const int nb = (d + 1) * (d + 2) / 2;
+  const int nb = n_basis(d, me->order);
   std::vector<double> Mref(nb * nb);
-  p2_mass_unit(d, Mref.data());
+  mass_unit(d, me->order, Mref.data());
   for (int k = 0; k < nvec; ++k) out[k] = 0.0;
   for_each_micro_simplex(*me, [&](int64_t m, int w[4][3]) {
     Located lc;
@@ -806,7 +859,7 @@ void orc_mass_products(void* h, int nvec, const double* a, const double* b, doub
     for (int j = 0; j < 4; ++j) lc.mu[j] = 0.0;
     int32_t node[10];
     double phi[10];
-    p2_stencil(*me, lc, node, phi);
+    stencil(*me, lc, node, phi);
     double V[4][3];
     for (int j = 0; j <= d; ++j) {
       int wt[4];
@@ -839,7 +892,7 @@ int64_t orc_micro_simplices(void* h, int64_t* macro, int32_t* wv) {
   return n;
 }
 
-// Reference P2 mass matrix for a simplex of unit volume ([nb, nb]).
-void orc_p2_mass_unit(int d, double* out) { p2_mass_unit(d, out); }
+// Reference P1 / P2 mass matrix for a simplex of unit volume ([nb, nb]).
+void orc_mass_unit(int d, int order, double* out) { mass_unit(d, order, out); }
 
 }  // extern "C"

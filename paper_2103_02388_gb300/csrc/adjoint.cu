@@ -394,10 +394,7 @@ __global__ void __launch_bounds__(kAdvectThreads)
     for (int k = 1; k < D; ++k) iface = iface || t.p[k] == t.p[k - 1];
     if (iface) {
       const int64_t own = args.owner_mp[args.unique_map[slot]];
-      t.m0 = int(own >> 32);
-      t.p[0] = int(own >> 20) & 1023;
-      t.p[1] = int(own >> 10) & 1023;
-      if (D == 3) t.p[D - 1] = int(own) & 1023;
+      t.m0 = unpack_owner<D>(own, t.p);
     }
   }
 #pragma unroll

@@ -72,7 +72,7 @@ struct AdvectArgs {
   int n_sub;
   unsigned* status;
   const int64_t* unique_map;  // storage slot -> unique id
-  const int64_t* owner_mp;    // unique id -> owner (macro << 32 | p1 << 20 | p2 << 10 | p3)
+  const int64_t* owner_mp;    // unique id -> owner record (pack_owner)
   const int4* chunks;         // (macro, p1, first index in slab, count) per thread block
   int n_chunks;
   StepConsts<float> k32;
@@ -95,7 +95,7 @@ struct elm_mesh_s {
   elm::MacroGeo32* d_geo32 = nullptr;
   int64_t* d_unique_map = nullptr;
   int64_t* d_owner = nullptr;
-  int64_t* d_owner_mp = nullptr;     // unique id -> owner (macro << 32 | p1 << 20 | p2 << 10 | p3)
+  int64_t* d_owner_mp = nullptr;     // unique id -> owner record (pack_owner)
   int4* d_chunks = nullptr;          // work list: one block-sized run of a slab each
   int64_t n_chunks = 0;
   void* d_u4[2] = {nullptr, nullptr};  // packed velocity records u_old, u_new
@@ -141,6 +141,22 @@ constexpr int kAdvectThreads = 128;
 // ---------------------------------------------------------------------------
 // Batched form: many independent meshes in one persistent launch.
 // ---------------------------------------------------------------------------
+// Owner record of a unique node: its owner macro and the owner's lattice
+// point (p1, p2[, p3]) in 11-bit fields, enough for lattice coordinates up
+// to 2047 (the largest lattice is 2^10 in 2D).
+constexpr int kOwnerBits = 11;
+constexpr int kOwnerMask = (1 << kOwnerBits) - 1;
+__host__ __device__ inline int64_t pack_owner(int64_t macro, int p1, int p2, int p3) {
+  return (macro << (3 * kOwnerBits)) | (int64_t(p1) << (2 * kOwnerBits)) | (int64_t(p2) << kOwnerBits) | p3;
+}
+template <int D>
+__host__ __device__ inline int unpack_owner(int64_t own, int* p) {
+  p[0] = int(own >> (2 * kOwnerBits)) & kOwnerMask;
+  p[1] = int(own >> kOwnerBits) & kOwnerMask;
+  if (D == 3) p[D - 1] = int(own) & kOwnerMask;
+  return int(own >> (3 * kOwnerBits));
+}
+
 constexpr int kMaxBatch = 128;
 constexpr int kMaxSub = ELM_MAX_SUBSTEPS;
 constexpr int kMaxAdjointSub = ELM_MAX_ADJOINT_SUBSTEPS;

@@ -209,23 +209,23 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
   if (me->host_only) return ELM_OK;
 
   // Device tables.
-  // Owner lattice points, packed (macro << 32 | p1 << 20 | p2 << 10 | p3).
+  // Owner records (elm::pack_owner): the owner macro and its lattice point.
   std::vector<int64_t> slot_p(me->npm);
   {
     int64_t k = 0;
     if (d == 2) {
       for (int p1 = 0; p1 <= M; ++p1)
-        for (int p2 = 0; p2 <= p1; ++p2) slot_p[k++] = (int64_t(p1) << 20) | (int64_t(p2) << 10);
+        for (int p2 = 0; p2 <= p1; ++p2) slot_p[k++] = elm::pack_owner(0, p1, p2, 0);
     } else {
       for (int p1 = 0; p1 <= M; ++p1)
         for (int p2 = 0; p2 <= p1; ++p2)
-          for (int p3 = 0; p3 <= p2; ++p3) slot_p[k++] = (int64_t(p1) << 20) | (int64_t(p2) << 10) | p3;
+          for (int p3 = 0; p3 <= p2; ++p3) slot_p[k++] = elm::pack_owner(0, p1, p2, p3);
     }
   }
   std::vector<int64_t> owner_mp(me->n_unique);
   for (int64_t u = 0; u < me->n_unique; ++u) {
     const int64_t m = me->owner[u] / me->npm;
-    owner_mp[u] = (m << 32) | slot_p[me->owner[u] - m * me->npm];
+    owner_mp[u] = elm::pack_owner(m, 0, 0, 0) | slot_p[me->owner[u] - m * me->npm];
   }
   // Work list: each slab p1 of each macro split into runs of kAdvectThreads
   // nodes (slab p1 holds (p1+1)(p1+2)/2 nodes in 3D, p1+1 in 2D).

@@ -652,10 +652,7 @@ __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab
     for (int k = 1; k < D; ++k) iface = iface || t.p[k] == t.p[k - 1];
     if (iface) {
       const int64_t own = job.owner_mp[job.unique_map[slot]];
-      t.m0 = int(own >> 32);
-      t.p[0] = int(own >> 20) & 1023;
-      t.p[1] = int(own >> 10) & 1023;
-      if (D == 3) t.p[D - 1] = int(own) & 1023;
+      t.m0 = unpack_owner<D>(own, t.p);
     }
   }
   {

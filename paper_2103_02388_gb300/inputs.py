@@ -225,6 +225,19 @@ def three_bodies(x):
     return slotted_cylinder(x) + cone(x) + hill(x)
 
 
+def half_space(x, cut: float = 0.5):
+    """The initial condition of Sec. 3.3: 1 where x_1 < cut, else 0."""
+    x = np.asarray(x, dtype=np.float64)
+    return (x[:, 0] < cut).astype(np.float64)
+
+
+def random_linear(x, seed: int):
+    """A seeded random affine function a + b . x (in the P1 space exactly)."""
+    x = np.asarray(x, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal() + x @ rng.standard_normal(x.shape[1])
+
+
 def random_quadratic(x, seed: int):
     """A seeded random quadratic polynomial q(x) (in the P2 space exactly)."""
     x = np.asarray(x, dtype=np.float64)

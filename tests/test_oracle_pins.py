@@ -495,3 +495,159 @@ def test_table1_three_bodies_b1():
     assert abs(got["h0"] / ref["h0"] - 1.0) < 0.02
     assert abs(got["var"] - ref["var"]) < 0.01
     assert abs(got["dm"] / ref["dm"] - 1.0) < 0.02
+
+
+# ---------------------------------------------------------------------------
+# Linear (P1) elements (Sec. 3.1: "linear (P1) or quadratic (P2) Lagrangian
+# finite element discretizations"): nodes are the micro vertices.
+# ---------------------------------------------------------------------------
+
+
+def _setup_p1(dim, level, perturbed=False):
+    if dim == 2:
+        v, m = inputs.square_block(2, 0.3, 7) if perturbed else inputs.unit_square()
+    else:
+        v, m = inputs.cube_block(2, 0.3, 7) if perturbed else inputs.unit_cube()
+    return oracle.OracleMesh(v, m, level, order=1)
+
+
+@pytest.mark.parametrize("dim,level", [(2, 0), (2, 4), (3, 0), (3, 3)])
+def test_p1_node_count_and_lattice(dim, level):
+    """P1 nodes of the refined unit square / cube are the (N+1)^d lattice."""
+    me = _setup_p1(dim, level)
+    N = 2 ** level
+    assert me.n_nodes == (N + 1) ** dim
+    lat = np.rint(me.coords * N)
+    assert np.abs(lat - me.coords * N).max() < 1e-12
+    assert len({tuple(r) for r in lat.astype(int)}) == me.n_nodes
+
+
+def test_p1_mass_matrix_textbook():
+    """Unit-volume simplex: M_ii = 2 / ((d+1)(d+2)), M_ij = 1 / ((d+1)(d+2))."""
+    for dim in (2, 3):
+        M = oracle.mass_unit(dim, 1)
+        k = (dim + 1) * (dim + 2)
+        expect = (np.ones((dim + 1, dim + 1)) + np.eye(dim + 1)) / k
+        assert np.abs(M - expect).max() < 1e-15
+
+
+def test_p1_mass_product_integrates_linears():
+    """a^T M b with the P1 mass matrix is the integral of the interpolants:
+    exact for the coordinate functions, which P1 reproduces."""
+    me = _setup_p1(3, 2, perturbed=True)
+    x = me.coords
+    one = np.ones(me.n_nodes)
+    assert abs(me.mass_product(one) - 1.0) < 1e-13
+    assert abs(me.mass_product(one, x[:, 2]) - 1 / 2) < 1e-13
+    assert abs(me.mass_product(x[:, 0], x[:, 1]) - 1 / 4) < 1e-13
+    assert abs(me.mass_product(x[:, 1], x[:, 1]) - 1 / 3) < 1e-13
+
+
+@pytest.mark.parametrize("dim,level,perturbed", [(2, 3, False), (3, 2, False), (3, 1, True), (2, 2, True)])
+def test_p1_reproduction_uniform_velocity(dim, level, perturbed):
+    """Linear T and uniform u: T_new(x_i) = l(clamp(x_i - u dt)) exactly, and
+    a constant T stays constant (partition of unity)."""
+    me = _setup_p1(dim, level, perturbed)
+    x = me.coords
+    U = np.array([0.37, -0.21, 0.11][:dim])
+    u = inputs.uniform_field(x, U)
+    T = inputs.random_linear(x, seed=9)
+    for dt, n_sub in ((0.3, 1), (0.45, 3)):
+        Tn = me.advect(T, u, dt, n_sub=n_sub)
+        expect = inputs.random_linear(_clamp01(x - U * dt), seed=9)
+        assert np.abs(Tn - expect).max() <= 1e-13 * np.abs(T).max()
+    uf = inputs.random_fourier(x, seed=3)
+    Tc = me.advect(np.full(me.n_nodes, -2.75), uf, inputs.dt_for_cfl(3.0, level, uf), n_sub=2)
+    assert np.abs(Tc + 2.75).max() <= 16 * EPS * 2.75
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_p1_interpolation_brute_force(dim):
+    """P1 evaluation at random points reproduces linears, and equals the
+    barycentric combination of the vertex values of a containing micro simplex
+    found by brute force."""
+    me = _setup_p1(dim, 2, perturbed=True)
+    rng = np.random.default_rng(5)
+    pts = rng.uniform(0, 1, size=(300, dim))
+    F = inputs.random_linear(me.coords, seed=2)
+    assert np.abs(me.eval(F, pts) - inputs.random_linear(pts, seed=2)).max() <= 1e-13 * np.abs(F).max()
+    G = np.sin(5.0 * me.coords[:, 0]) + me.coords[:, 1] ** 2
+    got = me.eval(G, pts)
+    x = me.coords
+    simplices = _all_micro_simplices_physical(me.vertices, me.macros, 2)
+    lookup = {tuple(np.round(p, 12)): i for i, p in enumerate(x)}
+    for y, g in zip(pts[:60], got[:60]):
+        for _, _, V in simplices:
+            A = np.vstack([V.T, np.ones(dim + 1)])
+            lam = np.linalg.solve(A, np.append(y, 1.0))
+            if lam.min() >= -1e-12:
+                ids = [lookup[tuple(np.round(vtx, 12))] for vtx in V]
+                assert abs(lam @ G[ids] - g) < 1e-12
+                break
+        else:
+            raise AssertionError("no containing micro simplex")
+
+
+def _table1_p1_row(b):
+    with open(os.path.join(GOLDEN, "table1_three_bodies_p1.json")) as f:
+        return [r for r in json.load(f)["rows"] if r["b"] == b][0]
+
+
+def _lookback_chain(me, c0, u, steps, b):
+    """T at t = steps * tau with look-back b (Sec. 2.3.3) for a steady u:
+    T^{n+1} comes from T^{n+1-b}, so the final value is a chain that starts
+    with a trace of (steps mod b) steps from c0 followed by traces of b steps;
+    a trace over k steps of a steady field is one trace over k tau with k
+    RK4 substeps."""
+    tau = 2 * np.pi / steps
+    T = c0.copy()
+    first = steps % b
+    for k in ([first] if first else []) + [b] * (steps // b):
+        T = me.advect(T, u, k * tau, n_sub=k)
+    return T
+
+
+@pytest.mark.parametrize("b", [100, 1000, "infinity"])
+def test_table1_three_bodies_p1(b):
+    """Table 1, P1 rows: H0 to 2%, var to 0.002; b = infinity at round-off."""
+    ref = _table1_p1_row(b)
+    me = _setup_p1(2, 7)
+    x = me.coords
+    c0 = inputs.three_bodies(x)
+    u = inputs.rotation_2d(x, omega=1.0)
+    steps = ref["steps"]
+    T = _lookback_chain(me, c0, u, steps, steps if b == "infinity" else b)
+    got = me.metrics(T, c0, c0)
+    if b == "infinity":
+        assert got["h0"] < 3 * ref["h0"] and abs(got["dm"]) < 1e-13
+        assert abs(got["var"] - 1.0) < 1e-12
+    else:
+        assert abs(got["h0"] / ref["h0"] - 1.0) < 0.02
+        assert abs(got["var"] - ref["var"]) < 0.002
+        assert abs(got["dm"]) < 1e-3
+
+
+def test_table3_swirl_p1_level5():
+    """Table 3 (swirling flow, time-dependent u, b = infinity, P1, 33^3 nodes):
+    each node is traced back over every interval [t_{k-1}, t_k] with that
+    interval's velocity pair, then c0 is evaluated.  The paper's exact values
+    depend on details it does not state; the pin is the magnitude (H0 within
+    a factor 3 of each printed value), var = 1 and |dm| < 3e-4.  Dropping the
+    time interpolation (only u^k or only u^{k-1} per interval) misses by two
+    orders of magnitude."""
+    with open(os.path.join(GOLDEN, "table3_swirl_p1_binf.json")) as f:
+        rows = [r for r in json.load(f)["rows"] if r["dofs"] == 35937]
+    v, m = inputs.unit_cube()
+    me = oracle.OracleMesh(v, m, 5, order=1)
+    x = me.coords
+    c0 = inputs.half_space(x)
+    for ref in rows:
+        tau = ref["tau"]
+        K = int(round(1.5 / tau))
+        X = x.copy()
+        for k in range(K, 0, -1):
+            X = me.trace(X, inputs.swirl_3d(x, (k - 1) * tau), tau, 1, u_new=inputs.swirl_3d(x, k * tau))
+        got = me.metrics(me.eval(c0, X), c0, c0)
+        assert ref["h0"] / 3 < got["h0"] < 3 * ref["h0"]
+        assert abs(got["var"] - 1.0) < 1e-12
+        assert abs(got["dm"]) < 3e-4

@@ -153,6 +153,26 @@ def test_accumulated_revolution_fp64():
     assert P.om.metrics(To, T0, T0)["h0"] < 0.03
 
 
+def test_largest_2d_level_interfaces():
+    """2D level 9: lattice coordinates reach 1024, the widest owner record.
+    Storage copies agree and sampled nodes (all of the diagonal interface,
+    both corners on it) match the oracle."""
+    P = Pair("square", 9)
+    u = inputs.rotation_2d(P.x, omega=1.0) + 0.1
+    T = inputs.hill(P.x)
+    dt = inputs.dt_for_cfl(3.0, 9, u)
+    P.gm.set_velocity(P.to_gpu(u))
+    out = P.gm.advect(P.to_gpu(T), dt, 1)
+    P.gm.status()
+    umap = torch.tensor(P.gm.unique_map(), device="cuda")
+    assert torch.equal(P.gm.to_unique(out)[umap], out), "storage copies of a node disagree"
+    got = P.from_gpu(out)
+    diag = np.flatnonzero(np.abs(P.x[:, 0] - P.x[:, 1]) < 1e-12)
+    idx = np.union1d(diag, np.random.default_rng(0).choice(P.om.n_nodes, 2000, replace=False))
+    ref = P.om.advect_nodes(T, u, dt, idx, 1)
+    assert np.abs(got[idx] - ref).max() <= TOL["fp64"] * np.abs(T).max()
+
+
 @pytest.mark.parametrize("precision,steps", [("fp64", 62), ("fp64", 628), ("fp32", 628)])
 def test_lookback_infinity(precision, steps):
     """Look-back b = infinity (Sec. 2.3.3, Table 2): one revolution of the hill
