@@ -4,16 +4,21 @@
  * Method: Kohl, Mohr, Eibl, Ruede, "A massively parallel Eulerian-Lagrangian
  * method for advection-dominated transport in viscous fluids" (arXiv
  * 2103.02388).  The library computes lines 3-4 of Algorithm 1 (departure
- * points and advection, no diffusion): for every P2 node x_i of a mesh of
- * macro triangles / tetrahedra refined uniformly L times (Sec. 2.1), the
- * departure point X(x_i, t_{n+1}, t_n) of Eq. (departure point) by classic
- * RK4 backwards in time through the P2 velocity, linearly interpolated in
+ * points and advection, no diffusion): for every P2 (or P1) node x_i of a
+ * mesh of macro triangles / tetrahedra refined uniformly L times (Sec. 2.1),
+ * the departure point X(x_i, t_{n+1}, t_n) of Eq. (departure point) by classic
+ * RK4 backwards in time through the P2 (P1) velocity, linearly interpolated in
  * time (Eq. linear interpolation), then T^{n+1}_i = T^n_h(X_i) (Sec. 2.3.1,
  * step (iii)).
  *
  * Conventions shared by every call:
+ *  - Elements: P2 (quadratic Lagrange, nodes = micro vertices and edge
+ *    midpoints) by default, or P1 (linear, nodes = micro vertices) with
+ *    ELM_P1 (Sec. 3.1: linear or quadratic elements for the temperature and
+ *    the velocity).  M = 2^(L+1) node lattice points per macro edge for P2,
+ *    M = 2^L for P1.
  *  - Node vectors live in STORAGE layout: macro after macro, each macro's
- *    P2 nodes p = (p1 >= p2 [>= p3] >= 0), p1 <= 2^(L+1), packed row by row
+ *    nodes p = (p1 >= p2 [>= p3] >= 0), p1 <= M, packed row by row
  *    (index p1(p1+1)(p1+2)/6 + p2(p2+1)/2 + p3 in 3D, p1(p1+1)/2 + p2 in 2D).
  *    Nodes on macro interfaces appear once per macro that holds them; the
  *    copy in the lowest-numbered macro is the owner.  elm_mesh_unique_map
@@ -64,6 +69,14 @@ enum { ELM_HOST_ONLY = 0x100 };
  * storage node). */
 enum { ELM_ADJOINT = 0x200 };
 
+/* Flag OR-ed into `precision` of elm_mesh_create: linear (P1) elements for
+ * the velocity and the scalar instead of quadratic (P2) ones (Sec. 3.1, test
+ * setup; Tables 1 and 3 use P1).  The location is the same; a field is
+ * evaluated from the d+1 vertices of the micro simplex with the micro
+ * barycentrics as basis.  Not combinable with ELM_ADJOINT; P1 meshes are not
+ * accepted by elm_batch_create. */
+enum { ELM_P1 = 0x400 };
+
 /* Builds the refined mesh (Sec. 2.1: coarse mesh T_0 refined uniformly after
  * Bey; Sec. 2.3.1, grid data structure: one DoF owner per interface node).
  *  dim            2 (triangles) or 3 (tetrahedra).
@@ -71,8 +84,9 @@ enum { ELM_ADJOINT = 0x200 };
  *  macro_vertices host, [n_macros, dim+1] vertex ids in [0, n_vertices).  The
  *                 order within a macro is irrelevant: vertices are sorted by
  *                 id, which makes the refinement conforming across faces.
- *  level          0..9 in 2D, 0..7 in 3D.
- *  precision      ELM_FP64 or ELM_FP32, optionally | ELM_HOST_ONLY.
+ *  level          P2: 0..9 in 2D, 0..7 in 3D; P1: 0..10 in 2D, 0..8 in 3D.
+ *  precision      ELM_FP64 or ELM_FP32, optionally | ELM_HOST_ONLY,
+ *                 | ELM_ADJOINT, | ELM_P1.
  * Copies everything it needs; allocates the mesh's device tables on the
  * current device.  Returns ELM_ERR_TOPOLOGY for a degenerate macro or a
  * non-manifold face.  *out is set only on success. */
@@ -86,7 +100,7 @@ elm_status elm_mesh_destroy(elm_mesh mesh);
 /* Storage length n of every node vector of this mesh (0 for a null mesh). */
 int64_t elm_mesh_num_nodes(elm_mesh mesh);
 
-/* Number of distinct (unique) P2 nodes. */
+/* Number of distinct (unique) nodes. */
 int64_t elm_mesh_num_unique(elm_mesh mesh);
 
 /* Node coordinates in storage order into host_out [n, dim] doubles. */
@@ -101,12 +115,12 @@ elm_status elm_mesh_unique_map(elm_mesh mesh, int64_t* host_out);
 elm_status elm_to_storage(elm_mesh mesh, const void* unique_dev, void* storage_dev, int ncomp, void* stream);
 elm_status elm_to_unique(elm_mesh mesh, const void* storage_dev, void* unique_dev, int ncomp, void* stream);
 
-/* Sets the P2 velocity at t_n (u_old) and t_{n+1} (u_new), storage layout
+/* Sets the nodal velocity at t_n (u_old) and t_{n+1} (u_new), storage layout
  * [n, dim], mesh precision (Sec. 2.3.1 step (ii), Eq. linear interpolation).
  * u_new == u_old means a steady velocity (no time interpolation).  The call
  * enqueues, on `stream`, a copy of the velocity into the mesh's own
  * device buffers in a padded 4-component record layout (one vector load per
- * P2 node in the kernel); the caller's buffers are not used afterwards.
+ * stencil node in the kernel); the caller's buffers are not used afterwards.
  * Work on other streams must be ordered after it by the caller. */
 elm_status elm_set_velocity(elm_mesh mesh, const void* u_old_dev, const void* u_new_dev, void* stream);
 
@@ -175,13 +189,44 @@ elm_status elm_advect_noalloc(elm_mesh mesh, const void* u_old_dev, const void* 
 elm_status elm_advect_adjoint(elm_mesh mesh, const void* T_old_dev, const void* gT_new_dev, void* gT_old_dev,
                               void* gU_old_dev, void* gU_new_dev, double dt, int n_sub, void* stream);
 
+/* ---- Look-back over a time-dependent velocity (Sec. 2.3.3) ----
+ * Tracing back b time steps needs the velocity of every intermediate step
+ * (b = infinity: of every step since t_0).  elm_trace continues backward
+ * traces over one interval at a time, with that interval's velocity pair
+ * from elm_set_velocity; elm_trace_eval then interpolates the temperature
+ * of the time the traces reached.  For T^{n+1} with look-back b:
+ *   D = NULL;  for k = n+1 down to n+2-b:
+ *     elm_set_velocity(u^{k-1}, u^k); elm_trace(D, D', tau, s); D = D';
+ *   elm_trace_eval(D, T^{n+1-b}, T^{n+1}).
+ * A steady velocity needs none of this: elm_advect(T^{n+1-b}, b tau, b s).
+ *
+ * elm_trace: for every node x_i, starts at x_i + D_in[i] (at x_i when D_in
+ * is NULL), traces back over dt with n_sub classic RK4 substeps through the
+ * current velocity (time-interpolated as in elm_advect, t_{n+1} being the
+ * start of this backward interval), clamps to the bounding box like
+ * elm_advect and writes the offset D_out[i] = X_i - x_i.
+ *  D_in, D_out  [n, dim] departure offsets, storage layout, mesh precision;
+ *               they must not overlap.  Every storage copy of an interface
+ *               node continues from the offset of the node's owner copy and
+ *               all copies receive the same result.
+ *  1 <= n_sub <= ELM_MAX_SUBSTEPS; dt finite and >= 0.
+ * One kernel launch on `stream`; allocates nothing; device conditions go to
+ * elm_get_status as for elm_advect. */
+elm_status elm_trace(elm_mesh mesh, const void* D_in_dev, void* D_out_dev, double dt, int n_sub, void* stream);
+
+/* T_dst[i] = T_src_h(x_i + D[i]) (Sec. 2.3.1, step (iii), at the end of
+ * traces made by elm_trace).  D is [n, dim], T_src and T_dst [n] (must not
+ * overlap), storage layout, mesh precision.  Needs no velocity.  One kernel
+ * launch on `stream`; allocates nothing. */
+elm_status elm_trace_eval(elm_mesh mesh, const void* D_dev, const void* T_src_dev, void* T_dst_dev, void* stream);
+
 /* Synchronises `stream`, returns the first device-side condition raised by
  * work on this mesh since the previous call (ELM_ERR_WALK_LIMIT or
  * ELM_ERR_NONFINITE), else ELM_OK, and clears the flags. */
 elm_status elm_get_status(elm_mesh mesh, void* stream);
 
 /* ---- Batched form: many independent advection instances in one launch ----
- * Each instance is a mesh with its own level, dimension, velocity
+ * Each instance is a P2 mesh with its own level, dimension, velocity
  * (elm_set_velocity on that mesh), dt and n_sub; every instance performs the
  * step of elm_advect (Algorithm 1, lines 3-4).  One persistent kernel takes
  * (instance, chunk) items from a shared work list, so small and large

@@ -28,6 +28,8 @@ SIGNATURES = [
     ("elm_advect", _I, [_P, _P, _P, _D, _I, _P]),
     ("elm_advect_noalloc", _I, [_P, _P, _P, _P, _P, _D, _I, _P]),
     ("elm_advect_adjoint", _I, [_P, _P, _P, _P, _P, _P, _D, _I, _P]),
+    ("elm_trace", _I, [_P, _P, _P, _D, _I, _P]),
+    ("elm_trace_eval", _I, [_P, _P, _P, _P, _P]),
     ("elm_get_status", _I, [_P, _P]),
     ("elm_batch_create", _I, [_P, _I, _I, ctypes.POINTER(_P)]),
     ("elm_batch_destroy", _I, [_P]),
@@ -66,3 +68,4 @@ def check(status: int) -> None:
 
 ELM_HOST_ONLY = 0x100
 ELM_ADJOINT = 0x200
+ELM_P1 = 0x400

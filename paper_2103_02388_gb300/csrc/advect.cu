@@ -53,7 +53,8 @@ namespace {
 // One block per work-list chunk: a run of up to blockDim consecutive nodes
 // of one slab p1 of one macro (host-built, so no thread divides or searches
 // for its lattice point beyond one row root).
-template <int D, class R, bool STEADY>
+// P is the element order (1 or 2), MODE what is done per node (NodeMode).
+template <int D, class R, bool STEADY, int P, int MODE>
 __global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
     k_advect(AdvectArgs args, Tables<R> tab, int chunk0) {
   const int4 ck = args.chunks[chunk0 + int(blockIdx.x)];
@@ -69,8 +70,10 @@ __global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
                        consts<R>(args),
                        args.N,
                        int(args.npm),
-                       args.n_sub};
-  advect_node<D, R, STEADY>(job, tab, ck, int(threadIdx.x));
+                       args.n_sub,
+                       static_cast<const R*>(args.D_in),
+                       static_cast<R*>(args.D_out)};
+  advect_node<D, R, STEADY, P, MODE>(job, tab, ck, int(threadIdx.x));
 }
 
 // Persistent batched kernel: each block repeatedly takes the next (instance,
@@ -147,18 +150,26 @@ __global__ void k_gather(const R* __restrict__ in, R* __restrict__ out, const in
   out[i] = in[idx[node] * ncomp + c];
 }
 
-template <int D, class R, bool STEADY>
-cudaError_t launch_drs(const AdvectArgs& a, Tables<R> t, cudaStream_t s) {
+template <int D, class R, bool STEADY, int P, int MODE>
+cudaError_t launch_k(const AdvectArgs& a, Tables<R> t, cudaStream_t s) {
   for (int c0 = 0; c0 < a.n_chunks; c0 += (1 << 30)) {
     const int nb = a.n_chunks - c0 < (1 << 30) ? a.n_chunks - c0 : (1 << 30);
-    k_advect<D, R, STEADY><<<nb, kAdvectThreads, 0, s>>>(a, t, c0);
+    k_advect<D, R, STEADY, P, MODE><<<nb, kAdvectThreads, 0, s>>>(a, t, c0);
   }
   return cudaGetLastError();
 }
 
+template <int D, class R, int P>
+cudaError_t launch_drp(const AdvectArgs& a, Tables<R> t, cudaStream_t s) {
+  if (a.mode == kEval) return launch_k<D, R, true, P, kEval>(a, t, s);  // no velocity is read
+  if (a.mode == kTrace)
+    return a.steady ? launch_k<D, R, true, P, kTrace>(a, t, s) : launch_k<D, R, false, P, kTrace>(a, t, s);
+  return a.steady ? launch_k<D, R, true, P, kStep>(a, t, s) : launch_k<D, R, false, P, kStep>(a, t, s);
+}
+
 template <int D, class R>
 cudaError_t launch_dr(const AdvectArgs& a, Tables<R> t, cudaStream_t s) {
-  return a.steady ? launch_drs<D, R, true>(a, t, s) : launch_drs<D, R, false>(a, t, s);
+  return a.order == 1 ? launch_drp<D, R, 1>(a, t, s) : launch_drp<D, R, 2>(a, t, s);
 }
 
 }  // namespace

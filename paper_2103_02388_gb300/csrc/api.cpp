@@ -61,6 +61,44 @@ bool ranges_overlap(const void* a, const void* b, size_t bytes) {
   return pa < pb + bytes && pb < pa + bytes;
 }
 
+// Launch arguments shared by every per-node kernel of a mesh: tables, sizes,
+// the current velocity and the step constants for (dt, n_sub).
+elm::AdvectArgs make_args(const elm_mesh_s* me, double dt, int n_sub) {
+  elm::AdvectArgs a{};
+  a.geo = me->d_geo;
+  a.geo32 = me->d_geo32;
+  a.n_macros = int32_t(me->n_macros);
+  a.N = me->N;
+  a.npm = me->npm;
+  a.n_storage = me->n_storage;
+  for (int r = 0; r < 3; ++r) {
+    a.lo[r] = me->lo[r];
+    a.hi[r] = me->hi[r];
+  }
+  a.u_old = me->steady ? me->d_u4[1] : me->d_u4[0];
+  a.u_new = me->d_u4[1];
+  a.steady = me->steady;
+  a.dt = dt;
+  a.n_sub = n_sub;
+  a.status = me->d_status;
+  a.unique_map = me->d_unique_map;
+  a.owner_mp = me->d_owner_mp;
+  a.chunks = me->d_chunks;
+  a.n_chunks = int(me->n_chunks);
+  a.order = me->order;
+  const double h = dt / n_sub;
+  a.k64 = {h, 0.5 * h, h / 6.0, dt, 1.0 / me->M, double(me->N), {0, 0, 0}, {0, 0, 0}};
+  a.k32 = {float(h), float(0.5 * h), float(h / 6.0), float(dt), float(1.0 / me->M), float(me->N),
+           {0, 0, 0}, {0, 0, 0}};
+  for (int r = 0; r < 3; ++r) {
+    a.k64.lo[r] = me->lo[r];
+    a.k64.hi[r] = me->hi[r];
+    a.k32.lo[r] = float(me->lo[r]);
+    a.k32.hi[r] = float(me->hi[r]);
+  }
+  return a;
+}
+
 }  // namespace
 
 namespace elm {
@@ -76,17 +114,23 @@ elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz
   if (n_vertices <= 0 || !vertex_xyz) return fail(ELM_ERR_ARG, "elm_mesh_create: no vertices");
   if (n_macros <= 0 || !macro_vertices) return fail(ELM_ERR_ARG, "elm_mesh_create: no macros");
   if (n_macros > (int64_t(1) << 30)) return fail(ELM_ERR_ARG, "elm_mesh_create: too many macros");
-  const int max_level = dim == 2 ? 9 : 7;
-  if (level < 0 || level > max_level)
-    return fail(ELM_ERR_ARG, "elm_mesh_create: level out of range (0.." + std::to_string(max_level) + ")");
   const bool host_only = (precision & ELM_HOST_ONLY) != 0;
   const bool with_adjoint = (precision & ELM_ADJOINT) != 0;
-  precision &= ~(ELM_HOST_ONLY | ELM_ADJOINT);
+  const int order = (precision & ELM_P1) != 0 ? 1 : 2;
+  precision &= ~(ELM_HOST_ONLY | ELM_ADJOINT | ELM_P1);
   if (precision != ELM_FP64 && precision != ELM_FP32)
     return fail(ELM_ERR_ARG, "elm_mesh_create: precision must be ELM_FP64 or ELM_FP32");
+  if (order == 1 && with_adjoint)
+    return fail(ELM_ERR_ARG, "elm_mesh_create: the adjoint is built for P2 meshes only (ELM_P1 with ELM_ADJOINT)");
+  // P1 puts one node lattice point per micro vertex, so it can go one level
+  // finer than P2 for the same lattice (at most 2^10 points per edge in 2D,
+  // 2^8 in 3D).
+  const int max_level = (dim == 2 ? 9 : 7) + (order == 1 ? 1 : 0);
+  if (level < 0 || level > max_level)
+    return fail(ELM_ERR_ARG, "elm_mesh_create: level out of range (0.." + std::to_string(max_level) + ")");
   {
     // the kernels index storage slots with 32-bit integers (int32 storage)
-    const int64_t M = int64_t(2) << level;
+    const int64_t M = int64_t(order) << level;
     const int64_t npm = dim == 3 ? (M + 1) * (M + 2) * (M + 3) / 6 : (M + 1) * (M + 2) / 2;
     if (n_macros * npm >= (int64_t(1) << 31))
       return fail(ELM_ERR_ARG, "elm_mesh_create: more than 2^31 - 1 storage nodes");
@@ -95,6 +139,7 @@ elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz
   if (!me) return fail(ELM_ERR_ARG, "elm_mesh_create: out of host memory");
   me->host_only = host_only;
   me->with_adjoint = with_adjoint;
+  me->order = order;
   if (!host_only) {
     cudaError_t e = cudaGetDevice(&me->device);
     if (e != cudaSuccess) {
@@ -215,41 +260,9 @@ elm_status elm_advect(elm_mesh me, const void* T_old_dev, void* T_new_dev, doubl
     return fail(ELM_ERR_ARG, "elm_advect: T_old and T_new overlap");
   DeviceGuard g(me->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  elm::AdvectArgs a{};
-  a.geo = me->d_geo;
-  a.geo32 = me->d_geo32;
-  a.n_macros = int32_t(me->n_macros);
-  a.N = me->N;
-  a.npm = me->npm;
-  a.n_storage = me->n_storage;
-  for (int r = 0; r < 3; ++r) {
-    a.lo[r] = me->lo[r];
-    a.hi[r] = me->hi[r];
-  }
-  a.u_old = me->steady ? me->d_u4[1] : me->d_u4[0];
-  a.u_new = me->d_u4[1];
-  a.steady = me->steady;
+  elm::AdvectArgs a = make_args(me, dt, n_sub);
   a.T_old = T_old_dev;
   a.T_new = T_new_dev;
-  a.dt = dt;
-  a.n_sub = n_sub;
-  a.status = me->d_status;
-  a.unique_map = me->d_unique_map;
-  {
-    const double h = dt / n_sub;
-    a.k64 = {h, 0.5 * h, h / 6.0, dt, 1.0 / me->M, double(me->N), {0, 0, 0}, {0, 0, 0}};
-    a.k32 = {float(h), float(0.5 * h), float(h / 6.0), float(dt), float(1.0 / me->M), float(me->N),
-             {0, 0, 0}, {0, 0, 0}};
-    for (int r = 0; r < 3; ++r) {
-      a.k64.lo[r] = me->lo[r];
-      a.k64.hi[r] = me->hi[r];
-      a.k32.lo[r] = float(me->lo[r]);
-      a.k32.hi[r] = float(me->hi[r]);
-    }
-  }
-  a.owner_mp = me->d_owner_mp;
-  a.chunks = me->d_chunks;
-  a.n_chunks = int(me->n_chunks);
   cudaError_t e = elm::launch_advect(me->dim, me->precision, a, s);
   if (e != cudaSuccess) return cuda_fail(e, "elm_advect");
   return ELM_OK;
@@ -272,45 +285,52 @@ elm_status elm_advect_adjoint(elm_mesh me, const void* T_old_dev, const void* gT
   if (ranges_overlap(gT_new_dev, gT_old_dev, bytes)) return fail(ELM_ERR_ARG, "elm_advect_adjoint: gT_new and gT_old overlap");
   DeviceGuard g(me->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  elm::AdvectArgs a{};
-  a.geo = me->d_geo;
-  a.geo32 = me->d_geo32;
-  a.n_macros = int32_t(me->n_macros);
-  a.N = me->N;
-  a.npm = me->npm;
-  a.n_storage = me->n_storage;
-  for (int r = 0; r < 3; ++r) {
-    a.lo[r] = me->lo[r];
-    a.hi[r] = me->hi[r];
-  }
-  a.u_old = me->steady ? me->d_u4[1] : me->d_u4[0];
-  a.u_new = me->d_u4[1];
-  a.steady = me->steady;
+  elm::AdvectArgs a = make_args(me, dt, n_sub);
   a.T_old = T_old_dev;
   a.T_new = nullptr;
-  a.dt = dt;
-  a.n_sub = n_sub;
-  a.status = me->d_status;
-  a.unique_map = me->d_unique_map;
-  a.owner_mp = me->d_owner_mp;
-  a.chunks = me->d_chunks;
-  a.n_chunks = int(me->n_chunks);
-  {
-    const double h = dt / n_sub;
-    a.k64 = {h, 0.5 * h, h / 6.0, dt, 1.0 / me->M, double(me->N), {0, 0, 0}, {0, 0, 0}};
-    a.k32 = {float(h), float(0.5 * h), float(h / 6.0), float(dt), float(1.0 / me->M), float(me->N),
-             {0, 0, 0}, {0, 0, 0}};
-    for (int r = 0; r < 3; ++r) {
-      a.k64.lo[r] = me->lo[r];
-      a.k64.hi[r] = me->hi[r];
-      a.k32.lo[r] = float(me->lo[r]);
-      a.k32.hi[r] = float(me->hi[r]);
-    }
-  }
   const elm::AdjointBuffers b{me->d_acc_T, me->d_acc_U, me->d_maxbits, me->d_owner};
   cudaError_t e = elm::launch_adjoint(me->dim, me->precision, a, b, gT_new_dev, gT_old_dev, gU_old_dev,
                                       me->steady ? nullptr : gU_new_dev, s);
   if (e != cudaSuccess) return cuda_fail(e, "elm_advect_adjoint");
+  return ELM_OK;
+}
+
+elm_status elm_trace(elm_mesh me, const void* D_in_dev, void* D_out_dev, double dt, int n_sub, void* stream) {
+  if (!me) return fail(ELM_ERR_ARG, "elm_trace: null mesh");
+  if (!D_out_dev) return fail(ELM_ERR_ARG, "elm_trace: null output buffer");
+  if (!std::isfinite(dt) || dt < 0.0) return fail(ELM_ERR_ARG, "elm_trace: dt must be finite and >= 0");
+  if (n_sub < 1 || n_sub > elm::kMaxSub)
+    return fail(ELM_ERR_ARG, "elm_trace: n_sub must be in 1.." + std::to_string(elm::kMaxSub));
+  if (me->host_only) return fail(ELM_ERR_STATE, "elm_trace: host-only mesh");
+  if (!me->have_velocity) return fail(ELM_ERR_STATE, "elm_trace: elm_set_velocity has not been called");
+  if (D_in_dev && ranges_overlap(D_in_dev, D_out_dev, elem_size(me) * size_t(me->n_storage) * me->dim))
+    return fail(ELM_ERR_ARG, "elm_trace: D_in and D_out overlap");
+  DeviceGuard g(me->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  elm::AdvectArgs a = make_args(me, dt, n_sub);
+  a.mode = 1;
+  a.D_in = D_in_dev;
+  a.D_out = D_out_dev;
+  cudaError_t e = elm::launch_advect(me->dim, me->precision, a, s);
+  if (e != cudaSuccess) return cuda_fail(e, "elm_trace");
+  return ELM_OK;
+}
+
+elm_status elm_trace_eval(elm_mesh me, const void* D_dev, const void* T_src_dev, void* T_dst_dev, void* stream) {
+  if (!me) return fail(ELM_ERR_ARG, "elm_trace_eval: null mesh");
+  if (!D_dev || !T_src_dev || !T_dst_dev) return fail(ELM_ERR_ARG, "elm_trace_eval: null buffer");
+  if (me->host_only) return fail(ELM_ERR_STATE, "elm_trace_eval: host-only mesh");
+  if (ranges_overlap(T_src_dev, T_dst_dev, elem_size(me) * size_t(me->n_storage)))
+    return fail(ELM_ERR_ARG, "elm_trace_eval: T_src and T_dst overlap");
+  DeviceGuard g(me->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  elm::AdvectArgs a = make_args(me, 0.0, 1);
+  a.mode = 2;
+  a.D_in = D_dev;
+  a.T_old = T_src_dev;
+  a.T_new = T_dst_dev;
+  cudaError_t e = elm::launch_advect(me->dim, me->precision, a, s);
+  if (e != cudaSuccess) return cuda_fail(e, "elm_trace_eval");
   return ELM_OK;
 }
 

@@ -49,7 +49,7 @@ template <class R>
 struct StepConsts {
   R h, h2, h6;     // substep, half substep, substep / 6
   R dt;
-  R invM;          // 1 / 2^(L+1)
+  R invM;          // 1 / M, M = order * 2^L (the node lattice)
   R Nf;            // 2^L
   R lo[3], hi[3];  // bounding box
 };
@@ -75,6 +75,10 @@ struct AdvectArgs {
   const int64_t* owner_mp;    // unique id -> owner record (pack_owner)
   const int4* chunks;         // (macro, p1, first index in slab, count) per thread block
   int n_chunks;
+  int order = 2;              // element order: 1 (P1) or 2 (P2)
+  int mode = 0;               // per-node work (NodeMode in tracer.cuh): step, trace, evaluation
+  const void* D_in = nullptr; // departure offsets [n, dim] (trace / evaluation)
+  void* D_out = nullptr;
   StepConsts<float> k32;
   StepConsts<double> k64;
 };
@@ -83,6 +87,7 @@ struct AdvectArgs {
 
 struct elm_mesh_s {
   int dim = 0, level = 0, N = 0, M = 0, precision = ELM_FP64;
+  int order = 2;                     // element order (P1 / P2); M = order * N
   bool host_only = false;
   int64_t n_macros = 0, npm = 0, n_storage = 0, n_unique = 0, n_ghost = 0;
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};

@@ -61,7 +61,7 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
   me->dim = d;
   me->level = level;
   me->N = 1 << level;
-  me->M = 2 * me->N;
+  me->M = me->order * me->N;  // node lattice points per macro edge
   me->precision = precision;
   me->n_macros = nm;
   me->npm = nodes_per_macro(d, me->M);

@@ -142,12 +142,13 @@ struct Min64 {
   int kmin;
 };
 
-// Start node x_i = v0_m0 + J_m0 (p / M) in FP64.
-template <int D>
+// Start node x_i = v0_m0 + J_m0 (p / M) in FP64; the node lattice has
+// M = P N points per macro edge (P2: vertices and midpoints, P1: vertices).
+template <int D, int P>
 __device__ __forceinline__ void node_position64(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N,
                                                 double* x) {
   const MacroGeo& g0 = geo[m0];
-  const double invM = 1.0 / double(2 * N);
+  const double invM = 1.0 / double(P * N);
   const double s[3] = {double(p0) * invM, double(p1) * invM, double(p2) * invM};
 #pragma unroll
   for (int r = 0; r < D; ++r) {
@@ -159,11 +160,11 @@ __device__ __forceinline__ void node_position64(const MacroGeo* geo, int m0, int
 }
 
 // Lattice coordinate of the start node in macro mm, FP64.
-template <int D>
+template <int D, int P>
 __device__ __forceinline__ void node_lattice64(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N, int mm,
                                                double* q) {
   double x[D];
-  node_position64<D>(geo, m0, p0, p1, p2, N, x);
+  node_position64<D, P>(geo, m0, p0, p1, p2, N, x);
   const MacroGeo& g = geo[mm];
 #pragma unroll
   for (int r = 0; r < D; ++r) {
@@ -174,10 +175,10 @@ __device__ __forceinline__ void node_lattice64(const MacroGeo* geo, int m0, int 
   }
 }
 
-template <int D>
+template <int D, int P>
 __device__ __noinline__ FrameD frame64(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N, int mm) {
   double q[3] = {0.0, 0.0, 0.0};
-  node_lattice64<D>(geo, m0, p0, p1, p2, N, mm, q);
+  node_lattice64<D, P>(geo, m0, p0, p1, p2, N, mm, q);
   FrameD f;
   f.bq0 = ::floor(q[0]);
   f.bq1 = ::floor(q[1]);
@@ -218,11 +219,11 @@ __device__ __noinline__ Frame frame_df(const MacroGeo32* tg, int m0, int p0, int
 }
 
 // FP64 minimum barycentric (lattice units) of x_i + d in macro m, and its face.
-template <int D>
+template <int D, int P>
 __device__ __noinline__ Min64 bary64_min(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N, int m,
                                          float d0, float d1, float d2) {
   double q[3] = {0.0, 0.0, 0.0};
-  node_lattice64<D>(geo, m0, p0, p1, p2, N, m, q);
+  node_lattice64<D, P>(geo, m0, p0, p1, p2, N, m, q);
   const MacroGeo& g = geo[m];
   const double d[3] = {double(d0), double(d1), double(d2)};
 #pragma unroll
@@ -265,10 +266,12 @@ __device__ __noinline__ Vec3<R> lattice_foreign(Tables<R> tab, int m, R r00, R r
   return Vec3<R>{r[0], r[1], r[2]};
 }
 
-// Per-thread tracing state.
-template <int D, class R, bool STEADY>
+// Per-thread tracing state.  P is the element order of the velocity and the
+// scalar (Sec. 3.1: linear P1 or quadratic P2 Lagrange elements).
+template <int D, class R, bool STEADY, int P = 2>
 struct Tracer {
-  static constexpr int NB = (D + 1) * (D + 2) / 2;  // P2 nodes of a simplex
+  static_assert(P == 1 || P == 2, "element order");
+  static constexpr int NB = P == 2 ? (D + 1) * (D + 2) / 2 : D + 1;  // nodes of a simplex
   // launch constants (copied, so no kernel parameter is addressed)
   const MacroGeo* geo;   // FP64 macro table (tie-breaks)
   Tables<R> tab;         // macro table in the working precision
@@ -279,7 +282,7 @@ struct Tracer {
   const R* T;
   R dt;
   R Nf;
-  R invM;          // 1 / 2^(L+1), exact
+  R invM;          // 1 / M, M = P 2^L (node lattice), exact
   unsigned* status;
   int m0;          // home macro
   int p[D];        // home lattice point
@@ -307,8 +310,13 @@ struct Tracer {
     m = m0;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      bq[k] = to_real<R>(p[k] >> 1);
-      r0[k] = (p[k] & 1) ? R(0.5) : R(0);
+      if (P == 2) {
+        bq[k] = to_real<R>(p[k] >> 1);
+        r0[k] = (p[k] & 1) ? R(0.5) : R(0);
+      } else {
+        bq[k] = to_real<R>(p[k]);
+        r0[k] = R(0);
+      }
     }
   }
 
@@ -320,7 +328,7 @@ struct Tracer {
     }
     m = mm;
     if constexpr (sizeof(R) == 8) {
-      const FrameD f = frame64<D>(geo, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, N, mm);
+      const FrameD f = frame64<D, P>(geo, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, N, mm);
       bq[0] = f.bq0;
       bq[1] = f.bq1;
       r0[0] = f.r00;
@@ -391,7 +399,7 @@ struct Tracer {
         nb = tab.nb(m, kmin);
         if (!outside && nb >= 0) {
           // tie band at an interior face: decide in FP64 from the exact start node
-          const Min64 r64 = bary64_min<D>(geo, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, N, m, float(d[0]),
+          const Min64 r64 = bary64_min<D, P>(geo, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, N, m, float(d[0]),
                                           float(d[1]), D == 3 ? float(d[D - 1]) : 0.0f);
           outside = r64.lmin < -kTol64;
           kmin = r64.kmin;
@@ -424,6 +432,10 @@ struct Tracer {
   // descending fraction (ties by axis) orders the Kuhn path c -> c + 1, and
   // each node's offsets along the sorted axes are fixed (alpha >= beta >= gamma).
   __device__ void stencil(const R* c, const R* f, int* slot, R* phi) const {
+    if constexpr (P == 1) {
+      stencil_p1(c, f, slot, phi);
+      return;
+    }
     int A[D][3];
     R fs[D];
     {
@@ -506,6 +518,64 @@ struct Tracer {
       phi[3] = R(4) * L[0] * L[1];
       phi[4] = R(4) * L[0] * L[D];
       phi[5] = R(4) * L[1] * L[D];
+    }
+  }
+
+  // P1 stencil: the d+1 vertices of the micro simplex holding (c, f), whose
+  // lattice points are c plus 0 or 1 per axis (node lattice = cell lattice),
+  // with the micro barycentrics as basis values (Sec. 3.1, linear elements).
+  // Per axis a the packed index contributes B_a[o], o in {0, 1}; sorting the
+  // axes by descending fraction orders the Kuhn path c -> c + 1.
+  __device__ void stencil_p1(const R* c, const R* f, int* slot, R* phi) const {
+    int B[D][2];
+    R fs[D];
+    {
+      const int base = m * npm;
+      const int c0 = f2i_exact(c[0]);
+      if (D == 3) {
+        const int c1 = f2i_exact(c[1]);
+        const int c2 = f2i_exact(c[D - 1]) + base;
+        B[0][0] = tri3(c0);
+        B[0][1] = B[0][0] + tri2(c0 + 1);
+        B[1][0] = tri2(c1);
+        B[1][1] = B[1][0] + c1 + 1;
+        B[D - 1][0] = c2;
+        B[D - 1][1] = c2 + 1;
+      } else {
+        const int c1 = f2i_exact(c[D - 1]) + base;
+        B[0][0] = tri2(c0);
+        B[0][1] = B[0][0] + c0 + 1;
+        B[D - 1][0] = c1;
+        B[D - 1][1] = c1 + 1;
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) fs[k] = f[k];
+    }
+    auto cswap = [&](int i, int j) {
+      if (fs[j] > fs[i]) {
+        R t = fs[i]; fs[i] = fs[j]; fs[j] = t;
+        int u0 = B[i][0]; B[i][0] = B[j][0]; B[j][0] = u0;
+        int u1 = B[i][1]; B[i][1] = B[j][1]; B[j][1] = u1;
+      }
+    };
+    if (D == 3) {
+      cswap(0, 1); cswap(1, 2); cswap(0, 1);
+      slot[0] = B[0][0] + B[1][0] + B[D - 1][0];
+      slot[1] = B[0][1] + B[1][0] + B[D - 1][0];
+      slot[2] = B[0][1] + B[1][1] + B[D - 1][0];
+      slot[D] = B[0][1] + B[1][1] + B[D - 1][1];
+      phi[0] = R(1) - fs[0];
+      phi[1] = fs[0] - fs[1];
+      phi[2] = fs[1] - fs[D - 1];
+      phi[D] = fs[D - 1];
+    } else {
+      cswap(0, 1);
+      slot[0] = B[0][0] + B[D - 1][0];
+      slot[1] = B[0][1] + B[D - 1][0];
+      slot[D] = B[0][1] + B[D - 1][1];
+      phi[0] = R(1) - fs[0];
+      phi[1] = fs[0] - fs[D - 1];
+      phi[D] = fs[D - 1];
     }
   }
 
@@ -609,15 +679,24 @@ struct NodeJob {
   int N;
   int npm;
   int n_sub;
+  const R* D_in = nullptr;  // departure offsets [n, D] (trace / evaluation modes)
+  R* D_out = nullptr;
+};
+
+// What advect_node does with a node.
+enum NodeMode {
+  kStep = 0,   // trace from the node over dt, then T_new = T_old_h(X)  (steps (i)-(iii))
+  kTrace = 1,  // continue the trace from x_i + D_in (or from x_i) over dt; D_out = X - x_i
+  kEval = 2    // T_new = T_old_h(x_i + D_in)
 };
 
 // One node: particle creation (i), backward RK4 (ii), T evaluation (iii).
 // The node is entry `tid` of chunk ck = (macro, slab p1, first index, count).
-template <int D, class R, bool STEADY>
+template <int D, class R, bool STEADY, int P = 2, int MODE = kStep>
 __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab, int4 ck, int tid) {
   const StepConsts<R>& K = job.K;
   const int npm = job.npm;
-  Tracer<D, R, STEADY> t;
+  Tracer<D, R, STEADY, P> t;
   t.geo = job.geo;
   t.tab = tab;
   t.N = job.N;
@@ -646,7 +725,7 @@ __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab
   }
   const int64_t slot = int64_t(t.m0) * npm + in_macro;
   {
-    const int M = 2 * job.N;
+    const int M = P * job.N;
     bool iface = t.p[0] == M || t.p[D - 1] == 0;
 #pragma unroll
     for (int k = 1; k < D; ++k) iface = iface || t.p[k] == t.p[k - 1];
@@ -666,44 +745,64 @@ __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab
     }
   }
   t.home_frame();
-  R u_node[D];
-  Tracer<D, R, STEADY>::load_rec(t.un, t.m0 * npm + packed<D>(t.p), u_node);
-  // (ii) backward RK4, n_sub substeps of h = dt / n_sub.  All 4 n_sub stage
-  // evaluations run through one loop with a single evaluation site (stage s
-  // of a substep sits at d, d - h/2 k, d - h/2 k, d - h k and has weight
-  // 1, 2, 2, 1), which keeps the kernel's code small.
-  const R h = K.h, h2 = K.h2, h6 = K.h6;
-  R d[D], k[D], acc[D];
+  const int own_slot = t.m0 * npm + packed<D>(t.p);
+  R d[D];
+  bool from_node = true;
 #pragma unroll
-  for (int q = 0; q < D; ++q) {
-    d[q] = R(0);
-    // the first stage sits on the node: the P2 interpolant is the nodal value
-    // (steady, or at t_{n+1} where only u^{n+1} has weight)
-    k[q] = u_node[q];
-    acc[q] = k[q];
+  for (int q = 0; q < D; ++q) d[q] = R(0);
+  if (MODE != kStep && job.D_in != nullptr) {
+    // every copy of an interface node continues from its owner's offset
+#pragma unroll
+    for (int q = 0; q < D; ++q) d[q] = job.D_in[int64_t(own_slot) * D + q];
+    t.clamp_box(d);
+    from_node = false;
   }
   bool finite = true;
-  const int n_eval = 4 * job.n_sub;
-#pragma unroll 1
-  for (int e = 1; e < n_eval; ++e) {
-    const int s = e & 3;
-    const R off = s == 0 ? R(0) : (s == 3 ? h : h2);
-    R z[D];
+  if (MODE != kEval) {
+    // (ii) backward RK4, n_sub substeps of h = dt / n_sub.  All 4 n_sub stage
+    // evaluations run through one loop with a single evaluation site (stage s
+    // of a substep sits at d, d - h/2 k, d - h/2 k, d - h k and has weight
+    // 1, 2, 2, 1), which keeps the kernel's code small.
+    const R h = K.h, h2 = K.h2, h6 = K.h6;
+    R k[D], acc[D];
+    R u_node[D];
+    Tracer<D, R, STEADY, P>::load_rec(t.un, own_slot, u_node);
 #pragma unroll
-    for (int q = 0; q < D; ++q) z[q] = d[q] - off * k[q];
-    t.clamp_box(z);
-    t.velocity(z, to_real<R>(e >> 2) * h + off, k);
-    const R w = (s == 1 || s == 2) ? R(2) : R(1);
-#pragma unroll
-    for (int q = 0; q < D; ++q) acc[q] = s == 0 ? k[q] : r_fma(w, k[q], acc[q]);
-    if (s == 3) {
-#pragma unroll
-      for (int q = 0; q < D; ++q) {
-        finite = finite && isfinite(acc[q]);
-        d[q] = d[q] - h6 * acc[q];
-      }
-      t.clamp_box(d);
+    for (int q = 0; q < D; ++q) {
+      // the first stage of a trace that starts on the node: the P1 / P2
+      // interpolant there is the nodal value (steady, or at t_{n+1} where
+      // only u^{n+1} has weight)
+      k[q] = u_node[q];
+      acc[q] = k[q];
     }
+    const int n_eval = 4 * job.n_sub;
+#pragma unroll 1
+    for (int e = from_node ? 1 : 0; e < n_eval; ++e) {
+      const int s = e & 3;
+      const R off = s == 0 ? R(0) : (s == 3 ? h : h2);
+      R z[D];
+#pragma unroll
+      for (int q = 0; q < D; ++q) z[q] = d[q] - off * k[q];
+      t.clamp_box(z);
+      t.velocity(z, to_real<R>(e >> 2) * h + off, k);
+      const R w = (s == 1 || s == 2) ? R(2) : R(1);
+#pragma unroll
+      for (int q = 0; q < D; ++q) acc[q] = s == 0 ? k[q] : r_fma(w, k[q], acc[q]);
+      if (s == 3) {
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          finite = finite && isfinite(acc[q]);
+          d[q] = d[q] - h6 * acc[q];
+        }
+        t.clamp_box(d);
+      }
+    }
+  }
+  if (MODE == kTrace) {
+    if (!finite) atomicOr(job.status, kFlagNonFinite);
+#pragma unroll
+    for (int q = 0; q < D; ++q) job.D_out[slot * D + q] = d[q];
+    return;
   }
   // (iii) temperature at the departure point
   const R v = t.scalar(d);

@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import ELM_ADJOINT, ELM_FP32, ELM_FP64, ELM_HOST_ONLY, check
+from ._lib import ELM_ADJOINT, ELM_FP32, ELM_FP64, ELM_HOST_ONLY, ELM_P1, check
 
 _DTYPES = {"fp64": (ELM_FP64, torch.float64, np.float64), "fp32": (ELM_FP32, torch.float32, np.float32)}
 
@@ -26,12 +26,13 @@ class Mesh:
     """A coarse macro mesh refined uniformly to ``level`` (Sec. 2.1).
 
     ``vertices``: [n_vertices, dim] coordinates; ``macros``: [n_macros, dim+1]
-    vertex ids; ``precision``: "fp64" or "fp32".  ``host_only=True`` builds only
-    the host tables (coordinates and the unique map), without a GPU.
+    vertex ids; ``precision``: "fp64" or "fp32"; ``order``: 2 (P2 elements) or
+    1 (P1, Sec. 3.1).  ``host_only=True`` builds only the host tables
+    (coordinates and the unique map), without a GPU.
     """
 
     def __init__(self, vertices, macros, level: int, precision: str = "fp64", host_only: bool = False,
-                 adjoint: bool = False):
+                 adjoint: bool = False, order: int = 2):
         lib = _lib.load()
         self.vertices = np.ascontiguousarray(vertices, dtype=np.float64)
         self.macros = np.ascontiguousarray(macros, dtype=np.int64)
@@ -41,13 +42,17 @@ class Mesh:
         code, self.dtype, self.np_dtype = _DTYPES[precision]
         self.host_only = host_only
         self.adjoint = adjoint
+        if order not in (1, 2):
+            raise ValueError("order must be 1 (P1) or 2 (P2)")
+        self.order = int(order)
         if not host_only:
             self.device = torch.device("cuda", torch.cuda.current_device())
         h = ctypes.c_void_p()
         check(lib.elm_mesh_create(self.dim, self.vertices.shape[0],
                                   self.vertices.ctypes.data_as(ctypes.c_void_p),
                                   self.macros.shape[0], self.macros.ctypes.data_as(ctypes.c_void_p),
-                                  self.level, code | (ELM_HOST_ONLY if host_only else 0) | (ELM_ADJOINT if adjoint else 0),
+                                  self.level, code | (ELM_HOST_ONLY if host_only else 0) | (ELM_ADJOINT if adjoint else 0)
+                                  | (ELM_P1 if order == 1 else 0),
                                   ctypes.byref(h)))
         self._h = h
         self.n_nodes = int(lib.elm_mesh_num_nodes(h))
@@ -157,6 +162,56 @@ class Mesh:
         if b < 1:
             raise ValueError("b must be >= 1")
         return self.advect(T_src, b * tau, b * n_sub, out=out, stream=stream)
+
+    def trace(self, D_in: torch.Tensor | None, dt: float, n_sub: int = 1, out: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+        """Continues the backward traces of every node over one interval of
+        length dt with the current velocity pair (Sec. 2.3.3): starts at
+        x_i + D_in[i] (at x_i when D_in is None) and returns the offsets
+        X_i - x_i, [n_nodes, dim] in storage layout."""
+        if D_in is not None:
+            self._check_tensor(D_in, "D_in")
+            if tuple(D_in.shape) != (self.n_nodes, self.dim):
+                raise ValueError(f"D_in must have shape ({self.n_nodes}, {self.dim})")
+        if out is None:
+            out = torch.empty((self.n_nodes, self.dim), dtype=self.dtype, device=self.device)
+        else:
+            self._check_tensor(out, "out")
+        check(_lib.load().elm_trace(self._h, ctypes.c_void_p(D_in.data_ptr()) if D_in is not None else None,
+                                    ctypes.c_void_p(out.data_ptr()), float(dt), int(n_sub), _stream_ptr(stream)))
+        return out
+
+    def trace_eval(self, D: torch.Tensor, T_src: torch.Tensor, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+        """T_dst[i] = T_src_h(x_i + D[i]) at the end of traces from ``trace``."""
+        self._check_tensor(D, "D")
+        self._check_tensor(T_src, "T_src")
+        if tuple(D.shape) != (self.n_nodes, self.dim) or T_src.shape != (self.n_nodes,):
+            raise ValueError("D must be [n_nodes, dim] and T_src [n_nodes]")
+        if out is None:
+            out = torch.empty_like(T_src)
+        else:
+            self._check_tensor(out, "out")
+        check(_lib.load().elm_trace_eval(self._h, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(T_src.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def advect_lookback_unsteady(self, T_src: torch.Tensor, velocities, tau: float, n_sub: int = 1) -> torch.Tensor:
+        """Look-back over a time-dependent velocity (Sec. 2.3.3): with
+        ``velocities`` = [u^{n+1-b}, ..., u^{n+1}] (b + 1 nodal fields, storage
+        layout) and T_src = T^{n+1-b}, traces every node back through the b
+        intervals, newest first, each with its velocity pair, and interpolates
+        T_src at the end (on the current stream).  Leaves the last pair
+        (u^{n+1-b}, u^{n+2-b}) set as the mesh's velocity."""
+        us = list(velocities)
+        if len(us) < 2:
+            raise ValueError("need at least two velocity fields (one interval)")
+        bufs = [torch.empty((self.n_nodes, self.dim), dtype=self.dtype, device=self.device) for _ in range(2)]
+        cur = None
+        for j, k in enumerate(range(len(us) - 1, 0, -1)):
+            self.set_velocity(us[k - 1], us[k])
+            cur = self.trace(cur, tau, n_sub, out=bufs[j % 2])
+        return self.trace_eval(cur, T_src)
 
     def advect_adjoint(self, T_old: torch.Tensor, gT_new: torch.Tensor, dt: float, n_sub: int = 1,
                        split: bool = True, stream=None):

@@ -128,6 +128,36 @@ def test_topology_and_argument_errors(lib):
     assert b"precision" in lib.elm_last_error()
 
 
+@pytest.mark.parametrize("mesh,level", [("square", 0), ("square", 5), ("cube", 1), ("cube", 3), ("block", 2)])
+def test_p1_host_mesh_matches_oracle_nodes(lib, mesh, level):
+    """ELM_P1: nodes are the micro vertices, M = 2^L lattice points per edge."""
+    from paper_2103_02388_gb300 import elm
+    v, m = {"square": inputs.unit_square, "cube": inputs.unit_cube,
+            "block": lambda: inputs.cube_block(2, 0.3, 1)}[mesh]()
+    gm = elm.Mesh(v, m, level, host_only=True, order=1)
+    om = oracle.OracleMesh(v, m, level, order=1)
+    assert gm.n_unique == om.n_nodes
+    M = 2 ** level
+    d = v.shape[1]
+    npm = (M + 1) * (M + 2) * (M + 3) // 6 if d == 3 else (M + 1) * (M + 2) // 2
+    assert gm.n_nodes == m.shape[0] * npm
+    perm = match_nodes(om.coords, gm.unique_coords())
+    assert sorted(perm) == list(range(gm.n_unique))
+    assert np.abs(gm.node_coords() - gm.unique_coords()[gm.unique_map()]).max() < 1e-12
+
+
+def test_p1_argument_errors(lib):
+    v, m = inputs.unit_cube()
+    st, h = _host_mesh(lib, v, m, 8, precision=_lib.ELM_FP64 | _lib.ELM_P1)
+    assert st == _lib.ELM_OK                            # P1 goes one level finer
+    lib.elm_mesh_destroy(h)
+    st, h = _host_mesh(lib, v, m, 9, precision=_lib.ELM_FP64 | _lib.ELM_P1)
+    assert st == _lib.ELM_ERR_ARG
+    st, h = _host_mesh(lib, v, m, 2, precision=_lib.ELM_FP32 | _lib.ELM_P1 | _lib.ELM_ADJOINT)
+    assert st == _lib.ELM_ERR_ARG                       # the adjoint is P2 only
+    assert b"adjoint" in lib.elm_last_error()
+
+
 def test_host_only_mesh_refuses_device_calls(lib):
     v, m = inputs.unit_square()
     st, h = _host_mesh(lib, v, m, 2)
@@ -136,6 +166,9 @@ def test_host_only_mesh_refuses_device_calls(lib):
     assert lib.elm_set_velocity(h, fake, fake, None) == _lib.ELM_ERR_STATE
     assert lib.elm_advect(h, fake, ctypes.c_void_p(4096), 0.1, 1, None) == _lib.ELM_ERR_STATE
     assert lib.elm_get_status(h, None) == _lib.ELM_ERR_STATE
+    assert lib.elm_trace(h, None, ctypes.c_void_p(4096), 0.1, 1, None) == _lib.ELM_ERR_STATE
+    assert lib.elm_trace_eval(h, fake, fake, ctypes.c_void_p(1 << 20), None) == _lib.ELM_ERR_STATE
+    assert lib.elm_trace(h, None, None, 0.1, 1, None) == _lib.ELM_ERR_ARG
     assert lib.elm_advect(None, fake, fake, 0.1, 1, None) == _lib.ELM_ERR_ARG
     assert lib.elm_mesh_destroy(h) == _lib.ELM_OK
     assert lib.elm_mesh_num_nodes(None) == 0

@@ -21,10 +21,10 @@ TOL = {"fp64": 1e-12, "fp32": 1e-5}
 class Pair:
     """The same mesh on both sides, with the node permutation between them."""
 
-    def __init__(self, mesh, level, precision="fp64"):
+    def __init__(self, mesh, level, precision="fp64", order=2):
         v, m = mesh_for(mesh) if isinstance(mesh, str) else mesh
-        self.om = oracle.OracleMesh(v, m, level)
-        self.gm = elm.Mesh(v, m, level, precision)
+        self.om = oracle.OracleMesh(v, m, level, order=order)
+        self.gm = elm.Mesh(v, m, level, precision, order=order)
         self.perm = match_nodes(self.om.coords, self.gm.unique_coords())
         self.precision = precision
         self.level = level
@@ -284,3 +284,156 @@ def test_argument_errors():
         gm.advect(T, -1.0)
     with pytest.raises(_lib.ElmError):
         gm.advect(T, 0.1, n_sub=65537)                   # above ELM_MAX_SUBSTEPS
+
+
+# ---------------------------------------------------------------------------
+# Linear (P1) elements (Sec. 3.1) and look-back over a time-dependent
+# velocity (Sec. 2.3.3) through elm_trace / elm_trace_eval.
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("mesh,level,vel,scal,cfl,n_sub,precision", [
+    ("square", 6, "rotation", "gauss", 3.0, 1, "fp64"),
+    ("square_block", 4, "fourier", "slotted", 6.0, 2, "fp64"),
+    ("cube", 4, "cellular", "slotted", 4.0, 2, "fp64"),
+    ("cube", 5, "fourier", "gauss", 8.0, 1, "fp64"),
+    ("cube_block", 2, "fourier", "gauss", 8.0, 2, "fp64"),
+    ("cube", 2, "rotation", "gauss", 5.0, 2, "fp64"),     # leaves the cube: clamping
+    ("square", 7, "fourier", "gauss", 4.0, 2, "fp32"),
+    ("cube", 5, "fourier", "gauss", 4.0, 1, "fp32"),
+    ("cube_block", 2, "cellular", "slotted", 8.0, 1, "fp32"),
+])
+def test_p1_parity(mesh, level, vel, scal, cfl, n_sub, precision):
+    P = Pair(mesh, level, precision, order=1)
+    u = velocity_for(vel, P.x)
+    T = scalar_for(scal, P.x)
+    dt = inputs.dt_for_cfl(cfl, level, u)
+    got, ref = P.step(T, u, dt, n_sub)
+    assert _err(got, ref, T) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_p1_time_dependent_velocity(precision):
+    P = Pair("cube", 4, precision, order=1)
+    u0 = inputs.cellular_flow(P.x)
+    u1 = inputs.random_fourier(P.x, seed=4)
+    T = scalar_for("gauss", P.x)
+    got, ref = P.step(T, u0, inputs.dt_for_cfl(3.0, 4, u1), 3, u_new=u1)
+    assert _err(got, ref, T) <= TOL[precision]
+
+
+def test_p1_table1_lookback_infinity():
+    """Table 1, 'MMOC P1 (b = infinity)': three bodies, one revolution in one
+    trace of 6283 RK4 substeps on 129 x 129 P1 nodes; the printed H0 is at
+    round-off level (1.38e-13), and the GPU matches the oracle to 1e-12."""
+    P = Pair("square", 7, "fp64", order=1)
+    u = inputs.rotation_2d(P.x, omega=1.0)
+    c0 = inputs.three_bodies(P.x)
+    P.gm.set_velocity(P.to_gpu(u))
+    got = P.from_gpu(P.gm.advect_lookback(P.to_gpu(c0), 2 * np.pi / 6283, 6283))
+    P.gm.status()
+    assert P.om.metrics(got, c0, c0)["h0"] < 3 * 1.38e-13
+    ref = P.om.advect(c0, u, 2 * np.pi, n_sub=6283)
+    assert _err(got, ref, c0) <= TOL["fp64"]
+
+
+def _trace_both(P, c0, fields, tau, n_sub=1):
+    """b = infinity over len(fields) - 1 intervals (newest first) on both
+    sides; returns (T_gpu, T_oracle, D_gpu, X_oracle) in oracle node order."""
+    us = [P.to_gpu(P.rounded(f)) for f in fields]
+    D = None
+    bufs = [torch.empty((P.gm.n_nodes, P.gm.dim), dtype=P.gm.dtype, device="cuda") for _ in range(2)]
+    for j, k in enumerate(range(len(fields) - 1, 0, -1)):
+        P.gm.set_velocity(us[k - 1], us[k])
+        D = P.gm.trace(D, tau, n_sub, out=bufs[j % 2])
+    Tg = P.gm.trace_eval(D, P.to_gpu(P.rounded(c0)))
+    P.gm.status()
+    X = P.x.copy()
+    for k in range(len(fields) - 1, 0, -1):
+        X = P.om.trace(X, P.rounded(fields[k - 1]), tau, n_sub, u_new=P.rounded(fields[k]))
+    To = P.om.eval(P.rounded(c0), X)
+    Dg = P.gm.to_unique(D).double().cpu().numpy()[P.perm]
+    return P.from_gpu(Tg), To, Dg, X
+
+
+@pytest.mark.parametrize("order,level,precision", [(1, 4, "fp64"), (2, 3, "fp64"), (1, 4, "fp32"), (2, 3, "fp32")])
+def test_trace_swirl_parity(order, level, precision):
+    """The swirling flow of Sec. 3.3 (time-dependent), b = infinity over 10
+    intervals of tau = 0.15: departure offsets and the final field against
+    the oracle's trace continuation."""
+    P = Pair("cube", level, precision, order=order)
+    c0 = inputs.gaussian(P.x, (0.35, 0.5, 0.5), 0.1)
+    tau = 0.15
+    fields = [inputs.swirl_3d(P.x, k * tau) for k in range(11)]
+    Tg, To, Dg, X = _trace_both(P, c0, fields, tau, n_sub=2)
+    dtol = 1e-12 if precision == "fp64" else 2e-5
+    assert np.abs((P.x + Dg) - X).max() <= dtol
+    assert _err(Tg, To, c0) <= (TOL["fp64"] if precision == "fp64" else 2e-4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_trace_then_eval_equals_advect(precision):
+    """One interval traced from the nodes and evaluated is the step itself,
+    bit for bit (same arithmetic, the offsets stored in the mesh precision)."""
+    v, m = inputs.cube_block(2, perturb=0.25, seed=7)
+    gm = elm.Mesh(v, m, 2, precision)
+    x = gm.node_coords()
+    u0 = torch.tensor(inputs.cellular_flow(x), dtype=gm.dtype, device="cuda")
+    u1 = torch.tensor(inputs.random_fourier(x, seed=2), dtype=gm.dtype, device="cuda")
+    T = torch.tensor(inputs.gaussian(x, (0.35, 0.5, 0.5), 0.1), dtype=gm.dtype, device="cuda")
+    for pair in ((u0, u0), (u0, u1)):
+        gm.set_velocity(*pair)
+        ref = gm.advect(T, 0.07, 2)
+        got = gm.trace_eval(gm.trace(None, 0.07, 2), T)
+        gm.status()
+        assert torch.equal(got, ref)
+
+
+def test_trace_copies_agree_and_errors():
+    P = Pair("cube_block", 1, "fp64", order=1)
+    u = P.to_gpu(inputs.random_fourier(P.x, seed=5))
+    P.gm.set_velocity(u)
+    D1 = P.gm.trace(None, 0.2, 1)
+    D2 = P.gm.trace(D1, 0.2, 1)
+    umap = torch.tensor(P.gm.unique_map(), device="cuda")
+    assert torch.equal(P.gm.to_unique(D2)[umap], D2)
+    with pytest.raises(_lib.ElmError):
+        P.gm.trace(D1, 0.2, 1, out=D1)             # in place: D_in and D_out overlap
+    with pytest.raises(_lib.ElmError):
+        P.gm.trace(D1, float("nan"), 1)
+    with pytest.raises(_lib.ElmError):
+        P.gm.trace(D1, 0.2, 0)
+    T = P.to_gpu(inputs.random_linear(P.x, seed=1))
+    with pytest.raises(_lib.ElmError):
+        P.gm.trace_eval(D1, T, out=T)              # T_src and T_dst overlap
+
+
+def test_table3_swirl_gpu():
+    """Table 3 (swirling flow, P1, b = infinity) on the GPU: the 33^3 rows
+    against the oracle (FP64, 1e-12) and all six rows against the printed
+    magnitudes (H0 within a factor 3, var = 1), including the 129^3 rows
+    (2,146,689 nodes)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table3_swirl_p1_binf.json")) as f:
+        rows = json.load(f)["rows"]
+    for level in (5, 7):
+        P = Pair("cube", level, "fp64", order=1)
+        assert P.gm.n_unique == {5: 35937, 7: 2146689}[level]
+        c0 = inputs.half_space(P.x)
+        c0g = P.to_gpu(c0)
+        for ref in [r for r in rows if r["dofs"] == P.gm.n_unique]:
+            tau = ref["tau"]
+            K = int(round(1.5 / tau))
+            fields = [P.to_gpu(inputs.swirl_3d(P.x, k * tau)) for k in range(K + 1)]
+            got = P.from_gpu(P.gm.advect_lookback_unsteady(c0g, fields, tau))
+            P.gm.status()
+            r = P.om.metrics(got, c0, c0)
+            assert ref["h0"] / 3 < r["h0"] < 3 * ref["h0"]
+            assert abs(r["var"] - 1.0) < 1e-12
+            if level == 5:
+                X = P.x.copy()
+                for k in range(K, 0, -1):
+                    X = P.om.trace(X, inputs.swirl_3d(P.x, (k - 1) * tau), tau, 1,
+                                   u_new=inputs.swirl_3d(P.x, k * tau))
+                assert _err(got, P.om.eval(c0, X), c0) <= TOL["fp64"]
