@@ -292,7 +292,10 @@ struct Tracer {
   R r0[D];
   int mb;             // the block's macro (uniform across the block)
   R njb[D * D];       // N J^{-1} of the block's macro
+  R bo[D + 1];        // per face of the block's macro: the tie band (interior face) or 0 (boundary face)
   R dlo[D], dhi[D];  // box limits as offsets from x_i
+
+  static constexpr R kBand = sizeof(R) == 4 ? R(kBand32) : R(kTol64);
 
   __device__ void load_block_macro(int mm) {
     mb = mm;
@@ -300,6 +303,22 @@ struct Tracer {
     for (int r = 0; r < D; ++r)
 #pragma unroll
       for (int c = 0; c < D; ++c) njb[r * D + c] = tab.nj(mm, r * 3 + c);
+    // A point within the band of a boundary face needs no walk decision (there
+    // is no macro behind it), so only interior faces keep the band.
+#pragma unroll
+    for (int k = 0; k <= D; ++k) bo[k] = tab.nb(mm, k) >= 0 ? kBand : R(0);
+  }
+
+  // Retraction into the reference simplex N >= q1 >= q2 (>= q3) >= 0: the
+  // cell is clamped to [0, N-1] and the order of the axes restored.
+  __device__ void retract(R* c, R* f) const {
+    if (c[0] < R(0)) { c[0] = R(0); f[0] = R(0); }
+    if (c[0] > Nf - R(1)) { c[0] = Nf - R(1); f[0] = R(1); }
+#pragma unroll
+    for (int k = 1; k < D; ++k) {
+      if (c[k] > c[k - 1] || (c[k] == c[k - 1] && f[k] > f[k - 1])) { c[k] = c[k - 1]; f[k] = f[k - 1]; }
+      if (c[k] < R(0)) { c[k] = R(0); f[k] = R(0); }
+    }
   }
 
   // N J^{-1} entry of the current macro: the block's macro from registers,
@@ -358,12 +377,26 @@ struct Tracer {
     for (int hop = 0;; ++hop) {
       R r[D];
       if (m == mb) {
+        if constexpr (sizeof(R) == 4 && D == 3) {
+          // rows 0 and 1 as one packed FP32x2 FMA chain (same per-lane rounding)
+          float2 a01 = make_float2(r0[0], r0[1]);
+          float a2 = r0[D - 1];
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-          R v = r0[k];
+          for (int j = 0; j < D; ++j) {
+            a01 = __ffma2_rn(make_float2(njb[j], njb[D + j]), make_float2(d[j], d[j]), a01);
+            a2 = fmaf(njb[2 * D + j], d[j], a2);
+          }
+          r[0] = a01.x;
+          r[1] = a01.y;
+          r[D - 1] = a2;
+        } else {
 #pragma unroll
-          for (int j = 0; j < D; ++j) v = r_fma(njb[k * D + j], d[j], v);
-          r[k] = v;
+          for (int k = 0; k < D; ++k) {
+            R v = r0[k];
+#pragma unroll
+            for (int j = 0; j < D; ++j) v = r_fma(njb[k * D + j], d[j], v);
+            r[k] = v;
+          }
         }
       } else {
         const Vec3<R> v = lattice_foreign<D, R>(tab, m, r0[0], r0[1], D == 3 ? r0[D - 1] : R(0), d[0], d[1],
@@ -383,11 +416,23 @@ struct Tracer {
 #pragma unroll
       for (int k = 1; k < D; ++k) l[k] = (c[k - 1] - c[k]) + (f[k - 1] - f[k]);
       l[D] = c[D - 1] + f[D - 1];
+      // common case: inside the block's macro, clear of its interior faces.
+      // With every l >= 0 the cell is in range except on the face q1 = N
+      // (c1 = N), which the retraction clamps.
+      {
+        bool in = m == mb;
+#pragma unroll
+        for (int k = 0; k <= D; ++k) in = in && l[k] >= bo[k];
+        if (in) {
+          if (c[0] > Nf - R(1)) retract(c, f);
+          return;
+        }
+      }
       lmin = l[0];
 #pragma unroll
       for (int k = 1; k <= D; ++k) lmin = r_min(lmin, l[k]);
-      // common case: inside the current macro, clear of its faces
-      if (lmin >= R(sizeof(R) == 4 ? kBand32 : kTol64)) return;
+      // a foreign macro, clear of its faces
+      if (lmin >= kBand) return;
       int kmin = D;
 #pragma unroll
       for (int k = D - 1; k >= 0; --k)
@@ -417,13 +462,7 @@ struct Tracer {
       foreign_frame(nb);
     }
     if (lmin > R(0)) return;
-    if (c[0] < R(0)) { c[0] = R(0); f[0] = R(0); }
-    if (c[0] > Nf - R(1)) { c[0] = Nf - R(1); f[0] = R(1); }
-#pragma unroll
-    for (int k = 1; k < D; ++k) {
-      if (c[k] > c[k - 1] || (c[k] == c[k - 1] && f[k] > f[k - 1])) { c[k] = c[k - 1]; f[k] = f[k - 1]; }
-      if (c[k] < R(0)) { c[k] = R(0); f[k] = R(0); }
-    }
+    retract(c, f);
   }
 
   // P2 stencil of the micro simplex holding (c, f): storage slots and basis
@@ -592,14 +631,29 @@ struct Tracer {
     int slot[NB];
     R phi[NB];
     stencil(c, f, slot, phi);
+    if constexpr (sizeof(R) == 4 && D == 3) {
+      // (x, y) as one packed FP32x2 FMA chain (same per-lane rounding and order)
+      float2 kxy = make_float2(0.f, 0.f);
+      float kz = 0.f;
 #pragma unroll
-    for (int r = 0; r < D; ++r) k[r] = R(0);
+      for (int j = 0; j < NB; ++j) {
+        const float4 w = __ldg(reinterpret_cast<const float4*>(un) + slot[j]);
+        kxy = __ffma2_rn(make_float2(phi[j], phi[j]), make_float2(w.x, w.y), kxy);
+        kz = fmaf(phi[j], w.z, kz);
+      }
+      k[0] = kxy.x;
+      k[1] = kxy.y;
+      k[D - 1] = kz;
+    } else {
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      R v[D];
-      load_rec(un, slot[j], v);
+      for (int r = 0; r < D; ++r) k[r] = R(0);
 #pragma unroll
-      for (int r = 0; r < D; ++r) k[r] = r_fma(phi[j], v[r], k[r]);
+      for (int j = 0; j < NB; ++j) {
+        R v[D];
+        load_rec(un, slot[j], v);
+#pragma unroll
+        for (int r = 0; r < D; ++r) k[r] = r_fma(phi[j], v[r], k[r]);
+      }
     }
     if constexpr (!STEADY) {
       R ko[D];
