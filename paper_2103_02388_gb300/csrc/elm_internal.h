@@ -21,11 +21,25 @@ constexpr unsigned kFlagNonFinite = 2u;
 // {1 >= s_1 >= .. >= s_d >= 0} is mapped by x = P_0 + J s with
 // J = [P_1 - P_0 | P_2 - P_1 | P_3 - P_2], and the level-L lattice coordinate
 // is q = N s = NJinv (x - P_0), N = 2^L.
+// Lattice frame change across face k of a macro m to its neighbour mm:
+// q_mm = A q_m + b with A = J_mm^{-1} J_m and b = N J_mm^{-1} (v0_m - v0_mm).
+// Stored when A and b are exactly integers (bit k of `exact`), as for macros
+// that are lattice-congruent images of one another (the Kuhn tetrahedra of a
+// cube, the two triangles of a square); a point on the lattice of m with
+// half-integer coordinates then changes frame in exact integer-valued
+// arithmetic instead of recomputing its position.
+struct FaceXform {
+  int8_t A[4][9];    // row-major d x d per face
+  int32_t b[4][3];
+  int32_t exact;     // bit k: face k's transform is stored
+};
+
 struct MacroGeo {
   double v0[3];
   double J[9];       // row-major d x d (leading d x d block used in 2D)
   double NJinv[9];   // row-major, N * J^{-1}
   int32_t nb[4];     // macro across the face opposite local vertex k; -1 = boundary
+  FaceXform x;
 };
 
 // FP32 copy of the macro data, used by the FP32 kernel.  Each FP64 value x is
@@ -40,6 +54,7 @@ struct MacroGeo32 {
   float NJinv_lo[9];
   float J_lo[9];
   float v0_lo[3];
+  FaceXform x;
 };
 
 // Launch constants in the kernel's working precision, computed once on the

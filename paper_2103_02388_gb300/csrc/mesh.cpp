@@ -147,6 +147,41 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
       me->geo[b.first].nb[b.second] = int32_t(a.first);
     }
   }
+  // Exact lattice frame changes across faces (FaceXform): A = J_mm^{-1} J_m
+  // = NJinv_mm J_m / N and b = NJinv_mm (v0_m - v0_mm), kept only when every
+  // entry is exactly an integer in FP64 and small.
+  for (int64_t m = 0; m < nm; ++m) {
+    MacroGeo& g = me->geo[m];
+    std::memset(&g.x, 0, sizeof(g.x));
+    for (int k = 0; k <= d; ++k) {
+      const int64_t mm = g.nb[k];
+      if (mm < 0) continue;
+      const MacroGeo& h = me->geo[mm];
+      bool ok = true;
+      double A[9] = {0}, b[3] = {0};
+      for (int r = 0; r < d; ++r) {
+        for (int c = 0; c < d; ++c) {
+          double s = 0.0;
+          for (int j = 0; j < d; ++j) s += h.NJinv[r * 3 + j] * g.J[j * 3 + c];
+          A[r * 3 + c] = s / double(me->N);
+        }
+        double t = 0.0;
+        for (int j = 0; j < d; ++j) t += h.NJinv[r * 3 + j] * (g.v0[j] - h.v0[j]);
+        b[r] = t;
+      }
+      for (int r = 0; r < d && ok; ++r) {
+        ok = b[r] == std::nearbyint(b[r]) && std::fabs(b[r]) < double(1 << 20);
+        for (int c = 0; c < d && ok; ++c)
+          ok = A[r * 3 + c] == std::nearbyint(A[r * 3 + c]) && std::fabs(A[r * 3 + c]) <= 8.0;
+      }
+      if (!ok) continue;
+      for (int r = 0; r < d; ++r) {
+        for (int c = 0; c < d; ++c) g.x.A[k][r * 3 + c] = int8_t(A[r * 3 + c]);
+        g.x.b[k][r] = int32_t(b[r]);
+      }
+      g.x.exact |= 1 << k;
+    }
+  }
 
   // Storage layout and interface owners.  Lattice point p of macro m sits at
   // slot m * npm + packed(p); its integer barycentric weights are
@@ -254,6 +289,7 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
     }
     for (int k = 0; k < 3; ++k) split(me->geo[m].v0[k], &g32[m].v0[k], &g32[m].v0_lo[k]);
     for (int k = 0; k < 4; ++k) g32[m].nb[k] = me->geo[m].nb[k];
+    g32[m].x = me->geo[m].x;
   }
   bool ok = upload((void**)&me->d_geo, me->geo.data(), sizeof(MacroGeo) * nm) &&
             upload((void**)&me->d_geo32, g32.data(), sizeof(MacroGeo32) * nm) &&

@@ -94,6 +94,7 @@ struct Tables<double> {
   __device__ double J(int m, int k) const { return g[m].J[k]; }
   __device__ double v0(int m, int k) const { return g[m].v0[k]; }
   __device__ int nb(int m, int k) const { return g[m].nb[k]; }
+  __device__ const FaceXform& xf(int m) const { return g[m].x; }
 };
 
 template <>
@@ -103,6 +104,7 @@ struct Tables<float> {
   __device__ float J(int m, int k) const { return g[m].J[k]; }
   __device__ float v0(int m, int k) const { return g[m].v0[k]; }
   __device__ int nb(int m, int k) const { return g[m].nb[k]; }
+  __device__ const FaceXform& xf(int m) const { return g[m].x; }
 };
 
 __device__ __forceinline__ int tri2(int k) { return k * (k + 1) / 2; }
@@ -369,6 +371,41 @@ struct Tracer {
     }
   }
 
+  // Walks across face k of the current macro into its neighbour mm.  Across a
+  // face with an exact integer frame change (FaceXform) a start node on the
+  // half-integer lattice of the current frame changes frame exactly in the
+  // working precision (a few FMAs); otherwise the frame is recomputed from
+  // the start node (foreign_frame).  Both give the same (bq, r0).
+  __device__ void cross_face(int mm, int k) {
+    if (mm != m0) {
+      const FaceXform& x = tab.xf(m);
+      bool half = ((x.exact >> k) & 1) != 0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) half = half && (r0[j] == R(0) || r0[j] == R(0.5));
+      if (half) {
+        R s[D], q[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) s[j] = bq[j] + r0[j];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+          R v = to_real<R>(x.b[k][r]);
+#pragma unroll
+          for (int c = 0; c < D; ++c) v = r_fma(to_real<R>(x.A[k][r * 3 + c]), s[c], v);
+          q[r] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+          const R fl = r_floor(q[r]);
+          bq[r] = fl;
+          r0[r] = q[r] - fl;
+        }
+        m = mm;
+        return;
+      }
+    }
+    foreign_frame(mm);
+  }
+
   // Locates x_i + d: walks macros from the current frame, returns the micro
   // cell c (integer-valued reals) and fractions f, retracted into the
   // macro's reference simplex N >= q1 >= q2 (>= q3) >= 0.
@@ -459,7 +496,7 @@ struct Tracer {
         atomicOr(status, kFlagWalkLimit);
         break;
       }
-      foreign_frame(nb);
+      cross_face(nb, kmin);
     }
     if (lmin > R(0)) return;
     retract(c, f);
