@@ -507,9 +507,71 @@ struct Tracer {
   // lattice offset o in {0, 1, 2} of the node from 2c; sorting the axes by
   // descending fraction (ties by axis) orders the Kuhn path c -> c + 1, and
   // each node's offsets along the sorted axes are fixed (alpha >= beta >= gamma).
+  // 3D P2 stencil by ranks (FP32 kernel): the packed index of c + o is S0
+  // plus per-axis increments (T3 / T2 differences for the first two axes, 1
+  // and 2 for the last), so with the axes in stable descending order of their
+  // fractions (sigma0, sigma1, sigma2) only the increments of sigma0 and
+  // sigma1 are selected, and the all-1 and all-2 offsets need no order.  Same
+  // slots and basis values as the sorting form below, with fewer selects;
+  // sigma0 != sigma1 by construction, so the slots are always those of a
+  // valid micro simplex.  (The FP64 kernel keeps the sorting form: its extra
+  // FP64 min operations would load the narrow FP64 pipe.)
+  __device__ void stencil_p2_3d(const R* c, const R* f, int* slot, R* phi) const {
+    const int k0 = 2 * f2i_exact(c[0]);
+    const int k1 = 2 * f2i_exact(c[1]);
+    const int k2 = 2 * f2i_exact(c[2]);
+    const int d10 = tri2(k0 + 1);          // T3(k0 + 1) - T3(k0)
+    const int d20 = d10 + tri2(k0 + 2);    // T3(k0 + 2) - T3(k0)
+    const int d11 = k1 + 1;                // T2(k1 + 1) - T2(k1)
+    const int d21 = 2 * k1 + 3;            // T2(k1 + 2) - T2(k1)
+    const int S0 = tri3(k0) + tri2(k1) + k2 + m * npm;
+    const int S1 = S0 + d10 + d11 + 1;
+    const int S2 = S0 + d20 + d21 + 2;
+    const bool g01 = f[1] > f[0], g02 = f[2] > f[0], g12 = f[2] > f[1];
+    const bool first0 = !g01 && !g02;      // sigma0 = 0
+    const bool first1 = !first0 && !g12;   // sigma0 = 1 (else 2)
+    const bool sec2 = first0 ? g12 : (first1 ? g02 : false);   // sigma1 = 2
+    const bool sec1 = first0 ? !g12 : (first1 ? false : g01);  // sigma1 = 1 (else 0)
+    const int a1 = first0 ? d10 : (first1 ? d11 : 1);
+    const int a2 = first0 ? d20 : (first1 ? d21 : 2);
+    const int b1 = sec2 ? 1 : (sec1 ? d11 : d10);
+    const int b2 = sec2 ? 2 : (sec1 ? d21 : d20);
+    const R fs0 = first0 ? f[0] : (first1 ? f[1] : f[2]);
+    const R fs1 = sec2 ? f[2] : (sec1 ? f[1] : f[0]);
+    const R fs2 = r_min(r_min(f[0], f[1]), f[2]);
+    const int v1 = S0 + a2;
+    const int e01 = S0 + a1;
+    const int e13 = S1 + a2 - a1;
+    slot[0] = S0;
+    slot[1] = v1;
+    slot[2] = v1 + b2;
+    slot[3] = S2;
+    slot[4] = e01;
+    slot[5] = e01 + b1;
+    slot[6] = S1;
+    slot[7] = v1 + b1;
+    slot[8] = e13;
+    slot[9] = e13 + b2 - b1;
+    const R L0 = R(1) - fs0, L1 = fs0 - fs1, L2 = fs1 - fs2, L3 = fs2;
+    phi[0] = L0 * (R(2) * L0 - R(1));
+    phi[1] = L1 * (R(2) * L1 - R(1));
+    phi[2] = L2 * (R(2) * L2 - R(1));
+    phi[3] = L3 * (R(2) * L3 - R(1));
+    phi[4] = R(4) * L0 * L1;
+    phi[5] = R(4) * L0 * L2;
+    phi[6] = R(4) * L0 * L3;
+    phi[7] = R(4) * L1 * L2;
+    phi[8] = R(4) * L1 * L3;
+    phi[9 % NB] = R(4) * L2 * L3;
+  }
+
   __device__ void stencil(const R* c, const R* f, int* slot, R* phi) const {
     if constexpr (P == 1) {
       stencil_p1(c, f, slot, phi);
+      return;
+    }
+    if constexpr (D == 3 && sizeof(R) == 4) {
+      stencil_p2_3d(c, f, slot, phi);
       return;
     }
     int A[D][3];
