@@ -105,14 +105,30 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(workload):
+def _profile_record():
+    """The committed ncu figures of the advection kernel, or None once the
+    kernel's sources have changed since they were taken."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
-        if t.get("kernel_sha") == _kernel_hash() and workload in t.get("per_launch_bytes", {}):
-            return float(t["per_launch_bytes"][workload])
+        if t.get("kernel_sha") == _kernel_hash():
+            return t
     except Exception:
         pass
+    return None
+
+
+def _traffic(workload):
+    t = _profile_record()
+    if t is not None and workload in t.get("per_launch_bytes", {}):
+        return float(t["per_launch_bytes"][workload])
+    return None
+
+
+def _utilisation(workload):
+    t = _profile_record()
+    if t is not None and workload in t.get("utilisation", {}):
+        return t["utilisation"][workload]
     return None
 
 
@@ -367,7 +383,8 @@ def run_ours(args, spec):
                      "traffic": _traffic(args.workload), "algorithmic_bytes_per_launch": alg_bytes,
                      "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                              "frac": hbm_achieved / hbm_peak, "peak_kind": peak_kind},
-                     "kernel": "k_advect", "avg_launch_ms": ms_per_step},
+                     "kernel": "k_advect", "avg_launch_ms": ms_per_step,
+                     "ncu_utilisation": _utilisation(args.workload)},
         "gpu_launches": args.steps,
         "clocks": clocks.summary(),
         "e2e": e2e,
