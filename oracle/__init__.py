@@ -65,6 +65,9 @@ def _load():
         lib.orc_micro_simplices.restype = I64
         lib.orc_micro_simplices.argtypes = [P, P, P]
         lib.orc_mass_unit.argtypes = [I32, I32, P]
+        lib.orc_element_matrices.restype = I64
+        lib.orc_element_matrices.argtypes = [P, P, P, P]
+        lib.orc_boundary_nodes.argtypes = [P, P]
         _lib = lib
     return _lib
 
@@ -220,6 +223,61 @@ class OracleMesh:
         _load().orc_advect_transpose(self._h, _ptr(u_old), _ptr(u_new), _ptr(g_new), _ptr(out),
                                      float(dt), int(n_sub))
         return out
+
+    # -- diffusion step (Eq. linear system) ----------------------------------
+    def element_matrices(self):
+        """(nodes [n_simplices, nb], M_e [n_simplices, nb, nb], A_e [...]) of every
+        micro simplex: local mass and stiffness matrices."""
+        lib = _load()
+        n = int(lib.orc_element_matrices(self._h, None, None, None))
+        nb = self.dim + 1 if self.order == 1 else (self.dim + 1) * (self.dim + 2) // 2
+        nodes = np.empty((n, nb), np.int32)
+        Me = np.empty((n, nb, nb))
+        Ae = np.empty((n, nb, nb))
+        lib.orc_element_matrices(self._h, _ptr(nodes), _ptr(Me), _ptr(Ae))
+        return nodes, Me, Ae
+
+    def assemble(self):
+        """Global sparse mass matrix M and stiffness matrix A (scipy CSR)."""
+        import scipy.sparse as sp
+        nodes, Me, Ae = self.element_matrices()
+        nb = nodes.shape[1]
+        rows = np.repeat(nodes, nb, axis=1).ravel()
+        cols = np.tile(nodes, (1, nb)).ravel()
+        shape = (self.n_nodes, self.n_nodes)
+        M = sp.coo_matrix((Me.ravel(), (rows, cols)), shape=shape).tocsr()
+        A = sp.coo_matrix((Ae.ravel(), (rows, cols)), shape=shape).tocsr()
+        return M, A
+
+    def boundary(self):
+        """Boolean mask of the nodes on the boundary of the mesh."""
+        out = np.empty(self.n_nodes, np.uint8)
+        _load().orc_boundary_nodes(self._h, _ptr(out))
+        return out.astype(bool)
+
+    def diffusion_step(self, c_hat, tau, kappa, theta=1.0, c_bnd=None, q_old=None, q_new=None):
+        """One solve of Eq. (linear system): (M + tau theta kappa A) c =
+        (M - tau (1 - theta) kappa A) c_hat + tau (theta q_new + (1 - theta) q_old),
+        with c = c_bnd on the boundary nodes (Dirichlet; c_bnd defaults to
+        c_hat there).  q_old / q_new are nodal source values (the load vector
+        is M q).  Direct sparse solve on the interior nodes."""
+        import scipy.sparse.linalg as sla
+        M, A = self._ma if getattr(self, "_ma", None) is not None else self.assemble()
+        self._ma = (M, A)
+        c_hat = _f64(c_hat)
+        E = (M + (tau * theta * kappa) * A).tocsr()
+        b = M @ c_hat - (tau * (1.0 - theta) * kappa) * (A @ c_hat)
+        if q_old is not None or q_new is not None:
+            q = theta * (_f64(q_new) if q_new is not None else 0.0) + (1.0 - theta) * (
+                _f64(q_old) if q_old is not None else 0.0)
+            b = b + tau * (M @ (q * np.ones(self.n_nodes)))
+        bnd = self.boundary()
+        c = np.empty(self.n_nodes)
+        c[bnd] = (c_hat if c_bnd is None else _f64(c_bnd))[bnd]
+        inner = ~bnd
+        rhs = b[inner] - E[inner][:, bnd] @ c[bnd]
+        c[inner] = sla.spsolve(E[inner][:, inner].tocsc(), rhs)
+        return c
 
     # -- metrics (Sec. 3.1) ---------------------------------------------------
     def mass_product(self, a, b=None):

@@ -553,6 +553,146 @@ double simplex_volume(int d, const double V[4][3]) {
 }
 
 // ---------------------------------------------------------------------------
+// Diffusion step (Eq. finite-dimensional Galerkin approximation, Eq. linear
+// system): mass and stiffness matrices of every micro simplex, assembled into
+// sparse M and A by the Python wrapper.  With grad phi_i = sum_k
+// (dphi_i / dlam_k) grad lam_k the stiffness entry is
+//   A_ij = sum_{k,l} (grad lam_k . grad lam_l) int_T (dphi_i/dlam_k)(dphi_j/dlam_l),
+// every integral exact by the barycentric monomial formula above.
+// ---------------------------------------------------------------------------
+
+Poly diff_poly(const Poly& P, int k) {
+  Poly D;
+  for (auto& t : P.c) {
+    if (t.first[k] == 0) continue;
+    std::array<int, 4> e = t.first;
+    const double f = t.second * e[k];
+    e[k] -= 1;
+    D.c[e] += f;
+  }
+  return D;
+}
+
+// int_T A B over a simplex of unit volume.
+double integrate_unit(int d, const Poly& A, const Poly& B) {
+  double s = 0.0;
+  for (auto& ta : A.c)
+    for (auto& tb : B.c) {
+      int tot = 0;
+      double num = factorial(d);
+      for (int k = 0; k <= d; ++k) {
+        const int e = ta.first[k] + tb.first[k];
+        tot += e;
+        num *= factorial(e);
+      }
+      s += ta.second * tb.second * num / factorial(d + tot);
+    }
+  return s;
+}
+
+// Gradients of the barycentric coordinates of the simplex V: for k >= 1 row
+// k-1 of J^{-1}, J = [V1 - V0 | ... | Vd - V0]; grad lam_0 = -sum of the others.
+void grad_lambdas(int d, const double V[4][3], double G[4][3]) {
+  double J[9], I[9];
+  for (int r = 0; r < d; ++r)
+    for (int c = 0; c < d; ++c) J[r * d + c] = V[c + 1][r] - V[0][r];
+  for (int c = 0; c < d; ++c) {  // column c of J^{-1}: solve J z = e_c
+    double e[3] = {0.0, 0.0, 0.0}, z[3];
+    e[c] = 1.0;
+    solve_small(d, J, e, z);
+    for (int r = 0; r < d; ++r) I[r * d + c] = z[r];
+  }
+  for (int r = 0; r < 3; ++r) G[0][r] = 0.0;
+  for (int k = 1; k <= d; ++k)
+    for (int r = 0; r < d; ++r) {
+      G[k][r] = I[(k - 1) * d + r];
+      G[0][r] -= G[k][r];
+    }
+}
+
+// Per-micro-simplex local node ids [n_simplices, nb] and matrices
+// [n_simplices, nb, nb] of the mass and the stiffness; returns the number of
+// micro simplices (the outputs may be null to query it).
+int64_t element_matrices(const Mesh& me, int32_t* node_out, double* M_out, double* A_out) {
+  const int d = me.d, nb = n_basis(d, me.order);
+  std::vector<double> Mref(nb * nb);
+  mass_unit(d, me.order, Mref.data());
+  // Iref[((i * nb + j) * (d+1) + k) * (d+1) + l] = int_unit (dphi_i/dlam_k)(dphi_j/dlam_l)
+  std::vector<double> Iref(nb * nb * (d + 1) * (d + 1));
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j)
+      for (int k = 0; k <= d; ++k)
+        for (int l = 0; l <= d; ++l)
+          Iref[((i * nb + j) * (d + 1) + k) * (d + 1) + l] =
+              integrate_unit(d, diff_poly(basis_poly(d, me.order, i), k), diff_poly(basis_poly(d, me.order, j), l));
+  int64_t n = 0;
+  for_each_micro_simplex(me, [&](int64_t m, int w[4][3]) {
+    if (node_out) {
+      Located lc;
+      lc.macro = m;
+      for (int j = 0; j <= d; ++j)
+        for (int r = 0; r < d; ++r) lc.w[j][r] = w[j][r];
+      for (int j = 0; j < 4; ++j) lc.mu[j] = 0.0;
+      double phi[10];
+      stencil(me, lc, node_out + n * nb, phi);
+      double V[4][3], G[4][3];
+      for (int j = 0; j <= d; ++j) {
+        int wt[4];
+        lattice_weights(d, me.N, w[j], wt);
+        lattice_point(me.mac[m], d, wt, me.N, V[j]);
+      }
+      const double vol = simplex_volume(d, V);
+      grad_lambdas(d, V, G);
+      double* Me = M_out + n * nb * nb;
+      double* Ae = A_out + n * nb * nb;
+      for (int i = 0; i < nb; ++i)
+        for (int j = 0; j < nb; ++j) {
+          Me[i * nb + j] = vol * Mref[i * nb + j];
+          double a = 0.0;
+          for (int k = 0; k <= d; ++k)
+            for (int l = 0; l <= d; ++l) {
+              double g = 0.0;
+              for (int r = 0; r < d; ++r) g += G[k][r] * G[l][r];
+              a += g * Iref[((i * nb + j) * (d + 1) + k) * (d + 1) + l];
+            }
+          Ae[i * nb + j] = vol * a;
+        }
+    }
+    ++n;
+  });
+  return n;
+}
+
+// Nodes on the boundary of the macro mesh: a node lies on face k of a macro
+// where its barycentric weight k is 0; the face is a boundary face when no
+// other macro shares its vertices.
+void boundary_nodes(const Mesh& me, uint8_t* out) {
+  const int d = me.d;
+  std::map<std::array<int64_t, 3>, int> count;
+  auto face_key = [&](const Macro& mc, int k) {
+    std::array<int64_t, 3> f{-1, -1, -1};
+    int n = 0;
+    for (int j = 0; j <= d; ++j)
+      if (j != k) f[n++] = mc.v[j];
+    std::sort(f.begin(), f.begin() + d);
+    return f;
+  };
+  for (auto& mc : me.mac)
+    for (int k = 0; k <= d; ++k) count[face_key(mc, k)] += 1;
+  std::fill(out, out + me.n_nodes, uint8_t(0));
+  for (int64_t m = 0; m < (int64_t)me.mac.size(); ++m) {
+    bool bface[4] = {false, false, false, false};
+    for (int k = 0; k <= d; ++k) bface[k] = count[face_key(me.mac[m], k)] == 1;
+    for_each_lattice_point(d, me.M, [&](const int* p) {
+      int w[4];
+      lattice_weights(d, me.M, p, w);
+      for (int k = 0; k <= d; ++k)
+        if (w[k] == 0 && bface[k]) out[me.id[m][me.dense(p)]] = 1;
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Forward-mode directional derivatives (dual numbers) of the advection step
 // with respect to the nodal velocity: each velocity value u_j becomes
 // u_j + eps v_j and every operation of the step above is repeated on pairs
@@ -891,6 +1031,15 @@ int64_t orc_micro_simplices(void* h, int64_t* macro, int32_t* wv) {
   });
   return n;
 }
+
+// Local node ids, mass and stiffness matrices of every micro simplex (see
+// element_matrices); returns the number of micro simplices.
+int64_t orc_element_matrices(void* h, int32_t* node_out, double* M_out, double* A_out) {
+  return element_matrices(*static_cast<Mesh*>(h), node_out, M_out, A_out);
+}
+
+// 1 for nodes on the boundary of the mesh, else 0 ([n_nodes]).
+void orc_boundary_nodes(void* h, uint8_t* out) { boundary_nodes(*static_cast<Mesh*>(h), out); }
 
 // Reference P1 / P2 mass matrix for a simplex of unit volume ([nb, nb]).
 void orc_mass_unit(int d, int order, double* out) { mass_unit(d, order, out); }

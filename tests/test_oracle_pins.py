@@ -651,3 +651,83 @@ def test_table3_swirl_p1_level5():
         assert ref["h0"] / 3 < got["h0"] < 3 * ref["h0"]
         assert abs(got["var"] - 1.0) < 1e-12
         assert abs(got["dm"]) < 3e-4
+
+
+# ---------------------------------------------------------------------------
+# Diffusion step (Eq. finite-dimensional Galerkin approximation, Eq. linear
+# system): stiffness and mass assembly and the Theta-scheme solve.
+# ---------------------------------------------------------------------------
+
+
+def test_p2_stiffness_reference_triangle_textbook():
+    """The P2 stiffness matrix of the right triangle (0,0), (1,0), (0,1) is the
+    textbook one: 1/6 [[6,1,1,-4,-4,0],[1,3,0,-4,0,0],[1,0,3,0,-4,0],
+    [-4,-4,0,16,0,-8],[-4,0,-4,0,16,-8],[0,0,0,-8,-8,16]] in the order
+    vertices, then edges (0,1), (0,2), (1,2)."""
+    me = oracle.OracleMesh(np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]]), np.array([[0, 1, 2]]), 0)
+    nodes, Me, Ae = me.element_matrices()
+    expect = np.array([[6, 1, 1, -4, -4, 0], [1, 3, 0, -4, 0, 0], [1, 0, 3, 0, -4, 0],
+                       [-4, -4, 0, 16, 0, -8], [-4, 0, -4, 0, 16, -8], [0, 0, 0, -8, -8, 16]]) / 6.0
+    assert np.abs(me.coords[nodes[0]] - [[0, 0], [1, 0], [0, 1], [0.5, 0], [0, 0.5], [0.5, 0.5]]).max() == 0
+    assert np.abs(Ae[0] - expect).max() < 1e-14
+
+
+@pytest.mark.parametrize("dim,order", [(2, 2), (3, 2), (2, 1), (3, 1)])
+def test_stiffness_integrates_gradients_exactly(dim, order):
+    """x^T A y = int grad x_h . grad y_h, exact for fields in the space (P2:
+    quadratics, P1: linears) on a perturbed mesh; A 1 = 0 and A symmetric."""
+    v, m = inputs.cube_block(2, 0.3, 7) if dim == 3 else inputs.square_block(2, 0.3, 7)
+    me = oracle.OracleMesh(v, m, 2 if dim == 3 else 3, order=order)
+    M, A = me.assemble()
+    x = me.coords
+    one = np.ones(me.n_nodes)
+    assert np.abs(A @ one).max() < 1e-12
+    assert abs(A - A.T).max() < 1e-14
+    if order == 2:
+        f = x[:, 0] ** 2                                   # |grad|^2 = 4 x^2
+        assert abs(f @ (A @ f) - 4.0 / 3.0) < 1e-12
+        g = x[:, 0] * x[:, 1]                              # |grad|^2 = x^2 + y^2
+        assert abs(g @ (A @ g) - 2.0 / 3.0) < 1e-12
+        assert abs(f @ (A @ g) - 2.0 / 4.0) < 1e-12        # int 2x * y = 1/2
+    else:
+        f = 2.0 * x[:, 0] - x[:, 1]
+        assert abs(f @ (A @ f) - 5.0) < 1e-12
+    assert abs(one @ (M @ one) - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("dim,order,theta", [(2, 2, 1.0), (3, 2, 0.5), (3, 1, 1.0), (2, 1, 0.5)])
+def test_diffusion_step_reproduces_fields_in_the_space(dim, order, theta):
+    """Manufactured solution: for u in the space (quadratic for P2, linear for
+    P1), c_hat = u - tau kappa Delta u differs from u by a constant, so
+    grad c_hat = grad u and, for every test function v vanishing on the
+    boundary, (u - c_hat, v) / tau + kappa (grad u, grad v) = kappa ((Delta u,
+    v) + (grad u, grad v)) = 0 by integration by parts, for any theta: u is
+    the exact discrete solution with c = u on the boundary."""
+    v, m = inputs.cube_block(2, 0.25, 3) if dim == 3 else inputs.square_block(2, 0.25, 3)
+    me = oracle.OracleMesh(v, m, 2 if dim == 3 else 3, order=order)
+    x = me.coords
+    if order == 2:
+        u = 0.3 + x[:, 0] ** 2 - 2.0 * x[:, 0] * x[:, 1] + 0.5 * x[:, 1] ** 2 + 0.2 * x[:, 0]
+        lap = 2.0 + 1.0                                    # Delta u
+    else:
+        u = 0.3 + 0.7 * x[:, 0] - 0.4 * x[:, 1]
+        lap = 0.0
+    tau, kappa = 0.05, 0.3
+    # c_hat quadratic with Delta c_hat = lap: (u - c_hat)/tau = kappa lap
+    c_hat = u - tau * kappa * lap
+    c = me.diffusion_step(c_hat, tau, kappa, theta, c_bnd=u)
+    assert np.abs(c - u).max() < 1e-12
+
+
+def test_diffusion_step_decays_a_fourier_mode():
+    """Implicit Euler on sin(pi x) sin(pi y) (zero on the boundary): one step
+    multiplies the mode by about 1 / (1 + tau kappa 2 pi^2) (the exact
+    eigenvalue of the Laplacian, up to the discretisation error)."""
+    v, m = inputs.unit_square()
+    me = oracle.OracleMesh(v, m, 5)
+    x = me.coords
+    mode = np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1])
+    tau, kappa = 0.01, 1.0
+    c = me.diffusion_step(mode, tau, kappa, 1.0, c_bnd=np.zeros(me.n_nodes))
+    ratio = (mode @ c) / (mode @ mode)
+    assert abs(ratio - 1.0 / (1.0 + tau * kappa * 2 * np.pi ** 2)) < 1e-5
