@@ -32,6 +32,8 @@
  *  - Errors: argument errors are returned synchronously and leave the
  *    mesh unchanged; device-side conditions (walk limit, non-finite values)
  *    set flags that elm_get_status reports.  No call traps or exits.
+ *    (elm_diffusion_step is the one call that also synchronises: its
+ *    iterative solve tests convergence on the host.)
  *    elm_last_error() returns a thread-local message for the last failure.
  */
 #ifndef ELM_H
@@ -53,7 +55,8 @@ typedef enum {
   ELM_ERR_TOPOLOGY = 3,   /* degenerate macro or a face shared by > 2 macros */
   ELM_ERR_WALK_LIMIT = 4, /* a point needed more macro hops than the limit */
   ELM_ERR_NONFINITE = 5,  /* a velocity or result value was NaN / Inf */
-  ELM_ERR_STATE = 6       /* call order violated (e.g. advect before set_velocity) */
+  ELM_ERR_STATE = 6,      /* call order violated (e.g. advect before set_velocity) */
+  ELM_ERR_NOT_CONVERGED = 7 /* an iterative solve stopped at its iteration limit */
 } elm_status;
 
 enum { ELM_FP64 = 0, ELM_FP32 = 1 };
@@ -77,6 +80,12 @@ enum { ELM_ADJOINT = 0x200 };
  * accepted by elm_batch_create. */
 enum { ELM_P1 = 0x400 };
 
+/* Flag OR-ed into `precision` of elm_mesh_create: also build the diffusion
+ * solver of elm_diffusion_step (per macro the element mass matrix and one
+ * stiffness matrix per micro-simplex orientation, the boundary mask, and 7
+ * solver vectors of elm_mesh_num_unique values in the mesh precision). */
+enum { ELM_DIFFUSION = 0x800 };
+
 /* Builds the refined mesh (Sec. 2.1: coarse mesh T_0 refined uniformly after
  * Bey; Sec. 2.3.1, grid data structure: one DoF owner per interface node).
  *  dim            2 (triangles) or 3 (tetrahedra).
@@ -86,7 +95,7 @@ enum { ELM_P1 = 0x400 };
  *                 id, which makes the refinement conforming across faces.
  *  level          P2: 0..9 in 2D, 0..7 in 3D; P1: 0..10 in 2D, 0..8 in 3D.
  *  precision      ELM_FP64 or ELM_FP32, optionally | ELM_HOST_ONLY,
- *                 | ELM_ADJOINT, | ELM_P1.
+ *                 | ELM_ADJOINT, | ELM_P1, | ELM_DIFFUSION.
  * Copies everything it needs; allocates the mesh's device tables on the
  * current device.  Returns ELM_ERR_TOPOLOGY for a degenerate macro or a
  * non-manifold face.  *out is set only on success. */
@@ -219,6 +228,32 @@ elm_status elm_trace(elm_mesh mesh, const void* D_in_dev, void* D_out_dev, doubl
  * overlap), storage layout, mesh precision.  Needs no velocity.  One kernel
  * launch on `stream`; allocates nothing. */
 elm_status elm_trace_eval(elm_mesh mesh, const void* D_dev, const void* T_src_dev, void* T_dst_dev, void* stream);
+
+/* ---- Diffusion step (Sec. 2.2, Eq. finite-dimensional Galerkin approximation
+ * and Eq. linear system; Algorithm 1 line 5 and the fractional steps of the
+ * Strang splitting, Algorithm 3) ----
+ * Solves, for the P1 / P2 mass matrix M and stiffness matrix A of the mesh,
+ *   (M + tau theta kappa A) c_new = (M - tau (1 - theta) kappa A) c_hat + tau M q
+ * with c_new = c_bnd on the boundary of the macro mesh (Dirichlet), by
+ * Jacobi-preconditioned conjugate gradients on the interior unknowns, to
+ * |r| <= rtol |b| (b the interior right-hand side).  theta = 1: implicit
+ * Euler; theta = 1/2: Crank-Nicolson.
+ *  c_hat_dev  [n] storage layout, mesh precision: the advected field.
+ *  c_bnd_dev  [n] boundary values (NULL: c_hat's values there).
+ *  q_dev      [n] nodal source values q (NULL: q = 0); the caller combines
+ *             theta q^{n+1} + (1 - theta) q^n.
+ *  c_new_dev  [n] result; must not overlap an input.  Every storage copy of a
+ *             node receives the node's value.
+ *  iterations, residual  optional host outputs: CG iterations and the final
+ *             relative residual.
+ * The operator is matrix-free; its element sums use atomics, so the last bits
+ * can differ between runs.  Requires ELM_DIFFUSION at creation.  Unlike the
+ * other calls this one synchronises `stream` (the convergence test reads the
+ * residual every iteration).  Returns ELM_ERR_NOT_CONVERGED (with c_new the
+ * last iterate) when max_iter iterations do not reach rtol. */
+elm_status elm_diffusion_step(elm_mesh mesh, const void* c_hat_dev, const void* c_bnd_dev, const void* q_dev,
+                              void* c_new_dev, double tau, double kappa, double theta, double rtol, int max_iter,
+                              int* iterations, double* residual, void* stream);
 
 /* Synchronises `stream`, returns the first device-side condition raised by
  * work on this mesh since the previous call (ELM_ERR_WALK_LIMIT or

@@ -8,10 +8,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libelm.so")
 
 ELM_OK, ELM_ERR_ARG, ELM_ERR_CUDA, ELM_ERR_TOPOLOGY = 0, 1, 2, 3
-ELM_ERR_WALK_LIMIT, ELM_ERR_NONFINITE, ELM_ERR_STATE = 4, 5, 6
+ELM_ERR_WALK_LIMIT, ELM_ERR_NONFINITE, ELM_ERR_STATE, ELM_ERR_NOT_CONVERGED = 4, 5, 6, 7
 ELM_FP64, ELM_FP32 = 0, 1
 STATUS_NAMES = {0: "ELM_OK", 1: "ELM_ERR_ARG", 2: "ELM_ERR_CUDA", 3: "ELM_ERR_TOPOLOGY",
-                4: "ELM_ERR_WALK_LIMIT", 5: "ELM_ERR_NONFINITE", 6: "ELM_ERR_STATE"}
+                4: "ELM_ERR_WALK_LIMIT", 5: "ELM_ERR_NONFINITE", 6: "ELM_ERR_STATE", 7: "ELM_ERR_NOT_CONVERGED"}
 
 # (name, restype, argtypes) of every entry point declared in include/elm.h
 _P, _I64, _I, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
@@ -30,6 +30,8 @@ SIGNATURES = [
     ("elm_advect_adjoint", _I, [_P, _P, _P, _P, _P, _P, _D, _I, _P]),
     ("elm_trace", _I, [_P, _P, _P, _D, _I, _P]),
     ("elm_trace_eval", _I, [_P, _P, _P, _P, _P]),
+    ("elm_diffusion_step", _I, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _I, ctypes.POINTER(_I),
+                                ctypes.POINTER(_D), _P]),
     ("elm_get_status", _I, [_P, _P]),
     ("elm_batch_create", _I, [_P, _I, _I, ctypes.POINTER(_P)]),
     ("elm_batch_destroy", _I, [_P]),
@@ -69,3 +71,4 @@ def check(status: int) -> None:
 ELM_HOST_ONLY = 0x100
 ELM_ADJOINT = 0x200
 ELM_P1 = 0x400
+ELM_DIFFUSION = 0x800

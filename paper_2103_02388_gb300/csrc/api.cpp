@@ -47,6 +47,16 @@ void free_tables(elm_mesh_s* me) {
   cudaFree(me->d_acc_U);
   cudaFree(me->d_maxbits);
   me->d_acc_T = me->d_acc_U = me->d_maxbits = nullptr;
+  cudaFree(me->d_dtab);
+  cudaFree(me->d_dbnd);
+  cudaFree(me->d_dcells);
+  cudaFree(me->d_dvec);
+  cudaFree(me->d_dpart);
+  cudaFree(me->d_dscal);
+  me->d_dtab = me->d_dvec = nullptr;
+  me->d_dbnd = nullptr;
+  me->d_dcells = nullptr;
+  me->d_dpart = me->d_dscal = nullptr;
   me->d_geo = nullptr;
   me->d_geo32 = nullptr;
   me->d_unique_map = me->d_owner = me->d_owner_mp = nullptr;
@@ -117,7 +127,8 @@ elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz
   const bool host_only = (precision & ELM_HOST_ONLY) != 0;
   const bool with_adjoint = (precision & ELM_ADJOINT) != 0;
   const int order = (precision & ELM_P1) != 0 ? 1 : 2;
-  precision &= ~(ELM_HOST_ONLY | ELM_ADJOINT | ELM_P1);
+  const bool with_diffusion = (precision & ELM_DIFFUSION) != 0;
+  precision &= ~(ELM_HOST_ONLY | ELM_ADJOINT | ELM_P1 | ELM_DIFFUSION);
   if (precision != ELM_FP64 && precision != ELM_FP32)
     return fail(ELM_ERR_ARG, "elm_mesh_create: precision must be ELM_FP64 or ELM_FP32");
   if (order == 1 && with_adjoint)
@@ -140,6 +151,7 @@ elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz
   me->host_only = host_only;
   me->with_adjoint = with_adjoint;
   me->order = order;
+  me->with_diffusion = with_diffusion;
   if (!host_only) {
     cudaError_t e = cudaGetDevice(&me->device);
     if (e != cudaSuccess) {

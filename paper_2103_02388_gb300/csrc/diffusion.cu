@@ -1,0 +1,731 @@
+// diffusion.cu -- the diffusion step of the advection-diffusion scheme
+// (arXiv 2103.02388, Sec. 2.2, Eq. finite-dimensional Galerkin approximation
+// and Eq. linear system; Algorithm 1 line 5, and the two fractional steps of
+// the Strang splitting, Algorithm 3):
+//
+//   (M + tau theta kappa A) c^{n+1} = (M - tau (1 - theta) kappa A) c_hat
+//                                     + tau M q,        c = c_bnd on the boundary,
+//
+// with the P1 / P2 mass matrix M and stiffness matrix A of the refined mesh,
+// solved by Jacobi-preconditioned conjugate gradients (the system matrix is
+// symmetric positive definite, Sec. 2.2).
+//
+// Matrix-free operator.  Every macro is an affine image of the reference
+// Kuhn simplex, and its micro simplices are the Kuhn simplices (one per axis
+// permutation sigma) of the lattice cells, so all micro simplices of a macro
+// with the same sigma are translates of one another: their element
+// matrices are equal.  The host computes, per macro, the mass matrix (the
+// same for every sigma, since all micro simplices have the same volume) and
+// one stiffness matrix per sigma; a thread per lattice cell applies the
+// element matrices of the cell's simplices that lie in the macro and adds the
+// results to the unique nodes with atomics.  The solver's vectors are in the
+// unique-node layout, so interface nodes shared by several macros are single
+// unknowns.  The FP atomics make the summation order, and so the last bits,
+// vary between runs; the solve converges to the same tolerance.
+//
+// Dirichlet conditions: boundary unknowns keep c_bnd; CG runs on the
+// interior unknowns (search directions are zero on the boundary).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "elm_internal.h"
+
+namespace elm {
+namespace {
+
+constexpr int kDiffThreads = 128;
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 608;  // 4 per SM of the 152-SM part: the partials of one reduction
+
+__host__ __device__ constexpr int n_local(int d, int p) { return p == 2 ? (d + 1) * (d + 2) / 2 : d + 1; }
+__host__ __device__ constexpr int n_perm(int d) { return d == 3 ? 6 : 2; }
+
+// The axis permutations of a cell in lexicographic order (3D: 012, 021, 102,
+// 120, 201, 210; 2D: 01, 10).
+__host__ __device__ inline void perm_of(int d, int k, int* s) {
+  if (d == 2) {
+    s[0] = k;
+    s[1] = 1 - k;
+    return;
+  }
+  const int t[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  s[0] = t[k][0];
+  s[1] = t[k][1];
+  s[2] = t[k][2];
+}
+
+// ---------------------------------------------------------------------------
+// Host: element matrices.
+// ---------------------------------------------------------------------------
+
+// A polynomial term c * prod lam_k^e_k of the barycentric coordinates.
+struct Term {
+  double c;
+  int e[4];
+};
+
+double fact(int n) { return n <= 1 ? 1.0 : n * fact(n - 1); }
+
+// int over a simplex of unit volume of prod lam_k^e_k: d! e_0! .. e_d! / (d + |e|)!.
+double monomial_unit(int d, const int* e) {
+  double num = fact(d);
+  int tot = 0;
+  for (int k = 0; k <= d; ++k) {
+    num *= fact(e[k]);
+    tot += e[k];
+  }
+  return num / fact(d + tot);
+}
+
+// Local basis in the order vertices 0..d, then edges (a, b), a < b,
+// lexicographic (P2); vertices only (P1).
+std::vector<std::vector<Term>> basis_terms(int d, int p) {
+  std::vector<std::vector<Term>> B;
+  for (int v = 0; v <= d; ++v) {
+    std::vector<Term> t;
+    Term sq{2.0, {0, 0, 0, 0}}, li{-1.0, {0, 0, 0, 0}}, one{1.0, {0, 0, 0, 0}};
+    sq.e[v] = 2;
+    li.e[v] = 1;
+    one.e[v] = 1;
+    if (p == 2) {
+      t.push_back(sq);
+      t.push_back(li);
+    } else {
+      t.push_back(one);
+    }
+    B.push_back(t);
+  }
+  if (p == 2)
+    for (int a = 0; a <= d; ++a)
+      for (int b = a + 1; b <= d; ++b) {
+        Term t{4.0, {0, 0, 0, 0}};
+        t.e[a] = 1;
+        t.e[b] = 1;
+        B.push_back({t});
+      }
+  return B;
+}
+
+// d phi_i / d lam_k = a[i][k] + sum_m b[i][k][m] lam_m (linear for P1 and P2).
+void basis_derivatives(int d, int p, std::vector<double>& a, std::vector<double>& b) {
+  const int nb = n_local(d, p), D1 = d + 1;
+  a.assign(nb * D1, 0.0);
+  b.assign(nb * D1 * D1, 0.0);
+  for (int v = 0; v <= d; ++v) {
+    if (p == 2) {  // 2 lam_v^2 - lam_v
+      a[v * D1 + v] = -1.0;
+      b[(v * D1 + v) * D1 + v] = 4.0;
+    } else {  // lam_v
+      a[v * D1 + v] = 1.0;
+    }
+  }
+  if (p == 2) {
+    int i = d + 1;
+    for (int s = 0; s <= d; ++s)
+      for (int t = s + 1; t <= d; ++t, ++i) {  // 4 lam_s lam_t
+        b[(i * D1 + s) * D1 + t] = 4.0;
+        b[(i * D1 + t) * D1 + s] = 4.0;
+      }
+  }
+}
+
+// Element tables of one macro: mass (nb x nb) and one stiffness matrix per
+// permutation ([n_perm, nb, nb]), FP64.
+void element_tables(int d, int p, int N, const MacroGeo& g, double* Mout, double* Aout) {
+  const int nb = n_local(d, p), D1 = d + 1;
+  // reference mass on unit volume
+  const auto B = basis_terms(d, p);
+  std::vector<double> Mref(nb * nb);
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) {
+      double s = 0.0;
+      for (const Term& ti : B[i])
+        for (const Term& tj : B[j]) {
+          int e[4];
+          for (int k = 0; k < 4; ++k) e[k] = ti.e[k] + tj.e[k];
+          s += ti.c * tj.c * monomial_unit(d, e);
+        }
+      Mref[i * nb + j] = s;
+    }
+  std::vector<double> da, db;
+  basis_derivatives(d, p, da, db);
+  // K[i][j][k][l] = int_unit (dphi_i/dlam_k)(dphi_j/dlam_l), with
+  // int lam_m = 1/(d+1), int lam_m lam_n = (1 + delta_mn)/((d+1)(d+2)).
+  std::vector<double> K(nb * nb * D1 * D1);
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j)
+      for (int k = 0; k < D1; ++k)
+        for (int l = 0; l < D1; ++l) {
+          const double ai = da[i * D1 + k], aj = da[j * D1 + l];
+          double sbi = 0.0, sbj = 0.0, bb = 0.0;
+          for (int m = 0; m < D1; ++m) {
+            sbi += db[(i * D1 + k) * D1 + m];
+            sbj += db[(j * D1 + l) * D1 + m];
+            for (int n = 0; n < D1; ++n)
+              bb += db[(i * D1 + k) * D1 + m] * db[(j * D1 + l) * D1 + n] * (m == n ? 2.0 : 1.0);
+          }
+          K[((i * nb + j) * D1 + k) * D1 + l] =
+              ai * aj + (ai * sbj + aj * sbi) / double(D1) + bb / double(D1 * (D1 + 1));
+        }
+  for (int sg = 0; sg < n_perm(d); ++sg) {
+    int s[3];
+    perm_of(d, sg, s);
+    // vertices of the cell-0 Kuhn simplex: w_0 = 0, w_k = w_{k-1} + e_{s_{k-1}}
+    double V[4][3] = {};
+    int w[3] = {0, 0, 0};
+    for (int k = 0; k <= d; ++k) {
+      if (k > 0) w[s[k - 1]] += 1;
+      for (int r = 0; r < d; ++r) {
+        double x = g.v0[r];
+        for (int c = 0; c < d; ++c) x += g.J[r * 3 + c] * (double(w[c]) / double(N));
+        V[k][r] = x;
+      }
+    }
+    // barycentric gradients: rows of E^{-1}, E = [V1 - V0 | ... ]
+    double E[9], Ei[9];
+    for (int r = 0; r < d; ++r)
+      for (int c = 0; c < d; ++c) E[r * d + c] = V[c + 1][r] - V[0][r];
+    double det;
+    if (d == 2) {
+      det = E[0] * E[3] - E[1] * E[2];
+      Ei[0] = E[3] / det;
+      Ei[1] = -E[1] / det;
+      Ei[2] = -E[2] / det;
+      Ei[3] = E[0] / det;
+    } else {
+      const double c00 = E[4] * E[8] - E[5] * E[7], c01 = E[5] * E[6] - E[3] * E[8], c02 = E[3] * E[7] - E[4] * E[6];
+      det = E[0] * c00 + E[1] * c01 + E[2] * c02;
+      Ei[0] = c00 / det;
+      Ei[1] = (E[2] * E[7] - E[1] * E[8]) / det;
+      Ei[2] = (E[1] * E[5] - E[2] * E[4]) / det;
+      Ei[3] = c01 / det;
+      Ei[4] = (E[0] * E[8] - E[2] * E[6]) / det;
+      Ei[5] = (E[2] * E[3] - E[0] * E[5]) / det;
+      Ei[6] = c02 / det;
+      Ei[7] = (E[1] * E[6] - E[0] * E[7]) / det;
+      Ei[8] = (E[0] * E[4] - E[1] * E[3]) / det;
+    }
+    const double vol = std::fabs(det) / (d == 2 ? 2.0 : 6.0);
+    double G[4][3] = {};
+    for (int k = 1; k <= d; ++k)
+      for (int r = 0; r < d; ++r) {
+        G[k][r] = Ei[(k - 1) * d + r];
+        G[0][r] -= G[k][r];
+      }
+    if (sg == 0)
+      for (int i = 0; i < nb * nb; ++i) Mout[i] = vol * Mref[i];
+    double* A = Aout + size_t(sg) * nb * nb;
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        double a = 0.0;
+        for (int k = 0; k < D1; ++k)
+          for (int l = 0; l < D1; ++l) {
+            double gg = 0.0;
+            for (int r = 0; r < d; ++r) gg += G[k][r] * G[l][r];
+            a += gg * K[((i * nb + j) * D1 + k) * D1 + l];
+          }
+        A[i * nb + j] = vol * a;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Device: the operator y += scale (M + alpha A) x over all micro simplices.
+// ---------------------------------------------------------------------------
+
+struct OpArgs {
+  const void* tables;       // per macro: M [nb*nb], then A [n_perm][nb*nb], mesh precision
+  const int4* cells;        // work list: (macro, c0, first index in slab c0, count)
+  const int64_t* unique_map;
+  int npm;                  // storage nodes per macro
+};
+
+__device__ __forceinline__ int tri2d(int k) { return k * (k + 1) / 2; }
+__device__ __forceinline__ int tri3d(int k) { return k * (k + 1) * (k + 2) / 6; }
+
+// Row r of the slab-c0 index i (3D: i = r(r+1)/2 + c2, c2 <= r).
+__device__ __forceinline__ int row_of(int i) {
+  int r = int((sqrtf(8.0f * float(i) + 1.0f) - 1.0f) * 0.5f);
+  while (r > 0 && tri2d(r) > i) --r;
+  while (tri2d(r + 1) <= i) ++r;
+  return r;
+}
+
+// DIAG: add only the diagonal of scale (M + alpha A) (x unused).
+template <int D, class R, int P, bool DIAG>
+__global__ void __launch_bounds__(kDiffThreads) k_apply(OpArgs a, const R* __restrict__ x, R* __restrict__ y,
+                                                        R alpha, R scale) {
+  constexpr int NB = n_local(D, P);
+  constexpr int NP = n_perm(D);
+  constexpr int TAB = NB * NB * (1 + NP);
+  __shared__ R E[NP][NB * NB];  // M + alpha A_sigma of the block's macro
+  const int4 ck = a.cells[blockIdx.x];
+  const R* tab = static_cast<const R*>(a.tables) + size_t(ck.x) * TAB;
+  for (int t = threadIdx.x; t < NP * NB * NB; t += blockDim.x) {
+    const int sg = t / (NB * NB), e = t - sg * NB * NB;
+    E[sg][e] = scale * (tab[e] + alpha * tab[NB * NB * (1 + sg) + e]);
+  }
+  __syncthreads();
+  if (int(threadIdx.x) >= ck.w) return;
+  // the cell c of this thread (c0 = slab, then row and position)
+  int c[3];
+  const int i = ck.z + int(threadIdx.x);
+  c[0] = ck.y;
+  if (D == 3) {
+    c[1] = row_of(i);
+    c[2] = i - tri2d(c[1]);
+  } else {
+    c[1] = i;
+  }
+  const int64_t base = int64_t(ck.x) * a.npm;
+  const int M = P * 1;  // node lattice points per cell edge
+#pragma unroll 1
+  for (int sg = 0; sg < NP; ++sg) {
+    int s[3];
+    perm_of(D, sg, s);
+    // the simplex lies in the macro's reference simplex iff axes with equal
+    // cell coordinates keep their order (a before b for a < b)
+    bool inside = true;
+#pragma unroll
+    for (int u = 0; u < D; ++u)
+#pragma unroll
+      for (int v = u + 1; v < D; ++v)
+        if (c[s[u]] == c[s[v]] && s[u] > s[v]) inside = false;
+    if (!inside) continue;
+    // lattice points of the vertices (node lattice: P c + P w_k)
+    int W[4][3];
+#pragma unroll
+    for (int r = 0; r < D; ++r) W[0][r] = M * c[r];
+#pragma unroll
+    for (int k = 1; k <= D; ++k) {
+#pragma unroll
+      for (int r = 0; r < D; ++r) W[k][r] = W[k - 1][r];
+      W[k][s[k - 1]] += M;
+    }
+    int64_t uid[NB];
+    R xl[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      int q[3];
+      if (j <= D) {
+#pragma unroll
+        for (int r = 0; r < D; ++r) q[r] = W[j][r];
+      } else {  // edge (u, v), u < v lexicographic: midpoint
+        int u = 0, v = 1, n = D + 1;
+#pragma unroll
+        for (int uu = 0; uu <= D; ++uu)
+#pragma unroll
+          for (int vv = uu + 1; vv <= D; ++vv, ++n)
+            if (n == j) { u = uu; v = vv; }
+#pragma unroll
+        for (int r = 0; r < D; ++r) q[r] = (W[u][r] + W[v][r]) / 2;
+      }
+      const int64_t slot = base + (D == 3 ? tri3d(q[0]) + tri2d(q[1]) + q[2] : tri2d(q[0]) + q[1]);
+      uid[j] = a.unique_map[slot];
+      xl[j] = DIAG ? R(0) : x[uid[j]];
+    }
+#pragma unroll
+    for (int ii = 0; ii < NB; ++ii) {
+      R v = R(0);
+      if (DIAG) {
+        v = E[sg][ii * NB + ii];
+      } else {
+#pragma unroll
+        for (int j = 0; j < NB; ++j) v += E[sg][ii * NB + j] * xl[j];
+      }
+      atomicAdd(y + uid[ii], v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Device: CG vector kernels and deterministic reductions (per-block partials
+// in a fixed order, then one block sums the partials in a fixed order).
+// ---------------------------------------------------------------------------
+
+struct Scalars {
+  double rz, rz_new, pq, rr, bb, alpha, beta, pad;
+};
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (int(threadIdx.x) < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// r := r with zero boundary; z = dinv r; p = z; partials (r.z, r.r).
+template <class R>
+__global__ void __launch_bounds__(kRedThreads) k_cg_start(R* r, R* z, R* p, const R* dinv, const uint8_t* bnd,
+                                                          int64_t n, double* part) {
+  __shared__ double sh[kRedThreads];
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    R ri = bnd[i] ? R(0) : r[i];
+    r[i] = ri;
+    const R zi = dinv[i] * ri;
+    z[i] = zi;
+    p[i] = zi;
+    rz += double(ri) * double(zi);
+    rr += double(ri) * double(ri);
+  }
+  const double s1 = block_sum(rz, sh);
+  __syncthreads();
+  const double s2 = block_sum(rr, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s1;
+    part[gridDim.x + blockIdx.x] = s2;
+  }
+}
+
+// partial of p.q (q zero on the boundary, p zero there already)
+template <class R>
+__global__ void __launch_bounds__(kRedThreads) k_cg_pq(const R* p, R* q, const uint8_t* bnd, int64_t n,
+                                                       double* part) {
+  __shared__ double sh[kRedThreads];
+  double pq = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    R qi = q[i];
+    if (bnd[i]) {
+      qi = R(0);
+      q[i] = qi;
+    }
+    pq += double(p[i]) * double(qi);
+  }
+  const double s = block_sum(pq, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// x += alpha p; r -= alpha q; z = dinv r; partials (r.z, r.r).
+template <class R>
+__global__ void __launch_bounds__(kRedThreads) k_cg_update(R* x, R* r, R* z, const R* p, const R* q, const R* dinv,
+                                                           const Scalars* sc, int64_t n, double* part) {
+  __shared__ double sh[kRedThreads];
+  const R al = R(sc->alpha);
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    x[i] += al * p[i];
+    const R ri = r[i] - al * q[i];
+    r[i] = ri;
+    const R zi = dinv[i] * ri;
+    z[i] = zi;
+    rz += double(ri) * double(zi);
+    rr += double(ri) * double(ri);
+  }
+  const double s1 = block_sum(rz, sh);
+  __syncthreads();
+  const double s2 = block_sum(rr, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s1;
+    part[gridDim.x + blockIdx.x] = s2;
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kRedThreads) k_cg_direction(R* p, const R* z, const Scalars* sc, int64_t n) {
+  const R be = R(sc->beta);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    p[i] = z[i] + be * p[i];
+}
+
+// Sums the partials of a reduction and updates the CG scalars:
+// what = 0: start (rz, rr); 1: p.q -> alpha; 2: update (rz_new, rr) -> beta.
+__global__ void __launch_bounds__(kRedThreads) k_cg_scalars(const double* part, int nparts, int what, Scalars* sc) {
+  __shared__ double sh[kRedThreads];
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    s1 += part[i];
+    if (what != 1) s2 += part[nparts + i];
+  }
+  const double a = block_sum(s1, sh);
+  __syncthreads();
+  const double b = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    if (what == 0) {
+      sc->rz = a;
+      sc->rr = b;
+    } else if (what == 1) {
+      sc->pq = a;
+      sc->alpha = a != 0.0 ? sc->rz / a : 0.0;
+    } else {
+      sc->rz_new = a;
+      sc->rr = b;
+      sc->beta = sc->rz != 0.0 ? a / sc->rz : 0.0;
+      sc->rz = a;
+    }
+  }
+}
+
+// |b|^2 over the interior unknowns (the residual reference).
+template <class R>
+__global__ void __launch_bounds__(kRedThreads) k_norm2(const R* b, const uint8_t* bnd, int64_t n, double* part) {
+  __shared__ double sh[kRedThreads];
+  double s = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    if (!bnd[i]) s += double(b[i]) * double(b[i]);
+  const double t = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_sum_into(const double* part, int nparts, double* out) {
+  __shared__ double sh[kRedThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+  const double t = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = t;
+}
+
+// dinv = 1 / diag (interior), 0 on the boundary.
+template <class R>
+__global__ void k_invert_diag(R* d, const uint8_t* bnd, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = (bnd[i] || d[i] == R(0)) ? R(0) : R(1) / d[i];
+}
+
+// x = where(bnd, v, x)
+template <class R>
+__global__ void k_set_boundary(R* x, const R* v, const uint8_t* bnd, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n && bnd[i]) x[i] = v[i];
+}
+
+template <class R>
+__global__ void k_copy(R* dst, const R* src, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host: set-up at mesh creation and the solve.
+// ---------------------------------------------------------------------------
+
+elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
+  const int d = me->dim, p = me->order, nb = n_local(d, p), np = n_perm(d);
+  const size_t tab = size_t(nb) * nb * (1 + np);
+  std::vector<double> t64(tab * me->n_macros);
+  for (int64_t m = 0; m < me->n_macros; ++m)
+    element_tables(d, p, me->N, me->geo[m], t64.data() + m * tab, t64.data() + m * tab + size_t(nb) * nb);
+  // boundary unknowns: a node on face k (barycentric weight k = 0) of a macro
+  // whose face k has no neighbour
+  std::vector<uint8_t> bnd(me->n_unique, 0);
+  {
+    const int M = me->M;
+    for (int64_t m = 0; m < me->n_macros; ++m) {
+      const MacroGeo& g = me->geo[m];
+      int64_t slot = m * me->npm;
+      int q[3] = {0, 0, 0};
+      auto visit = [&]() {
+        const int pp[5] = {M, q[0], q[1], d == 3 ? q[2] : 0, 0};
+        bool on = false;
+        for (int k = 0; k <= d; ++k) {
+          const int w = (d == 3 || k < d) ? pp[k] - pp[k + 1] : pp[k];
+          if (w == 0 && g.nb[k] < 0) on = true;
+        }
+        if (on) bnd[me->unique_map[slot]] = 1;
+        ++slot;
+      };
+      if (d == 2) {
+        for (q[0] = 0; q[0] <= M; ++q[0])
+          for (q[1] = 0; q[1] <= q[0]; ++q[1]) visit();
+      } else {
+        for (q[0] = 0; q[0] <= M; ++q[0])
+          for (q[1] = 0; q[1] <= q[0]; ++q[1])
+            for (q[2] = 0; q[2] <= q[1]; ++q[2]) visit();
+      }
+    }
+  }
+  // cell work list: slab c0 holds (c0+1)(c0+2)/2 cells in 3D, c0+1 in 2D
+  std::vector<int4> cells;
+  for (int64_t m = 0; m < me->n_macros; ++m)
+    for (int c0 = 0; c0 < me->N; ++c0) {
+      const int len = d == 3 ? (c0 + 1) * (c0 + 2) / 2 : c0 + 1;
+      for (int i0 = 0; i0 < len; i0 += kDiffThreads)
+        cells.push_back(make_int4(int(m), c0, i0, std::min(kDiffThreads, len - i0)));
+    }
+  me->n_cell_chunks = int64_t(cells.size());
+  const size_t es = me->precision == ELM_FP64 ? 8 : 4;
+  bool ok = true;
+  ok = ok && cudaMalloc(&me->d_dtab, tab * me->n_macros * es) == cudaSuccess;
+  if (ok) {
+    if (me->precision == ELM_FP64) {
+      ok = cudaMemcpy(me->d_dtab, t64.data(), tab * me->n_macros * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    } else {
+      std::vector<float> t32(t64.begin(), t64.end());
+      ok = cudaMemcpy(me->d_dtab, t32.data(), tab * me->n_macros * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+  }
+  ok = ok && cudaMalloc((void**)&me->d_dbnd, me->n_unique) == cudaSuccess &&
+       cudaMemcpy(me->d_dbnd, bnd.data(), me->n_unique, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&me->d_dcells, sizeof(int4) * cells.size()) == cudaSuccess &&
+       cudaMemcpy(me->d_dcells, cells.data(), sizeof(int4) * cells.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMalloc(&me->d_dvec, size_t(kDiffVectors) * me->n_unique * es) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&me->d_dpart, sizeof(double) * 2 * kRedBlocks) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&me->d_dscal, sizeof(Scalars) + sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    *err = std::string("diffusion tables: ") + cudaGetErrorString(cudaGetLastError());
+    return ELM_ERR_CUDA;
+  }
+  me->n_boundary = 0;
+  for (uint8_t b : bnd) me->n_boundary += b;
+  return ELM_OK;
+}
+
+namespace {
+
+template <class R>
+cudaError_t apply_op(const elm_mesh_s* me, const R* x, R* y, double alpha, double scale, bool diag, cudaStream_t s) {
+  OpArgs a{me->d_dtab, me->d_dcells, me->d_unique_map, int(me->npm)};
+  const unsigned g = unsigned(me->n_cell_chunks);
+  if (g == 0) return cudaSuccess;
+  const R al = R(alpha), sc = R(scale);
+#define ELM_APPLY(DD, PP)                                                              \
+  if (diag) k_apply<DD, R, PP, true><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);     \
+  else k_apply<DD, R, PP, false><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);
+  if (me->dim == 3) {
+    if (me->order == 2) { ELM_APPLY(3, 2) } else { ELM_APPLY(3, 1) }
+  } else {
+    if (me->order == 2) { ELM_APPLY(2, 2) } else { ELM_APPLY(2, 1) }
+  }
+#undef ELM_APPLY
+  return cudaGetLastError();
+}
+
+template <class R>
+elm_status solve(elm_mesh_s* me, const void* c_hat, const void* c_bnd, const void* q, void* c_new, double tau,
+                 double kappa, double theta, double rtol, int max_iter, int* iters, double* resid, cudaStream_t s,
+                 std::string* err) {
+  const int64_t n = me->n_unique;
+  R* v = static_cast<R*>(me->d_dvec);
+  R* x = v;
+  R* r = v + n;
+  R* z = v + 2 * n;
+  R* p = v + 3 * n;
+  R* qv = v + 4 * n;
+  R* b = v + 5 * n;
+  R* dinv = v + 6 * n;
+  double* part = me->d_dpart;
+  Scalars* sc = reinterpret_cast<Scalars*>(me->d_dscal);
+  double* bnorm = me->d_dscal + sizeof(Scalars) / sizeof(double);
+  const size_t bytes = size_t(n) * sizeof(R);
+  const unsigned eb = unsigned((n + 255) / 256);
+  const int nred = kRedBlocks;
+  const int prec = me->precision;
+  auto chk = [&](cudaError_t e, const char* where) {
+    if (e != cudaSuccess) *err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaSuccess;
+  };
+  // c_hat (storage) -> x (unique); right-hand side b
+  if (!chk(launch_gather(prec, c_hat, x, me->d_owner, n, 1, s), "gather c_hat")) return ELM_ERR_CUDA;
+  if (!chk(cudaMemsetAsync(b, 0, bytes, s), "memset")) return ELM_ERR_CUDA;
+  if (!chk(apply_op<R>(me, x, b, -tau * (1.0 - theta) * kappa, 1.0, false, s), "rhs")) return ELM_ERR_CUDA;
+  if (q) {
+    if (!chk(launch_gather(prec, q, z, me->d_owner, n, 1, s), "gather q")) return ELM_ERR_CUDA;
+    if (!chk(apply_op<R>(me, z, b, 0.0, tau, false, s), "source")) return ELM_ERR_CUDA;
+  }
+  if (c_bnd) {
+    if (!chk(launch_gather(prec, c_bnd, z, me->d_owner, n, 1, s), "gather c_bnd")) return ELM_ERR_CUDA;
+    k_set_boundary<R><<<eb, 256, 0, s>>>(x, z, me->d_dbnd, n);
+  }
+  // Jacobi preconditioner of E = M + tau theta kappa A
+  const double alpha = tau * theta * kappa;
+  if (!chk(cudaMemsetAsync(dinv, 0, bytes, s), "memset")) return ELM_ERR_CUDA;
+  if (!chk(apply_op<R>(me, x, dinv, alpha, 1.0, true, s), "diagonal")) return ELM_ERR_CUDA;
+  k_invert_diag<R><<<eb, 256, 0, s>>>(dinv, me->d_dbnd, n);
+  k_norm2<R><<<nred, kRedThreads, 0, s>>>(b, me->d_dbnd, n, part);
+  k_sum_into<<<1, kRedThreads, 0, s>>>(part, nred, bnorm);
+  // r = b - E x, restricted to the interior; z = D^{-1} r; p = z
+  k_copy<R><<<eb, 256, 0, s>>>(r, b, n);
+  if (!chk(apply_op<R>(me, x, r, alpha, -1.0, false, s), "residual")) return ELM_ERR_CUDA;
+  k_cg_start<R><<<nred, kRedThreads, 0, s>>>(r, z, p, dinv, me->d_dbnd, n, part);
+  k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 0, sc);
+  double host[2] = {0.0, 0.0};
+  auto read_norms = [&]() -> bool {
+    Scalars h;
+    if (!chk(cudaMemcpyAsync(&h, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s), "read") ||
+        !chk(cudaMemcpyAsync(&host[1], bnorm, sizeof(double), cudaMemcpyDeviceToHost, s), "read") ||
+        !chk(cudaStreamSynchronize(s), "sync"))
+      return false;
+    host[0] = h.rr;
+    return true;
+  };
+  if (!read_norms()) return ELM_ERR_CUDA;
+  const double bn = std::sqrt(host[1]);
+  double rel = bn > 0.0 ? std::sqrt(host[0]) / bn : std::sqrt(host[0]);
+  int it = 0;
+  const bool interior = me->n_unique > me->n_boundary;
+  while (interior && rel > rtol && it < max_iter) {
+    if (!chk(cudaMemsetAsync(qv, 0, bytes, s), "memset")) return ELM_ERR_CUDA;
+    if (!chk(apply_op<R>(me, p, qv, alpha, 1.0, false, s), "apply")) return ELM_ERR_CUDA;
+    k_cg_pq<R><<<nred, kRedThreads, 0, s>>>(p, qv, me->d_dbnd, n, part);
+    k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 1, sc);
+    k_cg_update<R><<<nred, kRedThreads, 0, s>>>(x, r, z, p, qv, dinv, sc, n, part);
+    k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 2, sc);
+    k_cg_direction<R><<<nred, kRedThreads, 0, s>>>(p, z, sc, n);
+    ++it;
+    if (!read_norms()) return ELM_ERR_CUDA;
+    rel = bn > 0.0 ? std::sqrt(host[0]) / bn : std::sqrt(host[0]);
+    if (!std::isfinite(rel)) break;
+  }
+  if (iters) *iters = it;
+  if (resid) *resid = rel;
+  if (!chk(launch_gather(prec, x, c_new, me->d_unique_map, me->n_storage, 1, s), "scatter")) return ELM_ERR_CUDA;
+  if (!std::isfinite(rel)) {
+    *err = "non-finite residual";
+    return ELM_ERR_NONFINITE;
+  }
+  if (rel > rtol && interior) {
+    *err = "CG did not reach the tolerance within max_iter iterations (relative residual " + std::to_string(rel) + ")";
+    return ELM_ERR_NOT_CONVERGED;
+  }
+  return ELM_OK;
+}
+
+}  // namespace
+}  // namespace elm
+
+extern "C" elm_status elm_diffusion_step(elm_mesh me, const void* c_hat_dev, const void* c_bnd_dev,
+                                         const void* q_dev, void* c_new_dev, double tau, double kappa, double theta,
+                                         double rtol, int max_iter, int* iterations, double* residual,
+                                         void* stream) {
+  auto fail = [](elm_status st, const std::string& m) {
+    elm::set_last_error("elm_diffusion_step: " + m);
+    return st;
+  };
+  if (!me) return fail(ELM_ERR_ARG, "null mesh");
+  if (!c_hat_dev || !c_new_dev) return fail(ELM_ERR_ARG, "null buffer");
+  if (!std::isfinite(tau) || tau < 0.0 || !std::isfinite(kappa) || kappa < 0.0 || !std::isfinite(theta) ||
+      theta < 0.0 || theta > 1.0)
+    return fail(ELM_ERR_ARG, "tau, kappa >= 0 finite and theta in [0, 1] required");
+  if (!(rtol > 0.0) || max_iter < 0) return fail(ELM_ERR_ARG, "rtol > 0 and max_iter >= 0 required");
+  if (me->host_only || !me->with_diffusion)
+    return fail(ELM_ERR_STATE, "mesh was created without ELM_DIFFUSION");
+  const size_t es = me->precision == ELM_FP64 ? 8 : 4;
+  const size_t bytes = es * size_t(me->n_storage);
+  auto overlap = [bytes](const void* a, const void* b) {
+    const char* pa = static_cast<const char*>(a);
+    const char* pb = static_cast<const char*>(b);
+    return a && b && pa < pb + bytes && pb < pa + bytes;
+  };
+  if (overlap(c_hat_dev, c_new_dev) || overlap(c_bnd_dev, c_new_dev) || overlap(q_dev, c_new_dev))
+    return fail(ELM_ERR_ARG, "c_new overlaps an input");
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  if (prev != me->device) cudaSetDevice(me->device);
+  std::string err;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  elm_status st = me->precision == ELM_FP64
+                      ? elm::solve<double>(me, c_hat_dev, c_bnd_dev, q_dev, c_new_dev, tau, kappa, theta, rtol,
+                                           max_iter, iterations, residual, s, &err)
+                      : elm::solve<float>(me, c_hat_dev, c_bnd_dev, q_dev, c_new_dev, tau, kappa, theta, rtol,
+                                          max_iter, iterations, residual, s, &err);
+  if (prev >= 0 && prev != me->device) cudaSetDevice(prev);
+  return st == ELM_OK ? ELM_OK : fail(st, err);
+}

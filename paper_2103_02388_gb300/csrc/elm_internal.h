@@ -127,12 +127,29 @@ struct elm_mesh_s {
   unsigned long long* d_acc_U = nullptr;
   unsigned long long* d_maxbits = nullptr;
   unsigned* d_status = nullptr;
+  // diffusion solver (ELM_DIFFUSION): element tables per macro, boundary mask
+  // and CG vectors in the unique layout, reduction space
+  bool with_diffusion = false;
+  void* d_dtab = nullptr;
+  uint8_t* d_dbnd = nullptr;
+  int4* d_dcells = nullptr;
+  int64_t n_cell_chunks = 0;
+  int64_t n_boundary = 0;
+  void* d_dvec = nullptr;
+  double* d_dpart = nullptr;
+  double* d_dscal = nullptr;
 };
 
 namespace elm {
 
 // Sets the thread-local message returned by elm_last_error (api.cpp).
 void set_last_error(const std::string& msg);
+
+// Vectors of the diffusion solver (x, r, z, p, q, b, inverse diagonal).
+constexpr int kDiffVectors = 7;
+
+// Diffusion solver set-up at mesh creation (diffusion.cu).
+elm_status build_diffusion(elm_mesh_s* me, std::string* err);
 
 // Host mesh construction (mesh.cpp).
 elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const int64_t* mv,

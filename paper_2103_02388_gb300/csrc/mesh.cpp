@@ -309,6 +309,7 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
     *err = std::string("device table upload failed: ") + cudaGetErrorString(cudaGetLastError());
     return ELM_ERR_CUDA;
   }
+  if (me->with_diffusion) return build_diffusion(me, err);
   return ELM_OK;
 }
 

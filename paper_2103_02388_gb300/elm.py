@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import ELM_ADJOINT, ELM_FP32, ELM_FP64, ELM_HOST_ONLY, ELM_P1, check
+from ._lib import ELM_ADJOINT, ELM_DIFFUSION, ELM_FP32, ELM_FP64, ELM_HOST_ONLY, ELM_P1, check
 
 _DTYPES = {"fp64": (ELM_FP64, torch.float64, np.float64), "fp32": (ELM_FP32, torch.float32, np.float32)}
 
@@ -32,7 +32,7 @@ class Mesh:
     """
 
     def __init__(self, vertices, macros, level: int, precision: str = "fp64", host_only: bool = False,
-                 adjoint: bool = False, order: int = 2):
+                 adjoint: bool = False, order: int = 2, diffusion: bool = False):
         lib = _lib.load()
         self.vertices = np.ascontiguousarray(vertices, dtype=np.float64)
         self.macros = np.ascontiguousarray(macros, dtype=np.int64)
@@ -52,7 +52,7 @@ class Mesh:
                                   self.vertices.ctypes.data_as(ctypes.c_void_p),
                                   self.macros.shape[0], self.macros.ctypes.data_as(ctypes.c_void_p),
                                   self.level, code | (ELM_HOST_ONLY if host_only else 0) | (ELM_ADJOINT if adjoint else 0)
-                                  | (ELM_P1 if order == 1 else 0),
+                                  | (ELM_P1 if order == 1 else 0) | (ELM_DIFFUSION if diffusion else 0),
                                   ctypes.byref(h)))
         self._h = h
         self.n_nodes = int(lib.elm_mesh_num_nodes(h))
@@ -212,6 +212,42 @@ class Mesh:
             self.set_velocity(us[k - 1], us[k])
             cur = self.trace(cur, tau, n_sub, out=bufs[j % 2])
         return self.trace_eval(cur, T_src)
+
+    def diffusion_step(self, c_hat: torch.Tensor, tau: float, kappa: float, theta: float = 1.0,
+                       c_bnd: torch.Tensor | None = None, q: torch.Tensor | None = None, rtol: float | None = None,
+                       max_iter: int = 1000, out: torch.Tensor | None = None, stream=None):
+        """The diffusion solve of Eq. (linear system) (storage layout): returns
+        (c_new, iterations, relative residual).  Needs ``diffusion=True`` at
+        construction.  Synchronises the stream."""
+        for name, t in (("c_hat", c_hat), ("c_bnd", c_bnd), ("q", q)):
+            if t is not None:
+                self._check_tensor(t, name)
+                if t.shape != (self.n_nodes,):
+                    raise ValueError(f"{name} must have shape ({self.n_nodes},)")
+        if out is None:
+            out = torch.empty_like(c_hat)
+        else:
+            self._check_tensor(out, "out")
+        if rtol is None:
+            rtol = 1e-11 if self.precision == "fp64" else 2e-6
+        it = ctypes.c_int(0)
+        res = ctypes.c_double(0.0)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        check(_lib.load().elm_diffusion_step(self._h, ptr(c_hat), ptr(c_bnd), ptr(q), ptr(out), float(tau),
+                                             float(kappa), float(theta), float(rtol), int(max_iter),
+                                             ctypes.byref(it), ctypes.byref(res), _stream_ptr(stream)))
+        return out, int(it.value), float(res.value)
+
+    def strang_step(self, c: torch.Tensor, tau: float, kappa: float, n_sub: int = 1, theta: float = 1.0,
+                    c_bnd: torch.Tensor | None = None, c_bnd_half: torch.Tensor | None = None, **solve):
+        """One step of the Strang splitting (Algorithm 3): a diffusion solve
+        over tau/2, the advection step over tau with the current velocity,
+        and another diffusion solve over tau/2.  ``c_bnd_half`` / ``c_bnd``
+        are the boundary values at t_n + tau/2 and t_{n+1} (None: keep c's)."""
+        c1, _, _ = self.diffusion_step(c, 0.5 * tau, kappa, theta, c_bnd=c_bnd_half, **solve)
+        c2 = self.advect(c1, tau, n_sub)
+        c3, _, _ = self.diffusion_step(c2, 0.5 * tau, kappa, theta, c_bnd=c_bnd, **solve)
+        return c3
 
     def advect_adjoint(self, T_old: torch.Tensor, gT_new: torch.Tensor, dt: float, n_sub: int = 1,
                        split: bool = True, stream=None):

@@ -731,3 +731,41 @@ def test_diffusion_step_decays_a_fourier_mode():
     c = me.diffusion_step(mode, tau, kappa, 1.0, c_bnd=np.zeros(me.n_nodes))
     ratio = (mode @ c) / (mode @ mode)
     assert abs(ratio - 1.0 / (1.0 + tau * kappa * 2 * np.pi ** 2)) < 1e-5
+
+
+def _rotating_heat(x, t, kappa):
+    """Exact solution of dc/dt + u . grad c = kappa Delta c for u = (0.5 - y,
+    x - 0.5): the heat kernel of the advection-diffusion benchmark (Sec. 3.4)
+    centred at the rotated position of (0.5, 0.75)."""
+    xc = np.array([0.5 - 0.25 * np.sin(t), 0.5 + 0.25 * np.cos(t)])
+    return np.exp(-np.sum((x - xc) ** 2, axis=1) / (4.0 * t * kappa)) / (4.0 * np.pi * t * kappa)
+
+
+def test_strang_splitting_follows_the_exact_solution():
+    """Algorithm 3 (implicit-Euler diffusion over tau/2, advection over tau,
+    diffusion over tau/2) on the diffusing, rotating hill: after a quarter
+    revolution in 20 steps the relative H0 error against the exact solution
+    is below 1% at level 5 and falls from level 4 to level 5 (measured 1.5%
+    and 0.28%); advection alone (no diffusion solve) misses it by far."""
+    v, m = inputs.unit_square()
+    kappa = 1e-3
+    t0 = 2 * np.pi * 1e-3 / kappa
+    steps, T = 20, 0.5 * np.pi
+    tau = T / steps
+    errs = []
+    for level, diffuse in ((4, True), (5, True), (5, False)):
+        me = oracle.OracleMesh(v, m, level)
+        x = me.coords
+        u = inputs.rotation_2d(x, omega=1.0)
+        c = _rotating_heat(x, t0, kappa)
+        for k in range(steps):
+            t = t0 + k * tau
+            if diffuse:
+                c = me.diffusion_step(c, 0.5 * tau, kappa, 1.0, c_bnd=_rotating_heat(x, t + 0.5 * tau, kappa))
+            c = me.advect(c, u, tau)
+            if diffuse:
+                c = me.diffusion_step(c, 0.5 * tau, kappa, 1.0, c_bnd=_rotating_heat(x, t + tau, kappa))
+        ex = _rotating_heat(x, t0 + T, kappa)
+        errs.append(np.sqrt(me.mass_product(c - ex) / me.mass_product(ex)))
+    assert errs[1] < 0.01 and errs[1] < errs[0]
+    assert errs[2] > 5 * errs[1]
