@@ -231,7 +231,7 @@ elm_status elm_trace_eval(elm_mesh mesh, const void* D_dev, const void* T_src_de
 
 /* ---- Diffusion step (Sec. 2.2, Eq. finite-dimensional Galerkin approximation
  * and Eq. linear system; Algorithm 1 line 5 and the fractional steps of the
- * Strang splitting, Algorithm 3) ----
+ * Strang splitting, Algorithm 2) ----
  * Solves, for the P1 / P2 mass matrix M and stiffness matrix A of the mesh,
  *   (M + tau theta kappa A) c_new = (M - tau (1 - theta) kappa A) c_hat + tau M q
  * with c_new = c_bnd on the boundary of the macro mesh (Dirichlet), by

@@ -1,7 +1,7 @@
 // diffusion.cu -- the diffusion step of the advection-diffusion scheme
 // (arXiv 2103.02388, Sec. 2.2, Eq. finite-dimensional Galerkin approximation
 // and Eq. linear system; Algorithm 1 line 5, and the two fractional steps of
-// the Strang splitting, Algorithm 3):
+// the Strang splitting, Algorithm 2):
 //
 //   (M + tau theta kappa A) c^{n+1} = (M - tau (1 - theta) kappa A) c_hat
 //                                     + tau M q,        c = c_bnd on the boundary,

@@ -240,7 +240,7 @@ class Mesh:
 
     def strang_step(self, c: torch.Tensor, tau: float, kappa: float, n_sub: int = 1, theta: float = 1.0,
                     c_bnd: torch.Tensor | None = None, c_bnd_half: torch.Tensor | None = None, **solve):
-        """One step of the Strang splitting (Algorithm 3): a diffusion solve
+        """One step of the Strang splitting (Algorithm 2): a diffusion solve
         over tau/2, the advection step over tau with the current velocity,
         and another diffusion solve over tau/2.  ``c_bnd_half`` / ``c_bnd``
         are the boundary values at t_n + tau/2 and t_{n+1} (None: keep c's)."""

@@ -1,6 +1,6 @@
 """GPU parity of the diffusion step (Eq. linear system: Theta scheme, P1 / P2
 mass and stiffness, Dirichlet boundary, Jacobi-preconditioned CG) and of the
-Strang splitting (Algorithm 3) against the CPU oracle (sparse direct solve),
+Strang splitting (Algorithm 2) against the CPU oracle (sparse direct solve),
 through the C ABI.
 
 FP64: the CG tolerance is 1e-12 relative; the solution is compared to 1e-10
@@ -101,7 +101,7 @@ def _rotating_heat(x, t, kappa):
 
 
 def test_strang_splitting_matches_oracle_and_analytic():
-    """Algorithm 3 (diffusion tau/2, advection tau, diffusion tau/2) for a
+    """Algorithm 2 (diffusion tau/2, advection tau, diffusion tau/2) for a
     diffusing hill carried by the rotation: the GPU follows the oracle's
     composed scheme step by step (1e-10), and both stay close to the exact
     solution (relative H0 error below 1% after a quarter revolution)."""

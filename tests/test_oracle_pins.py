@@ -742,7 +742,7 @@ def _rotating_heat(x, t, kappa):
 
 
 def test_strang_splitting_follows_the_exact_solution():
-    """Algorithm 3 (implicit-Euler diffusion over tau/2, advection over tau,
+    """Algorithm 2 (implicit-Euler diffusion over tau/2, advection over tau,
     diffusion over tau/2) on the diffusing, rotating hill: after a quarter
     revolution in 20 steps the relative H0 error against the exact solution
     is below 1% at level 5 and falls from level 4 to level 5 (measured 1.5%
