@@ -455,17 +455,107 @@ def run_diffusion(args):
         "clocks": clocks.summary()}))
 
 
+VARIANT_WORKLOADS = {
+    # P1 elements (Sec. 3.1): the same node count as the default P2 workload
+    # (257^3 unique nodes at level 8), one advection step per launch
+    "c3-l8-p1-fp32": {"dim": 3, "level": 8, "precision": "fp32", "order": 1, "cfl": 4.0, "mode": "step"},
+    # look-back over the time-dependent swirling flow (Sec. 3.3, Table 3's
+    # 129^3-node P1 mesh, tau = 0.025): one interval of elm_trace per step,
+    # with the interval's velocity pair packed by elm_set_velocity
+    "swirl-l7-p1-fp32-trace": {"dim": 3, "level": 7, "precision": "fp32", "order": 1, "tau": 0.025,
+                               "mode": "trace"},
+}
+
+
+def run_variant(args):
+    """P1 and trace forms of the advection kernel: CUDA-event time per step
+    on the launching stream, with the HBM roofline of their compulsory bytes."""
+    import torch
+    from paper_2103_02388_gb300 import elm, inputs
+    w = VARIANT_WORKLOADS[args.workload]
+    dim, level, precision = w["dim"], w["level"], w["precision"]
+    v, m = inputs.unit_cube()
+    mesh = elm.Mesh(v, m, level, precision, order=w["order"])
+    x = mesh.unique_coords()
+    esz = 8 if precision == "fp64" else 4
+    n, ns = mesh.n_unique, mesh.n_nodes
+    stream = torch.cuda.current_stream()
+    tg = lambda a: mesh.to_storage(torch.tensor(a, dtype=mesh.dtype, device="cuda"))  # noqa: E731
+    if w["mode"] == "step":
+        u = inputs.random_fourier(x, seed=3)
+        dt = inputs.dt_for_cfl(w["cfl"], level, u)
+        mesh.set_velocity(tg(u))
+        Ta = tg(inputs.gaussian(x, (0.35, 0.5, 0.5), 0.1))
+        Tb = torch.empty_like(Ta)
+
+        def step(i):
+            nonlocal Ta, Tb
+            mesh.advect(Ta, dt, 1, out=Tb)
+            Ta, Tb = Tb, Ta
+        alg_bytes = ns * (dim * esz + 2 * esz)
+        launches = 1
+        cfg = {"cfl": w["cfl"], "dt": dt}
+    else:
+        tau = w["tau"]
+        K = int(round(1.5 / tau))
+        fields = [tg(inputs.swirl_3d(x, k * tau)) for k in range(K + 1)]
+        D = [torch.zeros((ns, dim), dtype=mesh.dtype, device="cuda") for _ in range(2)]
+
+        def step(i):
+            k = K - (i % K)
+            mesh.set_velocity(fields[k - 1], fields[k])
+            mesh.trace(D[i % 2] if i % K else None, tau, 1, out=D[(i + 1) % 2])
+        # read u^{k-1}, u^k ([n, 3] each), read D_in, write D_out
+        alg_bytes = ns * (2 * dim * esz + 2 * dim * esz)
+        launches = 3
+        cfg = {"tau": tau, "intervals": K}
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    mesh.status()
+    times = []
+    with ClockSampler(0) as clocks:
+        for i in range(args.steps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            step(args.warmup + i)
+            e.record(stream)
+            times.append((s, e))
+        torch.cuda.synchronize()
+    mesh.status()
+    ms = float(np.mean([s.elapsed_time(e) for s, e in times]))
+    hbm_peak, _, kind = _peaks()
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    print(json.dumps({
+        "metric": "traced node updates/s per step (1 GPU)" if w["mode"] == "step" else
+                  "traced node updates/s per look-back interval (1 GPU)",
+        "value": n / (ms * 1e-3), "unit": "node updates/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if precision == "fp32" else "f64", "data": "synthetic",
+        "config": dict({"workload": args.workload, "mesh": "unit cube, 6 Kuhn macro tetrahedra", "level": level,
+                        "order": w["order"], "unique_nodes": n, "storage_nodes": ns,
+                        "l2": "inputs larger than L2 (not flushed)"}, **cfg),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_kind": kind, "algorithmic_bytes_per_step": alg_bytes,
+                     "kernel": "k_advect" + (" (P1)" if w["mode"] == "step" else " (kTrace) + k_pack_velocity")},
+        "gpu_launches": launches * args.steps, "clocks": clocks.summary()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3-l7-fp32", choices=sorted(WORKLOADS) + sorted(DIFFUSION_WORKLOADS))
+    ap.add_argument("--workload", default="c3-l7-fp32",
+                    choices=sorted(WORKLOADS) + sorted(DIFFUSION_WORKLOADS) + sorted(VARIANT_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload in DIFFUSION_WORKLOADS:
         run_diffusion(args)
+        return
+    if args.workload in VARIANT_WORKLOADS:
+        run_variant(args)
         return
     spec = WORKLOADS[args.workload]
     if args.impl == "reference":
