@@ -106,6 +106,22 @@ elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz
 /* Frees the mesh and its device tables (after pending work on its streams). */
 elm_status elm_mesh_destroy(elm_mesh mesh);
 
+/* Blending onto an annulus (Sec. 2.1, blending map Phi; the curved domain of
+ * Sec. 3.4).  The 2D macro mesh must be a ring of n_sectors sectors: every
+ * vertex on a circle of radius in [r_min, r_max] at an angle
+ * theta0 + k 2 pi / n_sectors, every macro spanning one sector.  Phi maps
+ * each sector in polar form: the computational point
+ * rho ((1 - lam) e_k + lam e_{k+1}) (e_k the unit vector at angle theta_k)
+ * goes to rho e(theta_k + lam 2 pi / n_sectors), so chords become arcs with
+ * uniform angle and the vertices stay.  Afterwards node coordinates are
+ * physical, traced points live in the physical annulus (stage and departure
+ * points with a radius outside [r_min, r_max] are projected radially onto
+ * it), and every field evaluation pulls its point back with Phi^{-1} before
+ * the location.  Meshes: ELM_FP64, 2D, P1 or P2, without ELM_ADJOINT or
+ * ELM_DIFFUSION; blended meshes are not batched.  Returns ELM_ERR_TOPOLOGY
+ * for a mesh that is not such a ring.  Call once, before elm_set_velocity. */
+elm_status elm_mesh_set_annulus(elm_mesh mesh, double r_min, double r_max, int n_sectors, double theta0);
+
 /* Storage length n of every node vector of this mesh (0 for a null mesh). */
 int64_t elm_mesh_num_nodes(elm_mesh mesh);
 

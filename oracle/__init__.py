@@ -68,6 +68,8 @@ def _load():
         lib.orc_element_matrices.restype = I64
         lib.orc_element_matrices.argtypes = [P, P, P, P]
         lib.orc_boundary_nodes.argtypes = [P, P]
+        lib.orc_set_annulus.restype = I32
+        lib.orc_set_annulus.argtypes = [P, D, D, I32, D]
         _lib = lib
     return _lib
 
@@ -93,7 +95,7 @@ class OracleMesh:
     library's numbering by coordinates.
     """
 
-    def __init__(self, vertices, macros, level: int, order: int = 2):
+    def __init__(self, vertices, macros, level: int, order: int = 2, annulus=None):
         lib = _load()
         self.vertices = _f64(vertices)
         self.macros = np.ascontiguousarray(macros, dtype=np.int64)
@@ -104,6 +106,12 @@ class OracleMesh:
                                       self.macros.shape[0], _ptr(self.macros), self.level, self.order)
         if not self._h:
             raise ValueError("oracle: invalid mesh")
+        self.annulus = annulus
+        if annulus is not None:
+            # (r_min, r_max, n_sectors, theta0): blended onto the annulus (Sec. 2.1)
+            rmin, rmax, nsec, th0 = annulus
+            if lib.orc_set_annulus(self._h, float(rmin), float(rmax), int(nsec), float(th0)) != 0:
+                raise ValueError("oracle: not a 2D ring mesh")
         self.n_nodes = int(lib.orc_num_nodes(self._h))
         self.coords = np.empty((self.n_nodes, self.dim))
         lib.orc_node_coords(self._h, _ptr(self.coords))

@@ -116,12 +116,27 @@ struct Macro {
   double P[4][3];    // their coordinates
 };
 
+// Blending (Sec. 2.1, blending map Phi): a 2D macro mesh that is a ring of
+// n sectors between two regular n-gons, with vertices on the circles r_min and
+// r_max at the angles theta_k = theta0 + k Delta, Delta = 2 pi / n, is mapped
+// onto the annulus sector by sector in polar form: a computational point
+// x = rho ((1 - lam) e_k + lam e_{k+1}) (e_k the unit vector at theta_k, rho
+// running from r_min on the inner chord to r_max on the outer one) goes to
+// rho e(theta_k + lam Delta).  Vertices stay, chords become arcs with uniform
+// angle along them, and det DPhi = Delta / sin(Delta) everywhere.
+struct Blend {
+  bool on = false;
+  double rmin = 0.0, rmax = 0.0, theta0 = 0.0;
+  int nsec = 0;
+};
+
 struct Mesh {
   int d = 0, L = 0, N = 0, M = 0;   // dimension, level, N = 2^L, M = order * N
   int order = 2;                     // 1: P1 (nodes = micro vertices), 2: P2
   std::vector<Macro> mac;
   std::vector<std::vector<int32_t>> id;  // per macro: dense (M+1)^d table p -> node
-  std::vector<double> X;                 // node coordinates, [n_nodes, d]
+  std::vector<double> X;                 // node coordinates, [n_nodes, d] (physical: Phi applied)
+  Blend bl;
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
   int64_t n_nodes = 0;
 
@@ -247,9 +262,64 @@ struct Located {
   double mu[4];     // barycentric coordinates of the point in that micro simplex
 };
 
+// Sector k of the polar angle of x (x != 0) and lam = (theta - theta_k)/Delta.
+void blend_sector(const Blend& b, double theta, int* k, double* lam) {
+  const double pi = 3.14159265358979323846;
+  const double delta = 2.0 * pi / b.nsec;
+  const double t = (theta - b.theta0) / delta;
+  double kf = std::floor(t);
+  *lam = t - kf;
+  int kk = int(kf) % b.nsec;
+  if (kk < 0) kk += b.nsec;
+  *k = kk;
+}
+
+void blend_phi(const Blend& b, const double* xc, double* xp) {
+  const double pi = 3.14159265358979323846;
+  const double delta = 2.0 * pi / b.nsec;
+  int k;
+  double lam0;
+  blend_sector(b, std::atan2(xc[1], xc[0]), &k, &lam0);
+  const double tk = b.theta0 + k * delta, tk1 = tk + delta;
+  const double ek[2] = {std::cos(tk), std::sin(tk)}, ek1[2] = {std::cos(tk1), std::sin(tk1)};
+  // x parallel to p(lam) = (1 - lam) e_k + lam e_{k+1}
+  const double ck = ek[0] * xc[1] - ek[1] * xc[0], ck1 = ek1[0] * xc[1] - ek1[1] * xc[0];
+  const double lam = ck / (ck - ck1);
+  const double p[2] = {(1 - lam) * ek[0] + lam * ek1[0], (1 - lam) * ek[1] + lam * ek1[1]};
+  const double rho = std::sqrt(xc[0] * xc[0] + xc[1] * xc[1]) / std::sqrt(p[0] * p[0] + p[1] * p[1]);
+  const double th = tk + lam * delta;
+  xp[0] = rho * std::cos(th);
+  xp[1] = rho * std::sin(th);
+}
+
+void blend_phi_inv(const Blend& b, const double* xp, double* xc) {
+  const double pi = 3.14159265358979323846;
+  const double delta = 2.0 * pi / b.nsec;
+  int k;
+  double lam;
+  blend_sector(b, std::atan2(xp[1], xp[0]), &k, &lam);
+  const double tk = b.theta0 + k * delta, tk1 = tk + delta;
+  const double rho = std::sqrt(xp[0] * xp[0] + xp[1] * xp[1]);
+  xc[0] = rho * ((1 - lam) * std::cos(tk) + lam * std::cos(tk1));
+  xc[1] = rho * ((1 - lam) * std::sin(tk) + lam * std::sin(tk1));
+}
+
 // Domain rule for points outside the domain: componentwise clamp to the
-// bounding box (box domains: the Euclidean projection).
+// bounding box (box domains: the Euclidean projection); on a blended annulus
+// the radius is clamped to [r_min, r_max] (its Euclidean projection).
 void clamp_to_box(const Mesh& me, double* y) {
+  if (me.bl.on) {
+    const double r = std::sqrt(y[0] * y[0] + y[1] * y[1]);
+    if (r == 0.0) {
+      y[0] = me.bl.rmin;
+      y[1] = 0.0;
+    } else if (r < me.bl.rmin || r > me.bl.rmax) {
+      const double t = std::min(std::max(r, me.bl.rmin), me.bl.rmax) / r;
+      y[0] *= t;
+      y[1] *= t;
+    }
+    return;
+  }
   for (int r = 0; r < me.d; ++r) y[r] = std::min(std::max(y[r], me.lo[r]), me.hi[r]);
 }
 
@@ -360,10 +430,13 @@ int stencil(const Mesh& me, const Located& lc, int32_t* node, double* phi) {
   return me.order == 1 ? p1_stencil(me, lc, node, phi) : p2_stencil(me, lc, node, phi);
 }
 
-// Evaluates an ncomp-component P1 / P2 field (node-major [n_nodes, ncomp]) at y.
+// Evaluates an ncomp-component P1 / P2 field (node-major [n_nodes, ncomp]) at y
+// (physical; pulled back with Phi^{-1} on a blended mesh).
 void eval_field(const Mesh& me, const double* F, int ncomp, double* y, double* out) {
   Located lc;
-  locate(me, y, lc);
+  double yc[3] = {y[0], y[1], me.d == 3 ? y[2] : 0.0};
+  if (me.bl.on) blend_phi_inv(me.bl, y, yc);
+  locate(me, yc, lc);
   int32_t node[10];
   double phi[10];
   int n = stencil(me, lc, node, phi);
@@ -987,6 +1060,7 @@ void orc_advect_transpose(void* h, const double* u_old, const double* u_new, con
 void orc_mass_products(void* h, int nvec, const double* a, const double* b, double* out) {
   Mesh* me = static_cast<Mesh*>(h);
   const int d = me->d;
+
   const int nb = n_basis(d, me->order);
   std::vector<double> Mref(nb * nb);
   mass_unit(d, me->order, Mref.data());
@@ -1015,6 +1089,11 @@ void orc_mass_products(void* h, int nvec, const double* a, const double* b, doub
       out[k] += vol * s;
     }
   });
+  // blended annulus: det DPhi = Delta / sin(Delta) on the whole mesh
+  if (me->bl.on) {
+    const double delta = 2.0 * 3.14159265358979323846 / me->bl.nsec;
+    for (int k = 0; k < nvec; ++k) out[k] *= delta / std::sin(delta);
+  }
 }
 
 // Every micro simplex: macro id and vertex lattice points ([count, d+1, d]).
@@ -1040,6 +1119,23 @@ int64_t orc_element_matrices(void* h, int32_t* node_out, double* M_out, double* 
 
 // 1 for nodes on the boundary of the mesh, else 0 ([n_nodes]).
 void orc_boundary_nodes(void* h, uint8_t* out) { boundary_nodes(*static_cast<Mesh*>(h), out); }
+
+// Turns a 2D ring mesh into a blended annulus (see Blend): node coordinates
+// become physical.  Returns 0 on success, -1 if the mesh is not such a ring.
+int orc_set_annulus(void* h, double rmin, double rmax, int nsec, double theta0) {
+  Mesh* me = static_cast<Mesh*>(h);
+  if (me->d != 2 || nsec < 3 || !(rmin > 0.0) || !(rmax > rmin)) return -1;
+  me->bl.on = true;
+  me->bl.rmin = rmin;
+  me->bl.rmax = rmax;
+  me->bl.nsec = nsec;
+  me->bl.theta0 = theta0;
+  for (int64_t i = 0; i < me->n_nodes; ++i) {
+    double xc[2] = {me->X[i * 2], me->X[i * 2 + 1]};
+    blend_phi(me->bl, xc, &me->X[i * 2]);
+  }
+  return 0;
+}
 
 // Reference P1 / P2 mass matrix for a simplex of unit volume ([nb, nb]).
 void orc_mass_unit(int d, int order, double* out) { mass_unit(d, order, out); }

@@ -20,6 +20,7 @@ SIGNATURES = [
     ("elm_mesh_destroy", _I, [_P]),
     ("elm_mesh_num_nodes", _I64, [_P]),
     ("elm_mesh_num_unique", _I64, [_P]),
+    ("elm_mesh_set_annulus", _I, [_P, _D, _D, _I, _D]),
     ("elm_mesh_node_coords", _I, [_P, _P]),
     ("elm_mesh_unique_map", _I, [_P, _P]),
     ("elm_to_storage", _I, [_P, _P, _P, _I, _P]),

@@ -53,13 +53,14 @@ namespace {
 // One block per work-list chunk: a run of up to blockDim consecutive nodes
 // of one slab p1 of one macro (host-built, so no thread divides or searches
 // for its lattice point beyond one row root).
-// P is the element order (1 or 2), MODE what is done per node (NodeMode).
-template <int D, class R, bool STEADY, int P, int MODE>
+// P is the element order (1 or 2), MODE what is done per node (NodeMode),
+// BLEND whether the mesh is blended onto an annulus.
+template <int D, class R, bool STEADY, int P, int MODE, int BLEND>
 __global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
     k_advect(AdvectArgs args, Tables<R> tab, int chunk0) {
   const int4 ck = args.chunks[chunk0 + int(blockIdx.x)];
   if (int(threadIdx.x) >= ck.w) return;
-  const NodeJob<R> job{args.geo,
+  NodeJob<R> job{args.geo,
                        static_cast<const R*>(args.u_new),
                        static_cast<const R*>(args.u_old),
                        static_cast<const R*>(args.T_old),
@@ -73,7 +74,11 @@ __global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
                        args.n_sub,
                        static_cast<const R*>(args.D_in),
                        static_cast<R*>(args.D_out)};
-  advect_node<D, R, STEADY, P, MODE>(job, tab, ck, int(threadIdx.x));
+  if constexpr (BLEND == 1) {
+    job.bl = args.blend;
+    job.n_macros = args.n_macros;
+  }
+  advect_node<D, R, STEADY, P, MODE, BLEND>(job, tab, ck, int(threadIdx.x));
 }
 
 // Persistent batched kernel: each block repeatedly takes the next (instance,
@@ -152,9 +157,20 @@ __global__ void k_gather(const R* __restrict__ in, R* __restrict__ out, const in
 
 template <int D, class R, bool STEADY, int P, int MODE>
 cudaError_t launch_k(const AdvectArgs& a, Tables<R> t, cudaStream_t s) {
+  const bool blended = a.blend.nsec > 0;
+  if constexpr (D == 2 && sizeof(R) == 8) {
+    if (blended) {
+      for (int c0 = 0; c0 < a.n_chunks; c0 += (1 << 30)) {
+        const int nb = a.n_chunks - c0 < (1 << 30) ? a.n_chunks - c0 : (1 << 30);
+        k_advect<D, R, STEADY, P, MODE, 1><<<nb, kAdvectThreads, 0, s>>>(a, t, c0);
+      }
+      return cudaGetLastError();
+    }
+  }
+  if (blended) return cudaErrorInvalidValue;  // blending is 2D FP64 only (checked by the API)
   for (int c0 = 0; c0 < a.n_chunks; c0 += (1 << 30)) {
     const int nb = a.n_chunks - c0 < (1 << 30) ? a.n_chunks - c0 : (1 << 30);
-    k_advect<D, R, STEADY, P, MODE><<<nb, kAdvectThreads, 0, s>>>(a, t, c0);
+    k_advect<D, R, STEADY, P, MODE, 0><<<nb, kAdvectThreads, 0, s>>>(a, t, c0);
   }
   return cudaGetLastError();
 }

@@ -47,6 +47,8 @@ void free_tables(elm_mesh_s* me) {
   cudaFree(me->d_acc_U);
   cudaFree(me->d_maxbits);
   me->d_acc_T = me->d_acc_U = me->d_maxbits = nullptr;
+  cudaFree(const_cast<double*>(me->blend.sec));
+  me->blend.sec = nullptr;
   cudaFree(me->d_dtab);
   cudaFree(me->d_dbnd);
   cudaFree(me->d_dcells);
@@ -96,6 +98,7 @@ elm::AdvectArgs make_args(const elm_mesh_s* me, double dt, int n_sub) {
   a.chunks = me->d_chunks;
   a.n_chunks = int(me->n_chunks);
   a.order = me->order;
+  a.blend = me->blend;
   const double h = dt / n_sub;
   a.k64 = {h, 0.5 * h, h / 6.0, dt, 1.0 / me->M, double(me->N), {0, 0, 0}, {0, 0, 0}};
   a.k32 = {float(h), float(0.5 * h), float(h / 6.0), float(dt), float(1.0 / me->M), float(me->N),
@@ -190,10 +193,41 @@ int64_t elm_mesh_num_nodes(elm_mesh me) { return me ? me->n_storage : 0; }
 
 int64_t elm_mesh_num_unique(elm_mesh me) { return me ? me->n_unique : 0; }
 
+namespace {
+// Phi of the annulus blending on the host (the kernels' formula: the sector of
+// x's polar angle, lam from x parallel to (1 - lam) e_k + lam e_{k+1}, then
+// rho e(theta_k + lam delta)).
+void blend_point(const elm::BlendArgs& b, const std::vector<double>& sec, double* x) {
+  const double t = (std::atan2(x[1], x[0]) - b.theta0) / b.delta;
+  int k = int(std::floor(t)) % b.nsec;
+  if (k < 0) k += b.nsec;
+  const double e0 = sec[2 * k], e1 = sec[2 * k + 1], f0 = sec[2 * k + 2], f1 = sec[2 * k + 3];
+  const double ck = e0 * x[1] - e1 * x[0], ck1 = f0 * x[1] - f1 * x[0];
+  const double lam = ck / (ck - ck1);
+  const double p0 = (1.0 - lam) * e0 + lam * f0, p1 = (1.0 - lam) * e1 + lam * f1;
+  const double rho = std::sqrt(x[0] * x[0] + x[1] * x[1]) / std::sqrt(p0 * p0 + p1 * p1);
+  const double th = b.theta0 + (double(k) + lam) * b.delta;
+  x[0] = rho * std::cos(th);
+  x[1] = rho * std::sin(th);
+}
+
+std::vector<double> sector_table(int n, double theta0) {
+  std::vector<double> sec(2 * (n + 1));
+  const double delta = 2.0 * 3.14159265358979323846 / n;
+  for (int k = 0; k <= n; ++k) {
+    sec[2 * k] = std::cos(theta0 + (k % n) * delta);
+    sec[2 * k + 1] = std::sin(theta0 + (k % n) * delta);
+  }
+  return sec;
+}
+}  // namespace
+
 elm_status elm_mesh_node_coords(elm_mesh me, double* host_out) {
   if (!me || !host_out) return fail(ELM_ERR_ARG, "elm_mesh_node_coords: null argument");
   const int d = me->dim;
   const double invM = 1.0 / me->M;
+  const bool blended = me->blend.nsec > 0;
+  const std::vector<double> sec = blended ? sector_table(me->blend.nsec, me->blend.theta0) : std::vector<double>();
   for (int64_t m = 0; m < me->n_macros; ++m) {
     const elm::MacroGeo& g = me->geo[m];
     int64_t slot = m * me->npm;
@@ -204,6 +238,7 @@ elm_status elm_mesh_node_coords(elm_mesh me, double* host_out) {
         for (int c = 0; c < d; ++c) x += g.J[r * 3 + c] * (p[c] * invM);
         host_out[slot * d + r] = x;
       }
+      if (blended) blend_point(me->blend, sec, host_out + slot * d);
       ++slot;
     };
     if (d == 2) {
@@ -343,6 +378,72 @@ elm_status elm_trace_eval(elm_mesh me, const void* D_dev, const void* T_src_dev,
   a.T_new = T_dst_dev;
   cudaError_t e = elm::launch_advect(me->dim, me->precision, a, s);
   if (e != cudaSuccess) return cuda_fail(e, "elm_trace_eval");
+  return ELM_OK;
+}
+
+elm_status elm_mesh_set_annulus(elm_mesh me, double r_min, double r_max, int n_sectors, double theta0) {
+  if (!me) return fail(ELM_ERR_ARG, "elm_mesh_set_annulus: null mesh");
+  if (me->dim != 2 || me->precision != ELM_FP64)
+    return fail(ELM_ERR_ARG, "elm_mesh_set_annulus: blending is built for 2D FP64 meshes");
+  if (me->with_adjoint || me->with_diffusion)
+    return fail(ELM_ERR_ARG, "elm_mesh_set_annulus: not combinable with ELM_ADJOINT or ELM_DIFFUSION");
+  if (me->blend.nsec > 0) return fail(ELM_ERR_STATE, "elm_mesh_set_annulus: the mesh is blended already");
+  if (n_sectors < 3 || n_sectors > 4096 || !std::isfinite(theta0) || !(r_min > 0.0) || !(r_max > r_min) ||
+      !std::isfinite(r_max))
+    return fail(ELM_ERR_ARG, "elm_mesh_set_annulus: need 3 <= n_sectors <= 4096 and 0 < r_min < r_max");
+  // every macro: vertices on circles within [r_min, r_max] at sector angles,
+  // spanning exactly one sector
+  const double delta = 2.0 * 3.14159265358979323846 / n_sectors;
+  for (int64_t m = 0; m < me->n_macros; ++m) {
+    const elm::MacroGeo& g = me->geo[m];
+    int ks[3];
+    for (int v = 0; v <= 2; ++v) {
+      double x[2] = {g.v0[0], g.v0[1]};
+      for (int c = 0; c < v; ++c) {
+        x[0] += g.J[0 * 3 + c];
+        x[1] += g.J[1 * 3 + c];
+      }
+      const double r = std::sqrt(x[0] * x[0] + x[1] * x[1]);
+      const double t = (std::atan2(x[1], x[0]) - theta0) / delta;
+      const double kr = std::nearbyint(t);
+      if (r < r_min * (1 - 1e-12) || r > r_max * (1 + 1e-12) || std::fabs(t - kr) > 1e-9)
+        return fail(ELM_ERR_TOPOLOGY, "elm_mesh_set_annulus: macro " + std::to_string(m) +
+                                          " has a vertex off the ring's sector rays or radii");
+      ks[v] = ((int(kr) % n_sectors) + n_sectors) % n_sectors;
+    }
+    int lo = ks[0];
+    bool one_sector = false;
+    for (int v = 0; v <= 2 && !one_sector; ++v) {
+      lo = ks[v];
+      bool ok = true;
+      for (int w = 0; w <= 2; ++w) ok = ok && (ks[w] == lo || ks[w] == (lo + 1) % n_sectors);
+      bool has_lo = false, has_hi = false;
+      for (int w = 0; w <= 2; ++w) {
+        has_lo = has_lo || ks[w] == lo;
+        has_hi = has_hi || ks[w] == (lo + 1) % n_sectors;
+      }
+      one_sector = ok && has_lo && has_hi;
+    }
+    if (!one_sector)
+      return fail(ELM_ERR_TOPOLOGY, "elm_mesh_set_annulus: macro " + std::to_string(m) + " does not span one sector");
+  }
+  const std::vector<double> sec = sector_table(n_sectors, theta0);
+  double* d_sec = nullptr;
+  if (!me->host_only) {
+    DeviceGuard g(me->device);
+    cudaError_t e = cudaMalloc((void**)&d_sec, sizeof(double) * sec.size());
+    if (e == cudaSuccess) e = cudaMemcpy(d_sec, sec.data(), sizeof(double) * sec.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d_sec);
+      return cuda_fail(e, "elm_mesh_set_annulus");
+    }
+  }
+  me->blend.sec = d_sec;
+  me->blend.nsec = n_sectors;
+  me->blend.theta0 = theta0;
+  me->blend.delta = delta;
+  me->blend.rmin = r_min;
+  me->blend.rmax = r_max;
   return ELM_OK;
 }
 

@@ -107,6 +107,8 @@ elm_status elm_batch_create(const elm_mesh* meshes, int count, int blocks_per_sm
   for (int k = 0; k < count; ++k) {
     if (!meshes[k]) return bfail(ELM_ERR_ARG, "elm_batch_create: null mesh " + std::to_string(k));
     if (meshes[k]->host_only) return bfail(ELM_ERR_STATE, "elm_batch_create: host-only mesh " + std::to_string(k));
+    if (meshes[k]->blend.nsec > 0)
+      return bfail(ELM_ERR_ARG, "elm_batch_create: blended meshes are not batched (mesh " + std::to_string(k) + ")");
     if (meshes[k]->order != 2)
       return bfail(ELM_ERR_ARG, "elm_batch_create: the batched form takes P2 meshes only (mesh " + std::to_string(k) + ")");
     if (meshes[k]->precision != meshes[0]->precision)

@@ -69,6 +69,16 @@ struct StepConsts {
   R lo[3], hi[3];  // bounding box
 };
 
+// Blending onto an annulus (Sec. 2.1, blending map Phi; elm_mesh_set_annulus):
+// a 2D ring mesh of nsec sectors with vertices at the angles theta0 + k delta
+// on circles, mapped sector by sector in polar form (see tracer.cuh).
+// nsec = 0: no blending (Phi = Id).
+struct BlendArgs {
+  const double* sec = nullptr;  // unit vectors e_k at theta0 + k delta, k = 0..nsec ([nsec + 1][2])
+  int nsec = 0;
+  double theta0 = 0.0, delta = 0.0, rmin = 0.0, rmax = 0.0;
+};
+
 // Everything a kernel launch needs, passed by value.
 struct AdvectArgs {
   const MacroGeo* geo;     // [n_macros]
@@ -94,6 +104,7 @@ struct AdvectArgs {
   int mode = 0;               // per-node work (NodeMode in tracer.cuh): step, trace, evaluation
   const void* D_in = nullptr; // departure offsets [n, dim] (trace / evaluation)
   void* D_out = nullptr;
+  BlendArgs blend;
   StepConsts<float> k32;
   StepConsts<double> k64;
 };
@@ -103,6 +114,7 @@ struct AdvectArgs {
 struct elm_mesh_s {
   int dim = 0, level = 0, N = 0, M = 0, precision = ELM_FP64;
   int order = 2;                     // element order (P1 / P2); M = order * N
+  elm::BlendArgs blend;              // annulus blending (nsec > 0), device sector table in blend.sec
   bool host_only = false;
   int64_t n_macros = 0, npm = 0, n_storage = 0, n_unique = 0, n_ghost = 0;
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};

@@ -127,6 +127,7 @@ extern "C" elm_status elm_advect_noalloc(elm_mesh me, const void* u_old_dev, con
   a.chunks = me->d_chunks;
   a.n_chunks = int(me->n_chunks);
   a.order = me->order;
+  a.blend = me->blend;
   {
     const double h = dt / n_sub;
     a.k64 = {h, 0.5 * h, h / 6.0, dt, 1.0 / me->M, double(me->N), {0, 0, 0}, {0, 0, 0}};

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "elm_internal.h"
 
@@ -247,6 +248,47 @@ __device__ __noinline__ Min64 bary64_min(const MacroGeo* geo, int m0, int p0, in
   return out;
 }
 
+// Brute-force macro search for x_i + d (rare path): the macro whose reference
+// simplex holds the point best (largest minimum barycentric, lattice units).
+// On a non-convex mesh (an annulus) the walk can end at a boundary face while
+// the point lies in the mesh behind it.
+template <int D, class R, int P>
+__device__ __noinline__ int best_macro(Tables<R> tab, const MacroGeo* geo, int nmac, int m0, int p0, int p1, int p2,
+                                       int N, float invM, R d0, R d1, R d2) {
+  const R d[3] = {d0, d1, d2};
+  int best = m0;
+  R bestl = R(-1e30);
+  for (int mm = 0; mm < nmac; ++mm) {
+    R bq[3], r0[3];
+    if constexpr (sizeof(R) == 8) {
+      const FrameD f = frame64<D, P>(geo, m0, p0, p1, p2, N, mm);
+      bq[0] = f.bq0; bq[1] = f.bq1; bq[2] = f.bq2;
+      r0[0] = f.r00; r0[1] = f.r01; r0[2] = f.r02;
+    } else {
+      const Frame f = frame_df<D>(tab.g, m0, p0, p1, p2, invM, mm);
+      bq[0] = f.bq0; bq[1] = f.bq1; bq[2] = f.bq2;
+      r0[0] = f.r00; r0[1] = f.r01; r0[2] = f.r02;
+    }
+    R q[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      R v = r0[k];
+#pragma unroll
+      for (int j = 0; j < D; ++j) v = r_fma(tab.nj(mm, k * 3 + j), d[j], v);
+      q[k] = bq[k] + v;
+    }
+    R l = R(N) - q[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) l = r_min(l, q[k - 1] - q[k]);
+    l = r_min(l, q[D - 1]);
+    if (l > bestl) {
+      bestl = l;
+      best = mm;
+    }
+  }
+  return best;
+}
+
 // r = r0 + N J_m^{-1} d in a macro other than the block's (after a hand-off;
 // not inlined so the common path carries no table loads or selects).
 template <class R>
@@ -268,10 +310,52 @@ __device__ __noinline__ Vec3<R> lattice_foreign(Tables<R> tab, int m, R r00, R r
   return Vec3<R>{r[0], r[1], r[2]};
 }
 
+// Blending onto an annulus (Sec. 2.1; 2D, FP64).  The ring mesh's sector k
+// (between the rays at theta_k = theta0 + k delta) holds the computational
+// points x = rho ((1 - lam) e_k + lam e_{k+1}), rho between the chords of two
+// circles; Phi(x) = rho e(theta_k + lam delta) carries chords onto arcs with
+// uniform angle.  Phi^{-1}(y): lam from the polar angle of y, rho = |y|.
+__device__ __noinline__ void blend_inv(const BlendArgs& b, double y0, double y1, double* xc) {
+  const double t = (atan2(y1, y0) - b.theta0) / b.delta;
+  const double kf = floor(t);
+  const double lam = t - kf;
+  int k = int(kf) % b.nsec;
+  if (k < 0) k += b.nsec;
+  const double rho = sqrt(y0 * y0 + y1 * y1);
+  xc[0] = rho * ((1.0 - lam) * b.sec[2 * k] + lam * b.sec[2 * k + 2]);
+  xc[1] = rho * ((1.0 - lam) * b.sec[2 * k + 1] + lam * b.sec[2 * k + 3]);
+}
+
+__device__ __noinline__ void blend_fwd(const BlendArgs& b, double x0, double x1, double* xp) {
+  const double t = (atan2(x1, x0) - b.theta0) / b.delta;
+  int k = int(floor(t)) % b.nsec;
+  if (k < 0) k += b.nsec;
+  const double e0 = b.sec[2 * k], e1 = b.sec[2 * k + 1], f0 = b.sec[2 * k + 2], f1 = b.sec[2 * k + 3];
+  // x parallel to (1 - lam) e_k + lam e_{k+1}
+  const double ck = e0 * x1 - e1 * x0, ck1 = f0 * x1 - f1 * x0;
+  const double lam = ck / (ck - ck1);
+  const double p0 = (1.0 - lam) * e0 + lam * f0, p1 = (1.0 - lam) * e1 + lam * f1;
+  const double rho = sqrt(x0 * x0 + x1 * x1) / sqrt(p0 * p0 + p1 * p1);
+  double s, c;
+  sincos(b.theta0 + (double(k) + lam) * b.delta, &s, &c);
+  xp[0] = rho * c;
+  xp[1] = rho * s;
+}
+
 // Per-thread tracing state.  P is the element order of the velocity and the
-// scalar (Sec. 3.1: linear P1 or quadratic P2 Lagrange elements).
-template <int D, class R, bool STEADY, int P = 2>
-struct Tracer {
+// scalar (Sec. 3.1: linear P1 or quadratic P2 Lagrange elements).  BLEND = 1:
+// the mesh is blended onto an annulus; points and offsets are physical and
+// pulled back with Phi^{-1} before location.
+// Start-node state of the blended form (empty otherwise).
+struct BlendState {
+  BlendArgs bl;
+  double xc[2], xp[2];  // start node: computational and physical position
+};
+struct NoBlendState {};
+
+template <int D, class R, bool STEADY, int P = 2, int BLEND = 0>
+struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
+  static_assert(BLEND == 0 || (D == 2 && sizeof(R) == 8), "blending: 2D FP64 only");
   static_assert(P == 1 || P == 2, "element order");
   static constexpr int NB = P == 2 ? (D + 1) * (D + 2) / 2 : D + 1;  // nodes of a simplex
   // launch constants (copied, so no kernel parameter is addressed)
@@ -279,6 +363,7 @@ struct Tracer {
   Tables<R> tab;         // macro table in the working precision
   int N;
   int npm;
+  int nmac = 0;    // macros of the mesh (0: no brute-force search)
   const R* un;
   const R* uo;
   const R* T;
@@ -411,6 +496,7 @@ struct Tracer {
   // macro's reference simplex N >= q1 >= q2 (>= q3) >= 0.
   __device__ void locate(const R* d, R* c, R* f) {
     R lmin;
+    bool searched = false;
     for (int hop = 0;; ++hop) {
       R r[D];
       if (m == mb) {
@@ -490,6 +576,37 @@ struct Tracer {
       } else {
         outside = lmin < R(-kTol64);
         nb = outside ? tab.nb(m, kmin) : -1;
+      }
+      if (outside && nb < 0) {
+        // The most negative face is a boundary face.  On a non-convex mesh
+        // (an annulus) the point can still lie in the mesh behind another
+        // negative face: walk across the most negative face that has a
+        // neighbour, if any.
+        R best = -kBand;
+#pragma unroll
+        for (int k = 0; k <= D; ++k) {
+          if (l[k] < best) {
+            const int n2 = tab.nb(m, k);
+            if (n2 >= 0) {
+              best = l[k];
+              kmin = k;
+              nb = n2;
+            }
+          }
+        }
+      }
+      if constexpr (BLEND == 1) {
+        if (outside && nb < 0 && nmac > 0 && !searched) {
+          // still outside only through boundary faces of a non-convex mesh:
+          // search every macro once
+          searched = true;
+          const int mm = best_macro<D, R, P>(tab, geo, nmac, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, N,
+                                             float(invM), d[0], d[1], D == 3 ? d[D - 1] : R(0));
+          if (mm != m) {
+            foreign_frame(mm);
+            continue;
+          }
+        }
       }
       if (!outside || nb < 0) break;  // inside, or outside the mesh (retraction clamps)
       if (hop >= kMaxHops) {
@@ -718,15 +835,46 @@ struct Tracer {
   }
 
   __device__ void clamp_box(R* d) const {
+    if constexpr (BLEND == 1) {
+      // the annulus: radius clamped to [r_min, r_max] (Euclidean projection)
+      const double y0 = this->xp[0] + d[0], y1 = this->xp[1] + d[1];
+      const double r = sqrt(y0 * y0 + y1 * y1);
+      if (r < this->bl.rmin || r > this->bl.rmax) {
+        const double s = r > 0.0 ? fmin(fmax(r, this->bl.rmin), this->bl.rmax) / r : 0.0;
+        d[0] = (r > 0.0 ? s * y0 : this->bl.rmin) - this->xp[0];
+        d[1] = s * y1 - this->xp[1];
+      }
+      return;
+    }
 #pragma unroll
     for (int k = 0; k < D; ++k) d[k] = r_clamp(d[k], dlo[k], dhi[k]);
+  }
+
+  // Offset in the coordinates the mesh is located in: d itself, or on a
+  // blended mesh Phi^{-1}(x_i + d) - Phi^{-1}(x_i).
+  __device__ void to_comp(const R* d, R* dc) const {
+    if constexpr (BLEND == 1) {
+      double yc[2];
+      blend_inv(this->bl, this->xp[0] + d[0], this->xp[1] + d[1], yc);
+      dc[0] = yc[0] - this->xc[0];
+      dc[1] = yc[1] - this->xc[1];
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) dc[k] = d[k];
+    }
   }
 
   // Velocity u~ at x_i + d at backward time `back` (Eq. linear interpolation).
   // Velocities are packed records (x, y[, z], 0): one vector load per node.
   __device__ void velocity(const R* d, R back, R* k) {
     R c[D], f[D];
-    locate(d, c, f);
+    if constexpr (BLEND == 1) {
+      R dc[D];
+      to_comp(d, dc);
+      locate(dc, c, f);
+    } else {
+      locate(d, c, f);
+    }
     int slot[NB];
     R phi[NB];
     stencil(c, f, slot, phi);
@@ -788,7 +936,13 @@ struct Tracer {
 
   __device__ R scalar(const R* d) {
     R c[D], f[D];
-    locate(d, c, f);
+    if constexpr (BLEND == 1) {
+      R dc[D];
+      to_comp(d, dc);
+      locate(dc, c, f);
+    } else {
+      locate(d, c, f);
+    }
     int slot[NB];
     R phi[NB];
     stencil(c, f, slot, phi);
@@ -834,6 +988,8 @@ struct NodeJob {
   int n_sub;
   const R* D_in = nullptr;  // departure offsets [n, D] (trace / evaluation modes)
   R* D_out = nullptr;
+  BlendArgs bl;             // annulus blending (BLEND = 1)
+  int n_macros = 0;         // enables the brute-force search of non-convex meshes (BLEND = 1)
 };
 
 // What advect_node does with a node.
@@ -845,15 +1001,16 @@ enum NodeMode {
 
 // One node: particle creation (i), backward RK4 (ii), T evaluation (iii).
 // The node is entry `tid` of chunk ck = (macro, slab p1, first index, count).
-template <int D, class R, bool STEADY, int P = 2, int MODE = kStep>
+template <int D, class R, bool STEADY, int P = 2, int MODE = kStep, int BLEND = 0>
 __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab, int4 ck, int tid) {
   const StepConsts<R>& K = job.K;
   const int npm = job.npm;
-  Tracer<D, R, STEADY, P> t;
+  Tracer<D, R, STEADY, P, BLEND> t;
   t.geo = job.geo;
   t.tab = tab;
   t.N = job.N;
   t.npm = npm;
+  t.nmac = job.n_macros;
   t.un = job.un;
   t.uo = job.uo;
   t.T = job.T_old;
@@ -895,6 +1052,11 @@ __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab
       for (int c = 0; c < D; ++c) x = r_fma(tab.J(t.m0, q * 3 + c), to_real<R>(t.p[c]) * K.invM, x);
       t.dlo[q] = K.lo[q] - x;
       t.dhi[q] = K.hi[q] - x;
+      if constexpr (BLEND == 1) t.xc[q] = double(x);
+    }
+    if constexpr (BLEND == 1) {
+      t.bl = job.bl;
+      blend_fwd(job.bl, t.xc[0], t.xc[1], t.xp);
     }
   }
   t.home_frame();
@@ -919,7 +1081,7 @@ __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab
     const R h = K.h, h2 = K.h2, h6 = K.h6;
     R k[D], acc[D];
     R u_node[D];
-    Tracer<D, R, STEADY, P>::load_rec(t.un, own_slot, u_node);
+    Tracer<D, R, STEADY, P, BLEND>::load_rec(t.un, own_slot, u_node);
 #pragma unroll
     for (int q = 0; q < D; ++q) {
       // the first stage of a trace that starts on the node: the P1 / P2

@@ -32,7 +32,7 @@ class Mesh:
     """
 
     def __init__(self, vertices, macros, level: int, precision: str = "fp64", host_only: bool = False,
-                 adjoint: bool = False, order: int = 2, diffusion: bool = False):
+                 adjoint: bool = False, order: int = 2, diffusion: bool = False, annulus=None):
         lib = _lib.load()
         self.vertices = np.ascontiguousarray(vertices, dtype=np.float64)
         self.macros = np.ascontiguousarray(macros, dtype=np.int64)
@@ -55,6 +55,11 @@ class Mesh:
                                   | (ELM_P1 if order == 1 else 0) | (ELM_DIFFUSION if diffusion else 0),
                                   ctypes.byref(h)))
         self._h = h
+        if annulus is not None:
+            # (r_min, r_max, n_sectors, theta0): blending onto the annulus (Sec. 2.1)
+            r_min, r_max, n_sec, th0 = annulus
+            check(lib.elm_mesh_set_annulus(h, float(r_min), float(r_max), int(n_sec), float(th0)))
+        self.annulus = annulus
         self.n_nodes = int(lib.elm_mesh_num_nodes(h))
         self.n_unique = int(lib.elm_mesh_num_unique(h))
         self._u = None

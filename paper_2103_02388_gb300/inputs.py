@@ -76,6 +76,36 @@ def cube_block(k: int, perturb: float = 0.0, seed: int = 0):
     return v, np.array(macros, dtype=np.int64)
 
 
+def annulus_ring(n_sectors: int = 6, n_layers: int = 2, r_min: float = 0.5, r_max: float = 1.5,
+                 theta0: float = 0.0):
+    """Coarse ring mesh of an annulus (Sec. 3.4): n_sectors sectors times
+    n_layers radial layers, vertices on the circles r_min + (r_max - r_min) j /
+    n_layers at the angles theta0 + 2 pi k / n_sectors, two triangles per
+    cell.  Blending maps it onto the annulus.  Returns (vertices, triangles)."""
+    th = theta0 + 2.0 * np.pi * np.arange(n_sectors) / n_sectors
+    radii = r_min + (r_max - r_min) * np.arange(n_layers + 1) / n_layers
+    v = np.concatenate([np.stack([r * np.cos(th), r * np.sin(th)], axis=1) for r in radii])
+    tris = []
+    for j in range(n_layers):
+        for k in range(n_sectors):
+            k1 = (k + 1) % n_sectors
+            a, b = j * n_sectors + k, j * n_sectors + k1
+            c, d = (j + 1) * n_sectors + k, (j + 1) * n_sectors + k1
+            tris.append([a, b, c])
+            tris.append([b, d, c])
+    return v, np.array(tris, dtype=np.int64)
+
+
+def heat_kernel_rotating(x, t: float, kappa: float, start=(0.0, 1.0)):
+    """The exact solution of the advection-diffusion benchmark of Sec. 3.4:
+    the heat kernel 1/(4 pi t kappa) exp(-r^2 / (4 t kappa)) centred at the
+    start point rotated by the angle t about the origin."""
+    x = np.asarray(x, dtype=np.float64)
+    c = np.array([start[0] * np.cos(t) - start[1] * np.sin(t), start[0] * np.sin(t) + start[1] * np.cos(t)])
+    r2 = np.sum((x - c) ** 2, axis=1)
+    return np.exp(-r2 / (4.0 * t * kappa)) / (4.0 * np.pi * t * kappa)
+
+
 def square_block(k: int, perturb: float = 0.0, seed: int = 0):
     """[0,1]^2 as a k x k block of squares, 2 triangles each (diagonal (1,1))."""
     g = np.linspace(0.0, 1.0, k + 1)

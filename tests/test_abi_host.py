@@ -182,3 +182,35 @@ def test_missing_library_fails_loudly(tmp_path):
             _lib.load(str(tmp_path / "libelm.so"))
     finally:
         _lib._lib = saved
+
+
+@pytest.mark.parametrize("order", [2, 1])
+def test_blended_annulus_host_coordinates(lib, order):
+    """elm_mesh_set_annulus: node coordinates become physical and equal the
+    oracle's blended nodes (matched as point sets)."""
+    from paper_2103_02388_gb300 import elm
+    v, m = inputs.annulus_ring(6, 2)
+    gm = elm.Mesh(v, m, 3, host_only=True, order=order, annulus=(0.5, 1.5, 6, 0.0))
+    om = oracle.OracleMesh(v, m, 3, order=order, annulus=(0.5, 1.5, 6, 0.0))
+    perm = match_nodes(om.coords, gm.unique_coords(), tol=1e-12)
+    assert sorted(perm) == list(range(gm.n_unique))
+    r = np.hypot(*gm.node_coords().T)
+    assert abs(r.min() - 0.5) < 1e-14 and abs(r.max() - 1.5) < 1e-14
+
+
+def test_blended_annulus_argument_errors(lib):
+    v, m = inputs.annulus_ring(6, 2)
+    st, h = _host_mesh(lib, v, m, 2)
+    assert lib.elm_mesh_set_annulus(h, 0.5, 1.5, 5, 0.0) == _lib.ELM_ERR_TOPOLOGY   # wrong sector count
+    assert lib.elm_mesh_set_annulus(h, 0.6, 1.5, 6, 0.0) == _lib.ELM_ERR_TOPOLOGY   # radius outside
+    assert lib.elm_mesh_set_annulus(h, 1.5, 0.5, 6, 0.0) == _lib.ELM_ERR_ARG
+    assert lib.elm_mesh_set_annulus(h, 0.5, 1.5, 6, 0.0) == _lib.ELM_OK
+    assert lib.elm_mesh_set_annulus(h, 0.5, 1.5, 6, 0.0) == _lib.ELM_ERR_STATE      # twice
+    st, h32 = _host_mesh(lib, v, m, 2, precision=_lib.ELM_FP32)
+    assert lib.elm_mesh_set_annulus(h32, 0.5, 1.5, 6, 0.0) == _lib.ELM_ERR_ARG     # FP64 only
+    sv, sm = inputs.unit_square()
+    st, hs = _host_mesh(lib, sv, sm, 2)
+    assert lib.elm_mesh_set_annulus(hs, 0.5, 1.5, 6, 0.0) == _lib.ELM_ERR_TOPOLOGY
+    cv, cm = inputs.unit_cube()
+    st, hc = _host_mesh(lib, cv, cm, 1)
+    assert lib.elm_mesh_set_annulus(hc, 0.5, 1.5, 6, 0.0) == _lib.ELM_ERR_ARG      # 2D only
