@@ -117,9 +117,13 @@ elm_status elm_mesh_destroy(elm_mesh mesh);
  * physical, traced points live in the physical annulus (stage and departure
  * points with a radius outside [r_min, r_max] are projected radially onto
  * it), and every field evaluation pulls its point back with Phi^{-1} before
- * the location.  Meshes: ELM_FP64, 2D, P1 or P2, without ELM_ADJOINT or
- * ELM_DIFFUSION; blended meshes are not batched.  Returns ELM_ERR_TOPOLOGY
- * for a mesh that is not such a ring.  Call once, before elm_set_velocity. */
+ * the location.  With ELM_DIFFUSION the call also builds the diffusion
+ * solver's per-micro-simplex mass and stiffness matrices of the blended
+ * geometry (the stiffness with the metric DPhi^{-1} DPhi^{-T} |det DPhi| by a
+ * 5 x 5 collapsed Gauss rule; 2 nb^2 doubles per micro simplex).  Meshes:
+ * ELM_FP64, 2D, P1 or P2, without ELM_ADJOINT; blended meshes are not
+ * batched.  Returns ELM_ERR_TOPOLOGY for a mesh that is not such a ring.
+ * Call once, before elm_set_velocity. */
 elm_status elm_mesh_set_annulus(elm_mesh mesh, double r_min, double r_max, int n_sectors, double theta0);
 
 /* Storage length n of every node vector of this mesh (0 for a null mesh). */

@@ -683,6 +683,72 @@ void grad_lambdas(int d, const double V[4][3], double G[4][3]) {
     }
 }
 
+double poly_eval(const Poly& P, const double* mu) {
+  double s = 0.0;
+  for (auto& t : P.c) {
+    double v = t.second;
+    for (int k = 0; k < 4; ++k)
+      for (int e = 0; e < t.first[k]; ++e) v *= mu[k];
+    s += v;
+  }
+  return s;
+}
+
+// Gauss-Legendre nodes and weights on [0, 1] (Newton on the Legendre
+// recurrence).
+void gauss_legendre01(int n, double* x, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) p0 = 1.0;
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Metric of the blended stiffness at a computational point x (2D annulus,
+// Sec. 2.1): G = DPhi^{-1} DPhi^{-T} |det DPhi|, so that
+// int grad_y a . grad_y b dy = int grad_x a^T G grad_x b dx.  DPhi from the
+// sector coordinates (lam, rho): x = rho p(lam), y = rho e(theta_k + lam Delta),
+// DPhi = (dy/d(lam, rho)) (dx/d(lam, rho))^{-1}.
+void blend_metric(const Blend& b, const double* x, double G[2][2]) {
+  const double pi = 3.14159265358979323846;
+  const double delta = 2.0 * pi / b.nsec;
+  int k;
+  double lam0;
+  blend_sector(b, std::atan2(x[1], x[0]), &k, &lam0);
+  const double tk = b.theta0 + k * delta;
+  const double ek[2] = {std::cos(tk), std::sin(tk)}, ek1[2] = {std::cos(tk + delta), std::sin(tk + delta)};
+  const double ck = ek[0] * x[1] - ek[1] * x[0], ck1 = ek1[0] * x[1] - ek1[1] * x[0];
+  const double lam = ck / (ck - ck1);
+  const double p[2] = {(1 - lam) * ek[0] + lam * ek1[0], (1 - lam) * ek[1] + lam * ek1[1]};
+  const double rho = std::sqrt(x[0] * x[0] + x[1] * x[1]) / std::sqrt(p[0] * p[0] + p[1] * p[1]);
+  const double th = tk + lam * delta;
+  const double Jx[2][2] = {{rho * (ek1[0] - ek[0]), p[0]}, {rho * (ek1[1] - ek[1]), p[1]}};
+  const double Jy[2][2] = {{-rho * delta * std::sin(th), std::cos(th)}, {rho * delta * std::cos(th), std::sin(th)}};
+  const double dx = Jx[0][0] * Jx[1][1] - Jx[0][1] * Jx[1][0];
+  const double Jxi[2][2] = {{Jx[1][1] / dx, -Jx[0][1] / dx}, {-Jx[1][0] / dx, Jx[0][0] / dx}};
+  double D[2][2];
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c) D[r][c] = Jy[r][0] * Jxi[0][c] + Jy[r][1] * Jxi[1][c];
+  const double det = D[0][0] * D[1][1] - D[0][1] * D[1][0];
+  const double Di[2][2] = {{D[1][1] / det, -D[0][1] / det}, {-D[1][0] / det, D[0][0] / det}};
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c) G[r][c] = (Di[r][0] * Di[c][0] + Di[r][1] * Di[c][1]) * std::fabs(det);
+}
+
 // Per-micro-simplex local node ids [n_simplices, nb] and matrices
 // [n_simplices, nb, nb] of the mass and the stiffness; returns the number of
 // micro simplices (the outputs may be null to query it).
@@ -718,6 +784,44 @@ int64_t element_matrices(const Mesh& me, int32_t* node_out, double* M_out, doubl
       grad_lambdas(d, V, G);
       double* Me = M_out + n * nb * nb;
       double* Ae = A_out + n * nb * nb;
+      if (me.bl.on) {
+        // blended (2D): det DPhi = Delta / sin(Delta) scales the mass; the
+        // stiffness by a 5 x 5 collapsed Gauss rule with the metric above
+        const double delta = 2.0 * 3.14159265358979323846 / me.bl.nsec;
+        const double jac = delta / std::sin(delta);
+        for (int i = 0; i < nb * nb; ++i) {
+          Me[i] = vol * Mref[i] * jac;
+          Ae[i] = 0.0;
+        }
+        double gx[5], gw[5];
+        gauss_legendre01(5, gx, gw);
+        for (int a = 0; a < 5; ++a)
+          for (int bq = 0; bq < 5; ++bq) {
+            const double u = gx[a], v = gx[bq];
+            const double mu[4] = {1.0 - u - v * (1.0 - u), u, v * (1.0 - u), 0.0};
+            const double W = gw[a] * gw[bq] * (1.0 - u) * 2.0 * vol;
+            double xq[2] = {0.0, 0.0};
+            for (int j = 0; j <= 2; ++j)
+              for (int r = 0; r < 2; ++r) xq[r] += mu[j] * V[j][r];
+            double Gm[2][2];
+            blend_metric(me.bl, xq, Gm);
+            double gr[10][2];
+            for (int i = 0; i < nb; ++i) {
+              gr[i][0] = gr[i][1] = 0.0;
+              for (int k = 0; k <= 2; ++k) {
+                const double dk = poly_eval(diff_poly(basis_poly(2, me.order, i), k), mu);
+                gr[i][0] += dk * G[k][0];
+                gr[i][1] += dk * G[k][1];
+              }
+            }
+            for (int i = 0; i < nb; ++i)
+              for (int j = 0; j < nb; ++j)
+                Ae[i * nb + j] += W * (gr[i][0] * (Gm[0][0] * gr[j][0] + Gm[0][1] * gr[j][1]) +
+                                       gr[i][1] * (Gm[1][0] * gr[j][0] + Gm[1][1] * gr[j][1]));
+          }
+        ++n;
+        return;
+      }
       for (int i = 0; i < nb; ++i)
         for (int j = 0; j < nb; ++j) {
           Me[i * nb + j] = vol * Mref[i * nb + j];

@@ -50,6 +50,8 @@ void free_tables(elm_mesh_s* me) {
   cudaFree(const_cast<double*>(me->blend.sec));
   me->blend.sec = nullptr;
   cudaFree(me->d_dtab);
+  cudaFree(me->d_dtab_el);
+  me->d_dtab_el = nullptr;
   cudaFree(me->d_dbnd);
   cudaFree(me->d_dcells);
   cudaFree(me->d_dvec);
@@ -385,8 +387,7 @@ elm_status elm_mesh_set_annulus(elm_mesh me, double r_min, double r_max, int n_s
   if (!me) return fail(ELM_ERR_ARG, "elm_mesh_set_annulus: null mesh");
   if (me->dim != 2 || me->precision != ELM_FP64)
     return fail(ELM_ERR_ARG, "elm_mesh_set_annulus: blending is built for 2D FP64 meshes");
-  if (me->with_adjoint || me->with_diffusion)
-    return fail(ELM_ERR_ARG, "elm_mesh_set_annulus: not combinable with ELM_ADJOINT or ELM_DIFFUSION");
+  if (me->with_adjoint) return fail(ELM_ERR_ARG, "elm_mesh_set_annulus: not combinable with ELM_ADJOINT");
   if (me->blend.nsec > 0) return fail(ELM_ERR_STATE, "elm_mesh_set_annulus: the mesh is blended already");
   if (n_sectors < 3 || n_sectors > 4096 || !std::isfinite(theta0) || !(r_min > 0.0) || !(r_max > r_min) ||
       !std::isfinite(r_max))
@@ -444,6 +445,12 @@ elm_status elm_mesh_set_annulus(elm_mesh me, double r_min, double r_max, int n_s
   me->blend.delta = delta;
   me->blend.rmin = r_min;
   me->blend.rmax = r_max;
+  if (me->with_diffusion && !me->host_only) {
+    DeviceGuard g(me->device);
+    std::string err;
+    const elm_status st = elm::build_diffusion_blended(me, &err);
+    if (st != ELM_OK) return fail(st, "elm_mesh_set_annulus: " + err);
+  }
   return ELM_OK;
 }
 

@@ -232,15 +232,119 @@ void element_tables(int d, int p, int N, const MacroGeo& g, double* Mout, double
   }
 }
 
+// Element tables of a mesh blended onto an annulus (2D; elm_mesh_set_annulus):
+// one mass and one stiffness matrix per micro simplex, [n_macros][T2(N)
+// cells][2 orientations][2][nb * nb], zero for simplices outside the macro.
+// With the polar sector map the Jacobian determinant is the constant
+// Delta / sin(Delta), so the mass is the affine one times it; the stiffness is
+// int grad_x phi_i^T G grad_x phi_j with the metric
+//   G = DPhi^{-1} DPhi^{-T} |det DPhi| = (Delta / sin Delta) (w w^T / Delta^2 + p p^T),
+// w = e_{k+1} - e_k, p = (1 - lam) e_k + lam e_{k+1}, lam the sector parameter
+// of the point, integrated with a 5 x 5 collapsed Gauss-Legendre rule.
+void blended_element_tables(const elm_mesh_s* me, std::vector<double>& out) {
+  const int d = 2, p = me->order, nb = n_local(d, p), N = me->N, D1 = 3;
+  const int64_t ncell = int64_t(N) * (N + 1) / 2;
+  out.assign(size_t(me->n_macros) * ncell * 2 * 2 * nb * nb, 0.0);
+  const auto B = basis_terms(d, p);
+  std::vector<double> Mref(nb * nb);
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) {
+      double s = 0.0;
+      for (const Term& ti : B[i])
+        for (const Term& tj : B[j]) {
+          int e[4];
+          for (int k = 0; k < 4; ++k) e[k] = ti.e[k] + tj.e[k];
+          s += ti.c * tj.c * monomial_unit(d, e);
+        }
+      Mref[i * nb + j] = s;
+    }
+  std::vector<double> da, db;
+  basis_derivatives(d, p, da, db);
+  const double delta = me->blend.delta, jac = delta / std::sin(delta);
+  // 5-point Gauss-Legendre on [-1, 1]
+  const double gx[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831, 0.9061798459386640};
+  const double gw[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889, 0.4786286704993665,
+                        0.2369268850561891};
+  for (int64_t m = 0; m < me->n_macros; ++m) {
+    const MacroGeo& g = me->geo[m];
+    // the macro's sector: from its centroid (every macro spans one sector)
+    double cx = g.v0[0] + (2.0 * g.J[0] + g.J[1]) / 3.0, cy = g.v0[1] + (2.0 * g.J[3] + g.J[4]) / 3.0;
+    const double tt = (std::atan2(cy, cx) - me->blend.theta0) / delta;
+    int k = int(std::floor(tt)) % me->blend.nsec;
+    if (k < 0) k += me->blend.nsec;
+    const double tk = me->blend.theta0 + k * delta;
+    const double ek[2] = {std::cos(tk), std::sin(tk)}, ek1[2] = {std::cos(tk + delta), std::sin(tk + delta)};
+    const double w[2] = {ek1[0] - ek[0], ek1[1] - ek[1]};
+    for (int c0 = 0; c0 < N; ++c0)
+      for (int c1 = 0; c1 <= c0; ++c1)
+        for (int sg = 0; sg < 2; ++sg) {
+          int s[2];
+          perm_of(2, sg, s);
+          const int c[2] = {c0, c1};
+          if (c[s[0]] == c[s[1]] && s[0] > s[1]) continue;  // outside the macro
+          double V[3][2];
+          int wl[2] = {c0, c1};
+          for (int v = 0; v <= 2; ++v) {
+            if (v > 0) wl[s[v - 1]] += 1;
+            for (int r = 0; r < 2; ++r)
+              V[v][r] = g.v0[r] + g.J[r * 3 + 0] * (double(wl[0]) / N) + g.J[r * 3 + 1] * (double(wl[1]) / N);
+          }
+          const double E00 = V[1][0] - V[0][0], E01 = V[2][0] - V[0][0], E10 = V[1][1] - V[0][1],
+                       E11 = V[2][1] - V[0][1];
+          const double det = E00 * E11 - E01 * E10, area = 0.5 * std::fabs(det);
+          // barycentric gradients: rows of E^{-1} for lam_1, lam_2
+          double G[3][2];
+          G[1][0] = E11 / det;
+          G[1][1] = -E01 / det;
+          G[2][0] = -E10 / det;
+          G[2][1] = E00 / det;
+          G[0][0] = -G[1][0] - G[2][0];
+          G[0][1] = -G[1][1] - G[2][1];
+          double* Me = out.data() + ((size_t(m) * ncell + size_t(c0) * (c0 + 1) / 2 + c1) * 2 + sg) * 2 * nb * nb;
+          double* Ae = Me + nb * nb;
+          for (int i = 0; i < nb * nb; ++i) Me[i] = area * Mref[i] * jac;
+          for (int a = 0; a < 5; ++a)
+            for (int b = 0; b < 5; ++b) {
+              const double u = 0.5 * (gx[a] + 1.0), v = 0.5 * (gx[b] + 1.0);
+              const double lam[3] = {1.0 - u, u * (1.0 - v), u * v};
+              const double W = 0.25 * gw[a] * gw[b] * u * 2.0 * area;
+              const double x = lam[0] * V[0][0] + lam[1] * V[1][0] + lam[2] * V[2][0];
+              const double y = lam[0] * V[0][1] + lam[1] * V[1][1] + lam[2] * V[2][1];
+              const double ck = ek[0] * y - ek[1] * x, ck1 = ek1[0] * y - ek1[1] * x;
+              const double sl = ck / (ck - ck1);
+              const double pp[2] = {(1.0 - sl) * ek[0] + sl * ek1[0], (1.0 - sl) * ek[1] + sl * ek1[1]};
+              double Gm[2][2];
+              for (int r = 0; r < 2; ++r)
+                for (int q = 0; q < 2; ++q) Gm[r][q] = jac * (w[r] * w[q] / (delta * delta) + pp[r] * pp[q]);
+              double gr[6][2];
+              for (int i = 0; i < nb; ++i) {
+                gr[i][0] = gr[i][1] = 0.0;
+                for (int kk = 0; kk < D1; ++kk) {
+                  double dk = da[i * D1 + kk];
+                  for (int mm = 0; mm < D1; ++mm) dk += db[(i * D1 + kk) * D1 + mm] * lam[mm];
+                  gr[i][0] += dk * G[kk][0];
+                  gr[i][1] += dk * G[kk][1];
+                }
+              }
+              for (int i = 0; i < nb; ++i)
+                for (int j = 0; j < nb; ++j)
+                  Ae[i * nb + j] += W * (gr[i][0] * (Gm[0][0] * gr[j][0] + Gm[0][1] * gr[j][1]) +
+                                         gr[i][1] * (Gm[1][0] * gr[j][0] + Gm[1][1] * gr[j][1]));
+            }
+        }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Device: the operator y += scale (M + alpha A) x over all micro simplices.
 // ---------------------------------------------------------------------------
 
 struct OpArgs {
-  const void* tables;       // per macro: M [nb*nb], then A [n_perm][nb*nb], mesh precision
+  const void* tables;       // per macro: M [nb*nb], then A [n_perm][nb*nb]; blended: per simplex
   const int4* cells;        // work list: (macro, c0, first index in slab c0, count)
   const int64_t* unique_map;
   int npm;                  // storage nodes per macro
+  int N;                    // 2^L
 };
 
 __device__ __forceinline__ int tri2d(int k) { return k * (k + 1) / 2; }
@@ -254,21 +358,25 @@ __device__ __forceinline__ int row_of(int i) {
   return r;
 }
 
-// DIAG: add only the diagonal of scale (M + alpha A) (x unused).
-template <int D, class R, int P, bool DIAG>
+// DIAG: add only the diagonal of scale (M + alpha A) (x unused).  BL: the
+// mesh is blended (2D) and every micro simplex has its own tables
+// (blended_element_tables) instead of one per orientation and macro.
+template <int D, class R, int P, bool DIAG, bool BL = false>
 __global__ void __launch_bounds__(kDiffThreads) k_apply(OpArgs a, const R* __restrict__ x, R* __restrict__ y,
                                                         R alpha, R scale) {
   constexpr int NB = n_local(D, P);
   constexpr int NP = n_perm(D);
   constexpr int TAB = NB * NB * (1 + NP);
-  __shared__ R E[NP][NB * NB];  // M + alpha A_sigma of the block's macro
+  __shared__ R E[BL ? 1 : NP][NB * NB];  // M + alpha A_sigma of the block's macro
   const int4 ck = a.cells[blockIdx.x];
-  const R* tab = static_cast<const R*>(a.tables) + size_t(ck.x) * TAB;
-  for (int t = threadIdx.x; t < NP * NB * NB; t += blockDim.x) {
-    const int sg = t / (NB * NB), e = t - sg * NB * NB;
-    E[sg][e] = scale * (tab[e] + alpha * tab[NB * NB * (1 + sg) + e]);
+  if constexpr (!BL) {
+    const R* tab = static_cast<const R*>(a.tables) + size_t(ck.x) * TAB;
+    for (int t = threadIdx.x; t < NP * NB * NB; t += blockDim.x) {
+      const int sg = t / (NB * NB), e = t - sg * NB * NB;
+      E[sg][e] = scale * (tab[e] + alpha * tab[NB * NB * (1 + sg) + e]);
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (int(threadIdx.x) >= ck.w) return;
   // the cell c of this thread (c0 = slab, then row and position)
   int c[3];
@@ -326,6 +434,24 @@ __global__ void __launch_bounds__(kDiffThreads) k_apply(OpArgs a, const R* __res
       const int64_t slot = base + (D == 3 ? tri3d(q[0]) + tri2d(q[1]) + q[2] : tri2d(q[0]) + q[1]);
       uid[j] = a.unique_map[slot];
       xl[j] = DIAG ? R(0) : x[uid[j]];
+    }
+    if constexpr (BL) {
+      // the simplex's own tables: [M | A] after the cells before it
+      const int64_t ncell = int64_t(a.N) * (a.N + 1) / 2;
+      const R* te = static_cast<const R*>(a.tables) +
+                    ((int64_t(ck.x) * ncell + tri2d(c[0]) + c[1]) * NP + sg) * 2 * NB * NB;
+#pragma unroll
+      for (int ii = 0; ii < NB; ++ii) {
+        R v = R(0);
+        if (DIAG) {
+          v = scale * (te[ii * NB + ii] + alpha * te[NB * NB + ii * NB + ii]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < NB; ++j) v += scale * (te[ii * NB + j] + alpha * te[NB * NB + ii * NB + j]) * xl[j];
+        }
+        atomicAdd(y + uid[ii], v);
+      }
+      continue;
     }
 #pragma unroll
     for (int ii = 0; ii < NB; ++ii) {
@@ -578,14 +704,41 @@ elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
   return ELM_OK;
 }
 
+elm_status build_diffusion_blended(elm_mesh_s* me, std::string* err) {
+  std::vector<double> t;
+  blended_element_tables(me, t);
+  cudaFree(me->d_dtab_el);
+  me->d_dtab_el = nullptr;
+  if (cudaMalloc(&me->d_dtab_el, t.size() * sizeof(double)) != cudaSuccess ||
+      cudaMemcpy(me->d_dtab_el, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    *err = std::string("blended diffusion tables: ") + cudaGetErrorString(cudaGetLastError());
+    return ELM_ERR_CUDA;
+  }
+  return ELM_OK;
+}
+
 namespace {
 
 template <class R>
 cudaError_t apply_op(const elm_mesh_s* me, const R* x, R* y, double alpha, double scale, bool diag, cudaStream_t s) {
-  OpArgs a{me->d_dtab, me->d_dcells, me->d_unique_map, int(me->npm)};
+  const bool blended = me->blend.nsec > 0;
+  OpArgs a{blended ? me->d_dtab_el : me->d_dtab, me->d_dcells, me->d_unique_map, int(me->npm), me->N};
   const unsigned g = unsigned(me->n_cell_chunks);
   if (g == 0) return cudaSuccess;
   const R al = R(alpha), sc = R(scale);
+  if constexpr (sizeof(R) == 8) {
+    if (blended) {  // 2D FP64 only (elm_mesh_set_annulus)
+      if (me->order == 2) {
+        if (diag) k_apply<2, R, 2, true, true><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);
+        else k_apply<2, R, 2, false, true><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);
+      } else {
+        if (diag) k_apply<2, R, 1, true, true><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);
+        else k_apply<2, R, 1, false, true><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);
+      }
+      return cudaGetLastError();
+    }
+  }
+  if (blended) return cudaErrorInvalidValue;
 #define ELM_APPLY(DD, PP)                                                              \
   if (diag) k_apply<DD, R, PP, true><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);     \
   else k_apply<DD, R, PP, false><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);

@@ -143,6 +143,7 @@ struct elm_mesh_s {
   // and CG vectors in the unique layout, reduction space
   bool with_diffusion = false;
   void* d_dtab = nullptr;
+  void* d_dtab_el = nullptr;         // blended meshes: per-simplex mass and stiffness
   uint8_t* d_dbnd = nullptr;
   int4* d_dcells = nullptr;
   int64_t n_cell_chunks = 0;
@@ -160,8 +161,10 @@ void set_last_error(const std::string& msg);
 // Vectors of the diffusion solver (x, r, z, p, q, b, inverse diagonal).
 constexpr int kDiffVectors = 7;
 
-// Diffusion solver set-up at mesh creation (diffusion.cu).
+// Diffusion solver set-up at mesh creation (diffusion.cu), and the per-simplex
+// tables of a blended mesh (at elm_mesh_set_annulus).
 elm_status build_diffusion(elm_mesh_s* me, std::string* err);
+elm_status build_diffusion_blended(elm_mesh_s* me, std::string* err);
 
 // Host mesh construction (mesh.cpp).
 elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const int64_t* mv,
