@@ -266,6 +266,10 @@ elm_status elm_trace_eval(elm_mesh mesh, const void* D_dev, const void* T_src_de
  *             node receives the node's value.
  *  iterations, residual  optional host outputs: CG iterations and the final
  *             relative residual.
+ * FP64 meshes (affine macros) solve by defect correction: the residual in
+ * FP64, the corrections by the same PCG in FP32 (to 3e-5 of their start), so
+ * `iterations` counts the FP32 iterations; blended FP64 meshes and FP32 meshes
+ * run the PCG in their own precision.
  * The operator is matrix-free; its element sums use atomics, so the last bits
  * can differ between runs.  Requires ELM_DIFFUSION at creation.  Unlike the
  * other calls this one synchronises `stream` (the convergence test reads the

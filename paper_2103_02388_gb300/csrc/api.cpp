@@ -51,7 +51,9 @@ void free_tables(elm_mesh_s* me) {
   me->blend.sec = nullptr;
   cudaFree(me->d_dtab);
   cudaFree(me->d_dtab_el);
-  me->d_dtab_el = nullptr;
+  cudaFree(me->d_dtab32);
+  cudaFree(me->d_dvec32);
+  me->d_dtab_el = me->d_dtab32 = me->d_dvec32 = nullptr;
   cudaFree(me->d_dbnd);
   cudaFree(me->d_dcells);
   cudaFree(me->d_dvec);

@@ -451,18 +451,18 @@ __global__ void __launch_bounds__(kDiffThreads) k_apply(OpArgs a, const R* __res
         }
         atomicAdd(y + uid[ii], v);
       }
-      continue;
-    }
+    } else {
 #pragma unroll
-    for (int ii = 0; ii < NB; ++ii) {
-      R v = R(0);
-      if (DIAG) {
-        v = E[sg][ii * NB + ii];
-      } else {
+      for (int ii = 0; ii < NB; ++ii) {
+        R v = R(0);
+        if (DIAG) {
+          v = E[sg][ii * NB + ii];
+        } else {
 #pragma unroll
-        for (int j = 0; j < NB; ++j) v += E[sg][ii * NB + j] * xl[j];
+          for (int j = 0; j < NB; ++j) v += E[sg][ii * NB + j] * xl[j];
+        }
+        atomicAdd(y + uid[ii], v);
       }
-      atomicAdd(y + uid[ii], v);
     }
   }
 }
@@ -621,6 +621,21 @@ __global__ void k_set_boundary(R* x, const R* v, const uint8_t* bnd, int64_t n) 
   if (i < n && bnd[i]) x[i] = v[i];
 }
 
+// r32 = float(r) on the interior, 0 on the boundary; d32 = 0.
+__global__ void k_residual_to_float(const double* r, float* r32, float* d32, const uint8_t* bnd, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) {
+    r32[i] = bnd[i] ? 0.0f : float(r[i]);
+    d32[i] = 0.0f;
+  }
+}
+
+// x += double(d32) (the correction of one inner solve)
+__global__ void k_add_correction(double* x, const float* d32, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) x[i] += double(d32[i]);
+}
+
 template <class R>
 __global__ void k_copy(R* dst, const R* src, int64_t n) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -694,7 +709,14 @@ elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
        cudaMemcpy(me->d_dcells, cells.data(), sizeof(int4) * cells.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMalloc(&me->d_dvec, size_t(kDiffVectors) * me->n_unique * es) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&me->d_dpart, sizeof(double) * 2 * kRedBlocks) == cudaSuccess;
-  ok = ok && cudaMalloc((void**)&me->d_dscal, sizeof(Scalars) + sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&me->d_dscal, sizeof(Scalars) + 2 * sizeof(double)) == cudaSuccess;
+  if (me->precision == ELM_FP64) {
+    // FP32 copies for the inner solves of the mixed-precision form
+    std::vector<float> t32(t64.begin(), t64.end());
+    ok = ok && cudaMalloc(&me->d_dtab32, tab * me->n_macros * 4) == cudaSuccess &&
+         cudaMemcpy(me->d_dtab32, t32.data(), tab * me->n_macros * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMalloc(&me->d_dvec32, size_t(kDiffVectors32) * me->n_unique * 4) == cudaSuccess;
+  }
   if (!ok) {
     *err = std::string("diffusion tables: ") + cudaGetErrorString(cudaGetLastError());
     return ELM_ERR_CUDA;
@@ -719,10 +741,13 @@ elm_status build_diffusion_blended(elm_mesh_s* me, std::string* err) {
 
 namespace {
 
+// tables: the element tables in the precision R (null: the mesh's own).
 template <class R>
-cudaError_t apply_op(const elm_mesh_s* me, const R* x, R* y, double alpha, double scale, bool diag, cudaStream_t s) {
+cudaError_t apply_op(const elm_mesh_s* me, const R* x, R* y, double alpha, double scale, bool diag, cudaStream_t s,
+                     const void* tables = nullptr) {
   const bool blended = me->blend.nsec > 0;
-  OpArgs a{blended ? me->d_dtab_el : me->d_dtab, me->d_dcells, me->d_unique_map, int(me->npm), me->N};
+  OpArgs a{tables ? tables : (blended ? me->d_dtab_el : me->d_dtab), me->d_dcells, me->d_unique_map, int(me->npm),
+           me->N};
   const unsigned g = unsigned(me->n_cell_chunks);
   if (g == 0) return cudaSuccess;
   const R al = R(alpha), sc = R(scale);
@@ -749,6 +774,147 @@ cudaError_t apply_op(const elm_mesh_s* me, const R* x, R* y, double alpha, doubl
   }
 #undef ELM_APPLY
   return cudaGetLastError();
+}
+
+// PCG iterations on the interior from the state of k_cg_start (r, z = D^{-1} r,
+// p = z, sc->rz / rr): stops when |r|^2 <= stop_rr or after `budget`
+// iterations.  *done = iterations run, *rr = final |r|^2.  Returns false on a
+// CUDA error (message in *err).
+template <class R>
+bool pcg_iterate(const elm_mesh_s* me, const void* tab, R* x, R* r, R* z, R* p, R* qv, const R* dinv, double alpha,
+                 double stop_rr, int budget, int* done, double* rr, cudaStream_t s, std::string* err) {
+  const int64_t n = me->n_unique;
+  double* part = me->d_dpart;
+  Scalars* sc = reinterpret_cast<Scalars*>(me->d_dscal);
+  const int nred = kRedBlocks;
+  auto chk = [&](cudaError_t e, const char* where) {
+    if (e != cudaSuccess) *err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaSuccess;
+  };
+  auto read_rr = [&]() -> bool {
+    Scalars h;
+    if (!chk(cudaMemcpyAsync(&h, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s), "read") ||
+        !chk(cudaStreamSynchronize(s), "sync"))
+      return false;
+    *rr = h.rr;
+    return true;
+  };
+  *done = 0;
+  if (!read_rr()) return false;
+  while (*rr > stop_rr && *done < budget && std::isfinite(*rr)) {
+    if (!chk(cudaMemsetAsync(qv, 0, size_t(n) * sizeof(R), s), "memset")) return false;
+    if (!chk(apply_op<R>(me, p, qv, alpha, 1.0, false, s, tab), "apply")) return false;
+    k_cg_pq<R><<<nred, kRedThreads, 0, s>>>(p, qv, me->d_dbnd, n, part);
+    k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 1, sc);
+    k_cg_update<R><<<nred, kRedThreads, 0, s>>>(x, r, z, p, qv, dinv, sc, n, part);
+    k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 2, sc);
+    k_cg_direction<R><<<nred, kRedThreads, 0, s>>>(p, z, sc, n);
+    ++*done;
+    if (!read_rr()) return false;
+  }
+  return true;
+}
+
+// FP64 meshes (affine macros): defect correction with FP32 inner solves.  The
+// residual r = b - E x is formed in FP64; E d = r is solved by the same PCG
+// in FP32 (to a relative residual of kInnerRtol) and x += d.  Each correction
+// gains about four digits, so a solve to 1e-11 takes three FP64 operator
+// applications instead of one per iteration: the FP64 element products run on
+// this part's narrow FP64 pipe, the FP32 ones on its FP32 pipe.
+constexpr double kInnerRtol = 3e-5;
+
+elm_status solve_mixed(elm_mesh_s* me, const void* c_hat, const void* c_bnd, const void* q, void* c_new,
+                       double tau, double kappa, double theta, double rtol, int max_iter, int* iters, double* resid,
+                       cudaStream_t s, std::string* err) {
+  const int64_t n = me->n_unique;
+  double* v = static_cast<double*>(me->d_dvec);
+  double* x = v;
+  double* r = v + n;
+  double* tmp = v + 2 * n;
+  double* b = v + 5 * n;
+  float* w = static_cast<float*>(me->d_dvec32);
+  float* r32 = w;
+  float* z32 = w + n;
+  float* p32 = w + 2 * n;
+  float* q32 = w + 3 * n;
+  float* d32 = w + 4 * n;
+  float* dinv32 = w + 5 * n;
+  double* part = me->d_dpart;
+  Scalars* sc = reinterpret_cast<Scalars*>(me->d_dscal);
+  double* bnorm = me->d_dscal + sizeof(Scalars) / sizeof(double);
+  double* rnorm = bnorm + 1;
+  const size_t bytes = size_t(n) * sizeof(double);
+  const unsigned eb = unsigned((n + 255) / 256);
+  const int nred = kRedBlocks;
+  auto chk = [&](cudaError_t e, const char* where) {
+    if (e != cudaSuccess) *err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaSuccess;
+  };
+  if (!chk(launch_gather(ELM_FP64, c_hat, x, me->d_owner, n, 1, s), "gather c_hat")) return ELM_ERR_CUDA;
+  if (!chk(cudaMemsetAsync(b, 0, bytes, s), "memset")) return ELM_ERR_CUDA;
+  if (!chk(apply_op<double>(me, x, b, -tau * (1.0 - theta) * kappa, 1.0, false, s), "rhs")) return ELM_ERR_CUDA;
+  if (q) {
+    if (!chk(launch_gather(ELM_FP64, q, tmp, me->d_owner, n, 1, s), "gather q")) return ELM_ERR_CUDA;
+    if (!chk(apply_op<double>(me, tmp, b, 0.0, tau, false, s), "source")) return ELM_ERR_CUDA;
+  }
+  if (c_bnd) {
+    if (!chk(launch_gather(ELM_FP64, c_bnd, tmp, me->d_owner, n, 1, s), "gather c_bnd")) return ELM_ERR_CUDA;
+    k_set_boundary<double><<<eb, 256, 0, s>>>(x, tmp, me->d_dbnd, n);
+  }
+  const double alpha = tau * theta * kappa;
+  if (!chk(cudaMemsetAsync(dinv32, 0, size_t(n) * 4, s), "memset")) return ELM_ERR_CUDA;
+  if (!chk(apply_op<float>(me, nullptr, dinv32, alpha, 1.0, true, s, me->d_dtab32), "diagonal")) return ELM_ERR_CUDA;
+  k_invert_diag<float><<<eb, 256, 0, s>>>(dinv32, me->d_dbnd, n);
+  k_norm2<double><<<nred, kRedThreads, 0, s>>>(b, me->d_dbnd, n, part);
+  k_sum_into<<<1, kRedThreads, 0, s>>>(part, nred, bnorm);
+  double hb = 0.0;
+  if (!chk(cudaMemcpyAsync(&hb, bnorm, sizeof(double), cudaMemcpyDeviceToHost, s), "read") ||
+      !chk(cudaStreamSynchronize(s), "sync"))
+    return ELM_ERR_CUDA;
+  const double bn = std::sqrt(hb);
+  const bool interior = me->n_unique > me->n_boundary;
+  int total = 0;
+  double rel = 0.0;
+  for (int outer = 0;; ++outer) {
+    // r = b - E x (FP64), interior only
+    k_copy<double><<<eb, 256, 0, s>>>(r, b, n);
+    if (!chk(apply_op<double>(me, x, r, alpha, -1.0, false, s), "residual")) return ELM_ERR_CUDA;
+    k_norm2<double><<<nred, kRedThreads, 0, s>>>(r, me->d_dbnd, n, part);
+    k_sum_into<<<1, kRedThreads, 0, s>>>(part, nred, rnorm);
+    double hr = 0.0;
+    if (!chk(cudaMemcpyAsync(&hr, rnorm, sizeof(double), cudaMemcpyDeviceToHost, s), "read") ||
+        !chk(cudaStreamSynchronize(s), "sync"))
+      return ELM_ERR_CUDA;
+    rel = bn > 0.0 ? std::sqrt(hr) / bn : std::sqrt(hr);
+    if (!interior || !(rel > rtol) || total >= max_iter || !std::isfinite(rel)) break;
+    // inner FP32 solve of E d = r from d = 0
+    k_residual_to_float<<<eb, 256, 0, s>>>(r, r32, d32, me->d_dbnd, n);
+    k_cg_start<float><<<nred, kRedThreads, 0, s>>>(r32, z32, p32, dinv32, me->d_dbnd, n, part);
+    k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 0, sc);
+    int done = 0;
+    double rr32 = 0.0;
+    // stop at kInnerRtol of the inner start, or where the outer tolerance is met
+    const double start_rr = hr;
+    const double stop = std::max(kInnerRtol * kInnerRtol * start_rr, 0.25 * rtol * rtol * bn * bn);
+    if (!pcg_iterate<float>(me, me->d_dtab32, d32, r32, z32, p32, q32, dinv32, alpha, stop, max_iter - total,
+                            &done, &rr32, s, err))
+      return ELM_ERR_CUDA;
+    total += done;
+    k_add_correction<<<eb, 256, 0, s>>>(x, d32, n);
+    if (outer > 64) break;  // safeguard: corrections stopped converging
+  }
+  if (iters) *iters = total;
+  if (resid) *resid = rel;
+  if (!chk(launch_gather(ELM_FP64, x, c_new, me->d_unique_map, me->n_storage, 1, s), "scatter")) return ELM_ERR_CUDA;
+  if (!std::isfinite(rel)) {
+    *err = "non-finite residual";
+    return ELM_ERR_NONFINITE;
+  }
+  if (rel > rtol && interior) {
+    *err = "CG did not reach the tolerance within max_iter iterations (relative residual " + std::to_string(rel) + ")";
+    return ELM_ERR_NOT_CONVERGED;
+  }
+  return ELM_OK;
 }
 
 template <class R>
@@ -799,34 +965,18 @@ elm_status solve(elm_mesh_s* me, const void* c_hat, const void* c_bnd, const voi
   if (!chk(apply_op<R>(me, x, r, alpha, -1.0, false, s), "residual")) return ELM_ERR_CUDA;
   k_cg_start<R><<<nred, kRedThreads, 0, s>>>(r, z, p, dinv, me->d_dbnd, n, part);
   k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 0, sc);
-  double host[2] = {0.0, 0.0};
-  auto read_norms = [&]() -> bool {
-    Scalars h;
-    if (!chk(cudaMemcpyAsync(&h, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s), "read") ||
-        !chk(cudaMemcpyAsync(&host[1], bnorm, sizeof(double), cudaMemcpyDeviceToHost, s), "read") ||
-        !chk(cudaStreamSynchronize(s), "sync"))
-      return false;
-    host[0] = h.rr;
-    return true;
-  };
-  if (!read_norms()) return ELM_ERR_CUDA;
-  const double bn = std::sqrt(host[1]);
-  double rel = bn > 0.0 ? std::sqrt(host[0]) / bn : std::sqrt(host[0]);
-  int it = 0;
+  double hb = 0.0;
+  if (!chk(cudaMemcpyAsync(&hb, bnorm, sizeof(double), cudaMemcpyDeviceToHost, s), "read") ||
+      !chk(cudaStreamSynchronize(s), "sync"))
+    return ELM_ERR_CUDA;
+  const double bn = std::sqrt(hb);
   const bool interior = me->n_unique > me->n_boundary;
-  while (interior && rel > rtol && it < max_iter) {
-    if (!chk(cudaMemsetAsync(qv, 0, bytes, s), "memset")) return ELM_ERR_CUDA;
-    if (!chk(apply_op<R>(me, p, qv, alpha, 1.0, false, s), "apply")) return ELM_ERR_CUDA;
-    k_cg_pq<R><<<nred, kRedThreads, 0, s>>>(p, qv, me->d_dbnd, n, part);
-    k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 1, sc);
-    k_cg_update<R><<<nred, kRedThreads, 0, s>>>(x, r, z, p, qv, dinv, sc, n, part);
-    k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 2, sc);
-    k_cg_direction<R><<<nred, kRedThreads, 0, s>>>(p, z, sc, n);
-    ++it;
-    if (!read_norms()) return ELM_ERR_CUDA;
-    rel = bn > 0.0 ? std::sqrt(host[0]) / bn : std::sqrt(host[0]);
-    if (!std::isfinite(rel)) break;
-  }
+  int it = 0;
+  double rr = 0.0;
+  const double stop = bn > 0.0 ? rtol * rtol * bn * bn : rtol * rtol;
+  if (!pcg_iterate<R>(me, nullptr, x, r, z, p, qv, dinv, alpha, stop, interior ? max_iter : 0, &it, &rr, s, err))
+    return ELM_ERR_CUDA;
+  const double rel = bn > 0.0 ? std::sqrt(rr) / bn : std::sqrt(rr);
   if (iters) *iters = it;
   if (resid) *resid = rel;
   if (!chk(launch_gather(prec, x, c_new, me->d_unique_map, me->n_storage, 1, s), "scatter")) return ELM_ERR_CUDA;
@@ -875,8 +1025,11 @@ extern "C" elm_status elm_diffusion_step(elm_mesh me, const void* c_hat_dev, con
   std::string err;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   elm_status st = me->precision == ELM_FP64
-                      ? elm::solve<double>(me, c_hat_dev, c_bnd_dev, q_dev, c_new_dev, tau, kappa, theta, rtol,
-                                           max_iter, iterations, residual, s, &err)
+                      ? (me->blend.nsec > 0
+                             ? elm::solve<double>(me, c_hat_dev, c_bnd_dev, q_dev, c_new_dev, tau, kappa, theta, rtol,
+                                                  max_iter, iterations, residual, s, &err)
+                             : elm::solve_mixed(me, c_hat_dev, c_bnd_dev, q_dev, c_new_dev, tau, kappa, theta, rtol,
+                                                max_iter, iterations, residual, s, &err))
                       : elm::solve<float>(me, c_hat_dev, c_bnd_dev, q_dev, c_new_dev, tau, kappa, theta, rtol,
                                           max_iter, iterations, residual, s, &err);
   if (prev >= 0 && prev != me->device) cudaSetDevice(prev);

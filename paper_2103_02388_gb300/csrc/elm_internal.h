@@ -144,6 +144,8 @@ struct elm_mesh_s {
   bool with_diffusion = false;
   void* d_dtab = nullptr;
   void* d_dtab_el = nullptr;         // blended meshes: per-simplex mass and stiffness
+  void* d_dtab32 = nullptr;          // FP64 meshes: FP32 copy of the tables (inner solves)
+  void* d_dvec32 = nullptr;          // FP64 meshes: FP32 vectors of the inner solves
   uint8_t* d_dbnd = nullptr;
   int4* d_dcells = nullptr;
   int64_t n_cell_chunks = 0;
@@ -158,8 +160,11 @@ namespace elm {
 // Sets the thread-local message returned by elm_last_error (api.cpp).
 void set_last_error(const std::string& msg);
 
-// Vectors of the diffusion solver (x, r, z, p, q, b, inverse diagonal).
+// Vectors of the diffusion solver (x, r, z, p, q, b, inverse diagonal), and
+// the FP32 vectors of the inner solves on FP64 meshes (r, z, p, q, d, inverse
+// diagonal).
 constexpr int kDiffVectors = 7;
+constexpr int kDiffVectors32 = 6;
 
 // Diffusion solver set-up at mesh creation (diffusion.cu), and the per-simplex
 // tables of a blended mesh (at elm_mesh_set_annulus).

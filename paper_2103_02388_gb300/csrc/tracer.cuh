@@ -577,25 +577,26 @@ struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
         outside = lmin < R(-kTol64);
         nb = outside ? tab.nb(m, kmin) : -1;
       }
-      if (outside && nb < 0) {
-        // The most negative face is a boundary face.  On a non-convex mesh
-        // (an annulus) the point can still lie in the mesh behind another
-        // negative face: walk across the most negative face that has a
-        // neighbour, if any.
-        R best = -kBand;
+      if constexpr (BLEND == 1) {
+        if (outside && nb < 0) {
+          // The most negative face is a boundary face.  On the non-convex
+          // annulus the point can still lie in the mesh behind another
+          // negative face: walk across the most negative face that has a
+          // neighbour, if any.  (Box domains are convex: a clamped point is
+          // never outside through a boundary face beyond the band.)
+          R best = -kBand;
 #pragma unroll
-        for (int k = 0; k <= D; ++k) {
-          if (l[k] < best) {
-            const int n2 = tab.nb(m, k);
-            if (n2 >= 0) {
-              best = l[k];
-              kmin = k;
-              nb = n2;
+          for (int k = 0; k <= D; ++k) {
+            if (l[k] < best) {
+              const int n2 = tab.nb(m, k);
+              if (n2 >= 0) {
+                best = l[k];
+                kmin = k;
+                nb = n2;
+              }
             }
           }
         }
-      }
-      if constexpr (BLEND == 1) {
         if (outside && nb < 0 && nmac > 0 && !searched) {
           // still outside only through boundary faces of a non-convex mesh:
           // search every macro once
