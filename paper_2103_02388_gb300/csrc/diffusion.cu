@@ -38,7 +38,13 @@ namespace {
 
 constexpr int kDiffThreads = 128;
 constexpr int kRedThreads = 256;
-constexpr int kRedBlocks = 608;  // 4 per SM of the 152-SM part: the partials of one reduction
+// Grid of the vector kernels and reductions: about 4 values per thread, at
+// most kRedMaxBlocks blocks (the partials of one reduction).
+constexpr int kRedMaxBlocks = 8192;
+inline int red_blocks(int64_t n) {
+  const int64_t b = (n + 4 * kRedThreads - 1) / (4 * kRedThreads);
+  return int(b < 1 ? 1 : (b > kRedMaxBlocks ? kRedMaxBlocks : b));
+}
 
 __host__ __device__ constexpr int n_local(int d, int p) { return p == 2 ? (d + 1) * (d + 2) / 2 : d + 1; }
 __host__ __device__ constexpr int n_perm(int d) { return d == 3 ? 6 : 2; }
@@ -476,34 +482,41 @@ struct Scalars {
   double rz, rz_new, pq, rr, bb, alpha, beta, pad;
 };
 
+// Sum over the block (fixed shuffle tree, so deterministic); valid in thread
+// 0.  sh holds one value per warp; callers separate two sums by a barrier.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
-  sh[threadIdx.x] = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (int(threadIdx.x) < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
+  if (threadIdx.x < 32) {
+    v = int(threadIdx.x) < int(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   }
-  return sh[0];
+  return v;
 }
 
-// r := r with zero boundary; z = dinv r; p = z; partials (r.z, r.r).
+// r := r with zero boundary; z = dinv r; p = z; q = 0; partials (r.z, r.r).
 template <class R>
-__global__ void __launch_bounds__(kRedThreads) k_cg_start(R* r, R* z, R* p, const R* dinv, const uint8_t* bnd,
+__global__ void __launch_bounds__(kRedThreads) k_cg_start(R* r, R* z, R* p, R* q, const R* dinv, const uint8_t* bnd,
                                                           int64_t n, double* part) {
-  __shared__ double sh[kRedThreads];
-  double rz = 0.0, rr = 0.0;
+  __shared__ double sh[kRedThreads / 32];
+  // per-thread partials in the working precision (a few terms each), summed in FP64
+  R rz = R(0), rr = R(0);
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     R ri = bnd[i] ? R(0) : r[i];
     r[i] = ri;
     const R zi = dinv[i] * ri;
     z[i] = zi;
     p[i] = zi;
-    rz += double(ri) * double(zi);
-    rr += double(ri) * double(ri);
+    q[i] = R(0);
+    rz += ri * zi;
+    rr += ri * ri;
   }
-  const double s1 = block_sum(rz, sh);
+  const double s1 = block_sum(double(rz), sh);
   __syncthreads();
-  const double s2 = block_sum(rr, sh);
+  const double s2 = block_sum(double(rr), sh);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = s1;
     part[gridDim.x + blockIdx.x] = s2;
@@ -514,17 +527,17 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_start(R* r, R* z, R* p, cons
 template <class R>
 __global__ void __launch_bounds__(kRedThreads) k_cg_pq(const R* p, R* q, const uint8_t* bnd, int64_t n,
                                                        double* part) {
-  __shared__ double sh[kRedThreads];
-  double pq = 0.0;
+  __shared__ double sh[kRedThreads / 32];
+  R pq = R(0);
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     R qi = q[i];
     if (bnd[i]) {
       qi = R(0);
       q[i] = qi;
     }
-    pq += double(p[i]) * double(qi);
+    pq += p[i] * qi;
   }
-  const double s = block_sum(pq, sh);
+  const double s = block_sum(double(pq), sh);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -532,38 +545,41 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_pq(const R* p, R* q, const u
 template <class R>
 __global__ void __launch_bounds__(kRedThreads) k_cg_update(R* x, R* r, R* z, const R* p, const R* q, const R* dinv,
                                                            const Scalars* sc, int64_t n, double* part) {
-  __shared__ double sh[kRedThreads];
+  __shared__ double sh[kRedThreads / 32];
   const R al = R(sc->alpha);
-  double rz = 0.0, rr = 0.0;
+  R rz = R(0), rr = R(0);
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     x[i] += al * p[i];
     const R ri = r[i] - al * q[i];
     r[i] = ri;
     const R zi = dinv[i] * ri;
     z[i] = zi;
-    rz += double(ri) * double(zi);
-    rr += double(ri) * double(ri);
+    rz += ri * zi;
+    rr += ri * ri;
   }
-  const double s1 = block_sum(rz, sh);
+  const double s1 = block_sum(double(rz), sh);
   __syncthreads();
-  const double s2 = block_sum(rr, sh);
+  const double s2 = block_sum(double(rr), sh);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = s1;
     part[gridDim.x + blockIdx.x] = s2;
   }
 }
 
+// p = z + beta p; q = 0 for the next operator application.
 template <class R>
-__global__ void __launch_bounds__(kRedThreads) k_cg_direction(R* p, const R* z, const Scalars* sc, int64_t n) {
+__global__ void __launch_bounds__(kRedThreads) k_cg_direction(R* p, R* q, const R* z, const Scalars* sc, int64_t n) {
   const R be = R(sc->beta);
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     p[i] = z[i] + be * p[i];
+    q[i] = R(0);
+  }
 }
 
 // Sums the partials of a reduction and updates the CG scalars:
 // what = 0: start (rz, rr); 1: p.q -> alpha; 2: update (rz_new, rr) -> beta.
 __global__ void __launch_bounds__(kRedThreads) k_cg_scalars(const double* part, int nparts, int what, Scalars* sc) {
-  __shared__ double sh[kRedThreads];
+  __shared__ double sh[kRedThreads / 32];
   double s1 = 0.0, s2 = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
     s1 += part[i];
@@ -591,7 +607,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_scalars(const double* part, 
 // |b|^2 over the interior unknowns (the residual reference).
 template <class R>
 __global__ void __launch_bounds__(kRedThreads) k_norm2(const R* b, const uint8_t* bnd, int64_t n, double* part) {
-  __shared__ double sh[kRedThreads];
+  __shared__ double sh[kRedThreads / 32];
   double s = 0.0;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     if (!bnd[i]) s += double(b[i]) * double(b[i]);
@@ -600,7 +616,7 @@ __global__ void __launch_bounds__(kRedThreads) k_norm2(const R* b, const uint8_t
 }
 
 __global__ void k_sum_into(const double* part, int nparts, double* out) {
-  __shared__ double sh[kRedThreads];
+  __shared__ double sh[kRedThreads / 32];
   double s = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
   const double t = block_sum(s, sh);
@@ -708,7 +724,7 @@ elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
   ok = ok && cudaMalloc((void**)&me->d_dcells, sizeof(int4) * cells.size()) == cudaSuccess &&
        cudaMemcpy(me->d_dcells, cells.data(), sizeof(int4) * cells.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMalloc(&me->d_dvec, size_t(kDiffVectors) * me->n_unique * es) == cudaSuccess;
-  ok = ok && cudaMalloc((void**)&me->d_dpart, sizeof(double) * 2 * kRedBlocks) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&me->d_dpart, sizeof(double) * 2 * kRedMaxBlocks) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&me->d_dscal, sizeof(Scalars) + 2 * sizeof(double)) == cudaSuccess;
   if (me->precision == ELM_FP64) {
     // FP32 copies for the inner solves of the mixed-precision form
@@ -786,7 +802,7 @@ bool pcg_iterate(const elm_mesh_s* me, const void* tab, R* x, R* r, R* z, R* p, 
   const int64_t n = me->n_unique;
   double* part = me->d_dpart;
   Scalars* sc = reinterpret_cast<Scalars*>(me->d_dscal);
-  const int nred = kRedBlocks;
+  const int nred = red_blocks(n);
   auto chk = [&](cudaError_t e, const char* where) {
     if (e != cudaSuccess) *err = std::string(where) + ": " + cudaGetErrorString(e);
     return e == cudaSuccess;
@@ -802,13 +818,13 @@ bool pcg_iterate(const elm_mesh_s* me, const void* tab, R* x, R* r, R* z, R* p, 
   *done = 0;
   if (!read_rr()) return false;
   while (*rr > stop_rr && *done < budget && std::isfinite(*rr)) {
-    if (!chk(cudaMemsetAsync(qv, 0, size_t(n) * sizeof(R), s), "memset")) return false;
+    // q is zero here (k_cg_start, k_cg_direction)
     if (!chk(apply_op<R>(me, p, qv, alpha, 1.0, false, s, tab), "apply")) return false;
     k_cg_pq<R><<<nred, kRedThreads, 0, s>>>(p, qv, me->d_dbnd, n, part);
     k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 1, sc);
     k_cg_update<R><<<nred, kRedThreads, 0, s>>>(x, r, z, p, qv, dinv, sc, n, part);
     k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 2, sc);
-    k_cg_direction<R><<<nred, kRedThreads, 0, s>>>(p, z, sc, n);
+    k_cg_direction<R><<<nred, kRedThreads, 0, s>>>(p, qv, z, sc, n);
     ++*done;
     if (!read_rr()) return false;
   }
@@ -845,7 +861,7 @@ elm_status solve_mixed(elm_mesh_s* me, const void* c_hat, const void* c_bnd, con
   double* rnorm = bnorm + 1;
   const size_t bytes = size_t(n) * sizeof(double);
   const unsigned eb = unsigned((n + 255) / 256);
-  const int nred = kRedBlocks;
+  const int nred = red_blocks(n);
   auto chk = [&](cudaError_t e, const char* where) {
     if (e != cudaSuccess) *err = std::string(where) + ": " + cudaGetErrorString(e);
     return e == cudaSuccess;
@@ -889,7 +905,7 @@ elm_status solve_mixed(elm_mesh_s* me, const void* c_hat, const void* c_bnd, con
     if (!interior || !(rel > rtol) || total >= max_iter || !std::isfinite(rel)) break;
     // inner FP32 solve of E d = r from d = 0
     k_residual_to_float<<<eb, 256, 0, s>>>(r, r32, d32, me->d_dbnd, n);
-    k_cg_start<float><<<nred, kRedThreads, 0, s>>>(r32, z32, p32, dinv32, me->d_dbnd, n, part);
+    k_cg_start<float><<<nred, kRedThreads, 0, s>>>(r32, z32, p32, q32, dinv32, me->d_dbnd, n, part);
     k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 0, sc);
     int done = 0;
     double rr32 = 0.0;
@@ -935,7 +951,7 @@ elm_status solve(elm_mesh_s* me, const void* c_hat, const void* c_bnd, const voi
   double* bnorm = me->d_dscal + sizeof(Scalars) / sizeof(double);
   const size_t bytes = size_t(n) * sizeof(R);
   const unsigned eb = unsigned((n + 255) / 256);
-  const int nred = kRedBlocks;
+  const int nred = red_blocks(n);
   const int prec = me->precision;
   auto chk = [&](cudaError_t e, const char* where) {
     if (e != cudaSuccess) *err = std::string(where) + ": " + cudaGetErrorString(e);
@@ -963,7 +979,7 @@ elm_status solve(elm_mesh_s* me, const void* c_hat, const void* c_bnd, const voi
   // r = b - E x, restricted to the interior; z = D^{-1} r; p = z
   k_copy<R><<<eb, 256, 0, s>>>(r, b, n);
   if (!chk(apply_op<R>(me, x, r, alpha, -1.0, false, s), "residual")) return ELM_ERR_CUDA;
-  k_cg_start<R><<<nred, kRedThreads, 0, s>>>(r, z, p, dinv, me->d_dbnd, n, part);
+  k_cg_start<R><<<nred, kRedThreads, 0, s>>>(r, z, p, qv, dinv, me->d_dbnd, n, part);
   k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 0, sc);
   double hb = 0.0;
   if (!chk(cudaMemcpyAsync(&hb, bnorm, sizeof(double), cudaMemcpyDeviceToHost, s), "read") ||
