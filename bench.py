@@ -214,10 +214,30 @@ def _cpu_baseline(spec, seconds: float = 12.0):
         if el >= seconds / 4 or len(idx) == om.n_nodes:
             break
         n = int(n * min(8.0, max(2.0, seconds / 2 / max(el, 1e-3))))
+    # the same oracle on one thread, on a sample sized for about the same time
+    n1 = max(1000, min(len(idx), int(len(idx) / max(threads, 1))))
+    idx1 = np.sort(rng.choice(om.n_nodes, n1, replace=False))
+    t0 = time.perf_counter()
+    om.advect_nodes(T, u, dt, idx1, n_sub=spec[6], threads=1)
+    el1 = time.perf_counter() - t0
     return {"value": len(idx) / el, "unit": "node updates/s", "cores": threads, "kind": "oracle",
             "sample": (f"all {len(idx)} nodes of the workload" if len(idx) == om.n_nodes else
                        f"{len(idx)} random nodes of the same workload") + f", one step, FP64, {threads} threads",
-            "seconds": el}
+            "seconds": el, "cpu_model": _cpu_model(),
+            "single_thread": {"value": n1 / el1, "unit": "node updates/s", "sample": f"{n1} random nodes, one step",
+                              "seconds": el1}}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args, spec):
