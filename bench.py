@@ -64,7 +64,7 @@ def _fields(spec, coords):
 
 
 def _peaks():
-    """(HBM GB/s, SM max MHz, kind) from the measured peaks, else the fallback."""
+    """(HBM GB/s, SM max MHz, kind) from MEASURED_PEAKS.json, else the fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)

@@ -39,7 +39,7 @@
 //     directional derivatives of T^{n+1} with respect to the nodal velocity and
 //     the transpose of the interpolation for T^n, used to check adjoints.
 //
-// Readings of points the paper leaves open (each also listed in the design doc):
+// Readings of points the paper leaves open:
 //   * Out-of-domain stage points: every RK stage point and the final departure
 //     point are clamped componentwise to the axis-aligned bounding box of the
 //     mesh (the Euclidean projection for box domains).  If the clamped point
