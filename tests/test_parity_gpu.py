@@ -206,11 +206,13 @@ def test_lookback_needs_steady_velocity():
         P.gm.advect_lookback(P.to_gpu(inputs.hill(P.x)), 0.1, 4)
 
 
-@pytest.mark.parametrize("precision,level,n_sub,cfl", [("fp64", 6, 2, 4.0), ("fp32", 7, 1, 4.0)])
-def test_full_size_sampled(precision, level, n_sub, cfl):
-    """The benchmark sizes (3D level 6 FP64, level 7 FP32), checked on 3000
-    sampled nodes the oracle evaluates one by one."""
-    P = Pair("cube", level, precision)
+@pytest.mark.parametrize("precision,level,n_sub,cfl,order", [("fp64", 6, 2, 4.0, 2), ("fp32", 7, 1, 4.0, 2),
+                                                              ("fp32", 8, 1, 4.0, 1)])
+def test_full_size_sampled(precision, level, n_sub, cfl, order):
+    """The benchmark sizes (3D level 6 FP64, level 7 FP32, and P1 at its
+    largest level 8, 257^3 nodes), checked on 3000 sampled nodes the oracle
+    evaluates one by one."""
+    P = Pair("cube", level, precision, order=order)
     if precision == "fp64":
         u = inputs.cellular_flow(P.x)
         T = inputs.slotted_sphere(P.x)
