@@ -86,6 +86,11 @@ enum { ELM_P1 = 0x400 };
  * solver vectors of elm_mesh_num_unique values in the mesh precision). */
 enum { ELM_DIFFUSION = 0x800 };
 
+/* Flag OR-ed into `precision` of elm_mesh_create: also set up elm_advect_host
+ * (two sets of device staging buffers, (2 dim + 2) values per storage node in
+ * the mesh precision each, and two internal non-blocking copy streams). */
+enum { ELM_HOST_STAGING = 0x1000 };
+
 /* Builds the refined mesh (Sec. 2.1: coarse mesh T_0 refined uniformly after
  * Bey; Sec. 2.3.1, grid data structure: one DoF owner per interface node).
  *  dim            2 (triangles) or 3 (tetrahedra).
@@ -95,7 +100,7 @@ enum { ELM_DIFFUSION = 0x800 };
  *                 id, which makes the refinement conforming across faces.
  *  level          P2: 0..9 in 2D, 0..7 in 3D; P1: 0..10 in 2D, 0..8 in 3D.
  *  precision      ELM_FP64 or ELM_FP32, optionally | ELM_HOST_ONLY,
- *                 | ELM_ADJOINT, | ELM_P1, | ELM_DIFFUSION.
+ *                 | ELM_ADJOINT, | ELM_P1, | ELM_DIFFUSION, | ELM_HOST_STAGING.
  * Copies everything it needs; allocates the mesh's device tables on the
  * current device.  Returns ELM_ERR_TOPOLOGY for a degenerate macro or a
  * non-manifold face.  *out is set only on success. */
@@ -172,6 +177,32 @@ elm_status elm_set_velocity(elm_mesh mesh, const void* u_old_dev, const void* u_
  * accumulated between steps). */
 elm_status elm_advect(elm_mesh mesh, const void* T_old_dev, void* T_new_dev, double dt, int n_sub,
                       void* stream);
+
+/* The advection step of elm_advect with every buffer in HOST memory, for a
+ * caller whose fields live on the host (Algorithm 1, lines 3-4: the step's
+ * inputs are the velocity at t_n and t_{n+1} and T^n; its result is T^{n+1}).
+ * Needs a mesh created with ELM_HOST_STAGING.
+ *  u_old_host, u_new_host  velocity [n, dim] (equal pointers: steady).
+ *  T_old_host, T_new_host  [n]; they may be the same buffer (in-place).
+ *  dt, n_sub, stream       as for elm_advect.
+ * All four must be page-locked host memory (cudaHostAlloc, cudaHostRegister
+ * or a pinned torch tensor): the call checks the first and last byte of each
+ * and returns ELM_ERR_ARG for pageable memory.  Everything is enqueued
+ * asynchronously; when `stream` has completed, T_new_host holds the result,
+ * and until then the caller must neither change the inputs nor read or reuse
+ * the output.  The velocity becomes the mesh's current velocity, as after
+ * elm_set_velocity.
+ * Pipelining: consecutive calls alternate between the two staging sets, and
+ * the copies run on the mesh's own streams, so the host-to-device copy of a
+ * call overlaps the step of the call before it, and each quarter of the
+ * result is copied back while the rest is computed.  A call whose inputs
+ * overlap the host result of the call in flight before it waits for that
+ * result first, so feeding T_new_host back as the next T_old_host is
+ * correct.  Successive calls on one mesh must use one stream (or be ordered
+ * by the caller).  Not capturable into a CUDA graph: returns ELM_ERR_STATE
+ * while `stream` is capturing. */
+elm_status elm_advect_host(elm_mesh mesh, const void* u_old_host, const void* u_new_host, const void* T_old_host,
+                           void* T_new_host, double dt, int n_sub, void* stream);
 
 /* The advection step of elm_advect for callers that cannot allocate device
  * memory where they advect (for example an application whose device memory

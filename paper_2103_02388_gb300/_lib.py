@@ -28,6 +28,7 @@ SIGNATURES = [
     ("elm_set_velocity", _I, [_P, _P, _P, _P]),
     ("elm_advect", _I, [_P, _P, _P, _D, _I, _P]),
     ("elm_advect_noalloc", _I, [_P, _P, _P, _P, _P, _D, _I, _P]),
+    ("elm_advect_host", _I, [_P, _P, _P, _P, _P, _D, _I, _P]),
     ("elm_advect_adjoint", _I, [_P, _P, _P, _P, _P, _P, _D, _I, _P]),
     ("elm_trace", _I, [_P, _P, _P, _D, _I, _P]),
     ("elm_trace_eval", _I, [_P, _P, _P, _P, _P]),
@@ -73,3 +74,4 @@ ELM_HOST_ONLY = 0x100
 ELM_ADJOINT = 0x200
 ELM_P1 = 0x400
 ELM_DIFFUSION = 0x800
+ELM_HOST_STAGING = 0x1000

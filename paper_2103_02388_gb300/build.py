@@ -17,7 +17,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["advect.cu", "noalloc.cu", "adjoint.cu", "diffusion.cu"]
-CPP_SOURCES = ["mesh.cpp", "api.cpp", "batch.cpp"]
+CPP_SOURCES = ["mesh.cpp", "api.cpp", "batch.cpp", "host_path.cpp"]
 HEADERS = ["elm_internal.h", "tracer.cuh"]
 
 

@@ -34,6 +34,7 @@ struct DeviceGuard {
 size_t elem_size(const elm_mesh_s* me) { return me->precision == ELM_FP64 ? 8 : 4; }
 
 void free_tables(elm_mesh_s* me) {
+  elm::free_host_staging(me);
   cudaFree(me->d_geo);
   cudaFree(me->d_geo32);
   cudaFree(me->d_unique_map);
@@ -77,9 +78,12 @@ bool ranges_overlap(const void* a, const void* b, size_t bytes) {
   return pa < pb + bytes && pb < pa + bytes;
 }
 
+}  // namespace
+
+namespace elm {
 // Launch arguments shared by every per-node kernel of a mesh: tables, sizes,
 // the current velocity and the step constants for (dt, n_sub).
-elm::AdvectArgs make_args(const elm_mesh_s* me, double dt, int n_sub) {
+AdvectArgs make_args(const elm_mesh_s* me, double dt, int n_sub) {
   elm::AdvectArgs a{};
   a.geo = me->d_geo;
   a.geo32 = me->d_geo32;
@@ -116,11 +120,10 @@ elm::AdvectArgs make_args(const elm_mesh_s* me, double dt, int n_sub) {
   return a;
 }
 
-}  // namespace
-
-namespace elm {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace elm
+
+using elm::make_args;
 
 extern "C" {
 
@@ -135,7 +138,8 @@ elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz
   const bool with_adjoint = (precision & ELM_ADJOINT) != 0;
   const int order = (precision & ELM_P1) != 0 ? 1 : 2;
   const bool with_diffusion = (precision & ELM_DIFFUSION) != 0;
-  precision &= ~(ELM_HOST_ONLY | ELM_ADJOINT | ELM_P1 | ELM_DIFFUSION);
+  const bool with_staging = (precision & ELM_HOST_STAGING) != 0;
+  precision &= ~(ELM_HOST_ONLY | ELM_ADJOINT | ELM_P1 | ELM_DIFFUSION | ELM_HOST_STAGING);
   if (precision != ELM_FP64 && precision != ELM_FP32)
     return fail(ELM_ERR_ARG, "elm_mesh_create: precision must be ELM_FP64 or ELM_FP32");
   if (order == 1 && with_adjoint)
@@ -170,6 +174,7 @@ elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz
   elm_status s;
   try {
     s = elm::build_mesh(dim, n_vertices, vertex_xyz, n_macros, macro_vertices, level, precision, me, &err);
+    if (s == ELM_OK && with_staging && !host_only) s = elm::setup_host_staging(me, &err);
   } catch (const std::bad_alloc&) {
     s = ELM_ERR_ARG;
     err = "out of host memory";

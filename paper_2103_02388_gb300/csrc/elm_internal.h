@@ -109,6 +109,29 @@ struct AdvectArgs {
   StepConsts<double> k64;
 };
 
+// Host-buffer step (elm_advect_host, ELM_HOST_STAGING): two sets of device
+// staging buffers used by alternate calls, so that the host-to-device copy of
+// one call runs while the previous call computes and copies its result back.
+// The step of a call is launched in kHostParts pieces (contiguous runs of the
+// work list, which cover contiguous storage ranges), and each piece's result
+// goes back to the host as soon as that piece is done.
+constexpr int kHostParts = 4;
+struct HostStaging {
+  void* u[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [set][old, new]: velocity [n, dim]
+  void* T_old[2] = {nullptr, nullptr};
+  void* T_new[2] = {nullptr, nullptr};
+  cudaStream_t h2d = nullptr, d2h = nullptr;   // non-blocking copy streams
+  cudaEvent_t ev_h2d[2] = {nullptr, nullptr};  // inputs of the set are on the device
+  cudaEvent_t ev_part[2][kHostParts] = {};     // piece p of the set's step is done
+  cudaEvent_t ev_d2h[2] = {nullptr, nullptr};  // the set's result is on the host
+  cudaEvent_t ev_free[2] = {nullptr, nullptr}; // the set may be overwritten
+  int next = 0;                                // set of the next call
+  const char* out_ptr[2] = {nullptr, nullptr}; // host result range of each set's last call
+  size_t out_bytes[2] = {0, 0};
+  int64_t part_chunk[kHostParts + 1] = {};     // piece p: chunks [part_chunk[p], part_chunk[p+1])
+  int64_t part_slot[kHostParts + 1] = {};      // and storage slots [part_slot[p], part_slot[p+1])
+};
+
 }  // namespace elm
 
 struct elm_mesh_s {
@@ -130,6 +153,8 @@ struct elm_mesh_s {
   int64_t* d_owner_mp = nullptr;     // unique id -> owner record (pack_owner)
   int4* d_chunks = nullptr;          // work list: one block-sized run of a slab each
   int64_t n_chunks = 0;
+  std::vector<int4> chunks;          // host copy of the work list
+  elm::HostStaging* staging = nullptr;  // ELM_HOST_STAGING
   void* d_u4[2] = {nullptr, nullptr};  // packed velocity records u_old, u_new
   bool have_velocity = false;
   bool steady = true;
@@ -170,6 +195,14 @@ constexpr int kDiffVectors32 = 6;
 // tables of a blended mesh (at elm_mesh_set_annulus).
 elm_status build_diffusion(elm_mesh_s* me, std::string* err);
 elm_status build_diffusion_blended(elm_mesh_s* me, std::string* err);
+
+// Host-buffer step set-up and tear-down (host_path.cpp).
+elm_status setup_host_staging(elm_mesh_s* me, std::string* err);
+void free_host_staging(elm_mesh_s* me);
+
+// Launch arguments of a per-node kernel of the mesh for a step (dt, n_sub):
+// tables, sizes, the current velocity and the step constants (api.cpp).
+AdvectArgs make_args(const elm_mesh_s* me, double dt, int n_sub);
 
 // Host mesh construction (mesh.cpp).
 elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const int64_t* mv,

@@ -272,6 +272,7 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
         chunks.push_back(make_int4(int(m), p1, i0, std::min(kAdvectThreads, len - i0)));
     }
   me->n_chunks = int64_t(chunks.size());
+  me->chunks = chunks;
   auto upload = [&](void** dst, const void* src, size_t bytes) -> bool {
     if (bytes == 0) { *dst = nullptr; return true; }
     if (cudaMalloc(dst, bytes) != cudaSuccess) return false;

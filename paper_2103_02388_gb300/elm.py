@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import ELM_ADJOINT, ELM_DIFFUSION, ELM_FP32, ELM_FP64, ELM_HOST_ONLY, ELM_P1, check
+from ._lib import ELM_ADJOINT, ELM_DIFFUSION, ELM_FP32, ELM_FP64, ELM_HOST_ONLY, ELM_HOST_STAGING, ELM_P1, check
 
 _DTYPES = {"fp64": (ELM_FP64, torch.float64, np.float64), "fp32": (ELM_FP32, torch.float32, np.float32)}
 
@@ -28,11 +28,13 @@ class Mesh:
     ``vertices``: [n_vertices, dim] coordinates; ``macros``: [n_macros, dim+1]
     vertex ids; ``precision``: "fp64" or "fp32"; ``order``: 2 (P2 elements) or
     1 (P1, Sec. 3.1).  ``host_only=True`` builds only the host tables
-    (coordinates and the unique map), without a GPU.
+    (coordinates and the unique map), without a GPU.  ``host_staging=True``
+    sets up ``advect_host`` (the step with pinned host buffers).
     """
 
     def __init__(self, vertices, macros, level: int, precision: str = "fp64", host_only: bool = False,
-                 adjoint: bool = False, order: int = 2, diffusion: bool = False, annulus=None):
+                 adjoint: bool = False, order: int = 2, diffusion: bool = False, annulus=None,
+                 host_staging: bool = False):
         lib = _lib.load()
         self.vertices = np.ascontiguousarray(vertices, dtype=np.float64)
         self.macros = np.ascontiguousarray(macros, dtype=np.int64)
@@ -52,7 +54,8 @@ class Mesh:
                                   self.vertices.ctypes.data_as(ctypes.c_void_p),
                                   self.macros.shape[0], self.macros.ctypes.data_as(ctypes.c_void_p),
                                   self.level, code | (ELM_HOST_ONLY if host_only else 0) | (ELM_ADJOINT if adjoint else 0)
-                                  | (ELM_P1 if order == 1 else 0) | (ELM_DIFFUSION if diffusion else 0),
+                                  | (ELM_P1 if order == 1 else 0) | (ELM_DIFFUSION if diffusion else 0)
+                                  | (ELM_HOST_STAGING if host_staging else 0),
                                   ctypes.byref(h)))
         self._h = h
         if annulus is not None:
@@ -63,6 +66,7 @@ class Mesh:
         self.n_nodes = int(lib.elm_mesh_num_nodes(h))
         self.n_unique = int(lib.elm_mesh_num_unique(h))
         self._u = None
+        self._host_inflight = []  # (event, host tensors) of advect_host calls not yet complete
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -151,6 +155,39 @@ class Mesh:
             self._check_tensor(out, "out")
         check(_lib.load().elm_advect(self._h, ctypes.c_void_p(T_old.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                      float(dt), int(n_sub), _stream_ptr(stream)))
+        return out
+
+    def advect_host(self, T_old: torch.Tensor, dt: float, n_sub: int = 1, u_old: torch.Tensor | None = None,
+                    u_new: torch.Tensor | None = None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """The advection step with page-locked HOST tensors (storage layout):
+        velocity ``u_old`` ([n, dim], at t_n) and ``u_new`` (at t_{n+1};
+        None = steady), ``T_old`` and the result ``out`` ([n]; may be
+        ``T_old`` itself).  Asynchronous on ``stream``: ``out`` is valid once
+        the stream has completed.  Consecutive calls overlap their copies with
+        the previous call's step (mesh created with ``host_staging=True``)."""
+        if u_old is None:
+            raise ValueError("advect_host needs the velocity u_old")
+        u_new = u_old if u_new is None else u_new
+        for name, t, shape in (("T_old", T_old, (self.n_nodes,)), ("u_old", u_old, (self.n_nodes, self.dim)),
+                               ("u_new", u_new, (self.n_nodes, self.dim))):
+            if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or not t.is_pinned():
+                raise ValueError(f"{name} must be a contiguous, pinned {self.dtype} CPU tensor")
+            if tuple(t.shape) != shape:
+                raise ValueError(f"{name} must have shape {shape}")
+        if out is None:
+            out = torch.empty(self.n_nodes, dtype=self.dtype, pin_memory=True)
+        elif out.is_cuda or out.dtype != self.dtype or not out.is_contiguous() or not out.is_pinned() \
+                or tuple(out.shape) != (self.n_nodes,):
+            raise ValueError(f"out must be a contiguous, pinned {self.dtype} CPU tensor of shape ({self.n_nodes},)")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        check(_lib.load().elm_advect_host(self._h, ctypes.c_void_p(u_old.data_ptr()), ctypes.c_void_p(u_new.data_ptr()),
+                                          ctypes.c_void_p(T_old.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                          float(dt), int(n_sub), ctypes.c_void_p(s.cuda_stream)))
+        # the host tensors stay referenced until the stream has passed this call
+        ev = torch.cuda.Event()
+        ev.record(s)
+        self._host_inflight = [x for x in self._host_inflight if not x[0].query()]
+        self._host_inflight.append((ev, (T_old, u_old, u_new, out)))
         return out
 
     def advect_lookback(self, T_src: torch.Tensor, tau: float, b: int, n_sub: int = 1,

@@ -174,6 +174,22 @@ def test_host_only_mesh_refuses_device_calls(lib):
     assert lib.elm_mesh_num_nodes(None) == 0
 
 
+def test_host_buffer_step_argument_errors(lib):
+    v, m = inputs.unit_cube()
+    st, h = _host_mesh(lib, v, m, 2, precision=_lib.ELM_FP32 | _lib.ELM_HOST_STAGING)
+    assert st == _lib.ELM_OK                            # a host-only mesh sets up no staging
+    fake = ctypes.c_void_p(4096)
+    assert lib.elm_advect_host(h, fake, fake, fake, fake, 0.1, 1, None) == _lib.ELM_ERR_STATE
+    assert b"host-only" in lib.elm_last_error()
+    assert lib.elm_advect_host(h, None, fake, fake, fake, 0.1, 1, None) == _lib.ELM_ERR_ARG
+    assert lib.elm_advect_host(h, fake, fake, fake, None, 0.1, 1, None) == _lib.ELM_ERR_ARG
+    assert lib.elm_advect_host(h, fake, fake, fake, fake, float("nan"), 1, None) == _lib.ELM_ERR_ARG
+    assert lib.elm_advect_host(h, fake, fake, fake, fake, -1.0, 1, None) == _lib.ELM_ERR_ARG
+    assert lib.elm_advect_host(h, fake, fake, fake, fake, 0.1, 0, None) == _lib.ELM_ERR_ARG
+    assert lib.elm_advect_host(None, fake, fake, fake, fake, 0.1, 1, None) == _lib.ELM_ERR_ARG
+    assert lib.elm_mesh_destroy(h) == _lib.ELM_OK
+
+
 def test_missing_library_fails_loudly(tmp_path):
     saved = _lib._lib
     _lib._lib = None
