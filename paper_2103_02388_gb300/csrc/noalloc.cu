@@ -8,7 +8,7 @@
 // itself never allocates or frees device memory.  It serves code that cannot
 // call cudaMalloc where it advects: for example a host application whose
 // device memory is handed out by its own pool and that forbids further
-// driver allocations, or a time-critical loop in which the implicit device
+// cudaMalloc calls, or a time-critical loop in which the implicit device
 // synchronisation of cudaMalloc / cudaFree is not acceptable.  The paper has
 // no counterpart; it only changes where the working copy of the velocity lives.
 #include <cmath>
