@@ -195,13 +195,67 @@ def aggregate(local_ms: float, local_units: int, dist=None, device=None):
     return float(t.item()), int(n.item())
 
 
-def _cpu_baseline(spec, seconds: float = 12.0):
-    """The CPU oracle timed on a bounded sample of the same workload."""
+def _oracle_mesh(spec):
     import oracle
     from paper_2103_02388_gb300 import inputs
-    dim, level = spec[0], spec[1]
-    v, m = inputs.unit_cube() if dim == 3 else inputs.unit_square()
-    om = oracle.OracleMesh(v, m, level)
+    v, m = inputs.unit_cube() if spec[0] == 3 else inputs.unit_square()
+    return oracle.OracleMesh(v, m, spec[1])
+
+
+def _match_nodes(coords_ref, coords_other, M: int):
+    """perm with coords_other[perm[i]] == coords_ref[i], for node sets on the
+    1/M lattice of the unit square / cube (P2: M = 2^(L+1))."""
+    def keys(c):
+        q = np.rint(c * M).astype(np.int64)
+        k = np.zeros(len(c), np.int64)
+        for a in range(c.shape[1]):
+            k = k * (M + 1) + q[:, a]
+        return k
+    ka, kb = keys(coords_ref), keys(coords_other)
+    oa, ob = np.argsort(ka), np.argsort(kb)
+    if not np.array_equal(ka[oa], kb[ob]):
+        raise RuntimeError("node sets of the oracle and the library differ")
+    perm = np.empty(len(ka), np.int64)
+    perm[oa] = ob
+    return perm
+
+
+def _accuracy(spec, om, mesh, T0_storage, dt, steps: int = 3):
+    """Error of the GPU step against the FP64 oracle on the same inputs (the
+    FP32-rounded fields for an FP32 workload), over every unique node: after
+    one step, and accumulated over ``steps`` steps with each side continuing
+    from its own state.  Relative to max |T^0| (max) and ||T_oracle|| (L2)."""
+    import torch
+    u, T0, _ = _fields(spec, om.coords)
+    n_sub = spec[6]
+    perm = _match_nodes(om.coords, mesh.unique_coords(), mesh.order << mesh.level)
+    Tg, out = T0_storage.clone(), torch.empty_like(T0_storage)
+    To = T0
+    tmax = float(np.abs(T0).max())
+    res = {"reference": "FP64 oracle on the same inputs" + (" (FP32-rounded)" if spec[2] == "fp32" else ""),
+           "nodes": int(om.n_nodes), "tolerance_one_step": 1e-5 if spec[2] == "fp32" else 1e-12}
+    t0 = time.perf_counter()
+    for k in range(1, steps + 1):
+        mesh.advect(Tg, dt, n_sub, out=out)
+        Tg, out = out, Tg
+        To = om.advect(To, u, dt, n_sub)
+        if k in (1, steps):
+            g = mesh.to_unique(Tg).double().cpu().numpy()[perm]
+            e = g - To
+            rec = {"max_rel": float(np.abs(e).max() / tmax), "l2_rel": float(np.linalg.norm(e) / np.linalg.norm(To))}
+            if k == 1:
+                res["one_step"] = rec
+            else:
+                res["accumulated"] = dict(steps=steps, **rec)
+    mesh.status()
+    res["seconds"] = time.perf_counter() - t0
+    return res
+
+
+def _cpu_baseline(spec, seconds: float = 12.0, om=None):
+    """The CPU oracle timed on a bounded sample of the same workload."""
+    import oracle
+    om = _oracle_mesh(spec) if om is None else om
     u, T, dt = _fields(spec, om.coords)
     threads = oracle.default_threads()
     rng = np.random.default_rng(1)
@@ -235,6 +289,13 @@ def _cpu_model():
                 if line.lower().startswith(("model name", "cpu model")):
                     return line.split(":", 1)[1].strip()
     except OSError:
+        pass
+    try:  # Arm hosts: /proc/cpuinfo has no model name, lscpu names the core
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
         pass
     import platform
     return platform.processor() or platform.machine()
@@ -294,6 +355,7 @@ def run_ours(args, spec):
     dtype = mesh.dtype
     u_s = mesh.to_storage(torch.tensor(u, dtype=dtype, device=dev))
     T_a = mesh.to_storage(torch.tensor(T0, dtype=dtype, device=dev))
+    T_init = T_a.clone()
     T_b = torch.empty_like(T_a)
     mesh.set_velocity(u_s)
     stream = torch.cuda.current_stream()
@@ -419,7 +481,9 @@ def run_ours(args, spec):
         "e2e": e2e,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline(spec)
+        om = _oracle_mesh(spec)
+        line["accuracy"] = _accuracy(spec, om, mesh, T_init, dt)
+        line["cpu_baseline"] = _cpu_baseline(spec, om=om)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -591,6 +655,144 @@ def run_variant(args):
         "gpu_launches": launches * args.steps, "clocks": clocks.summary()}))
 
 
+BATCH_WORKLOADS = {
+    # 64 independent instances (2D levels 4-8, 3D levels 4-6), one CUDA graph of the time loop
+    "c4-batch-fp32": "fp32",
+    "c4-batch-fp64": "fp64",
+}
+
+
+def run_batch(args):
+    """The batched form: every instance of the seeded recipe advanced by one
+    persistent launch per step, the time loop of ``steps`` steps captured in
+    one CUDA graph; launch shape from the autotuner.  Time = CUDA events
+    around one replay of the graph on its stream."""
+    import torch
+    from paper_2103_02388_gb300 import elm, inputs
+    from paper_2103_02388_gb300.autotune import tune_batch
+    precision = BATCH_WORKLOADS[args.workload]
+    recipe = inputs.batch_recipe(seed=4, count=64)
+    meshes, Ta, Tb, dts, subs = [], [], [], [], []
+    nodes = storage = alg_bytes = 0
+    esz = 8 if precision == "fp64" else 4
+    for e in recipe:
+        v, m = inputs.unit_cube() if e["dim"] == 3 else inputs.unit_square()
+        gm = elm.Mesh(v, m, e["level"], precision)
+        u, T, dt = inputs.batch_fields(e, gm.node_coords())
+        gm.set_velocity(torch.tensor(u, dtype=gm.dtype, device="cuda"))
+        meshes.append(gm)
+        Ta.append(torch.tensor(T, dtype=gm.dtype, device="cuda"))
+        Tb.append(torch.empty_like(Ta[-1]))
+        dts.append(dt)
+        subs.append(1)
+        nodes += gm.n_unique
+        storage += gm.n_nodes
+        alg_bytes += gm.n_nodes * (e["dim"] * esz + 2 * esz)
+    tune = tune_batch(meshes, Ta, Tb, dts, subs, reps=3)
+    batch = elm.Batch(meshes, tune["blocks_per_sm"])
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            batch.advect(Ta, Tb, dts, subs)
+            Ta, Tb = Tb, Ta
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        x, y = Ta, Tb
+        for _ in range(args.steps):
+            batch.advect(x, y, dts, subs)
+            x, y = y, x
+    graph.replay()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            graph.replay()
+            ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    for gm in meshes:
+        gm.status()
+    hbm_peak, _, kind = _peaks()
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    print(json.dumps({
+        "metric": "traced node updates/s per batched step (1 GPU)", "value": nodes / (ms * 1e-3),
+        "unit": "node updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "instances": len(meshes), "unique_nodes": nodes,
+                   "storage_nodes": storage, "recipe": "inputs.batch_recipe(seed=4, count=64)",
+                   "graph": f"{args.steps} steps in one CUDA graph", "autotune": tune,
+                   "l2": "inputs larger than L2 (not flushed)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_kind": kind, "algorithmic_bytes_per_step": alg_bytes,
+                     "kernel": "k_advect_batch"},
+        "gpu_launches": args.steps, "clocks": clocks.summary()}))
+
+
+ADJOINT_WORKLOADS = {
+    # 3D level 6, cellular flow, 50 steps, checkpoints every 10, loss 0.5 ||T^50 - T*||^2
+    "c5-adjoint-l6-fp64": "fp64",
+    "c5-adjoint-l6-fp32": "fp32",
+}
+
+
+def run_adjoint(args):
+    """Gradient of a 50-step rollout (Sec. 2.3.1 step, differentiated): the
+    forward steps, the recomputation inside checkpointed segments and the
+    adjoint steps, for T^0 and the velocity.  One 'step' of the metric is one
+    forward step plus its share of the backward pass."""
+    import torch
+    from paper_2103_02388_gb300 import autograd, elm, inputs
+    precision = ADJOINT_WORKLOADS[args.workload]
+    level, steps_roll, every = 6, 50, 10
+    v, m = inputs.unit_cube()
+    mesh = elm.Mesh(v, m, level, precision, adjoint=True)
+    x = mesh.unique_coords()
+    tg = lambda a: mesh.to_storage(torch.tensor(a, dtype=mesh.dtype, device="cuda"))  # noqa: E731
+    u = inputs.cellular_flow(x)
+    dt = inputs.dt_for_cfl(4.0, level, u)
+    T0 = tg(inputs.gaussian(x, (0.35, 0.5, 0.5), 0.1))
+    Tstar = tg(inputs.random_fourier(x, seed=5)[:, 0])
+    u_s = tg(u)
+
+    def one():
+        T = T0.clone().requires_grad_(True)
+        uu = u_s.clone().requires_grad_(True)
+        loss = 0.5 * ((autograd.rollout(T, uu, mesh, dt, steps_roll, 1, every) - Tstar) ** 2).sum()
+        loss.backward()
+        return T.grad, uu.grad
+    for _ in range(max(1, args.warmup)):
+        one()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    reps = max(1, args.steps // steps_roll)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        ev0.record(stream)
+        for _ in range(reps):
+            gT, gU = one()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    mesh.status()
+    if not (torch.isfinite(gT).all() and torch.isfinite(gU).all()):
+        raise RuntimeError("non-finite gradient")
+    ms = ev0.elapsed_time(ev1) / (reps * steps_roll)
+    print(json.dumps({
+        "metric": "node updates/s of forward + adjoint per step of a checkpointed rollout (1 GPU)",
+        "value": mesh.n_unique / (ms * 1e-3), "unit": "node updates/s", "n_gpus": 1,
+        "steps": reps * steps_roll, "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "mesh": "unit cube, 6 Kuhn macro tetrahedra", "level": level,
+                   "unique_nodes": mesh.n_unique, "velocity": "cellular", "cfl": 4.0, "rollout_steps": steps_roll,
+                   "checkpoint_every": every, "loss": "0.5 ||T^50 - T*||^2, T* = random Fourier (seed 5)",
+                   "timed": f"{reps} gradient(s) of the whole rollout, CUDA events (host launch gaps included)"},
+        "gpu_launches": None, "clocks": clocks.summary()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -598,7 +800,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3-l7-fp32",
-                    choices=sorted(WORKLOADS) + sorted(DIFFUSION_WORKLOADS) + sorted(VARIANT_WORKLOADS))
+                    choices=sorted(WORKLOADS) + sorted(DIFFUSION_WORKLOADS) + sorted(VARIANT_WORKLOADS)
+                    + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload in DIFFUSION_WORKLOADS:
@@ -606,6 +809,12 @@ def main():
         return
     if args.workload in VARIANT_WORKLOADS:
         run_variant(args)
+        return
+    if args.workload in BATCH_WORKLOADS:
+        run_batch(args)
+        return
+    if args.workload in ADJOINT_WORKLOADS:
+        run_adjoint(args)
         return
     spec = WORKLOADS[args.workload]
     if args.impl == "reference":
