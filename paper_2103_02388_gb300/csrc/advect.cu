@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
     job.bl = args.blend;
     job.n_macros = args.n_macros;
   }
+  job.skip_ghosts = args.skip_ghosts;
   advect_node<D, R, STEADY, P, MODE, BLEND>(job, tab, ck, int(threadIdx.x));
 }
 
@@ -145,6 +146,17 @@ __global__ void k_pack_velocity(const R* __restrict__ u, R* __restrict__ u4, int
   for (int r = 0; r < 4; ++r) u4[i * 4 + r] = w[r];
 }
 
+// Interface copies (a5): out[ghost] = out[owner] for every (ghost slot,
+// owner slot) pair, ncomp values per slot.
+template <class R>
+__global__ void k_ghost_copy(const int2* __restrict__ g, int n, R* __restrict__ out, int ncomp) {
+  const int i = int(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n * ncomp) return;
+  const int j = i / ncomp, c = i - j * ncomp;
+  const int2 p = g[j];
+  out[int64_t(p.x) * ncomp + c] = out[int64_t(p.y) * ncomp + c];
+}
+
 template <class R>
 __global__ void k_gather(const R* __restrict__ in, R* __restrict__ out, const int64_t* __restrict__ idx,
                          int64_t n, int ncomp) {
@@ -192,12 +204,24 @@ cudaError_t launch_dr(const AdvectArgs& a, Tables<R> t, cudaStream_t s) {
 
 cudaError_t launch_advect(int dim, int precision, const AdvectArgs& a, cudaStream_t s) {
   if (a.n_storage == 0) return cudaSuccess;
+  cudaError_t e;
   if (precision == ELM_FP64) {
     Tables<double> t{a.geo};
-    return dim == 3 ? launch_dr<3, double>(a, t, s) : launch_dr<2, double>(a, t, s);
+    e = dim == 3 ? launch_dr<3, double>(a, t, s) : launch_dr<2, double>(a, t, s);
+  } else {
+    Tables<float> t{a.geo32};
+    e = dim == 3 ? launch_dr<3, float>(a, t, s) : launch_dr<2, float>(a, t, s);
   }
-  Tables<float> t{a.geo32};
-  return dim == 3 ? launch_dr<3, float>(a, t, s) : launch_dr<2, float>(a, t, s);
+  if (e != cudaSuccess || !a.skip_ghosts || a.n_ghosts == 0) return e;
+  // the per-node kernel skipped the non-owner copies: fill them
+  const int ncomp = a.mode == kTrace ? dim : 1;
+  void* out = a.mode == kTrace ? a.D_out : a.T_new;
+  const unsigned blocks = unsigned((int64_t(a.n_ghosts) * ncomp + 255) / 256);
+  if (precision == ELM_FP64)
+    k_ghost_copy<double><<<blocks, 256, 0, s>>>(a.ghosts, a.n_ghosts, static_cast<double*>(out), ncomp);
+  else
+    k_ghost_copy<float><<<blocks, 256, 0, s>>>(a.ghosts, a.n_ghosts, static_cast<float*>(out), ncomp);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batch32(const BatchParams<float>& p, int grid, cudaStream_t s) {

@@ -41,6 +41,8 @@ void free_tables(elm_mesh_s* me) {
   cudaFree(me->d_owner);
   cudaFree(me->d_owner_mp);
   cudaFree(me->d_chunks);
+  cudaFree(me->d_ghosts);
+  me->d_ghosts = nullptr;
   cudaFree(me->d_u4[0]);
   cudaFree(me->d_u4[1]);
   cudaFree(me->d_status);
@@ -105,6 +107,9 @@ AdvectArgs make_args(const elm_mesh_s* me, double dt, int n_sub) {
   a.owner_mp = me->d_owner_mp;
   a.chunks = me->d_chunks;
   a.n_chunks = int(me->n_chunks);
+  a.ghosts = me->d_ghosts;
+  a.n_ghosts = int(me->ghosts.size());
+  a.skip_ghosts = 1;
   a.order = me->order;
   a.blend = me->blend;
   const double h = dt / n_sub;

@@ -100,6 +100,12 @@ struct AdvectArgs {
   const int64_t* owner_mp;    // unique id -> owner record (pack_owner)
   const int4* chunks;         // (macro, p1, first index in slab, count) per thread block
   int n_chunks;
+  // Interface copies (a5, ghost copy): with skip_ghosts the per-node kernel
+  // computes each node once, in its owner's slot, and a copy pass then fills
+  // the other storage copies from the (ghost slot, owner slot) pairs.
+  const int2* ghosts = nullptr;
+  int n_ghosts = 0;
+  int skip_ghosts = 0;
   int order = 2;              // element order: 1 (P1) or 2 (P2)
   int mode = 0;               // per-node work (NodeMode in tracer.cuh): step, trace, evaluation
   const void* D_in = nullptr; // departure offsets [n, dim] (trace / evaluation)
@@ -130,6 +136,7 @@ struct HostStaging {
   size_t out_bytes[2] = {0, 0};
   int64_t part_chunk[kHostParts + 1] = {};     // piece p: chunks [part_chunk[p], part_chunk[p+1])
   int64_t part_slot[kHostParts + 1] = {};      // and storage slots [part_slot[p], part_slot[p+1])
+  int64_t part_ghost[kHostParts + 1] = {};     // and ghost pairs [part_ghost[p], part_ghost[p+1])
 };
 
 }  // namespace elm
@@ -154,6 +161,8 @@ struct elm_mesh_s {
   int4* d_chunks = nullptr;          // work list: one block-sized run of a slab each
   int64_t n_chunks = 0;
   std::vector<int4> chunks;          // host copy of the work list
+  std::vector<int2> ghosts;          // (ghost slot, owner slot), ascending ghost slot
+  int2* d_ghosts = nullptr;
   elm::HostStaging* staging = nullptr;  // ELM_HOST_STAGING
   void* d_u4[2] = {nullptr, nullptr};  // packed velocity records u_old, u_new
   bool have_velocity = false;

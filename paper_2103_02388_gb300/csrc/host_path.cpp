@@ -3,6 +3,7 @@
 // and the step launched in pieces whose results go back while the rest is
 // computed.  The step itself is the kernel of elm_advect (Algorithm 1,
 // lines 3-4); this file only moves data and orders streams.
+#include <algorithm>
 #include <cmath>
 #include <string>
 
@@ -98,6 +99,11 @@ elm_status setup_host_staging(elm_mesh_s* me, std::string* err) {
     H->part_chunk[p] = nc * p / kHostParts;
     H->part_slot[p] = H->part_chunk[p] < nc ? chunk_first_slot(me, me->chunks[size_t(H->part_chunk[p])])
                                             : me->n_storage;
+    // the piece's interface copies; their owners lie in this or an earlier
+    // piece (an owner's slot precedes its copies')
+    H->part_ghost[p] = std::lower_bound(me->ghosts.begin(), me->ghosts.end(), H->part_slot[p],
+                                        [](const int2& g, int64_t v) { return g.x < v; }) -
+                       me->ghosts.begin();
   }
   return ELM_OK;
 }
@@ -184,6 +190,8 @@ extern "C" elm_status elm_advect_host(elm_mesh me, const void* u_old_host, const
     if (c1 > c0) {
       a.chunks = me->d_chunks + c0;
       a.n_chunks = int(c1 - c0);
+      a.ghosts = me->d_ghosts + H.part_ghost[p];
+      a.n_ghosts = int(H.part_ghost[p + 1] - H.part_ghost[p]);
       e = elm::launch_advect(me->dim, me->precision, a, s);
     }
     if (e == cudaSuccess) e = cudaEventRecord(H.ev_part[k][p], s);

@@ -273,6 +273,15 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
     }
   me->n_chunks = int64_t(chunks.size());
   me->chunks = chunks;
+  // Interface copies other than the owner's, in storage order.  The owner is
+  // the first macro holding the node, so its slot (and its work-list chunk)
+  // always comes before the copy's.
+  me->ghosts.clear();
+  me->ghosts.reserve(size_t(me->n_ghost));
+  for (int64_t s = 0; s < me->n_storage; ++s) {
+    const int64_t o = me->owner[size_t(me->unique_map[size_t(s)])];
+    if (o != s) me->ghosts.push_back(make_int2(int(s), int(o)));
+  }
   auto upload = [&](void** dst, const void* src, size_t bytes) -> bool {
     if (bytes == 0) { *dst = nullptr; return true; }
     if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
@@ -298,6 +307,7 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
             upload((void**)&me->d_owner, me->owner.data(), sizeof(int64_t) * me->n_unique) &&
             upload((void**)&me->d_owner_mp, owner_mp.data(), sizeof(int64_t) * me->n_unique) &&
             upload((void**)&me->d_chunks, chunks.data(), sizeof(int4) * chunks.size()) &&
+            upload((void**)&me->d_ghosts, me->ghosts.data(), sizeof(int2) * me->ghosts.size()) &&
             cudaMalloc(&me->d_u4[0], size_t(me->n_storage) * 4 * (precision == ELM_FP64 ? 8 : 4)) == cudaSuccess &&
             cudaMalloc(&me->d_u4[1], size_t(me->n_storage) * 4 * (precision == ELM_FP64 ? 8 : 4)) == cudaSuccess &&
             (!me->with_adjoint ||

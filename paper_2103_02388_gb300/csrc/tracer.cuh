@@ -991,6 +991,7 @@ struct NodeJob {
   R* D_out = nullptr;
   BlendArgs bl;             // annulus blending (BLEND = 1)
   int n_macros = 0;         // enables the brute-force search of non-convex meshes (BLEND = 1)
+  int skip_ghosts = 0;      // copies held by a non-owner macro return at once (a copy pass fills them)
 };
 
 // What advect_node does with a node.
@@ -1043,6 +1044,9 @@ __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab
     if (iface) {
       const int64_t own = job.owner_mp[job.unique_map[slot]];
       t.m0 = unpack_owner<D>(own, t.p);
+      // one owner per node (Sec. 2.3.1): a copy held by another macro is
+      // filled from its owner's slot after the step
+      if (job.skip_ghosts && t.m0 != ck.x) return;
     }
   }
   {
