@@ -76,8 +76,9 @@ enum { ELM_ADJOINT = 0x200 };
  * the velocity and the scalar instead of quadratic (P2) ones (Sec. 3.1, test
  * setup; Tables 1 and 3 use P1).  The location is the same; a field is
  * evaluated from the d+1 vertices of the micro simplex with the micro
- * barycentrics as basis.  Not combinable with ELM_ADJOINT; P1 meshes are not
- * accepted by elm_batch_create. */
+ * barycentrics as basis.  Combinable with ELM_ADJOINT (the adjoint then
+ * differentiates the P1 interpolants); P1 meshes are not accepted by
+ * elm_batch_create. */
 enum { ELM_P1 = 0x400 };
 
 /* Flag OR-ed into `precision` of elm_mesh_create: also build the diffusion
@@ -230,7 +231,7 @@ elm_status elm_advect_noalloc(elm_mesh mesh, const void* u_old_dev, const void* 
  *   gT_old = W^T gT_new, W the interpolation matrix of the step
  *            (W_ij = phi_j(X_i)), and
  *   gU_old, gU_new = dL/du^n, dL/du^{n+1} through the backward RK4 stages,
- *            the P2 velocity evaluations, the time interpolation and the box
+ *            the P1 / P2 velocity evaluations, the time interpolation and the box
  *            clamps (a clamped coordinate passes no derivative), for
  *            L = <gT_new, T_new(u)>.
  * T_old, gT_new, gT_old: [n]; gU_old, gU_new: [n, dim]; storage layout, mesh
@@ -242,7 +243,7 @@ elm_status elm_advect_noalloc(elm_mesh mesh, const void* u_old_dev, const void* 
  * summed as 64-bit fixed-point integers (scale from a first pass), so
  * repeated calls give bitwise equal results.  Requires ELM_ADJOINT at
  * creation; allocates nothing; a few kernel launches on `stream`.  The map
- * is only piecewise smooth (P2 is C0); on element faces the derivative of
+ * is only piecewise smooth (P1 and P2 are C0); on element faces the derivative of
  * the element the point is located in is used.
  * 1 <= n_sub <= ELM_MAX_ADJOINT_SUBSTEPS (the reverse sweep recomputes each
  * substep's start from the node, O(n_sub^2) work). */

@@ -4,13 +4,13 @@
 // For T^{n+1}_i = T^n_h(X_i(u)) and an incoming gradient g = dL/dT^{n+1}:
 //   dL/dT^n_j  = sum_i phi_j(X_i) g_i                (transpose interpolation)
 //   dL/du_j    = sum_i g_i grad T^n_h(X_i) . dX_i/du_j  (reverse mode through
-//                the backward RK4 stages, the P2 velocity evaluations, the
+//                the backward RK4 stages, the P1 / P2 velocity evaluations, the
 //                time interpolation and the box clamps)
 // Each node i recomputes its forward trace (a substep is replayed from the
 // start for every substep it reverses, so no trace is stored), then runs
 // reverse mode: a stage k_s = u~(z_s) sends phi_j(z_s) a_k to node j's
 // velocity and J_u(z_s)^T a_k back to z_s, where J_u is the gradient of the
-// P2 interpolant; a clamped coordinate passes no derivative.
+// P1 / P2 interpolant; a clamped coordinate passes no derivative.
 //
 // Deterministic scatter-add: every contribution c is accumulated as a 64-bit
 // integer round(c * 2^k) with integer atomics, which add exactly and in any
@@ -58,10 +58,11 @@ __device__ __forceinline__ int scale_exponent(double m) {
   return kAccBits - kHeadroomBits - e;
 }
 
-template <int D, class R, bool STEADY>
+template <int D, class R, bool STEADY, int P>
 struct Adjoint {
-  static constexpr int NB = Tracer<D, R, STEADY>::NB;
-  Tracer<D, R, STEADY> t;
+  using Tr = Tracer<D, R, STEADY, P>;
+  static constexpr int NB = Tr::NB;
+  Tr t;
   AdjArgs A;
   int n_storage;
   double sT, sU;       // pass 1: scales 2^k
@@ -98,7 +99,7 @@ struct Adjoint {
     atomicAdd(A.acc_U + (int64_t(set) * n_storage + slot) * D + r, (unsigned long long)q);
   }
 
-  // P2 stencil with barycentrics L and the axis of each sorted fraction.
+  // P1 / P2 stencil with barycentrics L and the axis of each sorted fraction.
   __device__ void stencil_ad(const R* c, const R* f, int* slot, R* phi, R* L, int* ax) const {
     t.stencil(c, f, slot, phi);
     // recompute the sorted order (same comparisons as stencil)
@@ -121,11 +122,17 @@ struct Adjoint {
     L[D] = fs[D - 1];
   }
 
-  // Physical gradient of a P2 field with stencil values hv at the located
-  // point (barycentrics L, sorted axes ax), in the current macro frame.
+  // Physical gradient of a P1 / P2 field with stencil values hv at the
+  // located point (barycentrics L, sorted axes ax), in the current macro
+  // frame.  G_v is the derivative with respect to barycentric L_v: the vertex
+  // value for P1 (the basis is L itself, in the stencil's vertex order), the
+  // derivative of the vertex and edge terms for P2.
   __device__ void grad_x(const R* hv, const R* L, const int* ax, R* gx) const {
     R G[D + 1];
-    if (D == 3) {
+    if constexpr (P == 1) {
+#pragma unroll
+      for (int v = 0; v <= D; ++v) G[v] = hv[v];
+    } else if (D == 3) {
       G[0] = hv[0] * (R(4) * L[0] - R(1)) + R(4) * (L[1] * hv[4] + L[2] * hv[5] + L[D] * hv[6]);
       G[1] = hv[1] * (R(4) * L[1] - R(1)) + R(4) * (L[0] * hv[4] + L[2] * hv[7] + L[D] * hv[8]);
       G[2] = hv[2] * (R(4) * L[2] - R(1)) + R(4) * (L[0] * hv[5] + L[1] * hv[7] + L[D] * hv[9 % NB]);
@@ -161,7 +168,7 @@ struct Adjoint {
       R k[D], acc[D], z[D];
       if (j == 0) {
         R un[D];
-        Tracer<D, R, STEADY>::load_rec(t.un, home_slot, un);
+        Tr::load_rec(t.un, home_slot, un);
 #pragma unroll
         for (int q = 0; q < D; ++q) k[q] = un[q];
       } else {
@@ -204,13 +211,13 @@ struct Adjoint {
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       R un[D];
-      Tracer<D, R, STEADY>::load_rec(t.un, slot[j], un);
+      Tr::load_rec(t.un, slot[j], un);
       R v = R(0);
 #pragma unroll
       for (int r = 0; r < D; ++r) v = r_fma(ak[r], un[r], v);
       if constexpr (!STEADY) {
         R uo[D];
-        Tracer<D, R, STEADY>::load_rec(t.uo, slot[j], uo);
+        Tr::load_rec(t.uo, slot[j], uo);
         R vo = R(0);
 #pragma unroll
         for (int r = 0; r < D; ++r) vo = r_fma(ak[r], uo[r], vo);
@@ -272,7 +279,7 @@ struct Adjoint {
       for (int q = 0; q < D; ++q) z[0][q] = d[q];
       if (jj == 0) {
         R un[D];
-        Tracer<D, R, STEADY>::load_rec(t.un, home_slot, un);
+        Tr::load_rec(t.un, home_slot, un);
 #pragma unroll
         for (int q = 0; q < D; ++q) k[0][q] = un[q];
       } else {
@@ -336,15 +343,15 @@ struct Adjoint {
   }
 };
 
-template <int D, class R, bool STEADY>
+template <int D, class R, bool STEADY, int P>
 __global__ void __launch_bounds__(kAdvectThreads)
     k_adjoint(AdvectArgs args, AdjArgs aa, Tables<R> tab, int chunk0) {
   const int4 ck = args.chunks[chunk0 + int(blockIdx.x)];
   if (int(threadIdx.x) >= ck.w) return;
   const StepConsts<R>& K = consts<R>(args);
   const int npm = int(args.npm);
-  Adjoint<D, R, STEADY> ad;
-  Tracer<D, R, STEADY>& t = ad.t;
+  Adjoint<D, R, STEADY, P> ad;
+  Tracer<D, R, STEADY, P>& t = ad.t;
   t.geo = args.geo;
   t.tab = tab;
   t.N = args.N;
@@ -388,7 +395,7 @@ __global__ void __launch_bounds__(kAdvectThreads)
   const R g = static_cast<const R*>(aa.gT_new)[slot];
   if (g == R(0)) return;
   {
-    const int M = 2 * args.N;
+    const int M = P * args.N;
     bool iface = t.p[0] == M || t.p[D - 1] == 0;
 #pragma unroll
     for (int k = 1; k < D; ++k) iface = iface || t.p[k] == t.p[k - 1];
@@ -445,7 +452,10 @@ __global__ void k_scale_out(const unsigned long long* __restrict__ acc, R* __res
 
 template <int D, class R, bool STEADY>
 cudaError_t launch_adj_drs(const AdvectArgs& a, const AdjArgs& aa, Tables<R> t, cudaStream_t s) {
-  k_adjoint<D, R, STEADY><<<a.n_chunks, kAdvectThreads, 0, s>>>(a, aa, t, 0);
+  if (a.order == 1)
+    k_adjoint<D, R, STEADY, 1><<<a.n_chunks, kAdvectThreads, 0, s>>>(a, aa, t, 0);
+  else
+    k_adjoint<D, R, STEADY, 2><<<a.n_chunks, kAdvectThreads, 0, s>>>(a, aa, t, 0);
   return cudaGetLastError();
 }
 

@@ -147,8 +147,6 @@ elm_status elm_mesh_create(int dim, int64_t n_vertices, const double* vertex_xyz
   precision &= ~(ELM_HOST_ONLY | ELM_ADJOINT | ELM_P1 | ELM_DIFFUSION | ELM_HOST_STAGING);
   if (precision != ELM_FP64 && precision != ELM_FP32)
     return fail(ELM_ERR_ARG, "elm_mesh_create: precision must be ELM_FP64 or ELM_FP32");
-  if (order == 1 && with_adjoint)
-    return fail(ELM_ERR_ARG, "elm_mesh_create: the adjoint is built for P2 meshes only (ELM_P1 with ELM_ADJOINT)");
   // P1 puts one node lattice point per micro vertex, so it can go one level
   // finer than P2 for the same lattice (at most 2^10 points per edge in 2D,
   // 2^8 in 3D).

@@ -16,11 +16,16 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
 
 
+# the same 17^3 node lattice for both element orders
+LEVEL = {2: 3, 1: 4}
+
+
 class Pair:
-    def __init__(self, level, precision, mesh="cube"):
+    def __init__(self, level, precision, mesh="cube", order=2):
         v, m = inputs.unit_cube() if mesh == "cube" else inputs.unit_square()
-        self.om = oracle.OracleMesh(v, m, level)
-        self.gm = elm.Mesh(v, m, level, precision, adjoint=True)
+        self.om = oracle.OracleMesh(v, m, level, order=order)
+        self.gm = elm.Mesh(v, m, level, precision, adjoint=True, order=order)
+        self.order = order
         self.perm = match_nodes(self.om.coords, self.gm.unique_coords())
         self.x = self.om.coords
         self.precision = precision
@@ -63,9 +68,10 @@ def _fields(P, kind):
     return P.rounded(u), P.rounded(T)
 
 
+@pytest.mark.parametrize("order", [2, 1])
 @pytest.mark.parametrize("precision,n_sub", [("fp64", 1), ("fp64", 3), ("fp32", 1)])
-def test_transpose_matches_oracle(precision, n_sub):
-    P = Pair(3, precision)
+def test_transpose_matches_oracle(precision, n_sub, order):
+    P = Pair(LEVEL[order], precision, order=order)
     u, T = _fields(P, "fourier")
     dt = inputs.dt_for_cfl(4.0, 3, u)
     g = np.random.default_rng(1).standard_normal(P.om.n_nodes)
@@ -82,8 +88,9 @@ def test_transpose_matches_oracle(precision, n_sub):
     assert np.all(gT_old.cpu().numpy()[ghosts] == 0)
 
 
-def test_dot_product_identity_on_gpu():
-    P = Pair(3, "fp64")
+@pytest.mark.parametrize("order", [2, 1])
+def test_dot_product_identity_on_gpu(order):
+    P = Pair(LEVEL[order], "fp64", order=order)
     u, T = _fields(P, "fourier")
     dt = inputs.dt_for_cfl(4.0, 3, u)
     rng = np.random.default_rng(4)
@@ -95,11 +102,12 @@ def test_dot_product_identity_on_gpu():
     assert abs(lhs - rhs) <= 1e-12 * np.abs(a).sum() * np.abs(b).max()
 
 
-@pytest.mark.parametrize("kind,n_sub", [("linear", 1), ("linear", 2), ("fourier", 1), ("fourier", 2)])
-def test_velocity_gradient_matches_oracle_jvp(kind, n_sub):
+@pytest.mark.parametrize("kind,n_sub,order", [("linear", 1, 2), ("linear", 2, 2), ("fourier", 1, 2), ("fourier", 2, 2),
+                                              ("linear", 2, 1), ("fourier", 1, 1), ("fourier", 2, 1)])
+def test_velocity_gradient_matches_oracle_jvp(kind, n_sub, order):
     """<dL/du, v> from the GPU adjoint equals <g, dT/d eps> of the oracle's
     forward-mode derivative for 8 random directions v (L = <g, T_new>)."""
-    P = Pair(3, "fp64")
+    P = Pair(LEVEL[order], "fp64", order=order)
     u, T = _fields(P, kind)
     dt = inputs.dt_for_cfl(3.0, 3, u)
     rng = np.random.default_rng(5)
@@ -114,8 +122,9 @@ def test_velocity_gradient_matches_oracle_jvp(kind, n_sub):
         assert abs(lhs - rhs) <= 1e-9 * (np.abs(g) @ np.abs(jvp) + 1e-30)
 
 
-def test_velocity_gradient_time_dependent_split():
-    P = Pair(3, "fp64")
+@pytest.mark.parametrize("order", [2, 1])
+def test_velocity_gradient_time_dependent_split(order):
+    P = Pair(LEVEL[order], "fp64", order=order)
     rng = np.random.default_rng(8)
     u0, T = _fields(P, "fourier")
     # a generic shift: no stage point runs exactly along a face of the box
@@ -135,10 +144,14 @@ def test_velocity_gradient_time_dependent_split():
         assert abs((gU1 * v).sum() - g @ j1) <= 1e-9 * (np.abs(g) @ np.abs(j1) + 1e-30)
 
 
-def test_velocity_gradient_finite_differences_gpu():
-    """Central differences of the GPU forward step on P2-exact (linear) fields."""
-    P = Pair(3, "fp64")
+@pytest.mark.parametrize("order", [2, 1])
+def test_velocity_gradient_finite_differences_gpu(order):
+    """Central differences of the GPU forward step on fields the elements
+    represent exactly (linear u; quadratic T for P2, linear T for P1)."""
+    P = Pair(LEVEL[order], "fp64", order=order)
     u, T = _fields(P, "linear")
+    if order == 1:
+        T = P.x @ np.array([0.3, -0.2, 0.5]) + 0.1
     dt = 0.04
     rng = np.random.default_rng(3)
     g = rng.standard_normal(P.om.n_nodes)
