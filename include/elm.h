@@ -77,8 +77,7 @@ enum { ELM_ADJOINT = 0x200 };
  * setup; Tables 1 and 3 use P1).  The location is the same; a field is
  * evaluated from the d+1 vertices of the micro simplex with the micro
  * barycentrics as basis.  Combinable with ELM_ADJOINT (the adjoint then
- * differentiates the P1 interpolants); P1 meshes are not accepted by
- * elm_batch_create. */
+ * differentiates the P1 interpolants) and with the batched form. */
 enum { ELM_P1 = 0x400 };
 
 /* Flag OR-ed into `precision` of elm_mesh_create: also build the diffusion
@@ -317,12 +316,13 @@ elm_status elm_diffusion_step(elm_mesh mesh, const void* c_hat_dev, const void* 
 elm_status elm_get_status(elm_mesh mesh, void* stream);
 
 /* ---- Batched form: many independent advection instances in one launch ----
- * Each instance is a P2 mesh with its own level, dimension, velocity
+ * Each instance is a P2 or P1 mesh with its own level, dimension, velocity
  * (elm_set_velocity on that mesh), dt and n_sub; every instance performs the
  * step of elm_advect (Algorithm 1, lines 3-4).  One persistent kernel takes
  * (instance, chunk) items from a shared work list, so small and large
- * instances share the GPU in a single launch.  The paper has no batched
- * form; it traces one field per run.
+ * instances share the GPU in a single launch (one launch per element order
+ * present: P2 instances first, then P1).  The paper has no batched form; it
+ * traces one field per run.
  *
  * elm_batch_create: count in 1..128 meshes, all of one precision and device,
  * borrowed (they must outlive the batch).  blocks_per_sm sets the persistent
@@ -336,8 +336,8 @@ int64_t elm_batch_num_items(elm_batch batch);
  * T_old, T_new, dt, n_sub are host arrays of `count` entries (device
  * pointers in storage layout, mesh precision).  Their values are copied into
  * the launch's parameters, so the call can be captured in a CUDA graph and
- * replayed with the same pointers.  Zeroes a device counter and launches
- * one kernel on `stream`; allocates nothing.  Each instance's device flags
+ * replayed with the same pointers.  Zeroes the device counters and launches
+ * one kernel per element order present on `stream`; allocates nothing.  Each instance's device flags
  * are reported by elm_get_status on its mesh. */
 elm_status elm_batch_advect(elm_batch batch, const void* const* T_old, void* const* T_new, const double* dt,
                             const int* n_sub, void* stream);

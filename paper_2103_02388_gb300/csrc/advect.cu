@@ -85,7 +85,9 @@ __global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
 // Persistent batched kernel: each block repeatedly takes the next (instance,
 // chunk) item from the work list and advects that chunk's nodes with the
 // instance's tables and this call's constants.  Dimension and steadiness are
-// per instance and uniform within a block.
+// per instance and uniform within a block; the element order P is per launch
+// (a batch that mixes P1 and P2 instances runs one launch per order over its
+// own part of the work list).
 template <class R>
 __device__ __forceinline__ Tables<R> tables_of(const BatchStatic& S);
 template <>
@@ -97,19 +99,19 @@ __device__ __forceinline__ Tables<double> tables_of<double>(const BatchStatic& S
 #define ELM_BATCH_MIN_BLOCKS 6
 #endif
 
-template <class R>
+template <class R, int P>
 __global__ void __launch_bounds__(kAdvectThreads, ELM_BATCH_MIN_BLOCKS)
-    k_advect_batch(const __grid_constant__ BatchParams<R> P) {
+    k_advect_batch(const __grid_constant__ BatchParams<R> B) {
   __shared__ int s_item;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(P.counter, 1);
+    if (threadIdx.x == 0) s_item = atomicAdd(B.counter, 1);
     __syncthreads();
     const int it = s_item;
     __syncthreads();
-    if (it >= P.n_items) return;
-    const int2 w = P.items[it];
-    const BatchStatic& S = P.inst[w.x];
-    const BatchCall<R>& C = P.call[w.x];
+    if (it >= B.n_items) return;
+    const int2 w = B.items[it];
+    const BatchStatic& S = B.inst[w.x];
+    const BatchCall<R>& C = B.call[w.x];
     const int4 ck = S.chunks[w.y];
     if (int(threadIdx.x) < ck.w) {
       const NodeJob<R> job{S.geo,
@@ -125,12 +127,13 @@ __global__ void __launch_bounds__(kAdvectThreads, ELM_BATCH_MIN_BLOCKS)
                            S.npm,
                            C.n_sub};
       const Tables<R> tab = tables_of<R>(S);
+      const int tid = int(threadIdx.x);
       if (S.dim == 3) {
-        if (C.steady) advect_node<3, R, true>(job, tab, ck, int(threadIdx.x));
-        else advect_node<3, R, false>(job, tab, ck, int(threadIdx.x));
+        if (C.steady) advect_node<3, R, true, P>(job, tab, ck, tid);
+        else advect_node<3, R, false, P>(job, tab, ck, tid);
       } else {
-        if (C.steady) advect_node<2, R, true>(job, tab, ck, int(threadIdx.x));
-        else advect_node<2, R, false>(job, tab, ck, int(threadIdx.x));
+        if (C.steady) advect_node<2, R, true, P>(job, tab, ck, tid);
+        else advect_node<2, R, false, P>(job, tab, ck, tid);
       }
     }
   }
@@ -224,13 +227,15 @@ cudaError_t launch_advect(int dim, int precision, const AdvectArgs& a, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch32(const BatchParams<float>& p, int grid, cudaStream_t s) {
-  k_advect_batch<float><<<grid, kAdvectThreads, 0, s>>>(p);
+cudaError_t launch_batch32(const BatchParams<float>& p, int order, int grid, cudaStream_t s) {
+  if (order == 1) k_advect_batch<float, 1><<<grid, kAdvectThreads, 0, s>>>(p);
+  else k_advect_batch<float, 2><<<grid, kAdvectThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch64(const BatchParams<double>& p, int grid, cudaStream_t s) {
-  k_advect_batch<double><<<grid, kAdvectThreads, 0, s>>>(p);
+cudaError_t launch_batch64(const BatchParams<double>& p, int order, int grid, cudaStream_t s) {
+  if (order == 1) k_advect_batch<double, 1><<<grid, kAdvectThreads, 0, s>>>(p);
+  else k_advect_batch<double, 2><<<grid, kAdvectThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 

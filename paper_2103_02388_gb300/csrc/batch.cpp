@@ -15,6 +15,7 @@ struct elm_batch_s {
   int device = 0;
   int grid = 0;
   int n_items = 0;
+  int n_items_p2 = 0;    // the work list holds the P2 instances' items first, then the P1 ones
   std::vector<elm_mesh> meshes;
   elm::BatchStatic* d_inst = nullptr;
   int2* d_items = nullptr;
@@ -70,10 +71,7 @@ elm_status launch(elm_batch_s* b, const void* const* T_old, void* const* T_new, 
   elm::BatchParams<R>* P = new (std::nothrow) elm::BatchParams<R>();
   if (!P) return bfail(ELM_ERR_ARG, "elm_batch_advect: out of host memory");
   P->inst = b->d_inst;
-  P->items = b->d_items;
-  P->n_items = b->n_items;
   P->count = b->count;
-  P->counter = b->d_counter;
   for (int k = 0; k < b->count; ++k) {
     const elm_mesh_s* me = b->meshes[k];
     elm::BatchCall<R>& c = P->call[k];
@@ -85,10 +83,17 @@ elm_status launch(elm_batch_s* b, const void* const* T_old, void* const* T_new, 
     c.n_sub = n_sub[k];
     fill_consts(c.K, me, dt[k], n_sub[k]);
   }
-  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
-  if (e == cudaSuccess) {
-    if constexpr (sizeof(R) == 4) e = elm::launch_batch32(*P, b->grid, s);
-    else e = elm::launch_batch64(*P, b->grid, s);
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), s);
+  // one persistent launch per element order present, each over its part of
+  // the work list with its own counter
+  const int part[2][2] = {{0, b->n_items_p2}, {b->n_items_p2, b->n_items}};
+  for (int o = 0; o < 2 && e == cudaSuccess; ++o) {
+    if (part[o][1] == part[o][0]) continue;
+    P->items = b->d_items + part[o][0];
+    P->n_items = part[o][1] - part[o][0];
+    P->counter = b->d_counter + o;
+    if constexpr (sizeof(R) == 4) e = elm::launch_batch32(*P, o == 0 ? 2 : 1, b->grid, s);
+    else e = elm::launch_batch64(*P, o == 0 ? 2 : 1, b->grid, s);
   }
   delete P;
   if (e != cudaSuccess) return bfail(ELM_ERR_CUDA, std::string("elm_batch_advect: ") + cudaGetErrorString(e));
@@ -109,8 +114,6 @@ elm_status elm_batch_create(const elm_mesh* meshes, int count, int blocks_per_sm
     if (meshes[k]->host_only) return bfail(ELM_ERR_STATE, "elm_batch_create: host-only mesh " + std::to_string(k));
     if (meshes[k]->blend.nsec > 0)
       return bfail(ELM_ERR_ARG, "elm_batch_create: blended meshes are not batched (mesh " + std::to_string(k) + ")");
-    if (meshes[k]->order != 2)
-      return bfail(ELM_ERR_ARG, "elm_batch_create: the batched form takes P2 meshes only (mesh " + std::to_string(k) + ")");
     if (meshes[k]->precision != meshes[0]->precision)
       return bfail(ELM_ERR_ARG, "elm_batch_create: all meshes must share one precision");
     if (meshes[k]->device != meshes[0]->device)
@@ -137,14 +140,19 @@ elm_status elm_batch_create(const elm_mesh* meshes, int count, int blocks_per_sm
     const elm_mesh_s* me = meshes[k];
     inst[k] = elm::BatchStatic{me->d_geo, me->d_geo32, me->d_unique_map, me->d_owner_mp, me->d_chunks,
                                me->d_status, me->N, int(me->npm), me->dim, 0};
-    for (int64_t c = 0; c < me->n_chunks; ++c) items.push_back(make_int2(k, int(c)));
+  }
+  for (int order : {2, 1}) {
+    for (int k = 0; k < count; ++k)
+      if (meshes[k]->order == order)
+        for (int64_t c = 0; c < meshes[k]->n_chunks; ++c) items.push_back(make_int2(k, int(c)));
+    if (order == 2) b->n_items_p2 = int(items.size());
   }
   b->n_items = int(items.size());
   e = cudaMalloc(&b->d_inst, sizeof(elm::BatchStatic) * count);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_inst, inst.data(), sizeof(elm::BatchStatic) * count, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int2) * items.size());
   if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 2 * sizeof(int));
   if (e != cudaSuccess) {
     free_batch(b);
     delete b;

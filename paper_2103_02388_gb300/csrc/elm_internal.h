@@ -307,7 +307,7 @@ struct AdjointBuffers {
 cudaError_t launch_adjoint(int dim, int precision, const AdvectArgs& a, const AdjointBuffers& b,
                            const void* gT_new, void* gT_old, void* gU_old, void* gU_new, cudaStream_t s);
 
-cudaError_t launch_batch32(const BatchParams<float>& p, int grid, cudaStream_t s);
-cudaError_t launch_batch64(const BatchParams<double>& p, int grid, cudaStream_t s);
+cudaError_t launch_batch32(const BatchParams<float>& p, int order, int grid, cudaStream_t s);
+cudaError_t launch_batch64(const BatchParams<double>& p, int order, int grid, cudaStream_t s);
 
 }  // namespace elm

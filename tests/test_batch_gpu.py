@@ -1,5 +1,6 @@
-"""Batched form: one persistent launch over many independent instances must
-give, for every instance, bitwise the result of its own elm_advect call;
+"""Batched form: one persistent launch (per element order) over many
+independent P2 and P1 instances must give, for every instance, bitwise the
+result of its own elm_advect call;
 CUDA-graph replay of a batched time loop must equal the eager loop."""
 import numpy as np
 import pytest
@@ -13,12 +14,15 @@ pytestmark = pytest.mark.gpu
 
 
 def _instances(precision):
-    specs = [("square", 3, "rotation", 1.5, 1), ("cube", 2, "fourier", 4.0, 2), ("square", 5, "fourier", 8.0, 1),
-             ("cube", 3, "rotation", 0.5, 3), ("cube_block", 1, "fourier", 6.0, 1), ("square_block", 2, "rotation", 2.0, 2)]
+    # (mesh, level, velocity, CFL, n_sub, element order): P2 and P1 instances mixed
+    specs = [("square", 3, "rotation", 1.5, 1, 2), ("cube", 2, "fourier", 4.0, 2, 2), ("square", 5, "fourier", 8.0, 1, 2),
+             ("cube", 3, "rotation", 0.5, 3, 2), ("cube_block", 1, "fourier", 6.0, 1, 2),
+             ("square_block", 2, "rotation", 2.0, 2, 2), ("cube", 4, "fourier", 4.0, 1, 1),
+             ("square", 6, "rotation", 3.0, 2, 1), ("cube_block", 2, "fourier", 5.0, 1, 1)]
     out = []
-    for k, (mesh, level, vel, cfl, n_sub) in enumerate(specs):
+    for k, (mesh, level, vel, cfl, n_sub, order) in enumerate(specs):
         v, m = mesh_for(mesh)
-        gm = elm.Mesh(v, m, level, precision)
+        gm = elm.Mesh(v, m, level, precision, order=order)
         x = gm.node_coords()
         u = (inputs.rotation_2d(x) if x.shape[1] == 2 else inputs.rotation_3d(x)) if vel == "rotation" \
             else inputs.random_fourier(x, seed=10 + k)
