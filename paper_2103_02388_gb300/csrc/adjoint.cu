@@ -110,7 +110,7 @@ struct Adjoint {
       ax[k] = k;
     }
     auto cswap = [&](int i, int j) {
-      if (fs[j] > fs[i]) {
+      if (r_greater(fs[j], fs[i])) {
         R tmp = fs[i]; fs[i] = fs[j]; fs[j] = tmp;
         int u = ax[i]; ax[i] = ax[j]; ax[j] = u;
       }

@@ -21,8 +21,15 @@ constexpr float kBand32 = 3e-5f;    // FP32 tie band re-decided in FP64, lattice
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int f2i_exact(float x) { return __float2int_rn(x); }
 __device__ __forceinline__ float i2f_exact(int i) { return __int2float_rn(i); }
+// The FP64 forms below run on the integer pipe: this GPU's FP64 pipe (2
+// lanes per SM and cycle) bounds the FP64 kernels, while their integer pipe
+// idles.  Each gives the FP64 instruction's result on the operands it meets.
+// Cell index of an integer-valued double 0 <= x < 2^21 (a located cell),
+// read from its exponent and leading mantissa bits.
 __device__ __forceinline__ int f2i_exact(double x) {
-  return int(__double_as_longlong(x + 6755399441055744.0) - 0x4338000000000000LL);
+  const int hi = __double2hiint(x);
+  const int e = (hi >> 20) - 1023;  // x = +0: e < 0
+  return e < 0 ? 0 : (((hi & 0xFFFFF) | 0x100000) >> (20 - e));
 }
 __device__ __forceinline__ double i2f_exact_d(int i) {
   return __longlong_as_double(0x4338000000000000LL + i) - 6755399441055744.0;
@@ -43,13 +50,41 @@ __device__ __forceinline__ float floor_small(float x) {
 
 // Precision-exact math: the float overloads never promote to FP64.
 __device__ __forceinline__ float r_floor(float x) { return floorf(x); }
-__device__ __forceinline__ double r_floor(double x) { return ::floor(x); }
+// floor of a finite double by clearing its fraction bits (one FP64
+// subtraction only for negative non-integers).
+__device__ __forceinline__ double r_floor(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = int((b >> 52) & 0x7FF) - 1023;
+  if (e >= 52) return x;                                           // integer already
+  if (e < 0) return b < 0 ? ((b << 1) == 0 ? x : -1.0) : 0.0;      // |x| < 1 (floor(-0) = -0)
+  const long long frac = (1LL << (52 - e)) - 1;
+  if ((b & frac) == 0) return x;
+  const double t = __longlong_as_double(b & ~frac);                // trunc(x)
+  return b < 0 ? t - 1.0 : t;
+}
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return ::fma(a, b, c); }
 __device__ __forceinline__ float r_clamp(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 __device__ __forceinline__ float r_min(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double r_min(double a, double b) { return ::fmin(a, b); }
-__device__ __forceinline__ double r_clamp(double x, double lo, double hi) { return ::fmin(::fmax(x, lo), hi); }
+// Order-preserving integer image of a double that is not NaN: x < y exactly
+// when d_key(x) < d_key(y) (-0 just below +0).
+__device__ __forceinline__ long long d_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+// clamp(x, lo, hi) for lo <= hi by integer compares; like fmin(fmax(x, lo),
+// hi) it returns a bound, never NaN, for a NaN x.
+__device__ __forceinline__ double r_clamp(double x, double lo, double hi) {
+  const long long k = d_key(x);
+  if (k < d_key(lo)) return lo;
+  return k > d_key(hi) ? hi : x;
+}
+// a > b for doubles that are not NaN, by an integer compare.
+__device__ __forceinline__ bool r_greater(double a, double b) { return d_key(a) > d_key(b); }
+__device__ __forceinline__ bool r_greater(float a, float b) { return a > b; }
+__device__ __forceinline__ bool r_geq(double a, double b) { return d_key(a) >= d_key(b); }
+__device__ __forceinline__ bool r_geq(float a, float b) { return a >= b; }
 
 // ---------------------------------------------------------------------------
 // Double-float helpers (error-free transformations; no FP64 instructions).
@@ -541,13 +576,15 @@ struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
       l[D] = c[D - 1] + f[D - 1];
       // common case: inside the block's macro, clear of its interior faces.
       // With every l >= 0 the cell is in range except on the face q1 = N
-      // (c1 = N), which the retraction clamps.
+      // (c1 = N) and where a tiny negative r (|r| below half an ulp of 1)
+      // made f = r - floor(r) round up to 1 with c = -1 in the last axis
+      // (l_d = c + f = 0 hides it); the retraction clamps both.
       {
         bool in = m == mb;
 #pragma unroll
-        for (int k = 0; k <= D; ++k) in = in && l[k] >= bo[k];
+        for (int k = 0; k <= D; ++k) in = in && r_geq(l[k], bo[k]);
         if (in) {
-          if (c[0] > Nf - R(1)) retract(c, f);
+          if (c[0] > Nf - R(1) || c[D - 1] < R(0)) retract(c, f);
           return;
         }
       }
@@ -722,7 +759,7 @@ struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
       for (int k = 0; k < D; ++k) fs[k] = f[k];
     }
     auto cswap = [&](int i, int j) {
-      if (fs[j] > fs[i]) {
+      if (r_greater(fs[j], fs[i])) {
         R t = fs[i]; fs[i] = fs[j]; fs[j] = t;
 #pragma unroll
         for (int o = 0; o < 3; ++o) { int u = A[i][o]; A[i][o] = A[j][o]; A[j][o] = u; }
@@ -808,7 +845,7 @@ struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
       for (int k = 0; k < D; ++k) fs[k] = f[k];
     }
     auto cswap = [&](int i, int j) {
-      if (fs[j] > fs[i]) {
+      if (r_greater(fs[j], fs[i])) {
         R t = fs[i]; fs[i] = fs[j]; fs[j] = t;
         int u0 = B[i][0]; B[i][0] = B[j][0]; B[j][0] = u0;
         int u1 = B[i][1]; B[i][1] = B[j][1]; B[j][1] = u1;
