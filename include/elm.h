@@ -174,7 +174,11 @@ elm_status elm_set_velocity(elm_mesh mesh, const void* u_old_dev, const void* u_
  * steps of tau with s RK4 substeps each and interpolating T^{n+1-b} is
  * exactly elm_advect(T^{n+1-b}, b*tau, b*s); b = infinity is T^0 with
  * dt = t_{n+1} (one trace over the whole time, no interpolation error
- * accumulated between steps). */
+ * accumulated between steps).
+ * Each node is computed once, by its owner copy (Sec. 2.3.1: one owner per
+ * degree of freedom); a second launch copies the result to the node's other
+ * storage copies, so all copies hold the same value.  Two kernel launches
+ * on `stream`; allocates nothing. */
 elm_status elm_advect(elm_mesh mesh, const void* T_old_dev, void* T_new_dev, double dt, int n_sub,
                       void* stream);
 
@@ -270,14 +274,15 @@ elm_status elm_advect_adjoint(elm_mesh mesh, const void* T_old_dev, const void* 
  *               node continues from the offset of the node's owner copy and
  *               all copies receive the same result.
  *  1 <= n_sub <= ELM_MAX_SUBSTEPS; dt finite and >= 0.
- * One kernel launch on `stream`; allocates nothing; device conditions go to
- * elm_get_status as for elm_advect. */
+ * Two kernel launches on `stream` (the traces, then the copy of each
+ * interface node's result to its other storage copies); allocates nothing;
+ * device conditions go to elm_get_status as for elm_advect. */
 elm_status elm_trace(elm_mesh mesh, const void* D_in_dev, void* D_out_dev, double dt, int n_sub, void* stream);
 
 /* T_dst[i] = T_src_h(x_i + D[i]) (Sec. 2.3.1, step (iii), at the end of
  * traces made by elm_trace).  D is [n, dim], T_src and T_dst [n] (must not
- * overlap), storage layout, mesh precision.  Needs no velocity.  One kernel
- * launch on `stream`; allocates nothing. */
+ * overlap), storage layout, mesh precision.  Needs no velocity.  Two kernel
+ * launches on `stream` (evaluation, interface copies); allocates nothing. */
 elm_status elm_trace_eval(elm_mesh mesh, const void* D_dev, const void* T_src_dev, void* T_dst_dev, void* stream);
 
 /* ---- Diffusion step (Sec. 2.2, Eq. finite-dimensional Galerkin approximation
