@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cfloat>
 #include <type_traits>
 
 #include "elm_internal.h"
@@ -26,10 +27,11 @@ __device__ __forceinline__ float i2f_exact(int i) { return __int2float_rn(i); }
 // idles.  Each gives the FP64 instruction's result on the operands it meets.
 // Cell index of an integer-valued double 0 <= x < 2^21 (a located cell),
 // read from its exponent and leading mantissa bits.
+// (Anything else, NaN included, gives an index in [0, 2^21).)
 __device__ __forceinline__ int f2i_exact(double x) {
   const int hi = __double2hiint(x);
   const int e = (hi >> 20) - 1023;  // x = +0: e < 0
-  return e < 0 ? 0 : (((hi & 0xFFFFF) | 0x100000) >> (20 - e));
+  return (e < 0 || e > 20) ? 0 : (((hi & 0xFFFFF) | 0x100000) >> (20 - e));
 }
 __device__ __forceinline__ double i2f_exact_d(int i) {
   return __longlong_as_double(0x4338000000000000LL + i) - 6755399441055744.0;
@@ -80,7 +82,9 @@ __device__ __forceinline__ double r_clamp(double x, double lo, double hi) {
   if (k < d_key(lo)) return lo;
   return k > d_key(hi) ? hi : x;
 }
-// a > b for doubles that are not NaN, by an integer compare.
+// a > b and a >= b for doubles that are not NaN, by integer compares.  The
+// location only meets finite values: every point it is given has passed the
+// clamp, which maps a NaN or infinite coordinate to a bound.
 __device__ __forceinline__ bool r_greater(double a, double b) { return d_key(a) > d_key(b); }
 __device__ __forceinline__ bool r_greater(float a, float b) { return a > b; }
 __device__ __forceinline__ bool r_geq(double a, double b) { return d_key(a) >= d_key(b); }
@@ -584,7 +588,7 @@ struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
 #pragma unroll
         for (int k = 0; k <= D; ++k) in = in && r_geq(l[k], bo[k]);
         if (in) {
-          if (c[0] > Nf - R(1) || c[D - 1] < R(0)) retract(c, f);
+          if (r_greater(c[0], Nf - R(1)) || r_greater(R(0), c[D - 1])) retract(c, f);
           return;
         }
       }
@@ -877,10 +881,17 @@ struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
       // the annulus: radius clamped to [r_min, r_max] (Euclidean projection)
       const double y0 = this->xp[0] + d[0], y1 = this->xp[1] + d[1];
       const double r = sqrt(y0 * y0 + y1 * y1);
-      if (r < this->bl.rmin || r > this->bl.rmax) {
-        const double s = r > 0.0 ? fmin(fmax(r, this->bl.rmin), this->bl.rmax) / r : 0.0;
-        d[0] = (r > 0.0 ? s * y0 : this->bl.rmin) - this->xp[0];
-        d[1] = s * y1 - this->xp[1];
+      if (!(r >= this->bl.rmin && r <= this->bl.rmax)) {
+        if (r > 0.0 && r <= DBL_MAX) {
+          const double s = fmin(fmax(r, this->bl.rmin), this->bl.rmax) / r;
+          d[0] = s * y0 - this->xp[0];
+          d[1] = s * y1 - this->xp[1];
+        } else {
+          // the centre, or a non-finite point (a NaN or infinite velocity):
+          // the point (r_min, 0), so that no later location sees a NaN
+          d[0] = this->bl.rmin - this->xp[0];
+          d[1] = -this->xp[1];
+        }
       }
       return;
     }

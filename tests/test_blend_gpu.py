@@ -180,3 +180,23 @@ def test_table4_advection_diffusion_gpu(kappa):
             assert abs(got.max() / ex.max() - 1.0 - ref["e_peak"]) < 1e-3
         else:
             assert ref["h0"] / 2.5 < h0 < 2.5 * ref["h0"]
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_blended_nonfinite_velocity_is_reported(bad):
+    """A NaN or infinite velocity on the annulus is a status flag: the radial
+    projection maps a non-finite point back onto the annulus, so every
+    location sees a finite point and the step's other values stay finite."""
+    v, m = inputs.annulus_ring(6, 2)
+    gm = elm.Mesh(v, m, 3, "fp64", annulus=ANN)
+    x = torch.tensor(gm.node_coords(), dtype=torch.float64, device="cuda")
+    u = torch.stack([-x[:, 1], x[:, 0]], dim=1).contiguous()
+    u[11, 0] = bad
+    gm.set_velocity(u)
+    T = torch.ones(gm.n_nodes, dtype=torch.float64, device="cuda")
+    out = gm.advect(T, 0.05, 2)
+    with pytest.raises(_lib.ElmError) as e:
+        gm.status()
+    assert e.value.status == _lib.ELM_ERR_NONFINITE
+    assert bool(torch.isfinite(out).all())
+    gm.status()  # flags were cleared
