@@ -190,7 +190,9 @@ template <int D, int P>
 __device__ __forceinline__ void node_position64(const MacroGeo* geo, int m0, int p0, int p1, int p2, int N,
                                                 double* x) {
   const MacroGeo& g0 = geo[m0];
-  const double invM = 1.0 / double(P * N);
+  // 1 / M, M = 2^k: the exponent field set directly (an FP64 division would
+  // take dozens of instructions on the narrow FP64 pipe)
+  const double invM = __longlong_as_double(static_cast<long long>(1024 - __ffs(P * N)) << 52);
   const double s[3] = {double(p0) * invM, double(p1) * invM, double(p2) * invM};
 #pragma unroll
   for (int r = 0; r < D; ++r) {
