@@ -607,6 +607,65 @@ def _lookback_chain(me, c0, u, steps, b):
     return T
 
 
+def test_p1_transpose_dot_product():
+    """<W a, b> = <a, W^T b>: the P1 transpose scatters with the weights the
+    P1 step gathers with."""
+    me = _setup_p1(3, 3)
+    rng = np.random.default_rng(13)
+    u = inputs.random_fourier(me.coords, seed=8)
+    dt = inputs.dt_for_cfl(2.0, 2, u)
+    a = rng.standard_normal(me.n_nodes)
+    b = rng.standard_normal(me.n_nodes)
+    lhs = me.advect(a, u, dt, n_sub=2) @ b
+    rhs = a @ me.advect_transpose(b, u, dt, n_sub=2)
+    assert abs(lhs - rhs) <= 1e-13 * np.abs(a).sum() * np.abs(b).max()
+
+
+@pytest.mark.parametrize("dim,n_sub", [(2, 1), (3, 2)])
+def test_p1_jvp_uniform_velocity_closed_form(dim, n_sub):
+    """P1, u and the direction v uniform, T linear (exact in P1): X = x - dt u,
+    so dT/deps = -dt v . grad T, the constant gradient."""
+    me = _setup_p1(dim, 3)
+    x = me.coords
+    U = np.array([0.3, -0.2, 0.1][:dim])
+    V = np.array([0.1, 0.2, -0.3][:dim])
+    g = np.array([0.7, -0.4, 0.25][:dim])
+    T = x @ g + 0.3
+    dt = 0.2
+    _, jvp = me.advect_jvp(T, inputs.uniform_field(x, U), inputs.uniform_field(x, V), dt, n_sub)
+    X = x - dt * U
+    inside = np.all((X > 1e-9) & (X < 1 - 1e-9), axis=1)
+    assert inside.sum() > 20
+    assert np.abs(jvp[inside] - (-dt * V) @ g).max() <= 1e-12
+
+
+@pytest.mark.parametrize("dim,steady", [(2, True), (3, False)])
+def test_p1_jvp_linear_fields_match_finite_differences(dim, steady):
+    """P1 with linear u, direction and T (all exact in P1): the step is smooth
+    away from the box clamp, so forward mode equals central differences."""
+    me = _setup_p1(dim, 4 if dim == 3 else 5)
+    x = me.coords
+    c = np.full(dim, 0.5)
+    rng = np.random.default_rng(17)
+    A = rng.standard_normal((dim, dim))
+    u0 = inputs.linear_field(x, A, c)
+    du0 = inputs.linear_field(x, rng.standard_normal((dim, dim)), c)
+    u1 = None if steady else inputs.linear_field(x, A + 0.5 * rng.standard_normal((dim, dim)), c)
+    du1 = None if steady else inputs.linear_field(x, rng.standard_normal((dim, dim)), c)
+    T = x @ rng.standard_normal(dim)
+    dt = 0.05
+    _, jvp = me.advect_jvp(T, u0, du0, dt, 2, u_new=u1, du_new=du1)
+    e = 1e-6
+
+    def step(s):
+        return me.advect(T, u0 + s * du0, dt, 2, u_new=None if steady else u1 + s * du1)
+
+    fd = (step(e) - step(-e)) / (2 * e)
+    inner = np.linalg.norm(x - c, axis=1) < 0.3
+    assert inner.sum() > 20
+    assert np.abs(fd[inner] - jvp[inner]).max() <= 1e-7 * max(1.0, np.abs(jvp[inner]).max())
+
+
 @pytest.mark.parametrize("b", [100, 1000, "infinity"])
 def test_table1_three_bodies_p1(b):
     """Table 1, P1 rows: H0 to 2%, var to 0.002; b = infinity at round-off."""
