@@ -95,7 +95,9 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
         return ELM_ERR_ARG;
       }
     }
-    std::sort(v.begin(), v.begin() + d + 1);
+    // ascending ids (at most 4: insertion sort)
+    for (int i = 1; i <= d; ++i)
+      for (int j = i; j > 0 && v[j - 1] > v[j]; --j) std::swap(v[j - 1], v[j]);
     for (int k = 0; k < d; ++k)
       if (v[k] == v[k + 1]) {
         *err = "macro " + std::to_string(m) + ": repeated vertex";
