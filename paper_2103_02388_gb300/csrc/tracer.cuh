@@ -394,6 +394,38 @@ struct BlendState {
 };
 struct NoBlendState {};
 
+// Kuhn ordering of the cell fractions f (descending, ties by axis): sigma0
+// and sigma1, the sorted fractions fs0 >= fs1 >= fs2, and the P2 basis values
+// of the micro simplex's vertices (v0..v3) and edges (01 02 03 12 13 23).
+struct KuhnP2 {
+  bool first0, first1;  // sigma0 = 0, sigma0 = 1 (else 2)
+  bool sec2, sec1;      // sigma1 = 2, sigma1 = 1 (else 0)
+};
+template <class R>
+__device__ __forceinline__ KuhnP2 kuhn_p2_3d(const R* f, R* phi) {
+  KuhnP2 o;
+  const bool g01 = f[1] > f[0], g02 = f[2] > f[0], g12 = f[2] > f[1];
+  o.first0 = !g01 && !g02;
+  o.first1 = !o.first0 && !g12;
+  o.sec2 = o.first0 ? g12 : (o.first1 ? g02 : false);
+  o.sec1 = o.first0 ? !g12 : (o.first1 ? false : g01);
+  const R fs0 = o.first0 ? f[0] : (o.first1 ? f[1] : f[2]);
+  const R fs1 = o.sec2 ? f[2] : (o.sec1 ? f[1] : f[0]);
+  const R fs2 = r_min(r_min(f[0], f[1]), f[2]);
+  const R L0 = R(1) - fs0, L1 = fs0 - fs1, L2 = fs1 - fs2, L3 = fs2;
+  phi[0] = L0 * (R(2) * L0 - R(1));
+  phi[1] = L1 * (R(2) * L1 - R(1));
+  phi[2] = L2 * (R(2) * L2 - R(1));
+  phi[3] = L3 * (R(2) * L3 - R(1));
+  phi[4] = R(4) * L0 * L1;
+  phi[5] = R(4) * L0 * L2;
+  phi[6] = R(4) * L0 * L3;
+  phi[7] = R(4) * L1 * L2;
+  phi[8] = R(4) * L1 * L3;
+  phi[9] = R(4) * L2 * L3;
+  return o;
+}
+
 template <int D, class R, bool STEADY, int P = 2, int BLEND = 0>
 struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
   static_assert(BLEND == 0 || (D == 2 && sizeof(R) == 8), "blending: 2D FP64 only");
@@ -678,6 +710,7 @@ struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
   // valid micro simplex.  (The FP64 kernel keeps the sorting form: its extra
   // FP64 min operations would load the narrow FP64 pipe.)
   __device__ void stencil_p2_3d(const R* c, const R* f, int* slot, R* phi) const {
+    static_assert(NB == 10, "3D P2 stencil");
     const int k0 = 2 * f2i_exact(c[0]);
     const int k1 = 2 * f2i_exact(c[1]);
     const int k2 = 2 * f2i_exact(c[2]);
@@ -688,18 +721,12 @@ struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
     const int S0 = tri3(k0) + tri2(k1) + k2 + m * npm;
     const int S1 = S0 + d10 + d11 + 1;
     const int S2 = S0 + d20 + d21 + 2;
-    const bool g01 = f[1] > f[0], g02 = f[2] > f[0], g12 = f[2] > f[1];
-    const bool first0 = !g01 && !g02;      // sigma0 = 0
-    const bool first1 = !first0 && !g12;   // sigma0 = 1 (else 2)
-    const bool sec2 = first0 ? g12 : (first1 ? g02 : false);   // sigma1 = 2
-    const bool sec1 = first0 ? !g12 : (first1 ? false : g01);  // sigma1 = 1 (else 0)
+    const KuhnP2 o = kuhn_p2_3d(f, phi);
+    const bool first0 = o.first0, first1 = o.first1, sec2 = o.sec2, sec1 = o.sec1;
     const int a1 = first0 ? d10 : (first1 ? d11 : 1);
     const int a2 = first0 ? d20 : (first1 ? d21 : 2);
     const int b1 = sec2 ? 1 : (sec1 ? d11 : d10);
     const int b2 = sec2 ? 2 : (sec1 ? d21 : d20);
-    const R fs0 = first0 ? f[0] : (first1 ? f[1] : f[2]);
-    const R fs1 = sec2 ? f[2] : (sec1 ? f[1] : f[0]);
-    const R fs2 = r_min(r_min(f[0], f[1]), f[2]);
     const int v1 = S0 + a2;
     const int e01 = S0 + a1;
     const int e13 = S1 + a2 - a1;
@@ -713,17 +740,6 @@ struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
     slot[7] = v1 + b1;
     slot[8] = e13;
     slot[9] = e13 + b2 - b1;
-    const R L0 = R(1) - fs0, L1 = fs0 - fs1, L2 = fs1 - fs2, L3 = fs2;
-    phi[0] = L0 * (R(2) * L0 - R(1));
-    phi[1] = L1 * (R(2) * L1 - R(1));
-    phi[2] = L2 * (R(2) * L2 - R(1));
-    phi[3] = L3 * (R(2) * L3 - R(1));
-    phi[4] = R(4) * L0 * L1;
-    phi[5] = R(4) * L0 * L2;
-    phi[6] = R(4) * L0 * L3;
-    phi[7] = R(4) * L1 * L2;
-    phi[8] = R(4) * L1 * L3;
-    phi[9 % NB] = R(4) * L2 * L3;
   }
 
   __device__ void stencil(const R* c, const R* f, int* slot, R* phi) const {
@@ -731,7 +747,7 @@ struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
       stencil_p1(c, f, slot, phi);
       return;
     }
-    if constexpr (D == 3 && sizeof(R) == 4) {
+    if constexpr (P == 2 && D == 3 && sizeof(R) == 4) {
       stencil_p2_3d(c, f, slot, phi);
       return;
     }
@@ -1051,6 +1067,49 @@ enum NodeMode {
   kEval = 2    // T_new = T_old_h(x_i + D_in)
 };
 
+// (ii) backward RK4 from x_i + d over dt: n_sub substeps of h = dt / n_sub.
+// All 4 n_sub stage evaluations run through one loop with a single
+// evaluation site (stage s of a substep sits at d, d - h/2 k, d - h/2 k,
+// d - h k and has weight 1, 2, 2, 1), which keeps the kernel's code small.
+// With from_node the first stage is the nodal value u_node (the P1 / P2
+// interpolant at the node: steady, or at t_{n+1} where only u^{n+1} has
+// weight).  Returns false if a stage combination was not finite.
+template <int D, class R, class TR>
+__device__ __forceinline__ bool rk4_backward(TR& t, const StepConsts<R>& K, int n_sub, const R* u_node,
+                                             bool from_node, R* d) {
+  const R h = K.h, h2 = K.h2, h6 = K.h6;
+  bool finite = true;
+  R k[D], acc[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    k[q] = u_node[q];
+    acc[q] = k[q];
+  }
+  const int n_eval = 4 * n_sub;
+#pragma unroll 1
+  for (int e = from_node ? 1 : 0; e < n_eval; ++e) {
+    const int s = e & 3;
+    const R off = s == 0 ? R(0) : (s == 3 ? h : h2);
+    R z[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) z[q] = d[q] - off * k[q];
+    t.clamp_box(z);
+    t.velocity(z, to_real<R>(e >> 2) * h + off, k);
+    const R w = (s == 1 || s == 2) ? R(2) : R(1);
+#pragma unroll
+    for (int q = 0; q < D; ++q) acc[q] = s == 0 ? k[q] : r_fma(w, k[q], acc[q]);
+    if (s == 3) {
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        finite = finite && isfinite(acc[q]);
+        d[q] = d[q] - h6 * acc[q];
+      }
+      t.clamp_box(d);
+    }
+  }
+  return finite;
+}
+
 // One node: particle creation (i), backward RK4 (ii), T evaluation (iii).
 // The node is entry `tid` of chunk ck = (macro, slab p1, first index, count).
 template <int D, class R, bool STEADY, int P = 2, int MODE = kStep, int BLEND = 0>
@@ -1129,44 +1188,9 @@ __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab
   }
   bool finite = true;
   if (MODE != kEval) {
-    // (ii) backward RK4, n_sub substeps of h = dt / n_sub.  All 4 n_sub stage
-    // evaluations run through one loop with a single evaluation site (stage s
-    // of a substep sits at d, d - h/2 k, d - h/2 k, d - h k and has weight
-    // 1, 2, 2, 1), which keeps the kernel's code small.
-    const R h = K.h, h2 = K.h2, h6 = K.h6;
-    R k[D], acc[D];
     R u_node[D];
     Tracer<D, R, STEADY, P, BLEND>::load_rec(t.un, own_slot, u_node);
-#pragma unroll
-    for (int q = 0; q < D; ++q) {
-      // the first stage of a trace that starts on the node: the P1 / P2
-      // interpolant there is the nodal value (steady, or at t_{n+1} where
-      // only u^{n+1} has weight)
-      k[q] = u_node[q];
-      acc[q] = k[q];
-    }
-    const int n_eval = 4 * job.n_sub;
-#pragma unroll 1
-    for (int e = from_node ? 1 : 0; e < n_eval; ++e) {
-      const int s = e & 3;
-      const R off = s == 0 ? R(0) : (s == 3 ? h : h2);
-      R z[D];
-#pragma unroll
-      for (int q = 0; q < D; ++q) z[q] = d[q] - off * k[q];
-      t.clamp_box(z);
-      t.velocity(z, to_real<R>(e >> 2) * h + off, k);
-      const R w = (s == 1 || s == 2) ? R(2) : R(1);
-#pragma unroll
-      for (int q = 0; q < D; ++q) acc[q] = s == 0 ? k[q] : r_fma(w, k[q], acc[q]);
-      if (s == 3) {
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-          finite = finite && isfinite(acc[q]);
-          d[q] = d[q] - h6 * acc[q];
-        }
-        t.clamp_box(d);
-      }
-    }
+    finite = rk4_backward<D>(t, K, job.n_sub, u_node, from_node, d);
   }
   if (MODE == kTrace) {
     if (!finite) atomicOr(job.status, kFlagNonFinite);
