@@ -4,7 +4,8 @@
  * Method: Kohl, Mohr, Eibl, Ruede, "A massively parallel Eulerian-Lagrangian
  * method for advection-dominated transport in viscous fluids" (arXiv
  * 2103.02388).  The library computes lines 3-4 of Algorithm 1 (departure
- * points and advection, no diffusion): for every P2 (or P1) node x_i of a
+ * points and advection; the diffusion solve of line 5 is elm_diffusion_step):
+ * for every P2 (or P1) node x_i of a
  * mesh of macro triangles / tetrahedra refined uniformly L times (Sec. 2.1),
  * the departure point X(x_i, t_{n+1}, t_n) of Eq. (departure point) by classic
  * RK4 backwards in time through the P2 (P1) velocity, linearly interpolated in
@@ -27,8 +28,12 @@
  *    precision (double for ELM_FP64, float for ELM_FP32).
  *  - Device pointers are borrowed, caller-owned, and used in stream order on
  *    the CUDA stream passed as `stream` (a cudaStream_t; NULL = legacy
- *    default stream).  No call allocates device memory or synchronises after
- *    elm_mesh_create, except elm_get_status, which synchronises `stream`.
+ *    default stream).  Device memory is allocated only by elm_mesh_create
+ *    (its tables and the buffers its flags ask for), elm_mesh_set_annulus (the
+ *    sector table, and the blended diffusion tables) and elm_batch_create;
+ *    the per-step calls allocate nothing.  No call synchronises, except
+ *    elm_get_status (which synchronises `stream`) and elm_diffusion_step
+ *    (below).
  *  - Errors: argument errors are returned synchronously and leave the
  *    mesh unchanged; device-side conditions (walk limit, non-finite values)
  *    set flags that elm_get_status reports.  No call traps or exits.
@@ -224,8 +229,11 @@ elm_status elm_advect_host(elm_mesh mesh, const void* u_old_host, const void* u_
  * Limit: meshes of at most 524288 (2^19) storage nodes; larger meshes return
  * ELM_ERR_ARG.  The first call on a device looks up the scratch array's device
  * address (with that device current); make that first call before any stream
- * capture.  Every call shares the one scratch array, so calls that overlap on
- * the GPU (other streams, other threads) race; order them. */
+ * capture.  That address is kept for the life of the process, so the device's
+ * context must not be reset (cudaDeviceReset) after the first call.  Every call
+ * shares the one scratch array, so calls that overlap on the GPU (other
+ * streams, other threads) race; order them.  Launches exactly what elm_advect
+ * launches (the step and the interface-copy pass), plus the velocity packing. */
 elm_status elm_advect_noalloc(elm_mesh mesh, const void* u_old_dev, const void* u_new_dev, const void* T_old_dev,
                               void* T_new_dev, double dt, int n_sub, void* stream);
 

@@ -7,10 +7,13 @@
 // P2 velocity (step (ii)) and interpolates T^n at the departure point
 // (step (iii)).  All macros are resident in HBM, so the paper's particle
 // migration between processes becomes an in-register macro walk.  A node on
-// a macro interface is stored once per macro holding it; the thread of every
-// copy traces the owner copy (same macro frame, same instructions), so all
-// copies receive bitwise the same value and no synchronisation pass is needed
-// (the single-owner rule of Sec. 2.3.1, grid data structure).
+// a macro interface is stored once per macro holding it and is computed once,
+// by the thread of its owner copy (the single-owner rule of Sec. 2.3.1, grid
+// data structure); the threads of the other copies return at once, and
+// k_ghost_copy then copies the owner's value into them, so all copies hold
+// bitwise the same value.  (The batched kernel has no pass after its launch:
+// there the thread of every copy traces the owner's node in the owner's frame,
+// which gives the same value.)
 //
 // Point representation.  A point is kept as an offset d from its start node
 // x_i, and its level-L lattice coordinate in the current macro m as

@@ -30,7 +30,9 @@ constexpr size_t kScratchBytes = size_t(2) * size_t(kNoAllocMaxNodes) * kRecordB
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Device address of g_noalloc_scratch per device ordinal, resolved once per
-// device on the first call (with that device current).
+// device on the first call (with that device current) and kept for the life
+// of the process: a device whose primary context is destroyed and recreated
+// after that first call (cudaDeviceReset) is not supported.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
@@ -103,43 +105,15 @@ extern "C" elm_status elm_advect_noalloc(elm_mesh me, const void* u_old_dev, con
     e = elm::launch_pack_velocity(me->precision, me->dim, u_old_dev, rec_old, me->n_storage, s);
   if (e != cudaSuccess) return noalloc_fail(ELM_ERR_CUDA, std::string("elm_advect_noalloc: ") + cudaGetErrorString(e));
 
-  elm::AdvectArgs a{};
-  a.geo = me->d_geo;
-  a.geo32 = me->d_geo32;
-  a.n_macros = int32_t(me->n_macros);
-  a.N = me->N;
-  a.npm = me->npm;
-  a.n_storage = me->n_storage;
-  for (int r = 0; r < 3; ++r) {
-    a.lo[r] = me->lo[r];
-    a.hi[r] = me->hi[r];
-  }
+  // Everything as elm_advect sets it (tables, step constants, the interface
+  // copy pass), with the velocity records in the scratch array and the
+  // caller's T buffers.
+  elm::AdvectArgs a = elm::make_args(me, dt, n_sub);
   a.u_old = steady ? rec_new : rec_old;
   a.u_new = rec_new;
   a.steady = steady;
   a.T_old = T_old_dev;
   a.T_new = T_new_dev;
-  a.dt = dt;
-  a.n_sub = n_sub;
-  a.status = me->d_status;
-  a.unique_map = me->d_unique_map;
-  a.owner_mp = me->d_owner_mp;
-  a.chunks = me->d_chunks;
-  a.n_chunks = int(me->n_chunks);
-  a.order = me->order;
-  a.blend = me->blend;
-  {
-    const double h = dt / n_sub;
-    a.k64 = {h, 0.5 * h, h / 6.0, dt, 1.0 / me->M, double(me->N), {0, 0, 0}, {0, 0, 0}};
-    a.k32 = {float(h), float(0.5 * h), float(h / 6.0), float(dt), float(1.0 / me->M), float(me->N),
-             {0, 0, 0}, {0, 0, 0}};
-    for (int r = 0; r < 3; ++r) {
-      a.k64.lo[r] = me->lo[r];
-      a.k64.hi[r] = me->hi[r];
-      a.k32.lo[r] = float(me->lo[r]);
-      a.k32.hi[r] = float(me->hi[r]);
-    }
-  }
   e = elm::launch_advect(me->dim, me->precision, a, s);
   if (e != cudaSuccess) return noalloc_fail(ELM_ERR_CUDA, std::string("elm_advect_noalloc: ") + cudaGetErrorString(e));
   return ELM_OK;

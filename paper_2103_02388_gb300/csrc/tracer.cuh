@@ -1130,7 +1130,7 @@ __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab
   t.invM = K.invM;
   t.status = job.status;
   t.load_block_macro(ck.x);
-  // (i) particle creation at the node (interface copies trace their owner)
+  // (i) particle creation at the node (an interface copy starts from its owner's lattice point)
   t.m0 = ck.x;
   const int i = ck.z + tid;  // index within slab p1
   t.p[0] = ck.y;

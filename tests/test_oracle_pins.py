@@ -290,6 +290,52 @@ def test_time_interpolation_direction():
     assert np.abs(swapped - exact).max() > 1e-5
 
 
+def test_trace_continuation_exact():
+    """Look-back over several intervals with a time-dependent velocity (Sec.
+    2.3.3 with Eq. linear interpolation in each interval): the interval
+    [t_{k-1}, t_k] has u^{k-1} = A_{k-1} (x - c) and u^k = A_k (x - c), linear
+    fields that P2 reproduces exactly, with non-commuting A_k.  Continuing the
+    trace interval by interval, newest first, must reach the exact departure
+    point: the solution of dz/ds = -((s/tau) A_{k-1} + (1 - s/tau) A_k) z over
+    each interval's elapsed backward time s, from the last interval to the
+    first.  RK4 converges to it at fourth order in the substep; taking the
+    intervals oldest first, or one velocity per interval, misses it."""
+    me = _setup(3, 2)
+    x = me.coords
+    c = np.full(3, 0.5)
+    rng = np.random.default_rng(11)
+    K, tau = 4, 0.05
+    A = []
+    for _ in range(K + 1):
+        S = rng.standard_normal((3, 3))
+        A.append(2.0 * (S - S.T) + 0.5 * np.diag(rng.standard_normal(3)))  # rotation plus stretch
+    inside = np.nonzero(np.linalg.norm(x - c, axis=1) < 0.3)[0]
+    assert len(inside) >= 20
+    exact = []
+    for i in inside:
+        z = x[i] - c
+        for k in range(K, 0, -1):
+            rhs = lambda s, zz, k=k: -(((s / tau) * A[k - 1] + (1 - s / tau) * A[k]) @ zz)  # noqa: E731
+            z = solve_ivp(rhs, (0.0, tau), z, rtol=1e-13, atol=1e-15, method="DOP853").y[:, -1]
+        exact.append(c + z)
+    exact = np.array(exact)
+    assert np.linalg.norm(exact - x[inside], axis=1).max() > 0.02  # the traces move several cells
+    fields = [inputs.linear_field(x, Ak, c) for Ak in A]
+
+    def trace(order, n_sub, pair=True):
+        X = x.copy()
+        for k in order:
+            X = me.trace(X, fields[k - 1], tau, n_sub, u_new=fields[k] if pair else fields[k - 1])
+        return X[inside]
+
+    newest_first = list(range(K, 0, -1))
+    err = [np.abs(trace(newest_first, n) - exact).max() for n in (4, 8, 16)]
+    assert err[2] < 1e-9
+    assert 10.0 < err[0] / err[1] < 24.0 and 10.0 < err[1] / err[2] < 24.0
+    assert np.abs(trace(newest_first[::-1], 16) - exact).max() > 1e-4
+    assert np.abs(trace(newest_first, 16, pair=False) - exact).max() > 1e-4
+
+
 # ---------------------------------------------------------------------------
 # Mass matrix (metrics of Sec. 3.1) and the transpose of the interpolation.
 # ---------------------------------------------------------------------------

@@ -1,12 +1,13 @@
 """elm_advect_noalloc: the advection step for callers that cannot allocate
 device memory at the call site (for example an application whose device
 memory is handed out by its own pool, or a time-critical loop that cannot
-take cudaMalloc's implicit synchronisation).  Its output must match the
-regular elm_advect path on the same inputs, on two calls in a row.  This file
-is collected last on purpose."""
+take cudaMalloc's implicit synchronisation).  It runs the same kernels on the
+same packed velocity records as elm_advect, so its output must equal the
+regular path bit for bit, on two calls in a row, for 2D and 3D meshes, P2 and
+P1 elements, and a mesh blended onto an annulus.  This file is collected last
+on purpose."""
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
@@ -14,7 +15,7 @@ from paper_2103_02388_gb300 import _lib, elm, inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
+ANNULUS = (0.5, 1.5, 6, 0.0)
 
 
 def _ptr(t):
@@ -28,26 +29,46 @@ def _noalloc(mesh, u_old, u_new, T_old, T_new, dt, n_sub):
                                       float(dt), int(n_sub), stream))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_noalloc_matches_advect(precision):
-    v, m = inputs.unit_cube()
-    mesh = elm.Mesh(v, m, 3, precision)
-    x = torch.tensor(mesh.node_coords())
+def _fields(mesh, dim):
+    x = mesh.node_coords()
     dt_ = mesh.dtype
-    u0 = torch.tensor(inputs.cellular_flow(x.numpy()), dtype=dt_, device="cuda")
-    u1 = torch.tensor(inputs.random_fourier(x.numpy(), seed=4), dtype=dt_, device="cuda")
-    T = torch.tensor(inputs.slotted_sphere(x.numpy()), dtype=dt_, device="cuda")
-    dt = inputs.dt_for_cfl(4.0, 3, u1.double().cpu().numpy())
-    tol = TOL[precision] * float(T.abs().max())
-    out = torch.empty_like(T)
-    # two calls in a row, steady and then time-dependent velocity
+    if mesh.annulus is not None:
+        u0 = 1.5 * (torch.tensor(x[:, ::-1].copy()) * torch.tensor([-1.0, 1.0]) + torch.tensor([0.3, -0.2]))
+        u1 = u0 * 0.8 + torch.tensor([0.1, 0.2])
+        T = torch.exp(-((torch.tensor(x) - torch.tensor([0.0, 1.0])) ** 2).sum(1) / 0.05)
+        return u0.to(dt_).cuda(), u1.to(dt_).cuda(), T.to(dt_).cuda(), 0.05
+    u0 = inputs.rotation_2d(x) if dim == 2 else inputs.cellular_flow(x)
+    u1 = inputs.random_fourier(x, seed=4)
+    T = inputs.gaussian(x, (0.35, 0.5, 0.5)[:dim], 0.15) if dim == 3 else inputs.slotted_cylinder(x)
+    dt = inputs.dt_for_cfl(4.0, mesh.level, u1)
+    return (torch.tensor(u0, dtype=dt_, device="cuda"), torch.tensor(u1, dtype=dt_, device="cuda"),
+            torch.tensor(T, dtype=dt_, device="cuda"), dt)
+
+
+CASES = [  # (dim, level, precision, order, annulus)
+    (3, 3, "fp64", 2, None), (3, 3, "fp32", 2, None), (3, 4, "fp32", 1, None), (3, 4, "fp64", 1, None),
+    (2, 5, "fp64", 2, None), (2, 5, "fp32", 2, None), (2, 6, "fp32", 1, None),
+    (2, 3, "fp64", 2, ANNULUS), (2, 4, "fp64", 1, ANNULUS),
+]
+
+
+@pytest.mark.parametrize("dim,level,precision,order,annulus", CASES)
+def test_noalloc_equals_advect(dim, level, precision, order, annulus):
+    if annulus is not None:
+        v, m = inputs.annulus_ring(6, 2)
+    else:
+        v, m = inputs.unit_cube() if dim == 3 else inputs.unit_square()
+    mesh = elm.Mesh(v, m, level, precision, order=order, annulus=annulus)
+    u0, u1, T, dt = _fields(mesh, dim)
+    out = torch.full_like(T, float("nan"))
+    # two calls in a row: steady, then time-dependent velocity
     for u_old, u_new, n_sub in ((u0, u0, 2), (u0, u1, 3)):
         mesh.set_velocity(u_old, u_new)
         ref = mesh.advect(T, dt, n_sub)
         _noalloc(mesh, u_old, u_new, T, out, dt, n_sub)
         torch.cuda.synchronize()
         mesh.status()
-        assert float((out - ref).abs().max()) <= tol
+        assert torch.equal(out, ref)
 
 
 def test_noalloc_rejects_meshes_beyond_the_limit():
