@@ -97,6 +97,84 @@ def alg_ops_per_node(dim: int, n_sub: int, steady: bool) -> int:
     return (4 * n_sub - 1) * vel + n_sub * combine + t_eval
 
 
+def alg_ops_split(dim: int, n_sub: int, steady: bool):
+    """alg_ops_per_node split by the SM pipe each operation issues on: (FMA
+    pipe: FMA, FADD, FMUL; ALU pipe: compares, min/max of the clamps and of the
+    barycentric minimum, the floor of the cell index and the sort compares).
+    The two parts add up to alg_ops_per_node."""
+    nb = (dim + 1) * (dim + 2) // 2
+    loc_fma = dim * dim + 2 * dim + 2 * (dim + 1)   # lattice coords, fraction and cell, both barycentrics
+    loc_alu = 2 * dim + dim * (dim - 1) // 2        # floor, minimum, sort
+    vel_fma = dim + loc_fma + 2 * nb + dim * nb + (0 if steady else dim * nb + 2 * dim)
+    vel_alu = 2 * dim + loc_alu                     # stage-point clamp
+    fma = (4 * n_sub - 1) * vel_fma + n_sub * 4 * dim + loc_fma + 3 * nb
+    alu = (4 * n_sub - 1) * vel_alu + n_sub * 2 * dim + loc_alu
+    assert fma + alu == alg_ops_per_node(dim, n_sub, steady)
+    return fma, alu
+
+
+def _device_props(index: int):
+    """SM count, L2 size and name of the device, from its properties."""
+    import torch
+    p = torch.cuda.get_device_properties(index)
+    return {"sms": int(p.multi_processor_count), "l2_bytes": getattr(p, "L2_cache_size", None), "name": p.name}
+
+
+def _probe_pipes():
+    """Pipe throughputs measured on this device by elm_probe_pipes (timed
+    loops of FFMA, FFMA2, FP32 min/max, integer min/max and DFMA)."""
+    import ctypes
+    import torch
+    from paper_2103_02388_gb300 import _lib
+    r = (ctypes.c_double * 5)()
+    _lib.check(_lib.load().elm_probe_pipes(r, 5, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return {"fp32_fma_per_s_ffma": r[0], "fp32_fma_per_s_ffma2": r[1], "fp32_minmax_per_s": r[2],
+            "int32_minmax_per_s": r[3], "fp64_fma_per_s": r[4],
+            "how": "elm_probe_pipes: 8 independent chains per thread, 8 x 256-thread blocks per SM, CUDA events"}
+
+
+def _compute_roofline(precision, dim, n_sub, n_storage, alg_bytes, launch_ms, hbm_peak, sm_mhz, props, pipes,
+                      util):
+    """The compute side of the roofline, beside the HBM fraction: issue rate
+    (warp instructions from the committed ncu record while the kernel's
+    sources match it) and the algorithmic operations against the measured
+    pipe peaks, with the time the algorithmic work alone would take at those
+    peaks and the HBM fraction that time would allow."""
+    t = launch_ms * 1e-3
+    issue_peak = props["sms"] * 4 * sm_mhz * 1e6
+    fma, alu = alg_ops_split(dim, n_sub, True)
+    out = {"issue": {"peak": issue_peak, "unit": "warp instructions/s",
+                     "peak_kind": f"unit counts: {props['sms']} SMs x 4 issue slots x {sm_mhz:.0f} MHz"}}
+    if util is not None and util.get("warp_instructions"):
+        wi = float(util["warp_instructions"])
+        out["issue"].update({"achieved": wi / t, "frac": wi / t / issue_peak, "warp_instructions_per_launch": wi,
+                             "source": "ncu smsp__inst_executed.sum of this kernel (profiles/advect_traffic.json)"})
+    else:
+        out["issue"].update({"achieved": None, "frac": None,
+                             "source": "no ncu record for these kernel sources"})
+    if precision == "fp32":
+        fma_peak, alu_peak = pipes["fp32_fma_per_s_ffma2"], pipes["fp32_minmax_per_s"]
+        ceil_s = max(fma * n_storage / fma_peak, alu * n_storage / alu_peak,
+                     (fma / 2 + alu) * n_storage / 32 / issue_peak)
+        out["fma_pipe"] = {"achieved": fma * n_storage / t, "peak": fma_peak, "unit": "FP32 FMA-pipe ops/s",
+                           "frac": fma * n_storage / t / fma_peak, "ops_per_node": fma,
+                           "peak_kind": "measured: FFMA2 loop, 2 FMAs per instruction"}
+        out["alu_pipe"] = {"achieved": alu * n_storage / t, "peak": alu_peak, "unit": "ALU-pipe ops/s",
+                           "frac": alu * n_storage / t / alu_peak, "ops_per_node": alu,
+                           "peak_kind": "measured: FP32 min/max loop"}
+        out["bound"] = "issue"
+    else:
+        ops = (fma + alu) * n_storage
+        fp64_peak = pipes["fp64_fma_per_s"]
+        ceil_s = ops / fp64_peak
+        out["fp64_pipe"] = {"achieved": ops / t, "peak": fp64_peak, "unit": "FP64 ops/s", "frac": ops / t / fp64_peak,
+                            "ops_per_node": fma + alu, "peak_kind": "measured: DFMA loop"}
+        out["bound"] = "fp64 pipe"
+    out["algorithmic_ceiling_ms"] = ceil_s * 1e3
+    out["hbm_frac_at_ceiling"] = alg_bytes / ceil_s / 1e9 / hbm_peak
+    return out
+
+
 def _kernel_hash():
     h = hashlib.sha256()
     for p in KERNEL_SRCS:
@@ -252,6 +330,114 @@ def _accuracy(spec, om, mesh, T0_storage, dt, steps: int = 3):
     return res
 
 
+def _time_steps(mesh, T, dt, n_sub, steps, warmup, flush):
+    """Mean CUDA-event time (ms) of ``steps`` elm_advect calls on the current
+    stream, after ``warmup`` calls; L2 flushed between steps if asked."""
+    import torch
+    stream = torch.cuda.current_stream()
+    a, b = T.clone(), torch.empty_like(T)
+    scratch = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=T.device) if flush else None
+    for _ in range(warmup):
+        mesh.advect(a, dt, n_sub, out=b)
+        a, b = b, a
+    torch.cuda.synchronize()
+    ev = []
+    for i in range(steps):
+        if flush:
+            scratch.fill_(float(i))
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        mesh.advect(a, dt, n_sub, out=b)
+        e.record(stream)
+        ev.append((s, e))
+        a, b = b, a
+    torch.cuda.synchronize()
+    mesh.status()
+    return float(np.mean([s.elapsed_time(e) for s, e in ev]))
+
+
+def _fp64_record(dev, hbm_peak, sm_mhz, props, pipes, with_oracle: bool, steps: int = 20, warmup: int = 3):
+    """Config 2's plain FP64 step on the GPU (unit cube, level 6, cellular
+    flow, slotted sphere, CFL 4): time per step, throughput, the FP64-pipe and
+    HBM fractions, and (with the oracle) its error against the FP64 oracle."""
+    import torch
+    from paper_2103_02388_gb300 import elm, inputs
+    spec = WORKLOADS["c2-l6-fp64"]
+    dim, level, _, vel, scal, cfl, n_sub = spec
+    mesh = elm.Mesh(*inputs.unit_cube(), level, "fp64")
+    u, T0, dt = _fields(spec, mesh.unique_coords())
+    mesh.set_velocity(mesh.to_storage(torch.tensor(u, dtype=torch.float64, device=dev)))
+    T = mesh.to_storage(torch.tensor(T0, dtype=torch.float64, device=dev))
+    alg_bytes = mesh.n_nodes * (dim * 8 + 16)
+    ms = _time_steps(mesh, T, dt, n_sub, steps, warmup, flush=alg_bytes < 2 * (props["l2_bytes"] or 129 * 2**20))
+    rec = {"workload": "c2-l6-fp64", "level": level, "unique_nodes": mesh.n_unique, "velocity": vel, "scalar": scal,
+           "cfl": cfl, "n_sub": n_sub, "steps": steps, "ms_per_step": ms,
+           "value": mesh.n_unique / (ms * 1e-3), "unit": "node updates/s",
+           "l2": "flushed between steps (256 MB write)",
+           "hbm": {"achieved": alg_bytes / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                   "frac": alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak, "algorithmic_bytes_per_launch": alg_bytes},
+           "compute": _compute_roofline("fp64", dim, n_sub, mesh.n_nodes, alg_bytes, ms, hbm_peak, sm_mhz, props,
+                                        pipes, _utilisation("c2-l6-fp64"))}
+    if with_oracle:
+        rec["accuracy"] = _accuracy(spec, _oracle_mesh(spec), mesh, T, dt)
+    return rec
+
+
+def _accumulated_record(dev, steps: int = 100, checkpoints=(1, 10, 25, 50, 100)):
+    """Config 3's error budget over a 100-step rollout at level 6 (random
+    Fourier velocity, Gaussian cone, CFL 4): the FP32 GPU path and the plain
+    FP64 GPU path, both on the FP32-rounded inputs, against the FP64 oracle
+    and against each other, accumulated (each side continuing from its own
+    state) and per step (one step of each GPU path from the oracle's state
+    against the oracle's step).  Relative to max |T^0| (max) and to the
+    reference's norm (L2)."""
+    import torch
+    from paper_2103_02388_gb300 import elm, inputs
+    spec = WORKLOADS["c3-l6-fp32"]
+    dim, level, _, _, _, cfl, n_sub = spec
+    om = _oracle_mesh(spec)
+    u, T0, dt = _fields(spec, om.coords)          # FP32-rounded fields, in FP64
+    g32 = elm.Mesh(*inputs.unit_cube(), level, "fp32")
+    g64 = elm.Mesh(*inputs.unit_cube(), level, "fp64")
+    perm = _match_nodes(om.coords, g32.unique_coords(), g32.order << level)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+
+    def to_dev(mesh, a, dtype):
+        return mesh.to_storage(torch.tensor(a[inv], dtype=dtype, device=dev))
+
+    def to_host(mesh, t):
+        return mesh.to_unique(t).double().cpu().numpy()[perm]
+    g32.set_velocity(to_dev(g32, u, torch.float32))
+    g64.set_velocity(to_dev(g64, u, torch.float64))
+    tmax = float(np.abs(T0).max())
+
+    def err(a, ref):
+        e = a - ref
+        return {"max_rel": float(np.abs(e).max() / tmax), "l2_rel": float(np.linalg.norm(e) / np.linalg.norm(ref))}
+    T32, T64, To = to_dev(g32, T0, torch.float32), to_dev(g64, T0, torch.float64), T0.copy()
+    rows = []
+    t0 = time.perf_counter()
+    for k in range(1, steps + 1):
+        prev = To
+        T32, T64 = g32.advect(T32, dt, n_sub), g64.advect(T64, dt, n_sub)
+        To = om.advect(To, u, dt, n_sub)
+        if k in checkpoints:
+            h32, h64 = to_host(g32, T32), to_host(g64, T64)
+            one32 = to_host(g32, g32.advect(to_dev(g32, prev, torch.float32), dt, n_sub))
+            one64 = to_host(g64, g64.advect(to_dev(g64, prev, torch.float64), dt, n_sub))
+            rows.append({"step": k,
+                         "accumulated": {"fp32_vs_oracle": err(h32, To), "fp32_vs_fp64_gpu": err(h32, h64),
+                                         "fp64_gpu_vs_oracle": err(h64, To)},
+                         "per_step": {"fp32_vs_oracle": err(one32, To), "fp64_gpu_vs_oracle": err(one64, To)}})
+    g32.status()
+    g64.status()
+    return {"workload": "c3-l6-fp32 (config 3 at level 6)", "level": level, "unique_nodes": int(om.n_nodes),
+            "cfl": cfl, "n_sub": n_sub, "dt": dt, "steps": steps,
+            "inputs": "FP32-rounded velocity and T^0 for every side", "tolerance_per_step": {"fp32": 1e-5, "fp64": 1e-12},
+            "rows": rows, "seconds": time.perf_counter() - t0}
+
+
 def _cpu_baseline(spec, seconds: float = 12.0, om=None):
     """The CPU oracle timed on a bounded sample of the same workload."""
     import oracle
@@ -363,7 +549,8 @@ def run_ours(args, spec):
     esz = 8 if precision == "fp64" else 4
     alg_bytes = n_storage * (dim * esz + 2 * esz)     # read u + read T_old + write T_new
     working_set = alg_bytes
-    l2_bytes = 129 * 2**20
+    props = _device_props(local)
+    l2_bytes = props["l2_bytes"] or 129 * 2**20
     flush = working_set < 2 * l2_bytes
     scratch = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev) if flush else None
 
@@ -433,15 +620,9 @@ def run_ours(args, spec):
         return
     hbm_peak, sm_mhz, peak_kind = _peaks()
     hbm_achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
-    # the dominant kernel is bound by instruction issue on the FP32/ALU pipes:
-    # peak = 152 SMs x 128 FP32 lanes x max SM clock (one operation per lane
-    # per cycle, FMA counted as one).  The FP64 kernel runs its arithmetic on
-    # the FP64 pipe: 1.25 TFLOP/s nominal on this part, i.e. 2 FP64 FMA lanes
-    # per SM and cycle at the maximum clock.
-    fp64_lanes = 2
-    alu_peak = 152 * (128 if precision == "fp32" else fp64_lanes) * sm_mhz * 1e6 / 1e12
-    ops = alg_ops_per_node(dim, n_sub, True) * n_storage
-    alu_achieved = ops / (ms_per_step * 1e-3) / 1e12
+    pipes = _probe_pipes()
+    compute = _compute_roofline(precision, dim, n_sub, n_storage, alg_bytes, ms_per_step, hbm_peak, sm_mhz, props,
+                                pipes, _utilisation(args.workload))
     line = {
         "metric": METRIC,
         "value": value,
@@ -462,29 +643,33 @@ def run_ours(args, spec):
             "scalar": scal, "cfl": cfl, "n_sub": n_sub, "dt": dt,
             "l2": "flushed between steps (256 MB write)" if flush else "inputs larger than L2 (not flushed)",
             "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU",
+            "device": props,
         },
-        "roofline": {"bound": "alu" if precision == "fp32" else "fp64 alu", "achieved": alu_achieved,
-                     "peak": alu_peak,
-                     "unit": "T ops/s (FP32 lanes)" if precision == "fp32" else "T ops/s (FP64 lanes)",
-                     "frac": alu_achieved / alu_peak,
-                     "peak_kind": (f"derived: 152 SM x 128 lanes x {sm_mhz:.0f} MHz" if precision == "fp32" else
-                                   f"derived: 152 SM x {fp64_lanes} FP64 FMA lanes x {sm_mhz:.0f} MHz "
-                                   "(1.25 TFLOP/s nominal FP64)"),
-                     "algorithmic_ops_per_launch": ops,
+        # the metric's roofline: algorithmic bytes of a step (read u, read T^n,
+        # write T^{n+1}) over the CUDA-event time of the step, against the
+        # measured HBM copy bandwidth; the compute side sits beside it
+        "roofline": {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": hbm_achieved / hbm_peak,
+                     "peak_kind": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                                   else "fallback: 6.8 TB/s, the profiling recipe's figure"),
                      "traffic": _traffic(args.workload), "algorithmic_bytes_per_launch": alg_bytes,
-                     "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": hbm_achieved / hbm_peak, "peak_kind": peak_kind},
                      "kernel": "k_advect (+ k_ghost_copy, about 1% of the step)", "avg_launch_ms": ms_per_step,
+                     "compute": compute, "pipes": pipes,
                      "ncu_utilisation": _utilisation(args.workload)},
         # per step: k_advect, then k_ghost_copy for the interface copies
         "gpu_launches": args.steps * (2 if n_storage > n_unique else 1),
         "clocks": clocks.summary(),
         "e2e": e2e,
     }
+    if world == 1:
+        # the plain FP64 form of the step (config 2), timed the same way
+        line["fp64"] = _fp64_record(dev, hbm_peak, sm_mhz, props, pipes, with_oracle=not args.no_cpu_baseline)
     if world == 1 and not args.no_cpu_baseline:
         om = _oracle_mesh(spec)
         line["accuracy"] = _accuracy(spec, om, mesh, T_init, dt)
         line["cpu_baseline"] = _cpu_baseline(spec, om=om)
+        del om
+        line["accumulated_100"] = _accumulated_record(dev)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -358,6 +358,18 @@ elm_status elm_batch_advect(elm_batch batch, const void* const* T_old, void* con
 /* Thread-local description of the last error returned on this thread. */
 const char* elm_last_error(void);
 
+/* Measured throughput of the SM pipes the advection kernels are bound by, on
+ * the current device (a timed loop of each instruction kind, 8 independent
+ * chains per thread, 8 resident 256-thread blocks per SM); the benchmark's
+ * compute roofline divides by these.  The paper has no counterpart.
+ *  rates_host  [n >= 5] doubles, written: FP32 FMAs per second issued as FFMA,
+ *              FP32 FMAs per second issued as packed FFMA2 (2 per instruction),
+ *              FP32 min/max per second, 32-bit integer min/max per second,
+ *              FP64 FMAs per second.
+ *  stream      as elsewhere; the call synchronises it (it reads CUDA events).
+ * Takes about 20 ms; allocates no device memory; ELM_ERR_ARG for n < 5. */
+elm_status elm_probe_pipes(double* rates_host, int n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,7 @@ SIGNATURES = [
     ("elm_batch_destroy", _I, [_P]),
     ("elm_batch_num_items", _I64, [_P]),
     ("elm_batch_advect", _I, [_P, _P, _P, _P, _P, _P]),
+    ("elm_probe_pipes", _I, [ctypes.POINTER(_D), _I, _P]),
     ("elm_last_error", ctypes.c_char_p, []),
 ]
 

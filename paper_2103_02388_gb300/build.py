@@ -16,7 +16,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["advect.cu", "noalloc.cu", "adjoint.cu", "diffusion.cu"]
+CU_SOURCES = ["advect.cu", "noalloc.cu", "adjoint.cu", "diffusion.cu", "probe.cu"]
 CPP_SOURCES = ["mesh.cpp", "api.cpp", "batch.cpp", "host_path.cpp"]
 HEADERS = ["elm_internal.h", "tracer.cuh"]
 

@@ -47,3 +47,16 @@ def test_default_workload_is_the_level7_fp32_step():
         | set(bench.BATCH_WORKLOADS) | set(bench.ADJOINT_WORKLOADS)
     assert len(names) == len(bench.WORKLOADS) + len(bench.DIFFUSION_WORKLOADS) + len(bench.VARIANT_WORKLOADS) \
         + len(bench.BATCH_WORKLOADS) + len(bench.ADJOINT_WORKLOADS)   # no name shadows another
+
+
+def test_alg_ops_split_adds_up():
+    """The FMA-pipe / ALU-pipe split of the algorithmic operations covers
+    every operation of alg_ops_per_node (3D P2 n_sub = 1: 293 + 60 = 353)."""
+    import bench
+    for dim in (2, 3):
+        for n_sub in (1, 2, 4):
+            for steady in (True, False):
+                fma, alu = bench.alg_ops_split(dim, n_sub, steady)
+                assert fma > 0 and alu > 0
+                assert fma + alu == bench.alg_ops_per_node(dim, n_sub, steady)
+    assert bench.alg_ops_split(3, 1, True) == (293, 60)
