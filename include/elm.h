@@ -73,8 +73,8 @@ enum { ELM_FP64 = 0, ELM_FP32 = 1 };
 enum { ELM_HOST_ONLY = 0x100 };
 
 /* Flag OR-ed into `precision` of elm_mesh_create: also allocate the scratch
- * of elm_advect_adjoint (64-bit accumulators: (1 + 2 dim) * 8 bytes per
- * storage node). */
+ * of elm_advect_adjoint (64-bit accumulators and per-slot scale statistics:
+ * (1 + 2 dim) * 8 + 6 * 8 + 3 * 4 bytes per storage node). */
 enum { ELM_ADJOINT = 0x200 };
 
 /* Flag OR-ed into `precision` of elm_mesh_create: linear (P1) elements for
@@ -162,6 +162,19 @@ elm_status elm_to_unique(elm_mesh mesh, const void* storage_dev, void* unique_de
  * stencil node in the kernel); the caller's buffers are not used afterwards.
  * Work on other streams must be ordered after it by the caller. */
 elm_status elm_set_velocity(elm_mesh mesh, const void* u_old_dev, const void* u_new_dev, void* stream);
+
+/* The velocity pair of the next older interval of a look-back over a
+ * time-dependent velocity (Sec. 2.3.3, intervals taken newest first, each
+ * with the linear time interpolation of its pair, Eq. linear
+ * interpolation): with (u^{k-1}, u^k) set, the current u_old becomes u_new
+ * (its packed records are kept, the caller's buffer is not read again) and
+ * u_old_dev ([n, dim], device, mesh precision) is packed as the new u_old,
+ * giving (u^{k-2}, u^{k-1}) for half the packing work of elm_set_velocity.
+ * After a steady velocity the current field becomes u_new.  Enqueued on
+ * `stream`, which must be the stream of the calls that read the previous
+ * pair (the repacked buffer is the previous u_new's).  ELM_ERR_STATE without
+ * a velocity; allocates nothing. */
+elm_status elm_shift_velocity(elm_mesh mesh, const void* u_old_dev, void* stream);
 
 /* Most RK4 substeps of one forward step (elm_advect, elm_advect_noalloc,
  * elm_batch_advect); elm_advect_adjoint, whose cost grows with the square of
@@ -251,8 +264,11 @@ elm_status elm_advect_noalloc(elm_mesh mesh, const void* u_old_dev, const void* 
  * gU_new may be NULL to receive the sum in gU_old.  Gradients are
  * accumulated onto each node's owner slot (duplicate slots get 0), so
  * elm_to_unique gives per-node gradients.  Deterministic: contributions are
- * summed as 64-bit fixed-point integers (scale from a first pass), so
- * repeated calls give bitwise equal results.  Requires ELM_ADJOINT at
+ * summed as 64-bit fixed-point integers with one scale per output slot, set
+ * by a first pass from the slot's largest contribution and its number of
+ * contributions so that no sum can overflow (however many departure points
+ * meet at one node) and every entry keeps its relative precision; repeated
+ * calls give bitwise equal results.  Requires ELM_ADJOINT at
  * creation; allocates nothing; a few kernel launches on `stream`.  The map
  * is only piecewise smooth (P1 and P2 are C0); on element faces the derivative of
  * the element the point is located in is used.
@@ -338,20 +354,26 @@ elm_status elm_get_status(elm_mesh mesh, void* stream);
  * traces one field per run.
  *
  * elm_batch_create: count in 1..128 meshes, all of one precision and device,
- * borrowed (they must outlive the batch).  blocks_per_sm sets the persistent
- * grid (resident blocks per SM; 0 = default 6); the autotuner picks it.
- * Allocates the batch's small device tables. */
-elm_status elm_batch_create(const elm_mesh* meshes, int count, int blocks_per_sm, elm_batch* out);
+ * borrowed (they must outlive the batch).  blocks_per_sm (0..32) sets the
+ * persistent grid (resident blocks per SM; 0 = default 6) and with it the
+ * kernel's register budget (8 or more: the 8-block budget, else the 6-block
+ * one); chunks_per_item (0..64; 0 = 1) is the tile a block takes per fetch
+ * from the work list: that many consecutive 128-node chunks of one instance.
+ * The autotuner picks both.  Allocates the batch's small device tables. */
+elm_status elm_batch_create(const elm_mesh* meshes, int count, int blocks_per_sm, int chunks_per_item,
+                            elm_batch* out);
 elm_status elm_batch_destroy(elm_batch batch);
-/* Number of (instance, chunk) work items of the batch. */
+/* Number of work items (runs of chunks of one instance) of the batch. */
 int64_t elm_batch_num_items(elm_batch batch);
 /* One step of every instance k: T_new[k] = advect(T_old[k], dt[k], n_sub[k]).
  * T_old, T_new, dt, n_sub are host arrays of `count` entries (device
  * pointers in storage layout, mesh precision).  Their values are copied into
  * the launch's parameters, so the call can be captured in a CUDA graph and
  * replayed with the same pointers.  Zeroes the device counters and launches
- * one kernel per element order present on `stream`; allocates nothing.  Each instance's device flags
- * are reported by elm_get_status on its mesh. */
+ * one kernel per element order present on `stream`, then one kernel that
+ * copies every instance's interface nodes from their owners (each node is
+ * computed once, by its owner copy, as in elm_advect); allocates nothing.
+ * Each instance's device flags are reported by elm_get_status on its mesh. */
 elm_status elm_batch_advect(elm_batch batch, const void* const* T_old, void* const* T_new, const double* dt,
                             const int* n_sub, void* stream);
 

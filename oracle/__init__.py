@@ -206,19 +206,22 @@ class OracleMesh:
                                  idx.shape[0], _ptr(idx), _ptr(out), threads or default_threads())
         return out
 
-    def advect_jvp(self, T_old, u_old, du_old, dt, n_sub=1, u_new=None, du_new=None, threads=None):
-        """(T_new, dT_new/d eps) for u -> u + eps du (forward mode, dual numbers).
-        For a steady velocity (u_new None) the direction is du_old."""
+    def advect_jvp(self, T_old, u_old, du_old, dt, n_sub=1, u_new=None, du_new=None, threads=None,
+                   begin=0, end=None):
+        """(T_new, dT_new/d eps) for u -> u + eps du (forward mode, dual numbers)
+        at nodes [begin, end).  For a steady velocity (u_new None) the
+        direction is du_old."""
         T_old = _f64(T_old)
         u_old = _f64(u_old)
         du_old = _f64(du_old)
         steady = u_new is None
         u_new = u_old if steady else _f64(u_new)
         du_new = du_old if steady else _f64(du_new)
-        out = np.empty(self.n_nodes)
-        jvp = np.empty(self.n_nodes)
+        end = self.n_nodes if end is None else end
+        out = np.empty(end - begin)
+        jvp = np.empty(end - begin)
         _load().orc_advect_jvp(self._h, _ptr(u_old), _ptr(u_new), _ptr(du_old), _ptr(du_new), _ptr(T_old),
-                               float(dt), int(n_sub), 0, self.n_nodes, _ptr(out), _ptr(jvp),
+                               float(dt), int(n_sub), int(begin), int(end), _ptr(out), _ptr(jvp),
                                threads or default_threads())
         return out, jvp
 

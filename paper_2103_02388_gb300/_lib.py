@@ -26,6 +26,7 @@ SIGNATURES = [
     ("elm_to_storage", _I, [_P, _P, _P, _I, _P]),
     ("elm_to_unique", _I, [_P, _P, _P, _I, _P]),
     ("elm_set_velocity", _I, [_P, _P, _P, _P]),
+    ("elm_shift_velocity", _I, [_P, _P, _P]),
     ("elm_advect", _I, [_P, _P, _P, _D, _I, _P]),
     ("elm_advect_noalloc", _I, [_P, _P, _P, _P, _P, _D, _I, _P]),
     ("elm_advect_host", _I, [_P, _P, _P, _P, _P, _D, _I, _P]),
@@ -35,7 +36,7 @@ SIGNATURES = [
     ("elm_diffusion_step", _I, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _I, ctypes.POINTER(_I),
                                 ctypes.POINTER(_D), _P]),
     ("elm_get_status", _I, [_P, _P]),
-    ("elm_batch_create", _I, [_P, _I, _I, ctypes.POINTER(_P)]),
+    ("elm_batch_create", _I, [_P, _I, _I, _I, ctypes.POINTER(_P)]),
     ("elm_batch_destroy", _I, [_P]),
     ("elm_batch_num_items", _I64, [_P]),
     ("elm_batch_advect", _I, [_P, _P, _P, _P, _P, _P]),

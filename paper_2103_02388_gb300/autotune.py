@@ -1,10 +1,16 @@
 """Autotuner for the batched advection launch.
 
-The persistent batched kernel runs ``blocks_per_sm`` resident blocks per SM
-(grid = #SM x blocks_per_sm).  The best value depends on the batch's mix of
-dimensions, levels, CFL numbers and substeps, so it is measured: every
-candidate is timed with CUDA events on the current stream and the fastest is
-kept, optionally in a JSON cache keyed by the batch's signature.
+The persistent batched kernel has two launch-shape knobs: ``blocks_per_sm``
+resident blocks per SM (grid = #SM x blocks_per_sm; 8 or more also selects
+the kernel compiled for an 8-block register budget, fewer the 6-block one)
+and ``chunks_per_item``, the tile a block takes per fetch from the shared
+work list (that many consecutive 128-node chunks of one instance: larger
+tiles mean fewer atomic fetches and block-wide barriers, smaller ones a
+finer balance at the end of the launch).  The best shape depends on the
+batch's mix of dimensions, levels, CFL numbers and substeps, so it is
+measured: every candidate is timed with CUDA events on the current stream and
+the fastest is kept, optionally in a JSON cache keyed by the batch's
+signature.
 """
 from __future__ import annotations
 
@@ -15,7 +21,8 @@ import torch
 
 from .elm import Batch
 
-CANDIDATES = (1, 2, 3, 4, 5, 6, 8)
+BLOCKS_PER_SM = (2, 4, 6, 8)
+CHUNKS_PER_ITEM = (1, 2, 4)
 
 
 def signature(meshes, n_sub) -> str:
@@ -23,9 +30,9 @@ def signature(meshes, n_sub) -> str:
     return "|".join(parts)
 
 
-def tune_batch(meshes, T_old, T_new, dt, n_sub, candidates=CANDIDATES, reps: int = 5,
-               cache_path: str | None = None) -> dict:
-    """Returns {"blocks_per_sm": best, "ms": {candidate: median ms}}."""
+def tune_batch(meshes, T_old, T_new, dt, n_sub, blocks_per_sm=BLOCKS_PER_SM, chunks_per_item=CHUNKS_PER_ITEM,
+               reps: int = 5, cache_path: str | None = None) -> dict:
+    """Returns {"blocks_per_sm": b, "chunks_per_item": c, "ms": {"b:c": median ms}}."""
     key = signature(meshes, n_sub)
     cache = {}
     if cache_path and os.path.exists(cache_path):
@@ -34,22 +41,24 @@ def tune_batch(meshes, T_old, T_new, dt, n_sub, candidates=CANDIDATES, reps: int
         if key in cache:
             return cache[key]
     times = {}
-    for bps in candidates:
-        b = Batch(meshes, bps)
-        b.advect(T_old, T_new, dt, n_sub)  # warm-up
-        ev = []
-        for _ in range(reps):
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record()
-            b.advect(T_old, T_new, dt, n_sub)
-            e.record()
-            ev.append((s, e))
-        torch.cuda.synchronize()
-        ms = sorted(s.elapsed_time(e) for s, e in ev)
-        times[bps] = ms[len(ms) // 2]
-        del b
+    for bps in blocks_per_sm:
+        for cpi in chunks_per_item:
+            b = Batch(meshes, bps, cpi)
+            b.advect(T_old, T_new, dt, n_sub)  # warm-up
+            ev = []
+            for _ in range(reps):
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record()
+                b.advect(T_old, T_new, dt, n_sub)
+                e.record()
+                ev.append((s, e))
+            torch.cuda.synchronize()
+            ms = sorted(s.elapsed_time(e) for s, e in ev)
+            times[(bps, cpi)] = ms[len(ms) // 2]
+            del b
     best = min(times, key=times.get)
-    result = {"blocks_per_sm": best, "ms": {str(k): v for k, v in times.items()}}
+    result = {"blocks_per_sm": best[0], "chunks_per_item": best[1],
+              "ms": {f"{k[0]}:{k[1]}": v for k, v in times.items()}}
     if cache_path:
         cache[key] = result
         os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)

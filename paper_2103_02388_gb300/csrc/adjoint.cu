@@ -12,12 +12,20 @@
 // velocity and J_u(z_s)^T a_k back to z_s, where J_u is the gradient of the
 // P1 / P2 interpolant; a clamped coordinate passes no derivative.
 //
-// Deterministic scatter-add: every contribution c is accumulated as a 64-bit
-// integer round(c * 2^k) with integer atomics, which add exactly and in any
-// order to the same sum.  A first pass finds the largest |c| (atomic max of
-// the value bits) and fixes k so that 2^10 contributions of that size still
-// fit; a second pass accumulates; ghost copies are folded into their owner
-// slot and the sums are scaled back.  No floating-point atomics.
+// Deterministic scatter-add with a scale per output slot: every contribution
+// c to slot j is accumulated as the 64-bit integer round(c 2^k_j) with integer
+// atomics, which add exactly and in any order to the same sum.  A first pass
+// records, per slot, the largest |c| (atomic maximum of its value bits) and
+// the number of contributions (atomic add); the storage copies of an
+// interface node take their owner's statistics.  k_j is then chosen so that
+// count_j * max_j 2^k_j < 2^61: the sum cannot leave the 64-bit range however
+// many contributions a slot receives (a convergent flow that clamps many
+// departure points onto one boundary node included), and each slot keeps
+// about 61 - log2(count_j) bits relative to its own largest contribution, so
+// small gradient entries keep their relative precision next to large ones.
+// A second pass accumulates; the copies' sums are folded into the owner
+// (same scale, exact) and every slot is scaled back.  No floating-point
+// atomics.
 #include <cstdint>
 
 #include "tracer.cuh"
@@ -25,16 +33,19 @@
 namespace elm {
 namespace {
 
-constexpr int kHeadroomBits = 10;   // up to 2^10 maximal contributions per node
-constexpr int kAccBits = 62;
+constexpr int kSumBits = 61;   // |sum of a slot| < 2^61 (64-bit accumulators)
 
 struct AdjArgs {
   const void* gT_new;
   unsigned long long* acc_T;   // [n] int64
   unsigned long long* acc_U;   // [nsets][n][dim] int64
-  unsigned long long* maxbits; // [2]: |contribution| maxima (T, U) as value bits
+  // per slot statistics and scales: T slots [0, n), velocity slots
+  // [n + set n, n + (set + 1) n)
+  unsigned long long* smax;    // largest |contribution| (value bits)
+  unsigned long long* scnt;    // number of contributions
+  const int* kexp;             // scale exponent k_j
   int split;                   // u_old and u_new gradients kept apart
-  int pass;                    // 0: maxima, 1: accumulate
+  int pass;                    // 0: statistics, 1: accumulate
 };
 
 template <class R>
@@ -50,12 +61,14 @@ struct Bits<double> {
   static __device__ double from(unsigned long long b) { return __longlong_as_double((long long)b); }
 };
 
-// 2^k scale from the largest contribution m (power of two: c * 2^k is exact).
-__device__ __forceinline__ int scale_exponent(double m) {
-  if (!(m > 0.0) || !isfinite(m)) return 0;
+// Scale exponent of a slot whose contributions number cnt with largest
+// magnitude m: cnt m 2^k < 2^kSumBits (m < 2^e, cnt <= 2^b).
+__device__ __forceinline__ int scale_exponent(double m, unsigned long long cnt) {
+  if (cnt == 0ull || !(m > 0.0) || !isfinite(m)) return 0;
   int e;
   frexp(m, &e);  // m < 2^e
-  return kAccBits - kHeadroomBits - e;
+  const int b = cnt <= 1ull ? 0 : 64 - __clzll((long long)(cnt - 1ull));
+  return kSumBits - b - e;
 }
 
 template <int D, class R, bool STEADY, int P>
@@ -65,11 +78,9 @@ struct Adjoint {
   Tr t;
   AdjArgs A;
   int n_storage;
-  double sT, sU;       // pass 1: scales 2^k
   R h, h2, h6;
   int n_sub;
   int home_slot;
-  R maxT, maxU;        // pass 0: running maxima of this thread
 
   __device__ void clamp_mask(R* z, unsigned& mask) const {
     mask = 0u;
@@ -81,22 +92,38 @@ struct Adjoint {
     }
   }
 
-  // Adds contribution c to accumulator slot (pass 1) or tracks its size (pass 0).
+  // Contribution c to dL/dT^n at slot: its statistics (pass 0) or its scaled
+  // integer (pass 1).  Zero contributions are skipped in both passes.
   __device__ void addT(int slot, R c) {
+    if (c == R(0)) return;
     if (A.pass == 0) {
-      maxT = fmax(maxT, R(fabs(c)));
+      atomicMax(A.smax + slot, Bits<R>::of(c));
+      atomicAdd(A.scnt + slot, 1ull);
       return;
     }
-    const long long q = llrint(double(c) * sT);
+    const long long q = llrint(ldexp(double(c), A.kexp[slot]));
     atomicAdd(A.acc_T + slot, (unsigned long long)q);
   }
-  __device__ void addU(int set, int slot, int r, R c) {
+  // Contribution v[0..D) to the velocity gradient of set `set` at slot: one
+  // statistic (the largest component; the integer order of the value bits
+  // puts NaN above every number) and one scale for the slot's components.
+  __device__ void addU(int set, int slot, const R* v) {
+    const int64_t st = int64_t(n_storage) * (1 + set) + slot;
     if (A.pass == 0) {
-      maxU = fmax(maxU, R(fabs(c)));
+      unsigned long long mb = 0ull;
+#pragma unroll
+      for (int r = 0; r < D; ++r) mb = max(mb, Bits<R>::of(v[r]));
+      if (mb == 0ull) return;
+      atomicMax(A.smax + st, mb);
+      atomicAdd(A.scnt + st, 1ull);
       return;
     }
-    const long long q = llrint(double(c) * sU);
-    atomicAdd(A.acc_U + (int64_t(set) * n_storage + slot) * D + r, (unsigned long long)q);
+    const int k = A.kexp[st];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+      if (v[r] != R(0))
+        atomicAdd(A.acc_U + (int64_t(set) * n_storage + slot) * D + r,
+                  (unsigned long long)llrint(ldexp(double(v[r]), k)));
   }
 
   // P1 / P2 stencil with barycentrics L and the axis of each sorted fraction.
@@ -227,17 +254,23 @@ struct Adjoint {
     }
     grad_x(hv, L, ax, az);
 #pragma unroll
-    for (int j = 0; j < NB; ++j)
+    for (int j = 0; j < NB; ++j) {
+      R pa[D];
 #pragma unroll
-      for (int r = 0; r < D; ++r) {
-        const R pa = phi[j] * ak[r];
-        if (STEADY || !A.split) {
-          addU(0, slot[j], r, pa);
-        } else {
-          addU(0, slot[j], r, w_old * pa);
-          addU(1, slot[j], r, w_new * pa);
+      for (int r = 0; r < D; ++r) pa[r] = phi[j] * ak[r];
+      if (STEADY || !A.split) {
+        addU(0, slot[j], pa);
+      } else {
+        R po[D], pn[D];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+          po[r] = w_old * pa[r];
+          pn[r] = w_new * pa[r];
         }
+        addU(0, slot[j], po);
+        addU(1, slot[j], pn);
       }
+    }
   }
 
   __device__ void run(R g) {
@@ -329,8 +362,7 @@ struct Adjoint {
       }
       if (jj == 0) {
         // first stage: the nodal value of u^{n+1} (weight 1 at t_{n+1})
-#pragma unroll
-        for (int r = 0; r < D; ++r) addU(STEADY || !A.split ? 0 : 1, home_slot, r, ak[0][r]);
+        addU(STEADY || !A.split ? 0 : 1, home_slot, ak[0]);
       } else {
         R az[D];
         velocity_adjoint(z[0], back, ak[0], az);
@@ -370,13 +402,6 @@ __global__ void __launch_bounds__(kAdvectThreads)
   ad.h2 = K.h2;
   ad.h6 = K.h6;
   ad.n_sub = args.n_sub;
-  ad.maxT = R(0);
-  ad.maxU = R(0);
-  ad.sT = ad.sU = 0.0;
-  if (aa.pass == 1) {
-    ad.sT = ldexp(1.0, scale_exponent(double(Bits<R>::from(aa.maxbits[0]))));
-    ad.sU = ldexp(1.0, scale_exponent(double(Bits<R>::from(aa.maxbits[1]))));
-  }
   // node and owner, as in the forward step
   t.m0 = ck.x;
   const int i = ck.z + int(threadIdx.x);
@@ -415,11 +440,40 @@ __global__ void __launch_bounds__(kAdvectThreads)
   t.home_frame();
   ad.home_slot = t.m0 * npm + packed<D>(t.p);
   ad.run(g);
-  if (aa.pass == 0) {
-    if (!isfinite(ad.maxT) || !isfinite(ad.maxU)) atomicOr(args.status, kFlagNonFinite);
-    atomicMax(aa.maxbits + 0, Bits<R>::of(ad.maxT));
-    atomicMax(aa.maxbits + 1, Bits<R>::of(ad.maxU));
-  }
+}
+
+// Interface copies: a copy's statistics are merged into its owner's (pass 0
+// result), then the owner's scale is handed back to the copy, so both sum at
+// one scale.  g = (copy slot, owner slot) pairs; one thread per (pair, set).
+__global__ void k_merge_stats(unsigned long long* smax, unsigned long long* scnt, int64_t n, int nsets,
+                              const int2* __restrict__ g, int n_ghosts) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= int64_t(n_ghosts) * nsets) return;
+  const int set = int(i / n_ghosts);
+  const int2 p = g[i - int64_t(set) * n_ghosts];
+  const int64_t a = set * n + p.x, o = set * n + p.y;
+  if (scnt[a] == 0ull) return;
+  atomicMax(smax + o, smax[a]);
+  atomicAdd(scnt + o, scnt[a]);
+}
+__global__ void k_copy_scales(int* kexp, int64_t n, int nsets, const int2* __restrict__ g, int n_ghosts) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= int64_t(n_ghosts) * nsets) return;
+  const int set = int(i / n_ghosts);
+  const int2 p = g[i - int64_t(set) * n_ghosts];
+  kexp[set * n + p.x] = kexp[set * n + p.y];
+}
+
+// Scale exponents of every slot from its statistics; a non-finite largest
+// contribution sets the status flag.
+template <class R>
+__global__ void k_scales(const unsigned long long* __restrict__ smax, const unsigned long long* __restrict__ scnt,
+                         int* kexp, int64_t count, unsigned* status) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double m = double(Bits<R>::from(smax[i]));
+  if (scnt[i] != 0ull && !isfinite(m)) atomicOr(status, kFlagNonFinite);
+  kexp[i] = scale_exponent(m, scnt[i]);
 }
 
 // Ghost copies of a node hand their sums to the owner slot.
@@ -440,14 +494,14 @@ __global__ void k_fold_ghosts(unsigned long long* acc, int ncomp, int nsets, int
     }
 }
 
-// out = acc * 2^-k (k from the recorded maximum).
+// out = acc 2^-k, k the slot's scale exponent (shared by the ncomp
+// components of a slot).
 template <class R>
 __global__ void k_scale_out(const unsigned long long* __restrict__ acc, R* __restrict__ out, int64_t count,
-                            const unsigned long long* __restrict__ maxbits, int which) {
+                            int ncomp, const int* __restrict__ kexp) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= count) return;
-  const int k = scale_exponent(double(Bits<R>::from(maxbits[which])));
-  out[i] = R(double((long long)acc[i]) * ldexp(1.0, -k));
+  out[i] = R(ldexp(double((long long)acc[i]), -kexp[i / ncomp]));
 }
 
 template <int D, class R, bool STEADY>
@@ -470,11 +524,14 @@ cudaError_t launch_adjoint(int dim, int precision, const AdvectArgs& a, const Ad
                            const void* gT_new, void* gT_old, void* gU_old, void* gU_new, cudaStream_t s) {
   const int64_t n = a.n_storage;
   const int nsets = (!a.steady && gU_new) ? 2 : 1;
+  const int64_t nstat = n * (1 + nsets);
   cudaError_t e = cudaMemsetAsync(b.acc_T, 0, sizeof(unsigned long long) * n, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.acc_U, 0, sizeof(unsigned long long) * n * dim * nsets, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b.maxbits, 0, sizeof(unsigned long long) * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.smax, 0, sizeof(unsigned long long) * nstat, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.scnt, 0, sizeof(unsigned long long) * nstat, s);
   if (e != cudaSuccess) return e;
-  AdjArgs aa{gT_new, b.acc_T, b.acc_U, b.maxbits, nsets == 2 ? 1 : 0, 0};
+  AdjArgs aa{gT_new, b.acc_T, b.acc_U, b.smax, b.scnt, b.kexp, nsets == 2 ? 1 : 0, 0};
+  const unsigned gb = unsigned((int64_t(b.n_ghosts) * (1 + nsets) + 255) / 256);
   for (int pass = 0; pass < 2; ++pass) {
     aa.pass = pass;
     if (precision == ELM_FP64) {
@@ -485,6 +542,20 @@ cudaError_t launch_adjoint(int dim, int precision, const AdvectArgs& a, const Ad
       e = dim == 3 ? launch_adj_dr<3, float>(a, aa, t, s) : launch_adj_dr<2, float>(a, aa, t, s);
     }
     if (e != cudaSuccess) return e;
+    if (pass == 0) {
+      // scales: copies' statistics into their owner, exponents, owner's
+      // exponent back to the copies
+      if (b.n_ghosts > 0)
+        k_merge_stats<<<gb, 256, 0, s>>>(b.smax, b.scnt, n, 1 + nsets, b.ghosts, b.n_ghosts);
+      const unsigned sb = unsigned((nstat + 255) / 256);
+      if (precision == ELM_FP64)
+        k_scales<double><<<sb, 256, 0, s>>>(b.smax, b.scnt, b.kexp, nstat, a.status);
+      else
+        k_scales<float><<<sb, 256, 0, s>>>(b.smax, b.scnt, b.kexp, nstat, a.status);
+      if (b.n_ghosts > 0) k_copy_scales<<<gb, 256, 0, s>>>(b.kexp, n, 1 + nsets, b.ghosts, b.n_ghosts);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
   }
   const unsigned fb = unsigned((n + 255) / 256);
   k_fold_ghosts<<<fb, 256, 0, s>>>(b.acc_T, 1, 1, n, a.unique_map, b.owner);
@@ -492,15 +563,17 @@ cudaError_t launch_adjoint(int dim, int precision, const AdvectArgs& a, const Ad
   const unsigned tb = unsigned((n + 255) / 256);
   const unsigned ub = unsigned((n * dim + 255) / 256);
   if (precision == ELM_FP64) {
-    k_scale_out<double><<<tb, 256, 0, s>>>(b.acc_T, static_cast<double*>(gT_old), n, b.maxbits, 0);
-    k_scale_out<double><<<ub, 256, 0, s>>>(b.acc_U, static_cast<double*>(gU_old), n * dim, b.maxbits, 1);
+    k_scale_out<double><<<tb, 256, 0, s>>>(b.acc_T, static_cast<double*>(gT_old), n, 1, b.kexp);
+    k_scale_out<double><<<ub, 256, 0, s>>>(b.acc_U, static_cast<double*>(gU_old), n * dim, dim, b.kexp + n);
     if (nsets == 2)
-      k_scale_out<double><<<ub, 256, 0, s>>>(b.acc_U + n * dim, static_cast<double*>(gU_new), n * dim, b.maxbits, 1);
+      k_scale_out<double><<<ub, 256, 0, s>>>(b.acc_U + n * dim, static_cast<double*>(gU_new), n * dim, dim,
+                                             b.kexp + 2 * n);
   } else {
-    k_scale_out<float><<<tb, 256, 0, s>>>(b.acc_T, static_cast<float*>(gT_old), n, b.maxbits, 0);
-    k_scale_out<float><<<ub, 256, 0, s>>>(b.acc_U, static_cast<float*>(gU_old), n * dim, b.maxbits, 1);
+    k_scale_out<float><<<tb, 256, 0, s>>>(b.acc_T, static_cast<float*>(gT_old), n, 1, b.kexp);
+    k_scale_out<float><<<ub, 256, 0, s>>>(b.acc_U, static_cast<float*>(gU_old), n * dim, dim, b.kexp + n);
     if (nsets == 2)
-      k_scale_out<float><<<ub, 256, 0, s>>>(b.acc_U + n * dim, static_cast<float*>(gU_new), n * dim, b.maxbits, 1);
+      k_scale_out<float><<<ub, 256, 0, s>>>(b.acc_U + n * dim, static_cast<float*>(gU_new), n * dim, dim,
+                                            b.kexp + 2 * n);
   }
   return cudaGetLastError();
 }

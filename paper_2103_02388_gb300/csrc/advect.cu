@@ -11,9 +11,8 @@
 // by the thread of its owner copy (the single-owner rule of Sec. 2.3.1, grid
 // data structure); the threads of the other copies return at once, and
 // k_ghost_copy then copies the owner's value into them, so all copies hold
-// bitwise the same value.  (The batched kernel has no pass after its launch:
-// there the thread of every copy traces the owner's node in the owner's frame,
-// which gives the same value.)
+// bitwise the same value.  The batched kernel does the same, with one copy
+// pass for all its instances.
 //
 // Point representation.  A point is kept as an offset d from its start node
 // x_i, and its level-L lattice coordinate in the current macro m as
@@ -85,12 +84,15 @@ __global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
   advect_node<D, R, STEADY, P, MODE, BLEND>(job, tab, ck, int(threadIdx.x));
 }
 
-// Persistent batched kernel: each block repeatedly takes the next (instance,
-// chunk) item from the work list and advects that chunk's nodes with the
-// instance's tables and this call's constants.  Dimension and steadiness are
-// per instance and uniform within a block; the element order P is per launch
-// (a batch that mixes P1 and P2 instances runs one launch per order over its
-// own part of the work list).
+// Persistent batched kernel: each block repeatedly takes the next work item
+// (instance, run of consecutive chunks) from the work list and advects those
+// chunks' nodes with the instance's tables and this call's constants.
+// Dimension and steadiness are per instance and uniform within a block; the
+// element order P is per launch (a batch that mixes P1 and P2 instances runs
+// one launch per order over its own part of the work list).  MINB is the
+// number of resident blocks per SM the register budget is sized for.  As in
+// k_advect, each interface node is computed once, by its owner copy; the
+// copies are filled by k_batch_ghost_copy afterwards.
 template <class R>
 __device__ __forceinline__ Tables<R> tables_of(const BatchStatic& S);
 template <>
@@ -98,12 +100,8 @@ __device__ __forceinline__ Tables<float> tables_of<float>(const BatchStatic& S) 
 template <>
 __device__ __forceinline__ Tables<double> tables_of<double>(const BatchStatic& S) { return Tables<double>{S.geo}; }
 
-#ifndef ELM_BATCH_MIN_BLOCKS
-#define ELM_BATCH_MIN_BLOCKS 6
-#endif
-
-template <class R, int P>
-__global__ void __launch_bounds__(kAdvectThreads, ELM_BATCH_MIN_BLOCKS)
+template <class R, int P, int MINB>
+__global__ void __launch_bounds__(kAdvectThreads, MINB)
     k_advect_batch(const __grid_constant__ BatchParams<R> B) {
   __shared__ int s_item;
   for (;;) {
@@ -112,34 +110,48 @@ __global__ void __launch_bounds__(kAdvectThreads, ELM_BATCH_MIN_BLOCKS)
     const int it = s_item;
     __syncthreads();
     if (it >= B.n_items) return;
-    const int2 w = B.items[it];
+    const int4 w = B.items[it];
     const BatchStatic& S = B.inst[w.x];
     const BatchCall<R>& C = B.call[w.x];
-    const int4 ck = S.chunks[w.y];
-    if (int(threadIdx.x) < ck.w) {
-      const NodeJob<R> job{S.geo,
-                           static_cast<const R*>(C.u_new),
-                           static_cast<const R*>(C.u_old),
-                           static_cast<const R*>(C.T_old),
-                           static_cast<R*>(C.T_new),
-                           S.status,
-                           S.unique_map,
-                           S.owner_mp,
-                           C.K,
-                           S.N,
-                           S.npm,
-                           C.n_sub};
-      const Tables<R> tab = tables_of<R>(S);
-      const int tid = int(threadIdx.x);
-      if (S.dim == 3) {
-        if (C.steady) advect_node<3, R, true, P>(job, tab, ck, tid);
-        else advect_node<3, R, false, P>(job, tab, ck, tid);
-      } else {
-        if (C.steady) advect_node<2, R, true, P>(job, tab, ck, tid);
-        else advect_node<2, R, false, P>(job, tab, ck, tid);
+    for (int cc = 0; cc < w.z; ++cc) {
+      const int4 ck = S.chunks[w.y + cc];
+      if (int(threadIdx.x) < ck.w) {
+        NodeJob<R> job{S.geo,
+                       static_cast<const R*>(C.u_new),
+                       static_cast<const R*>(C.u_old),
+                       static_cast<const R*>(C.T_old),
+                       static_cast<R*>(C.T_new),
+                       S.status,
+                       S.unique_map,
+                       S.owner_mp,
+                       C.K,
+                       S.N,
+                       S.npm,
+                       C.n_sub};
+        job.skip_ghosts = 1;
+        const Tables<R> tab = tables_of<R>(S);
+        const int tid = int(threadIdx.x);
+        if (S.dim == 3) {
+          if (C.steady) advect_node<3, R, true, P>(job, tab, ck, tid);
+          else advect_node<3, R, false, P>(job, tab, ck, tid);
+        } else {
+          if (C.steady) advect_node<2, R, true, P>(job, tab, ck, tid);
+          else advect_node<2, R, false, P>(job, tab, ck, tid);
+        }
       }
     }
   }
+}
+
+// Interface copies of every instance of a batch (a5): T_new[g.y] = T_new[g.z]
+// of instance g.x, for the (instance, copy slot, owner slot) triples g.
+template <class R>
+__global__ void k_batch_ghost_copy(const __grid_constant__ BatchParams<R> B, const int4* __restrict__ g, int n) {
+  const int i = int(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int4 t = g[i];
+  R* out = static_cast<R*>(B.call[t.x].T_new);
+  out[t.y] = out[t.z];
 }
 
 // [n, dim] -> packed records [n, 4] (x, y[, z], 0).
@@ -230,15 +242,37 @@ cudaError_t launch_advect(int dim, int precision, const AdvectArgs& a, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch32(const BatchParams<float>& p, int order, int grid, cudaStream_t s) {
-  if (order == 1) k_advect_batch<float, 1><<<grid, kAdvectThreads, 0, s>>>(p);
-  else k_advect_batch<float, 2><<<grid, kAdvectThreads, 0, s>>>(p);
+cudaError_t launch_batch32(const BatchParams<float>& p, int order, int min_blocks, int grid, cudaStream_t s) {
+  if (min_blocks >= 8) {
+    if (order == 1) k_advect_batch<float, 1, 8><<<grid, kAdvectThreads, 0, s>>>(p);
+    else k_advect_batch<float, 2, 8><<<grid, kAdvectThreads, 0, s>>>(p);
+  } else {
+    if (order == 1) k_advect_batch<float, 1, 6><<<grid, kAdvectThreads, 0, s>>>(p);
+    else k_advect_batch<float, 2, 6><<<grid, kAdvectThreads, 0, s>>>(p);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch64(const BatchParams<double>& p, int order, int grid, cudaStream_t s) {
-  if (order == 1) k_advect_batch<double, 1><<<grid, kAdvectThreads, 0, s>>>(p);
-  else k_advect_batch<double, 2><<<grid, kAdvectThreads, 0, s>>>(p);
+cudaError_t launch_batch64(const BatchParams<double>& p, int order, int min_blocks, int grid, cudaStream_t s) {
+  if (min_blocks >= 8) {
+    if (order == 1) k_advect_batch<double, 1, 8><<<grid, kAdvectThreads, 0, s>>>(p);
+    else k_advect_batch<double, 2, 8><<<grid, kAdvectThreads, 0, s>>>(p);
+  } else {
+    if (order == 1) k_advect_batch<double, 1, 6><<<grid, kAdvectThreads, 0, s>>>(p);
+    else k_advect_batch<double, 2, 6><<<grid, kAdvectThreads, 0, s>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ghosts32(const BatchParams<float>& p, const int4* g, int n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_batch_ghost_copy<float><<<unsigned((n + 255) / 256), 256, 0, s>>>(p, g, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ghosts64(const BatchParams<double>& p, const int4* g, int n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_batch_ghost_copy<double><<<unsigned((n + 255) / 256), 256, 0, s>>>(p, g, n);
   return cudaGetLastError();
 }
 

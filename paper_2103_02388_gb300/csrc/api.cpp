@@ -3,6 +3,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 
 #include "elm_internal.h"
 
@@ -48,8 +49,10 @@ void free_tables(elm_mesh_s* me) {
   cudaFree(me->d_status);
   cudaFree(me->d_acc_T);
   cudaFree(me->d_acc_U);
-  cudaFree(me->d_maxbits);
-  me->d_acc_T = me->d_acc_U = me->d_maxbits = nullptr;
+  cudaFree(me->d_adj_stat);
+  cudaFree(me->d_adj_kexp);
+  me->d_acc_T = me->d_acc_U = me->d_adj_stat = nullptr;
+  me->d_adj_kexp = nullptr;
   cudaFree(const_cast<double*>(me->blend.sec));
   me->blend.sec = nullptr;
   cudaFree(me->d_dtab);
@@ -307,6 +310,22 @@ elm_status elm_set_velocity(elm_mesh me, const void* u_old_dev, const void* u_ne
   return ELM_OK;
 }
 
+elm_status elm_shift_velocity(elm_mesh me, const void* u_old_dev, void* stream) {
+  if (!me) return fail(ELM_ERR_ARG, "elm_shift_velocity: null mesh");
+  if (!u_old_dev) return fail(ELM_ERR_ARG, "elm_shift_velocity: null velocity");
+  if (me->host_only) return fail(ELM_ERR_STATE, "elm_shift_velocity: host-only mesh");
+  if (!me->have_velocity) return fail(ELM_ERR_STATE, "elm_shift_velocity: elm_set_velocity has not been called");
+  DeviceGuard g(me->device);
+  // the current u_old's records (d_u4[0], or d_u4[1] when steady) become
+  // u_new's; the other buffer receives the new u_old
+  if (!me->steady) std::swap(me->d_u4[0], me->d_u4[1]);
+  cudaError_t e = elm::launch_pack_velocity(me->precision, me->dim, u_old_dev, me->d_u4[0], me->n_storage,
+                                            static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "elm_shift_velocity");
+  me->steady = false;
+  return ELM_OK;
+}
+
 elm_status elm_advect(elm_mesh me, const void* T_old_dev, void* T_new_dev, double dt, int n_sub, void* stream) {
   if (!me) return fail(ELM_ERR_ARG, "elm_advect: null mesh");
   if (!T_old_dev || !T_new_dev) return fail(ELM_ERR_ARG, "elm_advect: null temperature buffer");
@@ -347,7 +366,8 @@ elm_status elm_advect_adjoint(elm_mesh me, const void* T_old_dev, const void* gT
   elm::AdvectArgs a = make_args(me, dt, n_sub);
   a.T_old = T_old_dev;
   a.T_new = nullptr;
-  const elm::AdjointBuffers b{me->d_acc_T, me->d_acc_U, me->d_maxbits, me->d_owner};
+  const elm::AdjointBuffers b{me->d_acc_T,  me->d_acc_U, me->d_adj_stat, me->d_adj_stat + 3 * me->n_storage,
+                              me->d_adj_kexp, me->d_owner, me->d_ghosts, int(me->ghosts.size())};
   cudaError_t e = elm::launch_adjoint(me->dim, me->precision, a, b, gT_new_dev, gT_old_dev, gU_old_dev,
                                       me->steady ? nullptr : gU_new_dev, s);
   if (e != cudaSuccess) return cuda_fail(e, "elm_advect_adjoint");

@@ -1,6 +1,7 @@
 // batch.cpp -- C ABI of the batched form: many independent advection
 // instances (meshes of different dimension and level, each with its own
 // velocity, dt and n_sub) advanced by one persistent kernel launch.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -16,9 +17,13 @@ struct elm_batch_s {
   int grid = 0;
   int n_items = 0;
   int n_items_p2 = 0;    // the work list holds the P2 instances' items first, then the P1 ones
+  int min_blocks = 6;    // register budget of the kernel: 6 or 8 resident blocks per SM
+  int chunks_per_item = 1;
+  int n_ghosts = 0;
   std::vector<elm_mesh> meshes;
   elm::BatchStatic* d_inst = nullptr;
-  int2* d_items = nullptr;
+  int4* d_items = nullptr;
+  int4* d_ghosts = nullptr;  // (instance, copy slot, owner slot) of every interface copy
   int* d_counter = nullptr;
 };
 
@@ -43,9 +48,11 @@ struct BatchDevice {
 void free_batch(elm_batch_s* b) {
   cudaFree(b->d_inst);
   cudaFree(b->d_items);
+  cudaFree(b->d_ghosts);
   cudaFree(b->d_counter);
   b->d_inst = nullptr;
   b->d_items = nullptr;
+  b->d_ghosts = nullptr;
   b->d_counter = nullptr;
 }
 
@@ -92,8 +99,13 @@ elm_status launch(elm_batch_s* b, const void* const* T_old, void* const* T_new, 
     P->items = b->d_items + part[o][0];
     P->n_items = part[o][1] - part[o][0];
     P->counter = b->d_counter + o;
-    if constexpr (sizeof(R) == 4) e = elm::launch_batch32(*P, o == 0 ? 2 : 1, b->grid, s);
-    else e = elm::launch_batch64(*P, o == 0 ? 2 : 1, b->grid, s);
+    if constexpr (sizeof(R) == 4) e = elm::launch_batch32(*P, o == 0 ? 2 : 1, b->min_blocks, b->grid, s);
+    else e = elm::launch_batch64(*P, o == 0 ? 2 : 1, b->min_blocks, b->grid, s);
+  }
+  // the interface copies of every instance, from their owners
+  if (e == cudaSuccess) {
+    if constexpr (sizeof(R) == 4) e = elm::launch_batch_ghosts32(*P, b->d_ghosts, b->n_ghosts, s);
+    else e = elm::launch_batch_ghosts64(*P, b->d_ghosts, b->n_ghosts, s);
   }
   delete P;
   if (e != cudaSuccess) return bfail(ELM_ERR_CUDA, std::string("elm_batch_advect: ") + cudaGetErrorString(e));
@@ -104,11 +116,14 @@ elm_status launch(elm_batch_s* b, const void* const* T_old, void* const* T_new, 
 
 extern "C" {
 
-elm_status elm_batch_create(const elm_mesh* meshes, int count, int blocks_per_sm, elm_batch* out) {
+elm_status elm_batch_create(const elm_mesh* meshes, int count, int blocks_per_sm, int chunks_per_item,
+                            elm_batch* out) {
   if (!out || !meshes) return bfail(ELM_ERR_ARG, "elm_batch_create: null argument");
   if (count < 1 || count > elm::kMaxBatch)
     return bfail(ELM_ERR_ARG, "elm_batch_create: count must be in 1.." + std::to_string(elm::kMaxBatch));
   if (blocks_per_sm < 0 || blocks_per_sm > 32) return bfail(ELM_ERR_ARG, "elm_batch_create: blocks_per_sm in 0..32");
+  if (chunks_per_item < 0 || chunks_per_item > 64)
+    return bfail(ELM_ERR_ARG, "elm_batch_create: chunks_per_item in 0..64");
   for (int k = 0; k < count; ++k) {
     if (!meshes[k]) return bfail(ELM_ERR_ARG, "elm_batch_create: null mesh " + std::to_string(k));
     if (meshes[k]->host_only) return bfail(ELM_ERR_STATE, "elm_batch_create: host-only mesh " + std::to_string(k));
@@ -132,26 +147,39 @@ elm_status elm_batch_create(const elm_mesh* meshes, int count, int blocks_per_sm
     delete b;
     return bfail(ELM_ERR_CUDA, std::string("elm_batch_create: ") + cudaGetErrorString(e));
   }
-  b->grid = n_sm * (blocks_per_sm > 0 ? blocks_per_sm : 6);
-  // Static per-instance table and the (instance, chunk) work list.
+  const int bps = blocks_per_sm > 0 ? blocks_per_sm : 6;
+  b->grid = n_sm * bps;
+  b->min_blocks = bps >= 8 ? 8 : 6;
+  b->chunks_per_item = chunks_per_item > 0 ? chunks_per_item : 1;
+  // Static per-instance table, the work list of runs of chunks_per_item
+  // consecutive chunks of one instance, and the interface copies.
   std::vector<elm::BatchStatic> inst(count);
-  std::vector<int2> items;
+  std::vector<int4> items;
+  std::vector<int4> ghosts;
   for (int k = 0; k < count; ++k) {
     const elm_mesh_s* me = meshes[k];
     inst[k] = elm::BatchStatic{me->d_geo, me->d_geo32, me->d_unique_map, me->d_owner_mp, me->d_chunks,
                                me->d_status, me->N, int(me->npm), me->dim, 0};
   }
+  const int G = b->chunks_per_item;
   for (int order : {2, 1}) {
     for (int k = 0; k < count; ++k)
       if (meshes[k]->order == order)
-        for (int64_t c = 0; c < meshes[k]->n_chunks; ++c) items.push_back(make_int2(k, int(c)));
+        for (int64_t c = 0; c < meshes[k]->n_chunks; c += G)
+          items.push_back(make_int4(k, int(c), int(std::min<int64_t>(G, meshes[k]->n_chunks - c)), 0));
     if (order == 2) b->n_items_p2 = int(items.size());
   }
   b->n_items = int(items.size());
+  for (int k = 0; k < count; ++k)
+    for (const int2& g : meshes[k]->ghosts) ghosts.push_back(make_int4(k, g.x, g.y, 0));
+  b->n_ghosts = int(ghosts.size());
   e = cudaMalloc(&b->d_inst, sizeof(elm::BatchStatic) * count);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_inst, inst.data(), sizeof(elm::BatchStatic) * count, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int2) * items.size());
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int4) * items.size());
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !ghosts.empty()) e = cudaMalloc(&b->d_ghosts, sizeof(int4) * ghosts.size());
+  if (e == cudaSuccess && !ghosts.empty())
+    e = cudaMemcpy(b->d_ghosts, ghosts.data(), sizeof(int4) * ghosts.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 2 * sizeof(int));
   if (e != cudaSuccess) {
     free_batch(b);

@@ -171,7 +171,8 @@ struct elm_mesh_s {
   bool with_adjoint = false;
   unsigned long long* d_acc_T = nullptr;
   unsigned long long* d_acc_U = nullptr;
-  unsigned long long* d_maxbits = nullptr;
+  unsigned long long* d_adj_stat = nullptr;  // [2][3 n]: largest |contribution| bits, count
+  int* d_adj_kexp = nullptr;                 // [3 n]
   unsigned* d_status = nullptr;
   // diffusion solver (ELM_DIFFUSION): element tables per macro, boundary mask
   // and CG vectors in the unique layout, reduction space
@@ -290,7 +291,7 @@ struct BatchCall {
 template <class R>
 struct BatchParams {
   const BatchStatic* inst;
-  const int2* items;  // (instance, chunk) work list
+  const int4* items;  // (instance, first chunk, chunks) work list: runs of consecutive chunks of one instance
   int n_items;
   int count;
   int* counter;       // next work item; zeroed before every launch
@@ -301,13 +302,23 @@ struct BatchParams {
 struct AdjointBuffers {
   unsigned long long* acc_T;    // [n] 64-bit fixed-point sums
   unsigned long long* acc_U;    // [2][n][dim]
-  unsigned long long* maxbits;  // [2]
+  unsigned long long* smax;     // [3 n] per slot: largest |contribution| (value bits); T, then 2 velocity sets
+  unsigned long long* scnt;     // [3 n] per slot: number of contributions
+  int* kexp;                    // [3 n] per slot: scale exponent
   const int64_t* owner;         // unique id -> owner slot
+  const int2* ghosts;           // (copy slot, owner slot) of every interface copy
+  int n_ghosts;
 };
 cudaError_t launch_adjoint(int dim, int precision, const AdvectArgs& a, const AdjointBuffers& b,
                            const void* gT_new, void* gT_old, void* gU_old, void* gU_new, cudaStream_t s);
 
-cudaError_t launch_batch32(const BatchParams<float>& p, int order, int grid, cudaStream_t s);
-cudaError_t launch_batch64(const BatchParams<double>& p, int order, int grid, cudaStream_t s);
+// The batched kernel of element order `order` with `min_blocks` resident
+// blocks per SM reserved by its register budget (6 or 8); the interface
+// copies of every instance are filled afterwards by launch_batch_ghosts from
+// (instance, copy slot, owner slot) triples.
+cudaError_t launch_batch32(const BatchParams<float>& p, int order, int min_blocks, int grid, cudaStream_t s);
+cudaError_t launch_batch64(const BatchParams<double>& p, int order, int min_blocks, int grid, cudaStream_t s);
+cudaError_t launch_batch_ghosts32(const BatchParams<float>& p, const int4* g, int n, cudaStream_t s);
+cudaError_t launch_batch_ghosts64(const BatchParams<double>& p, const int4* g, int n, cudaStream_t s);
 
 }  // namespace elm

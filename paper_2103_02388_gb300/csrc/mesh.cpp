@@ -315,7 +315,8 @@ elm_status build_mesh(int dim, int64_t nv, const double* xyz, int64_t nm, const 
             (!me->with_adjoint ||
              (cudaMalloc((void**)&me->d_acc_T, sizeof(unsigned long long) * me->n_storage) == cudaSuccess &&
               cudaMalloc((void**)&me->d_acc_U, sizeof(unsigned long long) * me->n_storage * d * 2) == cudaSuccess &&
-              cudaMalloc((void**)&me->d_maxbits, sizeof(unsigned long long) * 2) == cudaSuccess)) &&
+              cudaMalloc((void**)&me->d_adj_stat, sizeof(unsigned long long) * me->n_storage * 6) == cudaSuccess &&
+              cudaMalloc((void**)&me->d_adj_kexp, sizeof(int) * me->n_storage * 3) == cudaSuccess)) &&
             cudaMalloc((void**)&me->d_status, sizeof(unsigned)) == cudaSuccess &&
             cudaMemset(me->d_status, 0, sizeof(unsigned)) == cudaSuccess;
   if (!ok) {

@@ -289,6 +289,55 @@ __device__ __noinline__ Min64 bary64_min(const MacroGeo* geo, int m0, int p0, in
   return out;
 }
 
+// The same minimum barycentric (lattice units) and face in double-float
+// arithmetic on the FP32 pipe (about 44 significant bits: the lattice
+// coordinate is exact to about 256 * 2^-44 = 1.5e-11, far inside the FP64
+// decision's 1e-9 band).  Used by the trace and evaluation kernels, whose
+// points can stay on an interior face for the whole trace (a flow that keeps
+// a face invariant sends every lookup of those nodes here): their tie
+// decisions then cost FP32 instructions instead of this part's narrow FP64
+// pipe.  Ties of the minimum keep the lowest face index, like bary64_min.
+template <int D>
+__device__ __noinline__ Min64 bary_df_min(const MacroGeo32* tg, int m0, int p0, int p1, int p2, float invM, int m,
+                                          float Nf, float d0, float d1, float d2) {
+  const MacroGeo32& g0 = tg[m0];
+  const MacroGeo32& g = tg[m];
+  const int pp[3] = {p0, p1, p2};
+  const float dd[3] = {d0, d1, d2};
+  df y[D];
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    df acc = {g0.v0[r], g0.v0_lo[r]};
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      acc = df_add(acc, df_mul_f(df{g0.J[r * 3 + c], g0.J_lo[r * 3 + c]}, i2f_exact(pp[c]) * invM));
+    acc = df_add(acc, df{dd[r], 0.0f});
+    y[r] = df_add(acc, df{-g.v0[r], -g.v0_lo[r]});
+  }
+  df q[D];
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    q[r] = df{0.0f, 0.0f};
+#pragma unroll
+    for (int c = 0; c < D; ++c) q[r] = df_add(q[r], df_mul(df{g.NJinv[r * 3 + c], g.NJinv_lo[r * 3 + c]}, y[c]));
+  }
+  df l[D + 1];
+  l[0] = df_add(df{Nf, 0.0f}, df{-q[0].hi, -q[0].lo});
+#pragma unroll
+  for (int k = 1; k < D; ++k) l[k] = df_add(q[k - 1], df{-q[k].hi, -q[k].lo});
+  l[D] = q[D - 1];
+  Min64 out{0.0, 0};
+  df best = l[0];
+#pragma unroll
+  for (int k = 1; k <= D; ++k)
+    if (l[k].hi < best.hi || (l[k].hi == best.hi && l[k].lo < best.lo)) {
+      best = l[k];
+      out.kmin = k;
+    }
+  out.lmin = double(best.hi + best.lo);
+  return out;
+}
+
 // Brute-force macro search for x_i + d (rare path): the macro whose reference
 // simplex holds the point best (largest minimum barycentric, lattice units).
 // On a non-convex mesh (an annulus) the walk can end at a boundary face while
@@ -426,10 +475,14 @@ __device__ __forceinline__ KuhnP2 kuhn_p2_3d(const R* f, R* phi) {
   return o;
 }
 
-template <int D, class R, bool STEADY, int P = 2, int BLEND = 0>
+// TIE_DF (FP32 only): interior-face tie decisions in double-float on the FP32
+// pipe (bary_df_min) instead of FP64 (bary64_min); the trace and evaluation
+// kernels use it, the step kernel keeps the FP64 decision.
+template <int D, class R, bool STEADY, int P = 2, int BLEND = 0, int TIE_DF = 0>
 struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
   static_assert(BLEND == 0 || (D == 2 && sizeof(R) == 8), "blending: 2D FP64 only");
   static_assert(P == 1 || P == 2, "element order");
+  static_assert(TIE_DF == 0 || sizeof(R) == 4, "double-float tie decisions serve the FP32 kernels");
   static constexpr int NB = P == 2 ? (D + 1) * (D + 2) / 2 : D + 1;  // nodes of a simplex
   // launch constants (copied, so no kernel parameter is addressed)
   const MacroGeo* geo;   // FP64 macro table (tie-breaks)
@@ -642,8 +695,13 @@ struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
         nb = tab.nb(m, kmin);
         if (!outside && nb >= 0) {
           // tie band at an interior face: decide in FP64 from the exact start node
-          const Min64 r64 = bary64_min<D, P>(geo, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, N, m, float(d[0]),
-                                          float(d[1]), D == 3 ? float(d[D - 1]) : 0.0f);
+          Min64 r64;
+          if constexpr (TIE_DF == 1)
+            r64 = bary_df_min<D>(tab.g, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, float(invM), m, float(Nf),
+                                 float(d[0]), float(d[1]), D == 3 ? float(d[D - 1]) : 0.0f);
+          else
+            r64 = bary64_min<D, P>(geo, m0, p[0], p[1], D == 3 ? p[D - 1] : 0, N, m, float(d[0]), float(d[1]),
+                                   D == 3 ? float(d[D - 1]) : 0.0f);
           outside = r64.lmin < -kTol64;
           kmin = r64.kmin;
           nb = tab.nb(m, kmin);
@@ -1116,7 +1174,8 @@ template <int D, class R, bool STEADY, int P = 2, int MODE = kStep, int BLEND = 
 __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab, int4 ck, int tid) {
   const StepConsts<R>& K = job.K;
   const int npm = job.npm;
-  Tracer<D, R, STEADY, P, BLEND> t;
+  constexpr int TIE_DF = (MODE != kStep && sizeof(R) == 4) ? 1 : 0;
+  Tracer<D, R, STEADY, P, BLEND, TIE_DF> t;
   t.geo = job.geo;
   t.tab = tab;
   t.N = job.N;
@@ -1189,7 +1248,7 @@ __device__ __forceinline__ void advect_node(const NodeJob<R>& job, Tables<R> tab
   bool finite = true;
   if (MODE != kEval) {
     R u_node[D];
-    Tracer<D, R, STEADY, P, BLEND>::load_rec(t.un, own_slot, u_node);
+    Tracer<D, R, STEADY, P, BLEND, TIE_DF>::load_rec(t.un, own_slot, u_node);
     finite = rk4_backward<D>(t, K, job.n_sub, u_node, from_node, d);
   }
   if (MODE == kTrace) {

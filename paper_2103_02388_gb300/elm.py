@@ -143,6 +143,16 @@ class Mesh:
                                            ctypes.c_void_p(u_new.data_ptr()), _stream_ptr()))
         self._u = (u_old, u_new)  # keep the borrowed buffers alive
 
+    def shift_velocity(self, u_old: torch.Tensor) -> None:
+        """Next older look-back interval (Sec. 2.3.3): the current u_old becomes
+        u_new (its packed copy is kept) and ``u_old`` ([n, dim], storage
+        layout) becomes the new u_old; on the current stream."""
+        self._check_tensor(u_old, "u_old")
+        if tuple(u_old.shape) != (self.n_nodes, self.dim):
+            raise ValueError(f"u_old must have shape ({self.n_nodes}, {self.dim})")
+        check(_lib.load().elm_shift_velocity(self._h, ctypes.c_void_p(u_old.data_ptr()), _stream_ptr()))
+        self._u = (u_old, self._u[0] if self._u is not None else u_old)
+
     def advect(self, T_old: torch.Tensor, dt: float, n_sub: int = 1, out: torch.Tensor | None = None,
                stream=None) -> torch.Tensor:
         """One MMOC advection step: T_new[i] = T_old_h(X_i) (storage layout)."""
@@ -251,7 +261,10 @@ class Mesh:
         bufs = [torch.empty((self.n_nodes, self.dim), dtype=self.dtype, device=self.device) for _ in range(2)]
         cur = None
         for j, k in enumerate(range(len(us) - 1, 0, -1)):
-            self.set_velocity(us[k - 1], us[k])
+            if j == 0:
+                self.set_velocity(us[k - 1], us[k])
+            else:
+                self.shift_velocity(us[k - 1])     # (u^{k-1}, u^k): u^k is the previous u_old
             cur = self.trace(cur, tau, n_sub, out=bufs[j % 2])
         return self.trace_eval(cur, T_src)
 
@@ -324,17 +337,20 @@ class Batch:
 
     Each mesh keeps its own velocity (``Mesh.set_velocity``).  ``advect`` takes
     lists of T_old / T_new tensors and per-instance dt and n_sub; it launches
-    one kernel on the current stream and can be captured in a CUDA graph.
+    the batched kernel (one per element order) and the interface-copy pass on
+    the current stream and can be captured in a CUDA graph.  ``blocks_per_sm``
+    and ``chunks_per_item`` are the launch shape (see autotune.tune_batch).
     """
 
-    def __init__(self, meshes, blocks_per_sm: int = 0):
+    def __init__(self, meshes, blocks_per_sm: int = 0, chunks_per_item: int = 1):
         lib = _lib.load()
         self.meshes = list(meshes)
         arr = (ctypes.c_void_p * len(self.meshes))(*[m.handle.value for m in self.meshes])
         h = ctypes.c_void_p()
-        check(lib.elm_batch_create(arr, len(self.meshes), int(blocks_per_sm), ctypes.byref(h)))
+        check(lib.elm_batch_create(arr, len(self.meshes), int(blocks_per_sm), int(chunks_per_item), ctypes.byref(h)))
         self._h = h
         self.blocks_per_sm = int(blocks_per_sm)
+        self.chunks_per_item = int(chunks_per_item)
         self.n_items = int(lib.elm_batch_num_items(h))
         n = len(self.meshes)
         self._told = (ctypes.c_void_p * n)()

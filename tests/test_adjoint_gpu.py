@@ -173,6 +173,142 @@ def test_velocity_gradient_finite_differences_gpu(order):
         assert abs((gU * v).sum() - fd) <= 1e-7 * (np.abs(g) @ np.abs((fp - fm) / (2 * e)) + 1e-30)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_convergent_flow_sums_exactly(precision):
+    """Every departure point clamped onto one corner node: a uniform velocity
+    toward the corner (1, 1, 1) traced back past it, so all 274,625 nodes of
+    the level-5 cube send phi = 1 times g_i = 1 to that node.  The sum must be
+    exactly n_unique (a fixed-point scale taken from the largest contribution
+    alone, with a few bits of headroom, would wrap around), every other entry
+    0, and no velocity gradient passes the clamp."""
+    P = Pair(5, precision)
+    n = P.om.n_nodes
+    u = inputs.uniform_field(P.x, [-2.0, -2.0, -2.0])
+    T = inputs.gaussian(P.x, (0.5, 0.5, 0.5), 0.2)
+    P.gm.set_velocity(P.to_gpu(u))
+    gT, gU, _ = P.gm.advect_adjoint(P.to_gpu(T), P.to_gpu_owner(np.ones(n)), 1.0, 1)
+    P.gm.status()
+    got = P.from_gpu(gT)
+    corner = int(np.argmin(np.abs(P.x - 1.0).sum(axis=1)))
+    assert got[corner] == float(n)
+    assert np.count_nonzero(got) == 1
+    assert not torch.any(gU != 0)
+    assert np.array_equal(got, P.om.advect_transpose(np.ones(n), u, 1.0, 1))
+
+
+def test_small_gradient_entries_keep_relative_precision():
+    """dL/dT^n entries spanning twelve decades: g_i = 2^(-40 x1_i), smooth,
+    so the few departure points that reach a node (CFL 0.5) carry g of one
+    size, and P1 elements, so every contribution phi_j g_i >= 0.  Each entry
+    matches the oracle transpose to 1e-12 of itself, not of the largest
+    entry (one fixed-point quantum of 2^-52 times the largest contribution
+    would already miss this for every entry below 2e-4 of the largest).  The
+    check covers the entries whose basis weights are not tiny (sum of phi of
+    at least 1e-3): for those, the two implementations' independent roundoff
+    in phi stays far below 1e-12 of the entry."""
+    P = Pair(LEVEL[1], "fp64", order=1)
+    u, T = _fields(P, "fourier")
+    dt = inputs.dt_for_cfl(0.5, LEVEL[1], u)
+    env = 2.0 ** (-40.0 * P.x[:, 0])
+    P.gm.set_velocity(P.to_gpu(u))
+    gT, _, _ = P.gm.advect_adjoint(P.to_gpu(T), P.to_gpu_owner(env), dt, 2)
+    P.gm.status()
+    got, ref = P.from_gpu(gT), P.om.advect_transpose(env, u, dt, 2)
+    weight = P.om.advect_transpose(np.ones(P.om.n_nodes), u, dt, 2)   # sum of phi per node
+    assert np.all((ref > 0) == (got > 0))
+    check = weight >= 1e-3
+    assert check.mean() > 0.95
+    assert ref[check].min() < 1e-11 * ref.max()       # the entries span many decades
+    assert np.all(np.abs(got[check] - ref[check]) <= 1e-12 * ref[check])
+
+
+def _kink_nodes(P, u, dt, idx, tol=1e-9):
+    """Nodes idx (one RK4 substep of dt) with a stage point or departure point
+    within tol lattice cells of a micro-element face of the unit cube's
+    Freudenthal lattice: a cell fraction near 0 or 1, or two fractions equal
+    (the Kuhn planes inside a cell).  Stage points from the oracle's own
+    field evaluation."""
+    N = 2 ** P.gm.level
+    xs = P.x[idx]
+    clamp = lambda p: np.clip(p, 0.0, 1.0)  # noqa: E731
+    k1 = u[idx]
+    z2 = clamp(xs - dt / 2 * k1)
+    k2 = P.om.eval(u, z2)
+    z3 = clamp(xs - dt / 2 * k2)
+    k3 = P.om.eval(u, z3)
+    z4 = clamp(xs - dt * k3)
+    k4 = P.om.eval(u, z4)
+    X = clamp(xs - dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4))
+    flag = np.zeros(len(idx), bool)
+    for p in (z2, z3, z4, X):
+        f = p * N - np.floor(p * N)
+        flag |= np.any((f < tol) | (f > 1 - tol), axis=1)
+        for a in range(3):
+            for b in range(a + 1, 3):
+                flag |= np.abs(f[:, a] - f[:, b]) < tol
+    return flag
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_config5_level6_velocity_gradient(precision):
+    """Config 5's setting at its own size (unit cube, level 6, cellular flow,
+    Gaussian T^n, CFL 4): L = <g, T^{n+1}> with g on sampled nodes (four runs
+    of 400 nodes; the nodes whose trace runs along a kink are flagged and
+    left out).  <dL/du, v> from the GPU adjoint equals the oracle's
+    forward-mode derivative on those nodes for 32 random directions v (FP64
+    1e-9, FP32 1e-4 relative to sum |g| |dT/d eps|); in FP64 it also matches
+    central differences of the GPU step for 8 of them (at most one direction
+    may straddle a micro-element face, where the step is only C0)."""
+    P = Pair(6, precision)
+    n = P.om.n_nodes
+    u = P.rounded(inputs.cellular_flow(P.x))
+    T = P.rounded(inputs.gaussian(P.x, (0.35, 0.5, 0.5), 0.1))
+    dt = inputs.dt_for_cfl(4.0, 6, u)
+    rng = np.random.default_rng(21)
+    runs = [(400 * b, 400 * b + 400) for b in sorted(rng.choice(n // 400, 4, replace=False))]
+    g = np.zeros(n)
+    for b, e in runs:
+        g[b:e] = rng.standard_normal(e - b)
+    # Flagged and left out: nodes whose trace runs along a kink of the step
+    # (the step is only C0 there, and the offset form of the GPU and the
+    # absolute coordinates of the oracle may round to different one-sided
+    # derivatives, both valid): the box boundary, where the cellular flow is
+    # tangential only up to rounding (sin(pi) != 0), and every node with an
+    # RK4 stage point or departure point on a micro-element face (the flow's
+    # symmetries keep whole traces on the planes x = 1/2, y = 1/2 and on
+    # diagonal Kuhn planes).
+    idx = np.nonzero(g)[0]
+    flag = _kink_nodes(P, u, dt, idx) | np.any((P.x[idx] == 0.0) | (P.x[idx] == 1.0), axis=1)
+    assert flag.mean() < 0.1
+    g[idx[flag]] = 0.0
+    Tg = P.to_gpu(T)
+    P.gm.set_velocity(P.to_gpu(u))
+    _, gU, _ = P.gm.advect_adjoint(Tg, P.to_gpu_owner(g), dt, 1)
+    P.gm.status()
+    gU = P.from_gpu(gU)
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    dirs = [rng.standard_normal(u.shape) for _ in range(32)]
+    for v in dirs:
+        lhs, rhs, scale = (gU * v).sum(), 0.0, 0.0
+        for b, e in runs:
+            _, jvp = P.om.advect_jvp(T, u, v, dt, 1, begin=b, end=e)
+            rhs += g[b:e] @ jvp
+            scale += np.abs(g[b:e]) @ np.abs(jvp)
+        assert abs(lhs - rhs) <= tol * scale
+    if precision != "fp64":
+        return
+    eps, bad = 1e-6, 0
+    for v in dirs[:8]:
+        P.gm.set_velocity(P.to_gpu(u + eps * v))
+        fp = P.from_gpu(P.gm.advect(Tg, dt, 1))
+        P.gm.set_velocity(P.to_gpu(u - eps * v))
+        fm = P.from_gpu(P.gm.advect(Tg, dt, 1))
+        dT = (fp - fm) / (2 * eps)
+        if abs((gU * v).sum() - g @ dT) > 1e-6 * (np.abs(g) @ np.abs(dT)):
+            bad += 1
+    assert bad <= 1
+
+
 def test_adjoint_substep_limit():
     P = Pair(2, "fp64")
     u, T = _fields(P, "linear")

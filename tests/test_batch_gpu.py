@@ -45,8 +45,10 @@ def test_batch_equals_single_runs(precision):
     dts = [i[2] for i in inst]
     subs = [i[3] for i in inst]
     ref = [m.advect(T, dt, s) for m, T, dt, s in zip(meshes, T_old, dts, subs)]
-    for bps in (1, 4, 6):
-        b = elm.Batch(meshes, bps)
+    # launch shapes: resident blocks per SM (and with them the register
+    # budget: 8 or more selects the 8-block kernel) and chunks per work item
+    for bps, cpi in ((1, 1), (4, 2), (6, 4), (8, 1), (8, 3)):
+        b = elm.Batch(meshes, bps, cpi)
         out = [torch.full_like(T, float("nan")) for T in T_old]
         b.advect(T_old, out, dts, subs)
         torch.cuda.synchronize()
@@ -117,9 +119,10 @@ def test_autotuner_picks_a_candidate(tmp_path):
     meshes = [i[0] for i in inst]
     T_old = [i[1] for i in inst]
     out = [torch.empty_like(T) for T in T_old]
-    res = tune_batch(meshes, T_old, out, [i[2] for i in inst], [i[3] for i in inst], candidates=(1, 4),
-                     reps=2, cache_path=str(tmp_path / "tune.json"))
-    assert res["blocks_per_sm"] in (1, 4)
-    again = tune_batch(meshes, T_old, out, [i[2] for i in inst], [i[3] for i in inst], candidates=(1, 4),
-                       cache_path=str(tmp_path / "tune.json"))
+    res = tune_batch(meshes, T_old, out, [i[2] for i in inst], [i[3] for i in inst], blocks_per_sm=(1, 8),
+                     chunks_per_item=(1, 3), reps=2, cache_path=str(tmp_path / "tune.json"))
+    assert res["blocks_per_sm"] in (1, 8) and res["chunks_per_item"] in (1, 3)
+    assert sorted(res["ms"]) == ["1:1", "1:3", "8:1", "8:3"]
+    again = tune_batch(meshes, T_old, out, [i[2] for i in inst], [i[3] for i in inst], blocks_per_sm=(1, 8),
+                       chunks_per_item=(1, 3), cache_path=str(tmp_path / "tune.json"))
     assert again == res

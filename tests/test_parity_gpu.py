@@ -439,3 +439,29 @@ def test_table3_swirl_gpu():
                     X = P.om.trace(X, inputs.swirl_3d(P.x, (k - 1) * tau), tau, 1,
                                    u_new=inputs.swirl_3d(P.x, k * tau))
                 assert _err(got, P.om.eval(c0, X), c0) <= TOL["fp64"]
+
+
+@pytest.mark.parametrize("precision,order", [("fp64", 2), ("fp32", 1)])
+def test_shift_velocity_equals_set_velocity(precision, order):
+    """elm_shift_velocity (the next older look-back interval: the current
+    u_old becomes u_new, a new u_old is packed) traces exactly as
+    elm_set_velocity with that pair, after a time-dependent pair and after a
+    steady field."""
+    v, m = inputs.unit_cube()
+    mesh = elm.Mesh(v, m, 3, precision, order=order)
+    x = mesh.node_coords()
+    f = [torch.tensor(inputs.swirl_3d(x, t), dtype=mesh.dtype, device="cuda") for t in (0.0, 0.1, 0.2)]
+    tau = 0.1
+    mesh.set_velocity(f[1], f[2])
+    D1 = mesh.trace(None, tau, 2)
+    mesh.shift_velocity(f[0])                       # (f0, f1)
+    got = mesh.trace(D1, tau, 2)
+    mesh.set_velocity(f[0], f[1])
+    ref = mesh.trace(D1, tau, 2)
+    assert torch.equal(got, ref)
+    mesh.set_velocity(f[2])                         # steady f2, then (f1, f2)
+    mesh.shift_velocity(f[1])
+    got = mesh.trace(None, tau, 2)
+    mesh.set_velocity(f[1], f[2])
+    assert torch.equal(got, mesh.trace(None, tau, 2))
+    mesh.status()
