@@ -62,6 +62,15 @@ void free_tables(elm_mesh_s* me) {
   me->d_dtab_el = me->d_dtab32 = me->d_dvec32 = nullptr;
   cudaFree(me->d_dbnd);
   cudaFree(me->d_dcells);
+  cudaFree(me->d_dcellv);
+  cudaFree(me->d_dfold_off);
+  cudaFree(me->d_dfold_slots);
+  cudaFree(me->d_dys);
+  cudaFree(me->d_dys32);
+  me->d_dys32 = nullptr;
+  me->d_dcellv = nullptr;
+  me->d_dfold_off = me->d_dfold_slots = nullptr;
+  me->d_dys = nullptr;
   cudaFree(me->d_dvec);
   cudaFree(me->d_dpart);
   cudaFree(me->d_dscal);

@@ -17,11 +17,31 @@
 // matrices are equal.  The host computes, per macro, the mass matrix (the
 // same for every sigma, since all micro simplices have the same volume) and
 // one stiffness matrix per sigma; a thread per lattice cell applies the
-// element matrices of the cell's simplices that lie in the macro and adds the
-// results to the unique nodes with atomics.  The solver's vectors are in the
-// unique-node layout, so interface nodes shared by several macros are single
-// unknowns.  The FP atomics make the summation order, and so the last bits,
-// vary between runs; the solve converges to the same tolerance.
+// element matrices of the cell's simplices that lie in the macro.  The
+// solver's vectors are in the unique-node layout, so interface nodes shared by
+// several macros are single unknowns.
+//
+// Deterministic assembly without atomics.  Two lattice cells whose indices
+// have the same parity in every axis share no node (their node ranges are at
+// least one cell apart).  So each of the 2^d parities (colours) has its own
+// accumulator vector in the storage layout (each macro writes its own copy of
+// an interface node): within one colour every slot has at most one writing
+// thread, which stores its cell's sum over the cell's simplices (added in a
+// fixed order), and all colours run in one launch.  Colours whose cells do
+// not hold a slot leave it zero.  The accumulators are tiled by 32 slots:
+// accumulator (slot, colour) sits at ((slot / 32) 2^d + colour) 32 + slot % 32,
+// so the 2^d colours of 32 consecutive slots form one contiguous block.  Every
+// accumulator that some cell of its colour covers is rewritten by that cell
+// on every application (zeros included), and the others are never written
+// and stay zero from the set-up.  A fold then adds, for every unique node, its
+// storage copies in ascending slot order and, for each copy, the 2^d colour
+// values in ascending order.  The summation order is fixed, so results are
+// bitwise equal run to run.
+//
+// Iterations run in batches of kCheckEvery between reads of the residual by
+// the host: the scalar kernel sets a done flag on the device once the residual
+// (or the iteration budget) is reached, and every later kernel of the batch
+// returns at once.
 //
 // Dirichlet conditions: boundary unknowns keep c_bnd; CG runs on the
 // interior unknowns (search directions are zero on the boundary).
@@ -29,6 +49,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "elm_internal.h"
@@ -345,36 +366,84 @@ void blended_element_tables(const elm_mesh_s* me, std::vector<double>& out) {
 // Device: the operator y += scale (M + alpha A) x over all micro simplices.
 // ---------------------------------------------------------------------------
 
+// CG scalars on the device.  done: the residual or the iteration budget was
+// reached (set by k_cg_scalars); iters: iterations completed.
+struct Scalars {
+  double rz, rz_new, pq, rr, bb, alpha, beta, stop_rr;
+  int done, iters, budget, pad;
+};
+
 struct OpArgs {
   const void* tables;       // per macro: M [nb*nb], then A [n_perm][nb*nb]; blended: per simplex
-  const int4* cells;        // work list: (macro, c0, first index in slab c0, count)
+  const int4* chunks;       // work list: (macro, first cell, count, colour) per block
+  const int4* cellv;        // cells (c0, c1, c2) of all colours, macro by macro
   const int64_t* unique_map;
   int npm;                  // storage nodes per macro
   int N;                    // 2^L
+  const Scalars* sc;        // CG scalars: the kernels return once sc->done is set (null: always run)
 };
 
 __device__ __forceinline__ int tri2d(int k) { return k * (k + 1) / 2; }
 __device__ __forceinline__ int tri3d(int k) { return k * (k + 1) * (k + 2) / 6; }
 
-// Row r of the slab-c0 index i (3D: i = r(r+1)/2 + c2, c2 <= r).
-__device__ __forceinline__ int row_of(int i) {
-  int r = int((sqrtf(8.0f * float(i) + 1.0f) - 1.0f) * 0.5f);
-  while (r > 0 && tri2d(r) > i) --r;
-  while (tri2d(r + 1) <= i) ++r;
-  return r;
+// Axis sigma_k of permutation sg (the order of perm_of), as a constant
+// expression for the unrolled simplex loop of k_apply.
+__host__ __device__ constexpr int perm_axis(int d, int sg, int k) {
+  return d == 2 ? (k == 0 ? sg : 1 - sg)
+                : (sg == 0 ? (k == 0 ? 0 : k == 1 ? 1 : 2)
+                   : sg == 1 ? (k == 0 ? 0 : k == 1 ? 2 : 1)
+                   : sg == 2 ? (k == 0 ? 1 : k == 1 ? 0 : 2)
+                   : sg == 3 ? (k == 0 ? 1 : k == 1 ? 2 : 0)
+                   : sg == 4 ? (k == 0 ? 2 : k == 1 ? 0 : 1)
+                             : (k == 0 ? 2 : k == 1 ? 1 : 0));
+}
+// Node lattice offset along axis r of vertex k of the Kuhn simplex sg of a
+// cell (P node points per cell edge): P times the number of the first k
+// sorted axes equal to r.
+__host__ __device__ constexpr int vtx_off(int d, int sg, int k, int r, int P) {
+  return P * ((k > 0 && perm_axis(d, sg, 0) == r) + (k > 1 && perm_axis(d, sg, 1) == r) +
+              (k > 2 && perm_axis(d, sg, 2) == r));
+}
+// Local node j of the simplex (vertices, then edges (u, v), u < v,
+// lexicographic), as an index of the cell's (P + 1)^d node box.
+__host__ __device__ constexpr int edge_u(int d, int j) {
+  return d == 3 ? (j == 4 || j == 5 || j == 6 ? 0 : j == 7 || j == 8 ? 1 : 2) : (j == 3 || j == 4 ? 0 : 1);
+}
+__host__ __device__ constexpr int edge_v(int d, int j) {
+  return d == 3 ? (j == 4 ? 1 : j == 5 || j == 7 ? 2 : 3) : (j == 3 ? 1 : 2);
+}
+__host__ __device__ constexpr int node_off(int d, int sg, int j, int r, int P) {
+  return j <= d ? vtx_off(d, sg, j, r, P)
+                : (vtx_off(d, sg, edge_u(d, j), r, P) + vtx_off(d, sg, edge_v(d, j), r, P)) / 2;
+}
+template <int D, int P>
+__host__ __device__ constexpr int local_index(int sg, int j) {
+  return D == 3 ? (node_off(D, sg, j, 0, P) * (P + 1) + node_off(D, sg, j, 1, P)) * (P + 1) + node_off(D, sg, j, 2, P)
+                : node_off(D, sg, j, 0, P) * (P + 1) + node_off(D, sg, j, 1, P);
 }
 
-// DIAG: add only the diagonal of scale (M + alpha A) (x unused).  BL: the
-// mesh is blended (2D) and every micro simplex has its own tables
-// (blended_element_tables) instead of one per orientation and macro.
+// ys[colour][slot] = scale (M + alpha A) x summed over the simplices of one
+// cell that lie in the macro, for every node of the cell's (P + 1)^d node box,
+// into the accumulators of the cell's colour (no two cells of one colour
+// share a node, so a store suffices).
+// The cell's x values are gathered once and its sums kept in registers (the
+// simplex loop is unrolled, so every local node index is a constant).  DIAG:
+// only the diagonal (x unused).  BL: the mesh is blended (2D) and every micro
+// simplex has its own tables (blended_element_tables) instead of one per
+// orientation and macro.
 template <int D, class R, int P, bool DIAG, bool BL = false>
-__global__ void __launch_bounds__(kDiffThreads) k_apply(OpArgs a, const R* __restrict__ x, R* __restrict__ y,
+__global__ void __launch_bounds__(kDiffThreads) k_apply(OpArgs a, const R* __restrict__ x, R* __restrict__ ys_all,
                                                         R alpha, R scale) {
   constexpr int NB = n_local(D, P);
   constexpr int NP = n_perm(D);
   constexpr int TAB = NB * NB * (1 + NP);
+  constexpr int W = P + 1;
+  constexpr int NC = D == 3 ? W * W * W : W * W;
   __shared__ R E[BL ? 1 : NP][NB * NB];  // M + alpha A_sigma of the block's macro
-  const int4 ck = a.cells[blockIdx.x];
+  if (a.sc != nullptr && a.sc->done) return;  // uniform over the grid
+  const int4 ck = a.chunks[blockIdx.x];
+  constexpr int NCOL = 1 << D;
+  R* ys = ys_all + 32 * ck.w;  // + (slot / 32) 32 NCOL + slot % 32
   if constexpr (!BL) {
     const R* tab = static_cast<const R*>(a.tables) + size_t(ck.x) * TAB;
     for (int t = threadIdx.x; t < NP * NB * NB; t += blockDim.x) {
@@ -383,23 +452,28 @@ __global__ void __launch_bounds__(kDiffThreads) k_apply(OpArgs a, const R* __res
     }
     __syncthreads();
   }
-  if (int(threadIdx.x) >= ck.w) return;
-  // the cell c of this thread (c0 = slab, then row and position)
-  int c[3];
-  const int i = ck.z + int(threadIdx.x);
-  c[0] = ck.y;
-  if (D == 3) {
-    c[1] = row_of(i);
-    c[2] = i - tri2d(c[1]);
-  } else {
-    c[1] = i;
-  }
+  if (int(threadIdx.x) >= ck.z) return;
+  const int4 cv = a.cellv[ck.y + int(threadIdx.x)];
+  const int c[3] = {cv.x, cv.y, cv.z};
   const int64_t base = int64_t(ck.x) * a.npm;
-  const int M = P * 1;  // node lattice points per cell edge
-#pragma unroll 1
+  // the cell's node box: slots (nodes outside the macro's reference simplex,
+  // p1 >= p2 [>= p3], do not exist and stay untouched)
+  int64_t sl[NC];
+  bool ex[NC];
+  R xc[NC], acc[NC];
+#pragma unroll
+  for (int l = 0; l < NC; ++l) {
+    const int i0 = D == 3 ? l / (W * W) : l / W;
+    const int i1 = D == 3 ? (l / W) % W : l % W;
+    const int i2 = D == 3 ? l % W : 0;
+    const int q0 = P * c[0] + i0, q1 = P * c[1] + i1, q2 = D == 3 ? P * c[2] + i2 : 0;
+    ex[l] = q0 >= q1 && (D == 2 || q1 >= q2);
+    sl[l] = base + (D == 3 ? tri3d(q0) + tri2d(q1) + q2 : tri2d(q0) + q1);
+    xc[l] = (!DIAG && ex[l]) ? x[a.unique_map[sl[l]]] : R(0);
+    acc[l] = R(0);
+  }
+#pragma unroll
   for (int sg = 0; sg < NP; ++sg) {
-    int s[3];
-    perm_of(D, sg, s);
     // the simplex lies in the macro's reference simplex iff axes with equal
     // cell coordinates keep their order (a before b for a < b)
     bool inside = true;
@@ -407,70 +481,55 @@ __global__ void __launch_bounds__(kDiffThreads) k_apply(OpArgs a, const R* __res
     for (int u = 0; u < D; ++u)
 #pragma unroll
       for (int v = u + 1; v < D; ++v)
-        if (c[s[u]] == c[s[v]] && s[u] > s[v]) inside = false;
+        if (c[perm_axis(D, sg, u)] == c[perm_axis(D, sg, v)] && perm_axis(D, sg, u) > perm_axis(D, sg, v))
+          inside = false;
     if (!inside) continue;
-    // lattice points of the vertices (node lattice: P c + P w_k)
-    int W[4][3];
-#pragma unroll
-    for (int r = 0; r < D; ++r) W[0][r] = M * c[r];
-#pragma unroll
-    for (int k = 1; k <= D; ++k) {
-#pragma unroll
-      for (int r = 0; r < D; ++r) W[k][r] = W[k - 1][r];
-      W[k][s[k - 1]] += M;
-    }
-    int64_t uid[NB];
-    R xl[NB];
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      int q[3];
-      if (j <= D) {
-#pragma unroll
-        for (int r = 0; r < D; ++r) q[r] = W[j][r];
-      } else {  // edge (u, v), u < v lexicographic: midpoint
-        int u = 0, v = 1, n = D + 1;
-#pragma unroll
-        for (int uu = 0; uu <= D; ++uu)
-#pragma unroll
-          for (int vv = uu + 1; vv <= D; ++vv, ++n)
-            if (n == j) { u = uu; v = vv; }
-#pragma unroll
-        for (int r = 0; r < D; ++r) q[r] = (W[u][r] + W[v][r]) / 2;
-      }
-      const int64_t slot = base + (D == 3 ? tri3d(q[0]) + tri2d(q[1]) + q[2] : tri2d(q[0]) + q[1]);
-      uid[j] = a.unique_map[slot];
-      xl[j] = DIAG ? R(0) : x[uid[j]];
-    }
+    const R* te = nullptr;
     if constexpr (BL) {
       // the simplex's own tables: [M | A] after the cells before it
       const int64_t ncell = int64_t(a.N) * (a.N + 1) / 2;
-      const R* te = static_cast<const R*>(a.tables) +
-                    ((int64_t(ck.x) * ncell + tri2d(c[0]) + c[1]) * NP + sg) * 2 * NB * NB;
+      te = static_cast<const R*>(a.tables) + ((int64_t(ck.x) * ncell + tri2d(c[0]) + c[1]) * NP + sg) * 2 * NB * NB;
+    }
 #pragma unroll
-      for (int ii = 0; ii < NB; ++ii) {
-        R v = R(0);
-        if (DIAG) {
-          v = scale * (te[ii * NB + ii] + alpha * te[NB * NB + ii * NB + ii]);
-        } else {
+    for (int ii = 0; ii < NB; ++ii) {
+      R v = R(0);
+      if (DIAG) {
+        v = BL ? scale * (te[ii * NB + ii] + alpha * te[NB * NB + ii * NB + ii]) : E[sg][ii * NB + ii];
+      } else {
 #pragma unroll
-          for (int j = 0; j < NB; ++j) v += scale * (te[ii * NB + j] + alpha * te[NB * NB + ii * NB + j]) * xl[j];
+        for (int j = 0; j < NB; ++j) {
+          const R e = BL ? scale * (te[ii * NB + j] + alpha * te[NB * NB + ii * NB + j]) : E[sg][ii * NB + j];
+          v += e * xc[local_index<D, P>(sg, j)];
         }
-        atomicAdd(y + uid[ii], v);
       }
-    } else {
-#pragma unroll
-      for (int ii = 0; ii < NB; ++ii) {
-        R v = R(0);
-        if (DIAG) {
-          v = E[sg][ii * NB + ii];
-        } else {
-#pragma unroll
-          for (int j = 0; j < NB; ++j) v += E[sg][ii * NB + j] * xl[j];
-        }
-        atomicAdd(y + uid[ii], v);
-      }
+      acc[local_index<D, P>(sg, ii)] += v;
     }
   }
+#pragma unroll
+  for (int l = 0; l < NC; ++l)
+    if (ex[l]) ys[(sl[l] >> 5) * (32 * NCOL) + (sl[l] & 31)] = acc[l];
+}
+
+// y[u] += the sum over the storage copies of unique node u (ascending slot
+// order: fold_off / fold_slots) of their NCOL colour accumulators (ascending
+// colour; one warp-uniform loop, so every access is coalesced).
+template <class R, int NCOL>
+__global__ void k_fold(const R* __restrict__ ys, R* __restrict__ y, const int* __restrict__ off,
+                       const int* __restrict__ slots, int64_t n, const Scalars* sc) {
+  if (sc != nullptr && sc->done) return;
+  const int64_t u = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  R v = R(0);
+  for (int k = off[u]; k < off[u + 1]; ++k) {
+    const int sl = slots[k];
+    const R* e = ys + int64_t(sl >> 5) * (32 * NCOL) + (sl & 31);
+    R w[NCOL];
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) w[c] = __ldg(e + 32 * c);
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) v += w[c];
+  }
+  y[u] += v;
 }
 
 // ---------------------------------------------------------------------------
@@ -478,9 +537,6 @@ __global__ void __launch_bounds__(kDiffThreads) k_apply(OpArgs a, const R* __res
 // in a fixed order, then one block sums the partials in a fixed order).
 // ---------------------------------------------------------------------------
 
-struct Scalars {
-  double rz, rz_new, pq, rr, bb, alpha, beta, pad;
-};
 
 // Sum over the block (fixed shuffle tree, so deterministic); valid in thread
 // 0.  sh holds one value per warp; callers separate two sums by a barrier.
@@ -523,22 +579,34 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_start(R* r, R* z, R* p, R* q
   }
 }
 
-// partial of p.q (q zero on the boundary, p zero there already)
-template <class R>
-__global__ void __launch_bounds__(kRedThreads) k_cg_pq(const R* p, R* q, const uint8_t* bnd, int64_t n,
-                                                       double* part) {
+// The CG iteration's operator result and p.q in one pass: q = the fold of
+// the colour accumulators (as k_fold; q is overwritten), zero on the
+// boundary; partial of p.q.
+template <class R, int NCOL>
+__global__ void __launch_bounds__(kRedThreads) k_fold_pq(const R* __restrict__ ys, const R* __restrict__ p,
+                                                         R* __restrict__ q, const int* __restrict__ off,
+                                                         const int* __restrict__ slots, const uint8_t* bnd,
+                                                         int64_t n, double* part, const Scalars* sc) {
   __shared__ double sh[kRedThreads / 32];
+  if (sc->done) return;
   R pq = R(0);
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    R qi = q[i];
-    if (bnd[i]) {
-      qi = R(0);
-      q[i] = qi;
+  for (int64_t u = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; u < n; u += int64_t(gridDim.x) * blockDim.x) {
+    R v = R(0);
+    for (int k = off[u]; k < off[u + 1]; ++k) {
+      const int sl = slots[k];
+      const R* e = ys + int64_t(sl >> 5) * (32 * NCOL) + (sl & 31);
+      R w[NCOL];
+#pragma unroll
+      for (int c = 0; c < NCOL; ++c) w[c] = __ldg(e + 32 * c);
+#pragma unroll
+      for (int c = 0; c < NCOL; ++c) v += w[c];
     }
-    pq += p[i] * qi;
+    if (bnd[u]) v = R(0);
+    q[u] = v;
+    pq += p[u] * v;
   }
-  const double s = block_sum(double(pq), sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  const double t = block_sum(double(pq), sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // x += alpha p; r -= alpha q; z = dinv r; partials (r.z, r.r).
@@ -546,6 +614,7 @@ template <class R>
 __global__ void __launch_bounds__(kRedThreads) k_cg_update(R* x, R* r, R* z, const R* p, const R* q, const R* dinv,
                                                            const Scalars* sc, int64_t n, double* part) {
   __shared__ double sh[kRedThreads / 32];
+  if (sc->done) return;
   const R al = R(sc->alpha);
   R rz = R(0), rr = R(0);
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
@@ -566,20 +635,23 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(R* x, R* r, R* z, con
   }
 }
 
-// p = z + beta p; q = 0 for the next operator application.
+// p = z + beta p (q is overwritten by the next k_fold_pq).
 template <class R>
-__global__ void __launch_bounds__(kRedThreads) k_cg_direction(R* p, R* q, const R* z, const Scalars* sc, int64_t n) {
+__global__ void __launch_bounds__(kRedThreads) k_cg_direction(R* p, const R* z, const Scalars* sc, int64_t n) {
+  if (sc->done) return;
   const R be = R(sc->beta);
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     p[i] = z[i] + be * p[i];
-    q[i] = R(0);
-  }
 }
 
 // Sums the partials of a reduction and updates the CG scalars:
-// what = 0: start (rz, rr); 1: p.q -> alpha; 2: update (rz_new, rr) -> beta.
-__global__ void __launch_bounds__(kRedThreads) k_cg_scalars(const double* part, int nparts, int what, Scalars* sc) {
+// what = 0: start (rz, rr; the stopping residual and the iteration budget);
+// 1: p.q -> alpha; 2: update (rz_new, rr) -> beta, one iteration done.  Sets
+// done once |r|^2 <= stop_rr (or it is not finite) or the budget is spent.
+__global__ void __launch_bounds__(kRedThreads) k_cg_scalars(const double* part, int nparts, int what, Scalars* sc,
+                                                            double stop_rr, int budget) {
   __shared__ double sh[kRedThreads / 32];
+  if (what != 0 && sc->done) return;
   double s1 = 0.0, s2 = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
     s1 += part[i];
@@ -592,6 +664,10 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_scalars(const double* part, 
     if (what == 0) {
       sc->rz = a;
       sc->rr = b;
+      sc->stop_rr = stop_rr;
+      sc->budget = budget;
+      sc->iters = 0;
+      sc->done = (b <= stop_rr || !isfinite(b) || budget <= 0) ? 1 : 0;
     } else if (what == 1) {
       sc->pq = a;
       sc->alpha = a != 0.0 ? sc->rz / a : 0.0;
@@ -600,6 +676,8 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_scalars(const double* part, 
       sc->rr = b;
       sc->beta = sc->rz != 0.0 ? a / sc->rz : 0.0;
       sc->rz = a;
+      sc->iters += 1;
+      if (b <= sc->stop_rr || !isfinite(b) || sc->iters >= sc->budget) sc->done = 1;
     }
   }
 }
@@ -699,15 +777,39 @@ elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
       }
     }
   }
-  // cell work list: slab c0 holds (c0+1)(c0+2)/2 cells in 3D, c0+1 in 2D
-  std::vector<int4> cells;
-  for (int64_t m = 0; m < me->n_macros; ++m)
-    for (int c0 = 0; c0 < me->N; ++c0) {
-      const int len = d == 3 ? (c0 + 1) * (c0 + 2) / 2 : c0 + 1;
-      for (int i0 = 0; i0 < len; i0 += kDiffThreads)
-        cells.push_back(make_int4(int(m), c0, i0, std::min(kDiffThreads, len - i0)));
+  // cells of every macro (c0 >= c1 [>= c2] >= 0, c0 < N) by colour (the
+  // parity of each index), then macro; chunks of at most kDiffThreads cells
+  // of one colour and one macro
+  const int ncol = 1 << d;
+  std::vector<int4> cells, cellv;
+  me->cell_color_off.assign(ncol + 1, 0);
+  for (int col = 0; col < ncol; ++col) {
+    me->cell_color_off[col] = int64_t(cells.size());
+    for (int64_t m = 0; m < me->n_macros; ++m) {
+      const int64_t first = int64_t(cellv.size());
+      for (int c0 = col & 1; c0 < me->N; c0 += 2)
+        for (int c1 = (col >> 1) & 1; c1 <= c0; c1 += 2) {
+          if (d == 2) {
+            cellv.push_back(make_int4(c0, c1, 0, 0));
+            continue;
+          }
+          for (int c2 = (col >> 2) & 1; c2 <= c1; c2 += 2) cellv.push_back(make_int4(c0, c1, c2, 0));
+        }
+      const int64_t last = int64_t(cellv.size());
+      for (int64_t c = first; c < last; c += kDiffThreads)
+        cells.push_back(make_int4(int(m), int(c), int(std::min<int64_t>(kDiffThreads, last - c)), col));
     }
+  }
+  me->cell_color_off[ncol] = int64_t(cells.size());
   me->n_cell_chunks = int64_t(cells.size());
+  // fold lists: the storage copies of every unique node in ascending slot order
+  std::vector<int> foff(me->n_unique + 1, 0), fslots(me->n_storage);
+  for (int64_t sl = 0; sl < me->n_storage; ++sl) ++foff[me->unique_map[sl] + 1];
+  for (int64_t u = 0; u < me->n_unique; ++u) foff[u + 1] += foff[u];
+  {
+    std::vector<int> next(foff.begin(), foff.end() - 1);
+    for (int64_t sl = 0; sl < me->n_storage; ++sl) fslots[next[me->unique_map[sl]]++] = int(sl);
+  }
   const size_t es = me->precision == ELM_FP64 ? 8 : 4;
   bool ok = true;
   ok = ok && cudaMalloc(&me->d_dtab, tab * me->n_macros * es) == cudaSuccess;
@@ -723,6 +825,21 @@ elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
        cudaMemcpy(me->d_dbnd, bnd.data(), me->n_unique, cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&me->d_dcells, sizeof(int4) * cells.size()) == cudaSuccess &&
        cudaMemcpy(me->d_dcells, cells.data(), sizeof(int4) * cells.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&me->d_dcellv, sizeof(int4) * cellv.size()) == cudaSuccess &&
+       cudaMemcpy(me->d_dcellv, cellv.data(), sizeof(int4) * cellv.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&me->d_dfold_off, sizeof(int) * foff.size()) == cudaSuccess &&
+       cudaMemcpy(me->d_dfold_off, foff.data(), sizeof(int) * foff.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&me->d_dfold_slots, sizeof(int) * fslots.size()) == cudaSuccess &&
+       cudaMemcpy(me->d_dfold_slots, fslots.data(), sizeof(int) * fslots.size(), cudaMemcpyHostToDevice) ==
+           cudaSuccess;
+  // the colour accumulators, tiled by 32 slots, in the mesh precision (and a
+  // second, FP32 set for the inner solves of FP64 meshes: the zero entries no
+  // cell writes must stay zero in each precision's own layout); zero where no
+  // cell of the colour ever writes
+  const size_t ysn = size_t((me->n_storage + 31) / 32 * 32) * size_t(ncol);
+  ok = ok && cudaMalloc(&me->d_dys, ysn * es) == cudaSuccess && cudaMemset(me->d_dys, 0, ysn * es) == cudaSuccess;
+  if (me->precision == ELM_FP64)
+    ok = ok && cudaMalloc(&me->d_dys32, ysn * 4) == cudaSuccess && cudaMemset(me->d_dys32, 0, ysn * 4) == cudaSuccess;
   ok = ok && cudaMalloc(&me->d_dvec, size_t(kDiffVectors) * me->n_unique * es) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&me->d_dpart, sizeof(double) * 2 * kRedMaxBlocks) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&me->d_dscal, sizeof(Scalars) + 2 * sizeof(double)) == cudaSuccess;
@@ -757,45 +874,66 @@ elm_status build_diffusion_blended(elm_mesh_s* me, std::string* err) {
 
 namespace {
 
-// tables: the element tables in the precision R (null: the mesh's own).
+// y += scale (M + alpha A) x (diag: the diagonal only): the cell pass into
+// the colour accumulators, then (fold) their fold into y.  tables: the element
+// tables in the precision R (null: the mesh's own).  sc: the CG scalars whose
+// done flag ends the work early (null: always applied).
 template <class R>
 cudaError_t apply_op(const elm_mesh_s* me, const R* x, R* y, double alpha, double scale, bool diag, cudaStream_t s,
-                     const void* tables = nullptr) {
+                     const void* tables = nullptr, const Scalars* sc = nullptr, bool fold = true) {
   const bool blended = me->blend.nsec > 0;
-  OpArgs a{tables ? tables : (blended ? me->d_dtab_el : me->d_dtab), me->d_dcells, me->d_unique_map, int(me->npm),
-           me->N};
+  OpArgs a{tables ? tables : (blended ? me->d_dtab_el : me->d_dtab), me->d_dcells, me->d_dcellv, me->d_unique_map,
+           int(me->npm), me->N, sc};
+  R* ys = static_cast<R*>(sizeof(R) == 4 && me->precision == ELM_FP64 ? me->d_dys32 : me->d_dys);
+  const R al = R(alpha), sca = R(scale);
   const unsigned g = unsigned(me->n_cell_chunks);
-  if (g == 0) return cudaSuccess;
-  const R al = R(alpha), sc = R(scale);
-  if constexpr (sizeof(R) == 8) {
-    if (blended) {  // 2D FP64 only (elm_mesh_set_annulus)
-      if (me->order == 2) {
-        if (diag) k_apply<2, R, 2, true, true><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);
-        else k_apply<2, R, 2, false, true><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);
-      } else {
-        if (diag) k_apply<2, R, 1, true, true><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);
-        else k_apply<2, R, 1, false, true><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);
+  if (g > 0) {
+    bool launched = false;
+    if constexpr (sizeof(R) == 8) {
+      if (blended) {  // 2D FP64 only (elm_mesh_set_annulus)
+        if (me->order == 2) {
+          if (diag) k_apply<2, R, 2, true, true><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);
+          else k_apply<2, R, 2, false, true><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);
+        } else {
+          if (diag) k_apply<2, R, 1, true, true><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);
+          else k_apply<2, R, 1, false, true><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);
+        }
+        launched = true;
       }
-      return cudaGetLastError();
+    }
+    if (!launched) {
+      if (blended) return cudaErrorInvalidValue;
+#define ELM_APPLY(DD, PP)                                                              \
+  if (diag) k_apply<DD, R, PP, true><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);   \
+  else k_apply<DD, R, PP, false><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);
+      if (me->dim == 3) {
+        if (me->order == 2) { ELM_APPLY(3, 2) } else { ELM_APPLY(3, 1) }
+      } else {
+        if (me->order == 2) { ELM_APPLY(2, 2) } else { ELM_APPLY(2, 1) }
+      }
+#undef ELM_APPLY
     }
   }
-  if (blended) return cudaErrorInvalidValue;
-#define ELM_APPLY(DD, PP)                                                              \
-  if (diag) k_apply<DD, R, PP, true><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);     \
-  else k_apply<DD, R, PP, false><<<g, kDiffThreads, 0, s>>>(a, x, y, al, sc);
-  if (me->dim == 3) {
-    if (me->order == 2) { ELM_APPLY(3, 2) } else { ELM_APPLY(3, 1) }
-  } else {
-    if (me->order == 2) { ELM_APPLY(2, 2) } else { ELM_APPLY(2, 1) }
+  const int64_t n = me->n_unique;
+  const unsigned fb = unsigned((n + 255) / 256);
+  if (fold && n > 0) {
+    if (me->dim == 3)
+      k_fold<R, 8><<<fb, 256, 0, s>>>(ys, y, me->d_dfold_off, me->d_dfold_slots, n, sc);
+    else
+      k_fold<R, 4><<<fb, 256, 0, s>>>(ys, y, me->d_dfold_off, me->d_dfold_slots, n, sc);
   }
-#undef ELM_APPLY
   return cudaGetLastError();
 }
 
 // PCG iterations on the interior from the state of k_cg_start (r, z = D^{-1} r,
-// p = z, sc->rz / rr): stops when |r|^2 <= stop_rr or after `budget`
-// iterations.  *done = iterations run, *rr = final |r|^2.  Returns false on a
-// CUDA error (message in *err).
+// p = z; its partials of r.z and r.r in the reduction space): stops when
+// |r|^2 <= stop_rr or after `budget` iterations.  The iterations are enqueued
+// in batches of kCheckEvery; the device sets the done flag (k_cg_scalars) and
+// the kernels after it return at once, so the host reads the scalars once per
+// batch.  *done = iterations run, *rr = final |r|^2.  Returns false on a CUDA
+// error (message in *err).
+constexpr int kCheckEvery = 8;
+
 template <class R>
 bool pcg_iterate(const elm_mesh_s* me, const void* tab, R* x, R* r, R* z, R* p, R* qv, const R* dinv, double alpha,
                  double stop_rr, int budget, int* done, double* rr, cudaStream_t s, std::string* err) {
@@ -807,27 +945,31 @@ bool pcg_iterate(const elm_mesh_s* me, const void* tab, R* x, R* r, R* z, R* p, 
     if (e != cudaSuccess) *err = std::string(where) + ": " + cudaGetErrorString(e);
     return e == cudaSuccess;
   };
-  auto read_rr = [&]() -> bool {
-    Scalars h;
+  k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 0, sc, stop_rr, budget);
+  Scalars h{};
+  for (;;) {
     if (!chk(cudaMemcpyAsync(&h, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s), "read") ||
         !chk(cudaStreamSynchronize(s), "sync"))
       return false;
-    *rr = h.rr;
-    return true;
-  };
-  *done = 0;
-  if (!read_rr()) return false;
-  while (*rr > stop_rr && *done < budget && std::isfinite(*rr)) {
-    // q is zero here (k_cg_start, k_cg_direction)
-    if (!chk(apply_op<R>(me, p, qv, alpha, 1.0, false, s, tab), "apply")) return false;
-    k_cg_pq<R><<<nred, kRedThreads, 0, s>>>(p, qv, me->d_dbnd, n, part);
-    k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 1, sc);
-    k_cg_update<R><<<nred, kRedThreads, 0, s>>>(x, r, z, p, qv, dinv, sc, n, part);
-    k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 2, sc);
-    k_cg_direction<R><<<nred, kRedThreads, 0, s>>>(p, qv, z, sc, n);
-    ++*done;
-    if (!read_rr()) return false;
+    if (h.done) break;
+    for (int k = 0; k < kCheckEvery; ++k) {
+      // q = E p (the fold of the cell pass) and p.q in one pass
+      if (!chk(apply_op<R>(me, p, qv, alpha, 1.0, false, s, tab, sc, false), "apply")) return false;
+      const R* ys = static_cast<const R*>(sizeof(R) == 4 && me->precision == ELM_FP64 ? me->d_dys32 : me->d_dys);
+      if (me->dim == 3)
+        k_fold_pq<R, 8><<<nred, kRedThreads, 0, s>>>(ys, p, qv, me->d_dfold_off, me->d_dfold_slots, me->d_dbnd, n,
+                                                     part, sc);
+      else
+        k_fold_pq<R, 4><<<nred, kRedThreads, 0, s>>>(ys, p, qv, me->d_dfold_off, me->d_dfold_slots, me->d_dbnd, n,
+                                                     part, sc);
+      k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 1, sc, 0.0, 0);
+      k_cg_update<R><<<nred, kRedThreads, 0, s>>>(x, r, z, p, qv, dinv, sc, n, part);
+      k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 2, sc, 0.0, 0);
+      k_cg_direction<R><<<nred, kRedThreads, 0, s>>>(p, z, sc, n);
+    }
   }
+  *done = h.iters;
+  *rr = h.rr;
   return true;
 }
 
@@ -856,7 +998,6 @@ elm_status solve_mixed(elm_mesh_s* me, const void* c_hat, const void* c_bnd, con
   float* d32 = w + 4 * n;
   float* dinv32 = w + 5 * n;
   double* part = me->d_dpart;
-  Scalars* sc = reinterpret_cast<Scalars*>(me->d_dscal);
   double* bnorm = me->d_dscal + sizeof(Scalars) / sizeof(double);
   double* rnorm = bnorm + 1;
   const size_t bytes = size_t(n) * sizeof(double);
@@ -906,7 +1047,6 @@ elm_status solve_mixed(elm_mesh_s* me, const void* c_hat, const void* c_bnd, con
     // inner FP32 solve of E d = r from d = 0
     k_residual_to_float<<<eb, 256, 0, s>>>(r, r32, d32, me->d_dbnd, n);
     k_cg_start<float><<<nred, kRedThreads, 0, s>>>(r32, z32, p32, q32, dinv32, me->d_dbnd, n, part);
-    k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 0, sc);
     int done = 0;
     double rr32 = 0.0;
     // stop at kInnerRtol of the inner start, or where the outer tolerance is met
@@ -947,7 +1087,6 @@ elm_status solve(elm_mesh_s* me, const void* c_hat, const void* c_bnd, const voi
   R* b = v + 5 * n;
   R* dinv = v + 6 * n;
   double* part = me->d_dpart;
-  Scalars* sc = reinterpret_cast<Scalars*>(me->d_dscal);
   double* bnorm = me->d_dscal + sizeof(Scalars) / sizeof(double);
   const size_t bytes = size_t(n) * sizeof(R);
   const unsigned eb = unsigned((n + 255) / 256);
@@ -980,7 +1119,6 @@ elm_status solve(elm_mesh_s* me, const void* c_hat, const void* c_bnd, const voi
   k_copy<R><<<eb, 256, 0, s>>>(r, b, n);
   if (!chk(apply_op<R>(me, x, r, alpha, -1.0, false, s), "residual")) return ELM_ERR_CUDA;
   k_cg_start<R><<<nred, kRedThreads, 0, s>>>(r, z, p, qv, dinv, me->d_dbnd, n, part);
-  k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 0, sc);
   double hb = 0.0;
   if (!chk(cudaMemcpyAsync(&hb, bnorm, sizeof(double), cudaMemcpyDeviceToHost, s), "read") ||
       !chk(cudaStreamSynchronize(s), "sync"))

@@ -182,8 +182,14 @@ struct elm_mesh_s {
   void* d_dtab32 = nullptr;          // FP64 meshes: FP32 copy of the tables (inner solves)
   void* d_dvec32 = nullptr;          // FP64 meshes: FP32 vectors of the inner solves
   uint8_t* d_dbnd = nullptr;
-  int4* d_dcells = nullptr;
+  int4* d_dcells = nullptr;          // (macro, first cell, count, colour) chunks of the operator
+  int4* d_dcellv = nullptr;          // cells (c0, c1, c2) in colour, then macro order
   int64_t n_cell_chunks = 0;
+  std::vector<int64_t> cell_color_off;  // chunks of colour k: [off[k], off[k + 1])
+  int* d_dfold_off = nullptr;        // unique id -> its storage copies, ascending slot: [off[u], off[u + 1])
+  int* d_dfold_slots = nullptr;
+  void* d_dys = nullptr;             // colour accumulators per storage slot (mesh precision)
+  void* d_dys32 = nullptr;           // FP64 meshes: the same in FP32 (inner solves)
   int64_t n_boundary = 0;
   void* d_dvec = nullptr;
   double* d_dpart = nullptr;

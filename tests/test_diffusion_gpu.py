@@ -153,3 +153,25 @@ def test_diffusion_errors():
     # kappa = 0 (or tau = 0): the mass matrix alone, c_new = c_hat
     out, _, _ = gm.diffusion_step(c, 0.1, 0.0)
     assert torch.allclose(out, c, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("case", ["cube-p2-fp64", "cube-p2-fp32", "cube-p1-fp32", "square-p2-fp64", "annulus-p2-fp64"])
+def test_diffusion_is_deterministic(case):
+    """The operator adds every element contribution in a fixed order (colour
+    passes and an ordered fold, no atomics), so repeated solves of one
+    system give bitwise the same result and the same iteration count."""
+    kind, p, prec = case.split("-")
+    order = int(p[1])
+    if kind == "annulus":
+        v, m = inputs.annulus_ring(6, 2)
+        mesh = elm.Mesh(v, m, 4, prec, order=order, diffusion=True, annulus=(0.5, 1.5, 6, 0.0))
+    else:
+        v, m = inputs.unit_cube() if kind == "cube" else inputs.unit_square()
+        mesh = elm.Mesh(v, m, 4 if kind == "cube" else 6, prec, order=order, diffusion=True)
+    x = mesh.node_coords()
+    c = torch.tensor(np.exp(-((x - 0.4) ** 2).sum(1) / 0.05) + 0.3 * x[:, 0], dtype=mesh.dtype, device="cuda")
+    rtol = 1e-11 if prec == "fp64" else 1e-5
+    outs = [mesh.diffusion_step(c, 0.01, 0.05, 1.0, rtol=rtol) for _ in range(3)]
+    for o in outs[1:]:
+        assert torch.equal(o[0], outs[0][0])
+        assert o[1] == outs[0][1]
