@@ -30,15 +30,17 @@
  *    the CUDA stream passed as `stream` (a cudaStream_t; NULL = legacy
  *    default stream).  Device memory is allocated only by elm_mesh_create
  *    (its tables and the buffers its flags ask for), elm_mesh_set_annulus (the
- *    sector table, and the blended diffusion tables) and elm_batch_create;
+ *    sector table, and the blended diffusion tables and work lists) and
+ *    elm_batch_create;
  *    the per-step calls allocate nothing.  No call synchronises, except
  *    elm_get_status (which synchronises `stream`) and elm_diffusion_step
  *    (below).
  *  - Errors: argument errors are returned synchronously and leave the
  *    mesh unchanged; device-side conditions (walk limit, non-finite values)
  *    set flags that elm_get_status reports.  No call traps or exits.
- *    (elm_diffusion_step is the one call that also synchronises: its
- *    iterative solve tests convergence on the host.)
+ *    (elm_diffusion_step is the one call that also synchronises: the host
+ *    reads the device's convergence decision between batches of CG
+ *    iterations.)
  *    elm_last_error() returns a thread-local message for the last failure.
  */
 #ifndef ELM_H
@@ -86,9 +88,12 @@ enum { ELM_ADJOINT = 0x200 };
 enum { ELM_P1 = 0x400 };
 
 /* Flag OR-ed into `precision` of elm_mesh_create: also build the diffusion
- * solver of elm_diffusion_step (per macro the element mass matrix and one
- * stiffness matrix per micro-simplex orientation, the boundary mask, and 7
- * solver vectors of elm_mesh_num_unique values in the mesh precision). */
+ * solver of elm_diffusion_step (per macro the element mass matrix, one
+ * stiffness matrix per micro-simplex orientation and the node-centred stencil
+ * weights of its interior; the work lists of the interior rows and of the
+ * cells touching a macro face; boundary and owner masks; 2^dim colour
+ * accumulators and 7 solver vectors per storage node in the mesh precision,
+ * and the FP32 copies of the inner solves on FP64 meshes). */
 enum { ELM_DIFFUSION = 0x800 };
 
 /* Flag OR-ed into `precision` of elm_mesh_create: also set up elm_advect_host
@@ -330,11 +335,14 @@ elm_status elm_trace_eval(elm_mesh mesh, const void* D_dev, const void* T_src_de
  * FP64, the corrections by the same PCG in FP32 (to 3e-5 of their start), so
  * `iterations` counts the FP32 iterations; blended FP64 meshes and FP32 meshes
  * run the PCG in their own precision.
- * The operator is matrix-free; its element sums use atomics, so the last bits
- * can differ between runs.  Requires ELM_DIFFUSION at creation.  Unlike the
- * other calls this one synchronises `stream` (the convergence test reads the
- * residual every iteration).  Returns ELM_ERR_NOT_CONVERGED (with c_new the
- * last iterate) when max_iter iterations do not reach rtol. */
+ * The operator is matrix-free: a node-centred stencil for the nodes inside a
+ * macro and an element pass over the cells touching a macro face (blended
+ * meshes: over every cell); it uses no atomics and sums in a fixed order, so
+ * repeated calls give bitwise equal results.  Requires ELM_DIFFUSION at
+ * creation.  Unlike the other calls this one synchronises `stream`: the
+ * device decides convergence, and the host reads the CG scalars once per 8
+ * iterations.  Returns ELM_ERR_NOT_CONVERGED (with c_new the last iterate)
+ * when max_iter iterations do not reach rtol. */
 elm_status elm_diffusion_step(elm_mesh mesh, const void* c_hat_dev, const void* c_bnd_dev, const void* q_dev,
                               void* c_new_dev, double tau, double kappa, double theta, double rtol, int max_iter,
                               int* iterations, double* residual, void* stream);

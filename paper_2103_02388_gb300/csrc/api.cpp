@@ -58,24 +58,41 @@ void free_tables(elm_mesh_s* me) {
   cudaFree(me->d_dtab);
   cudaFree(me->d_dtab_el);
   cudaFree(me->d_dtab32);
+  cudaFree(me->d_dwtab);
+  cudaFree(me->d_dwtab32);
   cudaFree(me->d_dvec32);
-  me->d_dtab_el = me->d_dtab32 = me->d_dvec32 = nullptr;
-  cudaFree(me->d_dbnd);
+  me->d_dtab_el = me->d_dtab32 = me->d_dwtab = me->d_dwtab32 = me->d_dvec32 = nullptr;
+  cudaFree(me->d_dbnd_s);
+  cudaFree(me->d_dact);
+  cudaFree(me->d_dslot_owner);
+  me->d_dbnd_s = me->d_dact = nullptr;
+  me->d_dslot_owner = nullptr;
+  cudaFree(me->d_dnodes);
+  cudaFree(me->d_ditems);
+  me->d_dnodes = nullptr;
+  me->d_ditems = nullptr;
+  cudaFree(me->d_drow_off);
+  cudaFree(me->d_drow_col);
+  cudaFree(me->d_drow_w);
+  cudaFree(me->d_drow_w32);
+  cudaFree(me->d_drow_copy_off);
+  cudaFree(me->d_drow_copies);
+  me->d_drow_off = me->d_drow_col = me->d_drow_copy_off = me->d_drow_copies = nullptr;
+  me->d_drow_w = me->d_drow_w32 = nullptr;
   cudaFree(me->d_dcells);
   cudaFree(me->d_dcellv);
   cudaFree(me->d_dfold_off);
   cudaFree(me->d_dfold_slots);
-  cudaFree(me->d_dys);
-  cudaFree(me->d_dys32);
-  me->d_dys32 = nullptr;
+  cudaFree(me->d_dfbnd);
+  me->d_dfbnd = nullptr;
   me->d_dcellv = nullptr;
   me->d_dfold_off = me->d_dfold_slots = nullptr;
+  cudaFree(me->d_dys);
   me->d_dys = nullptr;
   cudaFree(me->d_dvec);
   cudaFree(me->d_dpart);
   cudaFree(me->d_dscal);
   me->d_dtab = me->d_dvec = nullptr;
-  me->d_dbnd = nullptr;
   me->d_dcells = nullptr;
   me->d_dpart = me->d_dscal = nullptr;
   me->d_geo = nullptr;

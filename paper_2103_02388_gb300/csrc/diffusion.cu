@@ -16,32 +16,42 @@
 // with the same sigma are translates of one another: their element
 // matrices are equal.  The host computes, per macro, the mass matrix (the
 // same for every sigma, since all micro simplices have the same volume) and
-// one stiffness matrix per sigma; a thread per lattice cell applies the
-// element matrices of the cell's simplices that lie in the macro.  The
-// solver's vectors are in the unique-node layout, so interface nodes shared by
-// several macros are single unknowns.
+// one stiffness matrix per sigma.
 //
-// Deterministic assembly without atomics.  Two lattice cells whose indices
-// have the same parity in every axis share no node (their node ranges are at
-// least one cell apart).  So each of the 2^d parities (colours) has its own
-// accumulator vector in the storage layout (each macro writes its own copy of
-// an interface node): within one colour every slot has at most one writing
-// thread, which stores its cell's sum over the cell's simplices (added in a
-// fixed order), and all colours run in one launch.  Colours whose cells do
-// not hold a slot leave it zero.  The accumulators are tiled by 32 slots:
-// accumulator (slot, colour) sits at ((slot / 32) 2^d + colour) 32 + slot % 32,
-// so the 2^d colours of 32 consecutive slots form one contiguous block.  Every
-// accumulator that some cell of its colour covers is rewritten by that cell
-// on every application (zeros included), and the others are never written
-// and stay zero from the set-up.  A fold then adds, for every unique node, its
-// storage copies in ascending slot order and, for each copy, the 2^d colour
-// values in ascending order.  The summation order is fixed, so results are
-// bitwise equal run to run.
+// Node-centred stencil in the macro interiors.  A node strictly inside a
+// macro lies only in micro simplices of that macro, and those of one
+// orientation are translates of one another, so its row of the assembled
+// matrix depends only on its class (its lattice coordinates mod P: vertex or
+// one of the edge-midpoint classes) and the macro: the host sums the element
+// matrices into per-class, per-macro weights at fixed lattice offsets
+// (StencilShape: 65 offsets for the 3D P2 vertex class, 19 or 27 for its edge
+// classes), and k_stencil applies them, one warp per row segment of one
+// class, each lane one node, every neighbour read directly from the storage
+// layout.  No atomics; each node's row sum has a fixed order.
 //
-// Iterations run in batches of kCheckEvery between reads of the residual by
-// the host: the scalar kernel sets a done flag on the device once the residual
-// (or the iteration budget) is reached, and every later kernel of the batch
-// returns at once.
+// Face nodes (on a face of their macro, shared with a neighbour or on the
+// domain boundary) take their rows from the cell pass over the cells that
+// touch a face.  Two lattice cells whose indices have the same parity in
+// every axis share no node, so each of the 2^d parities (colours) has its own
+// accumulator vector in the storage layout: within one colour every slot has
+// at most one writing thread, which stores its cell's sum over the cell's
+// simplices (added in a fixed order), and all colours run in one launch.  The
+// accumulators are tiled by 32 slots: accumulator (slot, colour) sits at
+// ((slot / 32) 2^d + colour) 32 + slot % 32.  Every accumulator that some
+// face cell of its colour covers is rewritten by that cell on every
+// application, and the others are never written and stay zero from the set-up.
+// A fold then adds, for every face node, its storage copies in ascending slot
+// order and, for each copy, the 2^d colour values in ascending order, and
+// writes the sum to every copy.  A blended mesh, whose simplices each have
+// their own matrices, takes every cell and node through this path.  The
+// summation order is fixed everywhere, so results are bitwise equal run to run.
+//
+// The solver's vectors are in the storage layout (the copies of an interface
+// node hold the same value); dot products count the owner copy of each
+// unknown.  Iterations run in batches of kCheckEvery between reads of the
+// residual by the host: the scalar kernel sets a done flag on the device once
+// the residual (or the iteration budget) is reached, and every later kernel
+// of the batch returns at once.
 //
 // Dirichlet conditions: boundary unknowns keep c_bnd; CG runs on the
 // interior unknowns (search directions are zero on the boundary).
@@ -50,6 +60,7 @@
 #include <cstring>
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "elm_internal.h"
@@ -363,7 +374,7 @@ void blended_element_tables(const elm_mesh_s* me, std::vector<double>& out) {
 }
 
 // ---------------------------------------------------------------------------
-// Device: the operator y += scale (M + alpha A) x over all micro simplices.
+// Device: the operator y += scale (M + alpha A) x.
 // ---------------------------------------------------------------------------
 
 // CG scalars on the device.  done: the residual or the iteration budget was
@@ -373,11 +384,17 @@ struct Scalars {
   int done, iters, budget, pad;
 };
 
+// What an operator pass does with its result v at a node.
+enum OpMode {
+  kOpAccum = 0,  // y += v
+  kOpCg = 1,     // y = v (0 on the Dirichlet boundary), and a partial of p.y (x = p)
+  kOpDiag = 2    // y += the diagonal entry (x unused)
+};
+
 struct OpArgs {
-  const void* tables;       // per macro: M [nb*nb], then A [n_perm][nb*nb]; blended: per simplex
-  const int4* chunks;       // work list: (macro, first cell, count, colour) per block
+  const void* tables;       // blended meshes: per-simplex mass and stiffness
+  const int4* chunks;       // cell pass: (macro, first cell, count, colour) per block
   const int4* cellv;        // cells (c0, c1, c2) of all colours, macro by macro
-  const int64_t* unique_map;
   int npm;                  // storage nodes per macro
   int N;                    // 2^L
   const Scalars* sc;        // CG scalars: the kernels return once sc->done is set (null: always run)
@@ -422,9 +439,269 @@ __host__ __device__ constexpr int local_index(int sg, int j) {
                 : node_off(D, sg, j, 0, P) * (P + 1) + node_off(D, sg, j, 1, P);
 }
 
+// Node-centred stencil of the assembled operator inside a macro.  A node q
+// strictly inside a macro's reference simplex lies only in micro simplices of
+// that macro, and the simplices of one orientation sigma are translates of
+// one another, so row q of the assembled matrix depends only on the class of
+// q (q mod P per axis: the vertex class and, for P2, the edge-midpoint
+// classes) and on the macro: entry (q, q + o) is the sum, over the simplices
+// holding q as their local node i, of the element entries (i, j) with node j
+// at offset o.  StencilShape lists, per class, the offsets o that occur
+// (lexicographic order) and the index of o = 0; the weights are per macro
+// (stencil_weights).  3D P2: 65 offsets for the vertex class, 19 or 27 for
+// the edge classes; P1: 15 (3D), 7 (2D).
+template <int D, int P>
+struct StencilShape {
+  static constexpr int NCLS = P == 2 ? (1 << D) : 1;
+  static constexpr int MAXE = D == 3 ? (2 * P + 1) * (2 * P + 1) * (2 * P + 1) : (2 * P + 1) * (2 * P + 1);
+  int n[NCLS];             // offsets of class k
+  int start[NCLS + 1];     // first entry of class k in the per-macro weight table
+  int centre[NCLS];        // entry of o = 0 within class k
+  int off[NCLS][MAXE][3];  // offsets (axis 0 = q0, the slowest axis of the packed index)
+  __host__ __device__ constexpr StencilShape() : n{}, start{}, centre{}, off{} {
+    for (int sg = 0; sg < n_perm(D); ++sg)
+      for (int i = 0; i < n_local(D, P); ++i) {
+        const int k = class_of_node(sg, i);
+        for (int j = 0; j < n_local(D, P); ++j) {
+          int o[3] = {0, 0, 0};
+          for (int r = 0; r < D; ++r) o[r] = node_off(D, sg, j, r, P) - node_off(D, sg, i, r, P);
+          int pos = 0;
+          bool found = false;
+          for (; pos < n[k]; ++pos) {
+            const int c = compare(off[k][pos], o);
+            if (c == 0) found = true;
+            if (c >= 0) break;
+          }
+          if (found) continue;
+          for (int t = n[k]; t > pos; --t)
+            for (int r = 0; r < 3; ++r) off[k][t][r] = off[k][t - 1][r];
+          for (int r = 0; r < 3; ++r) off[k][pos][r] = o[r];
+          ++n[k];
+        }
+      }
+    for (int k = 0; k < NCLS; ++k) {
+      start[k + 1] = start[k] + n[k];
+      const int z[3] = {0, 0, 0};
+      for (int e = 0; e < n[k]; ++e)
+        if (compare(off[k][e], z) == 0) centre[k] = e;
+    }
+  }
+  // class of local node i of the simplex sg in a cell at the lattice origin
+  __host__ __device__ static constexpr int class_of_node(int sg, int i) {
+    int k = 0;
+    for (int r = 0; r < D; ++r) k |= (node_off(D, sg, i, r, P) % P) << r;
+    return k;
+  }
+  __host__ __device__ static constexpr int compare(const int* a, const int* b) {
+    for (int r = 0; r < 3; ++r)
+      if (a[r] != b[r]) return a[r] < b[r] ? -1 : 1;
+    return 0;
+  }
+  __host__ __device__ constexpr int total() const { return start[NCLS]; }
+};
+// One shape per (D, P).  Device code reads it only through the integral
+// constants below (template arguments), so it sees plain constants.
+template <int D, int P>
+struct Shape {
+  static constexpr StencilShape<D, P> s{};
+};
+template <int D, int P, int K, int E, int C>
+__host__ __device__ constexpr int shape_off() {
+  return std::integral_constant<int, Shape<D, P>::s.off[K][E][C]>::value;
+}
+template <int D, int P, int K>
+__host__ __device__ constexpr int shape_n() {
+  return std::integral_constant<int, Shape<D, P>::s.n[K]>::value;
+}
+template <int D, int P, int K>
+__host__ __device__ constexpr int shape_start() {
+  return std::integral_constant<int, Shape<D, P>::s.start[K]>::value;
+}
+template <int D, int P, int K>
+__host__ __device__ constexpr int shape_centre() {
+  return std::integral_constant<int, Shape<D, P>::s.centre[K]>::value;
+}
+template <int D, int P>
+__host__ __device__ constexpr int shape_total() {
+  return std::integral_constant<int, Shape<D, P>::s.start[StencilShape<D, P>::NCLS]>::value;
+}
+
+template <class R>
+__device__ __forceinline__ R fma_r(R a, R b, R c);
+template <>
+__device__ __forceinline__ float fma_r<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <>
+__device__ __forceinline__ double fma_r<double>(double a, double b, double c) { return fma(a, b, c); }
+
+// Row sum of class K at storage slot `slot`: sum over the class's offsets, in
+// their fixed order, of weight * x at the neighbour.  d0 / d1: packed-index
+// increments of the two slower axes for offsets -P..P (the fastest axis adds
+// its offset itself).
+template <int D, class R, int P, int K, int... E>
+__device__ __forceinline__ R stencil_row(std::integer_sequence<int, E...>, const R* W, const R* __restrict__ x,
+                                         int64_t slot, const int* d0, const int* d1) {
+  constexpr int S0 = shape_start<D, P, K>();
+  R v = R(0);
+  if constexpr (D == 3)
+    ((v = fma_r<R>(W[S0 + E],
+                   __ldg(x + slot + (d0[shape_off<D, P, K, E, 0>() + P] + d1[shape_off<D, P, K, E, 1>() + P] +
+                                     shape_off<D, P, K, E, 2>())),
+                   v)),
+     ...);
+  else
+    ((v = fma_r<R>(W[S0 + E], __ldg(x + slot + (d0[shape_off<D, P, K, E, 0>() + P] + shape_off<D, P, K, E, 1>())), v)),
+     ...);
+  return v;
+}
+template <int D, class R, int P, int MODE, int K = 0>
+__device__ __forceinline__ R stencil_node(int k, const R* W, const R* __restrict__ x, int64_t slot, const int* d0,
+                                          const int* d1) {
+  if constexpr (K + 1 < StencilShape<D, P>::NCLS) {
+    if (k != K) return stencil_node<D, R, P, MODE, K + 1>(k, W, x, slot, d0, d1);
+  }
+  if constexpr (MODE == kOpDiag) {
+    constexpr int c = shape_start<D, P, K>() + shape_centre<D, P, K>();
+    return W[c];
+  } else {
+    return stencil_row<D, R, P, K>(std::make_integer_sequence<int, shape_n<D, P, K>()>{}, W, x, slot, d0, d1);
+  }
+}
+
+// Sum over the block (fixed shuffle tree, so deterministic); valid in thread
+// 0.  sh holds one value per warp; callers separate two sums by a barrier.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = int(threadIdx.x) < int(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+struct StencilArgs {
+  const void* wtab;       // per macro: mass weights, then stiffness weights ([2][entries])
+  const uint32_t* nodes;  // interior lattice points, packed (3D: q0 | q1 << 10 | q2 << 20; 2D: q0 | q1 << 16)
+  const int4* items;      // (macro, class, first node, count); 4 per group, one macro per group
+  int64_t n_groups;
+  int npm;
+  const Scalars* sc;
+};
+
+// The stencil pass over the interior nodes: each warp takes up to 32 nodes
+// of one class of one macro (consecutive in the class's list, which follows
+// the storage order), each lane one node; a block takes groups of 4 such
+// items of one macro (persistent over the groups), with that macro's weights
+// scale (Wm + alpha Wa) in shared memory.  kOpCg leaves one partial of p.q
+// per block in part[blockIdx.x].
+template <int D, class R, int P, int MODE>
+__global__ void __launch_bounds__(128) k_stencil(StencilArgs a, const R* __restrict__ x, R* __restrict__ y, R alpha,
+                                                 R scale, double* part) {
+  constexpr int NT = shape_total<D, P>();
+  __shared__ R W[NT];
+  __shared__ double sh[4];
+  if (a.sc != nullptr && a.sc->done) return;  // uniform over the grid
+  const int warp = int(threadIdx.x) >> 5, lane = int(threadIdx.x) & 31;
+  R pq = R(0);
+  int cur = -1;
+  for (int64_t g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
+    const int m = a.items[g * 4].x;  // the group's macro (uniform over the block)
+    if (m != cur) {
+      __syncthreads();
+      const R* tab = static_cast<const R*>(a.wtab) + size_t(m) * 2 * NT;
+      for (int t = threadIdx.x; t < NT; t += blockDim.x) W[t] = scale * (tab[t] + alpha * tab[NT + t]);
+      __syncthreads();
+      cur = m;
+    }
+    const int4 it = a.items[g * 4 + warp];
+    if (lane >= it.w) continue;
+    const uint32_t pk = a.nodes[it.z + lane];
+    const int q0 = D == 3 ? int(pk & 1023u) : int(pk & 0xFFFFu);
+    const int q1 = D == 3 ? int((pk >> 10) & 1023u) : int(pk >> 16);
+    const int q2 = D == 3 ? int(pk >> 20) : 0;
+    const int64_t slot = int64_t(m) * a.npm + (D == 3 ? tri3d(q0) + tri2d(q1) + q2 : tri2d(q0) + q1);
+    int d0[2 * P + 1], d1[2 * P + 1];
+#pragma unroll
+    for (int o = -P; o <= P; ++o) {
+      d0[o + P] = D == 3 ? tri3d(q0 + o) - tri3d(q0) : tri2d(q0 + o) - tri2d(q0);
+      d1[o + P] = D == 3 ? tri2d(q1 + o) - tri2d(q1) : 0;
+    }
+    const R v = stencil_node<D, R, P, MODE>(it.y, W, x, slot, d0, d1);
+    if constexpr (MODE == kOpCg) {
+      y[slot] = v;
+      pq = fma_r<R>(x[slot], v, pq);  // interior nodes: owners, never on the boundary
+    } else {
+      y[slot] += v;
+    }
+  }
+  if constexpr (MODE == kOpCg) {
+    const double t = block_sum(double(pq), sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+  }
+}
+
+struct FaceRows {
+  const int* off;        // row r: entries [off[r], off[r + 1])
+  const int* col;        // column: a storage slot of the neighbour
+  const void* w;         // [2][nnz]: mass weights, then stiffness weights
+  int64_t nnz;
+  const int* copy_off;   // row r's node: storage copies [copy_off[r], copy_off[r + 1]), owner first
+  const int* copies;
+  int64_t n;             // rows
+  const Scalars* sc;
+};
+
+// The assembled rows of the face nodes off the Dirichlet boundary (nodes on a
+// face shared by two or more macros): one warp per row, lane e taking
+// entries e, e + 32, ..., then a butterfly sum (every lane ends with the same
+// bits, so any lane may write).  The row's value goes to every storage copy
+// of its node.  kOpCg: y = v and a partial of p.q per block (p = x at the
+// owner copy); kOpDiag: the entry whose column is the owner copy.
+template <class R, int MODE>
+__global__ void __launch_bounds__(kRedThreads) k_face_rows(FaceRows a, const R* __restrict__ x, R* __restrict__ y,
+                                                           R alpha, R scale, double* part) {
+  __shared__ double sh[kRedThreads / 32];
+  if (a.sc != nullptr && a.sc->done) return;
+  const int lane = int(threadIdx.x) & 31;
+  const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const R* wm = static_cast<const R*>(a.w);
+  const R* wa = wm + a.nnz;
+  R pq = R(0);
+  for (int64_t r = w0; r < a.n; r += nw) {
+    const int e0 = a.off[r], e1 = a.off[r + 1];
+    const int c0 = a.copy_off[r], c1 = a.copy_off[r + 1];
+    const int self = a.copies[c0];
+    R v = R(0);
+    for (int e = e0 + lane; e < e1; e += 32) {
+      const R wt = scale * fma_r<R>(alpha, __ldg(wa + e), __ldg(wm + e));
+      const int c = __ldg(a.col + e);
+      if constexpr (MODE == kOpDiag) {
+        if (c == self) v += wt;
+      } else {
+        v = fma_r<R>(wt, __ldg(x + c), v);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int k = c0 + lane; k < c1; k += 32) {
+      if constexpr (MODE == kOpCg) y[a.copies[k]] = v;
+      else y[a.copies[k]] += v;
+    }
+    if (MODE == kOpCg && lane == 0) pq = fma_r<R>(x[self], v, pq);
+  }
+  if constexpr (MODE == kOpCg) {
+    const double t = block_sum(double(pq), sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+  }
+}
+
 // ys[colour][slot] = scale (M + alpha A) x summed over the simplices of one
-// cell that lie in the macro, for every node of the cell's (P + 1)^d node box,
-// into the accumulators of the cell's colour (no two cells of one colour
+// cell that lie in the macro, for every node of the cell's (P + 1)^d node
+// box, into the accumulators of the cell's colour (no two cells of one colour
 // share a node, so a store suffices).
 // The cell's x values are gathered once and its sums kept in registers (the
 // simplex loop is unrolled, so every local node index is a constant).  DIAG:
@@ -469,7 +746,7 @@ __global__ void __launch_bounds__(kDiffThreads) k_apply(OpArgs a, const R* __res
     const int q0 = P * c[0] + i0, q1 = P * c[1] + i1, q2 = D == 3 ? P * c[2] + i2 : 0;
     ex[l] = q0 >= q1 && (D == 2 || q1 >= q2);
     sl[l] = base + (D == 3 ? tri3d(q0) + tri2d(q1) + q2 : tri2d(q0) + q1);
-    xc[l] = (!DIAG && ex[l]) ? x[a.unique_map[sl[l]]] : R(0);
+    xc[l] = (!DIAG && ex[l]) ? x[sl[l]] : R(0);
     acc[l] = R(0);
   }
 #pragma unroll
@@ -510,53 +787,57 @@ __global__ void __launch_bounds__(kDiffThreads) k_apply(OpArgs a, const R* __res
     if (ex[l]) ys[(sl[l] >> 5) * (32 * NCOL) + (sl[l] & 31)] = acc[l];
 }
 
-// y[u] += the sum over the storage copies of unique node u (ascending slot
-// order: fold_off / fold_slots) of their NCOL colour accumulators (ascending
-// colour; one warp-uniform loop, so every access is coalesced).
-template <class R, int NCOL>
-__global__ void k_fold(const R* __restrict__ ys, R* __restrict__ y, const int* __restrict__ off,
-                       const int* __restrict__ slots, int64_t n, const Scalars* sc) {
+// The fold of the cell pass: for every fold node f, the sum over its
+// storage copies (ascending slot order: off / slots) of their NCOL colour
+// accumulators (ascending colour), applied to every copy (kOpAccum / kOpDiag:
+// y += v; kOpCg: y = v, 0 on the boundary, with a partial of p.q per block
+// in part[blockIdx.x], p = x at the node's first copy).
+template <class R, int NCOL, int MODE>
+__global__ void __launch_bounds__(kRedThreads) k_fold_nodes(const R* __restrict__ ys, R* __restrict__ y,
+                                                            const int* __restrict__ off, const int* __restrict__ slots,
+                                                            const uint8_t* __restrict__ fbnd, int64_t nf,
+                                                            const R* __restrict__ x, double* part, const Scalars* sc) {
+  __shared__ double sh[kRedThreads / 32];
   if (sc != nullptr && sc->done) return;
-  const int64_t u = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (u >= n) return;
-  R v = R(0);
-  for (int k = off[u]; k < off[u + 1]; ++k) {
-    const int sl = slots[k];
-    const R* e = ys + int64_t(sl >> 5) * (32 * NCOL) + (sl & 31);
-    R w[NCOL];
+  R pq = R(0);
+  for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
+    const int k0 = off[f], k1 = off[f + 1];
+    R v = R(0);
+    for (int k = k0; k < k1; ++k) {
+      const int sl = slots[k];
+      const R* e = ys + int64_t(sl >> 5) * (32 * NCOL) + (sl & 31);
+      R w[NCOL];
 #pragma unroll
-    for (int c = 0; c < NCOL; ++c) w[c] = __ldg(e + 32 * c);
+      for (int c = 0; c < NCOL; ++c) w[c] = __ldg(e + 32 * c);
 #pragma unroll
-    for (int c = 0; c < NCOL; ++c) v += w[c];
+      for (int c = 0; c < NCOL; ++c) v += w[c];
+    }
+    if constexpr (MODE == kOpCg) {
+      if (fbnd[f]) v = R(0);
+      for (int k = k0; k < k1; ++k) y[slots[k]] = v;
+      pq = fma_r<R>(x[slots[k0]], v, pq);
+    } else {
+      for (int k = k0; k < k1; ++k) y[slots[k]] += v;
+    }
   }
-  y[u] += v;
+  if constexpr (MODE == kOpCg) {
+    const double t = block_sum(double(pq), sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Device: CG vector kernels and deterministic reductions (per-block partials
-// in a fixed order, then one block sums the partials in a fixed order).
+// in a fixed order, then one block sums the partials in a fixed order).  The
+// vectors are in the storage layout: the copies of an interface node hold the
+// same value, and the dot products count each interior unknown once (act: the
+// owner copy of a node off the Dirichlet boundary).
 // ---------------------------------------------------------------------------
-
-
-// Sum over the block (fixed shuffle tree, so deterministic); valid in thread
-// 0.  sh holds one value per warp; callers separate two sums by a barrier.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    v = int(threadIdx.x) < int(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  }
-  return v;
-}
 
 // r := r with zero boundary; z = dinv r; p = z; q = 0; partials (r.z, r.r).
 template <class R>
 __global__ void __launch_bounds__(kRedThreads) k_cg_start(R* r, R* z, R* p, R* q, const R* dinv, const uint8_t* bnd,
-                                                          int64_t n, double* part) {
+                                                          const uint8_t* act, int64_t n, double* part) {
   __shared__ double sh[kRedThreads / 32];
   // per-thread partials in the working precision (a few terms each), summed in FP64
   R rz = R(0), rr = R(0);
@@ -567,8 +848,10 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_start(R* r, R* z, R* p, R* q
     z[i] = zi;
     p[i] = zi;
     q[i] = R(0);
-    rz += ri * zi;
-    rr += ri * ri;
+    if (act[i]) {
+      rz += ri * zi;
+      rr += ri * ri;
+    }
   }
   const double s1 = block_sum(double(rz), sh);
   __syncthreads();
@@ -579,40 +862,11 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_start(R* r, R* z, R* p, R* q
   }
 }
 
-// The CG iteration's operator result and p.q in one pass: q = the fold of
-// the colour accumulators (as k_fold; q is overwritten), zero on the
-// boundary; partial of p.q.
-template <class R, int NCOL>
-__global__ void __launch_bounds__(kRedThreads) k_fold_pq(const R* __restrict__ ys, const R* __restrict__ p,
-                                                         R* __restrict__ q, const int* __restrict__ off,
-                                                         const int* __restrict__ slots, const uint8_t* bnd,
-                                                         int64_t n, double* part, const Scalars* sc) {
-  __shared__ double sh[kRedThreads / 32];
-  if (sc->done) return;
-  R pq = R(0);
-  for (int64_t u = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; u < n; u += int64_t(gridDim.x) * blockDim.x) {
-    R v = R(0);
-    for (int k = off[u]; k < off[u + 1]; ++k) {
-      const int sl = slots[k];
-      const R* e = ys + int64_t(sl >> 5) * (32 * NCOL) + (sl & 31);
-      R w[NCOL];
-#pragma unroll
-      for (int c = 0; c < NCOL; ++c) w[c] = __ldg(e + 32 * c);
-#pragma unroll
-      for (int c = 0; c < NCOL; ++c) v += w[c];
-    }
-    if (bnd[u]) v = R(0);
-    q[u] = v;
-    pq += p[u] * v;
-  }
-  const double t = block_sum(double(pq), sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
 // x += alpha p; r -= alpha q; z = dinv r; partials (r.z, r.r).
 template <class R>
 __global__ void __launch_bounds__(kRedThreads) k_cg_update(R* x, R* r, R* z, const R* p, const R* q, const R* dinv,
-                                                           const Scalars* sc, int64_t n, double* part) {
+                                                           const uint8_t* act, const Scalars* sc, int64_t n,
+                                                           double* part) {
   __shared__ double sh[kRedThreads / 32];
   if (sc->done) return;
   const R al = R(sc->alpha);
@@ -623,8 +877,10 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(R* x, R* r, R* z, con
     r[i] = ri;
     const R zi = dinv[i] * ri;
     z[i] = zi;
-    rz += ri * zi;
-    rr += ri * ri;
+    if (act[i]) {
+      rz += ri * zi;
+      rr += ri * ri;
+    }
   }
   const double s1 = block_sum(double(rz), sh);
   __syncthreads();
@@ -635,7 +891,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(R* x, R* r, R* z, con
   }
 }
 
-// p = z + beta p (q is overwritten by the next k_fold_pq).
+// p = z + beta p (q is overwritten by the next operator pass).
 template <class R>
 __global__ void __launch_bounds__(kRedThreads) k_cg_direction(R* p, const R* z, const Scalars* sc, int64_t n) {
   if (sc->done) return;
@@ -684,11 +940,11 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_scalars(const double* part, 
 
 // |b|^2 over the interior unknowns (the residual reference).
 template <class R>
-__global__ void __launch_bounds__(kRedThreads) k_norm2(const R* b, const uint8_t* bnd, int64_t n, double* part) {
+__global__ void __launch_bounds__(kRedThreads) k_norm2(const R* b, const uint8_t* act, int64_t n, double* part) {
   __shared__ double sh[kRedThreads / 32];
   double s = 0.0;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    if (!bnd[i]) s += double(b[i]) * double(b[i]);
+    if (act[i]) s += double(b[i]) * double(b[i]);
   const double t = block_sum(s, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
@@ -742,52 +998,199 @@ __global__ void k_copy(R* dst, const R* src, int64_t n) {
 // Host: set-up at mesh creation and the solve.
 // ---------------------------------------------------------------------------
 
-elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
-  const int d = me->dim, p = me->order, nb = n_local(d, p), np = n_perm(d);
-  const size_t tab = size_t(nb) * nb * (1 + np);
-  std::vector<double> t64(tab * me->n_macros);
-  for (int64_t m = 0; m < me->n_macros; ++m)
-    element_tables(d, p, me->N, me->geo[m], t64.data() + m * tab, t64.data() + m * tab + size_t(nb) * nb);
-  // boundary unknowns: a node on face k (barycentric weight k = 0) of a macro
-  // whose face k has no neighbour
-  std::vector<uint8_t> bnd(me->n_unique, 0);
-  {
-    const int M = me->M;
-    for (int64_t m = 0; m < me->n_macros; ++m) {
-      const MacroGeo& g = me->geo[m];
-      int64_t slot = m * me->npm;
-      int q[3] = {0, 0, 0};
-      auto visit = [&]() {
-        const int pp[5] = {M, q[0], q[1], d == 3 ? q[2] : 0, 0};
-        bool on = false;
-        for (int k = 0; k <= d; ++k) {
-          const int w = (d == 3 || k < d) ? pp[k] - pp[k + 1] : pp[k];
-          if (w == 0 && g.nb[k] < 0) on = true;
-        }
-        if (on) bnd[me->unique_map[slot]] = 1;
-        ++slot;
-      };
-      if (d == 2) {
-        for (q[0] = 0; q[0] <= M; ++q[0])
-          for (q[1] = 0; q[1] <= q[0]; ++q[1]) visit();
-      } else {
-        for (q[0] = 0; q[0] <= M; ++q[0])
-          for (q[1] = 0; q[1] <= q[0]; ++q[1])
-            for (q[2] = 0; q[2] <= q[1]; ++q[2]) visit();
+namespace {
+
+// Node-centred stencil weights of one affine macro from its element tables
+// (mass Mt [nb*nb], stiffness At [n_perm][nb*nb]): out[0 .. NT) mass,
+// out[NT .. 2 NT) stiffness, in StencilShape order.  Every simplex holding a
+// node of class k as its local node i adds its row i at the offsets of the
+// other local nodes.
+template <int D, int P>
+void stencil_weights(const double* Mt, const double* At, double* out) {
+  constexpr StencilShape<D, P> S{};
+  constexpr int NB = n_local(D, P), NT = S.total();
+  std::fill(out, out + 2 * NT, 0.0);
+  for (int sg = 0; sg < n_perm(D); ++sg)
+    for (int i = 0; i < NB; ++i) {
+      const int k = StencilShape<D, P>::class_of_node(sg, i);
+      for (int j = 0; j < NB; ++j) {
+        int o[3] = {0, 0, 0};
+        for (int r = 0; r < D; ++r) o[r] = node_off(D, sg, j, r, P) - node_off(D, sg, i, r, P);
+        int e = 0;
+        while (e < S.n[k] && StencilShape<D, P>::compare(S.off[k][e], o) != 0) ++e;
+        out[S.start[k] + e] += Mt[i * NB + j];
+        out[NT + S.start[k] + e] += At[(size_t(sg) * NB + i) * NB + j];
       }
     }
+}
+
+int stencil_entries(int d, int p) {
+  if (d == 3) return p == 2 ? shape_total<3, 2>() : shape_total<3, 1>();
+  return p == 2 ? shape_total<2, 2>() : shape_total<2, 1>();
+}
+
+template <class T>
+bool upload(T** dst, const std::vector<T>& v) {
+  cudaFree(*dst);
+  *dst = nullptr;
+  if (v.empty()) return true;
+  return cudaMalloc((void**)dst, sizeof(T) * v.size()) == cudaSuccess &&
+         cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+// Lattice point (q0, q1, q2) of every slot of one macro, in storage order.
+template <class F>
+void for_each_lattice_point(int d, int M, F f) {
+  int64_t s = 0;
+  if (d == 2) {
+    for (int q0 = 0; q0 <= M; ++q0)
+      for (int q1 = 0; q1 <= q0; ++q1) f(s++, q0, q1, 0);
+  } else {
+    for (int q0 = 0; q0 <= M; ++q0)
+      for (int q1 = 0; q1 <= q0; ++q1)
+        for (int q2 = 0; q2 <= q1; ++q2) f(s++, q0, q1, q2);
   }
-  // cells of every macro (c0 >= c1 [>= c2] >= 0, c0 < N) by colour (the
-  // parity of each index), then macro; chunks of at most kDiffThreads cells
-  // of one colour and one macro
+}
+
+bool on_macro_face(int d, int M, int q0, int q1, int q2) {
+  return d == 3 ? (q0 == M || q0 == q1 || q1 == q2 || q2 == 0) : (q0 == M || q0 == q1 || q1 == 0);
+}
+
+// Interior nodes (strictly inside their macro: the stencil pass), as lists
+// per macro and class in storage order, and the warp items over them: up to
+// 32 nodes of one class each, 4 items of one macro per group (padded with
+// empty items).
+void interior_lists(const elm_mesh_s* me, std::vector<uint32_t>& nodes, std::vector<int4>& items) {
+  const int d = me->dim, P = me->order, M = me->M;
+  const int ncls = P == 2 ? (1 << d) : 1;
+  for (int64_t m = 0; m < me->n_macros; ++m) {
+    const size_t first_item = items.size();
+    for (int k = 0; k < ncls; ++k) {
+      const size_t first = nodes.size();
+      for_each_lattice_point(d, M, [&](int64_t, int q0, int q1, int q2) {
+        const bool interior = d == 3 ? (q0 < M && q0 > q1 && q1 > q2 && q2 > 0) : (q0 < M && q0 > q1 && q1 > 0);
+        if (!interior) return;
+        const int cls = P == 2 ? (d == 3 ? (q0 & 1) | ((q1 & 1) << 1) | ((q2 & 1) << 2) : (q0 & 1) | ((q1 & 1) << 1)) : 0;
+        if (cls != k) return;
+        nodes.push_back(d == 3 ? uint32_t(q0) | (uint32_t(q1) << 10) | (uint32_t(q2) << 20)
+                               : uint32_t(q0) | (uint32_t(q1) << 16));
+      });
+      for (size_t a = first; a < nodes.size(); a += 32)
+        items.push_back(make_int4(int(m), k, int(a), int(std::min<size_t>(32, nodes.size() - a))));
+    }
+    while ((items.size() - first_item) % 4) items.push_back(make_int4(int(m), 0, 0, 0));
+  }
+}
+
+// The assembled rows of the face nodes off the Dirichlet boundary (the nodes
+// on a face shared with another macro): every micro simplex holding such a
+// node as its local node i adds its element row i (mass and stiffness) at the
+// owner slots of its other local nodes; equal columns are summed (in the
+// order of the cells, then simplices), and the columns sorted by unique id.
+struct RowsHost {
+  std::vector<int> off{0}, col, copy_off{0}, copies;
+  std::vector<double> wm, wa;
+};
+RowsHost face_rows(const elm_mesh_s* me, const std::vector<double>& t64) {
+  const int d = me->dim, P = me->order, N = me->N, M = me->M, nb = n_local(d, P), np = n_perm(d);
+  const size_t tab = size_t(nb) * nb * (1 + np);
+  std::vector<uint8_t> face_slot(me->n_storage, 0);
+  for (int64_t m = 0; m < me->n_macros; ++m)
+    for_each_lattice_point(d, M, [&](int64_t s, int q0, int q1, int q2) {
+      if (on_macro_face(d, M, q0, q1, q2)) face_slot[m * me->npm + s] = 1;
+    });
+  std::vector<int64_t> rid(me->n_unique, -1);
+  int64_t nrows = 0;
+  RowsHost h;
+  for (int64_t u = 0; u < me->n_unique; ++u)
+    if (face_slot[me->owner[u]] && !me->dbnd[u]) rid[u] = nrows++;
+  struct Raw {
+    int64_t row, colu;
+    double m, a;
+  };
+  std::vector<Raw> raw;
+  for (int64_t m = 0; m < me->n_macros; ++m) {
+    const double* Mt = t64.data() + m * tab;
+    const double* At = Mt + size_t(nb) * nb;
+    const int64_t base = m * me->npm;
+    for (int c0 = 0; c0 < N; ++c0)
+      for (int c1 = 0; c1 <= c0; ++c1)
+        for (int c2 = 0; c2 <= (d == 3 ? c1 : 0); ++c2) {
+          const int c[3] = {c0, c1, c2};
+          for (int sg = 0; sg < np; ++sg) {
+            int s[3] = {0, 1, 2};
+            perm_of(d, sg, s);
+            bool inside = true;
+            for (int a = 0; a < d; ++a)
+              for (int b = a + 1; b < d; ++b)
+                if (c[s[a]] == c[s[b]] && s[a] > s[b]) inside = false;
+            if (!inside) continue;
+            int64_t u[10];
+            bool any = false;
+            for (int j = 0; j < nb; ++j) {
+              int q[3] = {0, 0, 0};
+              for (int r = 0; r < d; ++r) q[r] = P * c[r] + node_off(d, sg, j, r, P);
+              const int64_t sl = base + (d == 3 ? int64_t(q[0]) * (q[0] + 1) * (q[0] + 2) / 6 +
+                                                      int64_t(q[1]) * (q[1] + 1) / 2 + q[2]
+                                                : int64_t(q[0]) * (q[0] + 1) / 2 + q[1]);
+              u[j] = me->unique_map[sl];
+              any = any || rid[u[j]] >= 0;
+            }
+            if (!any) continue;
+            for (int i = 0; i < nb; ++i) {
+              if (rid[u[i]] < 0) continue;
+              for (int j = 0; j < nb; ++j)
+                raw.push_back({rid[u[i]], u[j], Mt[i * nb + j], At[(size_t(sg) * nb + i) * nb + j]});
+            }
+          }
+        }
+  }
+  std::stable_sort(raw.begin(), raw.end(), [](const Raw& x, const Raw& y) {
+    return x.row != y.row ? x.row < y.row : x.colu < y.colu;
+  });
+  int64_t r = 0;
+  for (size_t k = 0; k < raw.size();) {
+    size_t e = k;
+    double wm = 0.0, wa = 0.0;
+    for (; e < raw.size() && raw[e].row == raw[k].row && raw[e].colu == raw[k].colu; ++e) {
+      wm += raw[e].m;
+      wa += raw[e].a;
+    }
+    for (; r < raw[k].row; ++r) h.off.push_back(int(h.col.size()));
+    h.col.push_back(int(me->owner[raw[k].colu]));
+    h.wm.push_back(wm);
+    h.wa.push_back(wa);
+    k = e;
+  }
+  for (; r < nrows; ++r) h.off.push_back(int(h.col.size()));
+  // copies of each row's node, owner first (ascending slot; the owner is the lowest)
+  std::vector<int64_t> row_of_slot(me->n_storage, -1);
+  std::vector<int> cnt(nrows + 1, 0);
+  for (int64_t sl = 0; sl < me->n_storage; ++sl) {
+    const int64_t rr = rid[me->unique_map[sl]];
+    if (rr >= 0) ++cnt[rr + 1];
+  }
+  for (int64_t k = 0; k < nrows; ++k) cnt[k + 1] += cnt[k];
+  h.copy_off.assign(cnt.begin(), cnt.end());
+  h.copies.assign(cnt.back(), 0);
+  for (int64_t sl = 0; sl < me->n_storage; ++sl) {
+    const int64_t rr = rid[me->unique_map[sl]];
+    if (rr >= 0) h.copies[cnt[rr]++] = int(sl);
+  }
+  return h;
+}
+
+// Blended meshes: the cell pass over every cell (chunks of at most
+// kDiffThreads cells of one colour and one macro, by colour, then macro) and
+// its fold into every node.
+bool build_cells_and_fold(elm_mesh_s* me) {
+  const int d = me->dim, N = me->N;
   const int ncol = 1 << d;
   std::vector<int4> cells, cellv;
-  me->cell_color_off.assign(ncol + 1, 0);
-  for (int col = 0; col < ncol; ++col) {
-    me->cell_color_off[col] = int64_t(cells.size());
+  for (int col = 0; col < ncol; ++col)
     for (int64_t m = 0; m < me->n_macros; ++m) {
       const int64_t first = int64_t(cellv.size());
-      for (int c0 = col & 1; c0 < me->N; c0 += 2)
+      for (int c0 = col & 1; c0 < N; c0 += 2)
         for (int c1 = (col >> 1) & 1; c1 <= c0; c1 += 2) {
           if (d == 2) {
             cellv.push_back(make_int4(c0, c1, 0, 0));
@@ -799,10 +1202,7 @@ elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
       for (int64_t c = first; c < last; c += kDiffThreads)
         cells.push_back(make_int4(int(m), int(c), int(std::min<int64_t>(kDiffThreads, last - c)), col));
     }
-  }
-  me->cell_color_off[ncol] = int64_t(cells.size());
   me->n_cell_chunks = int64_t(cells.size());
-  // fold lists: the storage copies of every unique node in ascending slot order
   std::vector<int> foff(me->n_unique + 1, 0), fslots(me->n_storage);
   for (int64_t sl = 0; sl < me->n_storage; ++sl) ++foff[me->unique_map[sl] + 1];
   for (int64_t u = 0; u < me->n_unique; ++u) foff[u + 1] += foff[u];
@@ -810,62 +1210,132 @@ elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
     std::vector<int> next(foff.begin(), foff.end() - 1);
     for (int64_t sl = 0; sl < me->n_storage; ++sl) fslots[next[me->unique_map[sl]]++] = int(sl);
   }
+  me->n_dface = me->n_unique;
+  // the colour accumulators, tiled by 32 slots; zero where no cell of the
+  // colour ever writes
+  const size_t ysn = size_t((me->n_storage + 31) / 32 * 32) * size_t(ncol);
   const size_t es = me->precision == ELM_FP64 ? 8 : 4;
-  bool ok = true;
-  ok = ok && cudaMalloc(&me->d_dtab, tab * me->n_macros * es) == cudaSuccess;
-  if (ok) {
-    if (me->precision == ELM_FP64) {
-      ok = cudaMemcpy(me->d_dtab, t64.data(), tab * me->n_macros * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+  cudaFree(me->d_dys);
+  me->d_dys = nullptr;
+  return upload(&me->d_dcells, cells) && upload(&me->d_dcellv, cellv) && upload(&me->d_dfold_off, foff) &&
+         upload(&me->d_dfold_slots, fslots) && upload(&me->d_dfbnd, me->dbnd) &&
+         cudaMalloc(&me->d_dys, ysn * es) == cudaSuccess && cudaMemset(me->d_dys, 0, ysn * es) == cudaSuccess;
+}
+
+}  // namespace
+
+namespace {
+
+// Everything the affine operator needs, built on the host: element tables
+// and stencil weights per macro, the Dirichlet mask, per-slot masks, the
+// interior lists and the face rows.
+struct DiffusionHost {
+  std::vector<double> t64, w64;
+  std::vector<uint8_t> dbnd, bnd_s, act;
+  std::vector<int64_t> slot_owner;
+  std::vector<uint32_t> nodes;
+  std::vector<int4> items;
+  RowsHost rows;
+};
+
+DiffusionHost diffusion_host(elm_mesh_s* me) {
+  DiffusionHost h;
+  const int d = me->dim, p = me->order, nb = n_local(d, p), np = n_perm(d);
+  const size_t tab = size_t(nb) * nb * (1 + np);
+  h.t64.assign(tab * me->n_macros, 0.0);
+  for (int64_t m = 0; m < me->n_macros; ++m)
+    element_tables(d, p, me->N, me->geo[m], h.t64.data() + m * tab, h.t64.data() + m * tab + size_t(nb) * nb);
+  const int nt = stencil_entries(d, p);
+  h.w64.assign(size_t(2) * nt * me->n_macros, 0.0);
+  for (int64_t m = 0; m < me->n_macros; ++m) {
+    const double* Mt = h.t64.data() + m * tab;
+    const double* At = Mt + size_t(nb) * nb;
+    double* w = h.w64.data() + size_t(2) * nt * m;
+    if (d == 3) {
+      if (p == 2) stencil_weights<3, 2>(Mt, At, w);
+      else stencil_weights<3, 1>(Mt, At, w);
     } else {
-      std::vector<float> t32(t64.begin(), t64.end());
-      ok = cudaMemcpy(me->d_dtab, t32.data(), tab * me->n_macros * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+      if (p == 2) stencil_weights<2, 2>(Mt, At, w);
+      else stencil_weights<2, 1>(Mt, At, w);
     }
   }
-  ok = ok && cudaMalloc((void**)&me->d_dbnd, me->n_unique) == cudaSuccess &&
-       cudaMemcpy(me->d_dbnd, bnd.data(), me->n_unique, cudaMemcpyHostToDevice) == cudaSuccess;
-  ok = ok && cudaMalloc((void**)&me->d_dcells, sizeof(int4) * cells.size()) == cudaSuccess &&
-       cudaMemcpy(me->d_dcells, cells.data(), sizeof(int4) * cells.size(), cudaMemcpyHostToDevice) == cudaSuccess;
-  ok = ok && cudaMalloc((void**)&me->d_dcellv, sizeof(int4) * cellv.size()) == cudaSuccess &&
-       cudaMemcpy(me->d_dcellv, cellv.data(), sizeof(int4) * cellv.size(), cudaMemcpyHostToDevice) == cudaSuccess;
-  ok = ok && cudaMalloc((void**)&me->d_dfold_off, sizeof(int) * foff.size()) == cudaSuccess &&
-       cudaMemcpy(me->d_dfold_off, foff.data(), sizeof(int) * foff.size(), cudaMemcpyHostToDevice) == cudaSuccess;
-  ok = ok && cudaMalloc((void**)&me->d_dfold_slots, sizeof(int) * fslots.size()) == cudaSuccess &&
-       cudaMemcpy(me->d_dfold_slots, fslots.data(), sizeof(int) * fslots.size(), cudaMemcpyHostToDevice) ==
-           cudaSuccess;
-  // the colour accumulators, tiled by 32 slots, in the mesh precision (and a
-  // second, FP32 set for the inner solves of FP64 meshes: the zero entries no
-  // cell writes must stay zero in each precision's own layout); zero where no
-  // cell of the colour ever writes
-  const size_t ysn = size_t((me->n_storage + 31) / 32 * 32) * size_t(ncol);
-  ok = ok && cudaMalloc(&me->d_dys, ysn * es) == cudaSuccess && cudaMemset(me->d_dys, 0, ysn * es) == cudaSuccess;
-  if (me->precision == ELM_FP64)
-    ok = ok && cudaMalloc(&me->d_dys32, ysn * 4) == cudaSuccess && cudaMemset(me->d_dys32, 0, ysn * 4) == cudaSuccess;
-  ok = ok && cudaMalloc(&me->d_dvec, size_t(kDiffVectors) * me->n_unique * es) == cudaSuccess;
+  // boundary unknowns: a node on face k (barycentric weight k = 0) of a macro
+  // whose face k has no neighbour
+  h.dbnd.assign(me->n_unique, 0);
+  for (int64_t m = 0; m < me->n_macros; ++m) {
+    const MacroGeo& g = me->geo[m];
+    for_each_lattice_point(d, me->M, [&](int64_t s, int q0, int q1, int q2) {
+      const int pp[5] = {me->M, q0, q1, d == 3 ? q2 : 0, 0};
+      bool on = false;
+      for (int k = 0; k <= d; ++k) {
+        const int w = (d == 3 || k < d) ? pp[k] - pp[k + 1] : pp[k];
+        if (w == 0 && g.nb[k] < 0) on = true;
+      }
+      if (on) h.dbnd[me->unique_map[m * me->npm + s]] = 1;
+    });
+  }
+  me->dbnd = h.dbnd;
+  // per slot: boundary, dot-product mask (owner copy, off the boundary), owner slot
+  h.bnd_s.assign(me->n_storage, 0);
+  h.act.assign(me->n_storage, 0);
+  h.slot_owner.assign(me->n_storage, 0);
+  for (int64_t sl = 0; sl < me->n_storage; ++sl) {
+    const int64_t u = me->unique_map[sl];
+    h.bnd_s[sl] = h.dbnd[u];
+    h.act[sl] = (me->owner[u] == sl && !h.dbnd[u]) ? 1 : 0;
+    h.slot_owner[sl] = me->owner[u];
+  }
+  interior_lists(me, h.nodes, h.items);
+  h.rows = face_rows(me, h.t64);
+  return h;
+}
+
+}  // namespace
+
+elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
+  const DiffusionHost h = diffusion_host(me);
+  me->n_ditems = int64_t(h.items.size());
+  me->n_drows = int64_t(h.rows.off.size()) - 1;
+  me->n_dnnz = int64_t(h.rows.col.size());
+  std::vector<double> rw(h.rows.wm);
+  rw.insert(rw.end(), h.rows.wa.begin(), h.rows.wa.end());
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&me->n_dsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    *err = std::string("diffusion set-up: ") + cudaGetErrorString(cudaGetLastError());
+    return ELM_ERR_CUDA;
+  }
+  const size_t es = me->precision == ELM_FP64 ? 8 : 4;
+  auto put = [&](void** dst, const std::vector<double>& v, bool fp64) {
+    if (fp64) return upload(reinterpret_cast<double**>(dst), v);
+    return upload(reinterpret_cast<float**>(dst), std::vector<float>(v.begin(), v.end()));
+  };
+  const bool f64 = me->precision == ELM_FP64;
+  bool ok = put(&me->d_dtab, h.t64, f64) && put(&me->d_dwtab, h.w64, f64) && put(&me->d_drow_w, rw, f64);
+  if (f64)  // FP32 copies for the inner solves of the mixed-precision form
+    ok = ok && put(&me->d_dtab32, h.t64, false) && put(&me->d_dwtab32, h.w64, false) &&
+         put(&me->d_drow_w32, rw, false);
+  ok = ok && upload(&me->d_dnodes, h.nodes) && upload(&me->d_ditems, h.items) && upload(&me->d_drow_off, h.rows.off) &&
+       upload(&me->d_drow_col, h.rows.col) && upload(&me->d_drow_copy_off, h.rows.copy_off) &&
+       upload(&me->d_drow_copies, h.rows.copies);
+  ok = ok && upload(&me->d_dbnd_s, h.bnd_s) && upload(&me->d_dact, h.act) && upload(&me->d_dslot_owner, h.slot_owner);
+  ok = ok && cudaMalloc(&me->d_dvec, size_t(kDiffVectors) * me->n_storage * es) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&me->d_dpart, sizeof(double) * 2 * kRedMaxBlocks) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&me->d_dscal, sizeof(Scalars) + 2 * sizeof(double)) == cudaSuccess;
-  if (me->precision == ELM_FP64) {
-    // FP32 copies for the inner solves of the mixed-precision form
-    std::vector<float> t32(t64.begin(), t64.end());
-    ok = ok && cudaMalloc(&me->d_dtab32, tab * me->n_macros * 4) == cudaSuccess &&
-         cudaMemcpy(me->d_dtab32, t32.data(), tab * me->n_macros * 4, cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMalloc(&me->d_dvec32, size_t(kDiffVectors32) * me->n_unique * 4) == cudaSuccess;
-  }
+  if (f64) ok = ok && cudaMalloc(&me->d_dvec32, size_t(kDiffVectors32) * me->n_storage * 4) == cudaSuccess;
   if (!ok) {
     *err = std::string("diffusion tables: ") + cudaGetErrorString(cudaGetLastError());
     return ELM_ERR_CUDA;
   }
   me->n_boundary = 0;
-  for (uint8_t b : bnd) me->n_boundary += b;
+  for (uint8_t b : me->dbnd) me->n_boundary += b;
   return ELM_OK;
 }
 
 elm_status build_diffusion_blended(elm_mesh_s* me, std::string* err) {
   std::vector<double> t;
   blended_element_tables(me, t);
-  cudaFree(me->d_dtab_el);
-  me->d_dtab_el = nullptr;
-  if (cudaMalloc(&me->d_dtab_el, t.size() * sizeof(double)) != cudaSuccess ||
-      cudaMemcpy(me->d_dtab_el, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (!upload(reinterpret_cast<double**>(&me->d_dtab_el), t) || !build_cells_and_fold(me)) {
     *err = std::string("blended diffusion tables: ") + cudaGetErrorString(cudaGetLastError());
     return ELM_ERR_CUDA;
   }
@@ -874,55 +1344,77 @@ elm_status build_diffusion_blended(elm_mesh_s* me, std::string* err) {
 
 namespace {
 
-// y += scale (M + alpha A) x (diag: the diagonal only): the cell pass into
-// the colour accumulators, then (fold) their fold into y.  tables: the element
-// tables in the precision R (null: the mesh's own).  sc: the CG scalars whose
-// done flag ends the work early (null: always applied).
-template <class R>
-cudaError_t apply_op(const elm_mesh_s* me, const R* x, R* y, double alpha, double scale, bool diag, cudaStream_t s,
-                     const void* tables = nullptr, const Scalars* sc = nullptr, bool fold = true) {
-  const bool blended = me->blend.nsec > 0;
-  OpArgs a{tables ? tables : (blended ? me->d_dtab_el : me->d_dtab), me->d_dcells, me->d_dcellv, me->d_unique_map,
-           int(me->npm), me->N, sc};
-  R* ys = static_cast<R*>(sizeof(R) == 4 && me->precision == ELM_FP64 ? me->d_dys32 : me->d_dys);
+// Grids of the operator passes: persistent blocks, at most 8 per SM (the
+// partials of one reduction stay few).
+inline int capped_blocks(const elm_mesh_s* me, int64_t want) {
+  const int64_t cap = 8 * int64_t(me->n_dsm > 0 ? me->n_dsm : 1);
+  return int(want < cap ? want : cap);
+}
+// the stencil pass (affine meshes), then the face rows or, on a blended
+// mesh, the cell pass's fold: blocks of each, in launch order
+inline int stencil_blocks(const elm_mesh_s* me) {
+  return me->blend.nsec > 0 || me->n_ditems == 0 ? 0 : capped_blocks(me, me->n_ditems / 4);
+}
+inline int second_blocks(const elm_mesh_s* me) {
+  if (me->blend.nsec > 0) return me->n_dface > 0 ? red_blocks(me->n_dface) : 0;
+  return me->n_drows > 0 ? capped_blocks(me, (me->n_drows + kRedThreads / 32 - 1) / (kRedThreads / 32)) : 0;
+}
+
+// The passes of one application, in order.  Affine meshes: the stencil over
+// the interior nodes, then the assembled face rows; blended meshes: the cell
+// pass into the colour accumulators, then their fold.  MODE (OpMode) says
+// what is done with the result; with kOpCg the partials of p.q are left in
+// part[0 .. stencil_blocks + second_blocks).  The FP32 inner solves of an
+// FP64 mesh use the FP32 copies of the weights.
+template <class R, int MODE>
+cudaError_t launch_op(const elm_mesh_s* me, const R* x, R* y, double alpha, double scale, cudaStream_t s,
+                      const Scalars* sc, double* part) {
   const R al = R(alpha), sca = R(scale);
-  const unsigned g = unsigned(me->n_cell_chunks);
-  if (g > 0) {
-    bool launched = false;
-    if constexpr (sizeof(R) == 8) {
-      if (blended) {  // 2D FP64 only (elm_mesh_set_annulus)
-        if (me->order == 2) {
-          if (diag) k_apply<2, R, 2, true, true><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);
-          else k_apply<2, R, 2, false, true><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);
-        } else {
-          if (diag) k_apply<2, R, 1, true, true><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);
-          else k_apply<2, R, 1, false, true><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);
-        }
-        launched = true;
+  if (me->blend.nsec > 0) {
+    if constexpr (sizeof(R) == 8) {  // 2D FP64 only (elm_mesh_set_annulus)
+      OpArgs a{me->d_dtab_el, me->d_dcells, me->d_dcellv, int(me->npm), me->N, sc};
+      R* ys = static_cast<R*>(me->d_dys);
+      constexpr bool DG = MODE == kOpDiag;
+      const unsigned g = unsigned(me->n_cell_chunks);
+      if (g > 0) {
+        if (me->order == 2) k_apply<2, R, 2, DG, true><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);
+        else k_apply<2, R, 1, DG, true><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);
       }
-    }
-    if (!launched) {
-      if (blended) return cudaErrorInvalidValue;
-#define ELM_APPLY(DD, PP)                                                              \
-  if (diag) k_apply<DD, R, PP, true><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);   \
-  else k_apply<DD, R, PP, false><<<g, kDiffThreads, 0, s>>>(a, x, ys, al, sca);
-      if (me->dim == 3) {
-        if (me->order == 2) { ELM_APPLY(3, 2) } else { ELM_APPLY(3, 1) }
-      } else {
-        if (me->order == 2) { ELM_APPLY(2, 2) } else { ELM_APPLY(2, 1) }
-      }
-#undef ELM_APPLY
+      if (me->n_dface > 0)
+        k_fold_nodes<R, 4, MODE><<<second_blocks(me), kRedThreads, 0, s>>>(
+            ys, y, me->d_dfold_off, me->d_dfold_slots, me->d_dfbnd, me->n_dface, x, part, sc);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
     }
   }
-  const int64_t n = me->n_unique;
-  const unsigned fb = unsigned((n + 255) / 256);
-  if (fold && n > 0) {
-    if (me->dim == 3)
-      k_fold<R, 8><<<fb, 256, 0, s>>>(ys, y, me->d_dfold_off, me->d_dfold_slots, n, sc);
-    else
-      k_fold<R, 4><<<fb, 256, 0, s>>>(ys, y, me->d_dfold_off, me->d_dfold_slots, n, sc);
+  const bool inner = sizeof(R) == 4 && me->precision == ELM_FP64;  // FP32 inner solves of an FP64 mesh
+  const int nsb = stencil_blocks(me);
+  if (nsb > 0) {
+    StencilArgs st{inner ? me->d_dwtab32 : me->d_dwtab, me->d_dnodes, me->d_ditems, me->n_ditems / 4, int(me->npm),
+                   sc};
+    if (me->dim == 3) {
+      if (me->order == 2) k_stencil<3, R, 2, MODE><<<nsb, 128, 0, s>>>(st, x, y, al, sca, part);
+      else k_stencil<3, R, 1, MODE><<<nsb, 128, 0, s>>>(st, x, y, al, sca, part);
+    } else {
+      if (me->order == 2) k_stencil<2, R, 2, MODE><<<nsb, 128, 0, s>>>(st, x, y, al, sca, part);
+      else k_stencil<2, R, 1, MODE><<<nsb, 128, 0, s>>>(st, x, y, al, sca, part);
+    }
+  }
+  if (me->n_drows > 0) {
+    const FaceRows fr{me->d_drow_off, me->d_drow_col, inner ? me->d_drow_w32 : me->d_drow_w,
+                      me->n_dnnz,      me->d_drow_copy_off, me->d_drow_copies,
+                      me->n_drows,     sc};
+    k_face_rows<R, MODE><<<second_blocks(me), kRedThreads, 0, s>>>(fr, x, y, al, sca, part ? part + nsb : nullptr);
   }
   return cudaGetLastError();
+}
+
+// y += scale (M + alpha A) x (diag: the diagonal only), storage layout.
+template <class R>
+cudaError_t apply_op(const elm_mesh_s* me, const R* x, R* y, double alpha, double scale, bool diag, cudaStream_t s) {
+  return diag ? launch_op<R, kOpDiag>(me, x, y, alpha, scale, s, nullptr, nullptr)
+              : launch_op<R, kOpAccum>(me, x, y, alpha, scale, s, nullptr, nullptr);
 }
 
 // PCG iterations on the interior from the state of k_cg_start (r, z = D^{-1} r,
@@ -935,12 +1427,13 @@ cudaError_t apply_op(const elm_mesh_s* me, const R* x, R* y, double alpha, doubl
 constexpr int kCheckEvery = 8;
 
 template <class R>
-bool pcg_iterate(const elm_mesh_s* me, const void* tab, R* x, R* r, R* z, R* p, R* qv, const R* dinv, double alpha,
-                 double stop_rr, int budget, int* done, double* rr, cudaStream_t s, std::string* err) {
-  const int64_t n = me->n_unique;
+bool pcg_iterate(const elm_mesh_s* me, R* x, R* r, R* z, R* p, R* qv, const R* dinv, double alpha, double stop_rr,
+                 int budget, int* done, double* rr, cudaStream_t s, std::string* err) {
+  const int64_t n = me->n_storage;
   double* part = me->d_dpart;
   Scalars* sc = reinterpret_cast<Scalars*>(me->d_dscal);
   const int nred = red_blocks(n);
+  const int nop = stencil_blocks(me) + second_blocks(me);
   auto chk = [&](cudaError_t e, const char* where) {
     if (e != cudaSuccess) *err = std::string(where) + ": " + cudaGetErrorString(e);
     return e == cudaSuccess;
@@ -953,17 +1446,10 @@ bool pcg_iterate(const elm_mesh_s* me, const void* tab, R* x, R* r, R* z, R* p, 
       return false;
     if (h.done) break;
     for (int k = 0; k < kCheckEvery; ++k) {
-      // q = E p (the fold of the cell pass) and p.q in one pass
-      if (!chk(apply_op<R>(me, p, qv, alpha, 1.0, false, s, tab, sc, false), "apply")) return false;
-      const R* ys = static_cast<const R*>(sizeof(R) == 4 && me->precision == ELM_FP64 ? me->d_dys32 : me->d_dys);
-      if (me->dim == 3)
-        k_fold_pq<R, 8><<<nred, kRedThreads, 0, s>>>(ys, p, qv, me->d_dfold_off, me->d_dfold_slots, me->d_dbnd, n,
-                                                     part, sc);
-      else
-        k_fold_pq<R, 4><<<nred, kRedThreads, 0, s>>>(ys, p, qv, me->d_dfold_off, me->d_dfold_slots, me->d_dbnd, n,
-                                                     part, sc);
-      k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 1, sc, 0.0, 0);
-      k_cg_update<R><<<nred, kRedThreads, 0, s>>>(x, r, z, p, qv, dinv, sc, n, part);
+      // q = E p (0 on the boundary) and the partials of p.q
+      if (!chk(launch_op<R, kOpCg>(me, p, qv, alpha, 1.0, s, sc, part), "apply")) return false;
+      k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nop, 1, sc, 0.0, 0);
+      k_cg_update<R><<<nred, kRedThreads, 0, s>>>(x, r, z, p, qv, dinv, me->d_dact, sc, n, part);
       k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 2, sc, 0.0, 0);
       k_cg_direction<R><<<nred, kRedThreads, 0, s>>>(p, z, sc, n);
     }
@@ -977,14 +1463,14 @@ bool pcg_iterate(const elm_mesh_s* me, const void* tab, R* x, R* r, R* z, R* p, 
 // residual r = b - E x is formed in FP64; E d = r is solved by the same PCG
 // in FP32 (to a relative residual of kInnerRtol) and x += d.  Each correction
 // gains about four digits, so a solve to 1e-11 takes three FP64 operator
-// applications instead of one per iteration: the FP64 element products run on
-// this part's narrow FP64 pipe, the FP32 ones on its FP32 pipe.
+// applications instead of one per iteration: the FP64 products run on this
+// part's narrow FP64 pipe, the FP32 ones on its FP32 pipe.
 constexpr double kInnerRtol = 3e-5;
 
 elm_status solve_mixed(elm_mesh_s* me, const void* c_hat, const void* c_bnd, const void* q, void* c_new,
                        double tau, double kappa, double theta, double rtol, int max_iter, int* iters, double* resid,
                        cudaStream_t s, std::string* err) {
-  const int64_t n = me->n_unique;
+  const int64_t n = me->n_storage;
   double* v = static_cast<double*>(me->d_dvec);
   double* x = v;
   double* r = v + n;
@@ -1007,22 +1493,23 @@ elm_status solve_mixed(elm_mesh_s* me, const void* c_hat, const void* c_bnd, con
     if (e != cudaSuccess) *err = std::string(where) + ": " + cudaGetErrorString(e);
     return e == cudaSuccess;
   };
-  if (!chk(launch_gather(ELM_FP64, c_hat, x, me->d_owner, n, 1, s), "gather c_hat")) return ELM_ERR_CUDA;
+  // inputs in the storage layout, every copy taking its owner's value
+  if (!chk(launch_gather(ELM_FP64, c_hat, x, me->d_dslot_owner, n, 1, s), "gather c_hat")) return ELM_ERR_CUDA;
   if (!chk(cudaMemsetAsync(b, 0, bytes, s), "memset")) return ELM_ERR_CUDA;
   if (!chk(apply_op<double>(me, x, b, -tau * (1.0 - theta) * kappa, 1.0, false, s), "rhs")) return ELM_ERR_CUDA;
   if (q) {
-    if (!chk(launch_gather(ELM_FP64, q, tmp, me->d_owner, n, 1, s), "gather q")) return ELM_ERR_CUDA;
+    if (!chk(launch_gather(ELM_FP64, q, tmp, me->d_dslot_owner, n, 1, s), "gather q")) return ELM_ERR_CUDA;
     if (!chk(apply_op<double>(me, tmp, b, 0.0, tau, false, s), "source")) return ELM_ERR_CUDA;
   }
   if (c_bnd) {
-    if (!chk(launch_gather(ELM_FP64, c_bnd, tmp, me->d_owner, n, 1, s), "gather c_bnd")) return ELM_ERR_CUDA;
-    k_set_boundary<double><<<eb, 256, 0, s>>>(x, tmp, me->d_dbnd, n);
+    if (!chk(launch_gather(ELM_FP64, c_bnd, tmp, me->d_dslot_owner, n, 1, s), "gather c_bnd")) return ELM_ERR_CUDA;
+    k_set_boundary<double><<<eb, 256, 0, s>>>(x, tmp, me->d_dbnd_s, n);
   }
   const double alpha = tau * theta * kappa;
   if (!chk(cudaMemsetAsync(dinv32, 0, size_t(n) * 4, s), "memset")) return ELM_ERR_CUDA;
-  if (!chk(apply_op<float>(me, nullptr, dinv32, alpha, 1.0, true, s, me->d_dtab32), "diagonal")) return ELM_ERR_CUDA;
-  k_invert_diag<float><<<eb, 256, 0, s>>>(dinv32, me->d_dbnd, n);
-  k_norm2<double><<<nred, kRedThreads, 0, s>>>(b, me->d_dbnd, n, part);
+  if (!chk(apply_op<float>(me, nullptr, dinv32, alpha, 1.0, true, s), "diagonal")) return ELM_ERR_CUDA;
+  k_invert_diag<float><<<eb, 256, 0, s>>>(dinv32, me->d_dbnd_s, n);
+  k_norm2<double><<<nred, kRedThreads, 0, s>>>(b, me->d_dact, n, part);
   k_sum_into<<<1, kRedThreads, 0, s>>>(part, nred, bnorm);
   double hb = 0.0;
   if (!chk(cudaMemcpyAsync(&hb, bnorm, sizeof(double), cudaMemcpyDeviceToHost, s), "read") ||
@@ -1036,7 +1523,7 @@ elm_status solve_mixed(elm_mesh_s* me, const void* c_hat, const void* c_bnd, con
     // r = b - E x (FP64), interior only
     k_copy<double><<<eb, 256, 0, s>>>(r, b, n);
     if (!chk(apply_op<double>(me, x, r, alpha, -1.0, false, s), "residual")) return ELM_ERR_CUDA;
-    k_norm2<double><<<nred, kRedThreads, 0, s>>>(r, me->d_dbnd, n, part);
+    k_norm2<double><<<nred, kRedThreads, 0, s>>>(r, me->d_dact, n, part);
     k_sum_into<<<1, kRedThreads, 0, s>>>(part, nred, rnorm);
     double hr = 0.0;
     if (!chk(cudaMemcpyAsync(&hr, rnorm, sizeof(double), cudaMemcpyDeviceToHost, s), "read") ||
@@ -1045,15 +1532,14 @@ elm_status solve_mixed(elm_mesh_s* me, const void* c_hat, const void* c_bnd, con
     rel = bn > 0.0 ? std::sqrt(hr) / bn : std::sqrt(hr);
     if (!interior || !(rel > rtol) || total >= max_iter || !std::isfinite(rel)) break;
     // inner FP32 solve of E d = r from d = 0
-    k_residual_to_float<<<eb, 256, 0, s>>>(r, r32, d32, me->d_dbnd, n);
-    k_cg_start<float><<<nred, kRedThreads, 0, s>>>(r32, z32, p32, q32, dinv32, me->d_dbnd, n, part);
+    k_residual_to_float<<<eb, 256, 0, s>>>(r, r32, d32, me->d_dbnd_s, n);
+    k_cg_start<float><<<nred, kRedThreads, 0, s>>>(r32, z32, p32, q32, dinv32, me->d_dbnd_s, me->d_dact, n, part);
     int done = 0;
     double rr32 = 0.0;
     // stop at kInnerRtol of the inner start, or where the outer tolerance is met
     const double start_rr = hr;
     const double stop = std::max(kInnerRtol * kInnerRtol * start_rr, 0.25 * rtol * rtol * bn * bn);
-    if (!pcg_iterate<float>(me, me->d_dtab32, d32, r32, z32, p32, q32, dinv32, alpha, stop, max_iter - total,
-                            &done, &rr32, s, err))
+    if (!pcg_iterate<float>(me, d32, r32, z32, p32, q32, dinv32, alpha, stop, max_iter - total, &done, &rr32, s, err))
       return ELM_ERR_CUDA;
     total += done;
     k_add_correction<<<eb, 256, 0, s>>>(x, d32, n);
@@ -1061,7 +1547,7 @@ elm_status solve_mixed(elm_mesh_s* me, const void* c_hat, const void* c_bnd, con
   }
   if (iters) *iters = total;
   if (resid) *resid = rel;
-  if (!chk(launch_gather(ELM_FP64, x, c_new, me->d_unique_map, me->n_storage, 1, s), "scatter")) return ELM_ERR_CUDA;
+  if (!chk(cudaMemcpyAsync(c_new, x, bytes, cudaMemcpyDeviceToDevice, s), "result")) return ELM_ERR_CUDA;
   if (!std::isfinite(rel)) {
     *err = "non-finite residual";
     return ELM_ERR_NONFINITE;
@@ -1077,7 +1563,7 @@ template <class R>
 elm_status solve(elm_mesh_s* me, const void* c_hat, const void* c_bnd, const void* q, void* c_new, double tau,
                  double kappa, double theta, double rtol, int max_iter, int* iters, double* resid, cudaStream_t s,
                  std::string* err) {
-  const int64_t n = me->n_unique;
+  const int64_t n = me->n_storage;
   R* v = static_cast<R*>(me->d_dvec);
   R* x = v;
   R* r = v + n;
@@ -1096,29 +1582,29 @@ elm_status solve(elm_mesh_s* me, const void* c_hat, const void* c_bnd, const voi
     if (e != cudaSuccess) *err = std::string(where) + ": " + cudaGetErrorString(e);
     return e == cudaSuccess;
   };
-  // c_hat (storage) -> x (unique); right-hand side b
-  if (!chk(launch_gather(prec, c_hat, x, me->d_owner, n, 1, s), "gather c_hat")) return ELM_ERR_CUDA;
+  // inputs in the storage layout, every copy taking its owner's value; right-hand side b
+  if (!chk(launch_gather(prec, c_hat, x, me->d_dslot_owner, n, 1, s), "gather c_hat")) return ELM_ERR_CUDA;
   if (!chk(cudaMemsetAsync(b, 0, bytes, s), "memset")) return ELM_ERR_CUDA;
   if (!chk(apply_op<R>(me, x, b, -tau * (1.0 - theta) * kappa, 1.0, false, s), "rhs")) return ELM_ERR_CUDA;
   if (q) {
-    if (!chk(launch_gather(prec, q, z, me->d_owner, n, 1, s), "gather q")) return ELM_ERR_CUDA;
+    if (!chk(launch_gather(prec, q, z, me->d_dslot_owner, n, 1, s), "gather q")) return ELM_ERR_CUDA;
     if (!chk(apply_op<R>(me, z, b, 0.0, tau, false, s), "source")) return ELM_ERR_CUDA;
   }
   if (c_bnd) {
-    if (!chk(launch_gather(prec, c_bnd, z, me->d_owner, n, 1, s), "gather c_bnd")) return ELM_ERR_CUDA;
-    k_set_boundary<R><<<eb, 256, 0, s>>>(x, z, me->d_dbnd, n);
+    if (!chk(launch_gather(prec, c_bnd, z, me->d_dslot_owner, n, 1, s), "gather c_bnd")) return ELM_ERR_CUDA;
+    k_set_boundary<R><<<eb, 256, 0, s>>>(x, z, me->d_dbnd_s, n);
   }
   // Jacobi preconditioner of E = M + tau theta kappa A
   const double alpha = tau * theta * kappa;
   if (!chk(cudaMemsetAsync(dinv, 0, bytes, s), "memset")) return ELM_ERR_CUDA;
   if (!chk(apply_op<R>(me, x, dinv, alpha, 1.0, true, s), "diagonal")) return ELM_ERR_CUDA;
-  k_invert_diag<R><<<eb, 256, 0, s>>>(dinv, me->d_dbnd, n);
-  k_norm2<R><<<nred, kRedThreads, 0, s>>>(b, me->d_dbnd, n, part);
+  k_invert_diag<R><<<eb, 256, 0, s>>>(dinv, me->d_dbnd_s, n);
+  k_norm2<R><<<nred, kRedThreads, 0, s>>>(b, me->d_dact, n, part);
   k_sum_into<<<1, kRedThreads, 0, s>>>(part, nred, bnorm);
   // r = b - E x, restricted to the interior; z = D^{-1} r; p = z
   k_copy<R><<<eb, 256, 0, s>>>(r, b, n);
   if (!chk(apply_op<R>(me, x, r, alpha, -1.0, false, s), "residual")) return ELM_ERR_CUDA;
-  k_cg_start<R><<<nred, kRedThreads, 0, s>>>(r, z, p, qv, dinv, me->d_dbnd, n, part);
+  k_cg_start<R><<<nred, kRedThreads, 0, s>>>(r, z, p, qv, dinv, me->d_dbnd_s, me->d_dact, n, part);
   double hb = 0.0;
   if (!chk(cudaMemcpyAsync(&hb, bnorm, sizeof(double), cudaMemcpyDeviceToHost, s), "read") ||
       !chk(cudaStreamSynchronize(s), "sync"))
@@ -1128,12 +1614,12 @@ elm_status solve(elm_mesh_s* me, const void* c_hat, const void* c_bnd, const voi
   int it = 0;
   double rr = 0.0;
   const double stop = bn > 0.0 ? rtol * rtol * bn * bn : rtol * rtol;
-  if (!pcg_iterate<R>(me, nullptr, x, r, z, p, qv, dinv, alpha, stop, interior ? max_iter : 0, &it, &rr, s, err))
+  if (!pcg_iterate<R>(me, x, r, z, p, qv, dinv, alpha, stop, interior ? max_iter : 0, &it, &rr, s, err))
     return ELM_ERR_CUDA;
   const double rel = bn > 0.0 ? std::sqrt(rr) / bn : std::sqrt(rr);
   if (iters) *iters = it;
   if (resid) *resid = rel;
-  if (!chk(launch_gather(prec, x, c_new, me->d_unique_map, me->n_storage, 1, s), "scatter")) return ELM_ERR_CUDA;
+  if (!chk(cudaMemcpyAsync(c_new, x, bytes, cudaMemcpyDeviceToDevice, s), "result")) return ELM_ERR_CUDA;
   if (!std::isfinite(rel)) {
     *err = "non-finite residual";
     return ELM_ERR_NONFINITE;

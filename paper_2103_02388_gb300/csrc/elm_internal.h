@@ -174,22 +174,48 @@ struct elm_mesh_s {
   unsigned long long* d_adj_stat = nullptr;  // [2][3 n]: largest |contribution| bits, count
   int* d_adj_kexp = nullptr;                 // [3 n]
   unsigned* d_status = nullptr;
-  // diffusion solver (ELM_DIFFUSION): element tables per macro, boundary mask
-  // and CG vectors in the unique layout, reduction space
+  // diffusion solver (ELM_DIFFUSION): element tables and stencil weights per
+  // macro, the interior node lists of the stencil pass, the assembled rows of
+  // the face nodes, masks and CG vectors in the storage layout, reduction
+  // space
   bool with_diffusion = false;
   void* d_dtab = nullptr;
   void* d_dtab_el = nullptr;         // blended meshes: per-simplex mass and stiffness
   void* d_dtab32 = nullptr;          // FP64 meshes: FP32 copy of the tables (inner solves)
+  void* d_dwtab = nullptr;           // node-centred stencil weights per macro: [mass | stiffness][entries]
+  void* d_dwtab32 = nullptr;         // FP64 meshes: FP32 copy of the stencil weights
   void* d_dvec32 = nullptr;          // FP64 meshes: FP32 vectors of the inner solves
-  uint8_t* d_dbnd = nullptr;
-  int4* d_dcells = nullptr;          // (macro, first cell, count, colour) chunks of the operator
+  std::vector<uint8_t> dbnd;         // per unique node: Dirichlet boundary
+  uint8_t* d_dbnd_s = nullptr;       // per storage slot: Dirichlet boundary
+  uint8_t* d_dact = nullptr;         // per storage slot: owner copy of an interior unknown (dot products)
+  int64_t* d_dslot_owner = nullptr;  // per storage slot: the owner slot of its node
+  // interior nodes (node-centred stencil): packed lattice points by macro and
+  // class, warp items (macro, class, first node, count), 4 per block (one macro)
+  uint32_t* d_dnodes = nullptr;
+  int4* d_ditems = nullptr;
+  int64_t n_ditems = 0;
+  int n_dsm = 0;                     // SMs of the device (grids of the operator passes)
+  // face nodes off the Dirichlet boundary (assembled rows): row r has entries
+  // [row_off[r], row_off[r + 1]) of (column slot, mass weight, stiffness
+  // weight) and writes its value to the copies [copy_off[r], copy_off[r + 1])
+  int64_t n_drows = 0;
+  int64_t n_dnnz = 0;
+  int* d_drow_off = nullptr;
+  int* d_drow_col = nullptr;
+  void* d_drow_w = nullptr;          // [2][nnz]: mass, then stiffness weights (mesh precision)
+  void* d_drow_w32 = nullptr;        // FP64 meshes: FP32 copy
+  int* d_drow_copy_off = nullptr;
+  int* d_drow_copies = nullptr;
+  // blended meshes (per-simplex tables): the cell pass over every cell and
+  // its fold into every node
+  int4* d_dcells = nullptr;          // (macro, first cell, count, colour) chunks of the cell pass
   int4* d_dcellv = nullptr;          // cells (c0, c1, c2) in colour, then macro order
   int64_t n_cell_chunks = 0;
-  std::vector<int64_t> cell_color_off;  // chunks of colour k: [off[k], off[k + 1])
-  int* d_dfold_off = nullptr;        // unique id -> its storage copies, ascending slot: [off[u], off[u + 1])
+  int64_t n_dface = 0;               // fold nodes (every unique node)
+  int* d_dfold_off = nullptr;        // fold node f -> its storage copies, ascending slot: [off[f], off[f + 1])
   int* d_dfold_slots = nullptr;
-  void* d_dys = nullptr;             // colour accumulators per storage slot (mesh precision)
-  void* d_dys32 = nullptr;           // FP64 meshes: the same in FP32 (inner solves)
+  uint8_t* d_dfbnd = nullptr;        // per fold node: Dirichlet boundary
+  void* d_dys = nullptr;             // blended meshes: colour accumulators per storage slot
   int64_t n_boundary = 0;
   void* d_dvec = nullptr;
   double* d_dpart = nullptr;
