@@ -378,11 +378,30 @@ void blended_element_tables(const elm_mesh_s* me, std::vector<double>& out) {
 // ---------------------------------------------------------------------------
 
 // CG scalars on the device.  done: the residual or the iteration budget was
-// reached (set by k_cg_scalars); iters: iterations completed.
+// reached; iters: iterations completed; arrived: blocks of the current grid
+// that have written their partial (the last one completes the reduction).
 struct Scalars {
   double rz, rz_new, pq, rr, bb, alpha, beta, stop_rr;
-  int done, iters, budget, pad;
+  int done, iters, budget;
+  unsigned arrived;
 };
+
+// Updates the CG scalars from reduced sums a (and b):
+// what = 1: p.q -> alpha; 2: (r.z, r.r) -> beta, one iteration done, and the
+// done flag once |r|^2 <= stop_rr (or it is not finite) or the budget is spent.
+__device__ __forceinline__ void cg_scalars_update(int what, double a, double b, Scalars* sc) {
+  if (what == 1) {
+    sc->pq = a;
+    sc->alpha = a != 0.0 ? sc->rz / a : 0.0;
+  } else {
+    sc->rz_new = a;
+    sc->rr = b;
+    sc->beta = sc->rz != 0.0 ? a / sc->rz : 0.0;
+    sc->rz = a;
+    sc->iters += 1;
+    if (b <= sc->stop_rr || !isfinite(b) || sc->iters >= sc->budget) sc->done = 1;
+  }
+}
 
 // What an operator pass does with its result v at a node.
 enum OpMode {
@@ -582,13 +601,44 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;
 }
 
+// Completes a CG reduction inside the kernel that produced its last
+// partials: every block has written its partial(s) (thread 0, before this
+// call); the last block to arrive sums part[0 .. nparts) (what = 2: and
+// part[nparts .. 2 nparts)) in a fixed order, so the result does not depend
+// on which block is last, updates the scalars and resets the arrival count.
+// No block waits for another.
+__device__ void finish_cg(const double* part, int nparts, int what, Scalars* sc, double* sh) {
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&sc->arrived, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    s1 += __ldcg(part + i);
+    if (what == 2) s2 += __ldcg(part + nparts + i);
+  }
+  const double a = block_sum(s1, sh);
+  __syncthreads();
+  const double b = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    cg_scalars_update(what, a, b, sc);
+    sc->arrived = 0;
+  }
+}
+
 struct StencilArgs {
   const void* wtab;       // per macro: mass weights, then stiffness weights ([2][entries])
   const uint32_t* nodes;  // interior lattice points, packed (3D: q0 | q1 << 10 | q2 << 20; 2D: q0 | q1 << 16)
   const int4* items;      // (macro, class, first node, count); 4 per group, one macro per group
   int64_t n_groups;
   int npm;
-  const Scalars* sc;
+  Scalars* sc;
+  int finish;             // kOpCg: > 0 when this pass completes the p.q reduction over `finish` partials
 };
 
 // The stencil pass over the interior nodes: each warp takes up to 32 nodes
@@ -638,8 +688,10 @@ __global__ void __launch_bounds__(128) k_stencil(StencilArgs a, const R* __restr
     }
   }
   if constexpr (MODE == kOpCg) {
+    __syncthreads();
     const double t = block_sum(double(pq), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (a.finish > 0) finish_cg(part, a.finish, 1, a.sc, sh);
   }
 }
 
@@ -651,7 +703,9 @@ struct FaceRows {
   const int* copy_off;   // row r's node: storage copies [copy_off[r], copy_off[r + 1]), owner first
   const int* copies;
   int64_t n;             // rows
-  const Scalars* sc;
+  Scalars* sc;
+  int finish;            // kOpCg: > 0 when this pass completes the p.q reduction over `finish` partials
+  double* part0;         // start of the reduction space (the stencil's partials come first)
 };
 
 // The assembled rows of the face nodes off the Dirichlet boundary (nodes on a
@@ -696,6 +750,7 @@ __global__ void __launch_bounds__(kRedThreads) k_face_rows(FaceRows a, const R* 
   if constexpr (MODE == kOpCg) {
     const double t = block_sum(double(pq), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (a.finish > 0) finish_cg(a.part0, a.finish, 1, a.sc, sh);
   }
 }
 
@@ -796,7 +851,7 @@ template <class R, int NCOL, int MODE>
 __global__ void __launch_bounds__(kRedThreads) k_fold_nodes(const R* __restrict__ ys, R* __restrict__ y,
                                                             const int* __restrict__ off, const int* __restrict__ slots,
                                                             const uint8_t* __restrict__ fbnd, int64_t nf,
-                                                            const R* __restrict__ x, double* part, const Scalars* sc) {
+                                                            const R* __restrict__ x, double* part, Scalars* sc) {
   __shared__ double sh[kRedThreads / 32];
   if (sc != nullptr && sc->done) return;
   R pq = R(0);
@@ -823,6 +878,7 @@ __global__ void __launch_bounds__(kRedThreads) k_fold_nodes(const R* __restrict_
   if constexpr (MODE == kOpCg) {
     const double t = block_sum(double(pq), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
+    finish_cg(part, int(gridDim.x), 1, sc, sh);
   }
 }
 
@@ -862,24 +918,47 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_start(R* r, R* z, R* p, R* q
   }
 }
 
-// x += alpha p; r -= alpha q; z = dinv r; partials (r.z, r.r).
+// x += alpha p; r -= alpha q; z = dinv r; partials (r.z, r.r), and the last
+// block completes the reduction (beta, the iteration count, the done flag).
+// Each thread takes kVec elements a grid stride apart per round (their loads
+// independent, so they are in flight together).
+constexpr int kVec = 4;
+
 template <class R>
 __global__ void __launch_bounds__(kRedThreads) k_cg_update(R* x, R* r, R* z, const R* p, const R* q, const R* dinv,
-                                                           const uint8_t* act, const Scalars* sc, int64_t n,
-                                                           double* part) {
+                                                           const uint8_t* act, Scalars* sc, int64_t n, double* part) {
   __shared__ double sh[kRedThreads / 32];
   if (sc->done) return;
   const R al = R(sc->alpha);
   R rz = R(0), rr = R(0);
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    x[i] += al * p[i];
-    const R ri = r[i] - al * q[i];
-    r[i] = ri;
-    const R zi = dinv[i] * ri;
-    z[i] = zi;
-    if (act[i]) {
-      rz += ri * zi;
-      rr += ri * ri;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < n; i0 += kVec * stride) {
+    R pv[kVec], qv[kVec], rv[kVec], dv[kVec], xv[kVec];
+    bool av[kVec];
+#pragma unroll
+    for (int j = 0; j < kVec; ++j) {
+      const int64_t i = i0 + j * stride;
+      const bool in = i < n;
+      pv[j] = in ? p[i] : R(0);
+      qv[j] = in ? q[i] : R(0);
+      rv[j] = in ? r[i] : R(0);
+      dv[j] = in ? dinv[i] : R(0);
+      xv[j] = in ? x[i] : R(0);
+      av[j] = in && act[i];
+    }
+#pragma unroll
+    for (int j = 0; j < kVec; ++j) {
+      const int64_t i = i0 + j * stride;
+      if (i >= n) continue;
+      x[i] = xv[j] + al * pv[j];
+      const R ri = rv[j] - al * qv[j];
+      r[i] = ri;
+      const R zi = dv[j] * ri;
+      z[i] = zi;
+      if (av[j]) {
+        rz += ri * zi;
+        rr += ri * ri;
+      }
     }
   }
   const double s1 = block_sum(double(rz), sh);
@@ -889,6 +968,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(R* x, R* r, R* z, con
     part[blockIdx.x] = s1;
     part[gridDim.x + blockIdx.x] = s2;
   }
+  finish_cg(part, int(gridDim.x), 2, sc, sh);
 }
 
 // p = z + beta p (q is overwritten by the next operator pass).
@@ -896,45 +976,44 @@ template <class R>
 __global__ void __launch_bounds__(kRedThreads) k_cg_direction(R* p, const R* z, const Scalars* sc, int64_t n) {
   if (sc->done) return;
   const R be = R(sc->beta);
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    p[i] = z[i] + be * p[i];
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < n; i0 += kVec * stride) {
+    R zv[kVec], pv[kVec];
+#pragma unroll
+    for (int j = 0; j < kVec; ++j) {
+      const int64_t i = i0 + j * stride;
+      zv[j] = i < n ? z[i] : R(0);
+      pv[j] = i < n ? p[i] : R(0);
+    }
+#pragma unroll
+    for (int j = 0; j < kVec; ++j) {
+      const int64_t i = i0 + j * stride;
+      if (i < n) p[i] = zv[j] + be * pv[j];
+    }
+  }
 }
 
-// Sums the partials of a reduction and updates the CG scalars:
-// what = 0: start (rz, rr; the stopping residual and the iteration budget);
-// 1: p.q -> alpha; 2: update (rz_new, rr) -> beta, one iteration done.  Sets
-// done once |r|^2 <= stop_rr (or it is not finite) or the budget is spent.
-__global__ void __launch_bounds__(kRedThreads) k_cg_scalars(const double* part, int nparts, int what, Scalars* sc,
-                                                            double stop_rr, int budget) {
+// Starts a CG run: sums the partials of k_cg_start (r.z, r.r) and sets the
+// stopping residual, the iteration budget and the done flag.
+__global__ void __launch_bounds__(kRedThreads) k_cg_begin(const double* part, int nparts, Scalars* sc, double stop_rr,
+                                                          int budget) {
   __shared__ double sh[kRedThreads / 32];
-  if (what != 0 && sc->done) return;
   double s1 = 0.0, s2 = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
     s1 += part[i];
-    if (what != 1) s2 += part[nparts + i];
+    s2 += part[nparts + i];
   }
   const double a = block_sum(s1, sh);
   __syncthreads();
   const double b = block_sum(s2, sh);
   if (threadIdx.x == 0) {
-    if (what == 0) {
-      sc->rz = a;
-      sc->rr = b;
-      sc->stop_rr = stop_rr;
-      sc->budget = budget;
-      sc->iters = 0;
-      sc->done = (b <= stop_rr || !isfinite(b) || budget <= 0) ? 1 : 0;
-    } else if (what == 1) {
-      sc->pq = a;
-      sc->alpha = a != 0.0 ? sc->rz / a : 0.0;
-    } else {
-      sc->rz_new = a;
-      sc->rr = b;
-      sc->beta = sc->rz != 0.0 ? a / sc->rz : 0.0;
-      sc->rz = a;
-      sc->iters += 1;
-      if (b <= sc->stop_rr || !isfinite(b) || sc->iters >= sc->budget) sc->done = 1;
-    }
+    sc->rz = a;
+    sc->rr = b;
+    sc->stop_rr = stop_rr;
+    sc->budget = budget;
+    sc->iters = 0;
+    sc->arrived = 0;
+    sc->done = (b <= stop_rr || !isfinite(b) || budget <= 0) ? 1 : 0;
   }
 }
 
@@ -1364,11 +1443,12 @@ inline int second_blocks(const elm_mesh_s* me) {
 // the interior nodes, then the assembled face rows; blended meshes: the cell
 // pass into the colour accumulators, then their fold.  MODE (OpMode) says
 // what is done with the result; with kOpCg the partials of p.q are left in
-// part[0 .. stencil_blocks + second_blocks).  The FP32 inner solves of an
-// FP64 mesh use the FP32 copies of the weights.
+// part[0 .. stencil_blocks + second_blocks), and the last pass completes the
+// reduction (alpha).  The FP32 inner solves of an FP64 mesh use the FP32
+// copies of the weights.
 template <class R, int MODE>
 cudaError_t launch_op(const elm_mesh_s* me, const R* x, R* y, double alpha, double scale, cudaStream_t s,
-                      const Scalars* sc, double* part) {
+                      Scalars* sc, double* part) {
   const R al = R(alpha), sca = R(scale);
   if (me->blend.nsec > 0) {
     if constexpr (sizeof(R) == 8) {  // 2D FP64 only (elm_mesh_set_annulus)
@@ -1389,10 +1469,11 @@ cudaError_t launch_op(const elm_mesh_s* me, const R* x, R* y, double alpha, doub
     }
   }
   const bool inner = sizeof(R) == 4 && me->precision == ELM_FP64;  // FP32 inner solves of an FP64 mesh
-  const int nsb = stencil_blocks(me);
+  const int nsb = stencil_blocks(me), nfb = me->n_drows > 0 ? second_blocks(me) : 0;
+  const bool cg = MODE == kOpCg;
   if (nsb > 0) {
     StencilArgs st{inner ? me->d_dwtab32 : me->d_dwtab, me->d_dnodes, me->d_ditems, me->n_ditems / 4, int(me->npm),
-                   sc};
+                   sc, cg && nfb == 0 ? nsb : 0};
     if (me->dim == 3) {
       if (me->order == 2) k_stencil<3, R, 2, MODE><<<nsb, 128, 0, s>>>(st, x, y, al, sca, part);
       else k_stencil<3, R, 1, MODE><<<nsb, 128, 0, s>>>(st, x, y, al, sca, part);
@@ -1402,10 +1483,11 @@ cudaError_t launch_op(const elm_mesh_s* me, const R* x, R* y, double alpha, doub
     }
   }
   if (me->n_drows > 0) {
-    const FaceRows fr{me->d_drow_off, me->d_drow_col, inner ? me->d_drow_w32 : me->d_drow_w,
+    const FaceRows fr{me->d_drow_off, me->d_drow_col,  inner ? me->d_drow_w32 : me->d_drow_w,
                       me->n_dnnz,      me->d_drow_copy_off, me->d_drow_copies,
-                      me->n_drows,     sc};
-    k_face_rows<R, MODE><<<second_blocks(me), kRedThreads, 0, s>>>(fr, x, y, al, sca, part ? part + nsb : nullptr);
+                      me->n_drows,     sc,                 cg ? nsb + nfb : 0,
+                      part};
+    k_face_rows<R, MODE><<<nfb, kRedThreads, 0, s>>>(fr, x, y, al, sca, part ? part + nsb : nullptr);
   }
   return cudaGetLastError();
 }
@@ -1419,11 +1501,13 @@ cudaError_t apply_op(const elm_mesh_s* me, const R* x, R* y, double alpha, doubl
 
 // PCG iterations on the interior from the state of k_cg_start (r, z = D^{-1} r,
 // p = z; its partials of r.z and r.r in the reduction space): stops when
-// |r|^2 <= stop_rr or after `budget` iterations.  The iterations are enqueued
-// in batches of kCheckEvery; the device sets the done flag (k_cg_scalars) and
-// the kernels after it return at once, so the host reads the scalars once per
-// batch.  *done = iterations run, *rr = final |r|^2.  Returns false on a CUDA
-// error (message in *err).
+// |r|^2 <= stop_rr or after `budget` iterations.  Each iteration is three
+// passes: the operator (q = E p; its last kernel completes p.q and alpha),
+// the update (x, r, z; its last block completes beta and the done flag) and
+// the direction.  The iterations are enqueued in batches of kCheckEvery; once
+// the device sets the done flag the kernels after it return at once, so the
+// host reads the scalars once per batch.  *done = iterations run, *rr = final
+// |r|^2.  Returns false on a CUDA error (message in *err).
 constexpr int kCheckEvery = 8;
 
 template <class R>
@@ -1433,12 +1517,12 @@ bool pcg_iterate(const elm_mesh_s* me, R* x, R* r, R* z, R* p, R* qv, const R* d
   double* part = me->d_dpart;
   Scalars* sc = reinterpret_cast<Scalars*>(me->d_dscal);
   const int nred = red_blocks(n);
-  const int nop = stencil_blocks(me) + second_blocks(me);
+  const int nupd = red_blocks(n / kVec + 1);
   auto chk = [&](cudaError_t e, const char* where) {
     if (e != cudaSuccess) *err = std::string(where) + ": " + cudaGetErrorString(e);
     return e == cudaSuccess;
   };
-  k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 0, sc, stop_rr, budget);
+  k_cg_begin<<<1, kRedThreads, 0, s>>>(part, nred, sc, stop_rr, budget);
   Scalars h{};
   for (;;) {
     if (!chk(cudaMemcpyAsync(&h, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s), "read") ||
@@ -1446,12 +1530,10 @@ bool pcg_iterate(const elm_mesh_s* me, R* x, R* r, R* z, R* p, R* qv, const R* d
       return false;
     if (h.done) break;
     for (int k = 0; k < kCheckEvery; ++k) {
-      // q = E p (0 on the boundary) and the partials of p.q
+      // q = E p (0 on the boundary), p.q and alpha
       if (!chk(launch_op<R, kOpCg>(me, p, qv, alpha, 1.0, s, sc, part), "apply")) return false;
-      k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nop, 1, sc, 0.0, 0);
-      k_cg_update<R><<<nred, kRedThreads, 0, s>>>(x, r, z, p, qv, dinv, me->d_dact, sc, n, part);
-      k_cg_scalars<<<1, kRedThreads, 0, s>>>(part, nred, 2, sc, 0.0, 0);
-      k_cg_direction<R><<<nred, kRedThreads, 0, s>>>(p, z, sc, n);
+      k_cg_update<R><<<nupd, kRedThreads, 0, s>>>(x, r, z, p, qv, dinv, me->d_dact, sc, n, part);
+      k_cg_direction<R><<<nupd, kRedThreads, 0, s>>>(p, z, sc, n);
     }
   }
   *done = h.iters;
