@@ -617,10 +617,22 @@ __device__ void finish_cg(const double* part, int nparts, int what, Scalars* sc,
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // eight independent loads in flight per thread; the grouping is fixed
   double s1 = 0.0, s2 = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-    s1 += __ldcg(part + i);
-    if (what == 2) s2 += __ldcg(part + nparts + i);
+  const int step = int(blockDim.x);
+  for (int i0 = threadIdx.x; i0 < nparts; i0 += 8 * step) {
+    double v1[8], v2[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = i0 + j * step;
+      v1[j] = i < nparts ? __ldcg(part + i) : 0.0;
+      v2[j] = (what == 2 && i < nparts) ? __ldcg(part + nparts + i) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      s1 += v1[j];
+      s2 += v2[j];
+    }
   }
   const double a = block_sum(s1, sh);
   __syncthreads();
