@@ -686,7 +686,7 @@ def run_diffusion(args):
     """The diffusion solve of Eq. (linear system) on the unit cube (P2, 6 Kuhn
     macros): CUDA-event time of whole elm_diffusion_step calls, CG iterations,
     and the compulsory bytes of one CG iteration (operator apply plus vector
-    updates, unique layout) against the measured HBM peak."""
+    updates, storage layout) against the measured HBM peak."""
     import torch
     from paper_2103_02388_gb300 import elm, inputs
     dim, level, precision, order, tau, kappa, theta = DIFFUSION_WORKLOADS[args.workload]
@@ -714,10 +714,11 @@ def run_diffusion(args):
     # few FP64 residuals
     esz = 4
     n, ns = mesh.n_unique, mesh.n_nodes
-    # per CG iteration: apply (zero q, read p, write q, read the storage->unique
-    # map), p.q (read p, q; the boundary mask), update (x, r read+write; p, q,
-    # inverse diagonal read; z write), direction (read z, p; write p)
-    bytes_iter = n * esz * (3 + 2 + 8 + 3) + ns * 8 + n
+    # per CG iteration, vectors in the storage layout (ns slots): operator (read
+    # p, write q), update (x, r read + write; p, q, inverse diagonal read; z
+    # write; the 1-byte dot-product mask), direction (read z, p; write p).  The
+    # operator's own tables (interior node lists, face rows) are not counted.
+    bytes_iter = ns * (esz * (2 + 8 + 3) + 1)
     ms = float(np.median(times))
     it = int(np.median(iters))
     ms_iter = ms / max(it, 1)
