@@ -52,16 +52,19 @@
 namespace elm {
 namespace {
 
-// One block per work-list chunk: a run of up to blockDim consecutive nodes
-// of one slab p1 of one macro (host-built, so no thread divides or searches
-// for its lattice point beyond one row root).
+// kAdvectSplit blocks per work-list chunk: a chunk is a run of up to
+// kAdvectThreads consecutive nodes of one slab p1 of one macro (host-built, so
+// no thread divides or searches for its lattice point beyond one row root),
+// and block b takes the nodes [(b mod kAdvectSplit) kStepThreads, ...) of
+// chunk b / kAdvectSplit.
 // P is the element order (1 or 2), MODE what is done per node (NodeMode),
 // BLEND whether the mesh is blended onto an annulus.
 template <int D, class R, bool STEADY, int P, int MODE, int BLEND>
-__global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
+__global__ void __launch_bounds__(kStepThreads, ELM_ADVECT_MIN_BLOCKS * kAdvectSplit)
     k_advect(AdvectArgs args, Tables<R> tab, int chunk0) {
-  const int4 ck = args.chunks[chunk0 + int(blockIdx.x)];
-  if (int(threadIdx.x) >= ck.w) return;
+  const int4 ck = args.chunks[chunk0 + int(blockIdx.x) / kAdvectSplit];
+  const int tid = (int(blockIdx.x) % kAdvectSplit) * kStepThreads + int(threadIdx.x);
+  if (tid >= ck.w) return;
   NodeJob<R> job{args.geo,
                        static_cast<const R*>(args.u_new),
                        static_cast<const R*>(args.u_old),
@@ -81,7 +84,7 @@ __global__ void __launch_bounds__(kAdvectThreads, ELM_ADVECT_MIN_BLOCKS)
     job.n_macros = args.n_macros;
   }
   job.skip_ghosts = args.skip_ghosts;
-  advect_node<D, R, STEADY, P, MODE, BLEND>(job, tab, ck, int(threadIdx.x));
+  advect_node<D, R, STEADY, P, MODE, BLEND>(job, tab, ck, tid);
 }
 
 // Persistent batched kernel: each block repeatedly takes the next work item
@@ -190,17 +193,17 @@ cudaError_t launch_k(const AdvectArgs& a, Tables<R> t, cudaStream_t s) {
   const bool blended = a.blend.nsec > 0;
   if constexpr (D == 2 && sizeof(R) == 8) {
     if (blended) {
-      for (int c0 = 0; c0 < a.n_chunks; c0 += (1 << 30)) {
-        const int nb = a.n_chunks - c0 < (1 << 30) ? a.n_chunks - c0 : (1 << 30);
-        k_advect<D, R, STEADY, P, MODE, 1><<<nb, kAdvectThreads, 0, s>>>(a, t, c0);
+      for (int c0 = 0; c0 < a.n_chunks; c0 += (1 << 29)) {
+        const int nb = a.n_chunks - c0 < (1 << 29) ? a.n_chunks - c0 : (1 << 29);
+        k_advect<D, R, STEADY, P, MODE, 1><<<nb * kAdvectSplit, kStepThreads, 0, s>>>(a, t, c0);
       }
       return cudaGetLastError();
     }
   }
   if (blended) return cudaErrorInvalidValue;  // blending is 2D FP64 only (checked by the API)
-  for (int c0 = 0; c0 < a.n_chunks; c0 += (1 << 30)) {
-    const int nb = a.n_chunks - c0 < (1 << 30) ? a.n_chunks - c0 : (1 << 30);
-    k_advect<D, R, STEADY, P, MODE, 0><<<nb, kAdvectThreads, 0, s>>>(a, t, c0);
+  for (int c0 = 0; c0 < a.n_chunks; c0 += (1 << 29)) {
+    const int nb = a.n_chunks - c0 < (1 << 29) ? a.n_chunks - c0 : (1 << 29);
+    k_advect<D, R, STEADY, P, MODE, 0><<<nb * kAdvectSplit, kStepThreads, 0, s>>>(a, t, c0);
   }
   return cudaGetLastError();
 }

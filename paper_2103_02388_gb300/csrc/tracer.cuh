@@ -1078,8 +1078,9 @@ struct Tracer : std::conditional_t<BLEND == 1, BlendState, NoBlendState> {
   }
 };
 
-// 128-thread blocks, 8 resident per SM (64 registers per thread): measured
-// fastest on GB300 for the level-7 FP32 step (occupancy beats the few spills).
+// Resident 128-node chunks per SM (k_advect: 2 blocks of 64 threads each, so
+// 16 blocks; 64 registers per thread): measured fastest on GB300 for the
+// level-7 FP32 step (occupancy beats the few spills).
 #ifndef ELM_ADVECT_MIN_BLOCKS
 #define ELM_ADVECT_MIN_BLOCKS 8
 #endif
