@@ -1435,8 +1435,10 @@ elm_status build_diffusion_blended(elm_mesh_s* me, std::string* err) {
 
 namespace {
 
-// Grids of the operator passes: persistent blocks, at most 8 per SM (the
-// partials of one reduction stay few).
+// Grids of the operator passes: persistent blocks, at most 8 per SM for the
+// face rows and 12 for the stencil pass (its registers allow 12 resident
+// 128-thread blocks; measured 4.54 against 4.64 ms for the level-6 FP64 solve
+// with 8), so the partials of one reduction stay a few thousand.
 inline int capped_blocks(const elm_mesh_s* me, int64_t want) {
   const int64_t cap = 8 * int64_t(me->n_dsm > 0 ? me->n_dsm : 1);
   return int(want < cap ? want : cap);
@@ -1444,7 +1446,9 @@ inline int capped_blocks(const elm_mesh_s* me, int64_t want) {
 // the stencil pass (affine meshes), then the face rows or, on a blended
 // mesh, the cell pass's fold: blocks of each, in launch order
 inline int stencil_blocks(const elm_mesh_s* me) {
-  return me->blend.nsec > 0 || me->n_ditems == 0 ? 0 : capped_blocks(me, me->n_ditems / 4);
+  if (me->blend.nsec > 0 || me->n_ditems == 0) return 0;
+  const int64_t groups = me->n_ditems / 4, cap = 12 * int64_t(me->n_dsm > 0 ? me->n_dsm : 1);
+  return int(groups < cap ? groups : cap);
 }
 inline int second_blocks(const elm_mesh_s* me) {
   if (me->blend.nsec > 0) return me->n_dface > 0 ? red_blocks(me->n_dface) : 0;
