@@ -29,29 +29,32 @@
 // class, each lane one node, every neighbour read directly from the storage
 // layout.  No atomics; each node's row sum has a fixed order.
 //
-// Face nodes (on a face of their macro, shared with a neighbour or on the
-// domain boundary) take their rows from the cell pass over the cells that
-// touch a face.  Two lattice cells whose indices have the same parity in
-// every axis share no node, so each of the 2^d parities (colours) has its own
-// accumulator vector in the storage layout: within one colour every slot has
-// at most one writing thread, which stores its cell's sum over the cell's
-// simplices (added in a fixed order), and all colours run in one launch.  The
+// Face nodes shared by two or more macros take explicit rows, assembled on
+// the host from every micro simplex holding them (k_face_rows, one warp per
+// row); rows of Dirichlet nodes are never formed, since the solver never
+// reads them.
+//
+// A blended mesh, whose simplices each have their own matrices, takes every
+// cell through a cell pass instead: two lattice cells whose indices have the
+// same parity in every axis share no node, so each of the 2^d parities
+// (colours) has its own accumulator vector in the storage layout; within one
+// colour every slot has at most one writing thread, which stores its cell's
+// sum over the cell's simplices, and all colours run in one launch.  The
 // accumulators are tiled by 32 slots: accumulator (slot, colour) sits at
 // ((slot / 32) 2^d + colour) 32 + slot % 32.  Every accumulator that some
-// face cell of its colour covers is rewritten by that cell on every
-// application, and the others are never written and stay zero from the set-up.
-// A fold then adds, for every face node, its storage copies in ascending slot
-// order and, for each copy, the 2^d colour values in ascending order, and
-// writes the sum to every copy.  A blended mesh, whose simplices each have
-// their own matrices, takes every cell and node through this path.  The
-// summation order is fixed everywhere, so results are bitwise equal run to run.
+// cell of its colour covers is rewritten on every application, and the
+// others stay zero from the set-up.  A fold then adds, for every node, its
+// storage copies in ascending slot order and each copy's colours in
+// ascending order, and writes the sum to every copy.
 //
-// The solver's vectors are in the storage layout (the copies of an interface
-// node hold the same value); dot products count the owner copy of each
-// unknown.  Iterations run in batches of kCheckEvery between reads of the
-// residual by the host: the scalar kernel sets a done flag on the device once
-// the residual (or the iteration budget) is reached, and every later kernel
-// of the batch returns at once.
+// The summation order is fixed everywhere, so results are bitwise equal run
+// to run.  The solver's vectors are in the storage layout (the copies of an
+// interface node hold the same value); dot products count the owner copy of
+// each unknown.  Each dot product is completed inside the kernel that forms
+// its partials (the last block to finish sums them in a fixed order), which
+// also sets the done flag once the residual or the iteration budget is
+// reached; every later kernel of the batch then returns at once, and the host
+// reads the scalars once per kCheckEvery iterations.
 //
 // Dirichlet conditions: boundary unknowns keep c_bnd; CG runs on the
 // interior unknowns (search directions are zero on the boundary).
