@@ -25,9 +25,10 @@
 // one of the edge-midpoint classes) and the macro: the host sums the element
 // matrices into per-class, per-macro weights at fixed lattice offsets
 // (StencilShape: 65 offsets for the 3D P2 vertex class, 19 or 27 for its edge
-// classes), and k_stencil applies them, one warp per row segment of one
-// class, each lane one node, every neighbour read directly from the storage
-// layout.  No atomics; each node's row sum has a fixed order.
+// classes), and k_stencil applies them, one warp per 32 interior nodes of
+// one class (from host-built lists in storage order), each lane one node,
+// every neighbour read directly from the storage layout.  No atomics; each
+// node's row sum has a fixed order.
 //
 // Face nodes shared by two or more macros take explicit rows, assembled on
 // the host from every micro simplex holding them (k_face_rows, one warp per
