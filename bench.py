@@ -670,9 +670,37 @@ def run_ours(args, spec):
         line["cpu_baseline"] = _cpu_baseline(spec, om=om)
         del om
         line["accumulated_100"] = _accumulated_record(dev)
+        line["other_forms"] = _other_forms()
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _other_forms():
+    """The batched form (config 4, FP32), the differentiated rollout (config
+    5, FP32) and the diffusion solve (level 6, FP64) measured in the default
+    run, each as its own workload would report it (compact)."""
+    import argparse as _ap
+    out = {}
+
+    def keep(rec, keys):
+        return {k: rec[k] for k in keys if k in rec}
+    try:
+        r = run_batch(_ap.Namespace(workload="c4-batch-fp32", steps=100, warmup=3), emit=False)
+        out["c4-batch-fp32"] = keep(r, ("metric", "value", "unit", "ms_per_step", "steps", "gpu_launches")) | {
+            "autotune": {k: r["config"]["autotune"][k] for k in ("blocks_per_sm", "chunks_per_item")},
+            "graph": r["config"]["graph"], "instances": r["config"]["instances"],
+            "hbm_frac": r["roofline"]["frac"]}
+        r = run_adjoint(_ap.Namespace(workload="c5-adjoint-l6-fp32", steps=50, warmup=1), emit=False)
+        out["c5-adjoint-l6-fp32"] = keep(r, ("metric", "value", "unit", "ms_per_step", "steps")) | {
+            "timed": r["config"]["timed"]}
+        r = run_diffusion(_ap.Namespace(workload="diffusion-l6-fp64", steps=10, warmup=2), emit=False)
+        out["diffusion-l6-fp64"] = keep(r, ("metric", "value", "unit", "ms_per_solve", "cg_iterations",
+                                            "relative_residual")) | {"solver": r["config"]["solver"],
+                                                                     "hbm_frac": r["roofline"]["frac"]}
+    except Exception as e:  # reported, never hides the main record
+        out["error"] = f"{type(e).__name__}: {e}"
+    return out
 
 
 DIFFUSION_WORKLOADS = {
@@ -682,7 +710,7 @@ DIFFUSION_WORKLOADS = {
 }
 
 
-def run_diffusion(args):
+def run_diffusion(args, emit: bool = True):
     """The diffusion solve of Eq. (linear system) on the unit cube (P2, 6 Kuhn
     macros): CUDA-event time of whole elm_diffusion_step calls, CG iterations,
     and the compulsory bytes of one CG iteration (operator apply plus vector
@@ -724,7 +752,7 @@ def run_diffusion(args):
     ms_iter = ms / max(it, 1)
     hbm_peak, _, kind = _peaks()
     achieved = bytes_iter / (ms_iter * 1e-3) / 1e9
-    print(json.dumps({
+    rec = {
         "metric": "diffusion solve (Eq. linear system): unknown updates per second (CG iterations x unknowns / s)",
         "value": n * it / (ms * 1e-3), "unit": "unknown updates/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_solve": ms, "cg_iterations": it, "ms_per_iteration": ms_iter,
@@ -737,7 +765,10 @@ def run_diffusion(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_kind": kind, "bytes_per_iteration": bytes_iter,
                      "scope": "one FP32 CG iteration (all its kernels), averaged over the solve"},
-        "clocks": clocks.summary()}))
+        "clocks": clocks.summary()}
+    if emit:
+        print(json.dumps(rec))
+    return rec
 
 
 VARIANT_WORKLOADS = {
@@ -853,7 +884,7 @@ BATCH_WORKLOADS = {
 }
 
 
-def run_batch(args):
+def run_batch(args, emit: bool = True):
     """The batched form: every instance of the seeded recipe advanced by one
     persistent launch per step, the time loop of ``steps`` steps captured in
     one CUDA graph; launch shape from the autotuner.  Time = CUDA events
@@ -908,7 +939,7 @@ def run_batch(args):
         gm.status()
     hbm_peak, _, kind = _peaks()
     achieved = alg_bytes / (ms * 1e-3) / 1e9
-    print(json.dumps({
+    rec = {
         "metric": "traced node updates/s per batched step (1 GPU)", "value": nodes / (ms * 1e-3),
         "unit": "node updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -922,7 +953,10 @@ def run_batch(args):
                      "kernel": "k_advect_batch"},
         # per step: the batched kernel (one per element order present) and the
         # interface-copy pass
-        "gpu_launches": args.steps * (len({m.order for m in meshes}) + 1), "clocks": clocks.summary()}))
+        "gpu_launches": args.steps * (len({m.order for m in meshes}) + 1), "clocks": clocks.summary()}
+    if emit:
+        print(json.dumps(rec))
+    return rec
 
 
 ADJOINT_WORKLOADS = {
@@ -932,7 +966,7 @@ ADJOINT_WORKLOADS = {
 }
 
 
-def run_adjoint(args):
+def run_adjoint(args, emit: bool = True):
     """Gradient of a 50-step rollout (Sec. 2.3.1 step, differentiated): the
     forward steps, the recomputation inside checkpointed segments and the
     adjoint steps, for T^0 and the velocity.  One 'step' of the metric is one
@@ -973,7 +1007,7 @@ def run_adjoint(args):
     if not (torch.isfinite(gT).all() and torch.isfinite(gU).all()):
         raise RuntimeError("non-finite gradient")
     ms = ev0.elapsed_time(ev1) / (reps * steps_roll)
-    print(json.dumps({
+    rec = {
         "metric": "node updates/s of forward + adjoint per step of a checkpointed rollout (1 GPU)",
         "value": mesh.n_unique / (ms * 1e-3), "unit": "node updates/s", "n_gpus": 1,
         "steps": reps * steps_roll, "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": True,
@@ -983,7 +1017,10 @@ def run_adjoint(args):
                    "unique_nodes": mesh.n_unique, "velocity": "cellular", "cfl": 4.0, "rollout_steps": steps_roll,
                    "checkpoint_every": every, "loss": "0.5 ||T^50 - T*||^2, T* = random Fourier (seed 5)",
                    "timed": f"{reps} gradient(s) of the whole rollout, CUDA events (host launch gaps included)"},
-        "gpu_launches": None, "clocks": clocks.summary()}))
+        "gpu_launches": None, "clocks": clocks.summary()}
+    if emit:
+        print(json.dumps(rec))
+    return rec
 
 
 def main():
