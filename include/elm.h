@@ -209,16 +209,19 @@ elm_status elm_advect(elm_mesh mesh, const void* T_old_dev, void* T_new_dev, dou
  * caller whose fields live on the host (Algorithm 1, lines 3-4: the step's
  * inputs are the velocity at t_n and t_{n+1} and T^n; its result is T^{n+1}).
  * Needs a mesh created with ELM_HOST_STAGING.
- *  u_old_host, u_new_host  velocity [n, dim] (equal pointers: steady).
+ *  u_old_host, u_new_host  velocity [n, dim] (equal pointers: steady); both
+ *                          NULL: the mesh's current velocity (from
+ *                          elm_set_velocity or an earlier call) is used and
+ *                          only T moves (ELM_ERR_STATE if none is set).
  *  T_old_host, T_new_host  [n]; they may be the same buffer (in-place).
  *  dt, n_sub, stream       as for elm_advect.
- * All four must be page-locked host memory (cudaHostAlloc, cudaHostRegister
+ * The buffers given must be page-locked host memory (cudaHostAlloc, cudaHostRegister
  * or a pinned torch tensor): the call checks the first and last byte of each
  * and returns ELM_ERR_ARG for pageable memory.  Everything is enqueued
  * asynchronously; when `stream` has completed, T_new_host holds the result,
  * and until then the caller must neither change the inputs nor read or reuse
- * the output.  The velocity becomes the mesh's current velocity, as after
- * elm_set_velocity.
+ * the output.  A velocity given becomes the mesh's current velocity, as
+ * after elm_set_velocity.
  * Pipelining: consecutive calls alternate between the two staging sets, and
  * the copies run on the mesh's own streams, so the host-to-device copy of a
  * call overlaps the step of the call before it, and each quarter of the

@@ -134,19 +134,23 @@ void free_host_staging(elm_mesh_s* me) {
 extern "C" elm_status elm_advect_host(elm_mesh me, const void* u_old_host, const void* u_new_host,
                                       const void* T_old_host, void* T_new_host, double dt, int n_sub, void* stream) {
   if (!me) return fail(ELM_ERR_ARG, "elm_advect_host: null mesh");
-  if (!u_old_host || !u_new_host || !T_old_host || !T_new_host)
+  // both velocity pointers null: the mesh's current velocity stays resident
+  const bool keep_u = !u_old_host && !u_new_host;
+  if ((!keep_u && (!u_old_host || !u_new_host)) || !T_old_host || !T_new_host)
     return fail(ELM_ERR_ARG, "elm_advect_host: null buffer");
   if (!std::isfinite(dt) || dt < 0.0) return fail(ELM_ERR_ARG, "elm_advect_host: dt must be finite and >= 0");
   if (n_sub < 1 || n_sub > elm::kMaxSub)
     return fail(ELM_ERR_ARG, "elm_advect_host: n_sub must be in 1.." + std::to_string(elm::kMaxSub));
   if (me->host_only) return fail(ELM_ERR_STATE, "elm_advect_host: host-only mesh");
   if (!me->staging) return fail(ELM_ERR_STATE, "elm_advect_host: mesh was created without ELM_HOST_STAGING");
+  if (keep_u && !me->have_velocity)
+    return fail(ELM_ERR_STATE, "elm_advect_host: no velocity pointers and no velocity set on the mesh");
   const size_t es = me->precision == ELM_FP64 ? 8 : 4;
-  const size_t tb = es * size_t(me->n_storage), ub = tb * size_t(me->dim);
-  const bool steady = u_old_host == u_new_host;
+  const size_t tb = es * size_t(me->n_storage), ub = keep_u ? 0 : tb * size_t(me->dim);
+  const bool steady = keep_u ? me->steady : u_old_host == u_new_host;
   DeviceGuard g(me->device);
-  if (!page_locked(u_new_host, ub) || (!steady && !page_locked(u_old_host, ub)) || !page_locked(T_old_host, tb) ||
-      !page_locked(T_new_host, tb))
+  if ((!keep_u && (!page_locked(u_new_host, ub) || (!steady && !page_locked(u_old_host, ub)))) ||
+      !page_locked(T_old_host, tb) || !page_locked(T_new_host, tb))
     return fail(ELM_ERR_ARG, "elm_advect_host: host buffers must be page-locked (cudaHostAlloc, cudaHostRegister)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -165,14 +169,16 @@ extern "C" elm_status elm_advect_host(elm_mesh me, const void* u_old_host, const
        overlap(u_old_host, ub, H.out_ptr[o], H.out_bytes[o]) ||
        overlap(T_old_host, tb, H.out_ptr[o], H.out_bytes[o])))
     e = cudaStreamWaitEvent(H.h2d, H.ev_d2h[o], 0);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(H.u[k][1], u_new_host, ub, cudaMemcpyHostToDevice, H.h2d);
-  if (e == cudaSuccess && !steady) e = cudaMemcpyAsync(H.u[k][0], u_old_host, ub, cudaMemcpyHostToDevice, H.h2d);
+  if (e == cudaSuccess && !keep_u) e = cudaMemcpyAsync(H.u[k][1], u_new_host, ub, cudaMemcpyHostToDevice, H.h2d);
+  if (e == cudaSuccess && !keep_u && !steady)
+    e = cudaMemcpyAsync(H.u[k][0], u_old_host, ub, cudaMemcpyHostToDevice, H.h2d);
   if (e == cudaSuccess) e = cudaMemcpyAsync(H.T_old[k], T_old_host, tb, cudaMemcpyHostToDevice, H.h2d);
   if (e == cudaSuccess) e = cudaEventRecord(H.ev_h2d[k], H.h2d);
   // 2. the velocity and the step on the caller's stream
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, H.ev_h2d[k], 0);
-  if (e == cudaSuccess) e = elm::launch_pack_velocity(me->precision, me->dim, H.u[k][1], me->d_u4[1], me->n_storage, s);
-  if (e == cudaSuccess && !steady)
+  if (e == cudaSuccess && !keep_u)
+    e = elm::launch_pack_velocity(me->precision, me->dim, H.u[k][1], me->d_u4[1], me->n_storage, s);
+  if (e == cudaSuccess && !keep_u && !steady)
     e = elm::launch_pack_velocity(me->precision, me->dim, H.u[k][0], me->d_u4[0], me->n_storage, s);
   if (e != cudaSuccess) return cuda_fail(e, "elm_advect_host");
   me->steady = steady;

@@ -172,14 +172,19 @@ class Mesh:
         """The advection step with page-locked HOST tensors (storage layout):
         velocity ``u_old`` ([n, dim], at t_n) and ``u_new`` (at t_{n+1};
         None = steady), ``T_old`` and the result ``out`` ([n]; may be
-        ``T_old`` itself).  Asynchronous on ``stream``: ``out`` is valid once
-        the stream has completed.  Consecutive calls overlap their copies with
-        the previous call's step (mesh created with ``host_staging=True``)."""
-        if u_old is None:
-            raise ValueError("advect_host needs the velocity u_old")
-        u_new = u_old if u_new is None else u_new
-        for name, t, shape in (("T_old", T_old, (self.n_nodes,)), ("u_old", u_old, (self.n_nodes, self.dim)),
-                               ("u_new", u_new, (self.n_nodes, self.dim))):
+        ``T_old`` itself).  ``u_old`` None: the mesh's current velocity
+        stays resident and only T moves.  Asynchronous on ``stream``: ``out``
+        is valid once the stream has completed.  Consecutive calls overlap
+        their copies with the previous call's step (mesh created with
+        ``host_staging=True``)."""
+        if u_old is None and u_new is not None:
+            raise ValueError("advect_host: u_new without u_old")
+        if u_old is not None:
+            u_new = u_old if u_new is None else u_new
+        checks = [("T_old", T_old, (self.n_nodes,))]
+        if u_old is not None:
+            checks += [("u_old", u_old, (self.n_nodes, self.dim)), ("u_new", u_new, (self.n_nodes, self.dim))]
+        for name, t, shape in checks:
             if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or not t.is_pinned():
                 raise ValueError(f"{name} must be a contiguous, pinned {self.dtype} CPU tensor")
             if tuple(t.shape) != shape:
@@ -190,7 +195,8 @@ class Mesh:
                 or tuple(out.shape) != (self.n_nodes,):
             raise ValueError(f"out must be a contiguous, pinned {self.dtype} CPU tensor of shape ({self.n_nodes},)")
         s = stream if stream is not None else torch.cuda.current_stream()
-        check(_lib.load().elm_advect_host(self._h, ctypes.c_void_p(u_old.data_ptr()), ctypes.c_void_p(u_new.data_ptr()),
+        up = (lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else None))  # noqa: E731
+        check(_lib.load().elm_advect_host(self._h, up(u_old), up(u_new),
                                           ctypes.c_void_p(T_old.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                           float(dt), int(n_sub), ctypes.c_void_p(s.cuda_stream)))
         # the host tensors stay referenced until the stream has passed this call

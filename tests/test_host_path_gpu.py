@@ -142,3 +142,33 @@ def test_host_step_refuses_pageable_and_unstaged():
     out = gm.advect_host(T.pin_memory(), 0.1, 1, u_old=u.pin_memory())
     torch.cuda.synchronize()
     assert torch.equal(out, _device_step(gm, T, u, 0.1, 1))
+
+
+@pytest.mark.parametrize("precision,steady", [("fp32", True), ("fp64", False)])
+def test_host_step_with_resident_velocity(precision, steady):
+    """Both velocity pointers null: the mesh's current velocity stays on the
+    device and only T moves.  A time loop of such calls equals the device
+    loop bit for bit; a mesh with no velocity refuses the call."""
+    v, m = mesh_for("cube")
+    gm = elm.Mesh(v, m, 3, precision, host_staging=True)
+    u0, T = _fields(gm, seed=3)
+    u1 = None if steady else _fields(gm, seed=4)[0]
+    dt = inputs.dt_for_cfl(4.0, 3, u0.double().numpy())
+    bare = elm.Mesh(v, m, 3, precision, host_staging=True)
+    with pytest.raises(_lib.ElmError) as e:
+        bare.advect_host(T.pin_memory(), dt, 1)
+    assert e.value.status == _lib.ELM_ERR_STATE
+    # device loop
+    gm.set_velocity(u0.cuda(), None if u1 is None else u1.cuda())
+    ref = T.cuda()
+    for _ in range(3):
+        ref = gm.advect(ref, dt, 1)
+    torch.cuda.synchronize()
+    # host loop: the velocity given once, then T alone (in place)
+    Th = T.clone().pin_memory()
+    gm.advect_host(Th, dt, 1, u_old=u0.pin_memory(), u_new=None if u1 is None else u1.pin_memory(), out=Th)
+    for _ in range(2):
+        gm.advect_host(Th, dt, 1, out=Th)
+    torch.cuda.synchronize()
+    gm.status()
+    assert torch.equal(Th, ref.cpu())
