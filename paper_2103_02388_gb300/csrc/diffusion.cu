@@ -60,6 +60,7 @@
 // Dirichlet conditions: boundary unknowns keep c_bnd; CG runs on the
 // interior unknowns (search directions are zero on the boundary).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -1124,13 +1125,25 @@ int stencil_entries(int d, int p) {
   return p == 2 ? shape_total<2, 2>() : shape_total<2, 1>();
 }
 
-template <class T>
-bool upload(T** dst, const std::vector<T>& v) {
+// Replaces *dst by a device copy of `bytes` bytes at `data` (nullptr when empty).
+bool upload_bytes(void** dst, const void* data, size_t bytes) {
   cudaFree(*dst);
   *dst = nullptr;
-  if (v.empty()) return true;
-  return cudaMalloc((void**)dst, sizeof(T) * v.size()) == cudaSuccess &&
-         cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (bytes == 0) return true;
+  return cudaMalloc(dst, bytes) == cudaSuccess && cudaMemcpy(*dst, data, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+template <class T>
+bool upload(T** dst, const std::vector<T>& v) {
+  void* p = *dst;
+  const bool ok = upload_bytes(&p, v.data(), sizeof(T) * v.size());
+  *dst = static_cast<T*>(p);
+  return ok;
+}
+// A table given in FP64 into an untyped device buffer, in FP64 or rounded to FP32.
+bool upload_real(void** dst, const std::vector<double>& v, bool fp64) {
+  if (fp64) return upload_bytes(dst, v.data(), sizeof(double) * v.size());
+  const std::vector<float> f(v.begin(), v.end());
+  return upload_bytes(dst, f.data(), sizeof(float) * f.size());
 }
 
 // Lattice point (q0, q1, q2) of every slot of one macro, in storage order.
@@ -1335,6 +1348,8 @@ struct DiffusionHost {
 
 DiffusionHost diffusion_host(elm_mesh_s* me) {
   DiffusionHost h;
+  // the interior lists pack lattice coordinates into 10 bits (3D) or 16 bits
+  // (2D) each; the level limits of elm_mesh_create keep M within both
   const int d = me->dim, p = me->order, nb = n_local(d, p), np = n_perm(d);
   const size_t tab = size_t(nb) * nb * (1 + np);
   h.t64.assign(tab * me->n_macros, 0.0);
@@ -1388,6 +1403,12 @@ DiffusionHost diffusion_host(elm_mesh_s* me) {
 }  // namespace
 
 elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
+  // packed interior lattice points (10 bits per coordinate in 3D, 16 in 2D)
+  // and 32-bit slot columns; elm_mesh_create's level limits keep both
+  if ((me->dim == 3 && me->M > 1023) || me->M > 65535 || me->n_storage > int64_t(INT32_MAX) / 2) {
+    *err = "diffusion: mesh too large for the solver's 32-bit tables";
+    return ELM_ERR_ARG;
+  }
   const DiffusionHost h = diffusion_host(me);
   me->n_ditems = int64_t(h.items.size());
   me->n_drows = int64_t(h.rows.off.size()) - 1;
@@ -1401,10 +1422,7 @@ elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
     return ELM_ERR_CUDA;
   }
   const size_t es = me->precision == ELM_FP64 ? 8 : 4;
-  auto put = [&](void** dst, const std::vector<double>& v, bool fp64) {
-    if (fp64) return upload(reinterpret_cast<double**>(dst), v);
-    return upload(reinterpret_cast<float**>(dst), std::vector<float>(v.begin(), v.end()));
-  };
+  auto put = [](void** dst, const std::vector<double>& v, bool fp64) { return upload_real(dst, v, fp64); };
   const bool f64 = me->precision == ELM_FP64;
   bool ok = put(&me->d_dtab, h.t64, f64) && put(&me->d_dwtab, h.w64, f64) && put(&me->d_drow_w, rw, f64);
   if (f64)  // FP32 copies for the inner solves of the mixed-precision form
@@ -1430,7 +1448,7 @@ elm_status build_diffusion(elm_mesh_s* me, std::string* err) {
 elm_status build_diffusion_blended(elm_mesh_s* me, std::string* err) {
   std::vector<double> t;
   blended_element_tables(me, t);
-  if (!upload(reinterpret_cast<double**>(&me->d_dtab_el), t) || !build_cells_and_fold(me)) {
+  if (!upload_real(&me->d_dtab_el, t, true) || !build_cells_and_fold(me)) {
     *err = std::string("blended diffusion tables: ") + cudaGetErrorString(cudaGetLastError());
     return ELM_ERR_CUDA;
   }
