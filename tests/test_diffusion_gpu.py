@@ -130,6 +130,35 @@ def test_strang_splitting_matches_oracle_and_analytic():
     assert np.sqrt(P.om.mass_product(e)) / np.sqrt(P.om.mass_product(exact)) < 0.01
 
 
+@pytest.mark.parametrize("mesh,level,order,precision", [
+    ("triangle", 3, 2, "fp64"),   # one macro: interior stencil only, no shared-face rows
+    ("triangle", 4, 1, "fp32"),
+    ("cube", 0, 2, "fp64"),       # shared-face rows only, no interior node
+    ("cube", 1, 2, "fp32"),
+    ("square", 1, 1, "fp64"),     # a single interior unknown, on the shared diagonal
+    ("cube", 0, 1, "fp64"),       # no interior unknown at all: nothing to solve
+])
+def test_diffusion_degenerate_layouts(mesh, level, order, precision):
+    """Meshes whose operator has no shared-face rows (the interior stencil
+    completes each CG reduction), no interior stencil rows (the face rows do),
+    or no interior unknowns, against the oracle."""
+    mesh_vm = (np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]]), np.array([[0, 1, 2]])) if mesh == "triangle" else mesh
+    P = Pair(mesh_vm, level, precision, order)
+    dim = P.x.shape[1]
+    c_hat = P.rounded(_gauss(P.x, (0.4, 0.45, 0.5)[:dim], 0.3) + 0.1 * P.x[:, 0])
+    c_bnd = P.rounded(0.2 + 0.1 * P.x[:, 1])
+    tau, kappa = 0.05, 0.05
+    out, it, res = P.gm.diffusion_step(P.to_gpu(c_hat), tau, kappa, 1.0, c_bnd=P.to_gpu(c_bnd),
+                                       rtol=RTOL[precision])
+    got = P.from_gpu(out)
+    ref = P.om.diffusion_step(c_hat, tau, kappa, 1.0, c_bnd=c_bnd)
+    assert np.abs(got - ref).max() <= TOL[precision] * np.abs(ref).max()
+    if mesh == "cube" and level == 0 and order == 1:
+        assert it == 0
+    else:
+        assert it > 0 and res <= RTOL[precision]
+
+
 def test_diffusion_errors():
     v, m = inputs.unit_cube()
     plain = elm.Mesh(v, m, 2, "fp64")
