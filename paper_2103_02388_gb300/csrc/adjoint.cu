@@ -28,6 +28,7 @@
 // atomics.
 #include <cstdint>
 
+#include "scaled_round.cuh"
 #include "tracer.cuh"
 
 namespace elm {
@@ -38,14 +39,14 @@ constexpr int kSumBits = 61;   // |sum of a slot| < 2^61 (64-bit accumulators)
 struct AdjArgs {
   const void* gT_new;
   unsigned long long* acc_T;   // [n] int64
-  unsigned long long* acc_U;   // [nsets][n][dim] int64
+  unsigned long long* acc_U;   // [nsets][dim][n] int64 (component-major)
   // per slot statistics and scales: T slots [0, n), velocity slots
   // [n + set n, n + (set + 1) n)
   unsigned long long* smax;    // largest |contribution| (value bits)
   unsigned long long* scnt;    // number of contributions
   const int* kexp;             // scale exponent k_j
   int split;                   // u_old and u_new gradients kept apart
-  int pass;                    // 0: statistics, 1: accumulate
+  int pass;                    // 0: statistics, 1: accumulate (selects the kernel)
 };
 
 template <class R>
@@ -71,7 +72,9 @@ __device__ __forceinline__ int scale_exponent(double m, unsigned long long cnt) 
   return kSumBits - b - e;
 }
 
-template <int D, class R, bool STEADY, int P>
+// PASS 0 gathers the slot statistics, PASS 1 the scaled sums: a kernel per
+// pass, so that each carries only its own accumulation code.
+template <int D, class R, bool STEADY, int P, int PASS>
 struct Adjoint {
   using Tr = Tracer<D, R, STEADY, P>;
   static constexpr int NB = Tr::NB;
@@ -92,16 +95,25 @@ struct Adjoint {
     }
   }
 
+  // round(c 2^k) as a 64-bit integer: by integer shifts in FP32 (no FP64
+  // conversion; the same integer, scaled_round.cuh), llrint in FP64.
+  static __device__ __forceinline__ long long to_fixed(R c, int k) {
+    if constexpr (sizeof(R) == 4)
+      return scaled_round(c, k);
+    else
+      return llrint(ldexp(c, k));
+  }
+
   // Contribution c to dL/dT^n at slot: its statistics (pass 0) or its scaled
   // integer (pass 1).  Zero contributions are skipped in both passes.
   __device__ void addT(int slot, R c) {
     if (c == R(0)) return;
-    if (A.pass == 0) {
+    if constexpr (PASS == 0) {
       atomicMax(A.smax + slot, Bits<R>::of(c));
       atomicAdd(A.scnt + slot, 1ull);
       return;
     }
-    const long long q = llrint(ldexp(double(c), A.kexp[slot]));
+    const long long q = to_fixed(c, A.kexp[slot]);
     atomicAdd(A.acc_T + slot, (unsigned long long)q);
   }
   // Contribution v[0..D) to the velocity gradient of set `set` at slot: one
@@ -109,7 +121,7 @@ struct Adjoint {
   // puts NaN above every number) and one scale for the slot's components.
   __device__ void addU(int set, int slot, const R* v) {
     const int64_t st = int64_t(n_storage) * (1 + set) + slot;
-    if (A.pass == 0) {
+    if constexpr (PASS == 0) {
       unsigned long long mb = 0ull;
 #pragma unroll
       for (int r = 0; r < D; ++r) mb = max(mb, Bits<R>::of(v[r]));
@@ -122,8 +134,8 @@ struct Adjoint {
 #pragma unroll
     for (int r = 0; r < D; ++r)
       if (v[r] != R(0))
-        atomicAdd(A.acc_U + (int64_t(set) * n_storage + slot) * D + r,
-                  (unsigned long long)llrint(ldexp(double(v[r]), k)));
+        atomicAdd(A.acc_U + (int64_t(set) * D + r) * n_storage + slot,
+                  (unsigned long long)to_fixed(v[r], k));
   }
 
   // P1 / P2 stencil with barycentrics L and the axis of each sorted fraction.
@@ -253,13 +265,12 @@ struct Adjoint {
       hv[j] = v;
     }
     grad_x(hv, L, ax, az);
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
+    auto scatter = [&](int sl, R ph) {
       R pa[D];
 #pragma unroll
-      for (int r = 0; r < D; ++r) pa[r] = phi[j] * ak[r];
+      for (int r = 0; r < D; ++r) pa[r] = ph * ak[r];
       if (STEADY || !A.split) {
-        addU(0, slot[j], pa);
+        addU(0, sl, pa);
       } else {
         R po[D], pn[D];
 #pragma unroll
@@ -267,9 +278,19 @@ struct Adjoint {
           po[r] = w_old * pa[r];
           pn[r] = w_new * pa[r];
         }
-        addU(0, slot[j], po);
-        addU(1, slot[j], pn);
+        addU(0, sl, po);
+        addU(1, sl, pn);
       }
+    };
+    // The scatter of the summing pass (conversions and atomics for every
+    // component) and every FP64 scatter run as a loop, for code size; the
+    // FP32 statistics pass keeps it unrolled (measured faster).
+    if constexpr (PASS == 1 || sizeof(R) == 8) {
+#pragma unroll 1
+      for (int j = 0; j < NB; ++j) scatter(slot[j], phi[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < NB; ++j) scatter(slot[j], phi[j]);
     }
   }
 
@@ -305,28 +326,42 @@ struct Adjoint {
       for (int q = 0; q < D; ++q) d[q] = R(0);
       forward(d, 0, jj);
       const R back = to_real<R>(jj) * h;
-      // forward substep jj, keeping its stage points, values and clamps
+      // forward substep jj, keeping its stage points, values and clamps.
+      // The stage loops here are not unrolled: one inlined copy of the
+      // velocity evaluation and of its adjoint instead of four keeps the
+      // kernel's code small enough for the instruction cache (instruction
+      // fetch was the largest stall of the unrolled form); the stage arrays
+      // go to the stack frame.
       R z[4][D], k[4][D], acc[D];
       unsigned mz[4] = {0u, 0u, 0u, 0u}, md = 0u;
+#pragma unroll 1
+      for (int s = 0; s < 4; ++s) {
+        const R off = s == 3 ? h : h2;
+        R zs[D], ks[D];
+        unsigned m = 0u;
+        if (s == 0) {
 #pragma unroll
-      for (int q = 0; q < D; ++q) z[0][q] = d[q];
-      if (jj == 0) {
-        R un[D];
-        Tr::load_rec(t.un, home_slot, un);
+          for (int q = 0; q < D; ++q) zs[q] = d[q];
+        } else {
 #pragma unroll
-        for (int q = 0; q < D; ++q) k[0][q] = un[q];
-      } else {
-        t.velocity(z[0], back, k[0]);
+          for (int q = 0; q < D; ++q) zs[q] = d[q] - off * k[s - 1][q];
+          clamp_mask(zs, m);
+        }
+        if (s == 0 && jj == 0)
+          Tr::load_rec(t.un, home_slot, ks);
+        else
+          t.velocity(zs, s == 0 ? back : back + off, ks);
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          z[s][q] = zs[q];
+          k[s][q] = ks[q];
+        }
+        mz[s] = m;
       }
 #pragma unroll
       for (int q = 0; q < D; ++q) acc[q] = k[0][q];
 #pragma unroll
       for (int s = 1; s < 4; ++s) {
-        const R off = s == 3 ? h : h2;
-#pragma unroll
-        for (int q = 0; q < D; ++q) z[s][q] = d[q] - off * k[s - 1][q];
-        clamp_mask(z[s], mz[s]);
-        t.velocity(z[s], back + off, k[s]);
         const R w = s == 3 ? R(1) : R(2);
 #pragma unroll
         for (int q = 0; q < D; ++q) acc[q] = r_fma(w, k[s][q], acc[q]);
@@ -348,26 +383,32 @@ struct Adjoint {
         ak[2][q] = R(-2) * h6 * ap;
         ak[3][q] = -h6 * ap;
       }
+#pragma unroll 1
+      for (int s = 3; s >= 0; --s) {
+        R as[D];
 #pragma unroll
-      for (int s = 3; s >= 1; --s) {
-        const R off = s == 3 ? h : h2;
-        R az[D];
-        velocity_adjoint(z[s], back + off, ak[s], az);
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-          const R v = (mz[s] >> q) & 1u ? R(0) : az[q];
-          ad[q] += v;                 // z_s = d - off k_{s-1}
-          ak[s - 1][q] -= off * v;
+        for (int q = 0; q < D; ++q) as[q] = ak[s][q];
+        if (s == 0 && jj == 0) {
+          // first stage: the nodal value of u^{n+1} (weight 1 at t_{n+1})
+          addU(STEADY || !A.split ? 0 : 1, home_slot, as);
+          break;
         }
-      }
-      if (jj == 0) {
-        // first stage: the nodal value of u^{n+1} (weight 1 at t_{n+1})
-        addU(STEADY || !A.split ? 0 : 1, home_slot, ak[0]);
-      } else {
-        R az[D];
-        velocity_adjoint(z[0], back, ak[0], az);
+        const R off = s == 3 ? h : h2;
+        R zs[D], az[D];
 #pragma unroll
-        for (int q = 0; q < D; ++q) ad[q] += az[q];
+        for (int q = 0; q < D; ++q) zs[q] = z[s][q];
+        velocity_adjoint(zs, s == 0 ? back : back + off, as, az);
+        if (s > 0) {
+#pragma unroll
+          for (int q = 0; q < D; ++q) {
+            const R v = (mz[s] >> q) & 1u ? R(0) : az[q];
+            ad[q] += v;                 // z_s = d - off k_{s-1}
+            ak[s - 1][q] -= off * v;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < D; ++q) ad[q] += az[q];
+        }
       }
 #pragma unroll
       for (int q = 0; q < D; ++q) a[q] = ad[q];
@@ -375,14 +416,14 @@ struct Adjoint {
   }
 };
 
-template <int D, class R, bool STEADY, int P>
+template <int D, class R, bool STEADY, int P, int PASS>
 __global__ void __launch_bounds__(kAdvectThreads)
     k_adjoint(AdvectArgs args, AdjArgs aa, Tables<R> tab, int chunk0) {
   const int4 ck = args.chunks[chunk0 + int(blockIdx.x)];
   if (int(threadIdx.x) >= ck.w) return;
   const StepConsts<R>& K = consts<R>(args);
   const int npm = int(args.npm);
-  Adjoint<D, R, STEADY, P> ad;
+  Adjoint<D, R, STEADY, P, PASS> ad;
   Tracer<D, R, STEADY, P>& t = ad.t;
   t.geo = args.geo;
   t.tab = tab;
@@ -485,31 +526,41 @@ __global__ void k_fold_ghosts(unsigned long long* acc, int ncomp, int nsets, int
   if (o == s) return;
   for (int set = 0; set < nsets; ++set)
     for (int c = 0; c < ncomp; ++c) {
-      unsigned long long* src = acc + (set * n + s) * ncomp + c;
+      unsigned long long* src = acc + (int64_t(set) * ncomp + c) * n + s;
       const unsigned long long v = *src;
       if (v) {
-        atomicAdd(acc + (set * n + o) * ncomp + c, v);
+        atomicAdd(acc + (int64_t(set) * ncomp + c) * n + o, v);
         *src = 0ull;
       }
     }
 }
 
-// out = acc 2^-k, k the slot's scale exponent (shared by the ncomp
-// components of a slot).
+// out[s ncomp + c] = acc[c n + s] 2^-k_s: component-major sums back to the
+// caller's interleaved layout (ncomp = 1 for the temperature), k_s the
+// slot's scale exponent (shared by its components).
 template <class R>
-__global__ void k_scale_out(const unsigned long long* __restrict__ acc, R* __restrict__ out, int64_t count,
+__global__ void k_scale_out(const unsigned long long* __restrict__ acc, R* __restrict__ out, int64_t n,
                             int ncomp, const int* __restrict__ kexp) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= count) return;
-  out[i] = R(ldexp(double((long long)acc[i]), -kexp[i / ncomp]));
+  if (i >= n * ncomp) return;
+  const int64_t sl = i / ncomp;
+  const int c = int(i - sl * ncomp);
+  out[i] = R(ldexp(double((long long)acc[c * n + sl]), -kexp[sl]));
 }
 
 template <int D, class R, bool STEADY>
 cudaError_t launch_adj_drs(const AdvectArgs& a, const AdjArgs& aa, Tables<R> t, cudaStream_t s) {
-  if (a.order == 1)
-    k_adjoint<D, R, STEADY, 1><<<a.n_chunks, kAdvectThreads, 0, s>>>(a, aa, t, 0);
-  else
-    k_adjoint<D, R, STEADY, 2><<<a.n_chunks, kAdvectThreads, 0, s>>>(a, aa, t, 0);
+  if (a.order == 1) {
+    if (aa.pass == 0)
+      k_adjoint<D, R, STEADY, 1, 0><<<a.n_chunks, kAdvectThreads, 0, s>>>(a, aa, t, 0);
+    else
+      k_adjoint<D, R, STEADY, 1, 1><<<a.n_chunks, kAdvectThreads, 0, s>>>(a, aa, t, 0);
+  } else {
+    if (aa.pass == 0)
+      k_adjoint<D, R, STEADY, 2, 0><<<a.n_chunks, kAdvectThreads, 0, s>>>(a, aa, t, 0);
+    else
+      k_adjoint<D, R, STEADY, 2, 1><<<a.n_chunks, kAdvectThreads, 0, s>>>(a, aa, t, 0);
+  }
   return cudaGetLastError();
 }
 
@@ -564,15 +615,15 @@ cudaError_t launch_adjoint(int dim, int precision, const AdvectArgs& a, const Ad
   const unsigned ub = unsigned((n * dim + 255) / 256);
   if (precision == ELM_FP64) {
     k_scale_out<double><<<tb, 256, 0, s>>>(b.acc_T, static_cast<double*>(gT_old), n, 1, b.kexp);
-    k_scale_out<double><<<ub, 256, 0, s>>>(b.acc_U, static_cast<double*>(gU_old), n * dim, dim, b.kexp + n);
+    k_scale_out<double><<<ub, 256, 0, s>>>(b.acc_U, static_cast<double*>(gU_old), n, dim, b.kexp + n);
     if (nsets == 2)
-      k_scale_out<double><<<ub, 256, 0, s>>>(b.acc_U + n * dim, static_cast<double*>(gU_new), n * dim, dim,
+      k_scale_out<double><<<ub, 256, 0, s>>>(b.acc_U + n * dim, static_cast<double*>(gU_new), n, dim,
                                              b.kexp + 2 * n);
   } else {
     k_scale_out<float><<<tb, 256, 0, s>>>(b.acc_T, static_cast<float*>(gT_old), n, 1, b.kexp);
-    k_scale_out<float><<<ub, 256, 0, s>>>(b.acc_U, static_cast<float*>(gU_old), n * dim, dim, b.kexp + n);
+    k_scale_out<float><<<ub, 256, 0, s>>>(b.acc_U, static_cast<float*>(gU_old), n, dim, b.kexp + n);
     if (nsets == 2)
-      k_scale_out<float><<<ub, 256, 0, s>>>(b.acc_U + n * dim, static_cast<float*>(gU_new), n * dim, dim,
+      k_scale_out<float><<<ub, 256, 0, s>>>(b.acc_U + n * dim, static_cast<float*>(gU_new), n, dim,
                                             b.kexp + 2 * n);
   }
   return cudaGetLastError();

@@ -340,7 +340,7 @@ struct BatchParams {
 // Scratch of the adjoint (allocated at mesh creation with ELM_ADJOINT).
 struct AdjointBuffers {
   unsigned long long* acc_T;    // [n] 64-bit fixed-point sums
-  unsigned long long* acc_U;    // [2][n][dim]
+  unsigned long long* acc_U;    // [2][dim][n] (component-major)
   unsigned long long* smax;     // [3 n] per slot: largest |contribution| (value bits); T, then 2 velocity sets
   unsigned long long* scnt;     // [3 n] per slot: number of contributions
   int* kexp;                    // [3 n] per slot: scale exponent
