@@ -294,89 +294,111 @@ struct Adjoint {
     }
   }
 
+  // Stage points z_s of one substep and the coordinates its clamps fixed
+  // (mz[s] for z_s, md for the end point).
+  struct Stages {
+    R z[4][D];
+    unsigned mz[4], md;
+  };
+
+  // Forward substep j from offset d, keeping its stage points and clamps; d
+  // becomes the substep's end point (the same arithmetic as forward()).
+  // The stage loop is not unrolled: one inlined copy of the velocity
+  // evaluation instead of four keeps the kernel's code small enough for the
+  // instruction cache (instruction fetch was the largest stall of the
+  // unrolled form); the stage arrays go to the stack frame.
+  // Keep a single call site: with two inlined copies of this rolled loop in
+  // run() the compiled kernels (nvcc 13.0, sm_103a, at every ptxas
+  // optimisation level and with FMA contraction off) computed wrong velocity
+  // gradients, although the two source forms are equivalent; with one copy,
+  // or the first copy unrolled, they pass every parity test.
+  __device__ void substep(R* d, int j, Stages& st) {
+    const R back = to_real<R>(j) * h;
+    R k[4][D], acc[D];
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) {
+      const R off = s == 3 ? h : h2;
+      R zs[D], ks[D];
+      unsigned m = 0u;
+      if (s == 0) {
+#pragma unroll
+        for (int q = 0; q < D; ++q) zs[q] = d[q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < D; ++q) zs[q] = d[q] - off * k[s - 1][q];
+        clamp_mask(zs, m);
+      }
+      if (s == 0 && j == 0)
+        Tr::load_rec(t.un, home_slot, ks);
+      else
+        t.velocity(zs, s == 0 ? back : back + off, ks);
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        st.z[s][q] = zs[q];
+        k[s][q] = ks[q];
+      }
+      st.mz[s] = m;
+    }
+#pragma unroll
+    for (int q = 0; q < D; ++q) acc[q] = k[0][q];
+#pragma unroll
+    for (int s = 1; s < 4; ++s) {
+      const R w = s == 3 ? R(1) : R(2);
+#pragma unroll
+      for (int q = 0; q < D; ++q) acc[q] = r_fma(w, k[s][q], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < D; ++q) d[q] = d[q] - h6 * acc[q];
+    clamp_mask(d, st.md);
+  }
+
   __device__ void run(R g) {
-    // forward to the departure point
+    // forward to the start of the last substep; the reverse loop below runs
+    // each substep's stages once (the last one also gives the departure point)
     R X[D];
 #pragma unroll
     for (int q = 0; q < D; ++q) X[q] = R(0);
-    forward(X, 0, n_sub);
-    // (iii) T^{n+1} = T_h(X): transpose interpolation and a_X = g grad T_h(X)
+    forward(X, 0, n_sub - 1);
+    Stages st;
     R a[D];
-    {
-      R c[D], f[D];
-      t.locate(X, c, f);
-      int slot[NB];
-      R phi[NB], L[D + 1];
-      int ax[D];
-      stencil_ad(c, f, slot, phi, L, ax);
-      R hv[NB];
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        hv[j] = __ldg(t.T + slot[j]);
-        addT(slot[j], phi[j] * g);
-      }
-      grad_x(hv, L, ax, a);
-#pragma unroll
-      for (int q = 0; q < D; ++q) a[q] *= g;
-    }
-    // (ii) reverse through the substeps, last first
+    // (ii) reverse through the substeps, last first; substep jj < n_sub - 1
+    // is replayed from the start node, and the last one is run only here
+    // (not also in the forward pass above)
     for (int jj = n_sub - 1; jj >= 0; --jj) {
       R d[D];
+      if (jj == n_sub - 1) {
 #pragma unroll
-      for (int q = 0; q < D; ++q) d[q] = R(0);
-      forward(d, 0, jj);
+        for (int q = 0; q < D; ++q) d[q] = X[q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < D; ++q) d[q] = R(0);
+        forward(d, 0, jj);
+      }
+      substep(d, jj, st);
+      if (jj == n_sub - 1) {
+        // (iii) T^{n+1} = T_h(X): transpose interpolation and a_X = g grad T_h(X)
+        R c[D], f[D];
+        t.locate(d, c, f);
+        int slot[NB];
+        R phi[NB], L[D + 1];
+        int ax[D];
+        stencil_ad(c, f, slot, phi, L, ax);
+        R hv[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          hv[j] = __ldg(t.T + slot[j]);
+          addT(slot[j], phi[j] * g);
+        }
+        grad_x(hv, L, ax, a);
+#pragma unroll
+        for (int q = 0; q < D; ++q) a[q] *= g;
+      }
       const R back = to_real<R>(jj) * h;
-      // forward substep jj, keeping its stage points, values and clamps.
-      // The stage loops here are not unrolled: one inlined copy of the
-      // velocity evaluation and of its adjoint instead of four keeps the
-      // kernel's code small enough for the instruction cache (instruction
-      // fetch was the largest stall of the unrolled form); the stage arrays
-      // go to the stack frame.
-      R z[4][D], k[4][D], acc[D];
-      unsigned mz[4] = {0u, 0u, 0u, 0u}, md = 0u;
-#pragma unroll 1
-      for (int s = 0; s < 4; ++s) {
-        const R off = s == 3 ? h : h2;
-        R zs[D], ks[D];
-        unsigned m = 0u;
-        if (s == 0) {
-#pragma unroll
-          for (int q = 0; q < D; ++q) zs[q] = d[q];
-        } else {
-#pragma unroll
-          for (int q = 0; q < D; ++q) zs[q] = d[q] - off * k[s - 1][q];
-          clamp_mask(zs, m);
-        }
-        if (s == 0 && jj == 0)
-          Tr::load_rec(t.un, home_slot, ks);
-        else
-          t.velocity(zs, s == 0 ? back : back + off, ks);
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-          z[s][q] = zs[q];
-          k[s][q] = ks[q];
-        }
-        mz[s] = m;
-      }
-#pragma unroll
-      for (int q = 0; q < D; ++q) acc[q] = k[0][q];
-#pragma unroll
-      for (int s = 1; s < 4; ++s) {
-        const R w = s == 3 ? R(1) : R(2);
-#pragma unroll
-        for (int q = 0; q < D; ++q) acc[q] = r_fma(w, k[s][q], acc[q]);
-      }
-      {
-        R dn[D];
-#pragma unroll
-        for (int q = 0; q < D; ++q) dn[q] = d[q] - h6 * acc[q];
-        clamp_mask(dn, md);
-      }
       // reverse: d_end = clamp(d - h/6 (k0 + 2 k1 + 2 k2 + k3))
       R ak[4][D], ad[D];
 #pragma unroll
       for (int q = 0; q < D; ++q) {
-        const R ap = (md >> q) & 1u ? R(0) : a[q];
+        const R ap = (st.md >> q) & 1u ? R(0) : a[q];
         ad[q] = ap;
         ak[0][q] = -h6 * ap;
         ak[1][q] = R(-2) * h6 * ap;
@@ -396,12 +418,12 @@ struct Adjoint {
         const R off = s == 3 ? h : h2;
         R zs[D], az[D];
 #pragma unroll
-        for (int q = 0; q < D; ++q) zs[q] = z[s][q];
+        for (int q = 0; q < D; ++q) zs[q] = st.z[s][q];
         velocity_adjoint(zs, s == 0 ? back : back + off, as, az);
         if (s > 0) {
 #pragma unroll
           for (int q = 0; q < D; ++q) {
-            const R v = (mz[s] >> q) & 1u ? R(0) : az[q];
+            const R v = (st.mz[s] >> q) & 1u ? R(0) : az[q];
             ad[q] += v;                 // z_s = d - off k_{s-1}
             ak[s - 1][q] -= off * v;
           }
