@@ -6,8 +6,9 @@
 //   dL/du_j    = sum_i g_i grad T^n_h(X_i) . dX_i/du_j  (reverse mode through
 //                the backward RK4 stages, the P1 / P2 velocity evaluations, the
 //                time interpolation and the box clamps)
-// Each node i recomputes its forward trace (a substep is replayed from the
-// start for every substep it reverses, so no trace is stored), then runs
+// Each node i recomputes its forward trace (substep j is replayed from the
+// start when it is reversed, so no trace is stored; the last substep is run
+// once and gives both the departure point and its reverse stages), then runs
 // reverse mode: a stage k_s = u~(z_s) sends phi_j(z_s) a_k to node j's
 // velocity and J_u(z_s)^T a_k back to z_s, where J_u is the gradient of the
 // P1 / P2 interpolant; a clamped coordinate passes no derivative.
