@@ -64,11 +64,17 @@ struct Bits<double> {
 };
 
 // Scale exponent of a slot whose contributions number cnt with largest
-// magnitude m: cnt m 2^k < 2^kSumBits (m < 2^e, cnt <= 2^b).
-__device__ __forceinline__ int scale_exponent(double m, unsigned long long cnt) {
-  if (cnt == 0ull || !(m > 0.0) || !isfinite(m)) return 0;
+// magnitude m: cnt m 2^k < 2^kSumBits (m < 2^e, cnt <= 2^b).  e from frexpf
+// for an FP32 m (the same exponent as of its exact double, without the FP64
+// pipe), from frexp for an FP64 one.
+template <class R>
+__device__ __forceinline__ int scale_exponent(R m, unsigned long long cnt) {
+  if (cnt == 0ull || !(m > R(0)) || !isfinite(m)) return 0;
   int e;
-  frexp(m, &e);  // m < 2^e
+  if constexpr (sizeof(R) == 4)
+    frexpf(m, &e);  // m < 2^e
+  else
+    frexp(m, &e);
   const int b = cnt <= 1ull ? 0 : 64 - __clzll((long long)(cnt - 1ull));
   return kSumBits - b - e;
 }
@@ -535,9 +541,9 @@ __global__ void k_scales(const unsigned long long* __restrict__ smax, const unsi
                          int* kexp, int64_t count, unsigned* status) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= count) return;
-  const double m = double(Bits<R>::from(smax[i]));
+  const R m = Bits<R>::from(smax[i]);
   if (scnt[i] != 0ull && !isfinite(m)) atomicOr(status, kFlagNonFinite);
-  kexp[i] = scale_exponent(m, scnt[i]);
+  kexp[i] = scale_exponent<R>(m, scnt[i]);
 }
 
 // Ghost copies of a node hand their sums to the owner slot.
@@ -560,7 +566,9 @@ __global__ void k_fold_ghosts(unsigned long long* acc, int ncomp, int nsets, int
 
 // out[s ncomp + c] = acc[c n + s] 2^-k_s: component-major sums back to the
 // caller's interleaved layout (ncomp = 1 for the temperature), k_s the
-// slot's scale exponent (shared by its components).
+// slot's scale exponent (shared by its components).  FP32: one correctly
+// rounded conversion of the 64-bit sum, then an exact scaling (no FP64
+// pipe); FP64: the same in double.
 template <class R>
 __global__ void k_scale_out(const unsigned long long* __restrict__ acc, R* __restrict__ out, int64_t n,
                             int ncomp, const int* __restrict__ kexp) {
@@ -568,7 +576,11 @@ __global__ void k_scale_out(const unsigned long long* __restrict__ acc, R* __res
   if (i >= n * ncomp) return;
   const int64_t sl = i / ncomp;
   const int c = int(i - sl * ncomp);
-  out[i] = R(ldexp(double((long long)acc[c * n + sl]), -kexp[sl]));
+  const long long v = (long long)acc[c * n + sl];
+  if constexpr (sizeof(R) == 4)
+    out[i] = ldexpf(__ll2float_rn(v), -kexp[sl]);
+  else
+    out[i] = ldexp(double(v), -kexp[sl]);
 }
 
 template <int D, class R, bool STEADY>
