@@ -1,0 +1,188 @@
+// kernel_host_check.cpp -- the advection kernel's device code (csrc/tracer.cuh,
+// advect_node) compiled with g++ and run on the CPU, one node at a time, for a
+// CPU parity check against the oracle (tests/test_kernel_host.py) under
+// AddressSanitizer and UndefinedBehaviorSanitizer.  No GPU.
+//
+// It mirrors k_advect: every entry of the host-built work list (a run of up to
+// 128 nodes of one slab of one macro) is handed to advect_node with the same
+// tables, step constants and packed velocity records the GPU path uses, each
+// interface node is computed once in its owner's slot, and the interface
+// copies are then filled from it (k_ghost_copy).
+//
+// Input file (little-endian, as numpy writes it): int64 header [dim,
+// n_vertices, n_macros, level, precision (0: FP64, 1: FP32), order, steady,
+// n_sub], double dt, vertex coordinates [n_vertices * dim], macro vertices
+// [n_macros * (dim + 1)] (int64), then in the mesh's storage layout u^n and
+// u^{n+1} [n_storage * dim] and T^n [n_storage] (doubles, already rounded to
+// FP32 for an FP32 run).  Output file: T^{n+1} [n_storage] (doubles).
+// Exit status: 0, 1 on bad input, 2 on a device-side status flag.
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "tracer.cuh"
+
+using namespace elm;
+
+namespace {
+
+struct HostTables {
+  std::vector<int64_t> owner_mp;
+  std::vector<int4> chunks;
+  std::vector<MacroGeo32> geo32;
+  std::vector<int2> ghosts;
+};
+
+// The tables the library uploads at mesh creation, built here from the
+// host-only mesh in the same way.
+HostTables host_tables(const elm_mesh_s* me) {
+  HostTables h;
+  const int d = me->dim, M = me->M;
+  std::vector<int64_t> slot_p(size_t(me->npm));
+  int64_t k = 0;
+  if (d == 2) {
+    for (int p1 = 0; p1 <= M; ++p1)
+      for (int p2 = 0; p2 <= p1; ++p2) slot_p[size_t(k++)] = pack_owner(0, p1, p2, 0);
+  } else {
+    for (int p1 = 0; p1 <= M; ++p1)
+      for (int p2 = 0; p2 <= p1; ++p2)
+        for (int p3 = 0; p3 <= p2; ++p3) slot_p[size_t(k++)] = pack_owner(0, p1, p2, p3);
+  }
+  h.owner_mp.resize(size_t(me->n_unique));
+  for (int64_t u = 0; u < me->n_unique; ++u) {
+    const int64_t m = me->owner[size_t(u)] / me->npm;
+    h.owner_mp[size_t(u)] = pack_owner(m, 0, 0, 0) | slot_p[size_t(me->owner[size_t(u)] - m * me->npm)];
+  }
+  for (int64_t m = 0; m < me->n_macros; ++m)
+    for (int p1 = 0; p1 <= M; ++p1) {
+      const int len = d == 3 ? (p1 + 1) * (p1 + 2) / 2 : p1 + 1;
+      for (int i0 = 0; i0 < len; i0 += kAdvectThreads)
+        h.chunks.push_back(make_int4(int(m), p1, i0, len - i0 < kAdvectThreads ? len - i0 : kAdvectThreads));
+    }
+  for (int64_t s = 0; s < me->n_storage; ++s) {
+    const int64_t o = me->owner[size_t(me->unique_map[size_t(s)])];
+    if (o != s) h.ghosts.push_back(make_int2(int(s), int(o)));
+  }
+  h.geo32.resize(size_t(me->n_macros));
+  auto split = [](double x, float* hi, float* lo) {
+    *hi = float(x);
+    *lo = float(x - double(*hi));
+  };
+  for (int64_t m = 0; m < me->n_macros; ++m) {
+    const MacroGeo& g = me->geo[size_t(m)];
+    MacroGeo32& g32 = h.geo32[size_t(m)];
+    for (int q = 0; q < 9; ++q) {
+      split(g.NJinv[q], &g32.NJinv[q], &g32.NJinv_lo[q]);
+      split(g.J[q], &g32.J[q], &g32.J_lo[q]);
+    }
+    for (int q = 0; q < 3; ++q) split(g.v0[q], &g32.v0[q], &g32.v0_lo[q]);
+    for (int q = 0; q < 4; ++q) g32.nb[q] = g.nb[q];
+    g32.x = g.x;
+  }
+  return h;
+}
+
+template <class R>
+StepConsts<R> step_consts(const elm_mesh_s* me, double dt, int n_sub) {
+  const double h = dt / n_sub;
+  StepConsts<R> K{R(h), R(0.5 * h), R(h / 6.0), R(dt), R(1.0 / me->M), R(me->N), {0, 0, 0}, {0, 0, 0}};
+  for (int r = 0; r < 3; ++r) {
+    K.lo[r] = R(me->lo[r]);
+    K.hi[r] = R(me->hi[r]);
+  }
+  return K;
+}
+
+template <int D, class R, bool STEADY, int P>
+unsigned step(const elm_mesh_s* me, const HostTables& h, const std::vector<double>& uo_in,
+              const std::vector<double>& un_in, const std::vector<double>& T_in, double dt, int n_sub,
+              std::vector<double>& T_out) {
+  const int64_t n = me->n_storage;
+  const size_t ns = static_cast<size_t>(n);
+  std::vector<R> un(ns * 4, R(0)), uo(ns * 4, R(0)), T(ns, R(0)), Tn(ns, R(0));
+  for (int64_t s = 0; s < n; ++s) {
+    for (int r = 0; r < D; ++r) {
+      un[size_t(s) * 4 + r] = R(un_in[size_t(s) * D + r]);
+      uo[size_t(s) * 4 + r] = R(uo_in[size_t(s) * D + r]);
+    }
+    T[size_t(s)] = R(T_in[size_t(s)]);
+  }
+  unsigned status = 0;
+  NodeJob<R> job{me->geo.data(), un.data(), STEADY ? un.data() : uo.data(), T.data(), Tn.data(), &status,
+                 me->unique_map.data(), h.owner_mp.data(), step_consts<R>(me, dt, n_sub), me->N,
+                 int(me->npm), n_sub};
+  job.skip_ghosts = 1;
+  Tables<R> tab;
+  if constexpr (sizeof(R) == 8)
+    tab.g = me->geo.data();
+  else
+    tab.g = h.geo32.data();
+  for (const int4& ck : h.chunks)
+    for (int tid = 0; tid < ck.w; ++tid) advect_node<D, R, STEADY, P, kStep, 0>(job, tab, ck, tid);
+  for (const int2& g : h.ghosts) Tn[size_t(g.x)] = Tn[size_t(g.y)];
+  T_out.assign(Tn.begin(), Tn.end());
+  return status;
+}
+
+template <int D, class R>
+unsigned dispatch(const elm_mesh_s* me, const HostTables& h, bool steady, const std::vector<double>& uo,
+                  const std::vector<double>& un, const std::vector<double>& T, double dt, int n_sub,
+                  std::vector<double>& out) {
+  if (me->order == 1)
+    return steady ? step<D, R, true, 1>(me, h, uo, un, T, dt, n_sub, out)
+                  : step<D, R, false, 1>(me, h, uo, un, T, dt, n_sub, out);
+  return steady ? step<D, R, true, 2>(me, h, uo, un, T, dt, n_sub, out)
+                : step<D, R, false, 2>(me, h, uo, un, T, dt, n_sub, out);
+}
+
+template <class T>
+bool read_n(FILE* f, std::vector<T>& v, size_t n) {
+  v.resize(n);
+  return n == 0 || std::fread(v.data(), sizeof(T), n, f) == n;
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+  if (argc != 3) {
+    std::fprintf(stderr, "usage: %s input output\n", argv[0]);
+    return 1;
+  }
+  FILE* f = std::fopen(argv[1], "rb");
+  if (!f) return 1;
+  std::vector<int64_t> hd;
+  std::vector<double> dtv;
+  if (!read_n(f, hd, 8) || !read_n(f, dtv, 1)) return 1;
+  const int dim = int(hd[0]), precision = int(hd[4]), order = int(hd[5]), n_sub = int(hd[7]);
+  const bool steady = hd[6] != 0;
+  std::vector<double> V;
+  std::vector<int64_t> Mc;
+  if (!read_n(f, V, size_t(hd[1] * dim)) || !read_n(f, Mc, size_t(hd[2] * (dim + 1)))) return 1;
+  elm_mesh mesh = nullptr;
+  const int prec = (precision == 0 ? ELM_FP64 : ELM_FP32) | ELM_HOST_ONLY | (order == 1 ? ELM_P1 : 0);
+  if (elm_mesh_create(dim, hd[1], V.data(), hd[2], Mc.data(), int(hd[3]), prec, &mesh) != ELM_OK) {
+    std::fprintf(stderr, "mesh: %s\n", elm_last_error());
+    return 1;
+  }
+  const int64_t n = mesh->n_storage;
+  std::vector<double> uo, un, T, out;
+  if (!read_n(f, uo, size_t(n * dim)) || !read_n(f, un, size_t(n * dim)) || !read_n(f, T, size_t(n))) return 1;
+  std::fclose(f);
+  const HostTables h = host_tables(mesh);
+  unsigned status;
+  if (dim == 3)
+    status = precision == 0 ? dispatch<3, double>(mesh, h, steady, uo, un, T, dtv[0], n_sub, out)
+                            : dispatch<3, float>(mesh, h, steady, uo, un, T, dtv[0], n_sub, out);
+  else
+    status = precision == 0 ? dispatch<2, double>(mesh, h, steady, uo, un, T, dtv[0], n_sub, out)
+                            : dispatch<2, float>(mesh, h, steady, uo, un, T, dtv[0], n_sub, out);
+  elm_mesh_destroy(mesh);
+  FILE* g = std::fopen(argv[2], "wb");
+  if (!g || std::fwrite(out.data(), sizeof(double), out.size(), g) != out.size()) return 1;
+  std::fclose(g);
+  if (status != 0) {
+    std::fprintf(stderr, "status flags %u\n", status);
+    return 2;
+  }
+  return 0;
+}
