@@ -18,7 +18,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["advect.cu", "noalloc.cu", "adjoint.cu", "diffusion.cu", "probe.cu"]
 CPP_SOURCES = ["mesh.cpp", "api.cpp", "batch.cpp", "host_path.cpp"]
-HEADERS = ["elm_internal.h", "tracer.cuh", "scaled_round.cuh"]
+HEADERS = ["elm_internal.h", "tracer.cuh", "scaled_round.cuh", "adjoint_kernels.cuh"]
 
 
 def _stale(target: str, deps: list[str]) -> bool:

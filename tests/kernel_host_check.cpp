@@ -20,67 +20,14 @@
 #include <cstdlib>
 #include <vector>
 
+#include "host_mesh_tables.h"
 #include "tracer.cuh"
 
 using namespace elm;
+using elm_host_check::HostTables;
+using elm_host_check::host_tables;
 
 namespace {
-
-struct HostTables {
-  std::vector<int64_t> owner_mp;
-  std::vector<int4> chunks;
-  std::vector<MacroGeo32> geo32;
-  std::vector<int2> ghosts;
-};
-
-// The tables the library uploads at mesh creation, built here from the
-// host-only mesh in the same way.
-HostTables host_tables(const elm_mesh_s* me) {
-  HostTables h;
-  const int d = me->dim, M = me->M;
-  std::vector<int64_t> slot_p(size_t(me->npm));
-  int64_t k = 0;
-  if (d == 2) {
-    for (int p1 = 0; p1 <= M; ++p1)
-      for (int p2 = 0; p2 <= p1; ++p2) slot_p[size_t(k++)] = pack_owner(0, p1, p2, 0);
-  } else {
-    for (int p1 = 0; p1 <= M; ++p1)
-      for (int p2 = 0; p2 <= p1; ++p2)
-        for (int p3 = 0; p3 <= p2; ++p3) slot_p[size_t(k++)] = pack_owner(0, p1, p2, p3);
-  }
-  h.owner_mp.resize(size_t(me->n_unique));
-  for (int64_t u = 0; u < me->n_unique; ++u) {
-    const int64_t m = me->owner[size_t(u)] / me->npm;
-    h.owner_mp[size_t(u)] = pack_owner(m, 0, 0, 0) | slot_p[size_t(me->owner[size_t(u)] - m * me->npm)];
-  }
-  for (int64_t m = 0; m < me->n_macros; ++m)
-    for (int p1 = 0; p1 <= M; ++p1) {
-      const int len = d == 3 ? (p1 + 1) * (p1 + 2) / 2 : p1 + 1;
-      for (int i0 = 0; i0 < len; i0 += kAdvectThreads)
-        h.chunks.push_back(make_int4(int(m), p1, i0, len - i0 < kAdvectThreads ? len - i0 : kAdvectThreads));
-    }
-  for (int64_t s = 0; s < me->n_storage; ++s) {
-    const int64_t o = me->owner[size_t(me->unique_map[size_t(s)])];
-    if (o != s) h.ghosts.push_back(make_int2(int(s), int(o)));
-  }
-  h.geo32.resize(size_t(me->n_macros));
-  auto split = [](double x, float* hi, float* lo) {
-    *hi = float(x);
-    *lo = float(x - double(*hi));
-  };
-  for (int64_t m = 0; m < me->n_macros; ++m) {
-    const MacroGeo& g = me->geo[size_t(m)];
-    MacroGeo32& g32 = h.geo32[size_t(m)];
-    for (int q = 0; q < 9; ++q) {
-      split(g.NJinv[q], &g32.NJinv[q], &g32.NJinv_lo[q]);
-      split(g.J[q], &g32.J[q], &g32.J_lo[q]);
-    }
-    for (int q = 0; q < 3; ++q) split(g.v0[q], &g32.v0[q], &g32.v0_lo[q]);
-    for (int q = 0; q < 4; ++q) g32.nb[q] = g.nb[q];
-    g32.x = g.x;
-  }
-  return h;
-}
 
 template <class R>
 StepConsts<R> step_consts(const elm_mesh_s* me, double dt, int n_sub) {

@@ -1,4 +1,4 @@
-"""Source guard for the adjoint kernel (csrc/adjoint.cu).
+"""Source guard for the adjoint kernel (csrc/adjoint_kernels.cuh).
 
 Adjoint::substep() runs the stage loop of one RK4 substep as a rolled loop.
 With two inlined copies of that loop in run(), the compiled kernels (nvcc 13.0,
@@ -10,7 +10,7 @@ import os
 import re
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-ADJOINT = os.path.join(ROOT, "paper_2103_02388_gb300", "csrc", "adjoint.cu")
+ADJOINT = os.path.join(ROOT, "paper_2103_02388_gb300", "csrc", "adjoint_kernels.cuh")
 
 
 def _code(path):

@@ -1,6 +1,7 @@
-"""CPU parity of the advection kernel's device code: csrc/tracer.cuh's
-advect_node, compiled with g++ (tests/cuda_host_shim.h stands in for the CUDA
-built-ins) and run node by node on the host (tests/kernel_host_check.cpp),
+"""CPU parity of the kernels' device code: csrc/tracer.cuh's advect_node and
+csrc/adjoint_kernels.cuh's adjoint kernels, compiled with g++
+(tests/cuda_host_shim.h stands in for the CUDA built-ins) and run thread by
+thread on the host (tests/kernel_host_check.cpp, tests/adjoint_host_check.cpp),
 against the oracle on the same seeded inputs, under AddressSanitizer and
 UndefinedBehaviorSanitizer.  No GPU: this checks the kernel source's logic
 (location, hand-off between macros, tie decisions, P1 / P2 stencils,
@@ -31,22 +32,31 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
 
 
-@pytest.fixture(scope="module")
-def exe(tmp_path_factory):
+def _build(tmp_path_factory, name):
     gxx = shutil.which("g++")
     if gxx is None or not os.path.exists(os.path.join(CUDA, "include", "cuda_runtime.h")):
         pytest.skip("g++ or the CUDA headers not found")
     build_library()
-    out = str(tmp_path_factory.mktemp("khc") / "kernel_host_check")
-    cmd = [gxx, "-std=c++17", "-O1", "-g", "-fno-omit-frame-pointer",
+    out = str(tmp_path_factory.mktemp(name) / name)
+    cmd = [gxx, "-std=c++17", "-O0", "-g", "-fno-omit-frame-pointer",
            "-fsanitize=address,undefined", "-fno-sanitize=shift-base", "-fno-sanitize-recover=all",
            "-I", os.path.join(CUDA, "include"), "-I", os.path.join(ROOT, "include"), "-I", os.path.join(PKG, "csrc"),
-           "-include", os.path.join(ROOT, "tests", "cuda_host_shim.h"),
-           os.path.join(ROOT, "tests", "kernel_host_check.cpp"), "-o", out,
+           "-I", os.path.join(ROOT, "tests"), "-include", os.path.join(ROOT, "tests", "cuda_host_shim.h"),
+           os.path.join(ROOT, "tests", name + ".cpp"), "-o", out,
            "-L", PKG, "-lelm", "-Wl,-rpath," + PKG, "-L", os.path.join(CUDA, "lib64"), "-lcudart"]
     b = subprocess.run(cmd, capture_output=True, text=True)
     assert b.returncode == 0, b.stdout + b.stderr
     return out
+
+
+@pytest.fixture(scope="module")
+def exe(tmp_path_factory):
+    return _build(tmp_path_factory, "kernel_host_check")
+
+
+@pytest.fixture(scope="module")
+def adj_exe(tmp_path_factory):
+    return _build(tmp_path_factory, "adjoint_host_check")
 
 
 def _host_step(exe, tmp, v, m, level, precision, order, T, u_old, u_new, dt, n_sub):
@@ -119,3 +129,108 @@ def test_kernel_code_time_dependent(exe, tmp_path, precision):
     got = _host_step(exe, tmp_path, v, m, 3, precision, 2, T, u0, u1, dt, 3)
     ref = om.advect(T, u0, dt, 3, u_new=u1)
     assert np.abs(got - ref).max() <= TOL[precision] * np.abs(T).max()
+
+
+# ---------------------------------------------------------------------------
+# The adjoint (tests/adjoint_host_check.cpp): the cases of the GPU adjoint tests
+# at levels 3 (P2) and 4 (P1), the same 17^3 node lattice.
+
+LEVEL = {2: 3, 1: 4}
+
+
+def _host_adjoint(adj_exe, tmp, v, m, level, precision, order, T, u_old, u_new, g, dt, n_sub):
+    """dL/dT^n, dL/du^n, dL/du^{n+1} through the host build of the adjoint
+    kernels; inputs and results in the oracle's unique node order, the
+    incoming gradient g on owner slots only."""
+    om_coords = oracle.OracleMesh(v, m, level, order=order).coords
+    gm = elm.Mesh(v, m, level, precision, order=order, host_only=True)
+    perm = match_nodes(om_coords, gm.unique_coords())
+    umap = gm.unique_map()
+    first = np.full(gm.n_unique, -1, np.int64)
+    first[umap[::-1]] = np.arange(gm.n_nodes)[::-1]
+
+    def storage(a):
+        x = np.empty_like(a)
+        x[perm] = a
+        return np.ascontiguousarray(x[umap], dtype=np.float64)
+
+    gg = np.empty_like(g)
+    gg[perm] = g
+    gs = np.zeros(gm.n_nodes)
+    gs[first] = gg
+    dim = v.shape[1]
+    split = u_new is not None
+    hd = np.array([dim, v.shape[0], m.shape[0], level, 0 if precision == "fp64" else 1, order,
+                   0 if split else 1, n_sub, 1 if split else 0], dtype=np.int64)
+    fin, fout = str(tmp / "adj_in.bin"), str(tmp / "adj_out.bin")
+    with open(fin, "wb") as f:
+        for a in (hd, np.array([dt], np.float64), np.ascontiguousarray(v, np.float64),
+                  np.ascontiguousarray(m, np.int64), storage(u_old), storage(u_old if u_new is None else u_new),
+                  storage(T), gs):
+            f.write(a.tobytes())
+    r = subprocess.run([adj_exe, fin, fout], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    out = np.fromfile(fout, dtype=np.float64)
+    n = gm.n_nodes
+    gT, gU0, gU1 = out[:n], out[n:n + n * dim].reshape(n, dim), out[n + n * dim:].reshape(n, dim)
+    return gT[first][perm], gU0[first][perm], gU1[first][perm]
+
+
+def _adjoint_fields(x, kind, precision):
+    if kind == "linear":
+        rng = np.random.default_rng(2)
+        u = inputs.linear_field(x, rng.standard_normal((3, 3)), np.full(3, 0.5))
+        T = inputs.random_quadratic(x, seed=6)
+    else:
+        u = inputs.random_fourier(x, seed=9) + 0.2 * inputs.uniform_field(x, [0.31, -0.17, 0.23])
+        T = inputs.gaussian(x, (0.45, 0.5, 0.55), 0.15)
+    return _rounded(u, precision), _rounded(T, precision)
+
+
+@pytest.mark.parametrize("precision,n_sub,order", [("fp64", 1, 2), ("fp64", 3, 2), ("fp32", 1, 2),
+                                                   ("fp64", 1, 1), ("fp64", 3, 1)])
+def test_adjoint_code_transpose(adj_exe, tmp_path, precision, n_sub, order):
+    v, m = mesh_for("cube")
+    om = oracle.OracleMesh(v, m, LEVEL[order], order=order)
+    u, T = _adjoint_fields(om.coords, "fourier", precision)
+    dt = inputs.dt_for_cfl(4.0, 3, u)
+    g = np.random.default_rng(1).standard_normal(om.n_nodes)
+    gT, _, _ = _host_adjoint(adj_exe, tmp_path, v, m, LEVEL[order], precision, order, T, u, None, g, dt, n_sub)
+    ref = om.advect_transpose(g, u, dt, n_sub)
+    assert np.abs(gT - ref).max() <= TOL[precision] * np.abs(ref).max() * 10
+
+
+@pytest.mark.parametrize("kind,n_sub,order", [("linear", 1, 2), ("linear", 2, 2), ("fourier", 1, 2),
+                                              ("fourier", 2, 2), ("fourier", 1, 1)])
+def test_adjoint_code_velocity_gradient(adj_exe, tmp_path, kind, n_sub, order):
+    """<dL/du, v> against the oracle's forward-mode derivative on 8 random
+    directions (L = <g, T^{n+1}>), FP64."""
+    v, m = mesh_for("cube")
+    om = oracle.OracleMesh(v, m, LEVEL[order], order=order)
+    u, T = _adjoint_fields(om.coords, kind, "fp64")
+    dt = inputs.dt_for_cfl(3.0, 3, u)
+    rng = np.random.default_rng(5)
+    g = rng.standard_normal(om.n_nodes)
+    _, gU, _ = _host_adjoint(adj_exe, tmp_path, v, m, LEVEL[order], "fp64", order, T, u, None, g, dt, n_sub)
+    for _ in range(8):
+        d = rng.standard_normal(u.shape)
+        _, jvp = om.advect_jvp(T, u, d, dt, n_sub)
+        assert abs((gU * d).sum() - g @ jvp) <= 1e-9 * (np.abs(g) @ np.abs(jvp) + 1e-30)
+
+
+def test_adjoint_code_time_dependent_split(adj_exe, tmp_path):
+    v, m = mesh_for("cube")
+    om = oracle.OracleMesh(v, m, 3)
+    u0, T = _adjoint_fields(om.coords, "fourier", "fp64")
+    u1 = inputs.random_fourier(om.coords, seed=12) + 0.2 * inputs.uniform_field(om.coords, [-0.21, 0.33, 0.14])
+    dt = inputs.dt_for_cfl(3.0, 3, u1)
+    rng = np.random.default_rng(8)
+    g = rng.standard_normal(om.n_nodes)
+    _, gU0, gU1 = _host_adjoint(adj_exe, tmp_path, v, m, 3, "fp64", 2, T, u0, u1, g, dt, 2)
+    zero = np.zeros_like(u0)
+    for _ in range(4):
+        d = rng.standard_normal(u0.shape)
+        _, j0 = om.advect_jvp(T, u0, d, dt, 2, u_new=u1, du_new=zero)
+        _, j1 = om.advect_jvp(T, u0, zero, dt, 2, u_new=u1, du_new=d)
+        assert abs((gU0 * d).sum() - g @ j0) <= 1e-9 * (np.abs(g) @ np.abs(j0) + 1e-30)
+        assert abs((gU1 * d).sum() - g @ j1) <= 1e-9 * (np.abs(g) @ np.abs(j1) + 1e-30)
