@@ -9,13 +9,21 @@
 // interface node is computed once in its owner's slot, and the interface
 // copies are then filled from it (k_ghost_copy).
 //
+// Three per-node modes, as the GPU path has: the step (T^{n+1} = T^n_h(X)),
+// a trace over one interval (from the node, or continued from given offsets;
+// the new offsets X - x_i are the result) and the evaluation of T at x_i plus
+// given offsets.
+//
 // Input file (little-endian, as numpy writes it): int64 header [dim,
 // n_vertices, n_macros, level, precision (0: FP64, 1: FP32), order, steady,
-// n_sub], double dt, vertex coordinates [n_vertices * dim], macro vertices
+// n_sub, mode (0: step, 1: trace, 2: evaluation), offsets given (0 / 1)],
+// double dt, vertex coordinates [n_vertices * dim], macro vertices
 // [n_macros * (dim + 1)] (int64), then in the mesh's storage layout u^n and
-// u^{n+1} [n_storage * dim] and T^n [n_storage] (doubles, already rounded to
-// FP32 for an FP32 run).  Output file: T^{n+1} [n_storage] (doubles).
-// Exit status: 0, 1 on bad input, 2 on a device-side status flag.
+// u^{n+1} [n_storage * dim], T^n [n_storage] and, if given, the offsets
+// [n_storage * dim] (doubles, already rounded to FP32 for an FP32 run).
+// Output file: T^{n+1} [n_storage] (step, evaluation) or the offsets
+// [n_storage * dim] (trace), doubles.  Exit status: 0, 1 on bad input, 2 on a
+// device-side status flag.
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -40,13 +48,14 @@ StepConsts<R> step_consts(const elm_mesh_s* me, double dt, int n_sub) {
   return K;
 }
 
-template <int D, class R, bool STEADY, int P>
+template <int D, class R, bool STEADY, int P, int MODE>
 unsigned step(const elm_mesh_s* me, const HostTables& h, const std::vector<double>& uo_in,
-              const std::vector<double>& un_in, const std::vector<double>& T_in, double dt, int n_sub,
-              std::vector<double>& T_out) {
+              const std::vector<double>& un_in, const std::vector<double>& T_in, const std::vector<double>* D_in,
+              double dt, int n_sub, std::vector<double>& out) {
   const int64_t n = me->n_storage;
   const size_t ns = static_cast<size_t>(n);
-  std::vector<R> un(ns * 4, R(0)), uo(ns * 4, R(0)), T(ns, R(0)), Tn(ns, R(0));
+  std::vector<R> un(ns * 4, R(0)), uo(ns * 4, R(0)), T(ns, R(0)), Tn(ns, R(0)), Din, Dout(ns * D, R(0));
+  if (D_in) Din.assign(D_in->begin(), D_in->end());
   for (int64_t s = 0; s < n; ++s) {
     for (int r = 0; r < D; ++r) {
       un[size_t(s) * 4 + r] = R(un_in[size_t(s) * D + r]);
@@ -59,27 +68,44 @@ unsigned step(const elm_mesh_s* me, const HostTables& h, const std::vector<doubl
                  me->unique_map.data(), h.owner_mp.data(), step_consts<R>(me, dt, n_sub), me->N,
                  int(me->npm), n_sub};
   job.skip_ghosts = 1;
+  job.D_in = D_in ? Din.data() : nullptr;
+  job.D_out = Dout.data();
   Tables<R> tab;
   if constexpr (sizeof(R) == 8)
     tab.g = me->geo.data();
   else
     tab.g = h.geo32.data();
   for (const int4& ck : h.chunks)
-    for (int tid = 0; tid < ck.w; ++tid) advect_node<D, R, STEADY, P, kStep, 0>(job, tab, ck, tid);
-  for (const int2& g : h.ghosts) Tn[size_t(g.x)] = Tn[size_t(g.y)];
-  T_out.assign(Tn.begin(), Tn.end());
+    for (int tid = 0; tid < ck.w; ++tid) advect_node<D, R, STEADY, P, MODE, 0>(job, tab, ck, tid);
+  if (MODE == kTrace) {
+    for (const int2& g : h.ghosts)
+      for (int q = 0; q < D; ++q) Dout[size_t(g.x) * D + q] = Dout[size_t(g.y) * D + q];
+    out.assign(Dout.begin(), Dout.end());
+  } else {
+    for (const int2& g : h.ghosts) Tn[size_t(g.x)] = Tn[size_t(g.y)];
+    out.assign(Tn.begin(), Tn.end());
+  }
   return status;
 }
 
-template <int D, class R>
-unsigned dispatch(const elm_mesh_s* me, const HostTables& h, bool steady, const std::vector<double>& uo,
-                  const std::vector<double>& un, const std::vector<double>& T, double dt, int n_sub,
-                  std::vector<double>& out) {
+template <int D, class R, int MODE>
+unsigned dispatch_mode(const elm_mesh_s* me, const HostTables& h, bool steady, const std::vector<double>& uo,
+                       const std::vector<double>& un, const std::vector<double>& T, const std::vector<double>* Di,
+                       double dt, int n_sub, std::vector<double>& out) {
   if (me->order == 1)
-    return steady ? step<D, R, true, 1>(me, h, uo, un, T, dt, n_sub, out)
-                  : step<D, R, false, 1>(me, h, uo, un, T, dt, n_sub, out);
-  return steady ? step<D, R, true, 2>(me, h, uo, un, T, dt, n_sub, out)
-                : step<D, R, false, 2>(me, h, uo, un, T, dt, n_sub, out);
+    return steady ? step<D, R, true, 1, MODE>(me, h, uo, un, T, Di, dt, n_sub, out)
+                  : step<D, R, false, 1, MODE>(me, h, uo, un, T, Di, dt, n_sub, out);
+  return steady ? step<D, R, true, 2, MODE>(me, h, uo, un, T, Di, dt, n_sub, out)
+                : step<D, R, false, 2, MODE>(me, h, uo, un, T, Di, dt, n_sub, out);
+}
+
+template <int D, class R>
+unsigned dispatch(const elm_mesh_s* me, const HostTables& h, int mode, bool steady, const std::vector<double>& uo,
+                  const std::vector<double>& un, const std::vector<double>& T, const std::vector<double>* Di,
+                  double dt, int n_sub, std::vector<double>& out) {
+  if (mode == kTrace) return dispatch_mode<D, R, kTrace>(me, h, steady, uo, un, T, Di, dt, n_sub, out);
+  if (mode == kEval) return dispatch_mode<D, R, kEval>(me, h, steady, uo, un, T, Di, dt, n_sub, out);
+  return dispatch_mode<D, R, kStep>(me, h, steady, uo, un, T, Di, dt, n_sub, out);
 }
 
 template <class T>
@@ -99,9 +125,10 @@ int main(int argc, char** argv) {
   if (!f) return 1;
   std::vector<int64_t> hd;
   std::vector<double> dtv;
-  if (!read_n(f, hd, 8) || !read_n(f, dtv, 1)) return 1;
-  const int dim = int(hd[0]), precision = int(hd[4]), order = int(hd[5]), n_sub = int(hd[7]);
-  const bool steady = hd[6] != 0;
+  if (!read_n(f, hd, 10) || !read_n(f, dtv, 1)) return 1;
+  const int dim = int(hd[0]), precision = int(hd[4]), order = int(hd[5]), n_sub = int(hd[7]), mode = int(hd[8]);
+  const bool steady = hd[6] != 0, has_din = hd[9] != 0;
+  if (mode < kStep || mode > kEval || (mode == kEval && !has_din)) return 1;
   std::vector<double> V;
   std::vector<int64_t> Mc;
   if (!read_n(f, V, size_t(hd[1] * dim)) || !read_n(f, Mc, size_t(hd[2] * (dim + 1)))) return 1;
@@ -112,17 +139,20 @@ int main(int argc, char** argv) {
     return 1;
   }
   const int64_t n = mesh->n_storage;
-  std::vector<double> uo, un, T, out;
-  if (!read_n(f, uo, size_t(n * dim)) || !read_n(f, un, size_t(n * dim)) || !read_n(f, T, size_t(n))) return 1;
+  std::vector<double> uo, un, T, Di, out;
+  if (!read_n(f, uo, size_t(n * dim)) || !read_n(f, un, size_t(n * dim)) || !read_n(f, T, size_t(n)) ||
+      (has_din && !read_n(f, Di, size_t(n * dim))))
+    return 1;
+  const std::vector<double>* dptr = has_din ? &Di : nullptr;
   std::fclose(f);
   const HostTables h = host_tables(mesh);
   unsigned status;
   if (dim == 3)
-    status = precision == 0 ? dispatch<3, double>(mesh, h, steady, uo, un, T, dtv[0], n_sub, out)
-                            : dispatch<3, float>(mesh, h, steady, uo, un, T, dtv[0], n_sub, out);
+    status = precision == 0 ? dispatch<3, double>(mesh, h, mode, steady, uo, un, T, dptr, dtv[0], n_sub, out)
+                            : dispatch<3, float>(mesh, h, mode, steady, uo, un, T, dptr, dtv[0], n_sub, out);
   else
-    status = precision == 0 ? dispatch<2, double>(mesh, h, steady, uo, un, T, dtv[0], n_sub, out)
-                            : dispatch<2, float>(mesh, h, steady, uo, un, T, dtv[0], n_sub, out);
+    status = precision == 0 ? dispatch<2, double>(mesh, h, mode, steady, uo, un, T, dptr, dtv[0], n_sub, out)
+                            : dispatch<2, float>(mesh, h, mode, steady, uo, un, T, dptr, dtv[0], n_sub, out);
   elm_mesh_destroy(mesh);
   FILE* g = std::fopen(argv[2], "wb");
   if (!g || std::fwrite(out.data(), sizeof(double), out.size(), g) != out.size()) return 1;

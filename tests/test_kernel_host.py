@@ -59,35 +59,60 @@ def adj_exe(tmp_path_factory):
     return _build(tmp_path_factory, "adjoint_host_check")
 
 
-def _host_step(exe, tmp, v, m, level, precision, order, T, u_old, u_new, dt, n_sub):
-    """One step through the host build of the kernel code; T, u in the
-    oracle's unique node order; returns T^{n+1} in that order."""
-    om_coords = oracle.OracleMesh(v, m, level, order=order).coords
-    gm = elm.Mesh(v, m, level, precision, order=order, host_only=True)
-    perm = match_nodes(om_coords, gm.unique_coords())
-    umap = gm.unique_map()
+class HostMesh:
+    """The host-only mesh's layout beside the oracle's node order."""
 
-    def storage(a):
+    def __init__(self, v, m, level, precision, order):
+        self.v, self.m, self.level, self.precision, self.order = v, m, level, precision, order
+        om_coords = oracle.OracleMesh(v, m, level, order=order).coords
+        self.gm = elm.Mesh(v, m, level, precision, order=order, host_only=True)
+        self.perm = match_nodes(om_coords, self.gm.unique_coords())
+        self.umap = self.gm.unique_map()
+
+    def storage(self, a):
+        """Unique field (oracle order) -> storage layout, copies everywhere."""
         g = np.empty_like(a)
-        g[perm] = a
-        return np.ascontiguousarray(g[umap], dtype=np.float64)
+        g[self.perm] = a
+        return np.ascontiguousarray(g[self.umap], dtype=np.float64)
 
-    dim = v.shape[1]
-    hd = np.array([dim, v.shape[0], m.shape[0], level, 0 if precision == "fp64" else 1, order,
-                   1 if u_new is None else 0, n_sub], dtype=np.int64)
+    def unique(self, a):
+        """Storage field -> oracle order; checks that all copies of a node agree."""
+        a = a.reshape((self.gm.n_nodes,) + (() if a.size == self.gm.n_nodes else (-1,)))
+        uniq = np.empty((self.gm.n_unique,) + a.shape[1:])
+        uniq[self.umap] = a
+        assert np.array_equal(uniq[self.umap], a), "storage copies of a node disagree"
+        return uniq[self.perm]
+
+
+MODE = {"step": 0, "trace": 1, "eval": 2}
+
+
+def _host_call(exe, tmp, hm, mode, T, u_old, u_new, dt, n_sub, D_in=None):
+    """One launch of the host build in `mode`; fields in the oracle's unique
+    order, offsets D_in in the storage layout; returns the storage-layout
+    result (T, or the offsets for a trace)."""
+    dim = hm.v.shape[1]
+    hd = np.array([dim, hm.v.shape[0], hm.m.shape[0], hm.level, 0 if hm.precision == "fp64" else 1, hm.order,
+                   1 if u_new is None else 0, n_sub, MODE[mode], 0 if D_in is None else 1], dtype=np.int64)
     fin, fout = str(tmp / "in.bin"), str(tmp / "out.bin")
+    parts = [hd, np.array([dt], np.float64), np.ascontiguousarray(hm.v, np.float64),
+             np.ascontiguousarray(hm.m, np.int64), hm.storage(u_old), hm.storage(u_old if u_new is None else u_new),
+             hm.storage(T)]
+    if D_in is not None:
+        parts.append(np.ascontiguousarray(D_in, np.float64))
     with open(fin, "wb") as f:
-        for a in (hd, np.array([dt], np.float64), np.ascontiguousarray(v, np.float64),
-                  np.ascontiguousarray(m, np.int64), storage(u_old), storage(u_old if u_new is None else u_new),
-                  storage(T)):
+        for a in parts:
             f.write(a.tobytes())
     r = subprocess.run([exe, fin, fout], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
-    out = np.fromfile(fout, dtype=np.float64)
-    uniq = np.empty(gm.n_unique)
-    uniq[umap] = out
-    assert np.array_equal(uniq[umap], out), "storage copies of a node disagree"
-    return uniq[perm]
+    return np.fromfile(fout, dtype=np.float64)
+
+
+def _host_step(exe, tmp, v, m, level, precision, order, T, u_old, u_new, dt, n_sub):
+    """One step through the host build of the kernel code; T, u in the
+    oracle's unique node order; returns T^{n+1} in that order."""
+    hm = HostMesh(v, m, level, precision, order)
+    return hm.unique(_host_call(exe, tmp, hm, "step", T, u_old, u_new, dt, n_sub))
 
 
 def _rounded(a, precision):
@@ -129,6 +154,33 @@ def test_kernel_code_time_dependent(exe, tmp_path, precision):
     got = _host_step(exe, tmp_path, v, m, 3, precision, 2, T, u0, u1, dt, 3)
     ref = om.advect(T, u0, dt, 3, u_new=u1)
     assert np.abs(got - ref).max() <= TOL[precision] * np.abs(T).max()
+
+
+@pytest.mark.parametrize("order,level,precision", [(2, 3, "fp64"), (1, 4, "fp64"), (2, 3, "fp32"), (1, 4, "fp32")])
+def test_kernel_code_trace_swirl(exe, tmp_path, order, level, precision):
+    """The swirling flow of Sec. 3.3 (time-dependent), look-back over 4
+    intervals of tau = 0.15 (newest first, offsets carried between intervals
+    in the storage layout), then T^0 evaluated at the traced points: offsets
+    and field against the oracle's trace continuation.  In FP32 the trace
+    mode decides ties in double-float arithmetic."""
+    v, m = mesh_for("cube")
+    om = oracle.OracleMesh(v, m, level, order=order)
+    hm = HostMesh(v, m, level, precision, order)
+    x = om.coords
+    c0 = _rounded(inputs.gaussian(x, (0.35, 0.5, 0.5), 0.1), precision)
+    tau = 0.15
+    fields = [_rounded(inputs.swirl_3d(x, k * tau), precision) for k in range(5)]
+    D = None
+    for k in range(len(fields) - 1, 0, -1):
+        D = _host_call(exe, tmp_path, hm, "trace", c0, fields[k - 1], fields[k], tau, 2, D_in=D)
+    T = hm.unique(_host_call(exe, tmp_path, hm, "eval", c0, fields[0], None, 0.0, 1, D_in=D))
+    X = x.copy()
+    for k in range(len(fields) - 1, 0, -1):
+        X = om.trace(X, fields[k - 1], tau, 2, u_new=fields[k])
+    To = om.eval(c0, X)
+    dtol = 1e-12 if precision == "fp64" else 2e-5
+    assert np.abs((x + hm.unique(D)) - X).max() <= dtol
+    assert np.abs(T - To).max() <= (TOL["fp64"] if precision == "fp64" else 2e-4) * np.abs(c0).max()
 
 
 # ---------------------------------------------------------------------------
