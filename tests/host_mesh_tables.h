@@ -1,10 +1,12 @@
 // host_mesh_tables.h -- the tables the library uploads at mesh creation (owner
 // records, the work list, the FP32 split of the macro tables, the interface
-// copies), built from a host-only mesh in the same way, for the host builds of
+// copies, the annulus sector table), built from a host-only mesh in the same
+// way, for the host builds of
 // the kernels' device code (tests/kernel_host_check.cpp,
 // tests/adjoint_host_check.cpp).  Test infrastructure only.
 #pragma once
 
+#include <cmath>
 #include <vector>
 
 #include "elm_internal.h"
@@ -65,6 +67,18 @@ inline HostTables host_tables(const elm_mesh_s* me) {
     g32.x = g.x;
   }
   return h;
+}
+
+// Unit vectors at the sector boundaries theta0 + k 2 pi / n, k = 0..n ([n + 1][2];
+// the last repeats the first), the annulus blending's sector table.
+inline std::vector<double> sector_table(int n, double theta0) {
+  std::vector<double> sec(size_t(2 * (n + 1)));
+  const double delta = 2.0 * 3.14159265358979323846 / n;
+  for (int k = 0; k <= n; ++k) {
+    sec[size_t(2 * k)] = std::cos(theta0 + (k % n) * delta);
+    sec[size_t(2 * k + 1)] = std::sin(theta0 + (k % n) * delta);
+  }
+  return sec;
 }
 
 }  // namespace elm_host_check

@@ -17,7 +17,8 @@
 // Input file (little-endian, as numpy writes it): int64 header [dim,
 // n_vertices, n_macros, level, precision (0: FP64, 1: FP32), order, steady,
 // n_sub, mode (0: step, 1: trace, 2: evaluation), offsets given (0 / 1)],
-// double dt, vertex coordinates [n_vertices * dim], macro vertices
+// doubles [dt, r_min, r_max, n_sectors, theta0] (n_sectors > 0: the mesh is
+// blended onto that annulus; 2D FP64), vertex coordinates [n_vertices * dim], macro vertices
 // [n_macros * (dim + 1)] (int64), then in the mesh's storage layout u^n and
 // u^{n+1} [n_storage * dim], T^n [n_storage] and, if given, the offsets
 // [n_storage * dim] (doubles, already rounded to FP32 for an FP32 run).
@@ -34,6 +35,7 @@
 using namespace elm;
 using elm_host_check::HostTables;
 using elm_host_check::host_tables;
+using elm_host_check::sector_table;
 
 namespace {
 
@@ -48,7 +50,7 @@ StepConsts<R> step_consts(const elm_mesh_s* me, double dt, int n_sub) {
   return K;
 }
 
-template <int D, class R, bool STEADY, int P, int MODE>
+template <int D, class R, bool STEADY, int P, int MODE, int BLEND>
 unsigned step(const elm_mesh_s* me, const HostTables& h, const std::vector<double>& uo_in,
               const std::vector<double>& un_in, const std::vector<double>& T_in, const std::vector<double>* D_in,
               double dt, int n_sub, std::vector<double>& out) {
@@ -68,6 +70,10 @@ unsigned step(const elm_mesh_s* me, const HostTables& h, const std::vector<doubl
                  me->unique_map.data(), h.owner_mp.data(), step_consts<R>(me, dt, n_sub), me->N,
                  int(me->npm), n_sub};
   job.skip_ghosts = 1;
+  if constexpr (BLEND == 1) {
+    job.bl = me->blend;
+    job.n_macros = int(me->n_macros);
+  }
   job.D_in = D_in ? Din.data() : nullptr;
   job.D_out = Dout.data();
   Tables<R> tab;
@@ -76,7 +82,7 @@ unsigned step(const elm_mesh_s* me, const HostTables& h, const std::vector<doubl
   else
     tab.g = h.geo32.data();
   for (const int4& ck : h.chunks)
-    for (int tid = 0; tid < ck.w; ++tid) advect_node<D, R, STEADY, P, MODE, 0>(job, tab, ck, tid);
+    for (int tid = 0; tid < ck.w; ++tid) advect_node<D, R, STEADY, P, MODE, BLEND>(job, tab, ck, tid);
   if (MODE == kTrace) {
     for (const int2& g : h.ghosts)
       for (int q = 0; q < D; ++q) Dout[size_t(g.x) * D + q] = Dout[size_t(g.y) * D + q];
@@ -88,15 +94,25 @@ unsigned step(const elm_mesh_s* me, const HostTables& h, const std::vector<doubl
   return status;
 }
 
+template <int D, class R, int MODE, int BLEND>
+unsigned dispatch_blend(const elm_mesh_s* me, const HostTables& h, bool steady, const std::vector<double>& uo,
+                        const std::vector<double>& un, const std::vector<double>& T, const std::vector<double>* Di,
+                        double dt, int n_sub, std::vector<double>& out) {
+  if (me->order == 1)
+    return steady ? step<D, R, true, 1, MODE, BLEND>(me, h, uo, un, T, Di, dt, n_sub, out)
+                  : step<D, R, false, 1, MODE, BLEND>(me, h, uo, un, T, Di, dt, n_sub, out);
+  return steady ? step<D, R, true, 2, MODE, BLEND>(me, h, uo, un, T, Di, dt, n_sub, out)
+                : step<D, R, false, 2, MODE, BLEND>(me, h, uo, un, T, Di, dt, n_sub, out);
+}
+
 template <int D, class R, int MODE>
 unsigned dispatch_mode(const elm_mesh_s* me, const HostTables& h, bool steady, const std::vector<double>& uo,
                        const std::vector<double>& un, const std::vector<double>& T, const std::vector<double>* Di,
                        double dt, int n_sub, std::vector<double>& out) {
-  if (me->order == 1)
-    return steady ? step<D, R, true, 1, MODE>(me, h, uo, un, T, Di, dt, n_sub, out)
-                  : step<D, R, false, 1, MODE>(me, h, uo, un, T, Di, dt, n_sub, out);
-  return steady ? step<D, R, true, 2, MODE>(me, h, uo, un, T, Di, dt, n_sub, out)
-                : step<D, R, false, 2, MODE>(me, h, uo, un, T, Di, dt, n_sub, out);
+  if constexpr (D == 2 && sizeof(R) == 8) {
+    if (me->blend.nsec > 0) return dispatch_blend<D, R, MODE, 1>(me, h, steady, uo, un, T, Di, dt, n_sub, out);
+  }
+  return dispatch_blend<D, R, MODE, 0>(me, h, steady, uo, un, T, Di, dt, n_sub, out);
 }
 
 template <int D, class R>
@@ -125,7 +141,7 @@ int main(int argc, char** argv) {
   if (!f) return 1;
   std::vector<int64_t> hd;
   std::vector<double> dtv;
-  if (!read_n(f, hd, 10) || !read_n(f, dtv, 1)) return 1;
+  if (!read_n(f, hd, 10) || !read_n(f, dtv, 5)) return 1;
   const int dim = int(hd[0]), precision = int(hd[4]), order = int(hd[5]), n_sub = int(hd[7]), mode = int(hd[8]);
   const bool steady = hd[6] != 0, has_din = hd[9] != 0;
   if (mode < kStep || mode > kEval || (mode == kEval && !has_din)) return 1;
@@ -137,6 +153,15 @@ int main(int argc, char** argv) {
   if (elm_mesh_create(dim, hd[1], V.data(), hd[2], Mc.data(), int(hd[3]), prec, &mesh) != ELM_OK) {
     std::fprintf(stderr, "mesh: %s\n", elm_last_error());
     return 1;
+  }
+  std::vector<double> sec;
+  if (dtv[3] > 0) {
+    if (elm_mesh_set_annulus(mesh, dtv[1], dtv[2], int(dtv[3]), dtv[4]) != ELM_OK) {
+      std::fprintf(stderr, "annulus: %s\n", elm_last_error());
+      return 1;
+    }
+    sec = sector_table(int(dtv[3]), dtv[4]);  // a host-only mesh keeps no copy of it
+    mesh->blend.sec = sec.data();
   }
   const int64_t n = mesh->n_storage;
   std::vector<double> uo, un, T, Di, out;
@@ -153,6 +178,7 @@ int main(int argc, char** argv) {
   else
     status = precision == 0 ? dispatch<2, double>(mesh, h, mode, steady, uo, un, T, dptr, dtv[0], n_sub, out)
                             : dispatch<2, float>(mesh, h, mode, steady, uo, un, T, dptr, dtv[0], n_sub, out);
+  mesh->blend.sec = nullptr;  // owned by `sec`
   elm_mesh_destroy(mesh);
   FILE* g = std::fopen(argv[2], "wb");
   if (!g || std::fwrite(out.data(), sizeof(double), out.size(), g) != out.size()) return 1;

@@ -62,11 +62,12 @@ def adj_exe(tmp_path_factory):
 class HostMesh:
     """The host-only mesh's layout beside the oracle's node order."""
 
-    def __init__(self, v, m, level, precision, order):
+    def __init__(self, v, m, level, precision, order, annulus=None):
         self.v, self.m, self.level, self.precision, self.order = v, m, level, precision, order
-        om_coords = oracle.OracleMesh(v, m, level, order=order).coords
-        self.gm = elm.Mesh(v, m, level, precision, order=order, host_only=True)
-        self.perm = match_nodes(om_coords, self.gm.unique_coords())
+        self.annulus = annulus
+        om_coords = oracle.OracleMesh(v, m, level, order=order, annulus=annulus).coords
+        self.gm = elm.Mesh(v, m, level, precision, order=order, host_only=True, annulus=annulus)
+        self.perm = match_nodes(om_coords, self.gm.unique_coords(), **({"tol": 1e-12} if annulus else {}))
         self.umap = self.gm.unique_map()
 
     def storage(self, a):
@@ -95,7 +96,8 @@ def _host_call(exe, tmp, hm, mode, T, u_old, u_new, dt, n_sub, D_in=None):
     hd = np.array([dim, hm.v.shape[0], hm.m.shape[0], hm.level, 0 if hm.precision == "fp64" else 1, hm.order,
                    1 if u_new is None else 0, n_sub, MODE[mode], 0 if D_in is None else 1], dtype=np.int64)
     fin, fout = str(tmp / "in.bin"), str(tmp / "out.bin")
-    parts = [hd, np.array([dt], np.float64), np.ascontiguousarray(hm.v, np.float64),
+    ann = (0.0, 0.0, 0, 0.0) if hm.annulus is None else hm.annulus
+    parts = [hd, np.array([dt, ann[0], ann[1], ann[2], ann[3]], np.float64), np.ascontiguousarray(hm.v, np.float64),
              np.ascontiguousarray(hm.m, np.int64), hm.storage(u_old), hm.storage(u_old if u_new is None else u_new),
              hm.storage(T)]
     if D_in is not None:
@@ -181,6 +183,23 @@ def test_kernel_code_trace_swirl(exe, tmp_path, order, level, precision):
     dtol = 1e-12 if precision == "fp64" else 2e-5
     assert np.abs((x + hm.unique(D)) - X).max() <= dtol
     assert np.abs(T - To).max() <= (TOL["fp64"] if precision == "fp64" else 2e-4) * np.abs(c0).max()
+
+
+@pytest.mark.parametrize("level,order,n_sub,speed", [(3, 2, 1, 1.0), (4, 2, 2, 3.0), (4, 1, 1, 2.0), (2, 2, 3, 6.0)])
+def test_kernel_code_blended_annulus(exe, tmp_path, level, order, n_sub, speed):
+    """The mesh blended onto the annulus r in [0.5, 1.5] (6 sectors, 2D FP64):
+    rotation plus a uniform drift, which pushes points across the circles
+    (radial clamping), against the oracle's blended step."""
+    v, m = inputs.annulus_ring(6, 2)
+    ann = (0.5, 1.5, 6, 0.0)
+    om = oracle.OracleMesh(v, m, level, order=order, annulus=ann)
+    hm = HostMesh(v, m, level, "fp64", order, annulus=ann)
+    x = om.coords
+    u = speed * (np.stack([-x[:, 1], x[:, 0]], axis=1) + np.array([0.4, -0.25]))
+    T = np.exp(-np.sum((x - np.array([0.0, 1.0])) ** 2, axis=1) / 0.05) + 0.2 * x[:, 0]
+    got = hm.unique(_host_call(exe, tmp_path, hm, "step", T, u, None, 0.05, n_sub))
+    ref = om.advect(T, u, 0.05, n_sub)
+    assert np.abs(got - ref).max() <= TOL["fp64"] * np.abs(T).max()
 
 
 # ---------------------------------------------------------------------------
