@@ -39,7 +39,7 @@ def _build(tmp_path_factory, name):
     build_library()
     out = str(tmp_path_factory.mktemp(name) / name)
     cmd = [gxx, "-std=c++17", "-O0", "-g", "-fno-omit-frame-pointer",
-           "-fsanitize=address,undefined", "-fno-sanitize=shift-base", "-fno-sanitize-recover=all",
+           "-fsanitize=address,undefined,float-cast-overflow", "-fno-sanitize=shift-base", "-fno-sanitize-recover=all",
            "-I", os.path.join(CUDA, "include"), "-I", os.path.join(ROOT, "include"), "-I", os.path.join(PKG, "csrc"),
            "-I", os.path.join(ROOT, "tests"), "-include", os.path.join(ROOT, "tests", "cuda_host_shim.h"),
            os.path.join(ROOT, "tests", name + ".cpp"), "-o", out,
