@@ -202,6 +202,46 @@ def test_kernel_code_blended_annulus(exe, tmp_path, level, order, n_sub, speed):
     assert np.abs(got - ref).max() <= TOL["fp64"] * np.abs(T).max()
 
 
+@pytest.mark.parametrize("mesh,level,precision,cfl,n_sub", [
+    ("cube", 0, "fp64", 40.0, 1), ("cube", 1, "fp64", 12.0, 8), ("square", 0, "fp64", 40.0, 1),
+    ("square_block", 2, "fp32", 12.0, 8), ("cube_block", 1, "fp32", 12.0, 8)])
+def test_kernel_code_extreme_cfl(exe, tmp_path, mesh, level, precision, cfl, n_sub):
+    """Far outside the benchmark regime (CFL 12-40 on the coarsest meshes):
+    no sanitizer finding, and T within a bound that allows for the
+    conditioning there.  Traces that leave an unstable stagnation point of the
+    backward flow (the random Fourier field vanishes at the cube's corners)
+    amplify rounding by exp(lambda dt) -- 16 times per interval in the worst
+    case -- so two correct implementations that round differently drift
+    apart; measured: 1e-10 (FP64) and 1.6e-5 (FP32) of max |T|."""
+    v, m = mesh_for(mesh)
+    om = oracle.OracleMesh(v, m, level)
+    hm = HostMesh(v, m, level, precision, 2)
+    u = _rounded(velocity_for("fourier", om.coords), precision)
+    T = _rounded(scalar_for("gauss", om.coords), precision)
+    dt = inputs.dt_for_cfl(cfl, max(level, 1), u)
+    got = hm.unique(_host_call(exe, tmp_path, hm, "step", T, u, None, dt, n_sub))
+    ref = om.advect(T, u, dt, n_sub)
+    assert np.abs(got - ref).max() <= (1e-8 if precision == "fp64" else 1e-4) * np.abs(T).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_kernel_code_non_finite_velocity(exe, tmp_path, precision):
+    """A NaN and an infinite velocity value: the status flag (exit 2), and no
+    sanitizer finding on the way (conversions, locations of non-finite
+    points)."""
+    v, m = mesh_for("cube")
+    om = oracle.OracleMesh(v, m, 2)
+    hm = HostMesh(v, m, 2, precision, 2)
+    u = velocity_for("fourier", om.coords).copy()
+    u[len(u) // 2, 0] = np.nan
+    u[len(u) // 3, -1] = np.inf
+    T = scalar_for("gauss", om.coords)
+    with pytest.raises(AssertionError) as e:
+        _host_call(exe, tmp_path, hm, "step", T, u, None, 0.1, 2)
+    msg = str(e.value)
+    assert "status flags" in msg and "runtime error" not in msg and "AddressSanitizer" not in msg
+
+
 # ---------------------------------------------------------------------------
 # The adjoint (tests/adjoint_host_check.cpp): the cases of the GPU adjoint tests
 # at levels 3 (P2) and 4 (P1), the same 17^3 node lattice.
