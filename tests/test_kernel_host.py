@@ -345,3 +345,18 @@ def test_adjoint_code_time_dependent_split(adj_exe, tmp_path):
         _, j1 = om.advect_jvp(T, u0, zero, dt, 2, u_new=u1, du_new=d)
         assert abs((gU0 * d).sum() - g @ j0) <= 1e-9 * (np.abs(g) @ np.abs(j0) + 1e-30)
         assert abs((gU1 * d).sum() - g @ j1) <= 1e-9 * (np.abs(g) @ np.abs(j1) + 1e-30)
+
+
+def test_adjoint_code_non_finite_velocity(adj_exe, tmp_path):
+    """A NaN velocity value in the adjoint: the status flag (exit 2) and no
+    sanitizer finding (scale exponents of non-finite statistics, conversions)."""
+    v, m = mesh_for("cube")
+    om = oracle.OracleMesh(v, m, 2)
+    u, T = _adjoint_fields(om.coords, "fourier", "fp64")
+    u = u.copy()
+    u[len(u) // 2, 0] = np.nan
+    g = np.random.default_rng(1).standard_normal(om.n_nodes)
+    with pytest.raises(AssertionError) as e:
+        _host_adjoint(adj_exe, tmp_path, v, m, 2, "fp64", 2, T, u, None, g, 0.1, 2)
+    msg = str(e.value)
+    assert "status flags" in msg and "runtime error" not in msg and "AddressSanitizer" not in msg
