@@ -202,6 +202,26 @@ def test_kernel_code_blended_annulus(exe, tmp_path, level, order, n_sub, speed):
     assert np.abs(got - ref).max() <= TOL["fp64"] * np.abs(T).max()
 
 
+@pytest.mark.parametrize("direction,level,order", [((1.0, 1.0, 1.0), 3, 2), ((1.0, 1.0, 0.0), 3, 2),
+                                                   ((1.0, 1.0, 1.0), 4, 1), ((0.0, 1.0, 1.0), 4, 1)])
+def test_kernel_code_departures_on_macro_faces(exe, tmp_path, direction, level, order):
+    """A uniform velocity along a Kuhn diagonal keeps the nodes of the planes
+    x_i = x_j on them: 10-27% of the departure points lie exactly on interior
+    macro faces (in FP32 the location then decides in FP64).  The step equals
+    the oracle's at the usual tolerances in both precisions."""
+    v, m = mesh_for("cube")
+    om = oracle.OracleMesh(v, m, level, order=order)
+    x = om.coords
+    for precision in ("fp64", "fp32"):
+        hm = HostMesh(v, m, level, precision, order)
+        u = _rounded(np.tile(0.37 * np.array(direction), (len(x), 1)), precision)
+        T = _rounded(inputs.random_quadratic(x, seed=5), precision)
+        dt = inputs.dt_for_cfl(3.0, level, u)
+        got = hm.unique(_host_call(exe, tmp_path, hm, "step", T, u, None, dt, 2))
+        ref = om.advect(T, u, dt, 2)
+        assert np.abs(got - ref).max() <= TOL[precision] * np.abs(T).max()
+
+
 @pytest.mark.parametrize("mesh,level,precision,cfl,n_sub", [
     ("cube", 0, "fp64", 40.0, 1), ("cube", 1, "fp64", 12.0, 8), ("square", 0, "fp64", 40.0, 1),
     ("square_block", 2, "fp32", 12.0, 8), ("cube_block", 1, "fp32", 12.0, 8)])
