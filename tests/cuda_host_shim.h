@@ -1,13 +1,15 @@
 // cuda_host_shim.h -- host stand-ins for the CUDA device built-ins and
-// intrinsics that the advection kernels' device code (csrc/tracer.cuh) uses,
-// so that the same source compiles with g++ and runs on the CPU (under
-// AddressSanitizer / UndefinedBehaviorSanitizer) in tests/kernel_host_check.cpp.
+// intrinsics that the kernels' device code uses, so that the same source
+// compiles with g++ and runs on the CPU (under AddressSanitizer /
+// UndefinedBehaviorSanitizer) in the host check programs of tests/.
 //
 // Each stand-in states the operation's meaning in plain C++: bit casts by
 // memcpy, conversions with the rounding the intrinsic's name gives (rn: to
 // nearest even, rd: down, rz: toward zero; out-of-range values saturate),
-// fused multiply-adds by std::fma, and atomics as plain read-modify-writes (the
-// host program runs one thread at a time).  Test infrastructure only.
+// fused multiply-adds by std::fma, and atomics as plain read-modify-writes when
+// the host program runs one thread at a time.  CUDA_HOST_THREADS switches to
+// running each block's threads together (barriers, warp exchanges, atomic
+// built-ins; end of this file).  Test infrastructure only.
 #pragma once
 
 #include <cuda_runtime.h>  // vector types (float2, int4, ...), dim3, uint3
@@ -17,8 +19,14 @@
 #include <cstdint>
 #include <cstring>
 
-// the launch geometry of the block being emulated
+// The launch geometry.  Without CUDA_HOST_THREADS the host program runs one
+// GPU thread at a time (kernels without barriers or warp exchanges); with it,
+// host_launch below runs each block's threads as host threads together.
+#ifdef CUDA_HOST_THREADS
+inline thread_local uint3 threadIdx, blockIdx;
+#else
 inline uint3 threadIdx, blockIdx;
+#endif
 inline dim3 blockDim, gridDim;
 
 // qualifiers nvcc knows and a host compiler does not
@@ -26,8 +34,10 @@ inline dim3 blockDim, gridDim;
 #define __noinline__
 #define __launch_bounds__(...)
 #define __grid_constant__
-#define __shared__ static
+#define __shared__ static  // blocks run one after another, so one copy serves each block
+#ifndef CUDA_HOST_THREADS
 inline void __syncthreads() {}
+#endif
 
 using std::frexp;
 using std::isfinite;
@@ -116,3 +126,87 @@ inline unsigned long long atomicMax(unsigned long long* p, unsigned long long v)
   if (v > o) *p = v;
   return o;
 }
+
+#ifdef CUDA_HOST_THREADS
+// Blocks run one after another; the threads of a block run together as host
+// threads.  __syncthreads is a barrier over the block's threads that have not
+// returned; a warp exchange (the shuffles) is a barrier over the warp's 32
+// threads, which all take part (full masks), with the values passed through
+// a per-warp table.  Atomics are the compiler's atomic built-ins.
+#include <array>
+#include <atomic>
+#include <barrier>
+#include <memory>
+#include <thread>
+#include <vector>
+
+struct HostBlock {
+  std::unique_ptr<std::barrier<>> block;
+  std::vector<std::unique_ptr<std::barrier<>>> warp;
+  std::vector<std::array<unsigned long long, 32>> xchg;
+};
+inline HostBlock* g_host_block = nullptr;
+
+inline void __syncthreads() { g_host_block->block->arrive_and_wait(); }
+inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
+template <class T>
+inline T __ldcg(const T* p) {
+  T v;
+  __atomic_load(p, &v, __ATOMIC_SEQ_CST);
+  return v;
+}
+
+template <class T>
+inline T host_warp_exchange(T v, unsigned src) {
+  static_assert(sizeof(T) <= 8, "one 64-bit word per lane");
+  const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  unsigned long long bits = 0;
+  std::memcpy(&bits, &v, sizeof(T));
+  g_host_block->xchg[w][lane] = bits;
+  g_host_block->warp[w]->arrive_and_wait();
+  const unsigned long long r = g_host_block->xchg[w][src];
+  g_host_block->warp[w]->arrive_and_wait();
+  T out;
+  std::memcpy(&out, &r, sizeof(T));
+  return out;
+}
+template <class T>
+inline T __shfl_down_sync(unsigned, T v, unsigned o) {
+  const unsigned lane = threadIdx.x & 31u;
+  return host_warp_exchange(v, lane + o < 32u ? lane + o : lane);  // out of range: the lane's own value
+}
+template <class T>
+inline T __shfl_xor_sync(unsigned, T v, int m) {
+  return host_warp_exchange(v, (threadIdx.x & 31u) ^ unsigned(m));
+}
+
+// kernel() runs once per thread of a grid of `blocks` blocks of `threads`
+// threads (a multiple of 32).
+template <class F>
+void host_launch(unsigned blocks, unsigned threads, F kernel) {
+  gridDim = dim3(blocks, 1, 1);
+  blockDim = dim3(threads, 1, 1);
+  for (unsigned b = 0; b < blocks; ++b) {
+    HostBlock hb;
+    hb.block = std::make_unique<std::barrier<>>(std::ptrdiff_t(threads));
+    for (unsigned w = 0; w < threads / 32; ++w) hb.warp.push_back(std::make_unique<std::barrier<>>(32));
+    hb.xchg.resize(threads / 32);
+    g_host_block = &hb;
+    std::vector<std::thread> th;
+    th.reserve(threads);
+    for (unsigned t = 0; t < threads; ++t)
+      th.emplace_back([&, t] {
+        threadIdx = make_uint3(t, 0, 0);
+        blockIdx = make_uint3(b, 0, 0);
+        kernel();
+        hb.block->arrive_and_drop();  // a returned thread is no longer waited for
+      });
+    for (auto& x : th) x.join();
+    g_host_block = nullptr;
+  }
+}
+
+#define atomicAdd(p, v) host_atomic_add_any(p, v)
+template <class T, class V>
+inline T host_atomic_add_any(T* p, V v) { return __atomic_fetch_add(p, T(v), __ATOMIC_SEQ_CST); }
+#endif

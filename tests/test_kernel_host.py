@@ -1,9 +1,12 @@
-"""CPU parity of the kernels' device code: csrc/tracer.cuh's advect_node and
-csrc/adjoint_kernels.cuh's adjoint kernels, compiled with g++
-(tests/cuda_host_shim.h stands in for the CUDA built-ins) and run thread by
-thread on the host (tests/kernel_host_check.cpp, tests/adjoint_host_check.cpp),
-against the oracle on the same seeded inputs, under AddressSanitizer and
-UndefinedBehaviorSanitizer.  No GPU: this checks the kernel source's logic
+"""CPU parity of the kernels' device code: csrc/tracer.cuh's advect_node,
+csrc/adjoint_kernels.cuh's adjoint kernels and the diffusion operator's
+kernels of csrc/diffusion.cu, compiled with g++ (tests/cuda_host_shim.h stands
+in for the CUDA built-ins) and run on the host -- one thread at a time
+(tests/kernel_host_check.cpp, tests/adjoint_host_check.cpp), or each block's
+threads together where the kernels use barriers and warp shuffles
+(tests/diffusion_host_kernels.cpp) -- against the oracle on the same seeded
+inputs, under AddressSanitizer and UndefinedBehaviorSanitizer (and
+ThreadSanitizer for the block-parallel diffusion passes).  No GPU: this checks the kernel source's logic
 (location, hand-off between macros, tie decisions, P1 / P2 stencils,
 interface owners) and its memory accesses wherever a GPU is not available; the
 GPU parity tests check the compiled kernels themselves.
@@ -32,14 +35,27 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
 
 
-def _build(tmp_path_factory, name):
+def _build(tmp_path_factory, name, extra=(), tsan=False):
     gxx = shutil.which("g++")
     if gxx is None or not os.path.exists(os.path.join(CUDA, "include", "cuda_runtime.h")):
         pytest.skip("g++ or the CUDA headers not found")
     build_library()
-    out = str(tmp_path_factory.mktemp(name) / name)
-    cmd = [gxx, "-std=c++17", "-O0", "-g", "-fno-omit-frame-pointer",
-           "-fsanitize=address,undefined,float-cast-overflow", "-fno-sanitize=shift-base", "-fno-sanitize-recover=all",
+    tmp = tmp_path_factory.mktemp(name + ("_tsan" if tsan else ""))
+    out = str(tmp / name)
+    if name == "diffusion_host_kernels":
+        # the part of diffusion.cu before the device set-up: kernels and
+        # host-built structures, no launches
+        with open(os.path.join(PKG, "csrc", "diffusion.cu")) as f:
+            src = f.read()
+        mark = "elm_status build_diffusion(elm_mesh_s* me"
+        assert mark in src, "diffusion.cu no longer has the expected layout"
+        with open(str(tmp / "diffusion_front.cuh"), "w") as f:
+            f.write("#pragma once\n" + src[:src.index(mark)] + "}  // namespace elm\n")
+        extra = list(extra) + ["-I", str(tmp), "-std=c++20", "-DCUDA_HOST_THREADS", "-pthread"]
+    sanitize = (["-fsanitize=thread"] if tsan else
+                ["-fsanitize=address,undefined,float-cast-overflow", "-fno-sanitize=shift-base",
+                 "-fno-sanitize-recover=all"])
+    cmd = [gxx, "-std=c++17", "-O0", "-g", "-fno-omit-frame-pointer", *extra, *sanitize,
            "-I", os.path.join(CUDA, "include"), "-I", os.path.join(ROOT, "include"), "-I", os.path.join(PKG, "csrc"),
            "-I", os.path.join(ROOT, "tests"), "-include", os.path.join(ROOT, "tests", "cuda_host_shim.h"),
            os.path.join(ROOT, "tests", name + ".cpp"), "-o", out,
@@ -57,6 +73,16 @@ def exe(tmp_path_factory):
 @pytest.fixture(scope="module")
 def adj_exe(tmp_path_factory):
     return _build(tmp_path_factory, "adjoint_host_check")
+
+
+@pytest.fixture(scope="module")
+def diff_exe(tmp_path_factory):
+    return _build(tmp_path_factory, "diffusion_host_kernels")
+
+
+@pytest.fixture(scope="module")
+def diff_exe_tsan(tmp_path_factory):
+    return _build(tmp_path_factory, "diffusion_host_kernels", tsan=True)
 
 
 class HostMesh:
@@ -380,3 +406,62 @@ def test_adjoint_code_non_finite_velocity(adj_exe, tmp_path):
         _host_adjoint(adj_exe, tmp_path, v, m, 2, "fp64", 2, T, u, None, g, 0.1, 2)
     msg = str(e.value)
     assert "status flags" in msg and "runtime error" not in msg and "AddressSanitizer" not in msg
+
+
+def _host_diffusion(exe, tmp, hm, x, alpha, scale, cg):
+    v, m = hm.v, hm.m
+    hd = np.array([v.shape[1], v.shape[0], m.shape[0], hm.level, 0 if hm.precision == "fp64" else 1, hm.order,
+                   int(cg)], dtype=np.int64)
+    fin, fout = str(tmp / "d_in.bin"), str(tmp / "d_out.bin")
+    with open(fin, "wb") as f:
+        for a in (hd, np.array([alpha, scale]), np.ascontiguousarray(v, np.float64), np.ascontiguousarray(m, np.int64),
+                  hm.storage(x)):
+            f.write(a.tobytes())
+    r = subprocess.run([exe, fin, fout], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "ThreadSanitizer" not in r.stderr, r.stderr
+    return np.fromfile(fout, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# The diffusion operator (tests/diffusion_host_kernels.cpp): k_stencil and
+# k_face_rows, each block's threads run together (barriers, warp shuffles, the
+# last block's completion of the p.q sum), against the oracle's assembled
+# mass and stiffness matrices.
+
+@pytest.mark.parametrize("mesh,level,order,precision,cg", [
+    ("cube", 2, 2, "fp64", False), ("cube", 3, 1, "fp64", False), ("square", 3, 2, "fp64", False),
+    ("cube_block", 1, 2, "fp64", False), ("cube", 2, 2, "fp32", False),
+    ("cube", 2, 2, "fp64", True), ("cube_block", 1, 2, "fp64", True), ("square", 3, 1, "fp32", True)])
+def test_diffusion_operator_code(diff_exe, tmp_path, mesh, level, order, precision, cg):
+    """y = scale (M + alpha A) x at every node off the Dirichlet boundary (and
+    y = 0 on it); in the CG form also p.q = x . y over those nodes, summed by
+    the kernels' fixed-order reduction."""
+    v, m = mesh_for(mesh)
+    om = oracle.OracleMesh(v, m, level, order=order)
+    hm = HostMesh(v, m, level, precision, order)
+    x = _rounded(np.random.default_rng(3).standard_normal(om.n_nodes), precision)
+    alpha, scale = 0.37, 1.3
+    out = _host_diffusion(diff_exe, tmp_path, hm, x, alpha, scale, cg)
+    y, pq = hm.unique(out[:-1]), out[-1]
+    M, A = om.assemble()
+    ref = scale * (M @ x + alpha * (A @ x))
+    bnd = om.boundary()
+    tol = 1e-13 if precision == "fp64" else 1e-5
+    assert np.abs(y - ref)[~bnd].max() <= tol * np.abs(ref[~bnd]).max()
+    assert np.all(y[bnd] == 0)
+    if cg:
+        pq_ref = x[~bnd] @ ref[~bnd]
+        assert abs(pq - pq_ref) <= tol * (np.abs(x[~bnd]) @ np.abs(ref[~bnd]))
+
+
+@pytest.mark.parametrize("mesh,level,order", [("cube", 2, 2), ("cube_block", 1, 2)])
+def test_diffusion_operator_code_has_no_data_race(diff_exe_tsan, tmp_path, mesh, level, order):
+    """The same passes in their CG form under ThreadSanitizer: no data race
+    between the threads of a block (shared-memory tables, warp exchanges, the
+    last block's reduction)."""
+    v, m = mesh_for(mesh)
+    om = oracle.OracleMesh(v, m, level, order=order)
+    hm = HostMesh(v, m, level, "fp64", order)
+    x = np.random.default_rng(3).standard_normal(om.n_nodes)
+    _host_diffusion(diff_exe_tsan, tmp_path, hm, x, 0.37, 1.3, True)
