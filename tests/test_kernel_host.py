@@ -1,12 +1,14 @@
 """CPU parity of the kernels' device code: csrc/tracer.cuh's advect_node,
-csrc/adjoint_kernels.cuh's adjoint kernels and the diffusion operator's
-kernels of csrc/diffusion.cu, compiled with g++ (tests/cuda_host_shim.h stands
-in for the CUDA built-ins) and run on the host -- one thread at a time
-(tests/kernel_host_check.cpp, tests/adjoint_host_check.cpp), or each block's
-threads together where the kernels use barriers and warp shuffles
-(tests/diffusion_host_kernels.cpp) -- against the oracle on the same seeded
-inputs, under AddressSanitizer and UndefinedBehaviorSanitizer (and
-ThreadSanitizer for the block-parallel diffusion passes).  No GPU: this checks the kernel source's logic
+csrc/adjoint_kernels.cuh's adjoint kernels, the batched persistent kernel of
+csrc/advect.cu and the diffusion operator's kernels of csrc/diffusion.cu,
+compiled with g++ (tests/cuda_host_shim.h stands in for the CUDA built-ins)
+and run on the host -- one thread at a time (tests/kernel_host_check.cpp,
+tests/adjoint_host_check.cpp), or each block's threads together where the
+kernels use barriers, warp shuffles or a shared work counter
+(tests/batch_host_check.cpp, tests/diffusion_host_kernels.cpp) -- against the
+oracle on the same seeded inputs, under AddressSanitizer and
+UndefinedBehaviorSanitizer (and ThreadSanitizer for the block-parallel
+kernels).  No GPU: this checks the kernel source's logic
 (location, hand-off between macros, tie decisions, P1 / P2 stencils,
 interface owners) and its memory accesses wherever a GPU is not available; the
 GPU parity tests check the compiled kernels themselves.
@@ -52,6 +54,15 @@ def _build(tmp_path_factory, name, extra=(), tsan=False):
         with open(str(tmp / "diffusion_front.cuh"), "w") as f:
             f.write("#pragma once\n" + src[:src.index(mark)] + "}  // namespace elm\n")
         extra = list(extra) + ["-I", str(tmp), "-std=c++20", "-DCUDA_HOST_THREADS", "-pthread"]
+    if name == "batch_host_check":
+        # the part of advect.cu before its launch functions: the kernels
+        with open(os.path.join(PKG, "csrc", "advect.cu")) as f:
+            src = f.read()
+        mark = "template <int D, class R, bool STEADY, int P, int MODE>\ncudaError_t launch_k("
+        assert mark in src, "advect.cu no longer has the expected layout"
+        with open(str(tmp / "advect_front.cuh"), "w") as f:
+            f.write("#pragma once\n" + src[:src.index(mark)] + "}  // namespace\n}  // namespace elm\n")
+        extra = list(extra) + ["-I", str(tmp), "-std=c++20", "-DCUDA_HOST_THREADS", "-pthread"]
     sanitize = (["-fsanitize=thread"] if tsan else
                 ["-fsanitize=address,undefined,float-cast-overflow", "-fno-sanitize=shift-base",
                  "-fno-sanitize-recover=all"])
@@ -83,6 +94,16 @@ def diff_exe(tmp_path_factory):
 @pytest.fixture(scope="module")
 def diff_exe_tsan(tmp_path_factory):
     return _build(tmp_path_factory, "diffusion_host_kernels", tsan=True)
+
+
+@pytest.fixture(scope="module")
+def batch_exe(tmp_path_factory):
+    return _build(tmp_path_factory, "batch_host_check")
+
+
+@pytest.fixture(scope="module")
+def batch_exe_tsan(tmp_path_factory):
+    return _build(tmp_path_factory, "batch_host_check", tsan=True)
 
 
 class HostMesh:
@@ -465,3 +486,69 @@ def test_diffusion_operator_code_has_no_data_race(diff_exe_tsan, tmp_path, mesh,
     hm = HostMesh(v, m, level, "fp64", order)
     x = np.random.default_rng(3).standard_normal(om.n_nodes)
     _host_diffusion(diff_exe_tsan, tmp_path, hm, x, 0.37, 1.3, True)
+
+
+# ---------------------------------------------------------------------------
+# The batched persistent kernel (tests/batch_host_check.cpp): k_advect_batch,
+# each block's threads run together (the shared work-item fetch), over a mix
+# of instances.
+
+BATCH = [("square", 3, "rotation", 1.5, 1, True), ("cube", 2, "fourier", 4.0, 2, False),
+         ("cube_block", 1, "fourier", 6.0, 1, True), ("square_block", 2, "rotation", 2.0, 2, True),
+         ("cube", 3, "cellular", 4.0, 1, True)]
+
+
+def _batch_inputs(precision):
+    out = []
+    for k, (mesh, level, vel, cfl, n_sub, steady) in enumerate(BATCH):
+        v, m = mesh_for(mesh)
+        om = oracle.OracleMesh(v, m, level)
+        hm = HostMesh(v, m, level, precision, 2)
+        x = om.coords
+        u = _rounded(velocity_for(vel, x), precision)
+        u1 = u if steady else _rounded(inputs.random_fourier(x, seed=50 + k), precision)
+        T = _rounded(scalar_for("gauss", x), precision)
+        out.append((om, hm, u, u1, T, inputs.dt_for_cfl(cfl, level, u), n_sub, steady))
+    return out
+
+
+def _host_batch(exe, tmp, precision, inst, chunks_per_item, blocks):
+    parts = [np.array([len(inst), 0 if precision == "fp64" else 1, chunks_per_item, blocks], np.int64)]
+    for om, hm, u, u1, T, dt, n_sub, steady in inst:
+        v, m = hm.v, hm.m
+        parts += [np.array([v.shape[1], v.shape[0], m.shape[0], hm.level, int(steady), n_sub], np.int64),
+                  np.array([dt]), np.ascontiguousarray(v, np.float64), np.ascontiguousarray(m, np.int64),
+                  hm.storage(u), hm.storage(u1), hm.storage(T)]
+    fin, fout = str(tmp / "b_in.bin"), str(tmp / "b_out.bin")
+    with open(fin, "wb") as f:
+        for a in parts:
+            f.write(a.tobytes())
+    r = subprocess.run([exe, fin, fout], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "ThreadSanitizer" not in r.stderr, r.stderr
+    out = np.fromfile(fout, dtype=np.float64)
+    res, o = [], 0
+    for _, hm, *_rest in inst:
+        res.append(out[o:o + hm.gm.n_nodes])
+        o += hm.gm.n_nodes
+    return res
+
+
+@pytest.mark.parametrize("precision,chunks_per_item,blocks", [("fp64", 1, 3), ("fp64", 4, 2), ("fp32", 2, 5)])
+def test_batch_kernel_code(batch_exe, exe, tmp_path, precision, chunks_per_item, blocks):
+    """Every instance of the batch equals its own single-instance host step bit
+    for bit, and the oracle at the usual tolerance."""
+    inst = _batch_inputs(precision)
+    got = _host_batch(batch_exe, tmp_path, precision, inst, chunks_per_item, blocks)
+    for (om, hm, u, u1, T, dt, n_sub, steady), g in zip(inst, got):
+        single = _host_call(exe, tmp_path, hm, "step", T, u, None if steady else u1, dt, n_sub)
+        assert np.array_equal(g, single)
+        ref = om.advect(T, u, dt, n_sub, u_new=None if steady else u1)
+        assert np.abs(hm.unique(g) - ref).max() <= TOL[precision] * np.abs(T).max()
+
+
+def test_batch_kernel_code_has_no_data_race(batch_exe_tsan, tmp_path):
+    """The persistent work fetch (one thread takes the next item from the
+    shared counter, the block reads it after a barrier) under ThreadSanitizer,
+    with more blocks than the work needs."""
+    _host_batch(batch_exe_tsan, tmp_path, "fp64", _batch_inputs("fp64"), 1, 6)
