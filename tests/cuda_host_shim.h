@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>  // vector types (float2, int4, ...), dim3, uint3
 
 #include <climits>
+#include <cstdlib>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -184,6 +185,7 @@ inline T __shfl_xor_sync(unsigned, T v, int m) {
 // threads (a multiple of 32).
 template <class F>
 void host_launch(unsigned blocks, unsigned threads, F kernel) {
+  if (threads == 0 || threads % 32 != 0) std::abort();  // whole warps only
   gridDim = dim3(blocks, 1, 1);
   blockDim = dim3(threads, 1, 1);
   for (unsigned b = 0; b < blocks; ++b) {
@@ -199,7 +201,12 @@ void host_launch(unsigned blocks, unsigned threads, F kernel) {
         threadIdx = make_uint3(t, 0, 0);
         blockIdx = make_uint3(b, 0, 0);
         kernel();
-        hb.block->arrive_and_drop();  // a returned thread is no longer waited for
+        // a returned thread is no longer waited for, by the block or its warp
+        // (a lane that returns before a warp exchange its warp still makes
+        // leaves that exchange's value undefined, as on the GPU; the results
+        // then differ instead of the emulation hanging)
+        hb.block->arrive_and_drop();
+        hb.warp[t / 32]->arrive_and_drop();
       });
     for (auto& x : th) x.join();
     g_host_block = nullptr;
