@@ -10,9 +10,9 @@
 // with the tables the library uploads (tests/host_mesh_tables.h); the batch's
 // static table, per-call parameters and work list (runs of `chunks_per_item`
 // chunks of one instance) are built as elm_batch_create and elm_batch_advect
-// build them, and every block takes work items from the shared counter until
-// the list is done.  The interface copies of every instance are filled
-// afterwards (k_batch_ghost_copy).
+// build them (the velocity records by k_pack_velocity), and every block takes
+// work items from the shared counter until the list is done.  The interface
+// copies of every instance are filled afterwards by k_batch_ghost_copy.
 //
 // Input file (little-endian): int64 [count, precision (0: FP64, 1: FP32),
 // chunks_per_item, blocks]; per instance int64 [dim, n_vertices, n_macros,
@@ -65,13 +65,12 @@ int run(std::vector<Instance>& inst, int chunks_per_item, unsigned blocks, std::
     uo[size_t(k)].assign(n * 4, R(0));
     T[size_t(k)].assign(n, R(0));
     Tn[size_t(k)].assign(n, R(0));
-    for (size_t s = 0; s < n; ++s) {
-      for (int r = 0; r < d; ++r) {
-        un[size_t(k)][s * 4 + r] = R(I.un[s * d + r]);
-        uo[size_t(k)][s * 4 + r] = R(I.uo[s * d + r]);
-      }
-      T[size_t(k)][s] = R(I.T[s]);
-    }
+    // the instance's velocity records, as elm_set_velocity packs them
+    std::vector<R> vn(I.un.begin(), I.un.end()), vo(I.uo.begin(), I.uo.end());
+    const unsigned pb = unsigned((n + 255) / 256);
+    host_launch(pb, 256, [&] { k_pack_velocity<R>(vn.data(), un[size_t(k)].data(), int64_t(n), d); });
+    host_launch(pb, 256, [&] { k_pack_velocity<R>(vo.data(), uo[size_t(k)].data(), int64_t(n), d); });
+    for (size_t s = 0; s < n; ++s) T[size_t(k)][s] = R(I.T[s]);
     st[size_t(k)] = BatchStatic{me->geo.data(), I.h.geo32.data(), me->unique_map.data(), I.h.owner_mp.data(),
                                 I.h.chunks.data(), &status[size_t(k)], me->N, int(me->npm), d, 0};
     const double h = I.dt / I.n_sub;
@@ -93,10 +92,15 @@ int run(std::vector<Instance>& inst, int chunks_per_item, unsigned blocks, std::
   B->count = count;
   B->counter = &counter;
   host_launch(blocks, kAdvectThreads, [&] { k_advect_batch<R, 2, 8>(*B); });
+  // every instance's interface copies: (instance, copy slot, owner slot)
+  std::vector<int4> ghosts;
+  for (int k = 0; k < count; ++k)
+    for (const int2& g : inst[size_t(k)].h.ghosts) ghosts.push_back(make_int4(k, g.x, g.y, 0));
+  const int ng = int(ghosts.size());
+  if (ng > 0) host_launch(unsigned((ng + 255) / 256), 256, [&] { k_batch_ghost_copy<R>(*B, ghosts.data(), ng); });
   out.clear();
   int flags = 0;
   for (int k = 0; k < count; ++k) {
-    for (const int2& g : inst[size_t(k)].h.ghosts) Tn[size_t(k)][size_t(g.x)] = Tn[size_t(k)][size_t(g.y)];
     out.insert(out.end(), Tn[size_t(k)].begin(), Tn[size_t(k)].end());
     flags |= int(status[size_t(k)]);
   }

@@ -128,6 +128,23 @@ inline unsigned long long atomicMax(unsigned long long* p, unsigned long long v)
   return o;
 }
 
+#ifndef CUDA_HOST_THREADS
+// kernel() runs once per thread of a grid of `blocks` blocks of `threads`
+// threads, one thread at a time (kernels without barriers or warp exchanges).
+template <class F>
+void host_serial_launch(unsigned blocks, unsigned threads, F kernel) {
+  gridDim = dim3(blocks, 1, 1);
+  blockDim = dim3(threads, 1, 1);
+  for (unsigned b = 0; b < blocks; ++b) {
+    blockIdx = make_uint3(b, 0, 0);
+    for (unsigned t = 0; t < threads; ++t) {
+      threadIdx = make_uint3(t, 0, 0);
+      kernel();
+    }
+  }
+}
+#endif
+
 #ifdef CUDA_HOST_THREADS
 // Blocks run one after another; the threads of a block run together as host
 // threads.  __syncthreads is a barrier over the block's threads that have not

@@ -1,13 +1,15 @@
-// kernel_host_check.cpp -- the advection kernel's device code (csrc/tracer.cuh,
-// advect_node) compiled with g++ and run on the CPU, one node at a time, for a
-// CPU parity check against the oracle (tests/test_kernel_host.py) under
+// kernel_host_check.cpp -- the advection step's kernels (csrc/advect.cu:
+// k_pack_velocity, k_advect, k_ghost_copy; the per-node work in csrc/
+// tracer.cuh) compiled with g++ and run on the CPU, one thread at a time, for
+// a CPU parity check against the oracle (tests/test_kernel_host.py) under
 // AddressSanitizer and UndefinedBehaviorSanitizer.  No GPU.
 //
-// It mirrors k_advect: every entry of the host-built work list (a run of up to
-// 128 nodes of one slab of one macro) is handed to advect_node with the same
-// tables, step constants and packed velocity records the GPU path uses, each
-// interface node is computed once in its owner's slot, and the interface
-// copies are then filled from it (k_ghost_copy).
+// The test writes advect_front.cuh, the part of advect.cu before its launch
+// functions.  The program launches what elm_set_velocity and elm_advect
+// launch, with the same arguments: the velocity records (k_pack_velocity), the
+// per-node kernel over the host-built work list (kAdvectSplit blocks per chunk
+// of up to 128 nodes of one slab of one macro; each interface node computed
+// once, in its owner's slot) and the interface copies (k_ghost_copy).
 //
 // Three per-node modes, as the GPU path has: the step (T^{n+1} = T^n_h(X)),
 // a trace over one interval (from the node, or continued from given offsets;
@@ -29,8 +31,8 @@
 #include <cstdlib>
 #include <vector>
 
+#include "advect_front.cuh"
 #include "host_mesh_tables.h"
-#include "tracer.cuh"
 
 using namespace elm;
 using elm_host_check::HostTables;
@@ -56,41 +58,79 @@ unsigned step(const elm_mesh_s* me, const HostTables& h, const std::vector<doubl
               double dt, int n_sub, std::vector<double>& out) {
   const int64_t n = me->n_storage;
   const size_t ns = static_cast<size_t>(n);
-  std::vector<R> un(ns * 4, R(0)), uo(ns * 4, R(0)), T(ns, R(0)), Tn(ns, R(0)), Din, Dout(ns * D, R(0));
+  // velocity records by k_pack_velocity, as elm_set_velocity makes them
+  std::vector<R> u_un(ns * D), u_uo(ns * D), un(ns * 4, R(0)), uo(ns * 4, R(0)), T(ns, R(0)), Tn(ns, R(0)), Din,
+      Dout(ns * D, R(0));
+  for (size_t s = 0; s < ns * D; ++s) {
+    u_un[s] = R(un_in[s]);
+    u_uo[s] = R(uo_in[s]);
+  }
+  const unsigned pb = unsigned((n + 255) / 256);
+  host_serial_launch(pb, 256, [&] { k_pack_velocity<R>(u_un.data(), un.data(), n, D); });
+  host_serial_launch(pb, 256, [&] { k_pack_velocity<R>(u_uo.data(), uo.data(), n, D); });
+  for (size_t s = 0; s < ns; ++s) T[s] = R(T_in[s]);
   if (D_in) Din.assign(D_in->begin(), D_in->end());
-  for (int64_t s = 0; s < n; ++s) {
-    for (int r = 0; r < D; ++r) {
-      un[size_t(s) * 4 + r] = R(un_in[size_t(s) * D + r]);
-      uo[size_t(s) * 4 + r] = R(uo_in[size_t(s) * D + r]);
-    }
-    T[size_t(s)] = R(T_in[size_t(s)]);
-  }
   unsigned status = 0;
-  NodeJob<R> job{me->geo.data(), un.data(), STEADY ? un.data() : uo.data(), T.data(), Tn.data(), &status,
-                 me->unique_map.data(), h.owner_mp.data(), step_consts<R>(me, dt, n_sub), me->N,
-                 int(me->npm), n_sub};
-  job.skip_ghosts = 1;
-  if constexpr (BLEND == 1) {
-    job.bl = me->blend;
-    job.n_macros = int(me->n_macros);
+  // the launch arguments, as make_args builds them
+  AdvectArgs a{};
+  a.geo = me->geo.data();
+  a.geo32 = h.geo32.data();
+  a.n_macros = int32_t(me->n_macros);
+  a.N = me->N;
+  a.npm = me->npm;
+  a.n_storage = n;
+  for (int r = 0; r < 3; ++r) {
+    a.lo[r] = me->lo[r];
+    a.hi[r] = me->hi[r];
   }
-  job.D_in = D_in ? Din.data() : nullptr;
-  job.D_out = Dout.data();
+  a.u_new = un.data();
+  a.u_old = STEADY ? un.data() : uo.data();
+  a.steady = STEADY;
+  a.T_old = T.data();
+  a.T_new = Tn.data();
+  a.dt = dt;
+  a.n_sub = n_sub;
+  a.status = &status;
+  a.unique_map = me->unique_map.data();
+  a.owner_mp = h.owner_mp.data();
+  a.chunks = h.chunks.data();
+  a.n_chunks = int(h.chunks.size());
+  a.ghosts = h.ghosts.data();
+  a.n_ghosts = int(h.ghosts.size());
+  a.skip_ghosts = 1;
+  a.order = me->order;
+  a.mode = MODE;
+  a.D_in = D_in ? static_cast<const void*>(Din.data()) : nullptr;
+  a.D_out = Dout.data();
+  a.blend = me->blend;
+  const double hs = dt / n_sub;
+  a.k64 = {hs, 0.5 * hs, hs / 6.0, dt, 1.0 / me->M, double(me->N), {0, 0, 0}, {0, 0, 0}};
+  a.k32 = {float(hs), float(0.5 * hs), float(hs / 6.0), float(dt), float(1.0 / me->M), float(me->N), {0, 0, 0},
+           {0, 0, 0}};
+  for (int r = 0; r < 3; ++r) {
+    a.k64.lo[r] = me->lo[r];
+    a.k64.hi[r] = me->hi[r];
+    a.k32.lo[r] = float(me->lo[r]);
+    a.k32.hi[r] = float(me->hi[r]);
+  }
   Tables<R> tab;
   if constexpr (sizeof(R) == 8)
     tab.g = me->geo.data();
   else
     tab.g = h.geo32.data();
-  for (const int4& ck : h.chunks)
-    for (int tid = 0; tid < ck.w; ++tid) advect_node<D, R, STEADY, P, MODE, BLEND>(job, tab, ck, tid);
-  if (MODE == kTrace) {
-    for (const int2& g : h.ghosts)
-      for (int q = 0; q < D; ++q) Dout[size_t(g.x) * D + q] = Dout[size_t(g.y) * D + q];
+  // k_advect over the work list (kAdvectSplit blocks per chunk), then
+  // k_ghost_copy for the interface copies
+  host_serial_launch(unsigned(a.n_chunks) * kAdvectSplit, kStepThreads,
+                     [&] { k_advect<D, R, STEADY, P, MODE, BLEND>(a, tab, 0); });
+  const int ncomp = MODE == kTrace ? D : 1;
+  R* res = MODE == kTrace ? Dout.data() : Tn.data();
+  if (a.n_ghosts > 0)
+    host_serial_launch(unsigned((int64_t(a.n_ghosts) * ncomp + 255) / 256), 256,
+                       [&] { k_ghost_copy<R>(a.ghosts, a.n_ghosts, res, ncomp); });
+  if (MODE == kTrace)
     out.assign(Dout.begin(), Dout.end());
-  } else {
-    for (const int2& g : h.ghosts) Tn[size_t(g.x)] = Tn[size_t(g.y)];
+  else
     out.assign(Tn.begin(), Tn.end());
-  }
   return status;
 }
 

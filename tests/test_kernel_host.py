@@ -54,7 +54,7 @@ def _build(tmp_path_factory, name, extra=(), tsan=False):
         with open(str(tmp / "diffusion_front.cuh"), "w") as f:
             f.write("#pragma once\n" + src[:src.index(mark)] + "}  // namespace elm\n")
         extra = list(extra) + ["-I", str(tmp), "-std=c++20", "-DCUDA_HOST_THREADS", "-pthread"]
-    if name == "batch_host_check":
+    if name in ("kernel_host_check", "batch_host_check"):
         # the part of advect.cu before its launch functions: the kernels
         with open(os.path.join(PKG, "csrc", "advect.cu")) as f:
             src = f.read()
@@ -62,7 +62,9 @@ def _build(tmp_path_factory, name, extra=(), tsan=False):
         assert mark in src, "advect.cu no longer has the expected layout"
         with open(str(tmp / "advect_front.cuh"), "w") as f:
             f.write("#pragma once\n" + src[:src.index(mark)] + "}  // namespace\n}  // namespace elm\n")
-        extra = list(extra) + ["-I", str(tmp), "-std=c++20", "-DCUDA_HOST_THREADS", "-pthread"]
+        extra = list(extra) + ["-I", str(tmp)]
+        if name == "batch_host_check":
+            extra += ["-std=c++20", "-DCUDA_HOST_THREADS", "-pthread"]
     sanitize = (["-fsanitize=thread"] if tsan else
                 ["-fsanitize=address,undefined,float-cast-overflow", "-fno-sanitize=shift-base",
                  "-fno-sanitize-recover=all"])
