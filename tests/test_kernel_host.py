@@ -37,12 +37,9 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
 
 
-def _build(tmp_path_factory, name, extra=(), tsan=False):
+def _build(tmp, name, extra=(), tsan=False):
+    """Builds tests/<name>.cpp into the directory tmp."""
     gxx = shutil.which("g++")
-    if gxx is None or not os.path.exists(os.path.join(CUDA, "include", "cuda_runtime.h")):
-        pytest.skip("g++ or the CUDA headers not found")
-    build_library()
-    tmp = tmp_path_factory.mktemp(name + ("_tsan" if tsan else ""))
     out = str(tmp / name)
     if name == "diffusion_host_kernels":
         # the part of diffusion.cu before the device set-up: kernels and
@@ -78,34 +75,53 @@ def _build(tmp_path_factory, name, extra=(), tsan=False):
     return out
 
 
-@pytest.fixture(scope="module")
-def exe(tmp_path_factory):
-    return _build(tmp_path_factory, "kernel_host_check")
+PROGRAMS = {"exe": ("kernel_host_check", False), "adj_exe": ("adjoint_host_check", False),
+            "diff_exe": ("diffusion_host_kernels", False), "diff_exe_tsan": ("diffusion_host_kernels", True),
+            "batch_exe": ("batch_host_check", False), "batch_exe_tsan": ("batch_host_check", True)}
 
 
 @pytest.fixture(scope="module")
-def adj_exe(tmp_path_factory):
-    return _build(tmp_path_factory, "adjoint_host_check")
+def programs(tmp_path_factory):
+    """All host check programs, built in parallel (each build is one g++ run)."""
+    from concurrent.futures import ThreadPoolExecutor
+    if shutil.which("g++") is None or not os.path.exists(os.path.join(CUDA, "include", "cuda_runtime.h")):
+        pytest.skip("g++ or the CUDA headers not found")
+    build_library()
+    # the directories first, in this thread (tmp_path_factory is not thread-safe)
+    dirs = {k: tmp_path_factory.mktemp(name + ("_tsan" if tsan else "")) for k, (name, tsan) in PROGRAMS.items()}
+    with ThreadPoolExecutor(max_workers=len(PROGRAMS)) as ex:
+        futs = {k: ex.submit(_build, dirs[k], name, (), tsan) for k, (name, tsan) in PROGRAMS.items()}
+        return {k: f.result() for k, f in futs.items()}
 
 
 @pytest.fixture(scope="module")
-def diff_exe(tmp_path_factory):
-    return _build(tmp_path_factory, "diffusion_host_kernels")
+def exe(programs):
+    return programs["exe"]
 
 
 @pytest.fixture(scope="module")
-def diff_exe_tsan(tmp_path_factory):
-    return _build(tmp_path_factory, "diffusion_host_kernels", tsan=True)
+def adj_exe(programs):
+    return programs["adj_exe"]
 
 
 @pytest.fixture(scope="module")
-def batch_exe(tmp_path_factory):
-    return _build(tmp_path_factory, "batch_host_check")
+def diff_exe(programs):
+    return programs["diff_exe"]
 
 
 @pytest.fixture(scope="module")
-def batch_exe_tsan(tmp_path_factory):
-    return _build(tmp_path_factory, "batch_host_check", tsan=True)
+def diff_exe_tsan(programs):
+    return programs["diff_exe_tsan"]
+
+
+@pytest.fixture(scope="module")
+def batch_exe(programs):
+    return programs["batch_exe"]
+
+
+@pytest.fixture(scope="module")
+def batch_exe_tsan(programs):
+    return programs["batch_exe_tsan"]
 
 
 class HostMesh:
