@@ -5,7 +5,8 @@ compiled with g++ (tests/cuda_host_shim.h stands in for the CUDA built-ins)
 and run on the host -- one thread at a time (tests/kernel_host_check.cpp,
 tests/adjoint_host_check.cpp), or each block's threads together where the
 kernels use barriers, warp shuffles or a shared work counter
-(tests/batch_host_check.cpp, tests/diffusion_host_kernels.cpp) -- against the
+(tests/batch_host_check.cpp, tests/diffusion_host_kernels.cpp,
+tests/cg_host_kernels.cpp) -- against the
 oracle on the same seeded inputs, under AddressSanitizer and
 UndefinedBehaviorSanitizer (and ThreadSanitizer for the block-parallel
 kernels).  No GPU: this checks the kernel source's logic
@@ -41,7 +42,7 @@ def _build(tmp, name, extra=(), tsan=False):
     """Builds tests/<name>.cpp into the directory tmp."""
     gxx = shutil.which("g++")
     out = str(tmp / name)
-    if name == "diffusion_host_kernels":
+    if name in ("diffusion_host_kernels", "cg_host_kernels"):
         # the part of diffusion.cu before the device set-up: kernels and
         # host-built structures, no launches
         with open(os.path.join(PKG, "csrc", "diffusion.cu")) as f:
@@ -77,7 +78,8 @@ def _build(tmp, name, extra=(), tsan=False):
 
 PROGRAMS = {"exe": ("kernel_host_check", False), "adj_exe": ("adjoint_host_check", False),
             "diff_exe": ("diffusion_host_kernels", False), "diff_exe_tsan": ("diffusion_host_kernels", True),
-            "batch_exe": ("batch_host_check", False), "batch_exe_tsan": ("batch_host_check", True)}
+            "batch_exe": ("batch_host_check", False), "batch_exe_tsan": ("batch_host_check", True),
+            "cg_exe": ("cg_host_kernels", False), "cg_exe_tsan": ("cg_host_kernels", True)}
 
 
 @pytest.fixture(scope="module")
@@ -122,6 +124,16 @@ def batch_exe(programs):
 @pytest.fixture(scope="module")
 def batch_exe_tsan(programs):
     return programs["batch_exe_tsan"]
+
+
+@pytest.fixture(scope="module")
+def cg_exe(programs):
+    return programs["cg_exe"]
+
+
+@pytest.fixture(scope="module")
+def cg_exe_tsan(programs):
+    return programs["cg_exe_tsan"]
 
 
 class HostMesh:
@@ -618,3 +630,81 @@ def test_batch_kernel_code_has_no_data_race(batch_exe_tsan, tmp_path):
     shared counter, the block reads it after a barrier) under ThreadSanitizer,
     with more blocks than the work needs."""
     _host_batch(batch_exe_tsan, tmp_path, "fp64", _batch_inputs("fp64"), 1, 6)
+
+
+# ---------------------------------------------------------------------------
+# The CG solve's vector kernels (tests/cg_host_kernels.cpp), each block's
+# threads together, in the order one iteration uses them: every kernel's effect
+# against NumPy in the working precision (element-wise results bit for bit:
+# the host build does not fuse multiply-adds, and NumPy rounds each operation
+# the same way), the sums to their rounding.
+
+def _run_cg(exe, tmp, n, precision, blocks, budget=10, alpha=0.3, stop_rr=1e-30, seed=0):
+    rng = np.random.default_rng(seed)
+    R = np.float64 if precision == "fp64" else np.float32
+    r, q, x, v = (rng.standard_normal(n).astype(R).astype(np.float64) for _ in range(4))
+    dinv = (0.5 + rng.random(n)).astype(R).astype(np.float64)
+    v[rng.random(n) < 0.05] = 0.0  # zero diagonal entries
+    bnd = (rng.random(n) < 0.1).astype(np.uint8)
+    act = ((rng.random(n) < 0.75) & (bnd == 0)).astype(np.uint8)
+    fin, fout = str(tmp / "cg_in.bin"), str(tmp / "cg_out.bin")
+    with open(fin, "wb") as f:
+        for a in (np.array([n, 0 if precision == "fp64" else 1, blocks, budget], np.int64),
+                  np.array([alpha, stop_rr]), r, dinv, q, x, v, bnd, act):
+            f.write(np.ascontiguousarray(a).tobytes())
+    res = subprocess.run([exe, fin, fout], capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stdout + res.stderr
+    assert "ThreadSanitizer" not in res.stderr, res.stderr
+    out = np.fromfile(fout, dtype=np.float64)
+    return out, (R, r, dinv, q, x, v, bnd.astype(bool), act.astype(bool), alpha, stop_rr, budget)
+
+
+@pytest.mark.parametrize("n,precision,blocks", [(1237, "fp64", 3), (5000, "fp32", 5), (64, "fp64", 2)])
+def test_cg_vector_kernels_code(cg_exe, tmp_path, n, precision, blocks):
+    out, (R, r, dinv, q, x, v, bnd, act, alpha, stop_rr, budget) = _run_cg(cg_exe, tmp_path, n, precision, blocks)
+    tol = 1e-13 if precision == "fp64" else 1e-5
+    o = 0
+
+    def take(k):
+        nonlocal o
+        a = out[o:o + k]
+        o += k
+        return a
+
+    Rv = lambda a: np.asarray(a, dtype=R)  # noqa: E731
+    r0 = np.where(bnd, R(0), Rv(r))
+    z0 = Rv(dinv) * r0
+    assert np.array_equal(take(n), r0) and np.array_equal(take(n), z0) and np.array_equal(take(n), z0)
+    rz0 = float(np.dot(r0[act].astype(np.float64), z0[act].astype(np.float64)))
+    rr0 = float(np.dot(r0[act].astype(np.float64), r0[act].astype(np.float64)))
+    rz, rr, done = take(3)
+    assert abs(rz - rz0) <= tol * abs(rz0) and abs(rr - rr0) <= tol * rr0 and done == 0
+    al = R(alpha)
+    x1 = Rv(x) + al * z0
+    r1 = r0 - al * Rv(q)
+    z1 = Rv(dinv) * r1
+    assert np.array_equal(take(n), x1) and np.array_equal(take(n), r1) and np.array_equal(take(n), z1)
+    rz1 = float(np.dot(r1[act].astype(np.float64), z1[act].astype(np.float64)))
+    rr1 = float(np.dot(r1[act].astype(np.float64), r1[act].astype(np.float64)))
+    rz_new, rr_u, beta, iters, done = take(5)
+    assert abs(rz_new - rz1) <= tol * abs(rz1) and abs(rr_u - rr1) <= tol * rr1
+    assert abs(beta - rz1 / rz0) <= 4 * tol * abs(rz1 / rz0) and iters == 1 and done == 0
+    p1 = z1 + R(beta) * z0
+    assert np.array_equal(take(n), p1)
+    nrm = take(1)[0]
+    assert abs(nrm - float(np.sum(r1[act].astype(np.float64) ** 2))) <= 1e-13 * rr1
+    with np.errstate(divide="ignore"):
+        d = np.where(bnd | (Rv(v) == 0), R(0), R(1) / Rv(v))
+    assert np.array_equal(take(n), d)
+    xb = np.where(bnd, Rv(v), x1)
+    assert np.array_equal(take(n), xb)
+    r32 = np.where(bnd, np.float32(0), xb.astype(np.float32))
+    assert np.array_equal(take(n), r32) and np.array_equal(take(n), np.zeros(n))
+    assert np.array_equal(take(n), xb.astype(np.float64) + r32.astype(np.float64))
+    assert o == out.size
+
+
+def test_cg_vector_kernels_have_no_data_race(cg_exe_tsan, tmp_path):
+    """The same sequence under ThreadSanitizer (block sums, the last block's
+    completion of the CG update)."""
+    _run_cg(cg_exe_tsan, tmp_path, 3000, "fp64", 4)
