@@ -295,10 +295,11 @@ struct Adjoint {
   // instruction cache (instruction fetch was the largest stall of the
   // unrolled form); the stage arrays go to the stack frame.
   // Keep a single call site: with two inlined copies of this rolled loop in
-  // run() the compiled kernels (nvcc 13.0, sm_103a, at every ptxas
-  // optimisation level and with FMA contraction off) computed wrong velocity
-  // gradients, although the two source forms are equivalent; with one copy,
-  // or the first copy unrolled, they pass every parity test.
+  // run() the compiled kernels (nvcc 13.0, sm_103a; ptxas at -O0 as at its
+  // default level, and with FMA contraction off) computed wrong velocity
+  // gradients, although the two source forms are equivalent (a host build of
+  // both gives bitwise the same sums); with one copy, or the first copy
+  // unrolled, they pass every parity test.
   __device__ void substep(R* d, int j, Stages& st) {
     const R back = to_real<R>(j) * h;
     R k[4][D], acc[D];
