@@ -14,10 +14,12 @@
 // 0).  Dirichlet nodes get no row.  With cg = 1 the passes run as in a CG
 // iteration (kOpCg): y = v, one partial of p.q per block, and the last block
 // of the face-row pass (or of the stencil pass, without face rows) sums all
-// partials in a fixed order into the scalars (p = x).
+// partials in a fixed order into the scalars (p = x).  With cg = 2 they add
+// the diagonal entry of each row instead (kOpDiag, x unused), as the Jacobi
+// preconditioner's set-up runs them.
 //
 // Input file (little-endian): int64 header [dim, n_vertices, n_macros, level,
-// precision (0: FP64, 1: FP32), order, cg], doubles [alpha, scale], vertex
+// precision (0: FP64, 1: FP32), order, cg (0, 1 or 2)], doubles [alpha, scale], vertex
 // coordinates, macro vertices (int64), x [n_storage] (doubles).  Output file:
 // y [n_storage], then p.q (doubles).  Exit status 0, or 1 on bad input.
 #include <cstdio>
@@ -117,7 +119,9 @@ int main(int argc, char** argv) {
   }
   if (!read_n(f, x, size_t(mesh->n_storage))) return 1;
   std::fclose(f);
-  if (cg)
+  if (hd[6] == 2)
+    dispatch<kOpDiag>(mesh, dim, precision, order, x, ab[0], ab[1], out);
+  else if (cg)
     dispatch<kOpCg>(mesh, dim, precision, order, x, ab[0], ab[1], out);
   else
     dispatch<kOpAccum>(mesh, dim, precision, order, x, ab[0], ab[1], out);

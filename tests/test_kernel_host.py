@@ -1,12 +1,14 @@
 """CPU parity of the kernels' device code: csrc/tracer.cuh's advect_node,
 csrc/adjoint_kernels.cuh's adjoint kernels, the batched persistent kernel of
-csrc/advect.cu and the diffusion operator's kernels of csrc/diffusion.cu,
+csrc/advect.cu and the diffusion operator's kernels of csrc/diffusion.cu (the
+stencil and face-row passes, the blended annulus's cell pass and fold, the CG
+vector kernels),
 compiled with g++ (tests/cuda_host_shim.h stands in for the CUDA built-ins)
 and run on the host -- one thread at a time (tests/kernel_host_check.cpp,
 tests/adjoint_host_check.cpp), or each block's threads together where the
 kernels use barriers, warp shuffles or a shared work counter
 (tests/batch_host_check.cpp, tests/diffusion_host_kernels.cpp,
-tests/cg_host_kernels.cpp) -- against the
+tests/blended_diffusion_host_check.cpp, tests/cg_host_kernels.cpp) -- against the
 oracle on the same seeded inputs, under AddressSanitizer and
 UndefinedBehaviorSanitizer (and ThreadSanitizer for the block-parallel
 kernels).  No GPU: this checks the kernel source's logic
@@ -42,7 +44,7 @@ def _build(tmp, name, extra=(), tsan=False):
     """Builds tests/<name>.cpp into the directory tmp."""
     gxx = shutil.which("g++")
     out = str(tmp / name)
-    if name in ("diffusion_host_kernels", "cg_host_kernels"):
+    if name in ("diffusion_host_kernels", "cg_host_kernels", "blended_diffusion_host_check"):
         # the part of diffusion.cu before the device set-up: kernels and
         # host-built structures, no launches
         with open(os.path.join(PKG, "csrc", "diffusion.cu")) as f:
@@ -79,7 +81,9 @@ def _build(tmp, name, extra=(), tsan=False):
 PROGRAMS = {"exe": ("kernel_host_check", False), "adj_exe": ("adjoint_host_check", False),
             "diff_exe": ("diffusion_host_kernels", False), "diff_exe_tsan": ("diffusion_host_kernels", True),
             "batch_exe": ("batch_host_check", False), "batch_exe_tsan": ("batch_host_check", True),
-            "cg_exe": ("cg_host_kernels", False), "cg_exe_tsan": ("cg_host_kernels", True)}
+            "cg_exe": ("cg_host_kernels", False), "cg_exe_tsan": ("cg_host_kernels", True),
+            "blend_diff_exe": ("blended_diffusion_host_check", False),
+            "blend_diff_exe_tsan": ("blended_diffusion_host_check", True)}
 
 
 @pytest.fixture(scope="module")
@@ -134,6 +138,16 @@ def cg_exe(programs):
 @pytest.fixture(scope="module")
 def cg_exe_tsan(programs):
     return programs["cg_exe_tsan"]
+
+
+@pytest.fixture(scope="module")
+def blend_diff_exe(programs):
+    return programs["blend_diff_exe"]
+
+
+@pytest.fixture(scope="module")
+def blend_diff_exe_tsan(programs):
+    return programs["blend_diff_exe_tsan"]
 
 
 class HostMesh:
@@ -554,6 +568,27 @@ def test_diffusion_operator_code(diff_exe, tmp_path, mesh, level, order, precisi
         assert abs(pq - pq_ref) <= tol * (np.abs(x[~bnd]) @ np.abs(ref[~bnd]))
 
 
+@pytest.mark.parametrize("mesh,level,order,precision", [
+    ("cube", 2, 2, "fp64"), ("cube_block", 1, 2, "fp64"), ("square", 3, 1, "fp64"), ("cube", 2, 1, "fp32")])
+def test_diffusion_operator_code_diagonal(diff_exe, tmp_path, mesh, level, order, precision):
+    """The diagonal form of the passes (the Jacobi preconditioner's set-up):
+    y = scale diag(M + alpha A) at every node off the Dirichlet boundary, 0 on
+    it; x is not read (NaN here)."""
+    v, m = mesh_for(mesh)
+    om = oracle.OracleMesh(v, m, level, order=order)
+    hm = HostMesh(v, m, level, precision, order)
+    x = np.full(om.n_nodes, np.nan)
+    alpha, scale = 0.37, 1.3
+    out = _host_diffusion(diff_exe, tmp_path, hm, x, alpha, scale, 2)
+    y = hm.unique(out[:-1])
+    M, A = om.assemble()
+    ref = scale * (M.diagonal() + alpha * A.diagonal())
+    bnd = om.boundary()
+    tol = 1e-13 if precision == "fp64" else 1e-6
+    assert np.abs(y - ref)[~bnd].max() <= tol * np.abs(ref[~bnd]).max()
+    assert np.all(y[bnd] == 0)
+
+
 @pytest.mark.parametrize("mesh,level,order", [("cube", 2, 2), ("cube_block", 1, 2)])
 def test_diffusion_operator_code_has_no_data_race(diff_exe_tsan, tmp_path, mesh, level, order):
     """The same passes in their CG form under ThreadSanitizer: no data race
@@ -564,6 +599,84 @@ def test_diffusion_operator_code_has_no_data_race(diff_exe_tsan, tmp_path, mesh,
     hm = HostMesh(v, m, level, "fp64", order)
     x = np.random.default_rng(3).standard_normal(om.n_nodes)
     _host_diffusion(diff_exe_tsan, tmp_path, hm, x, 0.37, 1.3, True)
+
+
+# ---------------------------------------------------------------------------
+# The blended annulus's operator (tests/blended_diffusion_host_check.cpp): the
+# per-simplex tables, the cell pass k_apply and its fold k_fold_nodes, each
+# block's threads run together, against the oracle's blended mass and
+# stiffness matrices (each side with its own 5 x 5 collapsed Gauss rule).
+
+ANNULUS = (0.5, 1.5, 6, 0.0)
+
+
+def _host_blended_diffusion(exe, tmp, hm, x, alpha, scale, mode):
+    v, m = hm.v, hm.m
+    hd = np.array([v.shape[0], m.shape[0], hm.level, hm.order, mode], dtype=np.int64)
+    fin, fout = str(tmp / "b_in.bin"), str(tmp / "b_out.bin")
+    with open(fin, "wb") as f:
+        for a in (hd, np.array([alpha, scale, *ANNULUS], np.float64), np.ascontiguousarray(v, np.float64),
+                  np.ascontiguousarray(m, np.int64), hm.storage(x)):
+            f.write(a.tobytes())
+    r = subprocess.run([exe, fin, fout], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "ThreadSanitizer" not in r.stderr, r.stderr
+    return np.fromfile(fout, dtype=np.float64)
+
+
+# The stiffness is where the two sides may differ beyond rounding.  Its
+# integrand is rational in the point (the sector parameter of the blending map),
+# and the oracle and the tables collapse their 5 x 5 Gauss rules at different
+# vertices of the simplex, so each has its own quadrature error.  Measured
+# difference of A x, relative to max |A x|: 3.9e-8, 7.9e-10, 1.2e-11, 1.0e-13
+# at levels 1-4 (P2); 3.1e-12, 3.0e-14, 4.7e-15 at levels 2-4 (P1).  That is a
+# fall of about 60 per level, as a quadrature error should fall, down to
+# rounding.  A wrong table entry or a lost contribution would be of order one.
+# The mass is exact on both sides (constant Jacobian determinant), so a
+# mass-only pass (alpha = 0) is held to rounding.
+BLEND_TOL = {(2, 2): 4e-9, (3, 1): 1e-13, (4, 2): 4e-13}
+
+
+@pytest.mark.parametrize("level,order", [(2, 2), (3, 1), (4, 2)])
+@pytest.mark.parametrize("mode", ["mass", "accum", "cg", "diag"])
+def test_blended_diffusion_operator_code(blend_diff_exe, tmp_path, level, order, mode):
+    """mass / accum: y = scale (M + alpha A) x at every node, boundary included
+    (the solver sets the Dirichlet values afterwards; mass: alpha = 0); cg: the
+    same with y = 0 on the boundary and p.q = x . y over the other nodes;
+    diag: y = scale diag(M + alpha A)."""
+    v, m = inputs.annulus_ring(6, 2)
+    om = oracle.OracleMesh(v, m, level, order=order, annulus=ANNULUS)
+    hm = HostMesh(v, m, level, "fp64", order, annulus=ANNULUS)
+    x = np.random.default_rng(5).standard_normal(om.n_nodes)
+    alpha, scale = (0.0 if mode == "mass" else 0.37), 1.3
+    code = {"mass": 0, "accum": 0, "cg": 1, "diag": 2}[mode]
+    out = _host_blended_diffusion(blend_diff_exe, tmp_path, hm, x, alpha, scale, code)
+    y, pq = hm.unique(out[:-1]), out[-1]
+    M, A = om.assemble()
+    bnd = om.boundary()
+    assert bnd.any() and not bnd.all()
+    if mode == "diag":
+        ref = scale * (M.diagonal() + alpha * A.diagonal())
+    else:
+        ref = scale * (M @ x + alpha * (A @ x))
+    tol = 1e-13 if mode == "mass" else BLEND_TOL[(level, order)]
+    if mode == "cg":
+        assert np.abs(y - ref)[~bnd].max() <= tol * np.abs(ref[~bnd]).max()
+        assert np.all(y[bnd] == 0)
+        assert abs(pq - x[~bnd] @ ref[~bnd]) <= tol * (np.abs(x[~bnd]) @ np.abs(ref[~bnd]))
+    else:
+        assert np.abs(y - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_blended_diffusion_operator_code_has_no_data_race(blend_diff_exe_tsan, tmp_path):
+    """The blended passes in their CG form under ThreadSanitizer: no data race
+    between the threads of a block (the cell pass's colour accumulators, the
+    fold's warp exchanges and the last block's reduction)."""
+    v, m = inputs.annulus_ring(6, 2)
+    hm = HostMesh(v, m, 2, "fp64", 2, annulus=ANNULUS)
+    x = np.random.default_rng(5).standard_normal(hm.gm.n_unique)
+    out = _host_blended_diffusion(blend_diff_exe_tsan, tmp_path, hm, x, 0.37, 1.3, 1)
+    assert np.all(np.isfinite(out))
 
 
 # ---------------------------------------------------------------------------
