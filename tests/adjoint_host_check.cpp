@@ -11,7 +11,7 @@
 //
 // Input file (little-endian): int64 header [dim, n_vertices, n_macros, level,
 // precision (0: FP64, 1: FP32), order, steady, n_sub, split], double dt, vertex
-// coordinates, macro vertices (int64; a 3D mesh), then in the storage layout u^n, u^{n+1}
+// coordinates, macro vertices (int64; 2D or 3D), then in the storage layout u^n, u^{n+1}
 // [n_storage * dim], T^n [n_storage] and the incoming gradient dL/dT^{n+1}
 // [n_storage] (doubles).  split = 1 keeps the gradients of u^n and u^{n+1}
 // apart (time-dependent velocity).  Output file: dL/dT^n [n_storage], dL/du^n
@@ -191,12 +191,12 @@ int main(int argc, char** argv) {
   std::fclose(f);
   const HostTables h = host_tables(mesh);
   unsigned status;
-  if (dim != 3) {
-    std::fprintf(stderr, "3D meshes only (the 2D forms are left out to keep the sanitizer build short)\n");
-    return 1;
-  }
-  status = precision == 0 ? dispatch<3, double>(mesh, h, steady, split, uo, un, T, g, dtv[0], n_sub, out)
-                          : dispatch<3, float>(mesh, h, steady, split, uo, un, T, g, dtv[0], n_sub, out);
+  if (dim == 3)
+    status = precision == 0 ? dispatch<3, double>(mesh, h, steady, split, uo, un, T, g, dtv[0], n_sub, out)
+                            : dispatch<3, float>(mesh, h, steady, split, uo, un, T, g, dtv[0], n_sub, out);
+  else
+    status = precision == 0 ? dispatch<2, double>(mesh, h, steady, split, uo, un, T, g, dtv[0], n_sub, out)
+                            : dispatch<2, float>(mesh, h, steady, split, uo, un, T, g, dtv[0], n_sub, out);
   elm_mesh_destroy(mesh);
   FILE* o = std::fopen(argv[2], "wb");
   if (!o || std::fwrite(out.data(), sizeof(double), out.size(), o) != out.size()) return 1;

@@ -488,6 +488,29 @@ def test_adjoint_code_velocity_gradient(adj_exe, tmp_path, kind, n_sub, order):
         assert abs((gU * d).sum() - g @ jvp) <= 1e-9 * (np.abs(g) @ np.abs(jvp) + 1e-30)
 
 
+@pytest.mark.parametrize("precision,n_sub,order", [("fp64", 1, 2), ("fp64", 2, 2), ("fp32", 1, 2), ("fp64", 1, 1)])
+def test_adjoint_code_2d(adj_exe, tmp_path, precision, n_sub, order):
+    """The 2D forms: dL/dT^n against the oracle's transpose, and (FP64)
+    <dL/du, v> against its forward-mode derivative on 4 random directions."""
+    v, m = mesh_for("square")
+    level = 5 if order == 2 else 6
+    om = oracle.OracleMesh(v, m, level, order=order)
+    x = om.coords
+    u = _rounded(inputs.random_fourier(x, seed=9) + 0.2 * inputs.uniform_field(x, [0.31, -0.17]), precision)
+    T = _rounded(inputs.gaussian(x, (0.45, 0.55), 0.15), precision)
+    dt = inputs.dt_for_cfl(4.0, level, u)
+    rng = np.random.default_rng(4)
+    g = rng.standard_normal(om.n_nodes)
+    gT, gU, _ = _host_adjoint(adj_exe, tmp_path, v, m, level, precision, order, T, u, None, g, dt, n_sub)
+    ref = om.advect_transpose(g, u, dt, n_sub)
+    assert np.abs(gT - ref).max() <= TOL[precision] * np.abs(ref).max() * 10
+    if precision == "fp64":
+        for _ in range(4):
+            d = rng.standard_normal(u.shape)
+            _, jvp = om.advect_jvp(T, u, d, dt, n_sub)
+            assert abs((gU * d).sum() - g @ jvp) <= 1e-9 * (np.abs(g) @ np.abs(jvp) + 1e-30)
+
+
 def test_adjoint_code_time_dependent_split(adj_exe, tmp_path):
     v, m = mesh_for("cube")
     om = oracle.OracleMesh(v, m, 3)
