@@ -1,7 +1,7 @@
 // cg_host_kernels.cpp -- the diffusion solve's vector kernels (csrc/
 // diffusion.cu: k_cg_start, k_cg_begin, k_cg_update with the last block's
 // completion, k_cg_direction, k_norm2, k_sum_into, k_invert_diag,
-// k_set_boundary, k_residual_to_float, k_add_correction) compiled with g++ and
+// k_set_boundary, k_residual_to_float, k_add_correction, k_copy) compiled with g++ and
 // run on the CPU, each block's threads together (CUDA_HOST_THREADS), under
 // AddressSanitizer / UndefinedBehaviorSanitizer or ThreadSanitizer, in the
 // order one CG iteration uses them, for a check of each kernel's effect
@@ -14,7 +14,8 @@
 // the given alpha and q) x, r, z and the scalars (rz_new, rr, beta, iters,
 // done); p after k_cg_direction; |r|^2 over act (k_norm2 + k_sum_into);
 // k_invert_diag of v; k_set_boundary(x, v); k_residual_to_float of x (r32,
-// d32); x + double(r32) (k_add_correction).
+// d32); x + double(r32) (k_add_correction); a copy of k_set_boundary's
+// result (k_copy).
 #include <cstdio>
 #include <vector>
 
@@ -84,6 +85,9 @@ std::vector<double> run(int64_t n, unsigned blocks, int budget, double alpha, do
   out.insert(out.end(), d32.begin(), d32.end());
   host_launch(eb, 256, [&] { k_add_correction(x64.data(), r32.data(), n); });
   out.insert(out.end(), x64.begin(), x64.end());
+  std::vector<R> cp(ns, R(0));
+  host_launch(eb, 256, [&] { k_copy<R>(cp.data(), xb.data(), n); });
+  put(cp);
   return out;
 }
 

@@ -837,6 +837,7 @@ def test_cg_vector_kernels_code(cg_exe, tmp_path, n, precision, blocks):
     r32 = np.where(bnd, np.float32(0), xb.astype(np.float32))
     assert np.array_equal(take(n), r32) and np.array_equal(take(n), np.zeros(n))
     assert np.array_equal(take(n), xb.astype(np.float64) + r32.astype(np.float64))
+    assert np.array_equal(take(n), xb)
     assert o == out.size
 
 
