@@ -12,14 +12,15 @@
 // chunks of one instance) are built as elm_batch_create and elm_batch_advect
 // build them (the velocity records by k_pack_velocity), and every block takes
 // work items from the shared counter until the list is done.  The interface
-// copies of every instance are filled afterwards by k_batch_ghost_copy.
+// copies of every instance are filled afterwards by k_batch_ghost_copy, and
+// k_gather reads each result back in node order (the owner copies).
 //
 // Input file (little-endian): int64 [count, precision (0: FP64, 1: FP32),
 // chunks_per_item, blocks]; per instance int64 [dim, n_vertices, n_macros,
 // level, steady, n_sub], double dt, vertex coordinates, macro vertices
 // (int64), u^n, u^{n+1} [n_storage * dim], T^n [n_storage] (doubles; P2
-// elements).  Output file: every instance's T^{n+1} [n_storage], in order
-// (doubles).  Exit status 0, 1 on bad input, 2 on a device-side status flag.
+// elements).  Output file: every instance's T^{n+1} [n_storage], in order,
+// then every instance's T^{n+1} [n_unique] in node order (doubles).  Exit status 0, 1 on bad input, 2 on a device-side status flag.
 #include <cstdio>
 #include <memory>
 #include <vector>
@@ -103,6 +104,15 @@ int run(std::vector<Instance>& inst, int chunks_per_item, unsigned blocks, std::
   for (int k = 0; k < count; ++k) {
     out.insert(out.end(), Tn[size_t(k)].begin(), Tn[size_t(k)].end());
     flags |= int(status[size_t(k)]);
+  }
+  // every instance's result in node order: the owner copies, by k_gather
+  for (int k = 0; k < count; ++k) {
+    const elm_mesh_s* me = inst[size_t(k)].me;
+    const int64_t nu = me->n_unique;
+    std::vector<R> Tu(static_cast<size_t>(nu), R(0));
+    host_launch(unsigned((nu + 255) / 256), 256,
+                [&] { k_gather<R>(Tn[size_t(k)].data(), Tu.data(), me->owner.data(), nu, 1); });
+    out.insert(out.end(), Tu.begin(), Tu.end());
   }
   return flags;
 }

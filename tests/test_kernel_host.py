@@ -745,6 +745,13 @@ def _host_batch(exe, tmp, precision, inst, chunks_per_item, blocks):
     for _, hm, *_rest in inst:
         res.append(out[o:o + hm.gm.n_nodes])
         o += hm.gm.n_nodes
+    # each result read back in node order (k_gather over the owner copies):
+    # every storage copy of a node holds the gathered value
+    for g, (_, hm, *_rest) in zip(res, inst):
+        gu = out[o:o + hm.gm.n_unique]
+        o += hm.gm.n_unique
+        assert np.array_equal(gu[hm.umap], g)
+    assert o == out.size
     return res
 
 
